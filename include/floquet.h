@@ -1,0 +1,174 @@
+/*
+ * floquet.h - C ABI of the GB300 (sm_103a) Magnus-Chebyshev Floquet propagator.
+ *
+ * Method (arXiv:1508.07621): the Floquet operator U_T of H(t) = H0 + f(t) H1 (Eq. 13) is
+ * built by propagating the N x N identity over one period T (§3, last paragraph) through a
+ * chain of M single-step propagators (Eq. 9).  Each step uses the 4th-order midpoint Magnus
+ * exponent Omega_m = a_m H0 + b_m H1 + c_m i[H0,H1] (Eq. 14 truncated after its leading
+ * commutator; a_m = h, b_m = h f + h^3 f''/24, c_m = h^3 f'/12 at the step midpoint), shifted
+ * and rescaled to spectrum [-1, 1] (Eq. 11), and applies exp(-i Omega_m) by the Chebyshev
+ * recurrence (Eq. 10) with Bessel weights a_0 = J_0(R), a_l = 2 J_l(R), R = h Delta E (Eq. 12).
+ * hbar = 1 throughout.
+ *
+ * Conventions
+ *  - Complex numbers at the boundary are interleaved (re, im) doubles, i.e. C99 double
+ *    complex / torch.complex128.
+ *  - A "state block" of ncols states is ncols x N, row-major: row r is state r, a contiguous
+ *    length-N vector (the paper stores its initial vectors as rows, §5).
+ *  - U_T is returned as the N x N row-major matrix U[i][j] = <i|U_T|j>: column j is basis
+ *    vector j propagated over the period.
+ *  - U_T = U_M ... U_1 (the earliest step acts first on column states).
+ *
+ * Ownership and memory
+ *  - Every device pointer argument is allocated and owned by the caller.  The library never
+ *    frees caller memory.  Device memory the library allocates itself is limited to what
+ *    floquet_plan_create makes (operators, per-step scalars, a status word); it is released
+ *    by floquet_plan_destroy.  All scratch space is the caller's workspace, whose size is
+ *    given by floquet_workspace_size / floquet_grad_workspace_size.
+ *  - Host arrays passed to floquet_plan_create are copied; the caller keeps ownership.
+ *
+ * Streams and errors
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Compute
+ *    calls only enqueue work on it and return without synchronising, except where stated.
+ *  - Every call returns an fq_status.  Argument errors are reported before any work is
+ *    enqueued.  Device-side checks (a propagated entry larger than the bound implied by
+ *    unitarity, or NaN) set bits in a per-plan status word; floquet_check_status
+ *    synchronises the stream, returns FQ_EBOUND if any bit was set, and clears it.  The
+ *    library never traps or aborts.  floquet_last_error returns a message for the last
+ *    failing call of the calling thread.
+ *  - Plans are not thread-safe: one plan must not be used by two concurrent calls.
+ */
+#ifndef FLOQUET_H
+#define FLOQUET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fq_status {
+  FQ_OK = 0,
+  FQ_EINVAL = 1,        /* invalid argument (NULL pointer, bad size, workspace too small) */
+  FQ_ENOMEM = 2,        /* device or host allocation failed in floquet_plan_create */
+  FQ_ECUDA = 3,         /* a CUDA runtime call failed; see floquet_last_error */
+  FQ_EBOUND = 4,        /* device check: |entry| above the unitarity bound, or NaN */
+  FQ_ETIMEOUT = 5,      /* a bounded device wait gave up */
+  FQ_EUNSUPPORTED = 6   /* valid request this build does not implement */
+} fq_status;
+
+typedef enum fq_format {
+  FQ_DENSE = 0,         /* H0, H1 dense real-symmetric N x N, row-major */
+  FQ_TRIDIAG = 1        /* H0 real-symmetric tridiagonal, H1 real diagonal */
+} fq_format;
+
+typedef enum fq_precision {
+  FQ_FP64 = 0,          /* every product and accumulation in FP64 (baseline path) */
+  FQ_FP32 = 1,          /* FP32 storage and FP32 arithmetic (tridiagonal format) */
+  FQ_BF16X3 = 2,        /* dense: 2-slice BF16 split, products hi*hi + hi*lo + lo*hi, FP32 accumulate */
+  FQ_BF16X6 = 3         /* dense: 3-slice BF16 split, 6 slice products, FP32 accumulate */
+} fq_precision;
+
+typedef enum fq_drive_kind {
+  FQ_DRIVE_COS = 0,       /* f(t) = f_dc + f_ac cos(omega t + phi0) */
+  FQ_DRIVE_PIECEWISE = 1  /* f constant on each step; values given per call (floquet_grad) */
+} fq_drive_kind;
+
+typedef enum fq_kernel {
+  FQ_KERNEL_AUTO = 0,       /* resident kernel when it applies, else streaming */
+  FQ_KERNEL_STREAM = 1,     /* tridiagonal: one launch per Chebyshev term, states in HBM */
+  FQ_KERNEL_RESIDENT = 2    /* tridiagonal FP32: one CTA per state runs the whole chain on chip
+                               (N <= 10240, L <= 128); FQ_EUNSUPPORTED otherwise */
+} fq_kernel;
+
+/* Problem statement (Eq. 13, §3): everything floquet_plan_create needs. */
+typedef struct fq_problem {
+  int32_t n;                /* Hilbert-space dimension N >= 1 */
+  int32_t format;           /* fq_format */
+  const double* h0;         /* DENSE: N*N row-major symmetric; TRIDIAG: diagonal, N values */
+  const double* h0_off;     /* TRIDIAG: H0[i+1][i] = H0[i][i+1], N-1 values; DENSE: ignored */
+  const double* h1;         /* DENSE: N*N row-major symmetric; TRIDIAG: diagonal, N values */
+  double period;            /* T > 0 */
+  int32_t steps;            /* M >= 1; h = T/M */
+  int32_t drive_kind;       /* fq_drive_kind */
+  double f_dc, f_ac, omega, phi0;   /* FQ_DRIVE_COS parameters */
+  const double* f_steps;    /* FQ_DRIVE_PIECEWISE: M amplitudes used to freeze the spectral
+                               bounds (range widened by 10%); later calls pass their own f_m */
+  double cheb_tol;          /* truncation |J_{L+1}(R)| < tol; <= 0 selects 1e-14 */
+  double e_min, e_max;      /* if e_max > e_min: caller's bounds of Omega/h, used as given */
+  int32_t precision;        /* fq_precision */
+  int32_t checkpoint_stride;/* floquet_grad: X_m stored every s steps; <= 0 selects 16 */
+  int32_t kernel;           /* fq_kernel: which tridiagonal kernel family runs the chain */
+} fq_problem;
+
+typedef struct fq_plan fq_plan;
+
+/* Host-computed planning results (stage a1): bounds (Eq. 11), R and L (Eq. 12). */
+typedef struct fq_plan_info {
+  int32_t n, steps, L, precision, format, drive_kind;
+  double h, e_min, e_max, beta, delta_e, R;
+} fq_plan_info;
+
+/* Host planning + upload (§3: Magnus scalars, [H0,H1] computed once, bounds, Bessel
+ * coefficients; Algorithm 1 steps 1-4).  Uses the current CUDA device; allocates the plan's
+ * device copies.  On failure *plan is NULL. */
+fq_status floquet_plan_create(fq_plan** plan, const fq_problem* problem);
+
+/* Frees the plan and its device memory (synchronises the device first).  NULL is a no-op. */
+void floquet_plan_destroy(fq_plan* plan);
+
+fq_status floquet_plan_get_info(const fq_plan* plan, fq_plan_info* info);
+
+/* Host planning only (no device needed): fills *info as floquet_plan_create would and writes
+ * the Bessel weights a_0 .. a_L (Eq. 12) into coeffs[0 .. min(L, cap-1)] if coeffs is not NULL. */
+fq_status floquet_plan_inspect(const fq_problem* problem, fq_plan_info* info, double* coeffs,
+                               int32_t cap);
+
+/* Bytes of workspace floquet_propagate / floquet_build_UT need for ncols states. */
+size_t floquet_workspace_size(const fq_plan* plan, int32_t ncols);
+
+/* U_T (Algorithm 1 steps 5-11): propagates the N x N identity over all M steps and writes
+ * d_U = N x N complex128, U[i][j] = <i|U_T|j>.  d_ws: floquet_workspace_size(plan, N) bytes,
+ * 256-byte aligned.  Asynchronous on `stream`. */
+fq_status floquet_build_UT(fq_plan* plan, void* d_U, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Propagates a block of ncols states through steps m_begin .. m_end-1 (0-based), i.e.
+ * X = U_{m_end} ... U_{m_begin+1} X0 (Eq. 9 restricted to those steps).  d_X0, d_X: ncols x N
+ * complex128, row r = state r; d_X may equal d_X0.  Used for the second propagation round of
+ * §3 (eigenvectors as initial states) and for resuming a chain. */
+fq_status floquet_propagate(fq_plan* plan, const void* d_X0, void* d_X, int32_t ncols,
+                            int32_t m_begin, int32_t m_end, void* d_ws, size_t ws_bytes,
+                            void* stream);
+
+/* Unitarity defect (§2: truncated Omega is Hermitian, so every step is unitary):
+ * over the k columns listed in d_cols (int32, device; NULL = all N columns, k ignored) of the
+ * N x N complex128 d_U, computes max_{c in cols, j} |(U^+ U - 1)[c][j]| and the Frobenius
+ * norm of those rows / sqrt(k).  Synchronises `stream`; results in host doubles.
+ * d_ws: floquet_defect_workspace_size(n) bytes. */
+size_t floquet_defect_workspace_size(int32_t n);
+fq_status floquet_unitarity_defect(const void* d_U, int32_t n, const int32_t* d_cols, int32_t k,
+                                   void* d_ws, size_t ws_bytes, void* stream,
+                                   double* max_abs, double* fro);
+
+/* Gate-fidelity loss and gradient for piecewise-constant drives (plan made with
+ * FQ_DRIVE_PIECEWISE, FQ_DENSE): L = 1 - |Tr(W^+ U_T)|^2 / N^2 with W = d_W (N x N complex128,
+ * row-major) and U_T built from the amplitudes d_f (M doubles, device); writes *d_loss
+ * (1 double, device) and d_grad[m] = dL/df_m (M doubles, device).  Reverse-mode through the
+ * Magnus-Chebyshev chain (Clenshaw-form adjoint of Eqs. 10-12) with X_m kept every
+ * checkpoint_stride steps and recomputed in between.  d_ws: floquet_grad_workspace_size. */
+size_t floquet_grad_workspace_size(const fq_plan* plan);
+fq_status floquet_grad(fq_plan* plan, const double* d_f, const void* d_W, double* d_loss,
+                       double* d_grad, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Synchronises `stream`; returns FQ_EBOUND (and clears the word) if a device check of this
+ * plan fired since the last call, FQ_OK otherwise. */
+fq_status floquet_check_status(fq_plan* plan, void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* floquet_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLOQUET_H */

@@ -1,0 +1,183 @@
+"""ctypes binding of libfloquet.so: argument marshalling only.
+
+Every function here has the name of the C entry point it calls and only converts
+arguments (torch tensors -> device pointers, torch streams -> cudaStream_t, Python numbers ->
+C types).  All computation happens in the library's CUDA kernels and host planner; there is
+no fallback: if libfloquet.so is missing, importing this module raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfloquet.so")
+
+FQ_OK, FQ_EINVAL, FQ_ENOMEM, FQ_ECUDA, FQ_EBOUND, FQ_ETIMEOUT, FQ_EUNSUPPORTED = range(7)
+FQ_DENSE, FQ_TRIDIAG = 0, 1
+FQ_FP64, FQ_FP32, FQ_BF16X3, FQ_BF16X6 = 0, 1, 2, 3
+FQ_DRIVE_COS, FQ_DRIVE_PIECEWISE = 0, 1
+FQ_KERNEL_AUTO, FQ_KERNEL_STREAM, FQ_KERNEL_RESIDENT = 0, 1, 2
+STATUS_NAMES = {0: "FQ_OK", 1: "FQ_EINVAL", 2: "FQ_ENOMEM", 3: "FQ_ECUDA", 4: "FQ_EBOUND",
+                5: "FQ_ETIMEOUT", 6: "FQ_EUNSUPPORTED"}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class fq_problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("format", ctypes.c_int32),
+                ("h0", _dp), ("h0_off", _dp), ("h1", _dp),
+                ("period", ctypes.c_double), ("steps", ctypes.c_int32), ("drive_kind", ctypes.c_int32),
+                ("f_dc", ctypes.c_double), ("f_ac", ctypes.c_double), ("omega", ctypes.c_double),
+                ("phi0", ctypes.c_double), ("f_steps", _dp), ("cheb_tol", ctypes.c_double),
+                ("e_min", ctypes.c_double), ("e_max", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("checkpoint_stride", ctypes.c_int32), ("kernel", ctypes.c_int32)]
+
+
+class fq_plan_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("steps", ctypes.c_int32), ("L", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("format", ctypes.c_int32), ("drive_kind", ctypes.c_int32),
+                ("h", ctypes.c_double), ("e_min", ctypes.c_double), ("e_max", ctypes.c_double),
+                ("beta", ctypes.c_double), ("delta_e", ctypes.c_double), ("R", ctypes.c_double)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run paper_1508_07621_gb300.build.build() "
+                      "(nvcc for sm_103a) first - there is no CPU fallback")
+lib = ctypes.CDLL(LIB_PATH)
+
+_vp, _sz, _i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32
+_SIGS = {
+    "floquet_plan_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(fq_problem)]),
+    "floquet_plan_destroy": (None, [_vp]),
+    "floquet_plan_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(fq_plan_info)]),
+    "floquet_plan_inspect": (ctypes.c_int, [ctypes.POINTER(fq_problem), ctypes.POINTER(fq_plan_info), _dp, _i32]),
+    "floquet_workspace_size": (_sz, [_vp, _i32]),
+    "floquet_build_UT": (ctypes.c_int, [_vp, _vp, _vp, _sz, _vp]),
+    "floquet_propagate": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _sz, _vp]),
+    "floquet_defect_workspace_size": (_sz, [_i32]),
+    "floquet_unitarity_defect": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _sz, _vp, _dp, _dp]),
+    "floquet_grad_workspace_size": (_sz, [_vp]),
+    "floquet_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "floquet_check_status": (ctypes.c_int, [_vp, _vp]),
+    "floquet_last_error": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class FloquetError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib.floquet_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != FQ_OK:
+        raise FloquetError(status, where)
+
+
+def _ptr(t):
+    """Device pointer of a tensor (None -> NULL)."""
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _darr(a):
+    import numpy as np
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    return arr, arr.ctypes.data_as(_dp)
+
+
+def make_problem(n, fmt, h0, h1, period, steps, h0_off=None, drive_kind=FQ_DRIVE_COS, f_dc=0.0, f_ac=0.0,
+                 omega=1.0, phi0=0.0, f_steps=None, cheb_tol=0.0, e_min=0.0, e_max=0.0,
+                 precision=FQ_FP64, checkpoint_stride=0, kernel=FQ_KERNEL_AUTO):
+    """Builds an fq_problem; returns (struct, keepalive) - the host arrays must outlive the call."""
+    a0, p0 = _darr(h0)
+    a1, p1 = _darr(h1)
+    ao, po = _darr(h0_off)
+    af, pf = _darr(f_steps)
+    prob = fq_problem(n, fmt, p0, po, p1, period, steps, drive_kind, f_dc, f_ac, omega, phi0, pf, cheb_tol,
+                      e_min, e_max, precision, checkpoint_stride, kernel)
+    return prob, (a0, a1, ao, af)
+
+
+def floquet_plan_create(problem) -> int:
+    plan = _vp()
+    _check(lib.floquet_plan_create(ctypes.byref(plan), ctypes.byref(problem)), "floquet_plan_create")
+    return plan.value
+
+
+def floquet_plan_destroy(plan: int) -> None:
+    lib.floquet_plan_destroy(_vp(plan))
+
+
+def floquet_plan_get_info(plan: int) -> fq_plan_info:
+    info = fq_plan_info()
+    _check(lib.floquet_plan_get_info(_vp(plan), ctypes.byref(info)), "floquet_plan_get_info")
+    return info
+
+
+def floquet_plan_inspect(problem, cap: int = 4096):
+    import numpy as np
+    info = fq_plan_info()
+    coeffs = np.zeros(cap)
+    _check(lib.floquet_plan_inspect(ctypes.byref(problem), ctypes.byref(info), coeffs.ctypes.data_as(_dp), cap),
+           "floquet_plan_inspect")
+    return info, coeffs[: info.L + 1].copy()
+
+
+def floquet_workspace_size(plan: int, ncols: int) -> int:
+    return int(lib.floquet_workspace_size(_vp(plan), ncols))
+
+
+def floquet_build_UT(plan: int, U, ws, stream=None) -> None:
+    _check(lib.floquet_build_UT(_vp(plan), _ptr(U), _ptr(ws), ws.numel() * ws.element_size() if ws is not None else 0,
+                                _stream(stream)), "floquet_build_UT")
+
+
+def floquet_propagate(plan: int, X0, X, ncols: int, m_begin: int, m_end: int, ws, stream=None) -> None:
+    _check(lib.floquet_propagate(_vp(plan), _ptr(X0), _ptr(X), ncols, m_begin, m_end, _ptr(ws),
+                                 ws.numel() * ws.element_size() if ws is not None else 0, _stream(stream)),
+           "floquet_propagate")
+
+
+def floquet_defect_workspace_size(n: int) -> int:
+    return int(lib.floquet_defect_workspace_size(n))
+
+
+def floquet_unitarity_defect(U, n: int, cols, k: int, ws, stream=None):
+    mx, fro = ctypes.c_double(), ctypes.c_double()
+    _check(lib.floquet_unitarity_defect(_ptr(U), n, _ptr(cols), k, _ptr(ws), ws.numel() * ws.element_size(),
+                                        _stream(stream), ctypes.byref(mx), ctypes.byref(fro)),
+           "floquet_unitarity_defect")
+    return mx.value, fro.value
+
+
+def floquet_grad_workspace_size(plan: int) -> int:
+    return int(lib.floquet_grad_workspace_size(_vp(plan)))
+
+
+def floquet_grad(plan: int, f, W, loss, grad, ws, stream=None) -> None:
+    _check(lib.floquet_grad(_vp(plan), _ptr(f), _ptr(W), _ptr(loss), _ptr(grad), _ptr(ws),
+                            ws.numel() * ws.element_size() if ws is not None else 0, _stream(stream)),
+           "floquet_grad")
+
+
+def floquet_check_status(plan: int, stream=None) -> int:
+    return int(lib.floquet_check_status(_vp(plan), _stream(stream)))
+
+
+def floquet_last_error() -> str:
+    return lib.floquet_last_error().decode(errors="replace")

@@ -1,0 +1,98 @@
+"""Convenience layer over the binding: a plan handle that frees itself, and torch-allocated
+outputs/workspaces.  Still marshalling only - every computation is a libfloquet.so call."""
+from __future__ import annotations
+
+import math
+
+from . import _binding as B
+
+
+def workspace(nbytes: int, device="cuda"):
+    """Caller-owned device workspace (torch allocation, 256-byte aligned by the allocator)."""
+    import torch
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+class Plan:
+    """Owns an fq_plan*; destroyed on close() / garbage collection."""
+
+    def __init__(self, problem, keepalive):
+        self._keep = keepalive
+        self.handle = B.floquet_plan_create(problem)
+        self.info = B.floquet_plan_get_info(self.handle)
+        self.n = self.info.n
+
+    # ---------------------------------------------------------------- constructors
+    @classmethod
+    def dense(cls, h0, h1, *, omega, f_ac, steps, f_dc=0.0, phi0=0.0, period=None, precision=B.FQ_FP64,
+              cheb_tol=0.0, e_min=0.0, e_max=0.0):
+        n = h0.shape[0]
+        T = period if period is not None else 2.0 * math.pi / omega
+        prob, keep = B.make_problem(n, B.FQ_DENSE, h0, h1, T, steps, f_dc=f_dc, f_ac=f_ac, omega=omega,
+                                    phi0=phi0, precision=precision, cheb_tol=cheb_tol, e_min=e_min, e_max=e_max)
+        return cls(prob, keep)
+
+    @classmethod
+    def tridiag(cls, h0_diag, h0_off, h1_diag, *, omega, f_ac, steps, f_dc=0.0, phi0=0.0, period=None,
+                precision=B.FQ_FP32, kernel=B.FQ_KERNEL_AUTO, cheb_tol=0.0, e_min=0.0, e_max=0.0):
+        n = h0_diag.shape[0]
+        T = period if period is not None else 2.0 * math.pi / omega
+        prob, keep = B.make_problem(n, B.FQ_TRIDIAG, h0_diag, h1_diag, T, steps, h0_off=h0_off, f_dc=f_dc,
+                                    f_ac=f_ac, omega=omega, phi0=phi0, precision=precision, kernel=kernel,
+                                    cheb_tol=cheb_tol, e_min=e_min, e_max=e_max)
+        return cls(prob, keep)
+
+    @classmethod
+    def piecewise(cls, h0, h1, f_steps, *, period, precision=B.FQ_FP64, checkpoint_stride=16, cheb_tol=0.0):
+        n = h0.shape[0]
+        prob, keep = B.make_problem(n, B.FQ_DENSE, h0, h1, period, len(f_steps), drive_kind=B.FQ_DRIVE_PIECEWISE,
+                                    f_steps=f_steps, precision=precision, checkpoint_stride=checkpoint_stride,
+                                    cheb_tol=cheb_tol)
+        return cls(prob, keep)
+
+    # ---------------------------------------------------------------- calls
+    def workspace_size(self, ncols=None) -> int:
+        return B.floquet_workspace_size(self.handle, self.n if ncols is None else ncols)
+
+    def build_UT(self, out=None, ws=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.n, self.n), dtype=torch.complex128, device="cuda")
+        if ws is None:
+            ws = workspace(self.workspace_size())
+        B.floquet_build_UT(self.handle, out, ws, stream)
+        return out
+
+    def propagate(self, x0, m_begin=0, m_end=None, out=None, ws=None, stream=None):
+        import torch
+        m_end = self.info.steps if m_end is None else m_end
+        ncols = x0.shape[0]
+        if out is None:
+            out = torch.empty_like(x0)
+        if ws is None:
+            ws = workspace(self.workspace_size(ncols))
+        B.floquet_propagate(self.handle, x0, out, ncols, m_begin, m_end, ws, stream)
+        return out
+
+    def check_status(self, stream=None) -> int:
+        return B.floquet_check_status(self.handle, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.floquet_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unitarity_defect(U, cols=None, stream=None):
+    """(max |U^+U - 1|, Frobenius / sqrt(k)) over the listed columns (all if None)."""
+    import torch
+    n = U.shape[0]
+    k = n if cols is None else cols.numel()
+    ws = workspace(2 * 8 * ((k + 15) // 16) * ((n + 255) // 256) + 256)
+    return B.floquet_unitarity_defect(U, n, cols, k, ws, stream)

@@ -1,0 +1,404 @@
+// C ABI: plan lifetime, workspace layout and the host loops that chain the kernels
+// (Algorithm 1 steps 5-11: M steps of L Chebyshev terms each, U_T written in place).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// Carves aligned regions out of the caller's workspace.
+struct Carver {
+  char* base;
+  size_t used = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  template <typename T>
+  T* take(size_t count) {
+    T* p = base ? (T*)(base + used) : nullptr;
+    used += align_up(count * sizeof(T));
+    return p;
+  }
+};
+
+int tri_ld(int n) { return (n + 3) & ~3; }
+
+// Workspace regions of floquet_propagate / floquet_build_UT.
+struct StateWs {
+  // dense FP64
+  double* S = nullptr;
+  double* A = nullptr;
+  // tridiagonal coefficients [nsteps][ld] (d, er, ei contiguous)
+  void* coeff = nullptr;
+  // three planar state buffers
+  void* buf[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+};
+
+size_t layout(const fq_plan* p, int nc, int nsteps, void* ws, StateWs* out) {
+  Carver c(ws);
+  StateWs w;
+  const int n = p->n;
+  if (p->path == PATH_DENSE_F64) {
+    w.S = c.take<double>((size_t)n * n);
+    w.A = c.take<double>((size_t)n * n);
+    for (int b = 0; b < 3; ++b)
+      for (int q = 0; q < 2; ++q) w.buf[b][q] = c.take<double>((size_t)nc * n);
+  } else if (p->path == PATH_TRI_STREAM) {
+    const size_t ld = tri_ld(n);
+    const size_t es = p->precision == FQ_FP64 ? sizeof(double) : sizeof(float);
+    w.coeff = c.take<char>(3 * ld * (size_t)nsteps * es);
+    for (int b = 0; b < 3; ++b)
+      for (int q = 0; q < 2; ++q) w.buf[b][q] = c.take<char>((size_t)nc * ld * es);
+  } else if (p->path == PATH_TRI_RESIDENT) {
+    w.coeff = c.take<char>(fq_resident_coeff_bytes(n, nsteps));
+  }
+  if (out) *out = w;
+  return c.used;
+}
+
+fq_status cuda_ok(cudaError_t e, const char* what) { return e == cudaSuccess ? FQ_OK : fq_cuda_fail(e, what); }
+
+template <typename T>
+fq_blk<T> blk(void* const (&b)[2]) { return fq_blk<T>{(T*)b[0], (T*)b[1]}; }
+
+// Runs steps [m_begin, m_end) on the planar block held in buffer `x` (index into w.buf);
+// returns the buffer index that holds the result.
+template <typename T>
+int run_chain(fq_plan* p, StateWs& w, int x, int nc, int m_begin, int m_end, cudaStream_t s) {
+  const int n = p->n, L = p->L;
+  const int ld = p->path == PATH_DENSE_F64 ? n : tri_ld(n);
+  const int nsteps = m_end - m_begin;
+  fq_term t{};
+  t.coef0 = p->cheb[0];
+  t.ph_re = p->phase_re;
+  t.ph_im = p->phase_im;
+  t.bound2 = p->precision == FQ_FP64 ? 1.0 + 1e-9 : 1.0 + 2e-3;
+  t.status = p->d_status;
+  const T* cd = nullptr;
+  const T* cer = nullptr;
+  const T* cei = nullptr;
+  if (p->path == PATH_TRI_STREAM) {
+    cd = (const T*)w.coeff;
+    cer = cd + (size_t)nsteps * ld;
+    cei = cer + (size_t)nsteps * ld;
+  }
+  for (int m = m_begin; m < m_end; ++m) {
+    if (p->path == PATH_DENSE_F64)
+      fq_launch_omega_dense_f64(p->d_h0, p->d_h1, p->d_k, n, p->sa[m], p->sb[m], p->sc[m], p->sbeta, w.S, w.A, s);
+    // buffers: cur = psi_l, prv = psi_{l-1}, acc; x holds psi_0
+    int cur = x, nxt = (x + 1) % 3, acc = (x + 2) % 3;
+    int prv = -1;
+    for (int l = 0; l < L; ++l) {
+      t.first = l == 0;
+      t.last = l == L - 1;
+      t.coef = p->cheb[l + 1];
+      // output: psi_{l+1} goes to a fresh buffer on the first term, in place of psi_{l-1}
+      // afterwards; the step result of a one-term step goes to the free third buffer
+      int out;
+      if (l == 0) out = t.last ? nxt : nxt;
+      else out = prv;
+      fq_blk<T> bc = blk<T>(w.buf[cur]);
+      fq_blk<T> bp = prv >= 0 ? blk<T>(w.buf[prv]) : bc;
+      fq_blk<T> ba = blk<T>(w.buf[acc]);
+      fq_blk<T> bo = blk<T>(w.buf[out]);
+      if (p->path == PATH_DENSE_F64) {
+        fq_launch_term_dense_f64(w.S, w.A, n, *(fq_blk<double>*)&bc, *(fq_blk<double>*)&bp, *(fq_blk<double>*)&ba,
+                                 *(fq_blk<double>*)&bo, nc, t, s);
+      } else {
+        const size_t off = (size_t)(m - m_begin) * ld;
+        if (sizeof(T) == 8)
+          fq_launch_term_tri_f64((const double*)cd + off, (const double*)cer + off, (const double*)cei + off, n,
+                                 *(fq_blk<double>*)&bc, *(fq_blk<double>*)&bp, *(fq_blk<double>*)&ba,
+                                 *(fq_blk<double>*)&bo, nc, ld, t, s);
+        else
+          fq_launch_term_tri_f32((const float*)cd + off, (const float*)cer + off, (const float*)cei + off, n,
+                                 *(fq_blk<float>*)&bc, *(fq_blk<float>*)&bp, *(fq_blk<float>*)&ba,
+                                 *(fq_blk<float>*)&bo, nc, ld, t, s);
+      }
+      if (t.last) {
+        x = out;
+      } else {
+        prv = cur;
+        cur = out;
+      }
+    }
+  }
+  return x;
+}
+
+fq_status check_ws(const fq_plan* p, int nc, int nsteps, void* ws, size_t bytes) {
+  const size_t need = layout(p, nc, nsteps, nullptr, nullptr);
+  if (need > 0 && (!ws || bytes < need)) {
+    fq_set_error("workspace too small: need %zu bytes, got %zu", need, bytes);
+    return FQ_EINVAL;
+  }
+  if (ws && ((uintptr_t)ws & (kAlign - 1))) {
+    fq_set_error("workspace must be 256-byte aligned");
+    return FQ_EINVAL;
+  }
+  return FQ_OK;
+}
+
+fq_status propagate_impl(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
+                         int transpose_out, void* ws, size_t ws_bytes, cudaStream_t s) {
+  const int n = p->n;
+  const int nsteps = m_end - m_begin;
+  fq_status st = check_ws(p, nc, nsteps, ws, ws_bytes);
+  if (st != FQ_OK) return st;
+  if (nc == 0 || n == 0) return FQ_OK;
+  if (p->path == PATH_TRI_STREAM && nc > 65535) {
+    fq_set_error("streaming tridiagonal kernel: at most 65535 states per call (got %d)", nc);
+    return FQ_EUNSUPPORTED;
+  }
+  StateWs w;
+  layout(p, nc, nsteps, ws, &w);
+  if (p->path == PATH_TRI_RESIDENT) {
+    const int ld = tri_ld(n);
+    float* d2 = (float*)w.coeff;
+    fq_launch_tri_coeffs_f32(p, m_begin, nsteps, 2.0, d2, d2 + (size_t)nsteps * ld, d2 + 2 * (size_t)nsteps * ld, s);
+    st = fq_launch_resident(p, d2, d2 + (size_t)nsteps * ld, identity ? nullptr : x0, x, transpose_out, nc, m_begin,
+                            m_end, s);
+    if (st != FQ_OK) return st;
+    return cuda_ok(cudaGetLastError(), "resident chain");
+  }
+  const bool f64 = p->precision == FQ_FP64;
+  const int ld = p->path == PATH_DENSE_F64 ? n : tri_ld(n);
+  if (p->path == PATH_TRI_STREAM) {
+    if (f64) {
+      double* d = (double*)w.coeff;
+      fq_launch_tri_coeffs_f64(p, m_begin, nsteps, 1.0, d, d + (size_t)nsteps * ld, d + 2 * (size_t)nsteps * ld, s);
+    } else {
+      float* d = (float*)w.coeff;
+      fq_launch_tri_coeffs_f32(p, m_begin, nsteps, 1.0, d, d + (size_t)nsteps * ld, d + 2 * (size_t)nsteps * ld, s);
+    }
+  }
+  int xb = 0;
+  if (f64) {
+    fq_blk<double> b0 = blk<double>(w.buf[0]);
+    if (identity) fq_launch_identity_f64(b0, nc, n, ld, s);
+    else fq_launch_load_states(x0, b0, nc, n, ld, s);
+    xb = run_chain<double>(p, w, 0, nc, m_begin, m_end, s);
+    fq_blk<double> bx = blk<double>(w.buf[xb]);
+    if (transpose_out) fq_launch_store_transpose_f64(bx, x, n, ld, s);
+    else fq_launch_store_states_f64(bx, x, nc, n, ld, s);
+  } else {
+    fq_blk<float> b0 = blk<float>(w.buf[0]);
+    if (identity) fq_launch_identity_f32(b0, nc, n, ld, s);
+    else fq_launch_load_states_f32(x0, b0, nc, n, ld, s);
+    xb = run_chain<float>(p, w, 0, nc, m_begin, m_end, s);
+    fq_blk<float> bx = blk<float>(w.buf[xb]);
+    if (transpose_out) fq_launch_store_transpose_f32(bx, x, n, ld, s);
+    else fq_launch_store_states_f32(bx, x, nc, n, ld, s);
+  }
+  return cuda_ok(cudaGetLastError(), "propagation kernels");
+}
+
+void free_plan(fq_plan* p) {
+  if (!p) return;
+  cudaFree(p->d_h0);
+  cudaFree(p->d_h1);
+  cudaFree(p->d_k);
+  cudaFree(p->d_h0o);
+  cudaFree(p->d_scal);
+  cudaFree(p->d_status);
+  delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
+  if (!out) { fq_set_error("plan pointer is NULL"); return FQ_EINVAL; }
+  *out = nullptr;
+  fq_plan* p = new (std::nothrow) fq_plan();
+  if (!p) { fq_set_error("host allocation failed"); return FQ_ENOMEM; }
+  fq_status st = fq_host_plan(prob, p);
+  if (st != FQ_OK) { delete p; return st; }
+  const int n = p->n, M = p->steps;
+  if (p->format == FQ_TRIDIAG) {
+    const bool res_ok = p->precision == FQ_FP32 && fq_resident_supported(n, p->L);
+    if (prob->kernel == FQ_KERNEL_RESIDENT && !res_ok) {
+      fq_set_error("resident kernel needs FQ_FP32, N <= 10240 and L <= 128 (N = %d, L = %d)", n, p->L);
+      delete p;
+      return FQ_EUNSUPPORTED;
+    }
+    p->path = (res_ok && prob->kernel != FQ_KERNEL_STREAM) ? PATH_TRI_RESIDENT : PATH_TRI_STREAM;
+  } else {
+    p->path = p->precision == FQ_FP64 ? PATH_DENSE_F64 : PATH_DENSE_SPLIT;
+    if (p->path == PATH_DENSE_SPLIT) {
+      fq_set_error("split-precision dense path not built yet");
+      delete p;
+      return FQ_EUNSUPPORTED;
+    }
+  }
+  cudaGetDevice(&p->device);
+  auto fail = [&](cudaError_t e, const char* what) {
+    fq_status r = (e == cudaErrorMemoryAllocation) ? FQ_ENOMEM : FQ_ECUDA;
+    fq_cuda_fail(e, what);
+    free_plan(p);
+    return r;
+  };
+  cudaError_t e;
+  const size_t opsz = p->format == FQ_DENSE ? (size_t)n * n : (size_t)n;
+  if ((e = cudaMalloc(&p->d_h0, opsz * sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc H0");
+  if ((e = cudaMalloc(&p->d_h1, opsz * sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc H1");
+  if ((e = cudaMalloc(&p->d_k, std::max<size_t>(opsz, 1) * sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc K");
+  if ((e = cudaMalloc(&p->d_scal, 3 * (size_t)M * sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc scalars");
+  if ((e = cudaMalloc(&p->d_status, sizeof(unsigned int))) != cudaSuccess) return fail(e, "cudaMalloc status");
+  if ((e = cudaMemset(p->d_status, 0, sizeof(unsigned int))) != cudaSuccess) return fail(e, "status clear");
+  if ((e = cudaMemcpy(p->d_h0, prob->h0, opsz * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "upload H0");
+  if ((e = cudaMemcpy(p->d_h1, prob->h1, opsz * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "upload H1");
+  std::vector<double> scal(3 * (size_t)M);
+  std::copy(p->sa.begin(), p->sa.end(), scal.begin());
+  std::copy(p->sb.begin(), p->sb.end(), scal.begin() + M);
+  std::copy(p->sc.begin(), p->sc.end(), scal.begin() + 2 * M);
+  if ((e = cudaMemcpy(p->d_scal, scal.data(), scal.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return fail(e, "upload scalars");
+  if (p->format == FQ_DENSE) {
+    // [H0, H1] = H0 H1 - H1 H0, once per plan (§3)
+    fq_launch_gemm_f64(p->d_h0, p->d_h1, p->d_k, n, 1.0, 0.0, 0);
+    fq_launch_gemm_f64(p->d_h1, p->d_h0, p->d_k, n, -1.0, 1.0, 0);
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "commutator");
+  } else {
+    std::vector<double> kl(std::max(1, n - 1), 0.0);
+    for (int i = 0; i + 1 < n; ++i) kl[i] = prob->h0_off[i] * (prob->h1[i] - prob->h1[i + 1]);
+    if ((e = cudaMalloc(&p->d_h0o, std::max(1, n - 1) * sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc H0 off");
+    if (n > 1) {
+      if ((e = cudaMemcpy(p->d_h0o, prob->h0_off, (n - 1) * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e, "upload H0 off");
+      if ((e = cudaMemcpy(p->d_k, kl.data(), (n - 1) * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e, "upload K");
+    }
+  }
+  *out = p;
+  return FQ_OK;
+}
+
+void floquet_plan_destroy(fq_plan* p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  free_plan(p);
+}
+
+fq_status floquet_plan_get_info(const fq_plan* p, fq_plan_info* info) {
+  if (!p || !info) { fq_set_error("NULL argument"); return FQ_EINVAL; }
+  info->n = p->n;
+  info->steps = p->steps;
+  info->L = p->L;
+  info->precision = p->precision;
+  info->format = p->format;
+  info->drive_kind = p->drive_kind;
+  info->h = p->h;
+  info->e_min = p->e_min;
+  info->e_max = p->e_max;
+  info->beta = p->beta;
+  info->delta_e = p->delta_e;
+  info->R = p->R;
+  return FQ_OK;
+}
+
+fq_status floquet_plan_inspect(const fq_problem* prob, fq_plan_info* info, double* coeffs, int32_t cap) {
+  fq_plan p;
+  fq_status st = fq_host_plan(prob, &p);
+  if (st != FQ_OK) return st;
+  st = floquet_plan_get_info(&p, info);
+  if (coeffs)
+    for (int l = 0; l <= p.L && l < cap; ++l) coeffs[l] = p.cheb[l];
+  return st;
+}
+
+size_t floquet_workspace_size(const fq_plan* p, int32_t ncols) {
+  if (!p || ncols < 0) return 0;
+  return layout(p, ncols, p->steps, nullptr, nullptr);
+}
+
+fq_status floquet_build_UT(fq_plan* p, void* d_U, void* d_ws, size_t ws_bytes, void* stream) {
+  if (!p || !d_U) { fq_set_error("NULL plan or output"); return FQ_EINVAL; }
+  return propagate_impl(p, nullptr, (double*)d_U, p->n, 0, p->steps, 1, 1, d_ws, ws_bytes, (cudaStream_t)stream);
+}
+
+fq_status floquet_propagate(fq_plan* p, const void* d_X0, void* d_X, int32_t ncols, int32_t m_begin, int32_t m_end,
+                            void* d_ws, size_t ws_bytes, void* stream) {
+  if (!p || !d_X0 || !d_X) { fq_set_error("NULL plan or state pointer"); return FQ_EINVAL; }
+  if (ncols < 0 || m_begin < 0 || m_end > p->steps || m_begin > m_end) {
+    fq_set_error("bad range: ncols %d, steps [%d, %d) of %d", ncols, m_begin, m_end, p->steps);
+    return FQ_EINVAL;
+  }
+  if (m_begin == m_end) {
+    if (d_X != d_X0)
+      return cuda_ok(cudaMemcpyAsync(d_X, d_X0, (size_t)ncols * p->n * 16, cudaMemcpyDeviceToDevice,
+                                     (cudaStream_t)stream), "copy");
+    return FQ_OK;
+  }
+  return propagate_impl(p, (const double*)d_X0, (double*)d_X, ncols, m_begin, m_end, 0, 0, d_ws, ws_bytes,
+                        (cudaStream_t)stream);
+}
+
+size_t floquet_defect_workspace_size(int32_t n) {
+  if (n < 1) return 0;
+  return align_up(2 * sizeof(double) * (size_t)((n + 15) / 16) * ((n + 255) / 256));
+}
+
+fq_status floquet_unitarity_defect(const void* d_U, int32_t n, const int32_t* d_cols, int32_t k, void* d_ws,
+                                   size_t ws_bytes, void* stream, double* max_abs, double* fro) {
+  if (!d_U || n < 1 || !max_abs || !fro) { fq_set_error("bad defect arguments"); return FQ_EINVAL; }
+  const int rows = d_cols ? k : n;
+  if (rows < 1 || rows > n) { fq_set_error("defect: k must be in [1, n]"); return FQ_EINVAL; }
+  const int nb = (n + 255) / 256;
+  const int chunks = (rows + 15) / 16;
+  const size_t need = align_up(2 * sizeof(double) * (size_t)chunks * nb);
+  if (!d_ws || ws_bytes < need) { fq_set_error("defect workspace too small (%zu < %zu)", ws_bytes, need); return FQ_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  fq_launch_defect((const double*)d_U, n, d_cols, rows, (double*)d_ws, s);
+  std::vector<double> h(2 * (size_t)chunks * nb);
+  cudaError_t e = cudaMemcpyAsync(h.data(), d_ws, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fq_cuda_fail(e, "defect");
+  double mx = 0.0, ss = 0.0;
+  for (size_t q = 0; q < h.size(); q += 2) {
+    mx = std::max(mx, h[q]);
+    ss += h[q + 1];
+  }
+  *max_abs = mx;
+  *fro = sqrt(ss / rows);  // Frobenius norm of the k rows of U^+U - 1, over sqrt(k)
+  return FQ_OK;
+}
+
+fq_status floquet_check_status(fq_plan* p, void* stream) {
+  if (!p) { fq_set_error("NULL plan"); return FQ_EINVAL; }
+  unsigned int v = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(&v, p->d_status, sizeof(v), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fq_cuda_fail(e, "status read");
+  if (v) {
+    cudaMemsetAsync(p->d_status, 0, sizeof(unsigned int), s);
+    cudaStreamSynchronize(s);
+    if (v & FQ_BIT_TIMEOUT) { fq_set_error("a bounded device wait timed out"); return FQ_ETIMEOUT; }
+    fq_set_error("device check: an entry exceeded the unitarity bound or was NaN (spectral bounds too tight?)");
+    return FQ_EBOUND;
+  }
+  return FQ_OK;
+}
+
+}  // extern "C"
+
+extern "C" size_t floquet_grad_workspace_size(const fq_plan* p) {
+  (void)p;
+  return 0;
+}
+
+extern "C" fq_status floquet_grad(fq_plan* p, const double* d_f, const void* d_W, double* d_loss, double* d_grad,
+                                  void* d_ws, size_t ws_bytes, void* stream) {
+  (void)p; (void)d_f; (void)d_W; (void)d_loss; (void)d_grad; (void)d_ws; (void)ws_bytes; (void)stream;
+  fq_set_error("floquet_grad: not built yet");
+  return FQ_EUNSUPPORTED;
+}

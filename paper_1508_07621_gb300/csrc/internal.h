@@ -1,0 +1,107 @@
+// Internal declarations shared by the host planner, the orchestration layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "floquet.h"
+
+// Status-word bits raised by device checks.
+enum : unsigned int { FQ_BIT_BOUND = 1u, FQ_BIT_TIMEOUT = 2u };
+
+// Which kernel family runs the recurrence for a plan.
+enum fq_path : int {
+  PATH_DENSE_F64 = 0,     // SIMT FP64 tiled complex GEMM per Chebyshev term
+  PATH_DENSE_SPLIT = 1,   // tcgen05 BF16 split GEMM per term
+  PATH_TRI_STREAM = 2,    // streaming tridiagonal term kernel (FP32 or FP64)
+  PATH_TRI_RESIDENT = 3,  // one CTA per state, whole chain on chip (FP32)
+};
+
+struct fq_plan {
+  // problem
+  int n = 0, steps = 0, format = 0, precision = 0, drive_kind = 0, stride = 16, L = 0;
+  double period = 0, h = 0, tol = 1e-14;
+  // bounds of Omega/h (Eq. 11) and Chebyshev data (Eq. 12)
+  double e_min = 0, e_max = 0, beta = 0, delta_e = 0, R = 0;
+  std::vector<double> cheb;            // a_0 .. a_L
+  double phase_re = 1, phase_im = 0;   // e^{-i beta h}
+  // per-step Magnus scalars a_m, b_m, c_m and their Omega~ forms
+  std::vector<double> ma, mb, mc;
+  std::vector<double> sa, sb, sc;      // Omega~_m = sa H0 + sb H1 + sc i[H0,H1] - sbeta 1
+  double sbeta = 0;
+  int path = PATH_DENSE_F64;
+  int device = 0;
+  // device copies (owned by the plan)
+  double* d_h0 = nullptr;    // DENSE: n*n      TRIDIAG: diag n
+  double* d_h1 = nullptr;    // DENSE: n*n      TRIDIAG: diag n
+  double* d_k = nullptr;     // DENSE: [H0,H1] n*n   TRIDIAG: lower off-diagonal of [H0,H1], n-1
+  double* d_h0o = nullptr;   // TRIDIAG: off-diagonal of H0, n-1
+  double* d_scal = nullptr;  // 3*M: sa | sb | sc
+  unsigned int* d_status = nullptr;
+  // dense split path: per-plan constants prepared once
+  void* split = nullptr;
+};
+
+// thread-local error message
+void fq_set_error(const char* fmt, ...);
+fq_status fq_cuda_fail(cudaError_t e, const char* what);
+
+// ---------------------------------------------------------------- host planning (plan.cpp)
+double fq_drive_f(int deriv, double f_dc, double f_ac, double omega, double phi0, double t);
+void fq_bessel_miller(double R, int L, double* out);    // J_0..J_L
+int fq_cheb_order(double R, double tol);
+void fq_tridiag_extremes(const double* diag, const double* off, int n, double* lo, double* hi);
+void fq_lanczos_extremes(const double* a, int n, int ksteps, uint64_t seed, double* lo, double* hi);
+fq_status fq_host_plan(const fq_problem* p, fq_plan* plan);   // everything but device work
+
+// ---------------------------------------------------------------- kernels (kernels.cu)
+struct fq_term {
+  int first, last;         // first term (l = 0) / last term (l = L-1) of a step
+  double coef0, coef;      // a_0 (first term) and a_{l+1}
+  double ph_re, ph_im;     // e^{-i beta h} (last term)
+  double bound2;           // |psi|^2 threshold of the device check (entries of unit-norm states)
+  unsigned int* status;
+};
+
+// state blocks: planar re/im, ncols rows of length ld (>= n)
+template <typename T> struct fq_blk { T* re; T* im; };
+
+void fq_launch_load_states(const double* x_interleaved, fq_blk<double> out, int nc, int n, int ld, cudaStream_t s);
+void fq_launch_load_states_f32(const double* x_interleaved, fq_blk<float> out, int nc, int n, int ld, cudaStream_t s);
+void fq_launch_identity_f64(fq_blk<double> out, int nc, int n, int ld, cudaStream_t s);
+void fq_launch_identity_f32(fq_blk<float> out, int nc, int n, int ld, cudaStream_t s);
+void fq_launch_store_states_f64(fq_blk<double> in, double* x, int nc, int n, int ld, cudaStream_t s);
+void fq_launch_store_states_f32(fq_blk<float> in, double* x, int nc, int n, int ld, cudaStream_t s);
+void fq_launch_store_transpose_f64(fq_blk<double> in, double* u, int n, int ld, cudaStream_t s);
+void fq_launch_store_transpose_f32(fq_blk<float> in, double* u, int n, int ld, cudaStream_t s);
+
+void fq_launch_gemm_f64(const double* a, const double* b, double* c, int n, double alpha, double beta,
+                        cudaStream_t s);
+void fq_launch_omega_dense_f64(const double* h0, const double* h1, const double* k, int n, double sa,
+                               double sb, double sc, double sbeta, double* S, double* A, cudaStream_t s);
+void fq_launch_term_dense_f64(const double* S, const double* A, int n, fq_blk<double> cur, fq_blk<double> prev,
+                              fq_blk<double> acc, fq_blk<double> out, int nc, const fq_term& t, cudaStream_t s);
+
+// coefficients of scale * Omega~_m for steps m_begin .. m_begin+nsteps-1, each array [nsteps][ld]
+void fq_launch_tri_coeffs_f64(const fq_plan* p, int m_begin, int nsteps, double scale, double* d, double* er,
+                              double* ei, cudaStream_t s);
+void fq_launch_tri_coeffs_f32(const fq_plan* p, int m_begin, int nsteps, double scale, float* d, float* er,
+                              float* ei, cudaStream_t s);
+void fq_launch_term_tri_f64(const double* d, const double* er, const double* ei, int n, fq_blk<double> cur,
+                            fq_blk<double> prev, fq_blk<double> acc, fq_blk<double> out, int nc, int ld,
+                            const fq_term& t, cudaStream_t s);
+void fq_launch_term_tri_f32(const float* d, const float* er, const float* ei, int n, fq_blk<float> cur,
+                            fq_blk<float> prev, fq_blk<float> acc, fq_blk<float> out, int nc, int ld,
+                            const fq_term& t, cudaStream_t s);
+
+// resident tridiagonal chain (tri_resident.cu)
+int fq_resident_supported(int n, int L);
+size_t fq_resident_coeff_bytes(int n, int steps);
+fq_status fq_launch_resident(const fq_plan* p, const float* d2, const float* e2, const double* x0,
+                             double* x, int transpose_out, int nc, int m_begin, int m_end, cudaStream_t s);
+
+void fq_launch_defect(const double* u, int n, const int32_t* cols, int k, double* partial, cudaStream_t s);

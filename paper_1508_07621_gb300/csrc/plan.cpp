@@ -1,0 +1,369 @@
+// Host planning (FP64): drive samples, Magnus-4 scalars, spectral bounds, Bessel weights.
+//
+// Everything here is computed once per plan, before any propagation (§3: the commutators
+// "have to be calculated only once"; Algorithm 1 steps 2-4).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+static thread_local char g_err[512] = "";
+
+void fq_set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+extern "C" const char* floquet_last_error(void) { return g_err; }
+
+fq_status fq_cuda_fail(cudaError_t e, const char* what) {
+  fq_set_error("%s: %s", what, cudaGetErrorString(e));
+  return FQ_ECUDA;
+}
+
+// f(t) = f_dc + f_ac cos(omega t + phi0) and its first two derivatives (Eq. 13).
+double fq_drive_f(int deriv, double f_dc, double f_ac, double omega, double phi0, double t) {
+  const double x = omega * t + phi0;
+  if (deriv == 0) return f_dc + f_ac * cos(x);
+  if (deriv == 1) return -f_ac * omega * sin(x);
+  return -f_ac * omega * omega * cos(x);
+}
+
+// J_0(R) .. J_L(R) by Miller's backward recurrence (J.C.P. Miller, British Association
+// Mathematical Tables X, 1952): run J_{k-1} = (2k/R) J_k - J_{k+1} downward from an index
+// well above max(L, R) with an arbitrary seed, then normalise with the identity
+// J_0 + 2 sum_{k>=1} J_{2k} = 1.  Downward recurrence is the stable direction for k > R.
+void fq_bessel_miller(double R, int L, double* out) {
+  if (fabs(R) < 0.5) {
+    // small argument: the power series J_l(R) = sum_k (-1)^k (R/2)^{2k+l} / (k! (k+l)!)
+    // converges to full precision in a few terms (and avoids 2k/R overflow).
+    const double x = 0.5 * R;
+    double lead = 1.0;  // (R/2)^l / l!
+    for (int l = 0; l <= L; ++l) {
+      if (l > 0) lead *= x / l;
+      double term = lead, sum = lead;
+      for (int k = 1; k < 30 && term != 0.0; ++k) {
+        term *= -x * x / ((double)k * (k + l));
+        sum += term;
+      }
+      out[l] = sum;
+    }
+    return;
+  }
+  const double top = std::max((double)L, fabs(R));
+  int K = (int)(top + 30.0 + 6.0 * sqrt(top));
+  K += K & 1;  // even start index keeps the normalisation sum simple
+  std::vector<double> j(K + 2, 0.0);
+  j[K + 1] = 0.0;
+  j[K] = 1e-300;
+  for (int k = K; k >= 1; --k) {
+    j[k - 1] = (2.0 * k / R) * j[k] - j[k + 1];
+    if (fabs(j[k - 1]) > 1e250) {  // rescale everything computed so far
+      for (int q = k - 1; q <= K + 1; ++q) j[q] *= 1e-250;
+    }
+  }
+  double s = j[0];
+  for (int k = 2; k <= K; k += 2) s += 2.0 * j[k];
+  for (int l = 0; l <= L; ++l) out[l] = j[l] / s;
+}
+
+// Truncation order (reading R5): smallest integer l > R, l >= 1, with |J_{l+1}(R)| < tol.
+int fq_cheb_order(double R, double tol) {
+  int l = std::max(1, (int)floor(R) + 1);
+  for (;;) {
+    std::vector<double> j(l + 2);
+    fq_bessel_miller(R, l + 1, j.data());
+    if (fabs(j[l + 1]) < tol || l > 100000) return l;
+    ++l;
+  }
+}
+
+// Number of eigenvalues < x of the symmetric tridiagonal (diag, off) by the Sturm count of
+// the LDL^T pivots.
+static int sturm_count(const double* d, const double* e, int n, double x) {
+  int c = 0;
+  double q = d[0] - x;
+  if (q < 0) ++c;
+  for (int i = 1; i < n; ++i) {
+    if (q == 0.0) q = 1e-300;
+    q = (d[i] - x) - e[i - 1] * e[i - 1] / q;
+    if (q < 0) ++c;
+  }
+  return c;
+}
+
+// Extreme eigenvalues of a real symmetric tridiagonal matrix by bisection on Sturm counts,
+// bracketed by Gershgorin discs; converged to a few ulps of the spectral radius.
+void fq_tridiag_extremes(const double* d, const double* e, int n, double* lo, double* hi) {
+  double glo = 1e300, ghi = -1e300;
+  for (int i = 0; i < n; ++i) {
+    double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+    glo = std::min(glo, d[i] - r);
+    ghi = std::max(ghi, d[i] + r);
+  }
+  const double scale = std::max(fabs(glo), fabs(ghi)) + 1e-300;
+  // lowest: smallest x with count(x) >= 1
+  double a = glo - 1e-12 * scale, b = ghi + 1e-12 * scale;
+  for (int it = 0; it < 200 && b - a > 4e-16 * scale; ++it) {
+    double m = 0.5 * (a + b);
+    if (sturm_count(d, e, n, m) >= 1) b = m; else a = m;
+  }
+  *lo = a;  // count(a) = 0: every eigenvalue >= a
+  a = glo - 1e-12 * scale;
+  b = ghi + 1e-12 * scale;
+  for (int it = 0; it < 200 && b - a > 4e-16 * scale; ++it) {
+    double m = 0.5 * (a + b);
+    if (sturm_count(d, e, n, m) >= n) b = m; else a = m;
+  }
+  *hi = b;  // count(b) = n: every eigenvalue < b
+}
+
+// y = A x for a dense row-major symmetric A, rows split over host threads.
+static void matvec(const double* a, const double* x, double* y, int n, int nthreads) {
+  auto work = [&](int r0, int r1) {
+    for (int i = r0; i < r1; ++i) {
+      const double* row = a + (size_t)i * n;
+      double s = 0.0;
+      for (int j = 0; j < n; ++j) s += row[j] * x[j];
+      y[i] = s;
+    }
+  };
+  if (nthreads <= 1 || n < 256) { work(0, n); return; }
+  std::vector<std::thread> th;
+  int chunk = (n + nthreads - 1) / nthreads;
+  for (int t = 0; t < nthreads; ++t) {
+    int r0 = t * chunk, r1 = std::min(n, r0 + chunk);
+    if (r0 < r1) th.emplace_back(work, r0, r1);
+  }
+  for (auto& t : th) t.join();
+}
+
+// Extreme eigenvalues of the dense symmetric A by the Lanczos method (Lanczos 1950) with
+// full reorthogonalisation.  Returned [lo, hi] is the Ritz interval widened by the residual
+// norms of the two extreme Ritz pairs (each such pair has an eigenvalue within its residual)
+// plus 1e-6 of the span; with k >= n it is exact up to rounding.
+void fq_lanczos_extremes(const double* a, int n, int ksteps, uint64_t seed, double* lo, double* hi) {
+  const int k = std::min(n, ksteps);
+  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::vector<double> V((size_t)(k + 1) * n), w(n), alpha(k), beta(k + 1, 0.0);
+  // start vector: splitmix64 uniforms in (-1, 1)
+  uint64_t s = seed;
+  double nrm = 0.0;
+  for (int i = 0; i < n; ++i) {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    V[i] = ((double)(z >> 11) + 0.5) * (2.0 / 9007199254740992.0) - 1.0;
+    nrm += V[i] * V[i];
+  }
+  nrm = sqrt(nrm);
+  for (int i = 0; i < n; ++i) V[i] /= nrm;
+  int m = k;
+  for (int j = 0; j < k; ++j) {
+    double* vj = &V[(size_t)j * n];
+    matvec(a, vj, w.data(), n, (int)nt);
+    double al = 0.0;
+    for (int i = 0; i < n; ++i) al += w[i] * vj[i];
+    alpha[j] = al;
+    // full reorthogonalisation (twice is enough)
+    for (int pass = 0; pass < 2; ++pass)
+      for (int q = 0; q <= j; ++q) {
+        const double* vq = &V[(size_t)q * n];
+        double c = 0.0;
+        for (int i = 0; i < n; ++i) c += w[i] * vq[i];
+        for (int i = 0; i < n; ++i) w[i] -= c * vq[i];
+      }
+    double b = 0.0;
+    for (int i = 0; i < n; ++i) b += w[i] * w[i];
+    b = sqrt(b);
+    beta[j + 1] = b;
+    if (j + 1 == k) break;
+    if (b < 1e-13 * (fabs(al) + 1e-300)) { m = j + 1; break; }  // invariant subspace
+    double* vn = &V[(size_t)(j + 1) * n];
+    for (int i = 0; i < n; ++i) vn[i] = w[i] / b;
+  }
+  // Ritz values of T_m
+  std::vector<double> off(std::max(1, m - 1));
+  for (int i = 0; i + 1 < m; ++i) off[i] = beta[i + 1];
+  double tlo, thi;
+  fq_tridiag_extremes(alpha.data(), off.data(), m, &tlo, &thi);
+  // residual beta_m |s_{m-1}| of each extreme Ritz vector s (inverse iteration on T_m)
+  auto resid = [&](double theta) {
+    if (m >= n) return 0.0;
+    std::vector<double> x(m, 1.0), dd(m), cc(m), y(m);
+    const double shift = theta + 1e-10 * (fabs(theta) + 1.0) * (theta == thi ? 1 : -1);
+    for (int it = 0; it < 4; ++it) {
+      // solve (T - shift) y = x by the tridiagonal Thomas algorithm
+      for (int i = 0; i < m; ++i) dd[i] = alpha[i] - shift;
+      for (int i = 0; i + 1 < m; ++i) cc[i] = off[i];
+      std::vector<double> rhs = x;
+      for (int i = 1; i < m; ++i) {
+        double piv = dd[i - 1] != 0.0 ? dd[i - 1] : 1e-300;
+        double f = off[i - 1] / piv;
+        dd[i] -= f * cc[i - 1];
+        rhs[i] -= f * rhs[i - 1];
+      }
+      y[m - 1] = rhs[m - 1] / (dd[m - 1] != 0.0 ? dd[m - 1] : 1e-300);
+      for (int i = m - 2; i >= 0; --i) y[i] = (rhs[i] - cc[i] * y[i + 1]) / (dd[i] != 0 ? dd[i] : 1e-300);
+      double nn = 0.0;
+      for (double v : y) nn += v * v;
+      nn = sqrt(nn);
+      for (int i = 0; i < m; ++i) x[i] = y[i] / nn;
+    }
+    return fabs(beta[m] * x[m - 1]);
+  };
+  const double span = thi - tlo;
+  *lo = tlo - resid(tlo) - 1e-6 * span;
+  *hi = thi + resid(thi) + 1e-6 * span;
+}
+
+// Host part of plan creation: validates the problem, forms the Magnus scalars (reading R1),
+// bounds (reading R4), R, L and a_l (Eq. 12, reading R5).  No device work.
+fq_status fq_host_plan(const fq_problem* p, fq_plan* plan) {
+  if (!p) { fq_set_error("problem is NULL"); return FQ_EINVAL; }
+  if (p->n < 1 || p->steps < 1 || !(p->period > 0)) {
+    fq_set_error("need n >= 1, steps >= 1, period > 0 (got %d, %d, %g)", p->n, p->steps, p->period);
+    return FQ_EINVAL;
+  }
+  if (p->format != FQ_DENSE && p->format != FQ_TRIDIAG) { fq_set_error("bad format %d", p->format); return FQ_EINVAL; }
+  if (!p->h0 || !p->h1 || (p->format == FQ_TRIDIAG && p->n > 1 && !p->h0_off)) {
+    fq_set_error("operator arrays missing");
+    return FQ_EINVAL;
+  }
+  if (p->drive_kind != FQ_DRIVE_COS && p->drive_kind != FQ_DRIVE_PIECEWISE) {
+    fq_set_error("bad drive kind %d", p->drive_kind);
+    return FQ_EINVAL;
+  }
+  if (p->drive_kind == FQ_DRIVE_PIECEWISE && !p->f_steps) { fq_set_error("piecewise drive needs f_steps"); return FQ_EINVAL; }
+  if (p->precision < FQ_FP64 || p->precision > FQ_BF16X6) { fq_set_error("bad precision %d", p->precision); return FQ_EINVAL; }
+  if (p->format == FQ_TRIDIAG && p->precision > FQ_FP32) {
+    fq_set_error("tridiagonal format supports FQ_FP64 and FQ_FP32");
+    return FQ_EUNSUPPORTED;
+  }
+  if (p->format == FQ_DENSE && p->precision == FQ_FP32) {
+    fq_set_error("dense format supports FQ_FP64, FQ_BF16X3 and FQ_BF16X6");
+    return FQ_EUNSUPPORTED;
+  }
+  const int n = p->n, M = p->steps;
+  plan->n = n;
+  plan->steps = M;
+  plan->format = p->format;
+  plan->precision = p->precision;
+  plan->drive_kind = p->drive_kind;
+  plan->stride = p->checkpoint_stride > 0 ? p->checkpoint_stride : 16;
+  plan->period = p->period;
+  plan->tol = p->cheb_tol > 0 ? p->cheb_tol : 1e-14;
+  const double h = p->period / M;
+  plan->h = h;
+  plan->ma.assign(M, h);
+  plan->mb.resize(M);
+  plan->mc.resize(M);
+  for (int m = 0; m < M; ++m) {
+    const double tau = (m + 0.5) * h;
+    if (p->drive_kind == FQ_DRIVE_COS) {
+      const double f = fq_drive_f(0, p->f_dc, p->f_ac, p->omega, p->phi0, tau);
+      const double f1 = fq_drive_f(1, p->f_dc, p->f_ac, p->omega, p->phi0, tau);
+      const double f2 = fq_drive_f(2, p->f_dc, p->f_ac, p->omega, p->phi0, tau);
+      plan->mb[m] = h * f + h * h * h * f2 / 24.0;
+      plan->mc[m] = h * h * h * f1 / 12.0;
+    } else {
+      plan->mb[m] = h * p->f_steps[m];
+      plan->mc[m] = 0.0;
+    }
+  }
+  // range of the H1 coefficient g_m = b_m / h
+  double glo = 1e300, ghi = -1e300, kmax = 0.0;
+  for (int m = 0; m < M; ++m) {
+    glo = std::min(glo, plan->mb[m] / h);
+    ghi = std::max(ghi, plan->mb[m] / h);
+    kmax = std::max(kmax, fabs(plan->mc[m] / h));
+  }
+  if (p->drive_kind == FQ_DRIVE_PIECEWISE) {  // reading R11: widen by 10% and freeze
+    const double pad = 0.1 * std::max(std::max(ghi - glo, fabs(glo)), std::max(fabs(ghi), 1e-3));
+    glo -= pad;
+    ghi += pad;
+  }
+  double emin, emax;
+  if (p->e_max > p->e_min) {
+    emin = p->e_min;
+    emax = p->e_max;
+  } else if (p->format == FQ_TRIDIAG) {
+    std::vector<double> d(n), k(std::max(1, n - 1));
+    double l1, h1v, l2, h2v;
+    for (int i = 0; i < n; ++i) d[i] = p->h0[i] + glo * p->h1[i];
+    fq_tridiag_extremes(d.data(), p->h0_off, n, &l1, &h1v);
+    for (int i = 0; i < n; ++i) d[i] = p->h0[i] + ghi * p->h1[i];
+    fq_tridiag_extremes(d.data(), p->h0_off, n, &l2, &h2v);
+    emin = std::min(l1, l2);
+    emax = std::max(h1v, h2v);
+    if (kmax > 0 && n > 1) {  // ||[H0,H1]||_2 from the tridiagonal with |K_{i+1,i}|
+      std::vector<double> z(n, 0.0);
+      for (int i = 0; i + 1 < n; ++i) k[i] = fabs(p->h0_off[i] * (p->h1[i] - p->h1[i + 1]));
+      double kl, kh;
+      fq_tridiag_extremes(z.data(), k.data(), n, &kl, &kh);
+      const double w = kmax * std::max(fabs(kl), fabs(kh));
+      emin -= w;
+      emax += w;
+    }
+  } else {
+    std::vector<double> a((size_t)n * n);
+    double l1, h1v, l2, h2v;
+    for (size_t i = 0; i < (size_t)n * n; ++i) a[i] = p->h0[i] + glo * p->h1[i];
+    fq_lanczos_extremes(a.data(), n, 320, 0x1234567ull, &l1, &h1v);
+    for (size_t i = 0; i < (size_t)n * n; ++i) a[i] = p->h0[i] + ghi * p->h1[i];
+    fq_lanczos_extremes(a.data(), n, 320, 0x7654321ull, &l2, &h2v);
+    emin = std::min(l1, l2);
+    emax = std::max(h1v, h2v);
+    if (kmax > 0) {  // ||[H0,H1]||_2 <= 2 ||H0||_2 ||H1||_2
+      double a0, b0, a1, b1;
+      fq_lanczos_extremes(p->h0, n, 160, 0x51ull, &a0, &b0);
+      fq_lanczos_extremes(p->h1, n, 160, 0x52ull, &a1, &b1);
+      const double w = kmax * 2.0 * std::max(fabs(a0), fabs(b0)) * std::max(fabs(a1), fabs(b1));
+      emin -= w;
+      emax += w;
+    }
+  }
+  if (!(p->e_max > p->e_min)) {
+    const double margin = 1e-12 * std::max(std::max(fabs(emin), fabs(emax)), 1.0);
+    emin -= margin;
+    emax += margin;
+  }
+  if (!(emax > emin)) {  // degenerate spectrum (N = 1, or H a multiple of 1)
+    const double w = 1e-12 * std::max(fabs(emin), 1.0);
+    emin -= w;
+    emax += w;
+  }
+  plan->e_min = emin;
+  plan->e_max = emax;
+  plan->delta_e = 0.5 * (emax - emin);
+  plan->beta = plan->delta_e + emin;
+  plan->R = h * plan->delta_e;
+  plan->L = fq_cheb_order(plan->R, plan->tol);
+  plan->cheb.resize(plan->L + 1);
+  fq_bessel_miller(plan->R, plan->L, plan->cheb.data());
+  for (int l = 1; l <= plan->L; ++l) plan->cheb[l] *= 2.0;
+  plan->phase_re = cos(plan->beta * h);
+  plan->phase_im = -sin(plan->beta * h);
+  // Omega~_m = (Omega_m / h - beta) / Delta E  (reading R2)
+  const double inv = 1.0 / (h * plan->delta_e);
+  plan->sa.resize(M);
+  plan->sb.resize(M);
+  plan->sc.resize(M);
+  for (int m = 0; m < M; ++m) {
+    plan->sa[m] = plan->ma[m] * inv;
+    plan->sb[m] = plan->mb[m] * inv;
+    plan->sc[m] = plan->mc[m] * inv;
+  }
+  plan->sbeta = plan->beta / plan->delta_e;
+  return FQ_OK;
+}

@@ -1,0 +1,89 @@
+"""C-ABI library on the CPU: it loads, exports every symbol include/floquet.h declares, and its
+host planner (stage a1: Magnus scalars, bounds, R, L, Bessel weights) agrees with the oracle.
+No compute call needs a GPU here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+from scipy.special import jv
+
+import floquet_inputs as fi
+import oracle as o
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_1508_07621_gb300", "libfloquet.so")
+
+
+@pytest.fixture(scope="module")
+def fq():
+    if not os.path.exists(LIB):
+        import __graft_entry__
+        __graft_entry__.build()
+    import paper_1508_07621_gb300 as fq
+    return fq
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "floquet.h")).read()
+    return sorted(set(re.findall(r"\b(floquet_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(fq):
+    names = declared_symbols()
+    assert len(names) >= 12
+    lib = ctypes.CDLL(LIB)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_dimer_plan_matches_oracle(fq):
+    d = fi.config_dimer()
+    prob, keep = fq.make_problem(d.n, fq.FQ_TRIDIAG, d.h0_diag, d.h1_diag, d.drive.period, d.steps,
+                                 h0_off=d.h0_off, f_ac=1.5, omega=3.0, precision=fq.FQ_FP32)
+    info, a = fq.floquet_plan_inspect(prob)
+    p = o.plan_for_drive_tridiag(d.h0_diag, d.h0_off, d.h1_diag, d.drive, d.steps)
+    assert info.L == p.L == 39
+    assert abs(info.R - p.R) < 1e-12 * p.R
+    assert abs(info.e_min - p.e_min) < 1e-9 * abs(p.e_min) and abs(info.e_max - p.e_max) < 1e-9 * p.e_max
+    # Miller recurrence in the library vs the library routine J_l (scipy)
+    ref = 2 * jv(np.arange(info.L + 1), info.R)
+    ref[0] /= 2
+    assert np.max(np.abs(a - ref)) < 1e-14
+
+
+@pytest.mark.parametrize("R", [0.0, 1e-6, 0.0859, 2.5, 13.947, 60.0])
+def test_library_bessel_and_order(fq, R):
+    """Library L and a_l against scipy J_l for a problem whose R is set through user bounds."""
+    n = 3
+    h = 1.0
+    prob, keep = fq.make_problem(n, fq.FQ_TRIDIAG, np.zeros(n), np.zeros(n), h, 1, h0_off=np.zeros(n - 1),
+                                 f_ac=0.0, omega=1.0, e_min=-R if R > 0 else -1e-300, e_max=R if R > 0 else 1e-300)
+    info, a = fq.floquet_plan_inspect(prob)
+    assert info.L == o.chebyshev_order(info.R)
+    ref = o.bessel_coefficients(info.R, info.L)
+    assert np.max(np.abs(a - ref)) < 1e-14 * max(1.0, info.L)
+
+
+def test_dense_plan_bounds_contain_exact(fq):
+    """Lanczos bounds of the library contain the oracle's exact bounds and are tight (<1e-3)."""
+    m = fi.config_goe64()
+    prob, keep = fq.make_problem(64, fq.FQ_DENSE, m.h0, m.h1, m.drive.period, m.steps, f_ac=1.0, omega=1.0)
+    info, _ = fq.floquet_plan_inspect(prob)
+    p = o.plan_for_drive_dense(m.h0, m.h1, m.drive, m.steps)
+    assert info.e_min <= p.e_min and info.e_max >= p.e_max
+    assert (info.e_max - info.e_min) < (p.e_max - p.e_min) * (1 + 1e-3)
+    assert info.L == p.L
+
+
+def test_argument_errors(fq):
+    prob, keep = fq.make_problem(0, fq.FQ_DENSE, np.zeros(1), np.zeros(1), 1.0, 1)
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_plan_inspect(prob)
+    assert e.value.status == fq.FQ_EINVAL
+    prob, keep = fq.make_problem(4, fq.FQ_TRIDIAG, np.zeros(4), np.zeros(4), 1.0, 2, h0_off=np.zeros(3),
+                                 precision=fq.FQ_BF16X3)
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_plan_inspect(prob)
+    assert e.value.status == fq.FQ_EUNSUPPORTED

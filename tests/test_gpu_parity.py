@@ -1,0 +1,243 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs.
+
+Tolerances (written here, derived in the design notes):
+  * FP64 paths: max |U - U_oracle| <= 1e-10 (the method's own truncation is 1e-14 per step).
+  * FP32 tridiagonal paths: max |U - U_oracle| <= tol_f32(M, L, R) = 2 M R u + 4 sqrt(M) L u,
+    u = 2^-24.  First term: the FP32 rounding of Omega~'s entries (|entries| <= 1, so
+    ||dOmega~||_2 <= 2u) perturbs each step's exponent exp(-i R Omega~) by at most 2Ru, and that
+    systematic error adds up coherently over M steps.  Second term: the rounding of the L
+    operator products of a step (about L u per step on a unit-norm state) adds up as a random
+    walk over M unitary steps (factor 4 of headroom).  Both bound a column's 2-norm error and so
+    its largest entry error.
+"""
+import math
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import floquet_inputs as fi
+import oracle as o
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+def tol_f32(M, L, R):
+    return 2.0 * M * R * U32 + 4.0 * math.sqrt(M) * L * U32
+
+
+@pytest.fixture(scope="module")
+def fq():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1508_07621_gb300 as fq
+    return fq
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def cuda_c128(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).cuda()
+
+
+# ------------------------------------------------------------------ dense FP64
+def test_goe64_fp64_build(fq):
+    m = fi.config_goe64()
+    plan = fq.Plan.dense(m.h0, m.h1, omega=m.drive.omega, f_ac=m.drive.f_ac, steps=m.steps)
+    assert plan.info.L == 7
+    U = plan.build_UT()
+    assert plan.check_status() == fq.FQ_OK
+    ref_plan = o.plan_for_drive_dense(m.h0, m.h1, m.drive, m.steps)
+    ref = o.build_ut_dense(m.h0, m.h1, ref_plan)
+    u = to_np(U)
+    assert np.max(np.abs(u - ref)) <= 1e-10
+    assert np.max(np.abs(u - u.T)) <= 1e-12          # even drive: U_T = U_T^T
+    mx, fro = fq.api.unitarity_defect(U)
+    assert mx <= 1e-12 and fro <= 1e-12
+    eps, eps_ref = o.quasienergies(u, m.drive.period), o.quasienergies(ref, m.drive.period)
+    assert np.max(np.abs(eps - eps_ref)) <= 1e-10
+
+
+def test_dense_fp64_ragged_propagate_range(fq):
+    """N = 37 (ragged against the 32/8 tiles), 5 random states, steps 3..10 of 16, non-even drive."""
+    n, M = 37, 16
+    h0, h1 = fi.goe(n, 801), fi.goe(n, 802)
+    drv = fi.Drive(0.3, 1.4, 1.1, 0.8)
+    x0 = fi.ginibre(n, 803)[:5]
+    x0 /= np.linalg.norm(x0, axis=1, keepdims=True)
+    plan = fq.Plan.dense(h0, h1, omega=drv.omega, f_ac=drv.f_ac, f_dc=drv.f_dc, phi0=drv.phi0, steps=M)
+    X = plan.propagate(cuda_c128(x0), 3, 11)
+    ref = o.propagate_dense(h0, h1, o.plan_for_drive_dense(h0, h1, drv, M), x0.T, 3, 11).T
+    assert np.max(np.abs(to_np(X) - ref)) <= 1e-10
+    # empty range copies, zero states is a no-op
+    Y = plan.propagate(cuda_c128(x0), 4, 4)
+    assert np.array_equal(to_np(Y), x0)
+
+
+@pytest.mark.parametrize("n,scale", [(1, 1.0), (2, 1.0), (6, 1e-9)])
+def test_dense_fp64_degenerate(fq, n, scale):
+    """N = 1 (zero spectral width), N = 2, and a tiny operator with L = 1 (one-term steps)."""
+    h0, h1 = scale * fi.goe(n, 901), scale * fi.goe(n, 902)
+    drv = fi.Drive(0.1, 0.7, 1.0, 0.2)
+    plan = fq.Plan.dense(h0, h1, omega=1.0, f_ac=0.7, f_dc=0.1, phi0=0.2, steps=12)
+    if scale < 1e-6:
+        assert plan.info.L == 1
+    U = to_np(plan.build_UT())
+    ref = o.build_ut_dense(h0, h1, o.plan_for_drive_dense(h0, h1, drv, 12))
+    assert np.max(np.abs(U - ref)) <= 1e-10
+
+
+# ------------------------------------------------------------------ tridiagonal
+def dimer_plan(fq, d, precision, kernel=0):
+    return fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=d.drive.f_ac,
+                           f_dc=d.drive.f_dc, phi0=d.drive.phi0, steps=d.steps, precision=precision,
+                           kernel=kernel)
+
+
+@pytest.mark.parametrize("precision,kernel", [(0, 1), (1, 1), (1, 2)])
+def test_dimer40_all_paths(fq, precision, kernel):
+    """Small dimer (dim 41, M = 100): FP64 streaming, FP32 streaming, FP32 resident."""
+    d = fi.config_dimer(nb=40, steps=100)
+    plan = dimer_plan(fq, d, precision, kernel)
+    U = to_np(plan.build_UT())
+    assert plan.check_status() == fq.FQ_OK
+    ref = o.build_ut_tridiag(d.h0_diag, d.h0_off, d.h1_diag,
+                             o.plan_for_drive_tridiag(d.h0_diag, d.h0_off, d.h1_diag, d.drive, d.steps))
+    tol = 1e-10 if precision == 0 else tol_f32(d.steps, plan.info.L, plan.info.R)
+    assert np.max(np.abs(U - ref)) <= tol
+
+
+@pytest.mark.parametrize("nb", [4, 2047, 6000, 10239])
+def test_dimer_resident_ragged_sizes(fq, nb):
+    """Resident kernel across its per-thread widths (4..20 rows) and ragged tails; 3 states,
+    20 steps of the M = 2000 chain (phase offset drive)."""
+    d = fi.config_dimer(nb=nb, steps=2000)
+    d.drive = fi.Drive(0.2, 1.5, 3.0, 0.4)
+    plan = dimer_plan(fq, d, 1, 2)
+    n = d.n
+    x0 = np.zeros((3, n), complex)
+    x0[0, 0] = 1
+    x0[1, n - 1] = 1
+    x0[2] = fi.ginibre(n, 11)[0] if n < 4000 else np.exp(2j * np.pi * fi.uniform(12, n))
+    x0[2] /= np.linalg.norm(x0[2])
+    X = to_np(plan.propagate(cuda_c128(x0), 0, 20))
+    refp = o.plan_for_drive_tridiag(d.h0_diag, d.h0_off, d.h1_diag, d.drive, d.steps)
+    ref = o.propagate_tridiag(d.h0_diag, d.h0_off, d.h1_diag, refp, x0.T, 0, 20).T
+    assert np.max(np.abs(X - ref)) <= tol_f32(20, plan.info.L, plan.info.R)
+
+
+def _oracle_dimer_column(j):
+    d = fi.config_dimer()
+    p = o.plan_for_drive_tridiag(d.h0_diag, d.h0_off, d.h1_diag, d.drive, d.steps)
+    return o.build_ut_tridiag(d.h0_diag, d.h0_off, d.h1_diag, p, [j])[:, 0]
+
+
+@pytest.mark.slow
+def test_dimer_full_size_resident_sampled_columns(fq):
+    """The benchmarked workload (dim 10001, M = 2000, L = 39, FP32 resident kernel, one launch
+    over all 10001 states): sampled columns against the oracle, unitarity on 64 columns."""
+    import torch
+    cols = [0, 1, 5000, 9999, 10000]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(cols)) as pool:
+        pending = pool.map_async(_oracle_dimer_column, cols)
+        d = fi.config_dimer()
+        plan = dimer_plan(fq, d, 1, 0)
+        assert plan.info.L == 39
+        U = plan.build_UT()
+        assert plan.check_status() == fq.FQ_OK
+        ref = np.stack(pending.get(timeout=1800), axis=1)
+    got = to_np(U[:, cols])
+    tol = tol_f32(d.steps, 39, plan.info.R)
+    err = np.max(np.abs(got - ref))
+    print(f"dimer 10001 FP32 resident: max err {err:.3e} (tol {tol:.3e})")
+    assert err <= tol
+    sample = torch.arange(0, d.n, 157, dtype=torch.int32, device="cuda")
+    mx, fro = fq.api.unitarity_defect(U, sample)
+    assert mx <= 2 * tol
+
+
+def test_dimer_u0_full_size_closed_form(fq):
+    """U = 0 dimer at dim 10001 (FP32 resident, one launch over all states): H is the nb-boson
+    image of h = [[f/2, -1], [-1, -f/2]], so U_T = D(u) with u the 2x2 Magnus chain of exact
+    exponentials (closed form, no oracle).  Checks: U_T maps the SU(2) coherent state
+    c_n = sqrt(C(nb, n)) a^n b^(nb-n) to the coherent state of u (a, b), and Tr U_T equals the
+    character sum_k l1^k l2^(nb-k)."""
+    import torch
+    from scipy.special import gammaln
+    nb = 10000
+    d = fi.config_dimer(nb=nb, U=0.0)
+    plan = dimer_plan(fq, d, 1, 0)
+    U = plan.build_UT()
+    assert plan.check_status() == fq.FQ_OK
+    h = d.drive.period / d.steps
+    sig = [np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]])]
+    u = np.eye(2, dtype=complex)
+    for m in range(d.steps):
+        tau = (m + 0.5) * h
+        f = d.drive.f_ac * math.cos(d.drive.omega * tau)
+        f1 = -d.drive.f_ac * d.drive.omega * math.sin(d.drive.omega * tau)
+        f2 = -d.drive.f_ac * d.drive.omega ** 2 * math.cos(d.drive.omega * tau)
+        b = h * f + h ** 3 * f2 / 24
+        c = h ** 3 * f1 / 12
+        # omega = a h0 + b h1 + c i[h0,h1] with h0 = -sigma_x, h1 = sigma_z / 2, i[h0,h1] = -sigma_y
+        w = np.array([-h, -c, 0.5 * b])
+        r = np.linalg.norm(w)
+        u = (math.cos(r) * np.eye(2) - 1j * math.sin(r) / r * sum(wi * s for wi, s in zip(w, sig))) @ u
+    tol = tol_f32(d.steps, plan.info.L, plan.info.R)
+
+    def coherent(a, b):
+        n = np.arange(nb + 1)
+        logc = 0.5 * (gammaln(nb + 1) - gammaln(n + 1) - gammaln(nb - n + 1)) + n * np.log(a + 0j) \
+            + (nb - n) * np.log(b + 0j)
+        return np.exp(logc)
+
+    a0, b0 = math.cos(0.55), np.exp(0.3j) * math.sin(0.55)
+    c0 = coherent(a0, b0)
+    a1, b1 = u @ np.array([a0, b0])
+    got = to_np(U @ cuda_c128(c0))
+    err = np.linalg.norm(got - coherent(a1, b1))
+    print(f"U=0 dimer coherent-state error {err:.3e} (tol {tol:.3e})")
+    assert err <= tol
+    l1, l2 = np.linalg.eigvals(u)
+    k = np.arange(nb + 1)
+    char = np.sum(np.exp(-1j * (k * -np.angle(l1) + (nb - k) * -np.angle(l2))))
+    assert abs(complex(U.diagonal().sum().item()) - char) <= math.sqrt(d.n) * tol
+
+
+def test_bound_violation_sets_status(fq):
+    """Host-made fault: caller bounds at half the true half-span make T_l grow; the device check
+    must report FQ_EBOUND (no trap), and the status clears for the next call."""
+    d = fi.config_dimer(nb=40, steps=100)
+    p = o.plan_for_drive_tridiag(d.h0_diag, d.h0_off, d.h1_diag, d.drive, d.steps)
+    c, w = 0.5 * (p.e_min + p.e_max), 0.25 * (p.e_max - p.e_min)
+    for precision, kernel in ((0, 1), (1, 1), (1, 2)):
+        plan = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=3.0, f_ac=1.5, steps=d.steps,
+                               precision=precision, kernel=kernel, e_min=c - w, e_max=c + w)
+        plan.build_UT()
+        assert plan.check_status() == fq.FQ_EBOUND, (precision, kernel)
+        assert plan.check_status() == fq.FQ_OK
+    m = fi.config_goe64()
+    pm = o.plan_for_drive_dense(m.h0, m.h1, m.drive, m.steps)
+    c, w = 0.5 * (pm.e_min + pm.e_max), 0.2 * (pm.e_max - pm.e_min)
+    plan = fq.Plan.dense(m.h0, m.h1, omega=1.0, f_ac=1.0, steps=m.steps, e_min=c - w, e_max=c + w)
+    plan.build_UT()
+    assert plan.check_status() == fq.FQ_EBOUND
+
+
+def test_workspace_errors(fq):
+    import torch
+    d = fi.config_dimer(nb=40, steps=10)
+    plan = dimer_plan(fq, d, 1, 1)
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    U = torch.empty((d.n, d.n), dtype=torch.complex128, device="cuda")
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_build_UT(plan.handle, U, small)
+    assert e.value.status == fq.FQ_EINVAL
+    with pytest.raises(fq.FloquetError):
+        fq.floquet_propagate(plan.handle, U, U, d.n, 5, 3, small)
