@@ -32,7 +32,8 @@
  *    calls only enqueue work on it and return without synchronising, except where stated.
  *  - Every call returns an fq_status.  Argument errors are reported before any work is
  *    enqueued.  Device-side checks (a propagated entry larger than the bound implied by
- *    unitarity, or NaN) set bits in a per-plan status word; floquet_check_status
+ *    unitarity, a Clenshaw vector above its bound, a state whose norm drifts by more than
+ *    1e-3 relative over the chain, or NaN) set bits in a per-plan status word; floquet_check_status
  *    synchronises the stream, returns FQ_EBOUND if any bit was set, and clears it.  The
  *    library never traps or aborts.  floquet_last_error returns a message for the last
  *    failing call of the calling thread.

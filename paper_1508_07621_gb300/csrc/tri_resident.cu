@@ -218,6 +218,23 @@ k_tri_resident(const float* __restrict__ d2, const float* __restrict__ e2r, cons
     // warp has consumed this step's last slots before they are overwritten
     __syncthreads();
   }
+  // unitarity of the chain: the state's norm must be preserved (a spectral bound that is too
+  // tight keeps the entries small but makes the truncated series non-unitary)
+  float nrm_end = 0.f;
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int s = q * RES_NT + t;
+    nrm_end = fmaf(R.vr[s], R.vr[s], fmaf(R.vi[s], R.vi[s], nrm_end));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nrm_end += __shfl_xor_sync(0xffffffffu, nrm_end, o);
+  __syncthreads();
+  if (R.lane == 0) R.sh->red[R.warp] = nrm_end;
+  __syncthreads();
+  float tot_end = 0.f;
+#pragma unroll
+  for (int w = 0; w < RES_NW; ++w) tot_end += R.sh->red[w];
+  bad |= !(fabsf(tot_end - tot) <= 1e-3f * tot + 1e-30f);
   if (bad) atomicOr(status, FQ_BIT_BOUND);
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
