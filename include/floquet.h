@@ -162,6 +162,26 @@ size_t floquet_grad_workspace_size(const fq_plan* plan);
 fq_status floquet_grad(fq_plan* plan, const double* d_f, const void* d_W, double* d_loss,
                        double* d_grad, void* d_ws, size_t ws_bytes, void* stream);
 
+/* Size of the library's static device scratch array used by floquet_build_UT_static. */
+#define FLOQUET_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* U_T without any device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc (code embedded in a runtime that owns all device
+ * memory, or that must not grow its device footprint after start-up).  It runs the same
+ * resident FP32 tridiagonal chain as floquet_build_UT, but takes the problem directly (host
+ * arrays, no plan) and keeps every intermediate - operators, per-step scalars, the 2 Omega~
+ * coefficient arrays (3 * M * ceil4(N) floats) and the status word - in one static __device__
+ * array of FLOQUET_STATIC_SCRATCH_BYTES that each GPU loading the library holds until exit.
+ *  - problem: FQ_TRIDIAG with FQ_FP32 only (N <= 10240, L <= 128); larger scratch needs are
+ *    rejected with FQ_EINVAL before any work, as are other formats (FQ_EUNSUPPORTED).
+ *  - d_U: caller-owned N x N complex128 output, U[i][j] = <i|U_T|j>, as floquet_build_UT.
+ *  - Calls no cudaMalloc/cudaFree.  The first call on a device looks up the array's device
+ *    address with that device current (make it before any stream capture).
+ *  - Synchronises `stream` and returns FQ_EBOUND if the device check fired.
+ *  - Every call shares the array and overwrites what the previous call left there; calls
+ *    that overlap on the GPU (other streams, other host threads) race and must not be made. */
+fq_status floquet_build_UT_static(const fq_problem* problem, void* d_U, void* stream);
+
 /* Synchronises `stream`; returns FQ_EBOUND (and clears the word) if a device check of this
  * plan fired since the last call, FQ_OK otherwise. */
 fq_status floquet_check_status(fq_plan* plan, void* stream);

@@ -60,6 +60,7 @@ _SIGS = {
     "floquet_grad_workspace_size": (_sz, [_vp]),
     "floquet_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "floquet_check_status": (ctypes.c_int, [_vp, _vp]),
+    "floquet_build_UT_static": (ctypes.c_int, [ctypes.POINTER(fq_problem), _vp, _vp]),
     "floquet_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -173,6 +174,11 @@ def floquet_grad(plan: int, f, W, loss, grad, ws, stream=None) -> None:
     _check(lib.floquet_grad(_vp(plan), _ptr(f), _ptr(W), _ptr(loss), _ptr(grad), _ptr(ws),
                             ws.numel() * ws.element_size() if ws is not None else 0, _stream(stream)),
            "floquet_grad")
+
+
+def floquet_build_UT_static(problem, U, stream=None) -> None:
+    """No-allocation U_T (resident FP32 tridiagonal chain, static device scratch); see floquet.h."""
+    _check(lib.floquet_build_UT_static(ctypes.byref(problem), _ptr(U), _stream(stream)), "floquet_build_UT_static")
 
 
 def floquet_check_status(plan: int, stream=None) -> int:
