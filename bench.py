@@ -37,7 +37,32 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", choices=["resident", "stream"], default=None,
+                    help="run one small capture case of a kernel twice and exit (for ncu --set full)")
     return ap.parse_args()
+
+
+def run_ncu_case(case):
+    """Small cases for detailed ncu captures (a few GB at most, inputs larger than L2):
+    resident: 152 states (one wave on 152 SMs) over steps 0..19 of the benchmark chain;
+    stream:   2048 states through step 0 (39 streaming FP32 term launches, 0.5 GB of states)."""
+    import torch
+    import floquet_inputs as fi
+    import paper_1508_07621_gb300 as fq
+    d = fi.config_dimer(nb=NB, steps=STEPS)
+    n = d.n
+    kernel = fq.FQ_KERNEL_RESIDENT if case == "resident" else fq.FQ_KERNEL_STREAM
+    plan = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=d.drive.f_ac,
+                           steps=d.steps, precision=fq.FQ_FP32, kernel=kernel)
+    nc, m_end = (152, 20) if case == "resident" else (2048, 1)
+    x0 = torch.zeros((nc, n), dtype=torch.complex128, device="cuda")
+    x0[torch.arange(nc), torch.arange(nc) * (n // nc)] = 1.0
+    ws = fq.workspace(plan.workspace_size(nc))
+    x = torch.empty_like(x0)
+    for _ in range(2):
+        fq.floquet_propagate(plan.handle, x0, x, nc, 0, m_end, ws)
+    torch.cuda.synchronize()
+    print(f"ncu case {case}: {nc} states, steps 0..{m_end - 1}, status {plan.check_status()}")
 
 
 def dist_env():
@@ -239,7 +264,9 @@ def run_ours(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.ncu_case:
+        run_ncu_case(a.ncu_case)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

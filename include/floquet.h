@@ -169,8 +169,9 @@ fq_status floquet_grad(fq_plan* plan, const double* d_f, const void* d_W, double
  * for callers that cannot call cudaMalloc (code embedded in a runtime that owns all device
  * memory, or that must not grow its device footprint after start-up).  It runs the same
  * resident FP32 tridiagonal chain as floquet_build_UT, but takes the problem directly (host
- * arrays, no plan) and keeps every intermediate - operators, per-step scalars, the 2 Omega~
- * coefficient arrays (3 * M * ceil4(N) floats) and the status word - in one static __device__
+ * arrays, no plan) and keeps every intermediate - operators, per-step scalars, the per-step
+ * operator coefficients and frame rotations ((2M + 1) * ceil4(N) float pairs) and the status
+ * word - in one static __device__
  * array of FLOQUET_STATIC_SCRATCH_BYTES that each GPU loading the library holds until exit.
  *  - problem: FQ_TRIDIAG with FQ_FP32 only (N <= 10240, L <= 128); larger scratch needs are
  *    rejected with FQ_EINVAL before any work, as are other formats (FQ_EUNSUPPORTED).

@@ -74,6 +74,16 @@ class Plan:
         B.floquet_propagate(self.handle, x0, out, ncols, m_begin, m_end, ws, stream)
         return out
 
+    def grad(self, f, W, ws=None, stream=None):
+        """(loss, dL/df) of L = 1 - |Tr(W^+ U_T)|^2 / N^2 for the piecewise amplitudes f (device tensors)."""
+        import torch
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        g = torch.empty(self.info.steps, dtype=torch.float64, device="cuda")
+        if ws is None:
+            ws = workspace(B.floquet_grad_workspace_size(self.handle))
+        B.floquet_grad(self.handle, f, W, loss, g, ws, stream)
+        return loss, g
+
     def check_status(self, stream=None) -> int:
         return B.floquet_check_status(self.handle, stream)
 

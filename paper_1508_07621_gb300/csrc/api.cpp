@@ -58,6 +58,8 @@ size_t layout(const fq_plan* p, int nc, int nsteps, void* ws, StateWs* out) {
       for (int q = 0; q < 2; ++q) w.buf[b][q] = c.take<char>((size_t)nc * ld * es);
   } else if (p->path == PATH_TRI_RESIDENT) {
     w.coeff = c.take<char>(fq_resident_coeff_bytes(n, nsteps));
+  } else if (p->path == PATH_DENSE_SPLIT) {
+    w.coeff = c.take<char>(fq_split_workspace(p, nc, nullptr, nullptr));
   }
   if (out) *out = w;
   return c.used;
@@ -153,20 +155,18 @@ fq_status propagate_impl(fq_plan* p, const double* x0, double* x, int nc, int m_
   fq_status st = check_ws(p, nc, nsteps, ws, ws_bytes);
   if (st != FQ_OK) return st;
   if (nc == 0 || n == 0) return FQ_OK;
-  if (p->path == PATH_TRI_STREAM && nc > 65535) {
-    fq_set_error("streaming tridiagonal kernel: at most 65535 states per call (got %d)", nc);
-    return FQ_EUNSUPPORTED;
-  }
   StateWs w;
   layout(p, nc, nsteps, ws, &w);
   if (p->path == PATH_TRI_RESIDENT) {
-    const int ld = tri_ld(n);
-    float* d2 = (float*)w.coeff;
-    fq_launch_tri_coeffs_f32(p, m_begin, nsteps, 2.0, d2, d2 + (size_t)nsteps * ld, d2 + 2 * (size_t)nsteps * ld, s);
-    st = fq_launch_resident(p, d2, d2 + (size_t)nsteps * ld, identity ? nullptr : x0, x, transpose_out, nc, m_begin,
-                            m_end, s);
+    fq_launch_gauge_coeffs(p, m_begin, nsteps, w.coeff, s);
+    st = fq_launch_resident(p, w.coeff, identity ? nullptr : x0, x, transpose_out, nc, m_begin, m_end, s);
     if (st != FQ_OK) return st;
     return cuda_ok(cudaGetLastError(), "resident chain");
+  }
+  if (p->path == PATH_DENSE_SPLIT) {
+    st = fq_split_propagate(p, x0, x, nc, m_begin, m_end, identity, transpose_out, w.coeff, s);
+    if (st != FQ_OK) return st;
+    return cuda_ok(cudaGetLastError(), "split-precision chain");
   }
   const bool f64 = p->precision == FQ_FP64;
   const int ld = p->path == PATH_DENSE_F64 ? n : tri_ld(n);
@@ -233,11 +233,6 @@ fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
     p->path = (res_ok && prob->kernel != FQ_KERNEL_STREAM) ? PATH_TRI_RESIDENT : PATH_TRI_STREAM;
   } else {
     p->path = p->precision == FQ_FP64 ? PATH_DENSE_F64 : PATH_DENSE_SPLIT;
-    if (p->path == PATH_DENSE_SPLIT) {
-      fq_set_error("split-precision dense path not built yet");
-      delete p;
-      return FQ_EUNSUPPORTED;
-    }
   }
   cudaGetDevice(&p->device);
   auto fail = [&](cudaError_t e, const char* what) {
@@ -390,15 +385,3 @@ fq_status floquet_check_status(fq_plan* p, void* stream) {
 }
 
 }  // extern "C"
-
-extern "C" size_t floquet_grad_workspace_size(const fq_plan* p) {
-  (void)p;
-  return 0;
-}
-
-extern "C" fq_status floquet_grad(fq_plan* p, const double* d_f, const void* d_W, double* d_loss, double* d_grad,
-                                  void* d_ws, size_t ws_bytes, void* stream) {
-  (void)p; (void)d_f; (void)d_W; (void)d_loss; (void)d_grad; (void)d_ws; (void)ws_bytes; (void)stream;
-  fq_set_error("floquet_grad: not built yet");
-  return FQ_EUNSUPPORTED;
-}

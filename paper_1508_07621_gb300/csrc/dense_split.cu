@@ -1,0 +1,563 @@
+// Split-precision dense Chebyshev term on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// One term of Eq. 10 on a block of nc state rows: Y^T = Psi^T Omega~^T with Omega~ = S + i A
+// (S real symmetric, A real antisymmetric).  Concatenating real and imaginary parts along K,
+//   Yr = [Psi_r | Psi_i] [S | -A]^T,   Yi = [Psi_r | Psi_i] [A | S]^T      (K' = 2 Np)
+// so both accumulators share the left operand.  Every operand is held as NS BF16 slices
+// (x = x_0 + x_1 + ..., x_s = bf16 of the remainder), and the products x_a y_b with a + b < NS
+// (3 for NS = 2, 6 for NS = 3) are summed in FP32 in tensor memory.  The epilogue applies the
+// recurrence psi_{l+1} = -2i Y + psi_{l-1}, the Bessel accumulation and the step phase on FP32
+// master copies (Eqs. 10, 12) and writes the next term's slices.
+//
+// CTA: 128 threads, tile 128 state rows x BN output columns.  Thread 0 of warp 0 issues TMA loads
+// (128-byte swizzle, K-major), thread 0 of warp 1 issues tcgen05.mma (A and B from shared memory,
+// D in tensor memory), stages handed over by mbarriers; all four warps read the accumulators
+// back with tcgen05.ld for the epilogue.  Every wait is bounded; a wait that gives up records
+// FQ_BIT_TIMEOUT, drains this CTA's own copies and MMAs, frees tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int BM = 128;      // state rows per tile (tcgen05 M)
+constexpr int BKE = 64;      // K elements per stage: one 128-byte swizzle row
+constexpr int NTHREADS = 128;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// ------------------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false if the phase did not complete within kWaitCycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major rows of 128 B, 128-byte swizzle, 8-row atoms of 1024 B.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading-dimension offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride between 8-row atoms
+  d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// ------------------------------------------------------------------------- slices
+template <int NS>
+__device__ __forceinline__ void split_f32(float x, __nv_bfloat16 (&s)[NS]) {
+  float r = x;
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    s[q] = __float2bfloat16_rn(r);
+    r -= __bfloat162float(s[q]);
+  }
+}
+
+template <int NS>
+__device__ __forceinline__ void split_f64(double x, __nv_bfloat16 (&s)[NS]) {
+  double r = x;
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    s[q] = __double2bfloat16(r);
+    r -= (double)__bfloat162float(s[q]);
+  }
+}
+
+// Products kept for NS slices: (a, b) with a + b < NS, ordered smallest first.
+template <int NS> struct Pairs;
+template <> struct Pairs<2> {
+  static constexpr int N = 3;
+  static __device__ __forceinline__ int a(int p) { return p == 0 ? 1 : 0; }  // (1,0), (0,1), (0,0)
+  static __device__ __forceinline__ int b(int p) { return p == 1 ? 1 : 0; }
+};
+template <> struct Pairs<3> {
+  static constexpr int N = 6;
+  static __device__ __forceinline__ int a(int p) { const int t[6] = {1, 0, 2, 1, 0, 0}; return t[p]; }
+  static __device__ __forceinline__ int b(int p) { const int t[6] = {1, 2, 0, 0, 1, 0}; return t[p]; }
+};
+
+struct SplitMaps {
+  CUtensorMap a[3];   // left operand slices [nc][Kp]
+  CUtensorMap br[3];  // [S | -A] slices   [Np][Kp]
+  CUtensorMap bi[3];  // [A | S] slices    [Np][Kp]
+};
+
+struct SplitEpi {
+  int n, nc, ldm, np;          // dims; ldm: FP32 master row stride; np: real part width in K'
+  const float* cur_re;         // psi_l masters (first term: psi_0)
+  const float* cur_im;
+  const float* prev_re;        // psi_{l-1}
+  const float* prev_im;
+  float* acc_re;
+  float* acc_im;
+  float* out_re;               // psi_{l+1} (in place of psi_{l-1}) or X at the last term
+  float* out_im;
+  __nv_bfloat16* slice_out;    // next left operand: NS slices, each [nc][Kp]
+  size_t slice_stride;         // elements between slices
+  int kp;
+  fq_term t;
+};
+
+template <int NS, int BN, int STAGES>
+struct SplitCfg {
+  static constexpr int A_BYTES = BM * 128;            // one slice, one stage
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int STAGE_BYTES = NS * A_BYTES + 2 * NS * B_BYTES;
+  static constexpr int TMEM_COLS = 2 * BN <= 32 ? 32 : (2 * BN <= 64 ? 64 : (2 * BN <= 128 ? 128 : 256));
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+template <int NS, int BN, int STAGES>
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_split_term(const __grid_constant__ SplitMaps maps, int nk, SplitEpi e) {
+  using Cfg = SplitCfg<NS, BN, STAGES>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned stage buffers (128-byte swizzle atoms), then barriers
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * Cfg::STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j0 = blockIdx.y * BM, i0 = blockIdx.x * BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)Cfg::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    bool ok = true;
+    for (int kb = 0; kb < nk && ok; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES) {
+        ok = mbar_wait(empty0 + 8 * s, ((kb / STAGES) - 1) & 1);
+        if (!ok) break;
+      }
+      const uint32_t st = base + s * Cfg::STAGE_BYTES;
+      mbar_expect_tx(full0 + 8 * s, Cfg::STAGE_BYTES);
+      const int kx = kb * BKE;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) tma_load_2d(st + q * Cfg::A_BYTES, &maps.a[q], full0 + 8 * s, kx, j0);
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        tma_load_2d(st + NS * Cfg::A_BYTES + q * Cfg::B_BYTES, &maps.br[q], full0 + 8 * s, kx, i0);
+        tma_load_2d(st + NS * Cfg::A_BYTES + (NS + q) * Cfg::B_BYTES, &maps.bi[q], full0 + 8 * s, kx, i0);
+      }
+      issued = kb + 1;
+    }
+    if (!ok) {
+      atomicExch(abort_flag, 1);
+      atomicOr(e.t.status, FQ_BIT_TIMEOUT);
+    }
+    // drain: every copy this thread issued must have landed before the CTA may exit
+    for (int kb = std::max(0, issued - STAGES); kb < issued; ++kb) mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                               ((uint32_t)(BM >> 4) << 24);
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      ok = mbar_wait(full0 + 8 * s, (kb / STAGES) & 1);
+      if (!ok || *(volatile int*)abort_flag) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t st = base + s * Cfg::STAGE_BYTES;
+#pragma unroll
+      for (int p = 0; p < Pairs<NS>::N; ++p) {
+        const uint32_t a_addr = st + Pairs<NS>::a(p) * Cfg::A_BYTES;
+        const uint32_t br_addr = st + NS * Cfg::A_BYTES + Pairs<NS>::b(p) * Cfg::B_BYTES;
+        const uint32_t bi_addr = st + NS * Cfg::A_BYTES + (NS + Pairs<NS>::b(p)) * Cfg::B_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BKE / 16; ++kk) {
+          const uint32_t acc = (kb > 0 || p > 0 || kk > 0) ? 1u : 0u;
+          const uint64_t ad = smem_desc(a_addr + 32 * kk);
+          mma_bf16(tmem, ad, smem_desc(br_addr + 32 * kk), idesc, acc);
+          mma_bf16(tmem + BN, ad, smem_desc(bi_addr + 32 * kk), idesc, acc);
+        }
+      }
+      mma_commit(empty0 + 8 * s);  // stage s free once these MMAs have read it
+    }
+    if (!ok) {
+      atomicExch(abort_flag, 1);
+      atomicOr(e.t.status, FQ_BIT_TIMEOUT);
+    }
+    mma_commit(done);  // arrives when every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: all 128 threads, thread = state row j
+  const bool got = mbar_wait(done, 0);
+  tc_fence_after();
+  if (!got) atomicOr(e.t.status, FQ_BIT_TIMEOUT);
+  const bool run = got && !*(volatile int*)abort_flag;
+  const int j = j0 + warp * 32 + lane;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  bool bad = false;
+#pragma unroll 1
+  for (int c0 = 0; c0 < BN; c0 += 16) {
+    float yr[16], yi[16];
+    tmem_ld16(trow + c0, yr);
+    tmem_ld16(trow + BN + c0, yi);
+    tmem_wait_ld();
+    if (!run || j >= e.nc) continue;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int i = i0 + c0 + q;
+      if (i >= e.n) break;
+      const size_t idx = (size_t)j * e.ldm + i;
+      float nr, ni, sr, si;
+      if (e.t.first) {
+        nr = yi[q];
+        ni = -yr[q];
+        sr = (float)e.t.coef0 * e.cur_re[idx] + (float)e.t.coef * nr;
+        si = (float)e.t.coef0 * e.cur_im[idx] + (float)e.t.coef * ni;
+      } else {
+        nr = 2.f * yi[q] + e.prev_re[idx];
+        ni = -2.f * yr[q] + e.prev_im[idx];
+        sr = e.acc_re[idx] + (float)e.t.coef * nr;
+        si = e.acc_im[idx] + (float)e.t.coef * ni;
+      }
+      bad |= !(nr * nr + ni * ni <= (float)e.t.bound2);
+      float o_r = nr, o_i = ni;
+      if (e.t.last) {
+        o_r = (float)e.t.ph_re * sr - (float)e.t.ph_im * si;
+        o_i = (float)e.t.ph_re * si + (float)e.t.ph_im * sr;
+      } else {
+        e.acc_re[idx] = sr;
+        e.acc_im[idx] = si;
+      }
+      e.out_re[idx] = o_r;
+      e.out_im[idx] = o_i;
+      __nv_bfloat16 sre[NS], sim[NS];
+      split_f32<NS>(o_r, sre);
+      split_f32<NS>(o_i, sim);
+      const size_t srow = (size_t)j * e.kp;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        e.slice_out[s * e.slice_stride + srow + i] = sre[s];
+        e.slice_out[s * e.slice_stride + srow + e.np + i] = sim[s];
+      }
+    }
+  }
+  if (bad) atomicOr(e.t.status, FQ_BIT_BOUND);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)Cfg::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// Right operands of step m: Br = [S | -A], Bi = [A | S] as NS BF16 slices [Np][Kp] each, from
+// Omega~_m = S + i A computed in FP64 (stage a2): S = sa H0 + sb H1 - sbeta 1, A = sc [H0,H1].
+template <int NS>
+__global__ void k_split_omega(const double* __restrict__ h0, const double* __restrict__ h1,
+                              const double* __restrict__ k, int n, int np, int kp, double sa, double sb, double sc,
+                              double sbeta, __nv_bfloat16* br, __nv_bfloat16* bi, size_t slice_stride) {
+  const size_t total = (size_t)np * kp;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q / kp), c = (int)(q % kp);
+    const bool im_half = c >= np;
+    const int kk = im_half ? c - np : c;
+    double S = 0.0, A = 0.0;
+    if (i < n && kk < n) {
+      const size_t o = (size_t)i * n + kk;
+      S = sa * h0[o] + sb * h1[o] - (i == kk ? sbeta : 0.0);
+      A = sc * k[o];
+    }
+    __nv_bfloat16 s1[NS], s2[NS];
+    split_f64<NS>(im_half ? -A : S, s1);  // [S | -A]
+    split_f64<NS>(im_half ? S : A, s2);   // [A | S]
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      br[s * slice_stride + q] = s1[s];
+      bi[s * slice_stride + q] = s2[s];
+    }
+  }
+}
+
+// Left operand and FP32 masters of the initial block: identity rows (build_UT) or given states.
+template <int NS>
+__global__ void k_split_init(const double2* __restrict__ x0, int n, int nc, int ldm, int np, int kp, float* mre,
+                             float* mim, __nv_bfloat16* sl, size_t slice_stride) {
+  const size_t total = (size_t)nc * kp;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(q / kp), c = (int)(q % kp);
+    const bool im_half = c >= np;
+    const int i = im_half ? c - np : c;
+    float v = 0.f;
+    if (i < n) {
+      double2 z = x0 ? x0[(size_t)j * n + i] : make_double2(i == j ? 1.0 : 0.0, 0.0);
+      v = (float)(im_half ? z.y : z.x);
+      if (im_half) mim[(size_t)j * ldm + i] = v;
+      else mre[(size_t)j * ldm + i] = v;
+    }
+    __nv_bfloat16 s[NS];
+    split_f32<NS>(v, s);
+#pragma unroll
+    for (int t = 0; t < NS; ++t) sl[t * slice_stride + q] = s[t];
+  }
+}
+
+// ------------------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+fq_status encode_fn() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  });
+  if (!g_encode) {
+    fq_set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return FQ_ECUDA;
+  }
+  return FQ_OK;
+}
+
+// 2-D BF16 map over [rows][cols] (row-major, cols contiguous), box = 64 cols x box_rows rows.
+fq_status make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows) {
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BKE, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    fq_set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return FQ_ECUDA;
+  }
+  return FQ_OK;
+}
+
+int grid_1d(size_t total) { return (int)std::min<size_t>(std::max<size_t>((total + 255) / 256, 1), 152 * 32); }
+
+template <int NS>
+constexpr int stages_for() { return NS == 2 ? 3 : 2; }
+constexpr int BN_SPLIT = 64;
+
+}  // namespace
+
+// ------------------------------------------------------------------------- orchestration
+// Workspace: B slices (Br, Bi), two left-operand slice buffers (ping-pong across terms), three
+// FP32 master state buffers (planar) for psi_l / psi_{l-1} / acc.
+struct SplitWs {
+  __nv_bfloat16* br;
+  __nv_bfloat16* bi;
+  __nv_bfloat16* a[2];
+  float* m[3][2];
+  int np, kp, ldm, ncp;
+  size_t bstride, astride;
+};
+
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t fq_split_workspace(const fq_plan* p, int nc, void* base, void* out) {
+  const int NS = p->precision == FQ_BF16X6 ? 3 : 2;
+  SplitWs w{};
+  w.np = (p->n + 63) & ~63;
+  w.kp = 2 * w.np;
+  w.ldm = (p->n + 3) & ~3;
+  w.bstride = (size_t)w.np * w.kp;
+  w.ncp = (nc + BM - 1) / BM * BM;  // left-operand rows padded to whole 128-row boxes (zeros)
+  w.astride = (size_t)w.ncp * w.kp;
+  char* b = (char*)base;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* q = b ? b + off : nullptr;
+    off += up256(bytes);
+    return q;
+  };
+  w.br = (__nv_bfloat16*)take(2 * NS * w.bstride);
+  w.bi = (__nv_bfloat16*)take(2 * NS * w.bstride);
+  w.a[0] = (__nv_bfloat16*)take(2 * NS * w.astride);
+  w.a[1] = (__nv_bfloat16*)take(2 * NS * w.astride);
+  for (int q = 0; q < 3; ++q)
+    for (int r = 0; r < 2; ++r) w.m[q][r] = (float*)take(sizeof(float) * (size_t)nc * w.ldm);
+  if (out) *(SplitWs*)out = w;
+  return off;
+}
+
+template <int NS>
+static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
+                           int transpose_out, void* ws, cudaStream_t s) {
+  constexpr int BN = BN_SPLIT, STAGES = stages_for<NS>();
+  using Cfg = SplitCfg<NS, BN, STAGES>;
+  fq_status st = encode_fn();
+  if (st != FQ_OK) return st;
+  SplitWs w;
+  fq_split_workspace(p, nc, ws, &w);
+  const int n = p->n, L = p->L;
+  SplitMaps maps[2];  // left operand in a[0] or a[1]
+  for (int v = 0; v < 2; ++v)
+    for (int q = 0; q < NS; ++q) {
+      if ((st = make_map(&maps[v].a[q], w.a[v] + q * w.astride, w.ncp, w.kp, BM)) != FQ_OK) return st;
+      if ((st = make_map(&maps[v].br[q], w.br + q * w.bstride, w.np, w.kp, BN)) != FQ_OK) return st;
+      if ((st = make_map(&maps[v].bi[q], w.bi + q * w.bstride, w.np, w.kp, BN)) != FQ_OK) return st;
+    }
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_split_term<NS, BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg::SMEM);
+    if (e != cudaSuccess) return fq_cuda_fail(e, "split kernel smem attribute");
+    attr = true;
+  }
+  // left-operand slices are only ever written for rows < nc and columns < n: zero the padding
+  cudaMemsetAsync(w.a[0], 0, sizeof(__nv_bfloat16) * NS * w.astride, s);
+  cudaMemsetAsync(w.a[1], 0, sizeof(__nv_bfloat16) * NS * w.astride, s);
+  k_split_init<NS><<<grid_1d((size_t)nc * w.kp), 256, 0, s>>>(identity ? nullptr : (const double2*)x0, n, nc, w.ldm,
+                                                               w.np, w.kp, w.m[0][0], w.m[0][1], w.a[0], w.astride);
+  const dim3 grid(w.np / BN, (nc + BM - 1) / BM);
+  const int nk = w.kp / BKE;
+  int xb = 0, av = 0;  // FP32 master holding psi_0 / X, left-operand buffer holding its slices
+  fq_term t{};
+  t.coef0 = p->cheb[0];
+  t.ph_re = p->phase_re;
+  t.ph_im = p->phase_im;
+  t.bound2 = 1.0 + 2e-3;
+  t.status = p->d_status;
+  for (int m = m_begin; m < m_end; ++m) {
+    k_split_omega<NS><<<grid_1d(w.bstride), 256, 0, s>>>(p->d_h0, p->d_h1, p->d_k, n, w.np, w.kp, p->sa[m], p->sb[m],
+                                                         p->sc[m], p->sbeta, w.br, w.bi, w.bstride);
+    int cur = xb, nxt = (xb + 1) % 3, acc = (xb + 2) % 3, prv = -1;
+    for (int l = 0; l < L; ++l) {
+      t.first = l == 0;
+      t.last = l == L - 1;
+      t.coef = p->cheb[l + 1];
+      const int out = l == 0 ? nxt : prv;
+      SplitEpi e{};
+      e.n = n;
+      e.nc = nc;
+      e.ldm = w.ldm;
+      e.np = w.np;
+      e.kp = w.kp;
+      e.cur_re = w.m[cur][0];
+      e.cur_im = w.m[cur][1];
+      e.prev_re = prv >= 0 ? w.m[prv][0] : w.m[cur][0];
+      e.prev_im = prv >= 0 ? w.m[prv][1] : w.m[cur][1];
+      e.acc_re = w.m[acc][0];
+      e.acc_im = w.m[acc][1];
+      e.out_re = w.m[out][0];
+      e.out_im = w.m[out][1];
+      e.slice_out = w.a[av ^ 1];
+      e.slice_stride = w.astride;
+      e.t = t;
+      k_split_term<NS, BN, STAGES><<<grid, NTHREADS, Cfg::SMEM, s>>>(maps[av], nk, e);
+      av ^= 1;
+      if (t.last) {
+        xb = out;
+      } else {
+        prv = cur;
+        cur = out;
+      }
+    }
+  }
+  fq_blk<float> bx{w.m[xb][0], w.m[xb][1]};
+  if (transpose_out) fq_launch_store_transpose_f32(bx, x, n, w.ldm, s);
+  else fq_launch_store_states_f32(bx, x, nc, n, w.ldm, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fq_cuda_fail(e, "split-precision kernels");
+  return FQ_OK;
+}
+
+fq_status fq_split_propagate(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
+                             int transpose_out, void* ws, cudaStream_t s) {
+  if (p->precision == FQ_BF16X6) return run_split<3>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s);
+  return run_split<2>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s);
+}

@@ -101,7 +101,14 @@ void fq_launch_term_tri_f32(const float* d, const float* er, const float* ei, in
 // resident tridiagonal chain (tri_resident.cu)
 int fq_resident_supported(int n, int L);
 size_t fq_resident_coeff_bytes(int n, int steps);
-fq_status fq_launch_resident(const fq_plan* p, const float* d2, const float* e2, const double* x0,
-                             double* x, int transpose_out, int nc, int m_begin, int m_end, cudaStream_t s);
+// per-step (2 d, 2 e') of the gauge-real operator and the frame rotations, into `coeff`
+void fq_launch_gauge_coeffs(const fq_plan* p, int m_begin, int nsteps, void* coeff, cudaStream_t s);
+fq_status fq_launch_resident(const fq_plan* p, const void* coeff, const double* x0, double* x, int transpose_out,
+                             int nc, int m_begin, int m_end, cudaStream_t s);
+
+// split-precision dense path (dense_split.cu)
+size_t fq_split_workspace(const fq_plan* p, int nc, void* base, void* out);
+fq_status fq_split_propagate(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
+                             int transpose_out, void* ws, cudaStream_t s);
 
 void fq_launch_defect(const double* u, int n, const int32_t* cols, int k, double* partial, cudaStream_t s);

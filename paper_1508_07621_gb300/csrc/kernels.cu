@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include "internal.h"
+#include "dense_core.cuh"
 
 namespace {
 
@@ -135,55 +136,20 @@ __global__ void k_omega_dense_f64(const double* __restrict__ h0, const double* _
   }
 }
 
-// One Chebyshev term, dense FP64: Y^T[j][i] = sum_k Psi[j][k] (S[i][k] + i A[i][k]) followed by
-// the fused epilogue.  BJ x BI output tile per CTA, (BJ/TJ) x (BI/TI) threads, TJ x TI
-// complex outputs per thread, K staged through shared memory in BK slices.
-template <int BJ, int BI, int BK, int TJ, int TI>
+// One Chebyshev term, dense FP64: Y^T[j][i] = sum_k Psi[j][k] (S[i][k] + i A[i][k]) (tile loop in
+// dense_core.cuh) followed by the fused recurrence / Bessel accumulation / step-close epilogue.
+// A == nullptr selects the real-operator variant (piecewise drives: c_m = 0).
+template <int BJ, int BI, int BK, int TJ, int TI, bool HAS_A>
 __global__ void __launch_bounds__((BJ / TJ) * (BI / TI))
 k_term_dense_f64(const double* __restrict__ S, const double* __restrict__ A, int n,
                  const double* __restrict__ cur_re, const double* __restrict__ cur_im,
                  const double* prev_re, const double* prev_im, double* acc_re, double* acc_im,
                  double* out_re, double* out_im, int nc, fq_term t) {
-  constexpr int NTX = BI / TI, NTY = BJ / TJ, NT = NTX * NTY;
-  __shared__ double sPr[BK][BJ + 1], sPi[BK][BJ + 1], sS[BK][BI + 1], sA[BK][BI + 1];
+  constexpr int NTX = BI / TI;
   const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
   const int j0 = blockIdx.y * BJ, i0 = blockIdx.x * BI;
   double yr[TJ][TI], yi[TJ][TI];
-#pragma unroll
-  for (int a = 0; a < TJ; ++a)
-#pragma unroll
-    for (int b = 0; b < TI; ++b) yr[a][b] = yi[a][b] = 0.0;
-  for (int k0 = 0; k0 < n; k0 += BK) {
-    for (int q = threadIdx.x; q < BJ * BK; q += NT) {
-      int r = q / BK, kk = q % BK, j = j0 + r, k = k0 + kk;
-      bool ok = j < nc && k < n;
-      sPr[kk][r] = ok ? cur_re[(size_t)j * n + k] : 0.0;
-      sPi[kk][r] = ok ? cur_im[(size_t)j * n + k] : 0.0;
-    }
-    for (int q = threadIdx.x; q < BI * BK; q += NT) {
-      int r = q / BK, kk = q % BK, i = i0 + r, k = k0 + kk;
-      bool ok = i < n && k < n;
-      sS[kk][r] = ok ? S[(size_t)i * n + k] : 0.0;
-      sA[kk][r] = ok ? A[(size_t)i * n + k] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < BK; ++kk) {
-      double pr[TJ], pi[TJ], s[TI], a[TI];
-#pragma unroll
-      for (int q = 0; q < TJ; ++q) { pr[q] = sPr[kk][ty * TJ + q]; pi[q] = sPi[kk][ty * TJ + q]; }
-#pragma unroll
-      for (int q = 0; q < TI; ++q) { s[q] = sS[kk][tx * TI + q]; a[q] = sA[kk][tx * TI + q]; }
-#pragma unroll
-      for (int u = 0; u < TJ; ++u)
-#pragma unroll
-        for (int v = 0; v < TI; ++v) {
-          yr[u][v] = fma(pr[u], s[v], fma(-pi[u], a[v], yr[u][v]));
-          yi[u][v] = fma(pi[u], s[v], fma(pr[u], a[v], yi[u][v]));
-        }
-    }
-    __syncthreads();
-  }
+  dense_tile_f64<BJ, BI, BK, TJ, TI, HAS_A>(S, A, n, cur_re, cur_im, nc, j0, i0, yr, yi);
 #pragma unroll
   for (int u = 0; u < TJ; ++u)
 #pragma unroll
@@ -220,7 +186,29 @@ __global__ void k_tri_coeffs(const double* __restrict__ h0d, const double* __res
 
 // Streaming tridiagonal term: every element reads psi_l with its two neighbours, psi_{l-1} and
 // acc, and writes psi_{l+1} (in place of psi_{l-1}) and acc.  4 consecutive elements per
-// thread; rows are padded to ld (multiple of 4) with zeros.
+// thread; rows are padded to ld (multiple of 4) with zeros.  All loads of a thread are issued
+// before any arithmetic (16-byte vector loads), so each thread pays one memory round trip.
+template <typename T> struct Quad;
+template <> struct Quad<float> {
+  static __device__ __forceinline__ void load(const float* p, float (&v)[4]) {
+    float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+  static __device__ __forceinline__ void store(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct Quad<double> {
+  static __device__ __forceinline__ void load(const double* p, double (&v)[4]) {
+    double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+  static __device__ __forceinline__ void store(double* p, const double (&v)[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_term_tri(const T* __restrict__ d, const T* __restrict__ er, const T* __restrict__ ei, int ld,
@@ -230,32 +218,63 @@ k_term_tri(const T* __restrict__ d, const T* __restrict__ er, const T* __restric
   const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (i0 >= ld) return;
   const size_t row = (size_t)j * ld;
-  T cr[6], ci[6], dd[4], lr[5], li[5];
-  cr[0] = i0 > 0 ? cur_re[row + i0 - 1] : (T)0;
-  ci[0] = i0 > 0 ? cur_im[row + i0 - 1] : (T)0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    cr[q + 1] = cur_re[row + i0 + q];
-    ci[q + 1] = cur_im[row + i0 + q];
-    dd[q] = d[i0 + q];
-    lr[q + 1] = er[i0 + q];
-    li[q + 1] = ei[i0 + q];
+  T cr[4], ci[4], dd[4], lr[4], li[4], pr[4], pi[4], ar[4], ai[4];
+  Quad<T>::load(cur_re + row + i0, cr);
+  Quad<T>::load(cur_im + row + i0, ci);
+  Quad<T>::load(d + i0, dd);
+  Quad<T>::load(er + i0, lr);
+  Quad<T>::load(ei + i0, li);
+  const T cl_r = i0 > 0 ? cur_re[row + i0 - 1] : (T)0, cl_i = i0 > 0 ? cur_im[row + i0 - 1] : (T)0;
+  const T cx_r = i0 + 4 < ld ? cur_re[row + i0 + 4] : (T)0, cx_i = i0 + 4 < ld ? cur_im[row + i0 + 4] : (T)0;
+  const T el_r = i0 > 0 ? er[i0 - 1] : (T)0, el_i = i0 > 0 ? ei[i0 - 1] : (T)0;
+  if (!t.first) {
+    Quad<T>::load(prev_re + row + i0, pr);
+    Quad<T>::load(prev_im + row + i0, pi);
+    Quad<T>::load(acc_re + row + i0, ar);
+    Quad<T>::load(acc_im + row + i0, ai);
   }
-  cr[5] = i0 + 4 < ld ? cur_re[row + i0 + 4] : (T)0;
-  ci[5] = i0 + 4 < ld ? cur_im[row + i0 + 4] : (T)0;
-  lr[0] = i0 > 0 ? er[i0 - 1] : (T)0;
-  li[0] = i0 > 0 ? ei[i0 - 1] : (T)0;
+  T o_r[4], o_i[4], a_r[4], a_i[4];
+  bool bad = false;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
+    const T xlr = q == 0 ? cl_r : cr[q - 1], xli = q == 0 ? cl_i : ci[q - 1];
+    const T xrr = q == 3 ? cx_r : cr[q + 1], xri = q == 3 ? cx_i : ci[q + 1];
+    const T elr = q == 0 ? el_r : lr[q - 1], eli = q == 0 ? el_i : li[q - 1];
     // y = d_i x_i + e_{i-1} x_{i-1} + conj(e_i) x_{i+1}
-    T yr = dd[q] * cr[q + 1];
-    T yi = dd[q] * ci[q + 1];
-    yr = fma(lr[q], cr[q], fma(-li[q], ci[q], yr));
-    yi = fma(lr[q], ci[q], fma(li[q], cr[q], yi));
-    yr = fma(lr[q + 1], cr[q + 2], fma(li[q + 1], ci[q + 2], yr));
-    yi = fma(lr[q + 1], ci[q + 2], fma(-li[q + 1], cr[q + 2], yi));
-    term_epilogue<T>(yr, yi, cr[q + 1], ci[q + 1], prev_re, prev_im, acc_re, acc_im, out_re, out_im,
-                     row + i0 + q, t);
+    T yr = dd[q] * cr[q], yi = dd[q] * ci[q];
+    yr = fma(elr, xlr, fma(-eli, xli, yr));
+    yi = fma(elr, xli, fma(eli, xlr, yi));
+    yr = fma(lr[q], xrr, fma(li[q], xri, yr));
+    yi = fma(lr[q], xri, fma(-li[q], xrr, yi));
+    T nr, ni, sr, si;
+    if (t.first) {
+      nr = yi;
+      ni = -yr;
+      sr = (T)t.coef0 * cr[q] + (T)t.coef * nr;
+      si = (T)t.coef0 * ci[q] + (T)t.coef * ni;
+    } else {
+      nr = (T)2 * yi + pr[q];
+      ni = (T)-2 * yr + pi[q];
+      sr = ar[q] + (T)t.coef * nr;
+      si = ai[q] + (T)t.coef * ni;
+    }
+    bad |= !((double)nr * nr + (double)ni * ni <= t.bound2);
+    if (t.last) {
+      o_r[q] = (T)t.ph_re * sr - (T)t.ph_im * si;
+      o_i[q] = (T)t.ph_re * si + (T)t.ph_im * sr;
+    } else {
+      o_r[q] = nr;
+      o_i[q] = ni;
+      a_r[q] = sr;
+      a_i[q] = si;
+    }
+  }
+  if (bad) atomicOr(t.status, FQ_BIT_BOUND);
+  Quad<T>::store(out_re + row + i0, o_r);
+  Quad<T>::store(out_im + row + i0, o_i);
+  if (!t.last) {
+    Quad<T>::store(acc_re + row + i0, a_r);
+    Quad<T>::store(acc_im + row + i0, a_i);
   }
 }
 
@@ -377,12 +396,20 @@ void fq_launch_term_dense_f64(const double* S, const double* A, int n, fq_blk<do
   const long big = (long)((n + 31) / 32) * ((nc + 31) / 32);
   if (big >= 2 * 152) {
     dim3 g((n + 31) / 32, (nc + 31) / 32);
-    k_term_dense_f64<32, 32, 16, 2, 2><<<g, 256, 0, s>>>(S, A, n, cur.re, cur.im, prev.re, prev.im, acc.re, acc.im,
-                                                          out.re, out.im, nc, t);
+    if (A)
+      k_term_dense_f64<32, 32, 16, 2, 2, true><<<g, 256, 0, s>>>(S, A, n, cur.re, cur.im, prev.re, prev.im, acc.re,
+                                                                 acc.im, out.re, out.im, nc, t);
+    else
+      k_term_dense_f64<32, 32, 16, 2, 2, false><<<g, 256, 0, s>>>(S, A, n, cur.re, cur.im, prev.re, prev.im, acc.re,
+                                                                  acc.im, out.re, out.im, nc, t);
   } else {
     dim3 g((n + 7) / 8, (nc + 7) / 8);
-    k_term_dense_f64<8, 8, 32, 1, 1><<<g, 64, 0, s>>>(S, A, n, cur.re, cur.im, prev.re, prev.im, acc.re, acc.im,
-                                                       out.re, out.im, nc, t);
+    if (A)
+      k_term_dense_f64<8, 8, 32, 1, 1, true><<<g, 64, 0, s>>>(S, A, n, cur.re, cur.im, prev.re, prev.im, acc.re,
+                                                              acc.im, out.re, out.im, nc, t);
+    else
+      k_term_dense_f64<8, 8, 32, 1, 1, false><<<g, 64, 0, s>>>(S, A, n, cur.re, cur.im, prev.re, prev.im, acc.re,
+                                                               acc.im, out.re, out.im, nc, t);
   }
 }
 
@@ -403,17 +430,25 @@ void fq_launch_term_tri_f64(const double* d, const double* er, const double* ei,
                             fq_blk<double> prev, fq_blk<double> acc, fq_blk<double> out, int nc, int ld,
                             const fq_term& t, cudaStream_t s) {
   (void)n;
-  dim3 g((ld / 4 + 255) / 256, nc);
-  k_term_tri<double><<<g, 256, 0, s>>>(d, er, ei, ld, cur.re, cur.im, prev.re, prev.im, acc.re, acc.im, out.re,
-                                       out.im, t);
+  for (int r0 = 0; r0 < nc; r0 += 65535) {  // gridDim.y limit
+    const int rows = nc - r0 < 65535 ? nc - r0 : 65535;
+    const size_t o = (size_t)r0 * ld;
+    dim3 g((ld / 4 + 255) / 256, rows);
+    k_term_tri<double><<<g, 256, 0, s>>>(d, er, ei, ld, cur.re + o, cur.im + o, prev.re + o, prev.im + o, acc.re + o,
+                                         acc.im + o, out.re + o, out.im + o, t);
+  }
 }
 void fq_launch_term_tri_f32(const float* d, const float* er, const float* ei, int n, fq_blk<float> cur,
                             fq_blk<float> prev, fq_blk<float> acc, fq_blk<float> out, int nc, int ld,
                             const fq_term& t, cudaStream_t s) {
   (void)n;
-  dim3 g((ld / 4 + 255) / 256, nc);
-  k_term_tri<float><<<g, 256, 0, s>>>(d, er, ei, ld, cur.re, cur.im, prev.re, prev.im, acc.re, acc.im, out.re,
-                                      out.im, t);
+  for (int r0 = 0; r0 < nc; r0 += 65535) {  // gridDim.y limit
+    const int rows = nc - r0 < 65535 ? nc - r0 : 65535;
+    const size_t o = (size_t)r0 * ld;
+    dim3 g((ld / 4 + 255) / 256, rows);
+    k_term_tri<float><<<g, 256, 0, s>>>(d, er, ei, ld, cur.re + o, cur.im + o, prev.re + o, prev.im + o, acc.re + o,
+                                        acc.im + o, out.re + o, out.im + o, t);
+  }
 }
 
 void fq_launch_defect(const double* u, int n, const int32_t* cols, int k, double* partial, cudaStream_t s) {

@@ -1,7 +1,8 @@
 // floquet_build_UT_static: U_T through the resident FP32 tridiagonal kernel without any device
 // allocation.  For callers that cannot call cudaMalloc - code that runs where another runtime
 // owns all device memory, or that must not grow its footprint after start-up.  All scratch
-// (operators, per-step scalars, the 2 Omega~ coefficient arrays and the status word) lives in
+// (operators, per-step scalars, the per-step operator coefficients and frame rotations, and the
+// status word) lives in
 // one file-scope __device__ array of FLOQUET_STATIC_SCRATCH_BYTES; the caller passes the problem
 // (host arrays) and the output.  The kernels are the library's existing ones.
 #include <cuda_runtime.h>
@@ -65,7 +66,6 @@ extern "C" fq_status floquet_build_UT_static(const fq_problem* prob, void* d_U, 
     fq_set_error("floquet_build_UT_static: resident kernel needs N <= 10240 and L <= 128 (N = %d, L = %d)", n, p.L);
     return FQ_EUNSUPPORTED;
   }
-  const size_t ld = (size_t)((n + 3) & ~3);
   const size_t nm1 = (size_t)(n > 1 ? n - 1 : 1);
   const size_t off_status = 0;
   const size_t off_scal = off_status + 256;
@@ -74,9 +74,9 @@ extern "C" fq_status floquet_build_UT_static(const fq_problem* prob, void* d_U, 
   const size_t off_h0o = off_h1 + up256((size_t)n * sizeof(double));
   const size_t off_k = off_h0o + up256(nm1 * sizeof(double));
   const size_t off_coef = off_k + up256(nm1 * sizeof(double));
-  const size_t need = off_coef + up256(3 * ld * (size_t)M * sizeof(float));
+  const size_t need = off_coef + up256(fq_resident_coeff_bytes(n, M));
   if (need > (size_t)FLOQUET_STATIC_SCRATCH_BYTES) {
-    fq_set_error("floquet_build_UT_static: needs %zu bytes of scratch (3*M*ceil4(N)*4 + small), limit %zu; "
+    fq_set_error("floquet_build_UT_static: needs %zu bytes of scratch ((2M+1)*ceil4(N)*8 + small), limit %zu; "
                  "use floquet_build_UT with a caller workspace",
                  need, (size_t)FLOQUET_STATIC_SCRATCH_BYTES);
     return FQ_EINVAL;
@@ -92,8 +92,7 @@ extern "C" fq_status floquet_build_UT_static(const fq_problem* prob, void* d_U, 
   p.d_h1 = (double*)(b + off_h1);
   p.d_h0o = (double*)(b + off_h0o);
   p.d_k = (double*)(b + off_k);
-  float* d2 = (float*)(b + off_coef);
-  float* e2 = d2 + ld * (size_t)M;
+  void* coef = b + off_coef;
 
   // host-side operands for the upload: per-step Omega~ scalars and the commutator diagonal
   std::vector<double> scal(3 * (size_t)M);
@@ -114,8 +113,8 @@ extern "C" fq_status floquet_build_UT_static(const fq_problem* prob, void* d_U, 
   if (e == cudaSuccess && n > 1) e = cudaMemcpyAsync(p.d_k, kl.data(), (n - 1) * sizeof(double), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return fq_cuda_fail(e, "floquet_build_UT_static upload");
 
-  fq_launch_tri_coeffs_f32(&p, 0, M, 2.0, d2, e2, e2 + ld * (size_t)M, s);
-  st = fq_launch_resident(&p, d2, e2, nullptr, (double*)d_U, 1, n, 0, M, s);
+  fq_launch_gauge_coeffs(&p, 0, M, coef, s);
+  st = fq_launch_resident(&p, coef, nullptr, (double*)d_U, 1, n, 0, M, s);
   if (st != FQ_OK) return st;
   // the host vectors above are staged by the copies; wait for the chain and read the check
   unsigned int bits = 0;
