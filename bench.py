@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ncu-case", choices=["resident", "stream"], default=None,
+    ap.add_argument("--ncu-case", choices=["resident", "stream", "split"], default=None,
                     help="run one small capture case of a kernel twice and exit (for ncu --set full)")
     return ap.parse_args()
 
@@ -45,10 +45,23 @@ def parse():
 def run_ncu_case(case):
     """Small cases for detailed ncu captures (a few GB at most, inputs larger than L2):
     resident: 152 states (one wave on 152 SMs) over steps 0..19 of the benchmark chain;
-    stream:   2048 states through step 0 (39 streaming FP32 term launches, 0.5 GB of states)."""
+    stream:   2048 states through step 0 (39 streaming FP32 term launches, 0.5 GB of states);
+    split:    dense GOE N = 4096 (seeds 3, 4), BF16X3 tensor-core terms of step 0 on the identity."""
     import torch
     import floquet_inputs as fi
     import paper_1508_07621_gb300 as fq
+    if case == "split":
+        m = fi.config_goe4096()
+        plan = fq.Plan.dense(m.h0, m.h1, omega=m.drive.omega, f_ac=m.drive.f_ac, steps=m.steps,
+                             precision=fq.FQ_BF16X3)
+        x0 = torch.zeros((4096, 4096), dtype=torch.complex128, device="cuda")
+        x0.diagonal().fill_(1.0)
+        ws = fq.workspace(plan.workspace_size(4096))
+        for _ in range(2):
+            fq.floquet_propagate(plan.handle, x0, x0, 4096, 0, 1, ws)
+        torch.cuda.synchronize()
+        print(f"ncu case split: status {plan.check_status()}")
+        return
     d = fi.config_dimer(nb=NB, steps=STEPS)
     n = d.n
     kernel = fq.FQ_KERNEL_RESIDENT if case == "resident" else fq.FQ_KERNEL_STREAM

@@ -101,6 +101,8 @@ typedef struct fq_problem {
   int32_t precision;        /* fq_precision */
   int32_t checkpoint_stride;/* floquet_grad: X_m stored every s steps; <= 0 selects 16 */
   int32_t kernel;           /* fq_kernel: which tridiagonal kernel family runs the chain */
+  int32_t tile_n;           /* split path: tensor-core output tile width 64 or 128; 0 = 64 until
+                               floquet_autotune picks one */
 } fq_problem;
 
 typedef struct fq_plan fq_plan;
@@ -182,6 +184,26 @@ fq_status floquet_grad(fq_plan* plan, const double* d_f, const void* d_W, double
  *  - Every call shares the array and overwrites what the previous call left there; calls
  *    that overlap on the GPU (other streams, other host threads) race and must not be made. */
 fq_status floquet_build_UT_static(const fq_problem* problem, void* d_U, void* stream);
+
+/* Batched scan (many independent problems, one launch).  Captures floquet_build_UT of every
+ * plan into one CUDA graph: plan i writes d_U[i] (its N_i x N_i complex128 output) using its
+ * slice of d_ws, and the instances run concurrently on `lanes` (1..32) graph branches, assigned
+ * longest-first by their cost N^3 M L.  floquet_batch_launch then replays the whole scan as a
+ * single graph launch on `stream`.  The plans, outputs and workspace must outlive the batch;
+ * the graph is bound to those pointers.  Capture enqueues nothing.
+ * d_ws: floquet_batch_workspace_size(plans, count) bytes, 256-byte aligned. */
+typedef struct fq_batch fq_batch;
+size_t floquet_batch_workspace_size(fq_plan* const* plans, int32_t count);
+fq_status floquet_batch_create(fq_batch** batch, fq_plan* const* plans, int32_t count, void* const* d_U,
+                               void* d_ws, size_t ws_bytes, int32_t lanes);
+fq_status floquet_batch_launch(fq_batch* batch, void* stream);
+void floquet_batch_destroy(fq_batch* batch);
+
+/* Autotuner for the split-precision dense path: times each tile width of the tensor-core term
+ * kernel on two steps of this plan (states: the identity block) and keeps the fastest for the
+ * plan's later calls.  d_ws as for floquet_build_UT.  Synchronises `stream`; no-op (FQ_OK) for
+ * other paths.  *tile_n receives the chosen width (NULL allowed). */
+fq_status floquet_autotune(fq_plan* plan, void* d_ws, size_t ws_bytes, void* stream, int32_t* tile_n);
 
 /* Synchronises `stream`; returns FQ_EBOUND (and clears the word) if a device check of this
  * plan fired since the last call, FQ_OK otherwise. */

@@ -29,6 +29,8 @@ Readings where the paper is silent or garbled (each is also listed in the design
   R7  quasienergies eps = theta/T with theta = -arg(lambda) in [-pi, pi).
   R11 piecewise-constant drives: the H1 coefficient range is widened by 10% of its span
       (or of max |f|) and frozen, so the bounds do not follow f.
+  R12 6th order (Eq. 14 in full): alphas as 3-point Gauss-Legendre moments (see magnus6_omega);
+      the literal midpoint-derivative alphas of Eq. 15 give only 4th order.
 """
 from __future__ import annotations
 
@@ -66,6 +68,70 @@ def magnus4_coefficients(period: float, steps: int, f, df, d2f):
     b = h * f(tau) + h ** 3 * d2f(tau) / 24.0
     c = h ** 3 * df(tau) / 12.0
     return h, a, b, c
+
+
+GL3_NODES = (0.5 - math.sqrt(15.0) / 10.0, 0.5, 0.5 + math.sqrt(15.0) / 10.0)
+
+
+def magnus6_from_alphas(a1, a2, a3):
+    """Eq. 14 in full for Y' = A Y: C1 = [alpha1, alpha2], C2 = -(1/60)[alpha1, 2 alpha3 + C1],
+    Omega_A = alpha1 + alpha3/12 + (1/240)[-20 alpha1 - alpha3 + C1, alpha2 + C2];
+    returned as the Hermitian Omega_H = i Omega_A (U = exp(-i Omega_H))."""
+    comm = lambda x, y: x @ y - y @ x
+    c1 = comm(a1, a2)
+    c2 = -comm(a1, 2.0 * a3 + c1) / 60.0
+    return 1j * (a1 + a3 / 12.0 + comm(-20.0 * a1 - a3 + c1, a2 + c2) / 240.0)
+
+
+def magnus6_omega_taylor(h0, h1, h, f, df, d2f):
+    """Eq. 14 with the alphas of Eq. 15 taken literally as midpoint derivatives,
+    alpha_j = h^j/(j-1)! A^(j-1)(t_1/2), A = -i(H0 + f H1).  Only 4th order for a general drive:
+    alpha1 + alpha3/12 = h A + h^3 A^(2)/24 misses the h^5 A^(4)/1920 term of the integral of A."""
+    a1 = -1j * h * (h0 + f * h1)
+    a2 = -1j * h ** 2 * df * h1
+    a3 = -1j * h ** 3 / 2.0 * d2f * h1
+    return magnus6_from_alphas(a1, a2, a3)
+
+
+def magnus6_omega(h0, h1, h, f1, f2, f3):
+    """Reading R12: Eq. 14 with its alphas as the Gauss-Legendre moments of A = -i(H0 + f H1) at
+    the nodes t + c_i h (c = 1/2 -+ sqrt(15)/10, 1/2), f_i = f(t + c_i h):
+        alpha1 = h A_2, alpha2 = (sqrt(15) h / 3)(A_3 - A_1), alpha3 = (10 h / 3)(A_3 - 2 A_2 + A_1),
+    which equal Eq. 15's derivative forms to leading order in h and make alpha1 + alpha3/12 the
+    3-point Gauss quadrature of the integral of A, so the scheme is genuinely 6th order."""
+    A1, A2, A3 = (-1j * (h0 + f * h1) for f in (f1, f2, f3))
+    a1 = h * A2
+    a2 = math.sqrt(15.0) * h / 3.0 * (A3 - A1)
+    a3 = 10.0 * h / 3.0 * (A3 - 2.0 * A2 + A1)
+    return magnus6_from_alphas(a1, a2, a3)
+
+
+def plan_dense6(h0, h1, drive, steps, tol=1e-14):
+    """Plan for the 6th-order scheme: per-step Omega_m/h kept explicitly; bounds are the extreme
+    eigenvalues over all steps (exact LAPACK) plus the relative margin of 1e-12."""
+    T = 2.0 * math.pi / drive.omega
+    h = T / steps
+    omegas = []
+    lo, hi = np.inf, -np.inf
+    for m in range(steps):
+        fs = [float(cos_drive(drive.f_dc, drive.f_ac, drive.omega, drive.phi0, (m + c) * h)[0])
+              for c in GL3_NODES]
+        om = magnus6_omega(h0, h1, h, *fs)
+        om = 0.5 * (om + om.conj().T)
+        w = np.linalg.eigvalsh(om / h)
+        lo, hi = min(lo, w[0]), max(hi, w[-1])
+        omegas.append(om)
+    plan = finish_plan(T, h, np.full(steps, h), np.zeros(steps), np.zeros(steps), lo, hi, 0.0, tol)
+    return plan, omegas
+
+
+def build_ut_dense6(plan, omegas):
+    n = omegas[0].shape[0]
+    x = np.eye(n, dtype=np.complex128)
+    for om in omegas:
+        omt = (om / plan.h - plan.beta * np.eye(n)) / plan.delta_e
+        x = chebyshev_step(lambda v: omt @ v, x, plan.coeffs, plan.phase)
+    return x
 
 
 def piecewise_coefficients(period: float, fm):

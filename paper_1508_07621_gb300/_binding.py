@@ -31,7 +31,7 @@ class fq_problem(ctypes.Structure):
                 ("f_dc", ctypes.c_double), ("f_ac", ctypes.c_double), ("omega", ctypes.c_double),
                 ("phi0", ctypes.c_double), ("f_steps", _dp), ("cheb_tol", ctypes.c_double),
                 ("e_min", ctypes.c_double), ("e_max", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("checkpoint_stride", ctypes.c_int32), ("kernel", ctypes.c_int32)]
+                ("checkpoint_stride", ctypes.c_int32), ("kernel", ctypes.c_int32), ("tile_n", ctypes.c_int32)]
 
 
 class fq_plan_info(ctypes.Structure):
@@ -61,6 +61,12 @@ _SIGS = {
     "floquet_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "floquet_check_status": (ctypes.c_int, [_vp, _vp]),
     "floquet_build_UT_static": (ctypes.c_int, [ctypes.POINTER(fq_problem), _vp, _vp]),
+    "floquet_batch_workspace_size": (_sz, [ctypes.POINTER(_vp), _i32]),
+    "floquet_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp),
+                                            _vp, _sz, _i32]),
+    "floquet_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "floquet_batch_destroy": (None, [_vp]),
+    "floquet_autotune": (ctypes.c_int, [_vp, _vp, _sz, _vp, ctypes.POINTER(_i32)]),
     "floquet_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -103,14 +109,14 @@ def _darr(a):
 
 def make_problem(n, fmt, h0, h1, period, steps, h0_off=None, drive_kind=FQ_DRIVE_COS, f_dc=0.0, f_ac=0.0,
                  omega=1.0, phi0=0.0, f_steps=None, cheb_tol=0.0, e_min=0.0, e_max=0.0,
-                 precision=FQ_FP64, checkpoint_stride=0, kernel=FQ_KERNEL_AUTO):
+                 precision=FQ_FP64, checkpoint_stride=0, kernel=FQ_KERNEL_AUTO, tile_n=0):
     """Builds an fq_problem; returns (struct, keepalive) - the host arrays must outlive the call."""
     a0, p0 = _darr(h0)
     a1, p1 = _darr(h1)
     ao, po = _darr(h0_off)
     af, pf = _darr(f_steps)
     prob = fq_problem(n, fmt, p0, po, p1, period, steps, drive_kind, f_dc, f_ac, omega, phi0, pf, cheb_tol,
-                      e_min, e_max, precision, checkpoint_stride, kernel)
+                      e_min, e_max, precision, checkpoint_stride, kernel, tile_n)
     return prob, (a0, a1, ao, af)
 
 
@@ -179,6 +185,36 @@ def floquet_grad(plan: int, f, W, loss, grad, ws, stream=None) -> None:
 def floquet_build_UT_static(problem, U, stream=None) -> None:
     """No-allocation U_T (resident FP32 tridiagonal chain, static device scratch); see floquet.h."""
     _check(lib.floquet_build_UT_static(ctypes.byref(problem), _ptr(U), _stream(stream)), "floquet_build_UT_static")
+
+
+def floquet_batch_workspace_size(plans) -> int:
+    arr = (_vp * len(plans))(*plans)
+    return int(lib.floquet_batch_workspace_size(arr, len(plans)))
+
+
+def floquet_batch_create(plans, outputs, ws, lanes: int = 8) -> int:
+    """One CUDA graph for the U_T builds of all plans; outputs[i]: N_i x N_i complex128 tensors."""
+    arr = (_vp * len(plans))(*plans)
+    outs = (_vp * len(outputs))(*[o.data_ptr() for o in outputs])
+    b = _vp()
+    _check(lib.floquet_batch_create(ctypes.byref(b), arr, len(plans), outs, _ptr(ws), ws.numel() * ws.element_size(),
+                                    lanes), "floquet_batch_create")
+    return b.value
+
+
+def floquet_batch_launch(batch: int, stream=None) -> None:
+    _check(lib.floquet_batch_launch(_vp(batch), _stream(stream)), "floquet_batch_launch")
+
+
+def floquet_batch_destroy(batch: int) -> None:
+    lib.floquet_batch_destroy(_vp(batch))
+
+
+def floquet_autotune(plan: int, ws, stream=None) -> int:
+    tile = _i32()
+    _check(lib.floquet_autotune(_vp(plan), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream),
+                                ctypes.byref(tile)), "floquet_autotune")
+    return tile.value
 
 
 def floquet_check_status(plan: int, stream=None) -> int:

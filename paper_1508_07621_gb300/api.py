@@ -25,11 +25,12 @@ class Plan:
     # ---------------------------------------------------------------- constructors
     @classmethod
     def dense(cls, h0, h1, *, omega, f_ac, steps, f_dc=0.0, phi0=0.0, period=None, precision=B.FQ_FP64,
-              cheb_tol=0.0, e_min=0.0, e_max=0.0):
+              cheb_tol=0.0, e_min=0.0, e_max=0.0, tile_n=0):
         n = h0.shape[0]
         T = period if period is not None else 2.0 * math.pi / omega
         prob, keep = B.make_problem(n, B.FQ_DENSE, h0, h1, T, steps, f_dc=f_dc, f_ac=f_ac, omega=omega,
-                                    phi0=phi0, precision=precision, cheb_tol=cheb_tol, e_min=e_min, e_max=e_max)
+                                    phi0=phi0, precision=precision, cheb_tol=cheb_tol, e_min=e_min, e_max=e_max,
+                                    tile_n=tile_n)
         return cls(prob, keep)
 
     @classmethod
@@ -83,6 +84,11 @@ class Plan:
             ws = workspace(B.floquet_grad_workspace_size(self.handle))
         B.floquet_grad(self.handle, f, W, loss, g, ws, stream)
         return loss, g
+
+    def autotune(self, ws=None, stream=None) -> int:
+        if ws is None:
+            ws = workspace(self.workspace_size())
+        return B.floquet_autotune(self.handle, ws, stream)
 
     def check_status(self, stream=None) -> int:
         return B.floquet_check_status(self.handle, stream)

@@ -428,9 +428,11 @@ fq_status make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_
 
 int grid_1d(size_t total) { return (int)std::min<size_t>(std::max<size_t>((total + 255) / 256, 1), 152 * 32); }
 
-template <int NS>
-constexpr int stages_for() { return NS == 2 ? 3 : 2; }
-constexpr int BN_SPLIT = 64;
+// Pipeline depth that fits 192 KB of stage buffers.
+template <int NS, int BN>
+constexpr int stages_for() {
+  return (196608 / (NS * BM * 128 + 2 * NS * BN * 128)) > 4 ? 4 : (196608 / (NS * BM * 128 + 2 * NS * BN * 128));
+}
 
 }  // namespace
 
@@ -451,7 +453,7 @@ static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t fq_split_workspace(const fq_plan* p, int nc, void* base, void* out) {
   const int NS = p->precision == FQ_BF16X6 ? 3 : 2;
   SplitWs w{};
-  w.np = (p->n + 63) & ~63;
+  w.np = (p->n + 127) & ~127;  // whole output tiles for both tile widths
   w.kp = 2 * w.np;
   w.ldm = (p->n + 3) & ~3;
   w.bstride = (size_t)w.np * w.kp;
@@ -474,10 +476,10 @@ size_t fq_split_workspace(const fq_plan* p, int nc, void* base, void* out) {
   return off;
 }
 
-template <int NS>
+template <int NS, int BN>
 static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
                            int transpose_out, void* ws, cudaStream_t s) {
-  constexpr int BN = BN_SPLIT, STAGES = stages_for<NS>();
+  constexpr int STAGES = stages_for<NS, BN>();
   using Cfg = SplitCfg<NS, BN, STAGES>;
   fq_status st = encode_fn();
   if (st != FQ_OK) return st;
@@ -549,8 +551,13 @@ static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int 
     }
   }
   fq_blk<float> bx{w.m[xb][0], w.m[xb][1]};
-  if (transpose_out) fq_launch_store_transpose_f32(bx, x, n, w.ldm, s);
-  else fq_launch_store_states_f32(bx, x, nc, n, w.ldm, s);
+  if (x == nullptr) {
+    // autotuning runs time the chain only
+  } else if (transpose_out) {
+    fq_launch_store_transpose_f32(bx, x, n, w.ldm, s);
+  } else {
+    fq_launch_store_states_f32(bx, x, nc, n, w.ldm, s);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fq_cuda_fail(e, "split-precision kernels");
   return FQ_OK;
@@ -558,6 +565,59 @@ static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int 
 
 fq_status fq_split_propagate(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
                              int transpose_out, void* ws, cudaStream_t s) {
-  if (p->precision == FQ_BF16X6) return run_split<3>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s);
-  return run_split<2>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s);
+  const bool wide = p->tile_n == 128;
+  if (p->precision == FQ_BF16X6)
+    return wide ? run_split<3, 128>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s)
+                : run_split<3, 64>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s);
+  return wide ? run_split<2, 128>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s)
+              : run_split<2, 64>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s);
+}
+
+// Times each tile width on two steps of the identity block and keeps the fastest.
+extern "C" fq_status floquet_autotune(fq_plan* p, void* ws, size_t bytes, void* stream, int32_t* tile_n) {
+  if (!p) {
+    fq_set_error("floquet_autotune: NULL plan");
+    return FQ_EINVAL;
+  }
+  if (p->path != PATH_DENSE_SPLIT) {
+    if (tile_n) *tile_n = 0;
+    return FQ_OK;
+  }
+  if (!ws || bytes < floquet_workspace_size(p, p->n) || ((uintptr_t)ws & 255)) {
+    fq_set_error("floquet_autotune: workspace must be floquet_workspace_size(plan, N) bytes, 256-byte aligned");
+    return FQ_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int steps = p->steps < 2 ? p->steps : 2;
+  const int cand[2] = {64, 128};
+  float best = 1e30f;
+  int pick = 64;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  for (int c : cand) {
+    p->tile_n = c;
+    fq_status st = fq_split_propagate(p, nullptr, nullptr, p->n, 0, steps, 1, 0, ws, s);  // warm-up
+    if (st != FQ_OK) break;
+    cudaEventRecord(a, s);
+    fq_split_propagate(p, nullptr, nullptr, p->n, 0, steps, 1, 0, ws, s);
+    cudaEventRecord(b, s);
+    cudaError_t e = cudaEventSynchronize(b);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      return fq_cuda_fail(e, "autotune");
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  p->tile_n = pick;
+  if (tile_n) *tile_n = pick;
+  return FQ_OK;
 }

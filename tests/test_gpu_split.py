@@ -39,10 +39,11 @@ def cuda_c128(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).cuda()
 
 
-@pytest.mark.parametrize("prec,ns", [(2, 2), (3, 3)])
-def test_split_goe64_build(fq, prec, ns):
+@pytest.mark.parametrize("prec,ns,tile", [(2, 2, 64), (3, 3, 64), (2, 2, 128), (3, 3, 128)])
+def test_split_goe64_build(fq, prec, ns, tile):
     m = fi.config_goe64()
-    plan = fq.Plan.dense(m.h0, m.h1, omega=m.drive.omega, f_ac=m.drive.f_ac, steps=m.steps, precision=prec)
+    plan = fq.Plan.dense(m.h0, m.h1, omega=m.drive.omega, f_ac=m.drive.f_ac, steps=m.steps, precision=prec,
+                         tile_n=tile)
     U = plan.build_UT().cpu().numpy()
     assert plan.check_status() == fq.FQ_OK
     ref = o.build_ut_dense(m.h0, m.h1, o.plan_for_drive_dense(m.h0, m.h1, m.drive, m.steps))
@@ -52,8 +53,8 @@ def test_split_goe64_build(fq, prec, ns):
     assert err <= tol
 
 
-@pytest.mark.parametrize("prec,ns", [(2, 2), (3, 3)])
-def test_split_ragged_propagate(fq, prec, ns):
+@pytest.mark.parametrize("prec,ns,tile", [(2, 2, 64), (3, 3, 64), (2, 2, 128), (3, 3, 128)])
+def test_split_ragged_propagate(fq, prec, ns, tile):
     """N = 200 (K' padded to 512, output tiles ragged), 37 states (one partial 128-row tile),
     steps 2..9 of 24, non-even drive."""
     n, M = 200, 24
@@ -62,7 +63,7 @@ def test_split_ragged_propagate(fq, prec, ns):
     x0 = fi.ginibre(n, 1303)[:37]
     x0 /= np.linalg.norm(x0, axis=1, keepdims=True)
     plan = fq.Plan.dense(h0, h1, omega=drv.omega, f_ac=drv.f_ac, f_dc=drv.f_dc, phi0=drv.phi0, steps=M,
-                         precision=prec)
+                         precision=prec, tile_n=tile)
     X = plan.propagate(cuda_c128(x0), 2, 10).cpu().numpy()
     ref = o.propagate_dense(h0, h1, o.plan_for_drive_dense(h0, h1, drv, M), x0.T, 2, 10).T
     err = np.max(np.abs(X - ref))

@@ -170,6 +170,43 @@ def test_order_test_catches_commutator_sign():
     assert e[1] / e[2] < 6.0
 
 
+def test_sixth_order_convergence_against_rk4():
+    """The full Eq. 14 (6th order, nine commutators) converges as h^6: error ratio ~2^6 per
+    doubling of M against the independent RK4 solution (non-even drive)."""
+    h0, h1 = fi.goe(4, 11), fi.goe(4, 12)
+    drv = fi.Drive(0.3, 1.2, 1.3, 0.7)
+    ref = rk4_propagator(h0, h1, drv, drv.period, 1 << 14)
+    errs = []
+    for M in (8, 16, 32):
+        plan, oms = o.plan_dense6(h0, h1, drv, M)
+        errs.append(np.max(np.abs(o.build_ut_dense6(plan, oms) - ref)))
+    for r in (errs[0] / errs[1], errs[1] / errs[2]):
+        assert 50.0 < r < 80.0, errs
+
+
+def test_sixth_order_literal_derivative_alphas_are_fourth_order():
+    """Reading R12 is needed: Eq. 14 with Eq. 15's alphas taken literally as midpoint derivatives
+    converges only as h^4 (ratio ~16), because alpha1 + alpha3/12 misses the h^5 term of the
+    integral of A; and for a constant drive both forms reduce to h (H0 + f H1) exactly."""
+    h0, h1 = fi.goe(4, 11), fi.goe(4, 12)
+    drv = fi.Drive(0.3, 1.2, 1.3, 0.7)
+    ref = rk4_propagator(h0, h1, drv, drv.period, 1 << 14)
+    errs = []
+    for M in (16, 32):
+        h = drv.period / M
+        u = np.eye(4, dtype=complex)
+        for m in range(M):
+            f, df, d2f = (float(v) for v in o.cos_drive(drv.f_dc, drv.f_ac, drv.omega, drv.phi0, (m + 0.5) * h))
+            om = o.magnus6_omega_taylor(h0, h1, h, f, df, d2f)
+            u = expm_herm(0.5 * (om + om.conj().T), 1.0) @ u
+        errs.append(np.max(np.abs(u - ref)))
+    assert 12.0 < errs[0] / errs[1] < 20.0, errs
+    h0, h1 = fi.goe(5, 21), fi.goe(5, 22)
+    h, f = 0.1, 0.7
+    assert np.max(np.abs(o.magnus6_omega(h0, h1, h, f, f, f) - h * (h0 + f * h1))) < 1e-14
+    assert np.max(np.abs(o.magnus6_omega_taylor(h0, h1, h, f, 0.0, 0.0) - h * (h0 + f * h1))) < 1e-14
+
+
 def test_bounds_contain_every_step_spectrum():
     """Reading R4: [E_min, E_max] contains the spectrum of Omega_m/h at every step."""
     h0, h1 = fi.goe(16, 401), fi.goe(16, 402)
