@@ -101,7 +101,7 @@ typedef struct fq_problem {
   int32_t precision;        /* fq_precision */
   int32_t checkpoint_stride;/* floquet_grad: X_m stored every s steps; <= 0 selects 16 */
   int32_t kernel;           /* fq_kernel: which tridiagonal kernel family runs the chain */
-  int32_t tile_n;           /* split path: tensor-core output tile width 64 or 128; 0 = 64 until
+  int32_t tile_n;           /* split path: tensor-core output tile width 64 or 128; 0 = 128 until
                                floquet_autotune picks one */
 } fq_problem;
 

@@ -34,7 +34,7 @@ struct fq_plan {
   std::vector<double> sa, sb, sc;      // Omega~_m = sa H0 + sb H1 + sc i[H0,H1] - sbeta 1
   double sbeta = 0;
   int path = PATH_DENSE_F64;
-  int tile_n = 64;           // split path: output tile width of the tensor-core kernel (autotuned)
+  int tile_n = 128;          // split path: output tile width of the tensor-core kernel (autotuned)
   int device = 0;
   // device copies (owned by the plan)
   double* d_h0 = nullptr;    // DENSE: n*n      TRIDIAG: diag n

@@ -265,7 +265,7 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan) {
     fq_set_error("tile_n must be 0, 64 or 128 (got %d)", p->tile_n);
     return FQ_EINVAL;
   }
-  plan->tile_n = p->tile_n ? p->tile_n : 64;
+  plan->tile_n = p->tile_n ? p->tile_n : 128;
   plan->period = p->period;
   plan->tol = p->cheb_tol > 0 ? p->cheb_tol : 1e-14;
   const double h = p->period / M;
