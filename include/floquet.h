@@ -103,6 +103,9 @@ typedef struct fq_problem {
   int32_t kernel;           /* fq_kernel: which tridiagonal kernel family runs the chain */
   int32_t tile_n;           /* split path: tensor-core output tile width 64 or 128; 0 = 128 until
                                floquet_autotune picks one */
+  int32_t magnus_order;     /* 4 (default, also 0) or 6: Eq. 14 in full with its alphas taken as
+                               3-point Gauss-Legendre moments (nine commutators of H0, H1 computed
+                               once on the device); 6 needs FQ_DENSE and FQ_DRIVE_COS */
 } fq_problem;
 
 typedef struct fq_plan fq_plan;
@@ -163,6 +166,16 @@ fq_status floquet_unitarity_defect(const void* d_U, int32_t n, const int32_t* d_
 size_t floquet_grad_workspace_size(const fq_plan* plan);
 fq_status floquet_grad(fq_plan* plan, const double* d_f, const void* d_W, double* d_loss,
                        double* d_grad, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Second propagation round (§3, last paragraph): propagates the ncols states d_X0 (ncols x N
+ * complex128, row r = state r, e.g. Floquet states from the eigenvectors of U_T) over the period
+ * and writes d_avg[r] = <A>_T = (1/T) int_0^T <psi_r(t)|A(t)|psi_r(t)> dt (Eq. 17) for
+ * A(t) = a0 H0 + (a1 + s_drive f(t)) H1 (A = H(t): a0 = 1, a1 = 0, s_drive = 1), the integral by
+ * composite Simpson over the step boundaries (trapezoid if M is odd).  Cosine-drive plans; dense
+ * N <= 8192.  d_X0 is not modified.  d_ws: floquet_observable_workspace_size(plan, ncols). */
+size_t floquet_observable_workspace_size(const fq_plan* plan, int32_t ncols);
+fq_status floquet_average_observable(fq_plan* plan, const void* d_X0, int32_t ncols, double a0, double a1,
+                                     double s_drive, double* d_avg, void* d_ws, size_t ws_bytes, void* stream);
 
 /* Size of the library's static device scratch array used by floquet_build_UT_static. */
 #define FLOQUET_STATIC_SCRATCH_BYTES (16u << 20)

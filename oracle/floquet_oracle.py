@@ -364,6 +364,52 @@ def quasienergies(u: np.ndarray, period: float) -> np.ndarray:
     return np.sort(theta / period)
 
 
+def simpson_weights(steps: int, h: float) -> np.ndarray:
+    """Quadrature weights over the step boundaries t_m = m h, m = 0..M: composite Simpson for
+    even M, trapezoid for odd M."""
+    w = np.full(steps + 1, h)
+    if steps % 2 == 0:
+        w[1:-1:2] = 4.0 * h / 3.0
+        w[2:-1:2] = 2.0 * h / 3.0
+        w[0] = w[-1] = h / 3.0
+    else:
+        w[0] = w[-1] = h / 2.0
+    return w
+
+
+def average_observable(propagate_step, expect, x0, drive, steps):
+    """Eq. 17: <A>_T = (1/T) int_0^T <psi(t)|A(t)|psi(t)> dt for each column state of x0,
+    evaluated at the step boundaries of the chain (second propagation round of §3).
+    `propagate_step(m, x)` applies step m, `expect(t, x)` returns <x_c|A(t)|x_c> per column."""
+    T = 2.0 * math.pi / drive.omega
+    h = T / steps
+    w = simpson_weights(steps, h)
+    x = np.array(x0, dtype=np.complex128)
+    acc = w[0] * expect(0.0, x)
+    for m in range(steps):
+        x = propagate_step(m, x)
+        acc = acc + w[m + 1] * expect((m + 1) * h, x)
+    return acc / T
+
+
+def expect_dense(h0, h1, a0, a1, s_drive, drive):
+    """<x|A(t)|x> per column with A(t) = a0 H0 + (a1 + s_drive f(t)) H1 (dense)."""
+    def ev(t, x):
+        f = float(cos_drive(drive.f_dc, drive.f_ac, drive.omega, drive.phi0, t)[0])
+        a = a0 * h0 + (a1 + s_drive * f) * h1
+        return np.real(np.einsum("ic,ic->c", np.conj(x), a @ x))
+    return ev
+
+
+def expect_tridiag(h0_diag, h0_off, h1_diag, a0, a1, s_drive, drive):
+    def ev(t, x):
+        f = float(cos_drive(drive.f_dc, drive.f_ac, drive.omega, drive.phi0, t)[0])
+        d = a0 * h0_diag + (a1 + s_drive * f) * h1_diag
+        y = apply_tridiag(d, (a0 * h0_off).astype(np.complex128), x)
+        return np.real(np.einsum("ic,ic->c", np.conj(x), y))
+    return ev
+
+
 def unitarity_defect(u: np.ndarray) -> tuple[float, float]:
     """max |U^+ U - 1| and ||U^+ U - 1||_F / sqrt(n) (unitarity of Eq. 9, §2)."""
     d = u.conj().T @ u - np.eye(u.shape[0])

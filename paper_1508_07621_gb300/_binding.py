@@ -31,7 +31,8 @@ class fq_problem(ctypes.Structure):
                 ("f_dc", ctypes.c_double), ("f_ac", ctypes.c_double), ("omega", ctypes.c_double),
                 ("phi0", ctypes.c_double), ("f_steps", _dp), ("cheb_tol", ctypes.c_double),
                 ("e_min", ctypes.c_double), ("e_max", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("checkpoint_stride", ctypes.c_int32), ("kernel", ctypes.c_int32), ("tile_n", ctypes.c_int32)]
+                ("checkpoint_stride", ctypes.c_int32), ("kernel", ctypes.c_int32), ("tile_n", ctypes.c_int32),
+                ("magnus_order", ctypes.c_int32)]
 
 
 class fq_plan_info(ctypes.Structure):
@@ -67,6 +68,9 @@ _SIGS = {
     "floquet_batch_launch": (ctypes.c_int, [_vp, _vp]),
     "floquet_batch_destroy": (None, [_vp]),
     "floquet_autotune": (ctypes.c_int, [_vp, _vp, _sz, _vp, ctypes.POINTER(_i32)]),
+    "floquet_observable_workspace_size": (_sz, [_vp, _i32]),
+    "floquet_average_observable": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_double, _vp, _vp, _sz, _vp]),
     "floquet_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -109,14 +113,14 @@ def _darr(a):
 
 def make_problem(n, fmt, h0, h1, period, steps, h0_off=None, drive_kind=FQ_DRIVE_COS, f_dc=0.0, f_ac=0.0,
                  omega=1.0, phi0=0.0, f_steps=None, cheb_tol=0.0, e_min=0.0, e_max=0.0,
-                 precision=FQ_FP64, checkpoint_stride=0, kernel=FQ_KERNEL_AUTO, tile_n=0):
+                 precision=FQ_FP64, checkpoint_stride=0, kernel=FQ_KERNEL_AUTO, tile_n=0, magnus_order=0):
     """Builds an fq_problem; returns (struct, keepalive) - the host arrays must outlive the call."""
     a0, p0 = _darr(h0)
     a1, p1 = _darr(h1)
     ao, po = _darr(h0_off)
     af, pf = _darr(f_steps)
     prob = fq_problem(n, fmt, p0, po, p1, period, steps, drive_kind, f_dc, f_ac, omega, phi0, pf, cheb_tol,
-                      e_min, e_max, precision, checkpoint_stride, kernel, tile_n)
+                      e_min, e_max, precision, checkpoint_stride, kernel, tile_n, magnus_order)
     return prob, (a0, a1, ao, af)
 
 
@@ -215,6 +219,17 @@ def floquet_autotune(plan: int, ws, stream=None) -> int:
     _check(lib.floquet_autotune(_vp(plan), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream),
                                 ctypes.byref(tile)), "floquet_autotune")
     return tile.value
+
+
+def floquet_observable_workspace_size(plan: int, ncols: int) -> int:
+    return int(lib.floquet_observable_workspace_size(_vp(plan), ncols))
+
+
+def floquet_average_observable(plan: int, X0, ncols: int, a0: float, a1: float, s_drive: float, out, ws,
+                               stream=None) -> None:
+    _check(lib.floquet_average_observable(_vp(plan), _ptr(X0), ncols, a0, a1, s_drive, _ptr(out), _ptr(ws),
+                                          ws.numel() * ws.element_size(), _stream(stream)),
+           "floquet_average_observable")
 
 
 def floquet_check_status(plan: int, stream=None) -> int:

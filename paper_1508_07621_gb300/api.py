@@ -25,12 +25,12 @@ class Plan:
     # ---------------------------------------------------------------- constructors
     @classmethod
     def dense(cls, h0, h1, *, omega, f_ac, steps, f_dc=0.0, phi0=0.0, period=None, precision=B.FQ_FP64,
-              cheb_tol=0.0, e_min=0.0, e_max=0.0, tile_n=0):
+              cheb_tol=0.0, e_min=0.0, e_max=0.0, tile_n=0, magnus_order=0):
         n = h0.shape[0]
         T = period if period is not None else 2.0 * math.pi / omega
         prob, keep = B.make_problem(n, B.FQ_DENSE, h0, h1, T, steps, f_dc=f_dc, f_ac=f_ac, omega=omega,
                                     phi0=phi0, precision=precision, cheb_tol=cheb_tol, e_min=e_min, e_max=e_max,
-                                    tile_n=tile_n)
+                                    tile_n=tile_n, magnus_order=magnus_order)
         return cls(prob, keep)
 
     @classmethod
@@ -85,6 +85,15 @@ class Plan:
         B.floquet_grad(self.handle, f, W, loss, g, ws, stream)
         return loss, g
 
+    def average_observable(self, states, a0=1.0, a1=0.0, s_drive=1.0, stream=None):
+        """<A>_T of every row of `states` (complex128, ncols x N) for A(t) = a0 H0 + (a1 + s f(t)) H1."""
+        import torch
+        ncols = states.shape[0]
+        out = torch.empty(ncols, dtype=torch.float64, device="cuda")
+        ws = workspace(B.floquet_observable_workspace_size(self.handle, ncols))
+        B.floquet_average_observable(self.handle, states, ncols, a0, a1, s_drive, out, ws, stream)
+        return out
+
     def autotune(self, ws=None, stream=None) -> int:
         if ws is None:
             ws = workspace(self.workspace_size())
@@ -112,3 +121,17 @@ def unitarity_defect(U, cols=None, stream=None):
     k = n if cols is None else cols.numel()
     ws = workspace(2 * 8 * ((k + 15) // 16) * ((n + 255) // 256) + 256)
     return B.floquet_unitarity_defect(U, n, cols, k, ws, stream)
+
+
+def floquet_states(U, period):
+    """Quasienergies eps (Eq. 5, eps = theta/T, theta = -arg(lambda) in [-pi, pi)) and Floquet
+    states (rows, unit norm) from U_T, by host FP64 LAPACK (zgeev) - outside the timed path."""
+    import numpy as np
+    import torch
+    u = U.detach().cpu().numpy()
+    lam, v = np.linalg.eig(u)
+    theta = -np.angle(lam)
+    theta = np.where(theta >= math.pi, theta - 2.0 * math.pi, theta)
+    order = np.argsort(theta)
+    v = v[:, order] / np.linalg.norm(v[:, order], axis=0, keepdims=True)
+    return theta[order] / period, torch.from_numpy(np.ascontiguousarray(v.T)).to(U.device)

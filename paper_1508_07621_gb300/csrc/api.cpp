@@ -92,8 +92,14 @@ int run_chain(fq_plan* p, StateWs& w, int x, int nc, int m_begin, int m_end, cud
     cei = cer + (size_t)nsteps * ld;
   }
   for (int m = m_begin; m < m_end; ++m) {
-    if (p->path == PATH_DENSE_F64)
+    if (p->path == PATH_DENSE_F64 && p->order == 6) {
+      double c[FQ_M6_TERMS];
+      const double inv = 1.0 / (p->h * p->delta_e);
+      for (int q = 0; q < FQ_M6_TERMS; ++q) c[q] = p->coef6[(size_t)m * FQ_M6_TERMS + q] * inv;
+      fq_launch_omega6_f64(p, c, w.S, w.A, s);
+    } else if (p->path == PATH_DENSE_F64) {
       fq_launch_omega_dense_f64(p->d_h0, p->d_h1, p->d_k, n, p->sa[m], p->sb[m], p->sc[m], p->sbeta, w.S, w.A, s);
+    }
     // buffers: cur = psi_l, prv = psi_{l-1}, acc; x holds psi_0
     int cur = x, nxt = (x + 1) % 3, acc = (x + 2) % 3;
     int prv = -1;
@@ -208,6 +214,7 @@ void free_plan(fq_plan* p) {
   cudaFree(p->d_h0o);
   cudaFree(p->d_scal);
   cudaFree(p->d_status);
+  cudaFree(p->d_cm);
   delete p;
 }
 
@@ -262,6 +269,39 @@ fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
     fq_launch_gemm_f64(p->d_h0, p->d_h1, p->d_k, n, 1.0, 0.0, 0);
     fq_launch_gemm_f64(p->d_h1, p->d_h0, p->d_k, n, -1.0, 1.0, 0);
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "commutator");
+    if (p->order == 6) {
+      // nested commutators K0 = [H0,K], K1 = [H1,K], K00 = [H0,K0], K01 = [H0,K1], K10 = [H1,K0],
+      // K11 = [H1,K1], KK0 = [K,K0], KK1 = [K,K1], computed once (§3)
+      const size_t nn = (size_t)n * n;
+      if ((e = cudaMalloc(&p->d_cm, 8 * nn * sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc commutators");
+      const double* K = p->d_k;
+      double* C = p->d_cm;
+      const double* lhs[8] = {p->d_h0, p->d_h1, p->d_h0, p->d_h0, p->d_h1, p->d_h1, K, K};
+      const double* rhs[8] = {K, K, C + 0 * nn, C + 1 * nn, C + 0 * nn, C + 1 * nn, C + 0 * nn, C + 1 * nn};
+      for (int q = 0; q < 8; ++q) {
+        fq_launch_gemm_f64(lhs[q], rhs[q], C + q * nn, n, 1.0, 0.0, 0);
+        fq_launch_gemm_f64(rhs[q], lhs[q], C + q * nn, n, -1.0, 1.0, 0);
+      }
+      // Weyl widening of the leading bounds by every commutator term, ||M||_2 <= ||M||_F
+      if (!(prob->e_max > prob->e_min)) {
+        double* d_nrm = nullptr;
+        if ((e = cudaMalloc(&d_nrm, 9 * sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc norms");
+        cudaMemset(d_nrm, 0, 9 * sizeof(double));
+        fq_launch_frobenius(K, nn, d_nrm, 0);
+        for (int q = 0; q < 8; ++q) fq_launch_frobenius(C + q * nn, nn, d_nrm + 1 + q, 0);
+        double nrm[9];
+        e = cudaMemcpy(nrm, d_nrm, sizeof(nrm), cudaMemcpyDeviceToHost);
+        cudaFree(d_nrm);
+        if (e != cudaSuccess) return fail(e, "commutator norms");
+        double wsum = 0.0;
+        for (int q = 2; q < FQ_M6_TERMS; ++q) {
+          double cmax = 0.0;
+          for (int m = 0; m < M; ++m) cmax = std::max(cmax, fabs(p->coef6[(size_t)m * FQ_M6_TERMS + q]));
+          wsum += cmax / p->h * sqrt(nrm[q - 2]);
+        }
+        fq_finish_bounds(p, p->e_min - wsum, p->e_max + wsum);
+      }
+    }
   } else {
     std::vector<double> kl(std::max(1, n - 1), 0.0);
     for (int i = 0; i + 1 < n; ++i) kl[i] = prob->h0_off[i] * (prob->h1[i] - prob->h1[i + 1]);

@@ -466,6 +466,40 @@ __global__ void k_split_omega(const double* __restrict__ h0, const double* __res
   }
 }
 
+// 6th order: S and A slices of Omega~ = sum_q c_q M_q (c already divided by h Delta E).
+struct Omega6Split {
+  const double* m[FQ_M6_TERMS];
+  double c[FQ_M6_TERMS];
+  double sbeta;
+  int n, np;
+};
+
+template <int NS>
+__global__ void k_split_omega6(Omega6Split a, __nv_bfloat16* os, __nv_bfloat16* oa, size_t slice_stride) {
+  const size_t total = (size_t)a.np * a.np;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q / a.np), c = (int)(q % a.np);
+    double S = 0.0, A = 0.0;
+    if (i < a.n && c < a.n) {
+      const size_t o = (size_t)i * a.n + c;
+      S = (i == c) ? -a.sbeta : 0.0;
+      const int sym[6] = {0, 1, 3, 4, 9, 10}, anti[5] = {2, 5, 6, 7, 8};
+#pragma unroll
+      for (int t = 0; t < 6; ++t) S = fma(a.c[sym[t]], a.m[sym[t]][o], S);
+#pragma unroll
+      for (int t = 0; t < 5; ++t) A = fma(a.c[anti[t]], a.m[anti[t]][o], A);
+    }
+    __nv_bfloat16 s1[NS], s2[NS];
+    split_f64<NS>(S, s1);
+    split_f64<NS>(A, s2);
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      os[t * slice_stride + q] = s1[t];
+      oa[t * slice_stride + q] = s2[t];
+    }
+  }
+}
+
 // Left operand and FP32 masters of the initial block: identity rows (build_UT) or given states.
 template <int NS>
 __global__ void k_split_init(const double2* __restrict__ x0, int n, int nc, int ldm, int np, int kp, float* mre,
@@ -610,8 +644,23 @@ static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int 
   t.bound2 = 1.0 + 2e-3;
   t.status = p->d_status;
   for (int m = m_begin; m < m_end; ++m) {
-    k_split_omega<NS><<<grid_1d(w.bstride), 256, 0, s>>>(p->d_h0, p->d_h1, p->d_k, n, w.np, p->sa[m], p->sb[m],
-                                                         p->sc[m], p->sbeta, w.os, w.oa, w.bstride);
+    if (p->order == 6) {
+      Omega6Split a;
+      const size_t nn = (size_t)n * n;
+      a.m[0] = p->d_h0;
+      a.m[1] = p->d_h1;
+      a.m[2] = p->d_k;
+      for (int q = 0; q < 8; ++q) a.m[3 + q] = p->d_cm + q * nn;
+      const double inv = 1.0 / (p->h * p->delta_e);
+      for (int q = 0; q < FQ_M6_TERMS; ++q) a.c[q] = p->coef6[(size_t)m * FQ_M6_TERMS + q] * inv;
+      a.sbeta = p->sbeta;
+      a.n = n;
+      a.np = w.np;
+      k_split_omega6<NS><<<grid_1d(w.bstride), 256, 0, s>>>(a, w.os, w.oa, w.bstride);
+    } else {
+      k_split_omega<NS><<<grid_1d(w.bstride), 256, 0, s>>>(p->d_h0, p->d_h1, p->d_k, n, w.np, p->sa[m], p->sb[m],
+                                                           p->sc[m], p->sbeta, w.os, w.oa, w.bstride);
+    }
     int cur = xb, nxt = (xb + 1) % 3, acc = (xb + 2) % 3, prv = -1;
     for (int l = 0; l < L; ++l) {
       t.first = l == 0;

@@ -25,6 +25,7 @@ struct fq_plan {
   // problem
   int n = 0, steps = 0, format = 0, precision = 0, drive_kind = 0, stride = 16, L = 0;
   double period = 0, h = 0, tol = 1e-14;
+  double f_dc = 0, f_ac = 0, omega = 0, phi0 = 0;   // cosine drive (observables)
   // bounds of Omega/h (Eq. 11) and Chebyshev data (Eq. 12)
   double e_min = 0, e_max = 0, beta = 0, delta_e = 0, R = 0;
   std::vector<double> cheb;            // a_0 .. a_L
@@ -34,6 +35,13 @@ struct fq_plan {
   std::vector<double> sa, sb, sc;      // Omega~_m = sa H0 + sb H1 + sc i[H0,H1] - sbeta 1
   double sbeta = 0;
   int path = PATH_DENSE_F64;
+  // 6th-order scheme: per step 11 coefficients of Omega_m over {H0, H1, K, K0, K1, K00, K01, K10,
+  // K11, KK0, KK1} (K = [H0,H1], K0 = [H0,K], K1 = [H1,K], K00 = [H0,K0], K01 = [H0,K1],
+  // K10 = [H1,K0], K11 = [H1,K1], KK0 = [K,K0], KK1 = [K,K1]); real for the symmetric ones,
+  // the imaginary factor of the antisymmetric ones
+  int order = 4;
+  std::vector<double> coef6;   // [M][11]
+  double* d_cm = nullptr;      // K0 .. KK1: 8 matrices n*n after d_k (= K)
   int tile_n = 128;          // split path: output tile width of the tensor-core kernel (autotuned)
   int device = 0;
   // device copies (owned by the plan)
@@ -58,6 +66,9 @@ int fq_cheb_order(double R, double tol);
 void fq_tridiag_extremes(const double* diag, const double* off, int n, double* lo, double* hi);
 void fq_lanczos_extremes(const double* a, int n, int ksteps, uint64_t seed, double* lo, double* hi);
 fq_status fq_host_plan(const fq_problem* p, fq_plan* plan);   // everything but device work
+// beta, Delta E, R, L, a_l, phase and the Omega~ scalars from bounds [emin, emax] of Omega/h
+void fq_finish_bounds(fq_plan* plan, double emin, double emax);
+constexpr int FQ_M6_TERMS = 11;
 
 // ---------------------------------------------------------------- kernels (kernels.cu)
 struct fq_term {
@@ -84,6 +95,10 @@ void fq_launch_gemm_f64(const double* a, const double* b, double* c, int n, doub
                         cudaStream_t s);
 void fq_launch_omega_dense_f64(const double* h0, const double* h1, const double* k, int n, double sa,
                                double sb, double sc, double sbeta, double* S, double* A, cudaStream_t s);
+// 6th order: S = sum of the symmetric terms - sbeta 1, A = sum of the antisymmetric ones; c[11]
+// already divided by h Delta E
+void fq_launch_omega6_f64(const fq_plan* p, const double* c, double* S, double* A, cudaStream_t s);
+void fq_launch_frobenius(const double* a, size_t count, double* out, cudaStream_t s);
 void fq_launch_term_dense_f64(const double* S, const double* A, int n, fq_blk<double> cur, fq_blk<double> prev,
                               fq_blk<double> acc, fq_blk<double> out, int nc, const fq_term& t, cudaStream_t s);
 

@@ -136,6 +136,50 @@ __global__ void k_omega_dense_f64(const double* __restrict__ h0, const double* _
   }
 }
 
+// 6th order: Omega~_m = sum_q c_q M_q with M_q over {H0, H1, K, K0, K1, K00, K01, K10, K11, KK0,
+// KK1}; the symmetric terms form S (minus sbeta 1), the antisymmetric ones A (Omega~ = S + i A).
+struct Omega6Args {
+  const double* m[FQ_M6_TERMS];
+  double c[FQ_M6_TERMS];
+  double sbeta;
+  int n;
+};
+
+__global__ void k_omega6_f64(Omega6Args a, double* S, double* A) {
+  const size_t total = (size_t)a.n * a.n;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q / a.n), j = (int)(q % a.n);
+    double s = (i == j) ? -a.sbeta : 0.0;
+    s = fma(a.c[0], a.m[0][q], s);
+    s = fma(a.c[1], a.m[1][q], s);
+    s = fma(a.c[3], a.m[3][q], s);
+    s = fma(a.c[4], a.m[4][q], s);
+    s = fma(a.c[9], a.m[9][q], s);
+    s = fma(a.c[10], a.m[10][q], s);
+    double t = a.c[2] * a.m[2][q];
+    t = fma(a.c[5], a.m[5][q], t);
+    t = fma(a.c[6], a.m[6][q], t);
+    t = fma(a.c[7], a.m[7][q], t);
+    t = fma(a.c[8], a.m[8][q], t);
+    S[q] = s;
+    A[q] = t;
+  }
+}
+
+__global__ void k_frobenius(const double* __restrict__ a, size_t count, double* out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < count; q += (size_t)gridDim.x * blockDim.x)
+    s = fma(a[q], a[q], s);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out, red[0]);
+}
+
 // One Chebyshev term, dense FP64: Y^T[j][i] = sum_k Psi[j][k] (S[i][k] + i A[i][k]) (tile loop in
 // dense_core.cuh) followed by the fused recurrence / Bessel accumulation / step-close epilogue.
 // A == nullptr selects the real-operator variant (piecewise drives: c_m = 0).
@@ -388,6 +432,27 @@ void fq_launch_gemm_f64(const double* a, const double* b, double* c, int n, doub
 void fq_launch_omega_dense_f64(const double* h0, const double* h1, const double* k, int n, double sa, double sb,
                                double sc, double sbeta, double* S, double* A, cudaStream_t s) {
   k_omega_dense_f64<<<grid_for((size_t)n * n, 256), 256, 0, s>>>(h0, h1, k, n, sa, sb, sc, sbeta, S, A);
+}
+
+Omega6Args omega6_args(const fq_plan* p, const double* c) {
+  Omega6Args a;
+  const size_t nn = (size_t)p->n * p->n;
+  a.m[0] = p->d_h0;
+  a.m[1] = p->d_h1;
+  a.m[2] = p->d_k;
+  for (int q = 0; q < 8; ++q) a.m[3 + q] = p->d_cm + q * nn;
+  for (int q = 0; q < FQ_M6_TERMS; ++q) a.c[q] = c[q];
+  a.sbeta = p->sbeta;
+  a.n = p->n;
+  return a;
+}
+
+void fq_launch_omega6_f64(const fq_plan* p, const double* c, double* S, double* A, cudaStream_t s) {
+  k_omega6_f64<<<grid_for((size_t)p->n * p->n, 256), 256, 0, s>>>(omega6_args(p, c), S, A);
+}
+
+void fq_launch_frobenius(const double* a, size_t count, double* out, cudaStream_t s) {
+  k_frobenius<<<grid_for(count, 256), 256, 0, s>>>(a, count, out);
 }
 
 void fq_launch_term_dense_f64(const double* S, const double* A, int n, fq_blk<double> cur, fq_blk<double> prev,

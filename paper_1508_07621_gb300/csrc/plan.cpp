@@ -227,6 +227,123 @@ void fq_lanczos_extremes(const double* a, int n, int ksteps, uint64_t seed, doub
   *hi = thi + resid(thi) + 1e-6 * span;
 }
 
+// ---------------------------------------------------------------- 6th-order Magnus (reading R12)
+// Elements of span{H0, H1, K, K0, K1, K00, K01, K10, K11, KK0, KK1} as complex coefficient
+// vectors; comm() is the commutator table of the pairs Eq. 14 needs for H = H0 + f H1.
+namespace {
+struct Cx { double re = 0, im = 0; };
+using Lie = Cx[FQ_M6_TERMS];
+void lie_zero(Lie& a) { for (auto& c : a) c = Cx{}; }
+void lie_axpy(Lie& y, double ar, double ai, const Lie& x) {  // y += (ar + i ai) x
+  for (int q = 0; q < FQ_M6_TERMS; ++q) {
+    y[q].re += ar * x[q].re - ai * x[q].im;
+    y[q].im += ar * x[q].im + ai * x[q].re;
+  }
+}
+// [e_i, e_j] = sign * e_k, or 0 (k = -1)
+void comm_basis(int i, int j, int* k, double* sign) {
+  static const int tab[5][5] = {
+      // H0   H1   K    K0   K1
+      {-1, 2, 3, 5, 6},    // H0: [H0,H1]=K, [H0,K]=K0, [H0,K0]=K00, [H0,K1]=K01
+      {-2, -1, 4, 7, 8},   // H1: [H1,H0]=-K, [H1,K]=K1, [H1,K0]=K10, [H1,K1]=K11
+      {-3, -4, -1, 9, 10}  // K:  [K,H0]=-K0, [K,H1]=-K1, [K,K0]=KK0, [K,K1]=KK1
+  };
+  *k = -1;
+  *sign = 0;
+  if (i > 2 || j > 4) return;
+  const int t = tab[i][j];
+  if (t == -1) return;
+  // entries 2..10 positive; -2 / -3 / -4 encode minus K, K0, K1
+  if (i == 1 && j == 0) { *k = 2; *sign = -1; return; }
+  if (i == 2 && j == 0) { *k = 3; *sign = -1; return; }
+  if (i == 2 && j == 1) { *k = 4; *sign = -1; return; }
+  *k = t;
+  *sign = 1;
+}
+void lie_comm(Lie& out, const Lie& x, const Lie& y) {
+  lie_zero(out);
+  for (int i = 0; i < FQ_M6_TERMS; ++i) {
+    if (x[i].re == 0 && x[i].im == 0) continue;
+    for (int j = 0; j < FQ_M6_TERMS; ++j) {
+      if (y[j].re == 0 && y[j].im == 0) continue;
+      int k;
+      double sg;
+      if (i <= 2 && j <= 4) comm_basis(i, j, &k, &sg);
+      else if (j <= 2 && i <= 4) { comm_basis(j, i, &k, &sg); sg = -sg; }
+      else { k = -2; sg = 0; }
+      if (k == -2) continue;  // outside the table: never produced by Eq. 14 for H0 + f H1
+      if (k < 0) continue;    // commutator of an element with itself
+      out[k].re += sg * (x[i].re * y[j].re - x[i].im * y[j].im);
+      out[k].im += sg * (x[i].re * y[j].im + x[i].im * y[j].re);
+    }
+  }
+}
+}  // namespace
+
+// Omega_H of step [t0, t0 + h] for Eq. 14 with alphas as 3-point Gauss-Legendre moments of
+// A = -i(H0 + f H1): alpha1 = h A_2, alpha2 = (sqrt(15) h/3)(A_3 - A_1),
+// alpha3 = (10 h/3)(A_3 - 2 A_2 + A_1); C1 = [alpha1, alpha2], C2 = -(1/60)[alpha1, 2 alpha3 + C1],
+// Omega_A = alpha1 + alpha3/12 + (1/240)[-20 alpha1 - alpha3 + C1, alpha2 + C2], Omega_H = i Omega_A.
+// out[q]: real coefficient of symmetric basis element q, imaginary factor of antisymmetric ones.
+static void magnus6_coefficients(double h, double f1, double f2, double f3, double* out) {
+  Lie a1, a2, a3, c1, c2, t, x, y, xy, om;
+  lie_zero(a1); lie_zero(a2); lie_zero(a3);
+  a1[0].im = -h; a1[1].im = -h * f2;
+  a2[1].im = -sqrt(15.0) * h / 3.0 * (f3 - f1);
+  a3[1].im = -10.0 * h / 3.0 * (f3 - 2.0 * f2 + f1);
+  lie_comm(c1, a1, a2);
+  lie_zero(t);
+  lie_axpy(t, 2.0, 0.0, a3);
+  lie_axpy(t, 1.0, 0.0, c1);
+  lie_comm(c2, a1, t);
+  for (auto& c : c2) { c.re /= -60.0; c.im /= -60.0; }
+  lie_zero(x);
+  lie_axpy(x, -20.0, 0.0, a1);
+  lie_axpy(x, -1.0, 0.0, a3);
+  lie_axpy(x, 1.0, 0.0, c1);
+  lie_zero(y);
+  lie_axpy(y, 1.0, 0.0, a2);
+  lie_axpy(y, 1.0, 0.0, c2);
+  lie_comm(xy, x, y);
+  lie_zero(om);
+  lie_axpy(om, 1.0, 0.0, a1);
+  lie_axpy(om, 1.0 / 12.0, 0.0, a3);
+  lie_axpy(om, 1.0 / 240.0, 0.0, xy);
+  // Omega_H = i Omega_A: (re, im) -> (-im, re)
+  static const bool sym[FQ_M6_TERMS] = {true, true, false, true, true, false, false, false, false, true, true};
+  for (int q = 0; q < FQ_M6_TERMS; ++q) {
+    const double re = -om[q].im, im = om[q].re;
+    out[q] = sym[q] ? re : im;
+  }
+}
+
+void fq_finish_bounds(fq_plan* plan, double emin, double emax) {
+  const double h = plan->h;
+  const int M = plan->steps;
+  plan->e_min = emin;
+  plan->e_max = emax;
+  plan->delta_e = 0.5 * (emax - emin);
+  plan->beta = plan->delta_e + emin;
+  plan->R = h * plan->delta_e;
+  plan->L = fq_cheb_order(plan->R, plan->tol);
+  plan->cheb.assign(plan->L + 1, 0.0);
+  fq_bessel_miller(plan->R, plan->L, plan->cheb.data());
+  for (int l = 1; l <= plan->L; ++l) plan->cheb[l] *= 2.0;
+  plan->phase_re = cos(plan->beta * h);
+  plan->phase_im = -sin(plan->beta * h);
+  // Omega~_m = (Omega_m / h - beta) / Delta E  (reading R2)
+  const double inv = 1.0 / (h * plan->delta_e);
+  plan->sa.resize(M);
+  plan->sb.resize(M);
+  plan->sc.resize(M);
+  for (int m = 0; m < M; ++m) {
+    plan->sa[m] = plan->ma[m] * inv;
+    plan->sb[m] = plan->mb[m] * inv;
+    plan->sc[m] = plan->mc[m] * inv;
+  }
+  plan->sbeta = plan->beta / plan->delta_e;
+}
+
 // Host part of plan creation: validates the problem, forms the Magnus scalars (reading R1),
 // bounds (reading R4), R, L and a_l (Eq. 12, reading R5).  No device work.
 fq_status fq_host_plan(const fq_problem* p, fq_plan* plan) {
@@ -255,6 +372,14 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan) {
     return FQ_EUNSUPPORTED;
   }
   const int n = p->n, M = p->steps;
+  const int order = p->magnus_order == 0 ? 4 : p->magnus_order;
+  if (order != 4 && order != 6) { fq_set_error("magnus_order must be 4 or 6 (got %d)", p->magnus_order); return FQ_EINVAL; }
+  if (order == 6 && (p->format != FQ_DENSE || p->drive_kind != FQ_DRIVE_COS)) {
+    fq_set_error("6th-order Magnus needs FQ_DENSE and FQ_DRIVE_COS (its nested commutators of a tridiagonal H0 are "
+                 "heptadiagonal)");
+    return FQ_EUNSUPPORTED;
+  }
+  plan->order = order;
   plan->n = n;
   plan->steps = M;
   plan->format = p->format;
@@ -268,14 +393,28 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan) {
   plan->tile_n = p->tile_n ? p->tile_n : 128;
   plan->period = p->period;
   plan->tol = p->cheb_tol > 0 ? p->cheb_tol : 1e-14;
+  plan->f_dc = p->f_dc;
+  plan->f_ac = p->f_ac;
+  plan->omega = p->omega;
+  plan->phi0 = p->phi0;
   const double h = p->period / M;
   plan->h = h;
   plan->ma.assign(M, h);
   plan->mb.resize(M);
   plan->mc.resize(M);
+  if (order == 6) plan->coef6.assign((size_t)M * FQ_M6_TERMS, 0.0);
   for (int m = 0; m < M; ++m) {
     const double tau = (m + 0.5) * h;
-    if (p->drive_kind == FQ_DRIVE_COS) {
+    if (order == 6) {
+      const double c = sqrt(15.0) / 10.0;
+      const double f1 = fq_drive_f(0, p->f_dc, p->f_ac, p->omega, p->phi0, tau - c * h);
+      const double f2 = fq_drive_f(0, p->f_dc, p->f_ac, p->omega, p->phi0, tau);
+      const double f3 = fq_drive_f(0, p->f_dc, p->f_ac, p->omega, p->phi0, tau + c * h);
+      double* cm = &plan->coef6[(size_t)m * FQ_M6_TERMS];
+      magnus6_coefficients(h, f1, f2, f3, cm);
+      plan->mb[m] = cm[1];  // leading part h (H0 + g H1); the commutator terms widen the bounds later
+      plan->mc[m] = 0.0;
+    } else if (p->drive_kind == FQ_DRIVE_COS) {
       const double f = fq_drive_f(0, p->f_dc, p->f_ac, p->omega, p->phi0, tau);
       const double f1 = fq_drive_f(1, p->f_dc, p->f_ac, p->omega, p->phi0, tau);
       const double f2 = fq_drive_f(2, p->f_dc, p->f_ac, p->omega, p->phi0, tau);
@@ -348,27 +487,6 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan) {
     emin -= w;
     emax += w;
   }
-  plan->e_min = emin;
-  plan->e_max = emax;
-  plan->delta_e = 0.5 * (emax - emin);
-  plan->beta = plan->delta_e + emin;
-  plan->R = h * plan->delta_e;
-  plan->L = fq_cheb_order(plan->R, plan->tol);
-  plan->cheb.resize(plan->L + 1);
-  fq_bessel_miller(plan->R, plan->L, plan->cheb.data());
-  for (int l = 1; l <= plan->L; ++l) plan->cheb[l] *= 2.0;
-  plan->phase_re = cos(plan->beta * h);
-  plan->phase_im = -sin(plan->beta * h);
-  // Omega~_m = (Omega_m / h - beta) / Delta E  (reading R2)
-  const double inv = 1.0 / (h * plan->delta_e);
-  plan->sa.resize(M);
-  plan->sb.resize(M);
-  plan->sc.resize(M);
-  for (int m = 0; m < M; ++m) {
-    plan->sa[m] = plan->ma[m] * inv;
-    plan->sb[m] = plan->mb[m] * inv;
-    plan->sc[m] = plan->mc[m] * inv;
-  }
-  plan->sbeta = plan->beta / plan->delta_e;
+  fq_finish_bounds(plan, emin, emax);
   return FQ_OK;
 }

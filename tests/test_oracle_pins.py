@@ -357,3 +357,42 @@ def test_golden_regression(name):
     assert np.max(np.abs(eps - np.array(g["eps"]))) < 1e-11
     for i, j, v in g["u"]:
         assert abs(u[i, j] - v) < 1e-12
+
+
+# -------------------------------------------------------------- period averages (Eq. 17)
+def test_average_energy_of_stationary_states():
+    """Undriven: eigenvectors of H0 are stationary, so <H(t)>_T equals their eigenvalues."""
+    n, M = 8, 40
+    h0, h1 = fi.goe(n, 41), fi.goe(n, 42)
+    drv = fi.Drive(0.0, 0.0, 1.7)
+    E, V = np.linalg.eigh(h0)
+    p = o.plan_for_drive_dense(h0, h1, drv, M)
+    k = o.commutator_dense(h0, h1)
+    step = lambda m, x: o.chebyshev_step(lambda v: o.omega_tilde_dense(h0, h1, k, p, m) @ v, x, p.coeffs, p.phase)
+    avg = o.average_observable(step, o.expect_dense(h0, h1, 1.0, 0.0, 1.0, drv), V, drv, M)
+    assert np.max(np.abs(avg - E)) < 1e-12
+
+
+def test_average_h1_is_quasienergy_slope():
+    """Floquet Hellmann-Feynman: for H = H0 + (f_dc + f_ac cos wt) H1, d eps_mu / d f_dc equals the
+    period average <H1>_T of Floquet state mu (Eq. 17 with A = H1): a relation between the
+    quasienergies (eigenvalues of U_T) and the second propagation round."""
+    n, M = 6, 80
+    h0, h1 = fi.goe(n, 31), fi.goe(n, 32)
+
+    def quasi(fdc):
+        drv = fi.Drive(fdc, 0.9, 1.3, 0.0)
+        p = o.plan_for_drive_dense(h0, h1, drv, M)
+        lam, V = np.linalg.eig(o.build_ut_dense(h0, h1, p))
+        return lam, V, drv, p
+
+    fdc, d = 0.2, 1e-4
+    lam, V, drv, p = quasi(fdc)
+    match = lambda l0, l1: np.array([l1[np.argmin(np.abs(l1 - x))] for x in l0])
+    lp, lm = quasi(fdc + d)[0], quasi(fdc - d)[0]
+    slope = (-np.angle(match(lam, lp) / lam) + np.angle(match(lam, lm) / lam)) / (2 * d * drv.period)
+    k = o.commutator_dense(h0, h1)
+    step = lambda m, x: o.chebyshev_step(lambda v: o.omega_tilde_dense(h0, h1, k, p, m) @ v, x, p.coeffs, p.phase)
+    avg = o.average_observable(step, o.expect_dense(h0, h1, 0.0, 1.0, 0.0, drv), V / np.linalg.norm(V, axis=0),
+                               drv, M)
+    assert np.max(np.abs(slope - avg)) < 1e-6
