@@ -42,9 +42,12 @@ struct ResCoef {
 };
 
 struct ResShared {
-  float2 slot_first[2][RES_MAXNW];
-  float2 slot_last[2][RES_MAXNW];
+  float4 slot_last[2][RES_MAXNW];  // last two rows of each warp's lane 31
   float red[RES_MAXNW];
+  float tot;           // squared norm of the initial state
+  float lim_state;     // bound on |X_m entry|^2
+  float lim_clenshaw;  // bound on |b_1 entry|^2
+  unsigned int bad;    // set by any thread whose check failed
 };
 
 // Position of row i in resident order (float2 units) for NT threads of EPT rows each.
@@ -185,70 +188,184 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 __device__ __forceinline__ float2 lo2(float4 a) { return make_float2(a.x, a.y); }
 __device__ __forceinline__ float2 hi2(float4 a) { return make_float2(a.z, a.w); }
 
+// c v for a real c (IM = false) or an imaginary c = i cc (IM = true)
+template <bool IM>
+__device__ __forceinline__ float2 cvec(float cc, float2 vv) {
+  return IM ? f2(-cc * vv.y, cc * vv.x) : f2(cc * vv.x, cc * vv.y);
+}
+
+// one row of a Clenshaw product: c v - o + (2 Omega' x)_row, where the row of the stored operator
+// 2 Omega' is (el, d, eh) on (xm, x0, xp).  Four packed FP32x2 FMAs for a real c.
+template <bool IM>
+__device__ __forceinline__ float2 row(float cc, float2 vv, float2 o, float d, float2 x0, float el, float2 xm, float eh,
+                                      float2 xp) {
+  float2 acc;
+  if (IM) acc = f2(fmaf(-cc, vv.y, -o.x), fmaf(cc, vv.x, -o.y));
+  else acc = __ffma2_rn(f2(cc, cc), vv, f2(-o.x, -o.y));
+  acc = __ffma2_rn(f2(d, d), x0, acc);
+  acc = __ffma2_rn(f2(el, el), xm, acc);
+  return __ffma2_rn(f2(eh, eh), xp, acc);
+}
+
+// the closing product: c0 v - o + (1/2)(2 Omega' x)_row, c0 real
+__device__ __forceinline__ float2 row_half(float cc, float2 vv, float2 o, float d, float2 x0, float el, float2 xm,
+                                           float eh, float2 xp) {
+  float2 s = __fmul2_rn(f2(d, d), x0);
+  s = __ffma2_rn(f2(el, el), xm, s);
+  s = __ffma2_rn(f2(eh, eh), xp, s);
+  return __ffma2_rn(f2(0.5f, 0.5f), s, __ffma2_rn(f2(cc, cc), vv, f2(-o.x, -o.y)));
+}
+
 template <int NT, int EPT>
-struct Resident {
+struct Chain {
   static constexpr int NW = NT / 32;
   static constexpr int NP = EPT / 2;
-  float4* v;   // [NP][NT] state in the step's frame, rows (2p, 2p+1)
-  float4* cf;  // [NP][NT] (2 d, 2 e') of rows (2p, 2p+1), e'_i = Omega'[i+1][i]
+  const float4* v;   // [NP][NT] state in the step's frame, rows (2p, 2p+1)
+  const float4* cf;  // [NP][NT] (2 d, 2 e') of rows (2p, 2p+1), e'_i = Omega'[i+1][i]
+  float4* first2;    // [2][NT] first two rows of b_{k+1} per thread (exchange buffers)
+  float4* bhalo;     // [NT] (b_k at row i0-1, b_k at row i0+EPT) per thread, carried between passes
   ResShared* sh;
   int t, lane, warp;
 
-  // halo of x: left = x[t*EPT - 1], right = x[t*EPT + EPT]
-  __device__ __forceinline__ void halo(const float2 (&x)[EPT], int par, float2& left, float2& right) {
-    float lr = __shfl_up_sync(0xffffffffu, x[EPT - 1].x, 1);
-    float li = __shfl_up_sync(0xffffffffu, x[EPT - 1].y, 1);
-    float rr = __shfl_down_sync(0xffffffffu, x[0].x, 1);
-    float ri = __shfl_down_sync(0xffffffffu, x[0].y, 1);
-    if (lane == 31) sh->slot_last[par][warp] = x[EPT - 1];
-    if (lane == 0) sh->slot_first[par][warp] = x[0];
+  // Publishes x's first two rows for the left neighbour (read back by right() after the sweep) and
+  // returns rows i0-2, i0-1 (as (re, im, re, im)) of the left neighbour; zero before row 0.
+  // One __syncthreads; the buffers alternate with par so that one barrier per pass suffices.
+  __device__ __forceinline__ float4 exchange(const float2 (&x)[EPT], int par) {
+    float4 l;
+    l.x = __shfl_up_sync(0xffffffffu, x[EPT - 2].x, 1);
+    l.y = __shfl_up_sync(0xffffffffu, x[EPT - 2].y, 1);
+    l.z = __shfl_up_sync(0xffffffffu, x[EPT - 1].x, 1);
+    l.w = __shfl_up_sync(0xffffffffu, x[EPT - 1].y, 1);
+    if (lane == 31) sh->slot_last[par][warp] = make_float4(x[EPT - 2].x, x[EPT - 2].y, x[EPT - 1].x, x[EPT - 1].y);
+    first2[par * NT + t] = make_float4(x[0].x, x[0].y, x[1].x, x[1].y);
     __syncthreads();
-    if (lane == 0) {
-      float2 w = warp > 0 ? sh->slot_last[par][warp - 1] : f2(0.f, 0.f);
-      lr = w.x;
-      li = w.y;
-    }
-    if (lane == 31) {
-      float2 w = warp < NW - 1 ? sh->slot_first[par][warp + 1] : f2(0.f, 0.f);
-      rr = w.x;
-      ri = w.y;
-    }
-    left = f2(lr, li);
-    right = f2(rr, ri);
+    if (lane == 0) l = warp > 0 ? sh->slot_last[par][warp - 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    return l;
+  }
+  // rows i0+EPT, i0+EPT+1 as published by the right neighbour in exchange(); zero past the end
+  __device__ __forceinline__ float4 right(int par) const {
+    return t < NT - 1 ? first2[par * NT + t + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 
-  // one row: out = c v + scale (2 Omega' x)_row - out on the (re, im) pair
-  __device__ __forceinline__ float2 row(float2 xm, float2 x0, float2 xp, float2 o, float2 vv, float dq, float elo,
-                                        float ehi, float cc, bool imag) {
-    // c v: a real c scales (re, im); an imaginary c = i cc maps (re, im) to cc (-im, re)
-    float2 acc = imag ? f2(-cc * vv.y, cc * vv.x) : f2(cc * vv.x, cc * vv.y);
-    acc = __ffma2_rn(f2(-1.f, -1.f), o, acc);
-    acc = __ffma2_rn(f2(dq, dq), x0, acc);
-    acc = __ffma2_rn(f2(elo, elo), xm, acc);
-    acc = __ffma2_rn(f2(ehi, ehi), xp, acc);
-    return acc;
-  }
-
-  // out = c v + scale (2 Omega') x - out for all rows of the thread.
-  // c = (cr, ci) is real (ci = 0) or imaginary (cr = 0).
-  __device__ __forceinline__ void apply(const float2 (&x)[EPT], float2 (&out)[EPT], float cr, float ci,
-                                        float scale, float el0, int par) {
-    float2 left, right;
-    halo(x, par, left, right);
-    const bool imag = ci != 0.f;
-    const float cc = imag ? ci : cr;
-    float elo = el0 * scale;
+  // Two Clenshaw products in one sweep over the rows (Eqs. 10 and 12 in backward form):
+  //   P1: b_k     = c_k v + 2 Omega' b_{k+1} - b_{k+2}   on rows i0-1 .. i0+EPT (own rows + one halo row a side)
+  //   P2: b_{k-1} = c_{k-1} v + 2 Omega' b_k - b_{k+1}   on own rows (FINAL: the closing sum with Omega')
+  // In: A = b_{k+1}, B = b_{k+2} (own rows), bhalo[t] = b_{k+2} on the halo rows (FIRST: all zero).
+  // Out: A = b_{k-1}, B = b_k, bhalo[t] = b_k on the halo rows (only thread t touches bhalo[t]).  The operator and v rows of a pair are
+  // read from shared memory once for both products; only b_{k+1} crosses threads (two rows a side).
+  // K_ODD: c_k = i c1 and c_{k-1} = c2 real; otherwise c_k = c1 real and c_{k-1} = i c2.
+  template <bool FIRST, bool FINAL, bool K_ODD>
+  __device__ __forceinline__ void pass(float2 (&A)[EPT], float2 (&B)[EPT], float c1, float c2, int par) {
+    constexpr bool IM1 = K_ODD, IM2 = !K_ODD;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 z2 = f2(0.f, 0.f);
+    const float4 al = FIRST ? z4 : exchange(A, par);
+    const float2 am2 = lo2(al), am1 = hi2(al);
+    // row i0-1: (., 2e'_{i0-2}, 2d_{i0-1}, 2e'_{i0-1}) and its v
+    const float4 cl = t > 0 ? cf[(NP - 1) * NT + t - 1] : z4;
+    const float2 vl = t > 0 ? hi2(v[(NP - 1) * NT + t - 1]) : z2;
+    const float2 nbl =
+        FIRST ? cvec<IM1>(c1, vl) : row<IM1>(c1, vl, lo2(bhalo[t]), cl.z, am1, cl.y, am2, cl.w, A[0]);
+    float4 cp = cl;  // operator of rows 2p-2, 2p-1
+    float2 vp = vl;  // v of row 2p-1
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-      const int s = p * NT + t;
-      const float4 c = cf[s];
-      const float4 vv = v[s];
       const int q = 2 * p;
-      const float d0 = c.x * scale, e0 = c.y * scale, d1 = c.z * scale, e1 = c.w * scale;
-      out[q] = row(q == 0 ? left : x[q - 1], x[q], x[q + 1], out[q], lo2(vv), d0, elo, e0, cc, imag);
-      out[q + 1] = row(x[q], x[q + 1], q + 1 == EPT - 1 ? right : x[q + 2], out[q + 1], hi2(vv), d1, e0, e1, cc,
-                       imag);
-      elo = e1;
+      const float4 c = cf[p * NT + t];
+      const float4 w = v[p * NT + t];
+      float2 b0, b1;
+      if (FIRST) {
+        b0 = cvec<IM1>(c1, lo2(w));
+        b1 = cvec<IM1>(c1, hi2(w));
+      } else {
+        b0 = row<IM1>(c1, lo2(w), B[q], c.x, A[q], cp.w, q == 0 ? am1 : A[q - 1], c.y, A[q + 1]);
+        b1 = row<IM1>(c1, hi2(w), B[q + 1], c.z, A[q + 1], c.y, A[q], c.w,
+                      q + 2 < EPT ? A[q + 2] : lo2(right(par)));
+      }
+      // P2 on row q-1 (its upper neighbour b0 is now known) and on row q
+      if (p > 0) {
+        const float2 o = FIRST ? z2 : A[q - 1];
+        A[q - 1] = FINAL ? row_half(c2, vp, o, cp.z, B[q - 1], cp.y, q >= 2 ? B[q - 2] : nbl, cp.w, b0)
+                         : row<IM2>(c2, vp, o, cp.z, B[q - 1], cp.y, q >= 2 ? B[q - 2] : nbl, cp.w, b0);
+      }
+      {
+        const float2 o = FIRST ? z2 : A[q];
+        A[q] = FINAL ? row_half(c2, lo2(w), o, c.x, b0, cp.w, q == 0 ? nbl : B[q - 1], c.y, b1)
+                     : row<IM2>(c2, lo2(w), o, c.x, b0, cp.w, q == 0 ? nbl : B[q - 1], c.y, b1);
+      }
+      B[q] = b0;
+      B[q + 1] = b1;
+      cp = c;
+      vp = hi2(w);
+    }
+    // row i0+EPT: (2d, 2e') of that row and its v
+    const float2 cr = t < NT - 1 ? lo2(cf[t + 1]) : z2;
+    const float2 vr = t < NT - 1 ? lo2(v[t + 1]) : z2;
+    float2 nbr;
+    if (FIRST) {
+      nbr = cvec<IM1>(c1, vr);
+    } else {
+      const float4 ar = right(par);
+      nbr = row<IM1>(c1, vr, hi2(bhalo[t]), cr.x, lo2(ar), cp.w, A[EPT - 1], cr.y, hi2(ar));
+    }
+    {
+      const float2 o = FIRST ? z2 : A[EPT - 1];
+      A[EPT - 1] = FINAL ? row_half(c2, vp, o, cp.z, B[EPT - 1], cp.y, B[EPT - 2], cp.w, nbr)
+                         : row<IM2>(c2, vp, o, cp.z, B[EPT - 1], cp.y, B[EPT - 2], cp.w, nbr);
+    }
+    bhalo[t] = make_float4(nbl.x, nbl.y, nbr.x, nbr.y);
+  }
+
+  // The closing product alone (an even number L): B <- c0 v + Omega' A - B on own rows, A = b_1.
+  __device__ __forceinline__ void single_final(const float2 (&A)[EPT], float2 (&B)[EPT], float c0, int par) {
+    const float2 am1 = hi2(exchange(A, par));
+    float el = t > 0 ? cf[(NP - 1) * NT + t - 1].w : 0.f;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int q = 2 * p;
+      const float4 c = cf[p * NT + t];
+      const float4 w = v[p * NT + t];
+      B[q] = row_half(c0, lo2(w), B[q], c.x, A[q], el, q == 0 ? am1 : A[q - 1], c.y, A[q + 1]);
+      B[q + 1] =
+          row_half(c0, hi2(w), B[q + 1], c.z, A[q + 1], c.y, A[q], c.w, q + 2 < EPT ? A[q + 2] : lo2(right(par)));
+      el = c.w;
+    }
+  }
+
+  // flags any entry of x with |x|^2 above lim
+  __device__ __forceinline__ void check(const float2 (&x)[EPT], float lim) {
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) ok &= x[q].x * x[q].x + x[q].y * x[q].y <= lim;
+    if (!ok) sh->bad = 1u;
+  }
+
+  // sum_{k=0}^{L} c_k T_k(Omega') v into A (c_k = (-i)^k a_k: imaginary exactly for odd k);
+  // checks |b_1| against the Clenshaw bound.
+  template <bool L_ODD>
+  __device__ __forceinline__ void series(float2 (&A)[EPT], float2 (&B)[EPT], int L, const ResCoef& coef) {
+    // c_k = i ci[k] for odd k, cr[k] for even k
+    auto cc = [&](int k) { return (k & 1) ? coef.ci[k] : coef.cr[k]; };
+    int par = 0;
+    if (L_ODD && L == 1) {
+      pass<true, true, true>(A, B, cc(1), cc(0), par);
+      check(B, sh->lim_clenshaw);
+      return;
+    }
+    pass<true, false, L_ODD>(A, B, cc(L), cc(L - 1), par);
+    int k = L - 2;
+    for (; k >= 2; k -= 2) {
+      pass<false, false, L_ODD>(A, B, cc(k), cc(k - 1), par);
+      par ^= 1;
+    }
+    if (L_ODD) {  // k == 1: the pair (1, 0) closes the series; B = b_1 afterwards
+      pass<false, true, true>(A, B, cc(1), cc(0), par);
+      check(B, sh->lim_clenshaw);
+    } else {  // k == 0: A = b_1, B = b_2
+      check(A, sh->lim_clenshaw);
+      single_final(A, B, cc(0), par);
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) A[q] = B[q];
     }
   }
 };
@@ -258,121 +375,83 @@ __global__ void __launch_bounds__(NT, 1)
 k_tri_resident(const float4* __restrict__ cf_all, const float4* __restrict__ rot_all, int n, int L, int nsteps,
                const double2* __restrict__ x0, double2* __restrict__ xout, int transpose_out, ResCoef coef,
                float ph_re, float ph_im, float clenshaw_bound, unsigned int* status) {
-  using Res = Resident<NT, EPT>;
+  using Ch = Chain<NT, EPT>;
   constexpr int NP = EPT / 2, NW = NT / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Res R;
-  float4* base = reinterpret_cast<float4*>(smem_raw);
-  R.v = base;
-  R.cf = base + NP * NT;
-  R.sh = reinterpret_cast<ResShared*>(base + 2 * NP * NT);
-  R.t = threadIdx.x;
-  R.lane = threadIdx.x & 31;
-  R.warp = threadIdx.x >> 5;
+  float4* sv = reinterpret_cast<float4*>(smem_raw);
+  float4* scf = sv + NP * NT;
+  Ch C;
+  C.v = sv;
+  C.cf = scf;
+  C.first2 = sv + 2 * NP * NT;
+  C.bhalo = sv + 2 * NP * NT + 2 * NT;
+  C.sh = reinterpret_cast<ResShared*>(sv + 2 * NP * NT + 3 * NT);
+  C.t = threadIdx.x;
+  C.lane = threadIdx.x & 31;
+  C.warp = threadIdx.x >> 5;
   const int t = threadIdx.x;
   const int j = blockIdx.x;  // state index
   const int i0 = t * EPT;
   const size_t stride = (size_t)NP * NT;  // one step of cf / rot, in float4
 
-  // initial state and its squared norm (unitarity bounds every later entry by it)
+  // initial state (registers) and its squared norm (unitarity bounds every later entry by it)
+  float2 A[EPT], B[EPT];
   float nrm = 0.f;
 #pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    float w[4];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int i = i0 + 2 * p + r;
-      float a = 0.f, b = 0.f;
-      if (i < n) {
-        if (x0) {
-          double2 z = x0[(size_t)j * n + i];
-          a = (float)z.x;
-          b = (float)z.y;
-        } else {
-          a = i == j ? 1.f : 0.f;
-        }
+  for (int q = 0; q < EPT; ++q) {
+    const int i = i0 + q;
+    float a = 0.f, b = 0.f;
+    if (i < n) {
+      if (x0) {
+        const double2 zz = x0[(size_t)j * n + i];
+        a = (float)zz.x;
+        b = (float)zz.y;
+      } else {
+        a = i == j ? 1.f : 0.f;
       }
-      w[2 * r] = a;
-      w[2 * r + 1] = b;
-      nrm = fmaf(a, a, fmaf(b, b, nrm));
     }
-    R.v[p * NT + t] = make_float4(w[0], w[1], w[2], w[3]);
+    A[q] = f2(a, b);
+    nrm = fmaf(a, a, fmaf(b, b, nrm));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-  if (R.lane == 0) R.sh->red[R.warp] = nrm;
+  if (C.lane == 0) C.sh->red[C.warp] = nrm;
   __syncthreads();
-  float tot = 0.f;
-#pragma unroll
-  for (int w = 0; w < NW; ++w) tot += R.sh->red[w];
-  const float bound2 = tot * 1.002f + 1e-30f;
-  // |b_k| <= sum_j |c_j| |U_{j-k}(Omega')| |v| <= sum_j (j+1)|a_j| |v| while the spectrum of
-  // Omega' lies in [-1, 1] (|U_n| <= n+1 there); outside it U_n grows exponentially.
-  const float bcl2 = tot * clenshaw_bound * clenshaw_bound * 1.01f + 1e-30f;
-  bool bad = false;
+  if (t == 0) {
+    float tot = 0.f;
+    for (int w = 0; w < NW; ++w) tot += C.sh->red[w];
+    C.sh->tot = tot;
+    C.sh->lim_state = tot * 1.002f + 1e-30f;
+    // |b_k| <= sum_j |c_j| |U_{j-k}(Omega')| |v| <= sum_j (j+1)|a_j| |v| while the spectrum of
+    // Omega' lies in [-1, 1] (|U_n| <= n+1 there); outside it U_n grows exponentially.
+    C.sh->lim_clenshaw = tot * clenshaw_bound * clenshaw_bound * 1.01f + 1e-30f;
+    C.sh->bad = 0u;
+  }
 
-  float2 bA[EPT], bB[EPT];
   for (int m = 0; m < nsteps; ++m) {
     const size_t off = (size_t)m * stride;
+    // every thread is done with the previous step's operator and state rows
+    __syncthreads();
     // this step's (2 d, 2 e') and the frame change D_m^+ D_{m-1} of the state (coalesced)
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       const int s = p * NT + t;
       const float4 c = cf_all[off + s];
       const float4 r = rot_all[off + s];
-      R.cf[s] = c;
-      const float4 w = R.v[s];
-      R.v[s] = make_float4(r.x * w.x - r.y * w.y, r.x * w.y + r.y * w.x, r.z * w.z - r.w * w.w,
-                           r.z * w.w + r.w * w.z);
+      scf[s] = c;
+      const float2 a = A[2 * p], b = A[2 * p + 1];
+      sv[s] = make_float4(r.x * a.x - r.y * a.y, r.x * a.y + r.y * a.x, r.z * b.x - r.w * b.y, r.z * b.y + r.w * b.x);
     }
-    // left neighbour's e' (last row of thread t-1)
-    const float el0 = t > 0 ? cf_all[off + (size_t)(NP - 1) * NT + t - 1].w : 0.f;
-    // b_L = c_L v ; b_{L+1} = 0
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const float4 w = R.v[p * NT + t];
-      bA[2 * p] = f2(coef.cr[L] * w.x - coef.ci[L] * w.y, coef.cr[L] * w.y + coef.ci[L] * w.x);
-      bA[2 * p + 1] = f2(coef.cr[L] * w.z - coef.ci[L] * w.w, coef.cr[L] * w.w + coef.ci[L] * w.z);
-      bB[2 * p] = f2(0.f, 0.f);
-      bB[2 * p + 1] = f2(0.f, 0.f);
-    }
-    int k = L - 1;
-    int par = 0;
-    // b_k = c_k v + 2 Omega' b_{k+1} - b_{k+2}, two per iteration so the roles stay static
-    while (k >= 2) {
-      R.apply(bA, bB, coef.cr[k], coef.ci[k], 1.f, el0, par);
-      par ^= 1;
-      --k;
-      R.apply(bB, bA, coef.cr[k], coef.ci[k], 1.f, el0, par);
-      par ^= 1;
-      --k;
-    }
-    if (k == 1) {
-      R.apply(bA, bB, coef.cr[1], coef.ci[1], 1.f, el0, par);
-      par ^= 1;
-#pragma unroll
-      for (int q = 0; q < EPT; ++q) bad |= !(bB[q].x * bB[q].x + bB[q].y * bB[q].y <= bcl2);
-      // b_1 in B, b_2 in A: sum = c_0 v + Omega' b_1 - b_2 (stored operator is 2 Omega')
-      R.apply(bB, bA, coef.cr[0], coef.ci[0], 0.5f, el0, par);
-#pragma unroll
-      for (int q = 0; q < EPT; ++q) bB[q] = bA[q];
-    } else {
-#pragma unroll
-      for (int q = 0; q < EPT; ++q) bad |= !(bA[q].x * bA[q].x + bA[q].y * bA[q].y <= bcl2);
-      R.apply(bA, bB, coef.cr[0], coef.ci[0], 0.5f, el0, par);
-    }
-    // X_m = e^{-i beta h} sum (in B, this step's frame); v <- X_m
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const float2 a = bB[2 * p], b = bB[2 * p + 1];
-      const float4 x = make_float4(ph_re * a.x - ph_im * a.y, ph_re * a.y + ph_im * a.x, ph_re * b.x - ph_im * b.y,
-                                   ph_re * b.y + ph_im * b.x);
-      bad |= !(x.x * x.x + x.y * x.y <= bound2) || !(x.z * x.z + x.w * x.w <= bound2);
-      R.v[p * NT + t] = x;
-    }
-    // the halo slots of the next step's first product use parity 0 again; make sure every
-    // warp has consumed this step's last slots before they are overwritten
+    C.check(A, C.sh->lim_state);  // X_{m-1} (or the initial state)
     __syncthreads();
+    if (L & 1) C.template series<true>(A, B, L, coef);
+    else C.template series<false>(A, B, L, coef);
+    // X_m = e^{-i beta h} sum (this step's frame)
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const float2 a = A[q];
+      A[q] = f2(ph_re * a.x - ph_im * a.y, ph_re * a.y + ph_im * a.x);
+    }
   }
   // back to the original frame: X = D_last v; unitarity check on the state's norm (a spectral
   // bound that is too tight keeps the entries small but makes the truncated series non-unitary)
@@ -380,35 +459,33 @@ k_tri_resident(const float4* __restrict__ cf_all, const float4* __restrict__ rot
   const size_t offr = (size_t)nsteps * stride;
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    const int s = p * NT + t;
-    const float4 r = rot_all[offr + s];
-    const float4 w = R.v[s];
-    const float4 x = make_float4(r.x * w.x - r.y * w.y, r.x * w.y + r.y * w.x, r.z * w.z - r.w * w.w,
-                                 r.z * w.w + r.w * w.z);
-    R.v[s] = x;
-    nrm_end = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, nrm_end))));
+    const float4 r = rot_all[offr + p * NT + t];
+    const float2 a = A[2 * p], b = A[2 * p + 1];
+    A[2 * p] = f2(r.x * a.x - r.y * a.y, r.x * a.y + r.y * a.x);
+    A[2 * p + 1] = f2(r.z * b.x - r.w * b.y, r.z * b.y + r.w * b.x);
+    nrm_end = fmaf(A[2 * p].x, A[2 * p].x, fmaf(A[2 * p].y, A[2 * p].y, nrm_end));
+    nrm_end = fmaf(A[2 * p + 1].x, A[2 * p + 1].x, fmaf(A[2 * p + 1].y, A[2 * p + 1].y, nrm_end));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nrm_end += __shfl_xor_sync(0xffffffffu, nrm_end, o);
   __syncthreads();
-  if (R.lane == 0) R.sh->red[R.warp] = nrm_end;
+  if (C.lane == 0) C.sh->red[C.warp] = nrm_end;
   __syncthreads();
-  float tot_end = 0.f;
+  if (t == 0) {
+    float tot_end = 0.f;
+    for (int w = 0; w < NW; ++w) tot_end += C.sh->red[w];
+    const float tot = C.sh->tot;
+    if (!(fabsf(tot_end - tot) <= 1e-3f * tot + 1e-30f)) C.sh->bad = 1u;
+  }
+  __syncthreads();
+  if (t == 0 && C.sh->bad) atomicOr(status, FQ_BIT_BOUND);
 #pragma unroll
-  for (int w = 0; w < NW; ++w) tot_end += R.sh->red[w];
-  bad |= !(fabsf(tot_end - tot) <= 1e-3f * tot + 1e-30f);
-  if (bad) atomicOr(status, FQ_BIT_BOUND);
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    const float4 w = R.v[p * NT + t];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int i = i0 + 2 * p + r;
-      if (i < n) {
-        const double2 x = r == 0 ? make_double2((double)w.x, (double)w.y) : make_double2((double)w.z, (double)w.w);
-        if (transpose_out) xout[(size_t)i * n + j] = x;
-        else xout[(size_t)j * n + i] = x;
-      }
+  for (int q = 0; q < EPT; ++q) {
+    const int i = i0 + q;
+    if (i < n) {
+      const double2 x = make_double2((double)A[q].x, (double)A[q].y);
+      if (transpose_out) xout[(size_t)i * n + j] = x;
+      else xout[(size_t)j * n + i] = x;
     }
   }
 }
@@ -416,7 +493,7 @@ k_tri_resident(const float4* __restrict__ cf_all, const float4* __restrict__ rot
 template <int NT, int EPT>
 fq_status launch_cfg(const fq_plan* p, const float4* cf, const float4* rot, const double* x0, double* x,
                      int transpose_out, int nc, int nsteps, const ResCoef& coef, float bcl, cudaStream_t s) {
-  const size_t smem = sizeof(float4) * EPT * NT + sizeof(ResShared);
+  const size_t smem = sizeof(float4) * (EPT + 3) * NT + sizeof(ResShared);
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e =
