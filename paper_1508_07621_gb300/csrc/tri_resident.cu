@@ -522,6 +522,11 @@ void res_config(int n, int* nt, int* ept) {
   }
   const int need = (n + 511) / 512;
   if (need > 20) return;
+  if (need > 18) {
+    *nt = 256;
+    *ept = 40;
+    return;
+  }
   *nt = 512;
   *ept = need + (need & 1);
 }
@@ -578,6 +583,7 @@ fq_status fq_launch_resident(const fq_plan* p, const void* coeff, const double* 
   const float b = (float)bcl;
   if (nt == 256 && ept == 2) return launch_cfg<256, 2>(p, cf, rot, x0, x, transpose_out, nc, nsteps, coef, b, s);
   if (nt == 256 && ept == 4) return launch_cfg<256, 4>(p, cf, rot, x0, x, transpose_out, nc, nsteps, coef, b, s);
+  if (nt == 256 && ept == 40) return launch_cfg<256, 40>(p, cf, rot, x0, x, transpose_out, nc, nsteps, coef, b, s);
   switch (ept) {
     case 4: return launch_cfg<512, 4>(p, cf, rot, x0, x, transpose_out, nc, nsteps, coef, b, s);
     case 6: return launch_cfg<512, 6>(p, cf, rot, x0, x, transpose_out, nc, nsteps, coef, b, s);
