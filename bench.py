@@ -27,6 +27,10 @@ NB = 10000
 STEPS = 2000
 FLOPS_PER_ELEMENT_TERM = 26   # complex tridiagonal apply 18 + recurrence 4 + Bessel accumulation 4
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# DRAM traffic of the resident kernel from one ncu capture of `--ncu-case resident` (152 states,
+# steps 0..19, k_tri_resident<256, 40>): bytes read, of which the 152 initial states are a fixed
+# part; the rest is the per-step (2d, 2e') and rotation stream, which grows with waves x steps.
+RES_NCU = {"read": 28.519936e6, "x0": 152 * 10001 * 16, "states": 152, "steps": 20}
 
 
 def parse():
@@ -268,8 +272,12 @@ def run_ours(args):
     avg = statistics.mean(per_step)
     achieved = flops / avg / 1e12
     peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    per_wave_step = (RES_NCU["read"] - RES_NCU["x0"]) / RES_NCU["steps"]
+    traffic = per_wave_step * (n / RES_NCU["states"]) * d.steps + 16.0 * n * n
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_tri_resident<20>",
+                "traffic": traffic, "traffic_note": "bytes per launch, scaled from an ncu capture of 152 states "
+                "x 20 steps (per-step coefficient reads x waves x steps) plus the U_T write",
+                "kernel": "k_tri_resident<256, 40>",
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)"}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
