@@ -44,11 +44,12 @@ class Plan:
         return cls(prob, keep)
 
     @classmethod
-    def piecewise(cls, h0, h1, f_steps, *, period, precision=B.FQ_FP64, checkpoint_stride=16, cheb_tol=0.0):
+    def piecewise(cls, h0, h1, f_steps, *, period, precision=B.FQ_FP64, checkpoint_stride=16, cheb_tol=0.0,
+                  tile_n=0):
         n = h0.shape[0]
         prob, keep = B.make_problem(n, B.FQ_DENSE, h0, h1, period, len(f_steps), drive_kind=B.FQ_DRIVE_PIECEWISE,
                                     f_steps=f_steps, precision=precision, checkpoint_stride=checkpoint_stride,
-                                    cheb_tol=cheb_tol)
+                                    cheb_tol=cheb_tol, tile_n=tile_n)
         return cls(prob, keep)
 
     # ---------------------------------------------------------------- calls
@@ -112,6 +113,40 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+_FIDELITY_FN = None
+
+
+def _fidelity_function():
+    """torch.autograd.Function whose forward and backward are one floquet_grad call: the loss
+    and dL/df come out of the same forward sweep plus adjoint chain, and backward scales the
+    kept gradient by the incoming cotangent."""
+    global _FIDELITY_FN
+    if _FIDELITY_FN is None:
+        import torch
+
+        class FidelityLoss(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, f, plan, W):
+                loss, g = plan.grad(f.detach().to(torch.float64).contiguous(), W)
+                ctx.save_for_backward(g)
+                return loss[0]
+
+            @staticmethod
+            def backward(ctx, gout):
+                (g,) = ctx.saved_tensors
+                return gout * g, None, None
+
+        _FIDELITY_FN = FidelityLoss
+    return _FIDELITY_FN
+
+
+def fidelity_loss(plan, f, W):
+    """Gate-fidelity loss L(f) = 1 - |Tr(W^+ U_T(f))|^2 / N^2 as a differentiable torch scalar of
+    the piecewise amplitudes f (float64 device tensor of length M; plan from Plan.piecewise, W an
+    N x N complex128 device tensor).  Its gradient is the library's adjoint (floquet_grad)."""
+    return _fidelity_function().apply(f, plan, W)
 
 
 def unitarity_defect(U, cols=None, stream=None):

@@ -314,8 +314,17 @@ void forward_step(const fq_plan* p, const GradWs& w, const double* d_f, int m, M
 
 }  // namespace
 
+void fq_launch_loss(const double2* partial, int count, int n, double* loss, double2* tau, cudaStream_t s) {
+  k_loss<<<1, 256, 0, s>>>(partial, count, n, loss, tau);
+}
+
+void fq_launch_grad_reduce(const double2* partial, int ncta, int L, double* grad_m, cudaStream_t s) {
+  k_grad_reduce<<<1, 256, 0, s>>>(partial, ncta, L, grad_m);
+}
+
 extern "C" size_t floquet_grad_workspace_size(const fq_plan* p) {
   if (!p || p->format != FQ_DENSE || p->drive_kind != FQ_DRIVE_PIECEWISE) return 0;
+  if (p->precision == FQ_BF16X3 || p->precision == FQ_BF16X6) return fq_grad_split_workspace(p);
   return grad_layout(p, nullptr, nullptr);
 }
 
@@ -329,16 +338,17 @@ extern "C" fq_status floquet_grad(fq_plan* p, const double* d_f, const void* d_W
     fq_set_error("floquet_grad needs a dense plan with FQ_DRIVE_PIECEWISE");
     return FQ_EINVAL;
   }
-  if (p->precision != FQ_FP64) {
-    fq_set_error("floquet_grad: only FQ_FP64 is built");
+  if (p->precision != FQ_FP64 && p->precision != FQ_BF16X3 && p->precision != FQ_BF16X6) {
+    fq_set_error("floquet_grad: FQ_FP64, FQ_BF16X3 and FQ_BF16X6 are built");
     return FQ_EUNSUPPORTED;
   }
-  const size_t need = grad_layout(p, nullptr, nullptr);
+  const size_t need = floquet_grad_workspace_size(p);
   if (!d_ws || ws_bytes < need || ((uintptr_t)d_ws & 255)) {
     fq_set_error("floquet_grad: workspace must be >= %zu bytes, 256-byte aligned (got %zu)", need, ws_bytes);
     return FQ_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (p->precision != FQ_FP64) return fq_grad_split(p, d_f, d_W, d_loss, d_grad, d_ws, s);
   GradWs w;
   grad_layout(p, d_ws, &w);
   const int n = p->n, M = p->steps, L = p->L, S = p->stride;

@@ -124,6 +124,14 @@ fq_status fq_launch_resident(const fq_plan* p, const void* coeff, const double* 
 
 // split-precision dense path (dense_split.cu)
 size_t fq_split_workspace(const fq_plan* p, int nc, void* base, void* out);
+// Gradient pieces shared by the FP64 and split adjoints (adjoint.cu): tau = sum of partials and
+// loss = 1 - |tau|^2 / N^2; grad_m = 2 Re sum_l w_l D_l from per-CTA partials of D_1..D_L.
+void fq_launch_loss(const double2* partial, int count, int n, double* loss, double2* tau, cudaStream_t s);
+void fq_launch_grad_reduce(const double2* partial, int ncta, int L, double* grad_m, cudaStream_t s);
+// floquet_grad on the tensor cores for BF16X3 / BF16X6 plans (adjoint_split.cu).
+size_t fq_grad_split_workspace(const fq_plan* p);
+fq_status fq_grad_split(fq_plan* p, const double* d_f, const void* d_W, double* d_loss, double* d_grad, void* d_ws,
+                        cudaStream_t s);
 fq_status fq_split_propagate(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
                              int transpose_out, void* ws, cudaStream_t s);
 

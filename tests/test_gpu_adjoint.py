@@ -92,3 +92,88 @@ def test_grad_argument_errors(fq):
     with pytest.raises(fq.FloquetError) as e:
         plan.grad(f, W, ws=torch.empty(256, dtype=torch.uint8, device="cuda"))
     assert e.value.status == fq.FQ_EINVAL
+
+
+def split_grad_tol(plan, h1, eps, loss):
+    """Bound on max_m |dL/df_m - exact| for a split-precision gradient, from the arithmetic:
+    the forward and adjoint chains each keep a state's 2-norm error below
+    eps_c = 2 M R eps + 4 sqrt(M L) eps (the forward split bound), the dot GEMM adds ~eps, and
+    every term |<bbar_l, E psi_{l-1}>| <= ||bbar_l||_F ||E||_2 ||psi_{l-1}||_F with
+    ||bbar_l||_F <= ||G||_F sum_j (j+1)|a_j|, ||G||_F = |tau| / N^{3/2} (unitary backward chain,
+    |tau| = N sqrt(1 - loss)), ||psi_{l-1}||_F <= sqrt(N); dL/df_m = 2 Re sum of L terms with
+    |w_l| <= 2."""
+    from scipy.special import jv
+    info = plan.info
+    M, L, R = info.steps, info.L, info.R
+    a = np.array([jv(0, R)] + [2 * jv(k, R) for k in range(1, L + 1)])
+    B = float(np.sum((np.arange(L + 1) + 1) * np.abs(a)))
+    e_norm = np.max(np.abs(np.linalg.eigvalsh(h1))) / info.delta_e
+    eps_c = 2 * M * R * eps + 4 * math.sqrt(M * L) * eps
+    term = math.sqrt(max(1.0 - loss, 0.0)) * B * e_norm
+    return 4 * L * (2 * eps_c + 2 * eps) * term
+
+
+@pytest.mark.parametrize("prec,eps", [("BF16X3", 2.0 ** -17), ("BF16X6", 2.0 ** -23)])
+@pytest.mark.parametrize("n,M,stride,tile", [(40, 20, 6, 64), (200, 12, 5, 128), (130, 9, 16, 64)])
+def test_split_grad_matches_oracle(fq, prec, eps, n, M, stride, tile):
+    """Tensor-core gradient (BF16 slices, FP32 accumulation) against the FP64 oracle: ragged
+    tiles (40, 130, 200 rows in 128-row tiles), ragged checkpoint segments and a single segment."""
+    h0, h1 = fi.goe(n, 1301), fi.goe(n, 1302)
+    w = fi.haar_unitary(n, 1303)
+    fm = 1.0 + 0.1 * fi.normal(1304, M)
+    T = 2 * math.pi
+    plan = fq.Plan.piecewise(h0, h1, fm, period=T, checkpoint_stride=stride, precision=getattr(fq, "FQ_" + prec),
+                             tile_n=tile)
+    loss, g = plan.grad(cuda(fm), cuda(w.astype(np.complex128)))
+    assert plan.check_status() == fq.FQ_OK
+    g = g.cpu().numpy()
+    ref_plan = o.plan_piecewise(h0, h1, T, fm)
+    ref_loss, ref_g = o.grad_piecewise(h0, h1, w, ref_plan, fm)
+    tol = split_grad_tol(plan, h1, eps, ref_loss)
+    err = np.max(np.abs(g - ref_g))
+    print(f"split grad {prec} n={n}: max err {err:.2e} (tol {tol:.2e}, max |g| {np.max(np.abs(ref_g)):.2e})")
+    assert err <= tol
+    assert abs(float(loss.item()) - ref_loss) <= 4 * (2 * M * plan.info.R * eps + 4 * math.sqrt(M * plan.info.L) * eps)
+
+
+def test_split_grad_config5_shape_vs_oracle(fq):
+    """The adjoint workload's shape (M = 256, checkpoints every 16) at N = 128, BF16X3."""
+    n, M = 128, 256
+    h0, h1 = fi.goe(n, 6), fi.goe(n, 7)
+    w = fi.haar_unitary(n, 8)
+    fm = 1.0 + 0.1 * fi.normal(9, M)
+    T = 2 * math.pi
+    plan = fq.Plan.piecewise(h0, h1, fm, period=T, checkpoint_stride=16, precision=fq.FQ_BF16X3)
+    loss, g = plan.grad(cuda(fm), cuda(w.astype(np.complex128)))
+    assert plan.check_status() == fq.FQ_OK
+    ref_plan = o.plan_piecewise(h0, h1, T, fm)
+    ref_loss, ref_g = o.grad_piecewise(h0, h1, w, ref_plan, fm)
+    err = np.max(np.abs(g.cpu().numpy() - ref_g))
+    tol = split_grad_tol(plan, h1, 2.0 ** -17, ref_loss)
+    print(f"split grad config-5 shape: max err {err:.2e} (tol {tol:.2e}, max |g| {np.max(np.abs(ref_g)):.2e})")
+    assert err <= tol
+
+
+def test_fidelity_loss_autograd(fq):
+    """fidelity_loss as a torch.autograd.Function: backward returns the library's adjoint scaled by
+    the cotangent (chain rule through 3 L + sum f), and <grad, v> matches a central difference of
+    the differentiable loss itself (FP64, <= 1e-6 relative)."""
+    import torch
+    n, M = 48, 24
+    h0, h1 = fi.goe(n, 1401), fi.goe(n, 1402)
+    w = fi.haar_unitary(n, 1403)
+    fm = 1.0 + 0.1 * fi.normal(1404, M)
+    v = fi.normal(1405, M)
+    plan = fq.Plan.piecewise(h0, h1, fm, period=2 * math.pi, checkpoint_stride=5)
+    W = cuda(w.astype(np.complex128))
+    f = cuda(fm).requires_grad_(True)
+    loss = fq.fidelity_loss(plan, f, W)
+    (3.0 * loss + f.sum()).backward()
+    _, g = plan.grad(cuda(fm), W)
+    assert torch.allclose(f.grad, 3.0 * g + 1.0, rtol=0, atol=1e-15)
+    d = 1e-5
+    with torch.no_grad():
+        lp = fq.fidelity_loss(plan, cuda(fm + d * v), W).item()
+        lm = fq.fidelity_loss(plan, cuda(fm - d * v), W).item()
+    gv = float(g.cpu().numpy() @ v)
+    assert abs((lp - lm) / (2 * d) - gv) <= 1e-6 * abs(gv)

@@ -57,7 +57,7 @@ def test_magnus6_split_bf16x6(fq):
     rp, oms = o.plan_dense6(m.h0, m.h1, m.drive, m.steps)
     ref = o.build_ut_dense6(rp, oms)
     eps = 2.0 ** -23
-    tol = 2 * m.steps * plan.info.R * eps + 4 * math.sqrt(m.steps * plan.info.L) * eps
+    tol = min(1e-5, 2 * m.steps * plan.info.R * eps + 4 * math.sqrt(m.steps * plan.info.L) * eps)  # split target
     assert np.max(np.abs(U - ref)) <= tol
 
 

@@ -1,7 +1,8 @@
 """Split-precision dense path (tcgen05 BF16 slices, FP32 accumulation) against the FP64 oracle.
 
-Tolerance: max |U - U_oracle| <= 2 M R eps + 4 sqrt(M L) eps, as for the FP32 tridiagonal path.
-eps is the relative error of one sliced product:
+Tolerance: max |U - U_oracle| <= min(1e-5, 2 M R eps + 4 sqrt(M L) eps).  1e-5 is the accuracy
+target for FP32-level split paths; the second term is the bound of the FP32 tridiagonal path with
+eps the relative error of one sliced product:
   * FQ_BF16X3 (2 slices, products hi*hi + hi*lo + lo*hi): a bf16 slice keeps 8 significant bits,
     so two slices represent x to 2^-18 relative, and the dropped lo*lo term is of the same
     size; eps = 2^-17.
@@ -21,9 +22,12 @@ pytestmark = pytest.mark.gpu
 EPS = {2: 2.0 ** -17, 3: 2.0 ** -23}
 
 
+SPLIT_TARGET = 1e-5
+
+
 def tol_split(M, L, R, ns):
     e = EPS[ns]
-    return 2.0 * M * R * e + 4.0 * math.sqrt(M * L) * e
+    return min(SPLIT_TARGET, 2.0 * M * R * e + 4.0 * math.sqrt(M * L) * e)
 
 
 @pytest.fixture(scope="module")
@@ -86,3 +90,30 @@ def test_split_goe4096_sampled(fq):
     err = np.max(np.abs(X - ref))
     print(f"GOE4096 BF16X6 8 steps: max err {err:.3e}")
     assert err <= tol_split(8, plan.info.L, plan.info.R, 3)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec,ns", [(2, 2), (3, 3)])
+def test_split_goe4096_full_build_sampled_columns(fq, prec, ns):
+    """The dense benchmark workload end to end (GOE N = 4096, M = 512, tile 128): the U_T the
+    library builds (one call, all 4096 states) against the oracle's propagation of 6 sampled
+    basis states through all 512 steps, and the unitarity defect over 64 columns (stated, and
+    checked against what the entry bound implies)."""
+    import torch
+    m = fi.config_goe4096()
+    plan = fq.Plan.dense(m.h0, m.h1, omega=m.drive.omega, f_ac=m.drive.f_ac, steps=m.steps, precision=prec)
+    U = plan.build_UT()
+    assert plan.check_status() == fq.FQ_OK
+    cols = [0, 1, 1000, 2047, 3001, 4095]
+    x0 = np.zeros((4096, len(cols)), complex)
+    x0[cols, np.arange(len(cols))] = 1.0
+    ref = o.propagate_dense(m.h0, m.h1, o.plan_for_drive_dense(m.h0, m.h1, m.drive, m.steps), x0)
+    got = U[:, cols].cpu().numpy()
+    err = np.max(np.abs(got - ref))
+    sample = torch.arange(0, 4096, 64, dtype=torch.int32, device="cuda")
+    mx, fro = fq.api.unitarity_defect(U, sample)
+    print(f"GOE4096 full build NS={ns}: max err {err:.3e} (tol {SPLIT_TARGET:.0e}); defect max {mx:.2e} fro {fro:.2e}")
+    assert err <= SPLIT_TARGET
+    # U = U_exact + D with |D_ij| <= e gives |(U^+U - 1)_cj| <= 2 sqrt(N) e + N e^2
+    e = SPLIT_TARGET
+    assert mx <= 2 * math.sqrt(4096) * e + 4096 * e * e
