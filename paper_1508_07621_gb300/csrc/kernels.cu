@@ -302,7 +302,7 @@ k_term_tri(const T* __restrict__ d, const T* __restrict__ er, const T* __restric
       sr = ar[q] + (T)t.coef * nr;
       si = ai[q] + (T)t.coef * ni;
     }
-    bad |= !((double)nr * nr + (double)ni * ni <= t.bound2);
+    bad |= !(nr * nr + ni * ni <= (T)t.bound2);  // in T: FP64 arithmetic runs far below the FP32 rate on sm_103
     if (t.last) {
       o_r[q] = (T)t.ph_re * sr - (T)t.ph_im * si;
       o_i[q] = (T)t.ph_re * si + (T)t.ph_im * sr;
