@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["dimer", "dimer-paper"], default="dimer",
+                    help="dimer: nb = 10^4, J = 1, U nb = 2, f = 1.5 cos 3t, M = 2000 (default); "
+                         "dimer-paper: the paper's parameters (U/2)(n1 - n2)^2, f = 2.7 + 2.5 cos 3t, M = 8000")
     ap.add_argument("--ncu-case", choices=["resident", "stream", "split"], default=None,
                     help="run one small capture case of a kernel twice and exit (for ncu --set full)")
     return ap.parse_args()
@@ -107,13 +110,15 @@ def job_throughput(local_seconds: float, steps: int, dist=None, device=None) -> 
 
 
 # ---------------------------------------------------------------------- oracle timing
-def oracle_sample(cols=24, steps=100):
-    """FP64 oracle on `cols` basis states over `steps` of the M = 2000 chain; returns
-    (U_T builds per second scaled to the full workload, seconds, description)."""
+def oracle_sample(cols=24, steps=100, d=None):
+    """FP64 oracle on `cols` basis states over `steps` of the workload's chain (default: the
+    M = 2000 dimer); returns (U_T builds per second scaled to the full workload, seconds,
+    description)."""
     import numpy as np
     import floquet_inputs as fi
     import oracle as o
-    d = fi.config_dimer(nb=NB, steps=STEPS)
+    if d is None:
+        d = fi.config_dimer(nb=NB, steps=STEPS)
     plan = o.plan_for_drive_tridiag(d.h0_diag, d.h0_off, d.h1_diag, d.drive, d.steps)
     idx = np.linspace(0, d.n - 1, cols).astype(int)
     x0 = np.zeros((d.n, cols), complex)
@@ -209,13 +214,15 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    # rank r scans its own drive amplitude; rank 0 runs exactly eps1 = 1.5
-    d = fi.config_dimer(nb=NB, steps=STEPS)
+    # rank r scans its own drive amplitude; rank 0 runs exactly the workload's amplitude
+    paper = args.workload == "dimer-paper"
+    d = fi.config_dimer_paper(nb=NB, steps=8000) if paper else fi.config_dimer(nb=NB, steps=STEPS)
     f_ac = rank_drive_amplitude(d.drive.f_ac, rank)
+    f_dc = d.drive.f_dc
     n = d.n
     stream = torch.cuda.current_stream()
-    plan = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=f_ac, steps=d.steps,
-                           precision=fq.FQ_FP32, kernel=fq.FQ_KERNEL_RESIDENT)
+    plan = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=f_ac, f_dc=f_dc,
+                           steps=d.steps, precision=fq.FQ_FP32, kernel=fq.FQ_KERNEL_RESIDENT)
     L = plan.info.L
     ws = fq.workspace(plan.workspace_size())
     U = torch.empty((n, n), dtype=torch.complex128, device="cuda")
@@ -253,8 +260,8 @@ def run_ours(args):
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        p2 = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=f_ac, steps=d.steps,
-                             precision=fq.FQ_FP32, kernel=fq.FQ_KERNEL_RESIDENT)
+        p2 = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=f_ac, f_dc=f_dc,
+                             steps=d.steps, precision=fq.FQ_FP32, kernel=fq.FQ_KERNEL_RESIDENT)
         fq.floquet_build_UT(p2.handle, U, ws, stream)
         host_u.copy_(U, non_blocking=True)
         torch.cuda.synchronize()
@@ -281,12 +288,15 @@ def run_ours(args):
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)"}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, dt, desc = oracle_sample()
+        v, dt, desc = oracle_sample(d=d)
         cpu = {"value": v, "unit": "U_T/s", "cores": 1, "kind": "oracle", "sample": desc}
-    line = {"metric": "U_T builds/sec (dim 10001 Bose-Hubbard dimer, M=2000)", "value": value, "unit": "U_T/s",
+    tag = ", paper parameters" if paper else ""
+    line = {"metric": f"U_T builds/sec (dim {n} Bose-Hubbard dimer{tag}, M={d.steps})", "value": value,
+            "unit": "U_T/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "bose-hubbard dimer nb=10000 (dim 10001), M=2000, L=%d, FP32 resident kernel" % L,
+            "config": {"workload": f"bose-hubbard dimer{tag} nb={n - 1} (dim {n}), M={d.steps}, L={L}, "
+                                   "FP32 resident kernel",
                        "dim": n, "steps_per_period": d.steps, "chebyshev_L": L, "R": plan.info.R,
                        "l2": "working set larger than L2 (2*Omega~ coefficients 240 MB, U_T 1.6 GB per step)",
                        "parallelism": f"weak: {world} independent drive amplitudes"},

@@ -14,7 +14,9 @@ Models (paper §4 and §6):
   * random-matrix model: H0, H1 independent GOE(N) members, Eq. 13 with f = cos-type drive;
     normalisation (G + G^T)/sqrt(2N), G_ij ~ N(0, 1) (semicircle radius 2);
   * Bose-Hubbard dimer, Eq. 18 family: H = -J(a1^+ a2 + h.c.) + (U/2) sum n_i(n_i - 1)
-    + f(t) (n1 - n2)/2 in the Fock basis |n, nb - n>, n = 0..nb (tridiagonal H0, diagonal H1).
+    + f(t) (n1 - n2)/2 in the Fock basis |n, nb - n>, n = 0..nb (tridiagonal H0, diagonal H1);
+    and the paper's own form, H = -v(a1^+ a2 + h.c.) + (U/2)(n1 - n2)^2 + f(t)(n2 - n1) with
+    f = 2.7 + 2.5 cos 3t.
 """
 from __future__ import annotations
 
@@ -140,6 +142,24 @@ def dimer_matrices(nb: int, J: float = 1.0, U: float | None = None):
     return h0_diag, h0_off, h1_diag
 
 
+def dimer_matrices_paper(nb: int, v: float = 1.0, U: float | None = None):
+    """The paper's dimer form (§4, its Eq. for H0 and H_mod) in the Fock basis |n, nb-n>:
+
+    H0 = -v (a1^+ a2 + a1 a2^+) + (U/2)(n1 - n2)^2, H1 = H_mod = n2 - n1.
+    U defaults to 2/nb (the interaction scaled with the boson number, U nb = 2).
+    Returns (h0_diag, h0_off, h1_diag), float64.
+    """
+    if U is None:
+        U = 2.0 / nb
+    n = np.arange(nb + 1, dtype=np.float64)
+    m = nb - n
+    h0_diag = 0.5 * U * (n - m) ** 2
+    k = np.arange(nb, dtype=np.float64)
+    h0_off = -v * np.sqrt((k + 1.0) * (nb - k))
+    h1_diag = m - n
+    return h0_diag, h0_off, h1_diag
+
+
 # ---------------------------------------------------------------- the five workloads
 def config_goe64() -> DenseModel:
     """GOE N=64, seeds 1 (H0) and 2 (H1); f = cos t, T = 2 pi, M = 200 (plain FP64)."""
@@ -150,6 +170,12 @@ def config_dimer(nb: int = 10000, steps: int = 2000, U: float | None = None) -> 
     """Dimer with nb bosons (dim nb+1): J = 1, U nb/J = 2, eps0 = 0, eps1 = 1.5, omega = 3."""
     d, o, h1 = dimer_matrices(nb, 1.0, U)
     return TridiagModel(d, o, h1, Drive(0.0, 1.5, 3.0), steps)
+
+
+def config_dimer_paper(nb: int = 10000, steps: int = 8000) -> TridiagModel:
+    """The paper's dimer parameters (§7): v = 1, U nb = 2, f(t) = 2.7 + 2.5 cos(3 t)."""
+    d, o, h1 = dimer_matrices_paper(nb)
+    return TridiagModel(d, o, h1, Drive(2.7, 2.5, 3.0), steps)
 
 
 def config_goe4096(n: int = 4096, steps: int = 512) -> DenseModel:

@@ -242,3 +242,27 @@ def test_workspace_errors(fq):
     assert e.value.status == fq.FQ_EINVAL
     with pytest.raises(fq.FloquetError):
         fq.floquet_propagate(plan.handle, U, U, d.n, 5, 3, small)
+
+
+@pytest.mark.parametrize("precision,kernel", [(1, 2), (1, 1), (0, 1)])
+def test_paper_dimer_parameters(fq, precision, kernel):
+    """The paper's own dimer (v = 1, U nb = 2, (U/2)(n1 - n2)^2, H_mod = n2 - n1, f = 2.7 +
+    2.5 cos 3t) at nb = 1000, M = 1000 (R = 11.1, L = 34): 4 states through steps 3..27 against
+    the oracle, on the resident and streaming FP32 kernels and the streaming FP64 kernel."""
+    d = fi.config_dimer_paper(nb=1000, steps=1000)
+    plan = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=d.drive.f_ac,
+                           f_dc=d.drive.f_dc, steps=d.steps, precision=precision, kernel=kernel)
+    assert plan.info.L == 34
+    n = d.n
+    x0 = np.zeros((4, n), complex)
+    x0[0, 0] = 1
+    x0[1, n // 2] = 1
+    x0[2, n - 1] = 1
+    x0[3] = fi.ginibre(n, 2101)[0]
+    x0[3] /= np.linalg.norm(x0[3])
+    X = to_np(plan.propagate(cuda_c128(x0), 3, 28))
+    assert plan.check_status() == fq.FQ_OK
+    refp = o.plan_for_drive_tridiag(d.h0_diag, d.h0_off, d.h1_diag, d.drive, d.steps)
+    ref = o.propagate_tridiag(d.h0_diag, d.h0_off, d.h1_diag, refp, x0.T, 3, 28).T
+    tol = 1e-10 if precision == 0 else tol_f32(25, plan.info.L, plan.info.R)
+    assert np.max(np.abs(X - ref)) <= tol

@@ -297,6 +297,22 @@ def test_dimer_u0_is_spin_representation():
     assert abs(np.trace(got) - char) < 1e-10
 
 
+def test_paper_dimer_u0_is_spin_representation():
+    """The paper's dimer form at U = 0: H0 = -v(a1^+ a2 + h.c.) = -2v J_x and H_mod = n2 - n1 =
+    -2 J_z, the nb-boson image of h0 = -v sigma_x, h1 = -sigma_z (i[h0, h1] = 2v sigma_y), with
+    the paper's dc + ac drive; U_T = D(u) for the 2x2 chain of exact exponentials."""
+    nb, v = 20, 1.0
+    d, off, h1d = fi.dimer_matrices_paper(nb, v, U=0.0)
+    drv = fi.Drive(2.7, 2.5, 3.0)
+    M = 400
+    plan = o.plan_for_drive_tridiag(d, off, h1d, drv, M)
+    got = o.build_ut_tridiag(d, off, h1d, plan)
+    u = np.eye(2, dtype=complex)
+    for m in range(M):
+        u = _su2_exp(0.0, -v * plan.a[m], 2 * v * plan.c[m], -plan.b[m]) @ u
+    assert np.max(np.abs(got - _spin_rep(u, nb))) < 1e-10
+
+
 def test_tridiagonal_form_matches_dense_form():
     """The tridiagonal operator path (diag/lower, commutator by formula) agrees with the
     dense path on the same dimer written as full matrices (transposition/conjugation pin)."""
