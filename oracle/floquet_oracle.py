@@ -31,6 +31,12 @@ Readings where the paper is silent or garbled (each is also listed in the design
       (or of max |f|) and frozen, so the bounds do not follow f.
   R12 6th order (Eq. 14 in full): alphas as 3-point Gauss-Legendre moments (see magnus6_omega);
       the literal midpoint-derivative alphas of Eq. 15 give only 4th order.
+  R13 period averages (Eq. 17): composite Simpson over the M + 1 step boundaries (trapezoid
+      for odd M).
+  R14 overlap phase error (Eq. 20): the eigenvector phases and the quasienergy phase are left
+      open, so Sigma_mu = |1 - e^{i eps~_mu T} <phi~_mu(0)| U_T |phi~_mu(0)>| with (phi~_mu,
+      eps~_mu) the Floquet states of the step-h/2 chain and U_T the step-h chain: the overlap
+      of one coarse period with the exact evolution e^{-i eps~ T} phi~ of the finer state.
 """
 from __future__ import annotations
 
@@ -362,6 +368,24 @@ def quasienergies(u: np.ndarray, period: float) -> np.ndarray:
     theta = -np.angle(lam)
     theta = np.where(theta >= math.pi, theta - 2.0 * math.pi, theta)
     return np.sort(theta / period)
+
+
+def overlap_phase_error(u_coarse: np.ndarray, u_fine: np.ndarray, period: float):
+    """Eq. 20 with reading R14.  Returns (eps~ ascending, Sigma_mu in that order); the Floquet
+    states of u_fine come from LAPACK zgeev, normalised."""
+    lam, v = np.linalg.eig(u_fine)
+    theta = -np.angle(lam)
+    theta = np.where(theta >= math.pi, theta - 2.0 * math.pi, theta)
+    order = np.argsort(theta)
+    theta = theta[order]
+    v = v[:, order]
+    v = v / np.linalg.norm(v, axis=0, keepdims=True)
+    sigma = np.empty(len(theta))
+    for mu in range(len(theta)):
+        phi = v[:, mu]
+        overlap = np.vdot(phi, u_coarse @ phi)
+        sigma[mu] = abs(1.0 - np.exp(1j * theta[mu]) * overlap)
+    return theta / period, sigma
 
 
 def simpson_weights(steps: int, h: float) -> np.ndarray:

@@ -5,4 +5,5 @@ csrc/); this package is its ctypes binding plus small conveniences that allocate
 memory through torch.  Importing it fails if the library has not been built.
 """
 from ._binding import *  # noqa: F401,F403
-from .api import Plan, fidelity_loss, floquet_states, unitarity_defect, workspace  # noqa: F401
+from .api import (Plan, fidelity_loss, floquet_analysis, floquet_states, overlap_phase_error,  # noqa: F401
+                  unitarity_defect, workspace)

@@ -170,3 +170,34 @@ def floquet_states(U, period):
     order = np.argsort(theta)
     v = v[:, order] / np.linalg.norm(v[:, order], axis=0, keepdims=True)
     return theta[order] / period, torch.from_numpy(np.ascontiguousarray(v.T)).to(U.device)
+
+
+def floquet_analysis(plan, U=None):
+    """The paper's post-processing (§3 last paragraph, §7): Floquet states of U_T (host zgeev),
+    their period-averaged energies <H(t)>_T from a second propagation round (Eq. 17, on the
+    library), and the states sorted by that energy.  Returns (avg_energy, eps, states), sorted
+    ascending in avg_energy; states are rows (complex128, device)."""
+    import numpy as np
+    import torch
+    if U is None:
+        U = plan.build_UT()
+    eps, states = floquet_states(U, plan.info.steps * plan.info.h)
+    avg = plan.average_observable(states, 1.0, 0.0, 1.0).cpu().numpy()
+    order = np.argsort(avg, kind="stable")
+    idx = torch.from_numpy(order).to(states.device)
+    return avg[order], eps[order], states.index_select(0, idx)
+
+
+def overlap_phase_error(plan, U_fine):
+    """Overlap phase error of Eq. 20 for the chain of `plan` (step h): with (phi~, eps~) the
+    Floquet states of U_fine, the U_T of the same drive at step h/2, Sigma_mu =
+    |1 - e^{i eps~_mu T} <phi~_mu| U_T |phi~_mu>|.  U_T phi~ comes from propagating the states
+    through the plan's chain on the library; the eigenvectors and the M overlaps are host FP64.
+    Returns (eps~ ascending, Sigma in that order)."""
+    import numpy as np
+    T = plan.info.steps * plan.info.h
+    eps, states = floquet_states(U_fine, T)
+    moved = plan.propagate(states).cpu().numpy()
+    phi = states.cpu().numpy()
+    overlap = np.einsum("mi,mi->m", phi.conj(), moved)
+    return eps, np.abs(1.0 - np.exp(1j * eps * T) * overlap)

@@ -88,3 +88,45 @@ def test_dimer_average_energy(fq, precision, kernel):
     assert np.max(np.abs(avg - ref)) <= tol
     order = np.argsort(avg)      # the paper sorts Floquet states by mean energy
     assert len(set(order.tolist())) == d.n
+
+
+def test_floquet_analysis_sorted_by_average_energy(fq):
+    """floquet_analysis: U_T, Floquet states, <H(t)>_T by the second round, sorted ascending;
+    energies match the oracle's averages of the same states and the order is by energy."""
+    n, M = 32, 50
+    h0, h1 = fi.goe(n, 1801), fi.goe(n, 1802)
+    drv = fi.Drive(0.3, 1.0, 1.4, 0.2)
+    plan = fq.Plan.dense(h0, h1, omega=drv.omega, f_ac=drv.f_ac, f_dc=drv.f_dc, phi0=drv.phi0, steps=M)
+    avg, eps, states = fq.floquet_analysis(plan)
+    assert np.all(np.diff(avg) >= 0)
+    p = o.plan_for_drive_dense(h0, h1, drv, M)
+    k = o.commutator_dense(h0, h1)
+    step = lambda m, x: o.chebyshev_step(lambda v: o.omega_tilde_dense(h0, h1, k, p, m) @ v, x, p.coeffs, p.phase)
+    ref = o.average_observable(step, o.expect_dense(h0, h1, 1.0, 0.0, 1.0, drv), states.cpu().numpy().T, drv, M)
+    assert np.max(np.abs(avg - ref)) <= 1e-10
+    # each row is a Floquet state: U_T phi = e^{-i eps T} phi
+    U = plan.build_UT().cpu().numpy()
+    phi = states.cpu().numpy()
+    res = U @ phi.T - phi.T * np.exp(-1j * eps * drv.period)[None, :]
+    assert np.max(np.abs(res)) < 1e-9
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_overlap_phase_error_matches_oracle(fq, precision):
+    """Eq. 20 on the library (coarse chain applied to the fine Floquet states by
+    floquet_propagate) against the oracle's Sigma from its own U_T's.  FP64 to 1e-9; the BF16X3
+    coarse chain to sqrt(N) 1e-5: the split target bounds U_T's entries by 1e-5, hence
+    ||dU phi||_2 <= sqrt(N) 1e-5 for a unit phi, and |dSigma| <= ||dU phi||_2."""
+    n, M = 24, 40
+    h0, h1 = fi.goe(n, 1901), fi.goe(n, 1902)
+    drv = fi.Drive(0.2, 1.2, 1.3, 0.4)
+    coarse = fq.Plan.dense(h0, h1, omega=drv.omega, f_ac=drv.f_ac, f_dc=drv.f_dc, phi0=drv.phi0, steps=M,
+                           precision=precision)
+    fine = fq.Plan.dense(h0, h1, omega=drv.omega, f_ac=drv.f_ac, f_dc=drv.f_dc, phi0=drv.phi0, steps=2 * M)
+    eps, sig = fq.overlap_phase_error(coarse, fine.build_UT())
+    uc = o.build_ut_dense(h0, h1, o.plan_for_drive_dense(h0, h1, drv, M))
+    uf = o.build_ut_dense(h0, h1, o.plan_for_drive_dense(h0, h1, drv, 2 * M))
+    ref_eps, ref_sig = o.overlap_phase_error(uc, uf, drv.period)
+    assert np.max(np.abs(eps - ref_eps)) < 1e-10
+    assert np.max(np.abs(sig - ref_sig)) <= (1e-9 if precision == 0 else math.sqrt(n) * 1e-5)
+    assert np.max(ref_sig) > 1e-7   # the test resolves the coarse chain's error

@@ -412,3 +412,28 @@ def test_average_h1_is_quasienergy_slope():
     avg = o.average_observable(step, o.expect_dense(h0, h1, 0.0, 1.0, 0.0, drv), V / np.linalg.norm(V, axis=0),
                                drv, M)
     assert np.max(np.abs(slope - avg)) < 1e-6
+
+
+# -------------------------------------------------------------------- overlap phase error (Eq. 20)
+def test_overlap_phase_error_undriven_is_truncation_level():
+    """With f = const the Magnus exponent is exact and both chains equal exp(-i H T) up to the
+    Chebyshev truncation, so Sigma_mu vanishes to rounding; a wrong sign of the quasienergy
+    phase would give |1 - e^{2 i eps T}| = O(1)."""
+    h0, h1 = fi.goe(12, 1601), fi.goe(12, 1602)
+    drv = fi.Drive(0.4, 0.0, 1.0)
+    uc = o.build_ut_dense(h0, h1, o.plan_for_drive_dense(h0, h1, drv, 10))
+    uf = o.build_ut_dense(h0, h1, o.plan_for_drive_dense(h0, h1, drv, 20))
+    eps, sig = o.overlap_phase_error(uc, uf, drv.period)
+    assert np.max(sig) < 1e-12
+    assert np.all(np.diff(eps) >= 0)
+
+
+def test_overlap_phase_error_decays_at_fourth_order():
+    """Driven GOE: the one-period error of the 4th-order chain is O(h^4), so Sigma(M) against
+    the 2M chain drops by about 2^4 per doubling of M (finer reference error included)."""
+    h0, h1 = fi.goe(10, 1701), fi.goe(10, 1702)
+    drv = fi.Drive(0.2, 1.2, 1.3, 0.4)
+    u = {M: o.build_ut_dense(h0, h1, o.plan_for_drive_dense(h0, h1, drv, M)) for M in (16, 32, 64, 128)}
+    s = [np.max(o.overlap_phase_error(u[M], u[2 * M], drv.period)[1]) for M in (16, 32, 64)]
+    for a, b in zip(s, s[1:]):
+        assert 12.0 < a / b < 20.0, s
