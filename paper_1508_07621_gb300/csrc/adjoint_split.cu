@@ -200,16 +200,34 @@ fq_status gemm_cfg(const GemmCtx& c, const __nv_bfloat16* left, const __nv_bfloa
     if ((st = make_map(&maps.a[q], left + q * c.astride, c.ncp, c.kp, BM, BKE)) != FQ_OK) return st;
     if ((st = make_map(&maps.os[q], right + q * c.bstride, c.np, c.np, BN, BKE)) != FQ_OK) return st;
   }
+  // the forward and adjoint terms run persistently (epilogue overlapped with the next tile's
+  // MMAs); the gradient dot keeps one tile per CTA for its per-CTA partial sums
+  constexpr bool persist = EPI != EPI_DOT;
   static bool attr = false;
+  static int sms = 0;
   if (!attr) {
-    cudaError_t r = cudaFuncSetAttribute(k_split_term<NS, BN, BKE, EPI, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
-    if (r != cudaSuccess) return fq_cuda_fail(r, "split gradient kernel smem attribute");
+    cudaError_t r;
+    if constexpr (persist)
+      r = cudaFuncSetAttribute(k_split_persist<NS, BN, BKE, EPI, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)Cfg::SMEM);
+    else
+      r = cudaFuncSetAttribute(k_split_term<NS, BN, BKE, EPI, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)Cfg::SMEM);
+    if (r == cudaSuccess) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (r != cudaSuccess) return fq_cuda_fail(r, "split gradient kernel attributes");
     attr = true;
   }
-  const int tiles_i = c.np / BN, tiles_j = c.ncp / BM;
-  k_split_term<NS, BN, BKE, EPI, false><<<tiles_i * tiles_j, NTHREADS, Cfg::SMEM, s>>>(maps, c.np / BKE, tiles_j,
-                                                                                      tiles_i, e);
+  const int tiles_i = c.np / BN, tiles_j = c.ncp / BM, nk = c.np / BKE;
+  if constexpr (persist)
+    k_split_persist<NS, BN, BKE, EPI, false><<<std::min(tiles_i * tiles_j, sms), PTHREADS, Cfg::SMEM, s>>>(
+        maps, nk, tiles_j, tiles_i, e);
+  else
+    k_split_term<NS, BN, BKE, EPI, false><<<tiles_i * tiles_j, NTHREADS, Cfg::SMEM, s>>>(maps, nk, tiles_j, tiles_i,
+                                                                                        e);
   return FQ_OK;
 }
 

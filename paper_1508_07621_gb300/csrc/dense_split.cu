@@ -149,10 +149,16 @@ static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int 
       if ((st = make_map(&maps[v].oa[q], w.oa + q * w.bstride, w.np, w.np, BN, BKE)) != FQ_OK) return st;
     }
   static bool attr = false;
+  static int sms = 0;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_split_term<NS, BN, BKE, EPI_FWD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg::SMEM);
-    if (e != cudaSuccess) return fq_cuda_fail(e, "split kernel smem attribute");
+    cudaError_t e = cudaFuncSetAttribute(k_split_persist<NS, BN, BKE, EPI_FWD, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    if (e == cudaSuccess) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (e != cudaSuccess) return fq_cuda_fail(e, "split kernel attributes");
     attr = true;
   }
   // left-operand slices are only ever written for rows < nc and columns < n: zero the padding
@@ -161,7 +167,7 @@ static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int 
   k_split_init<NS><<<grid_1d((size_t)nc * w.kp), 256, 0, s>>>(identity ? nullptr : (const double2*)x0, n, nc, w.ldm,
                                                                w.np, w.kp, w.m[0][0], w.m[0][1], w.a[0], w.astride);
   const int tiles_i = w.np / BN, tiles_j = (nc + BM - 1) / BM;
-  const dim3 grid(tiles_i * tiles_j);
+  const dim3 grid(std::min(tiles_i * tiles_j, sms));  // persistent: at most one CTA per SM
   const int nk = w.np / BKE;
   int xb = 0, av = 0;  // FP32 master holding psi_0 / X, left-operand buffer holding its slices
   fq_term t{};
@@ -211,7 +217,7 @@ static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int 
       e.slice_out = w.a[av ^ 1];
       e.slice_stride = w.astride;
       e.t = t;
-      k_split_term<NS, BN, BKE, EPI_FWD, true><<<grid, NTHREADS, Cfg::SMEM, s>>>(maps[av], nk, tiles_j, tiles_i, e);
+      k_split_persist<NS, BN, BKE, EPI_FWD, true><<<grid, PTHREADS, Cfg::SMEM, s>>>(maps[av], nk, tiles_j, tiles_i, e);
       av ^= 1;
       if (t.last) {
         xb = out;

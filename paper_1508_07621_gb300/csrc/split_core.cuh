@@ -98,6 +98,10 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -269,6 +273,86 @@ __device__ __forceinline__ void store_slices(const SplitEpi& e, int j, int ib, i
   }
 }
 
+// Epilogue of one 16-column chunk of row j: Y entries yr, yi of columns ib .. ib + 15 (cnt valid).
+template <int NS, int EPI>
+__device__ __forceinline__ void epi_chunk(const SplitEpi& e, const float (&yr)[16], const float (&yi)[16], int j,
+                                          int ib, bool& bad, double& dsr, double& dsi) {
+  const float c0f = (float)e.t.coef0, cf = (float)e.t.coef, pr_ = (float)e.t.ph_re, pi_ = (float)e.t.ph_im;
+  const float b2 = (float)e.t.bound2;
+  const int cnt = min(16, e.n - ib);
+  const size_t idx = (size_t)j * e.ldm + ib;
+  if (EPI == EPI_DOT) {
+    float br[16], bi[16];
+    load16(e.cur_re, idx, cnt, br);
+    load16(e.cur_im, idx, cnt, bi);
+    float sr = 0.f, si = 0.f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {  // conj(b) Y; entries beyond cnt are zero in b
+      sr = fmaf(br[q], yr[q], fmaf(bi[q], yi[q], sr));
+      si = fmaf(br[q], yi[q], fmaf(-bi[q], yr[q], si));
+    }
+    dsr += (double)sr;
+    dsi += (double)si;
+    return;
+  }
+  float o_r[16], o_i[16];
+  if (EPI == EPI_ADJ) {  // out = cpa g + i cw Y + b2
+    float g_r[16], g_i[16], p_r[16], p_i[16];
+    load16(e.cur_re, idx, cnt, g_r);
+    load16(e.cur_im, idx, cnt, g_i);
+    load16(e.prev_re, idx, cnt, p_r);
+    load16(e.prev_im, idx, cnt, p_i);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      o_r[q] = e.cpa_re * g_r[q] - e.cpa_im * g_i[q] - e.cw * yi[q] + p_r[q];
+      o_i[q] = e.cpa_re * g_i[q] + e.cpa_im * g_r[q] + e.cw * yr[q] + p_i[q];
+      bad |= q < cnt && !(o_r[q] * o_r[q] + o_i[q] * o_i[q] <= b2);
+    }
+    store16(e.out_re, idx, cnt, o_r);
+    store16(e.out_im, idx, cnt, o_i);
+    store_slices<NS>(e, j, ib, cnt, o_r, o_i);
+    return;
+  }
+  // EPI_FWD
+  float a_r[16], a_i[16], p_r[16], p_i[16];
+  load16(e.t.first ? e.cur_re : e.prev_re, idx, cnt, p_r);
+  load16(e.t.first ? e.cur_im : e.prev_im, idx, cnt, p_i);
+  load16(e.t.first ? nullptr : e.acc_re, idx, cnt, a_r);
+  load16(e.t.first ? nullptr : e.acc_im, idx, cnt, a_i);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    float nr, ni, sr, si;
+    if (e.t.first) {  // psi_1 = -i Y, acc = a_0 psi_0 + a_1 psi_1
+      nr = yi[q];
+      ni = -yr[q];
+      sr = c0f * p_r[q] + cf * nr;
+      si = c0f * p_i[q] + cf * ni;
+    } else {  // psi_{l+1} = -2i Y + psi_{l-1}, acc += a_{l+1} psi_{l+1}
+      nr = 2.f * yi[q] + p_r[q];
+      ni = -2.f * yr[q] + p_i[q];
+      sr = a_r[q] + cf * nr;
+      si = a_i[q] + cf * ni;
+    }
+    bad |= q < cnt && !(nr * nr + ni * ni <= b2);
+    if (e.t.last) {  // X = e^{-i beta h} (acc + a_L psi_L)
+      o_r[q] = pr_ * sr - pi_ * si;
+      o_i[q] = pr_ * si + pi_ * sr;
+    } else {
+      o_r[q] = nr;
+      o_i[q] = ni;
+    }
+    a_r[q] = sr;
+    a_i[q] = si;
+  }
+  store16(e.out_re, idx, cnt, o_r);
+  store16(e.out_im, idx, cnt, o_i);
+  if (!e.t.last) {
+    store16(e.acc_re, idx, cnt, a_r);
+    store16(e.acc_im, idx, cnt, a_i);
+  }
+  store_slices<NS>(e, j, ib, cnt, o_r, o_i);
+}
+
 // One split GEMM on a 128-row x BN-column tile of Y = left . right^T:
 //   HAS_A:  Yr = Psi_r.S - Psi_i.A,  Yi = Psi_r.A + Psi_i.S   (right = S + i A)
 //   !HAS_A: Yr = Psi_r.S,            Yi = Psi_i.S             (right = S real)
@@ -405,8 +489,6 @@ k_split_term(const __grid_constant__ SplitMaps maps, int nk, int tiles_j, int ti
   const bool run = got && !*(volatile int*)abort_flag;
   const int j = j0 + warp * 32 + lane;
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-  const float c0f = (float)e.t.coef0, cf = (float)e.t.coef, pr_ = (float)e.t.ph_re, pi_ = (float)e.t.ph_im;
-  const float b2 = (float)e.t.bound2;
   bool bad = false;
   double dsr = 0.0, dsi = 0.0;  // DOT partial of this thread
 #pragma unroll 1
@@ -417,78 +499,7 @@ k_split_term(const __grid_constant__ SplitMaps maps, int nk, int tiles_j, int ti
     tmem_wait_ld();
     const int ib = i0 + c0;
     if (!run || j >= e.nc || ib >= e.n) continue;
-    const int cnt = min(16, e.n - ib);
-    const size_t idx = (size_t)j * e.ldm + ib;
-    if (EPI == EPI_DOT) {
-      float br[16], bi[16];
-      load16(e.cur_re, idx, cnt, br);
-      load16(e.cur_im, idx, cnt, bi);
-      float sr = 0.f, si = 0.f;
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {  // conj(b) Y; entries beyond cnt are zero in b
-        sr = fmaf(br[q], yr[q], fmaf(bi[q], yi[q], sr));
-        si = fmaf(br[q], yi[q], fmaf(-bi[q], yr[q], si));
-      }
-      dsr += (double)sr;
-      dsi += (double)si;
-      continue;
-    }
-    float o_r[16], o_i[16];
-    if (EPI == EPI_ADJ) {  // out = cpa g + i cw Y + b2
-      float g_r[16], g_i[16], p_r[16], p_i[16];
-      load16(e.cur_re, idx, cnt, g_r);
-      load16(e.cur_im, idx, cnt, g_i);
-      load16(e.prev_re, idx, cnt, p_r);
-      load16(e.prev_im, idx, cnt, p_i);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        o_r[q] = e.cpa_re * g_r[q] - e.cpa_im * g_i[q] - e.cw * yi[q] + p_r[q];
-        o_i[q] = e.cpa_re * g_i[q] + e.cpa_im * g_r[q] + e.cw * yr[q] + p_i[q];
-        bad |= q < cnt && !(o_r[q] * o_r[q] + o_i[q] * o_i[q] <= b2);
-      }
-      store16(e.out_re, idx, cnt, o_r);
-      store16(e.out_im, idx, cnt, o_i);
-      store_slices<NS>(e, j, ib, cnt, o_r, o_i);
-      continue;
-    }
-    // EPI_FWD
-    float a_r[16], a_i[16], p_r[16], p_i[16];
-    load16(e.t.first ? e.cur_re : e.prev_re, idx, cnt, p_r);
-    load16(e.t.first ? e.cur_im : e.prev_im, idx, cnt, p_i);
-    load16(e.t.first ? nullptr : e.acc_re, idx, cnt, a_r);
-    load16(e.t.first ? nullptr : e.acc_im, idx, cnt, a_i);
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      float nr, ni, sr, si;
-      if (e.t.first) {  // psi_1 = -i Y, acc = a_0 psi_0 + a_1 psi_1
-        nr = yi[q];
-        ni = -yr[q];
-        sr = c0f * p_r[q] + cf * nr;
-        si = c0f * p_i[q] + cf * ni;
-      } else {  // psi_{l+1} = -2i Y + psi_{l-1}, acc += a_{l+1} psi_{l+1}
-        nr = 2.f * yi[q] + p_r[q];
-        ni = -2.f * yr[q] + p_i[q];
-        sr = a_r[q] + cf * nr;
-        si = a_i[q] + cf * ni;
-      }
-      bad |= q < cnt && !(nr * nr + ni * ni <= b2);
-      if (e.t.last) {  // X = e^{-i beta h} (acc + a_L psi_L)
-        o_r[q] = pr_ * sr - pi_ * si;
-        o_i[q] = pr_ * si + pi_ * sr;
-      } else {
-        o_r[q] = nr;
-        o_i[q] = ni;
-      }
-      a_r[q] = sr;
-      a_i[q] = si;
-    }
-    store16(e.out_re, idx, cnt, o_r);
-    store16(e.out_im, idx, cnt, o_i);
-    if (!e.t.last) {
-      store16(e.acc_re, idx, cnt, a_r);
-      store16(e.acc_im, idx, cnt, a_i);
-    }
-    store_slices<NS>(e, j, ib, cnt, o_r, o_i);
+    epi_chunk<NS, EPI>(e, yr, yi, j, ib, bad, dsr, dsi);
   }
   if (bad) atomicOr(e.t.status, FQ_BIT_BOUND);
   if (EPI == EPI_DOT) {
@@ -509,6 +520,203 @@ k_split_term(const __grid_constant__ SplitMaps maps, int nk, int tiles_j, int ti
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)Cfg::TMEM_COLS)
                  : "memory");
+  }
+}
+
+// Persistent form of k_split_term for the forward and adjoint epilogues: one CTA per SM walks
+// the tiles blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 0 (one thread) streams TMA stages,
+// warp 1 (one thread) issues the MMAs of tile i into tensor-memory buffer i & 1, and warps 2-5
+// run the epilogue of tile i from its buffer while tile i + 1 accumulates in the other one.
+// Buffers are handed over by mbarriers (tfull: MMAs of a tile done; tempty: its accumulators
+// read).  Every wait is bounded as in k_split_term.
+constexpr int PTHREADS = 192;
+
+template <int NS, int BN, int BKE, int EPI, bool HAS_A>
+__global__ void __launch_bounds__(PTHREADS, 1)
+k_split_persist(const __grid_constant__ SplitMaps maps, int nk, int tiles_j, int tiles_i, SplitEpi e) {
+  static_assert(EPI != EPI_DOT, "the gradient dot keeps the one-tile kernel (per-CTA partials)");
+  using Cfg = SplitCfg<NS, BN, BKE, HAS_A>;
+  constexpr int STAGES = Cfg::STAGES;
+  constexpr uint32_t BUF_COLS = 2 * BN;             // Yr and Yi of one tile
+  constexpr uint32_t TMEM_COLS = 2 * BUF_COLS;      // two buffers (<= 512)
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * Cfg::STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t tfull0 = smem_u32(bars + 2 * STAGES), tempty0 = smem_u32(bars + 2 * STAGES + 2);
+  const uint32_t done = smem_u32(bars + 2 * STAGES + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = tiles_i * tiles_j;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, 4);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto coords = [&](int t, int& j0, int& i0) {
+    const int per = RASTER_GROUP * tiles_i, g = t / per;
+    const int gj = min(RASTER_GROUP, tiles_j - g * RASTER_GROUP), r = t - g * per;
+    j0 = (g * RASTER_GROUP + r % gj) * BM;
+    i0 = (r / gj) * BN;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------- TMA producer
+      int g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int j0, i0;
+        coords(t, j0, i0);
+        for (int kb = 0; kb < nk; ++kb) {
+          const int s = g % STAGES;
+          if (g >= STAGES && !(ok = mbar_wait(empty0 + 8 * s, ((g / STAGES) - 1) & 1))) break;
+          if (*(volatile int*)abort_flag) {
+            ok = false;
+            break;
+          }
+          const uint32_t st = base + s * Cfg::STAGE_BYTES;
+          const uint32_t bar = full0 + 8 * s;
+          mbar_expect_tx(bar, Cfg::STAGE_BYTES);
+          const int kx = kb * BKE;
+#pragma unroll
+          for (int q = 0; q < NS; ++q) {
+            tma_load_2d(st + q * Cfg::A_BYTES, &maps.a[q], bar, kx, j0);
+            tma_load_2d(st + (NS + q) * Cfg::A_BYTES, &maps.a[q], bar, e.np + kx, j0);
+            tma_load_2d(st + 2 * NS * Cfg::A_BYTES + q * Cfg::B_BYTES, &maps.os[q], bar, kx, i0);
+            if (HAS_A)
+              tma_load_2d(st + 2 * NS * Cfg::A_BYTES + (NS + q) * Cfg::B_BYTES, &maps.oa[q], bar, kx, i0);
+          }
+          ++g;
+        }
+      }
+      if (!ok) {
+        atomicExch(abort_flag, 1);
+        atomicOr(e.t.status, FQ_BIT_TIMEOUT);
+      }
+      // every copy issued must have landed before the CTA may exit
+      for (int q = max(0, g - STAGES); q < g; ++q) mbar_wait(full0 + 8 * (q % STAGES), (q / STAGES) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------- MMA issuer
+      constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                 ((uint32_t)(BM >> 4) << 24);
+      constexpr uint32_t idesc_neg = idesc | (1u << 13);
+      int g = 0, i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+        const int b = i & 1;
+        if (i >= 2 && !(ok = mbar_wait(tempty0 + 8 * b, ((i >> 1) - 1) & 1))) break;
+        const uint32_t acc = tmem + (uint32_t)b * BUF_COLS;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % STAGES;
+          ok = mbar_wait(full0 + 8 * s, (g / STAGES) & 1);
+          if (!ok || *(volatile int*)abort_flag) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = base + s * Cfg::STAGE_BYTES;
+#pragma unroll
+          for (int p = 0; p < Pairs<NS>::N; ++p) {
+            const uint32_t pr = st + Pairs<NS>::a(p) * Cfg::A_BYTES;
+            const uint32_t pi = st + (NS + Pairs<NS>::a(p)) * Cfg::A_BYTES;
+            const uint32_t os = st + 2 * NS * Cfg::A_BYTES + Pairs<NS>::b(p) * Cfg::B_BYTES;
+            const uint32_t oa = st + 2 * NS * Cfg::A_BYTES + (NS + Pairs<NS>::b(p)) * Cfg::B_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BKE / 16; ++kk) {
+              const uint32_t first = (kb == 0 && p == 0 && kk == 0) ? 0u : 1u;
+              const uint64_t dpr = smem_desc<Cfg::ROWB>(pr + 32 * kk), dpi = smem_desc<Cfg::ROWB>(pi + 32 * kk);
+              const uint64_t dos = smem_desc<Cfg::ROWB>(os + 32 * kk);
+              if (HAS_A) {
+                const uint64_t doa = smem_desc<Cfg::ROWB>(oa + 32 * kk);
+                mma_bf16(acc, dpr, dos, idesc, first);
+                mma_bf16(acc, dpi, doa, idesc_neg, 1u);
+                mma_bf16(acc + BN, dpr, doa, idesc, first);
+                mma_bf16(acc + BN, dpi, dos, idesc, 1u);
+              } else {
+                mma_bf16(acc, dpr, dos, idesc, first);
+                mma_bf16(acc + BN, dpi, dos, idesc, first);
+              }
+            }
+          }
+          mma_commit(empty0 + 8 * s);
+        }
+        if (!ok) break;
+        mma_commit(tfull0 + 8 * b);  // this tile's accumulators are complete once its MMAs are
+      }
+      if (!ok) {
+        atomicExch(abort_flag, 1);
+        atomicOr(e.t.status, FQ_BIT_TIMEOUT);
+      }
+      mma_commit(done);  // every MMA issued above has completed once this arrives
+      mbar_wait(done, 0);
+    }
+  } else {  // ---------------- epilogue warps 2-5: tensor-memory lane quarter warp % 4
+    const int quarter = warp & 3;
+    bool bad = false, ok = true;
+    double dsr = 0.0, dsi = 0.0;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int b = i & 1;
+      bool go = mbar_wait(tfull0 + 8 * b, (i >> 1) & 1);
+      tc_fence_after();
+      go = __all_sync(0xffffffffu, go && !*(volatile int*)abort_flag);  // warp-uniform: tcgen05.ld is .aligned
+      if (!go) {
+        ok = false;
+        break;
+      }
+      int j0, i0;
+      coords(t, j0, i0);
+      const int j = j0 + quarter * 32 + lane;
+      const uint32_t trow = tmem + (uint32_t)b * BUF_COLS + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float yr[16], yi[16];
+        tmem_ld16(trow + c0, yr);
+        tmem_ld16(trow + BN + c0, yi);
+        tmem_wait_ld();
+        const int ib = i0 + c0;
+        if (j >= e.nc || ib >= e.n) continue;
+        epi_chunk<NS, EPI>(e, yr, yi, j, ib, bad, dsr, dsi);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+    }
+    if (!ok) {
+      atomicExch(abort_flag, 1);
+      atomicOr(e.t.status, FQ_BIT_TIMEOUT);
+    }
+    if (bad) atomicOr(e.t.status, FQ_BIT_BOUND);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
 }
 
