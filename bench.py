@@ -15,6 +15,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -124,11 +125,25 @@ def oracle_sample(cols=24, steps=100, d=None):
     x0 = np.zeros((d.n, cols), complex)
     x0[idx, np.arange(cols)] = 1.0
     t0 = time.perf_counter()
-    o.propagate_tridiag(d.h0_diag, d.h0_off, d.h1_diag, plan, x0, 0, steps)
+    x = o.propagate_tridiag(d.h0_diag, d.h0_off, d.h1_diag, plan, x0, 0, steps)
     dt = time.perf_counter() - t0
     frac = (cols / d.n) * (steps / d.steps)
     desc = f"{cols} of {d.n} basis states over {steps} of {d.steps} steps (FP64 numpy oracle, 1 thread)"
-    return frac / dt, dt, desc
+    return frac / dt, dt, desc, (x0, x, steps)
+
+
+def host_info():
+    """Host cores and CPU model (the oracle baseline runs on them)."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
 
 
 # ---------------------------------------------------------------------- clocks
@@ -187,7 +202,7 @@ def run_reference(args):
     vals, secs = [], 0.0
     desc = ""
     for _ in range(args.steps):
-        v, dt, desc = oracle_sample()
+        v, dt, desc, _ = oracle_sample()
         vals.append(v)
         secs += dt
     value = statistics.median(vals)
@@ -251,6 +266,9 @@ def run_ours(args):
     value, total = job_throughput(ev[0].elapsed_time(ev[-1]) / 1000.0, args.steps, dist if world > 1 else None,
                                   "cuda")
     status_ok = plan.check_status() == fq.FQ_OK
+    # accuracy of the timed result: unitarity defect of U_T over 64 sampled columns (FP64, on the GPU)
+    sample_cols = torch.arange(0, n, n // 64, dtype=torch.int32, device="cuda")[:64]
+    defect_max, defect_fro = fq.api.unitarity_defect(U, sample_cols)
 
     # end to end through the C ABI with host buffers: plan from host arrays (H2D inside the
     # call), build, and the D2H copy of U_T into pinned host memory, every step
@@ -287,9 +305,16 @@ def run_ours(args):
                 "kernel": "k_tri_resident<256, 40>",
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)"}
     cpu = None
+    accuracy = {"unitarity_defect_max": defect_max, "unitarity_defect_fro": defect_fro,
+                "defect_columns": int(sample_cols.numel())}
     if not args.no_cpu_baseline and world == 1:
-        v, dt, desc = oracle_sample(d=d)
+        v, dt, desc, (x0s, xs, nst) = oracle_sample(d=d)
         cpu = {"value": v, "unit": "U_T/s", "cores": 1, "kind": "oracle", "sample": desc}
+        # the same states through the same steps on the library: max-abs difference to the oracle
+        rows = torch.from_numpy(np.ascontiguousarray(x0s.T)).to("cuda")
+        got = plan.propagate(rows, 0, nst).cpu().numpy().T
+        accuracy["sample_max_err_vs_oracle"] = float(np.max(np.abs(got - xs)))
+        accuracy["sample"] = desc
     tag = ", paper parameters" if paper else ""
     line = {"metric": f"U_T builds/sec (dim {n} Bose-Hubbard dimer{tag}, M={d.steps})", "value": value,
             "unit": "U_T/s",
@@ -298,12 +323,14 @@ def run_ours(args):
             "config": {"workload": f"bose-hubbard dimer{tag} nb={n - 1} (dim {n}), M={d.steps}, L={L}, "
                                    "FP32 resident kernel",
                        "dim": n, "steps_per_period": d.steps, "chebyshev_L": L, "R": plan.info.R,
+                       "delta_e": plan.info.delta_e,
                        "l2": "working set larger than L2 (2*Omega~ coefficients 240 MB, U_T 1.6 GB per step)",
                        "parallelism": f"weak: {world} independent drive amplitudes"},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "U_T/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * n * n},
             "gpu_launches": 2 * args.steps, "clocks": clk, "device_status_ok": status_ok,
-            "per_step_s": per_step}
+            "accuracy": accuracy, "median_step_s": statistics.median(per_step), "per_step_s": per_step,
+            "host": host_info()}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -203,9 +203,8 @@ fq_status gemm_cfg(const GemmCtx& c, const __nv_bfloat16* left, const __nv_bfloa
   // the forward and adjoint terms run persistently (epilogue overlapped with the next tile's
   // MMAs); the gradient dot keeps one tile per CTA for its per-CTA partial sums
   constexpr bool persist = EPI != EPI_DOT;
-  static bool attr = false;
-  static int sms = 0;
-  if (!attr) {
+  static std::atomic<unsigned> attr_set{0};
+  if (fq_first_on_device(attr_set)) {
     cudaError_t r;
     if constexpr (persist)
       r = cudaFuncSetAttribute(k_split_persist<NS, BN, BKE, EPI, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -213,14 +212,9 @@ fq_status gemm_cfg(const GemmCtx& c, const __nv_bfloat16* left, const __nv_bfloa
     else
       r = cudaFuncSetAttribute(k_split_term<NS, BN, BKE, EPI, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)Cfg::SMEM);
-    if (r == cudaSuccess) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
-    if (r != cudaSuccess) return fq_cuda_fail(r, "split gradient kernel attributes");
-    attr = true;
+    if (r != cudaSuccess) return fq_cuda_fail(r, "split gradient kernel shared-memory attribute");
   }
+  const int sms = fq_sm_count();
   const int tiles_i = c.np / BN, tiles_j = c.ncp / BM, nk = c.np / BKE;
   if constexpr (persist)
     k_split_persist<NS, BN, BKE, EPI, false><<<std::min(tiles_i * tiles_j, sms), PTHREADS, Cfg::SMEM, s>>>(

@@ -148,19 +148,13 @@ static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int 
       if ((st = make_map(&maps[v].os[q], w.os + q * w.bstride, w.np, w.np, BN, BKE)) != FQ_OK) return st;
       if ((st = make_map(&maps[v].oa[q], w.oa + q * w.bstride, w.np, w.np, BN, BKE)) != FQ_OK) return st;
     }
-  static bool attr = false;
-  static int sms = 0;
-  if (!attr) {
+  static std::atomic<unsigned> attr_set{0};
+  if (fq_first_on_device(attr_set)) {
     cudaError_t e = cudaFuncSetAttribute(k_split_persist<NS, BN, BKE, EPI_FWD, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
-    if (e == cudaSuccess) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
-    if (e != cudaSuccess) return fq_cuda_fail(e, "split kernel attributes");
-    attr = true;
+    if (e != cudaSuccess) return fq_cuda_fail(e, "split kernel shared-memory attribute");
   }
+  const int sms = fq_sm_count();
   // left-operand slices are only ever written for rows < nc and columns < n: zero the padding
   cudaMemsetAsync(w.a[0], 0, sizeof(__nv_bfloat16) * NS * w.astride, s);
   cudaMemsetAsync(w.a[1], 0, sizeof(__nv_bfloat16) * NS * w.astride, s);

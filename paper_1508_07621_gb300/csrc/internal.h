@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <atomic>
+
 #include "floquet.h"
 
 // Status-word bits raised by device checks.
@@ -124,6 +126,29 @@ fq_status fq_launch_resident(const fq_plan* p, const void* coeff, const double* 
 
 // split-precision dense path (dense_split.cu)
 size_t fq_split_workspace(const fq_plan* p, int nc, void* base, void* out);
+// True the first time it is called on the current device for this flag word (one bit per
+// device, devices 0..31): per-device one-time set-up such as kernel attributes, which the
+// runtime keeps per device.
+inline bool fq_first_on_device(std::atomic<unsigned>& done) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned bit = 1u << (dev & 31);
+  return (done.fetch_or(bit) & bit) == 0;
+}
+
+// SMs of the current device (queried once per device).
+inline int fq_sm_count() {
+  static std::atomic<int> cache[32];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int v = cache[dev & 31].load();
+  if (v == 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+    cache[dev & 31].store(v);
+  }
+  return v;
+}
+
 // Gradient pieces shared by the FP64 and split adjoints (adjoint.cu): tau = sum of partials and
 // loss = 1 - |tau|^2 / N^2; grad_m = 2 Re sum_l w_l D_l from per-CTA partials of D_1..D_L.
 void fq_launch_loss(const double2* partial, int count, int n, double* loss, double2* tau, cudaStream_t s);

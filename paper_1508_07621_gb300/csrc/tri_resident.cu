@@ -494,12 +494,11 @@ template <int NT, int EPT>
 fq_status launch_cfg(const fq_plan* p, const float4* cf, const float4* rot, const double* x0, double* x,
                      int transpose_out, int nc, int nsteps, const ResCoef& coef, float bcl, cudaStream_t s) {
   const size_t smem = sizeof(float4) * (EPT + 3) * NT + sizeof(ResShared);
-  static bool attr_done = false;
-  if (!attr_done) {
+  static std::atomic<unsigned> attr_set{0};
+  if (fq_first_on_device(attr_set)) {
     cudaError_t e =
         cudaFuncSetAttribute(k_tri_resident<NT, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fq_cuda_fail(e, "resident kernel smem attribute");
-    attr_done = true;
   }
   k_tri_resident<NT, EPT><<<nc, NT, smem, s>>>(cf, rot, p->n, p->L, nsteps, (const double2*)x0, (double2*)x,
                                                 transpose_out, coef, (float)p->phase_re, (float)p->phase_im, bcl,
