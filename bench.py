@@ -111,25 +111,54 @@ def job_throughput(local_seconds: float, steps: int, dist=None, device=None) -> 
 
 
 # ---------------------------------------------------------------------- oracle timing
-def oracle_sample(cols=24, steps=100, d=None):
-    """FP64 oracle on `cols` basis states over `steps` of the workload's chain (default: the
-    M = 2000 dimer); returns (U_T builds per second scaled to the full workload, seconds,
-    description)."""
+def _oracle_worker_init():
+    # one thread per process: the oracle's tridiagonal products are elementwise numpy
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+
+
+def _oracle_ready(_):
+    import numpy  # noqa: F401
+    import oracle  # noqa: F401
+    return os.getpid()
+
+
+def _oracle_block(job):
+    """One block of basis states through `steps` steps of the oracle's chain (worker process)."""
+    import numpy as np
+    import oracle as o
+    d, plan, idx, steps = job
+    x0 = np.zeros((d.n, len(idx)), complex)
+    x0[idx, np.arange(len(idx))] = 1.0
+    return x0, o.propagate_tridiag(d.h0_diag, d.h0_off, d.h1_diag, plan, x0, 0, steps)
+
+
+def oracle_sample(cols_per_core=6, steps=100, d=None, cores=None):
+    """FP64 oracle on cols_per_core basis states per host core over `steps` of the workload's
+    chain (default: the M = 2000 dimer), one spawned process per core; returns (U_T builds per
+    second scaled to the full workload, seconds, description, cores, (x0, x, steps))."""
+    import multiprocessing as mp
     import numpy as np
     import floquet_inputs as fi
     import oracle as o
     if d is None:
         d = fi.config_dimer(nb=NB, steps=STEPS)
+    cores = cores or os.cpu_count() or 1
+    cols = cols_per_core * cores
     plan = o.plan_for_drive_tridiag(d.h0_diag, d.h0_off, d.h1_diag, d.drive, d.steps)
     idx = np.linspace(0, d.n - 1, cols).astype(int)
-    x0 = np.zeros((d.n, cols), complex)
-    x0[idx, np.arange(cols)] = 1.0
-    t0 = time.perf_counter()
-    x = o.propagate_tridiag(d.h0_diag, d.h0_off, d.h1_diag, plan, x0, 0, steps)
-    dt = time.perf_counter() - t0
+    blocks = np.array_split(idx, cores)
+    with mp.get_context("spawn").Pool(cores, initializer=_oracle_worker_init) as pool:
+        pool.map(_oracle_ready, range(cores))  # workers started and imported before timing
+        t0 = time.perf_counter()
+        outs = pool.map(_oracle_block, [(d, plan, b, steps) for b in blocks])
+        dt = time.perf_counter() - t0
+    x0 = np.concatenate([a for a, _ in outs], axis=1)
+    x = np.concatenate([b for _, b in outs], axis=1)
     frac = (cols / d.n) * (steps / d.steps)
-    desc = f"{cols} of {d.n} basis states over {steps} of {d.steps} steps (FP64 numpy oracle, 1 thread)"
-    return frac / dt, dt, desc, (x0, x, steps)
+    desc = (f"{cols} of {d.n} basis states over {steps} of {d.steps} steps (FP64 numpy oracle, {cores} processes "
+            f"x 1 thread)")
+    return frac / dt, dt, desc, cores, (x0, x, steps)
 
 
 def host_info():
@@ -198,11 +227,11 @@ def run_reference(args):
         return
     import floquet_inputs  # noqa: F401
     for _ in range(args.warmup):
-        oracle_sample(cols=4, steps=20)
+        oracle_sample(cols_per_core=1, steps=20)
     vals, secs = [], 0.0
-    desc = ""
+    desc, cores = "", 1
     for _ in range(args.steps):
-        v, dt, desc, _ = oracle_sample()
+        v, dt, desc, cores, _ = oracle_sample()
         vals.append(v)
         secs += dt
     value = statistics.median(vals)
@@ -211,7 +240,7 @@ def run_reference(args):
             "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": "bose-hubbard dimer nb=10000 (dim 10001), M=2000, L=39"},
-            "cpu_baseline": {"value": value, "unit": "U_T/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "U_T/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "U_T/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -308,8 +337,8 @@ def run_ours(args):
     accuracy = {"unitarity_defect_max": defect_max, "unitarity_defect_fro": defect_fro,
                 "defect_columns": int(sample_cols.numel())}
     if not args.no_cpu_baseline and world == 1:
-        v, dt, desc, (x0s, xs, nst) = oracle_sample(d=d)
-        cpu = {"value": v, "unit": "U_T/s", "cores": 1, "kind": "oracle", "sample": desc}
+        v, dt, desc, cores, (x0s, xs, nst) = oracle_sample(d=d)
+        cpu = {"value": v, "unit": "U_T/s", "cores": cores, "kind": "oracle", "sample": desc}
         # the same states through the same steps on the library: max-abs difference to the oracle
         rows = torch.from_numpy(np.ascontiguousarray(x0s.T)).to("cuda")
         got = plan.propagate(rows, 0, nst).cpu().numpy().T
