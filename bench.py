@@ -172,6 +172,8 @@ def host_info():
                     break
     except OSError:
         pass
+    arm_parts = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1"}
+    model = arm_parts.get(model.lower(), model)
     return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
 
 
