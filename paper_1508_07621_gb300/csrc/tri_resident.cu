@@ -430,6 +430,12 @@ k_tri_resident(const float4* __restrict__ cf_all, const float4* __restrict__ rot
 
   for (int m = 0; m < nsteps; ++m) {
     const size_t off = (size_t)m * stride;
+    // the next step's operator and rotation blocks into L2 while this step runs (one thread each)
+    if (t < 2 && m + 1 < nsteps) {
+      const float4* nxt = (t == 0 ? cf_all : rot_all) + off + stride;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(nxt), "r"((unsigned)(stride * sizeof(float4)))
+                   : "memory");
+    }
     // every thread is done with the previous step's operator and state rows
     __syncthreads();
     // this step's (2 d, 2 e') and the frame change D_m^+ D_{m-1} of the state (coalesced)
