@@ -13,7 +13,9 @@
 //   dL/df_m = 2 Re sum_l w_l D_l  (w_1 = -i, w_l = -2i).
 // Memory: FP32 masters of X every s = checkpoint_stride steps; each segment is recomputed once
 // with the slices of every psi_l kept (they are the left operands of the dot products) and then
-// walked backward.
+// walked backward.  The slots are stored slice-major ([slice][slot][row][k]) and bbar_1..bbar_L
+// of a step are kept as one stacked block, so the L gradient dots of a step run as one GEMM over
+// L x Np stacked rows.
 #include <vector>
 
 #include "split_core.cuh"
@@ -129,13 +131,19 @@ struct SplitGradWs {
   __nv_bfloat16* S;       // Omega~_m slices
   __nv_bfloat16* E;       // E = H1 / Delta E slices
   __nv_bfloat16* lsl[2];  // left-operand ping-pong (forward sweep, adjoint terms)
-  __nv_bfloat16* slots;   // psi_l slices of one recomputed segment: nslots x NS x [ncp][kp]
-  Master f[6];            // FP32 masters: forward cur / prev / acc; adjoint G, bbar pair
+  __nv_bfloat16* slots;   // psi_l slices of one recomputed segment: NS x nslots x [ncp][kp]
+  Master f[5];            // FP32 masters: forward cur / prev / acc; adjoint G and the next G
+  Master bbar;            // bbar_1 .. bbar_L of one step: L blocks of ncp rows (padding rows zero)
   float* ck_base;         // nseg checkpoints of X, each 2 planes [n][ldm]
   double2* partial;       // (L + 1) x ncta
   double2* tau_partial;   // n
   double2* tau;
-  __nv_bfloat16* slot(int q) const { return slots + (size_t)q * ns * astride; }
+  size_t slot_slice() const { return (size_t)nslots * astride; }  // elements between slot slices
+  __nv_bfloat16* slot(int q) const { return slots + (size_t)q * astride; }
+  Master bbar_block(int l) const {  // bbar_l, l = 1..L
+    const size_t o = (size_t)(l - 1) * ncp * ldm;
+    return Master{bbar.re + o, bbar.im + o};
+  }
   Master ckpt(int k, int n) const {
     float* b = ck_base + (size_t)k * 2 * n * ldm;
     return Master{b, b + (size_t)n * ldm};
@@ -171,10 +179,13 @@ size_t split_grad_layout(const fq_plan* p, void* base, SplitGradWs* out) {
   w.lsl[0] = (__nv_bfloat16*)take(2 * w.ns * w.astride);
   w.lsl[1] = (__nv_bfloat16*)take(2 * w.ns * w.astride);
   w.slots = (__nv_bfloat16*)take(2 * w.ns * w.astride * (size_t)w.nslots);
-  for (int q = 0; q < 6; ++q) {
+  for (int q = 0; q < 5; ++q) {
     float* m = (float*)take(sizeof(float) * 2 * plane);
     w.f[q] = Master{m, m ? m + plane : nullptr};
   }
+  const size_t stacked = (size_t)L * w.ncp * w.ldm;
+  float* bb = (float*)take(sizeof(float) * 2 * stacked);
+  w.bbar = Master{bb, bb ? bb + stacked : nullptr};
   w.ck_base = (float*)take(sizeof(float) * 2 * plane * (size_t)w.nseg);
   w.partial = (double2*)take(sizeof(double2) * (size_t)(L + 1) * w.ncta);
   w.tau_partial = (double2*)take(sizeof(double2) * n);
@@ -190,14 +201,20 @@ struct GemmCtx {
   size_t bstride, astride;
 };
 
+// Left operand: `rows` rows of kp BF16 per slice (a multiple of 128), slice q at left + q * lstride.
+struct Left {
+  const __nv_bfloat16* base;
+  size_t lstride;
+  int rows;
+};
+
 template <int NS, int BN, int BKE, int EPI>
-fq_status gemm_cfg(const GemmCtx& c, const __nv_bfloat16* left, const __nv_bfloat16* right, const SplitEpi& e,
-                   cudaStream_t s) {
+fq_status gemm_cfg(const GemmCtx& c, Left left, const __nv_bfloat16* right, const SplitEpi& e, cudaStream_t s) {
   using Cfg = SplitCfg<NS, BN, BKE, false>;
   SplitMaps maps{};
   fq_status st;
   for (int q = 0; q < NS; ++q) {
-    if ((st = make_map(&maps.a[q], left + q * c.astride, c.ncp, c.kp, BM, BKE)) != FQ_OK) return st;
+    if ((st = make_map(&maps.a[q], left.base + q * left.lstride, left.rows, c.kp, BM, BKE)) != FQ_OK) return st;
     if ((st = make_map(&maps.os[q], right + q * c.bstride, c.np, c.np, BN, BKE)) != FQ_OK) return st;
   }
   // the forward and adjoint terms run persistently (epilogue overlapped with the next tile's
@@ -215,7 +232,7 @@ fq_status gemm_cfg(const GemmCtx& c, const __nv_bfloat16* left, const __nv_bfloa
     if (r != cudaSuccess) return fq_cuda_fail(r, "split gradient kernel shared-memory attribute");
   }
   const int sms = fq_sm_count();
-  const int tiles_i = c.np / BN, tiles_j = c.ncp / BM, nk = c.np / BKE;
+  const int tiles_i = c.np / BN, tiles_j = left.rows / BM, nk = c.np / BKE;
   if constexpr (persist)
     k_split_persist<NS, BN, BKE, EPI, false><<<std::min(tiles_i * tiles_j, sms), PTHREADS, Cfg::SMEM, s>>>(
         maps, nk, tiles_j, tiles_i, e);
@@ -226,8 +243,7 @@ fq_status gemm_cfg(const GemmCtx& c, const __nv_bfloat16* left, const __nv_bfloa
 }
 
 template <int EPI>
-fq_status gemm(const GemmCtx& c, const __nv_bfloat16* left, const __nv_bfloat16* right, const SplitEpi& e,
-               cudaStream_t s) {
+fq_status gemm(const GemmCtx& c, Left left, const __nv_bfloat16* right, const SplitEpi& e, cudaStream_t s) {
   if (c.ns == 3)
     return c.bn == 128 ? gemm_cfg<3, 128, 32, EPI>(c, left, right, e, s) : gemm_cfg<3, 64, 32, EPI>(c, left, right, e, s);
   return c.bn == 128 ? gemm_cfg<2, 128, 32, EPI>(c, left, right, e, s) : gemm_cfg<2, 64, 64, EPI>(c, left, right, e, s);
@@ -245,9 +261,9 @@ void launch_real_slices(const fq_plan* p, const double* f, int m, bool omega, co
 
 template <int NS>
 void launch_scale_slices(const SplitGradWs& w, int n, Master in, float cr, float ci, Master out, __nv_bfloat16* sl,
-                         cudaStream_t s) {
+                         size_t stride, cudaStream_t s) {
   k_scale_slices<NS><<<grid_n((size_t)n * n), 256, 0, s>>>(in.re, in.im, cr, ci, out.re, out.im, n, n, w.ldm, w.np,
-                                                            w.kp, sl, w.astride);
+                                                            w.kp, sl, stride);
 }
 
 struct Runner {
@@ -261,9 +277,9 @@ struct Runner {
     if (w.ns == 3) launch_real_slices<3>(p, f, m, true, w, s);
     else launch_real_slices<2>(p, f, m, true, w, s);
   }
-  void scale_slices(Master in, float cr, float ci, Master out, __nv_bfloat16* sl) {
-    if (w.ns == 3) launch_scale_slices<3>(w, p->n, in, cr, ci, out, sl, s);
-    else launch_scale_slices<2>(w, p->n, in, cr, ci, out, sl, s);
+  void scale_slices(Master in, float cr, float ci, Master out, __nv_bfloat16* sl, size_t stride) {
+    if (w.ns == 3) launch_scale_slices<3>(w, p->n, in, cr, ci, out, sl, stride, s);
+    else launch_scale_slices<2>(w, p->n, in, cr, ci, out, sl, stride, s);
   }
   SplitEpi epi() const {
     SplitEpi e{};
@@ -279,7 +295,8 @@ struct Runner {
 
   // Step m of the forward chain: X_{m-1} in master f[*xb] with slices left[0] -> X_m in a master
   // of f[0..2] (returned through xb) with slices left[L]; left[l] receives the slices of psi_l.
-  fq_status step(int m, int* xb, __nv_bfloat16* const* left) {
+  // `stride`: elements between the slices of one left operand.
+  fq_status step(int m, int* xb, __nv_bfloat16* const* left, size_t stride) {
     const int L = p->L;
     omega(m);
     fq_term t{};
@@ -304,8 +321,9 @@ struct Runner {
       e.out_re = w.f[out].re;
       e.out_im = w.f[out].im;
       e.slice_out = left[l + 1];
+      e.slice_stride = stride;
       e.t = t;
-      fq_status st = gemm<EPI_FWD>(c, left[l], w.S, e, s);
+      fq_status st = gemm<EPI_FWD>(c, Left{left[l], stride, w.ncp}, w.S, e, s);
       if (st != FQ_OK) return st;
       if (t.last) {
         *xb = out;
@@ -336,21 +354,22 @@ fq_status fq_grad_split(fq_plan* p, const double* d_f, const void* d_W, double* 
   const int n = p->n, M = p->steps, L = p->L, S = p->stride;
   const size_t plane_bytes = sizeof(float) * (size_t)n * w.ldm;
 
-  // slices are written only inside N x N: zero every slice buffer once (padding rows and columns)
+  // slices and bbar are written only inside N x N: zero them once (padding rows and columns)
   cudaMemsetAsync(w.lsl[0], 0, sizeof(__nv_bfloat16) * w.ns * w.astride, s);
   cudaMemsetAsync(w.lsl[1], 0, sizeof(__nv_bfloat16) * w.ns * w.astride, s);
   cudaMemsetAsync(w.slots, 0, sizeof(__nv_bfloat16) * w.ns * w.astride * (size_t)w.nslots, s);
+  cudaMemsetAsync(w.bbar.re, 0, sizeof(float) * 2 * (size_t)L * w.ncp * w.ldm, s);
   if (w.ns == 3) launch_real_slices<3>(p, nullptr, 0, false, w, s);
   else launch_real_slices<2>(p, nullptr, 0, false, w, s);
 
   // ---- forward sweep, checkpoints X_{kS} as FP32 masters
   int xb = 0;
-  r.scale_slices(Master{nullptr, nullptr}, 1.f, 0.f, w.f[0], w.lsl[0]);
+  r.scale_slices(Master{nullptr, nullptr}, 1.f, 0.f, w.f[0], w.lsl[0], w.astride);
   cudaMemcpyAsync(w.ckpt(0, n).re, w.f[0].re, 2 * plane_bytes, cudaMemcpyDeviceToDevice, s);
   std::vector<__nv_bfloat16*> left(L + 1);
   for (int m = 0; m < M; ++m) {
     for (int l = 0; l <= L; ++l) left[l] = w.lsl[l & 1];
-    if ((st = r.step(m, &xb, left.data())) != FQ_OK) return st;
+    if ((st = r.step(m, &xb, left.data(), w.astride)) != FQ_OK) return st;
     // the last term wrote X_m's slices into left[L]; the next step reads them from lsl[0]
     if (L & 1) std::swap(w.lsl[0], w.lsl[1]);
     if ((m + 1) % S == 0 && (m + 1) / S < w.nseg)
@@ -359,63 +378,57 @@ fq_status fq_grad_split(fq_plan* p, const double* d_f, const void* d_W, double* 
   // ---- loss and seed
   k_trace_f32<<<n, 256, 0, s>>>((const double2*)d_W, w.f[xb].re, w.f[xb].im, n, w.ldm, w.tau_partial);
   fq_launch_loss(w.tau_partial, n, n, d_loss, w.tau, s);
-  int gi = 3, b1i = 4, b2i = 5;  // G, bbar pair (indices into f)
+  int gi = 3, gn = 4;  // G of the current step, and the buffer that receives bbar_0 = G_{m-1}
   k_seed_f32<<<grid_n((size_t)n * n), 256, 0, s>>>((const double2*)d_W, w.tau, n, w.ldm, w.f[gi].re, w.f[gi].im);
 
   // ---- backward, one checkpoint segment at a time
   const float cph_r = (float)p->phase_re, cph_i = (float)-p->phase_im;  // conj(e^{-i beta h})
+  const size_t ss = w.slot_slice();
   for (int k = w.nseg - 1; k >= 0; --k) {
     const int m0 = k * S, m1 = std::min(M, m0 + S);
     // recompute the segment forward keeping the slices of every psi_l (slot st * L + l)
     cudaMemcpyAsync(w.f[0].re, w.ckpt(k, n).re, 2 * plane_bytes, cudaMemcpyDeviceToDevice, s);
-    r.scale_slices(w.f[0], 1.f, 0.f, Master{nullptr, nullptr}, w.slot(0));
+    r.scale_slices(w.f[0], 1.f, 0.f, Master{nullptr, nullptr}, w.slot(0), ss);
     xb = 0;
     for (int st_ = 0; st_ < m1 - m0; ++st_) {
       for (int l = 0; l <= L; ++l) left[l] = w.slot(st_ * L + l);
-      if ((st = r.step(m0 + st_, &xb, left.data())) != FQ_OK) return st;
+      if ((st = r.step(m0 + st_, &xb, left.data(), ss)) != FQ_OK) return st;
     }
     for (int st_ = m1 - m0 - 1; st_ >= 0; --st_) {
       const int m = m0 + st_;
       r.omega(m);
-      // bbar_L = conj(phase) a_L G (FP32 and slices)
+      // bbar_L = conj(phase) a_L G (FP32 in its stacked block, slices in lsl[0])
       const double aL = p->cheb[L];
-      r.scale_slices(w.f[gi], (float)(cph_r * aL), (float)(cph_i * aL), w.f[b1i], w.lsl[0]);
+      r.scale_slices(w.f[gi], (float)(cph_r * aL), (float)(cph_i * aL), w.bbar_block(L), w.lsl[0], w.astride);
       int sl = 0;
-      SplitEpi d = r.epi();
-      d.cur_re = w.f[b1i].re;
-      d.cur_im = w.f[b1i].im;
-      d.partial = w.partial + (size_t)L * w.ncta;
-      if ((st = gemm<EPI_DOT>(r.c, w.slot(st_ * L + L - 1), w.E, d, s)) != FQ_OK) return st;
-      bool have2 = false;
       for (int l = L - 1; l >= 0; --l) {
         const double a = p->cheb[l];
+        const Master out = l >= 1 ? w.bbar_block(l) : w.f[gn];
         SplitEpi e = r.epi();
         e.cur_re = w.f[gi].re;
         e.cur_im = w.f[gi].im;
-        e.prev_re = have2 ? w.f[b2i].re : nullptr;
-        e.prev_im = have2 ? w.f[b2i].im : nullptr;
-        e.out_re = w.f[b2i].re;
-        e.out_im = w.f[b2i].im;
+        e.prev_re = l + 2 <= L ? w.bbar_block(l + 2).re : nullptr;
+        e.prev_im = l + 2 <= L ? w.bbar_block(l + 2).im : nullptr;
+        e.out_re = out.re;
+        e.out_im = out.im;
         e.slice_out = w.lsl[sl ^ 1];
         e.cpa_re = (float)(cph_r * a);
         e.cpa_im = (float)(cph_i * a);
         e.cw = l == 0 ? 1.f : 2.f;
         e.t.bound2 = 1e30;  // NaN / overflow check only
-        if ((st = gemm<EPI_ADJ>(r.c, w.lsl[sl], w.S, e, s)) != FQ_OK) return st;
-        if (l >= 1) {
-          SplitEpi dd = r.epi();
-          dd.cur_re = w.f[b2i].re;
-          dd.cur_im = w.f[b2i].im;
-          dd.partial = w.partial + (size_t)l * w.ncta;
-          if ((st = gemm<EPI_DOT>(r.c, w.slot(st_ * L + l - 1), w.E, dd, s)) != FQ_OK) return st;
-        }
-        std::swap(b1i, b2i);  // b1 = bbar_l, b2 = bbar_{l+1}
+        if ((st = gemm<EPI_ADJ>(r.c, Left{w.lsl[sl], w.astride, w.ncp}, w.S, e, s)) != FQ_OK) return st;
         sl ^= 1;
-        have2 = true;
       }
-      // bbar_0 = G_{m-1} is in b1; the old G becomes scratch
-      std::swap(gi, b1i);
+      // D_l = <bbar_l, E psi_{l-1}>, l = 1..L, as one GEMM over the L stacked blocks: psi_0..psi_{L-1}
+      // are the consecutive slots st*L .. st*L+L-1, bbar_1..bbar_L the stacked FP32 blocks
+      SplitEpi d = r.epi();
+      d.nc = L * w.ncp;
+      d.cur_re = w.bbar.re;
+      d.cur_im = w.bbar.im;
+      d.partial = w.partial + w.ncta;  // block l at partial + l * ncta
+      if ((st = gemm<EPI_DOT>(r.c, Left{w.slot(st_ * L), ss, L * w.ncp}, w.E, d, s)) != FQ_OK) return st;
       fq_launch_grad_reduce(w.partial, w.ncta, L, d_grad + m, s);
+      std::swap(gi, gn);  // bbar_0 is the next G
     }
   }
   cudaError_t e = cudaGetLastError();

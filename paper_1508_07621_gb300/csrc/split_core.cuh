@@ -516,7 +516,7 @@ k_split_term(const __grid_constant__ SplitMaps maps, int nk, int tiles_j, int ti
   tc_fence_before();
   __syncthreads();
   if (EPI == EPI_DOT && threadIdx.x == 0)
-    e.partial[blockIdx.x] = make_double2(red[0] + red[2] + red[4] + red[6], red[1] + red[3] + red[5] + red[7]);
+    e.partial[tj * tiles_i + ti] = make_double2(red[0] + red[2] + red[4] + red[6], red[1] + red[3] + red[5] + red[7]);
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)Cfg::TMEM_COLS)
                  : "memory");
