@@ -77,10 +77,14 @@ typedef enum fq_drive_kind {
 } fq_drive_kind;
 
 typedef enum fq_kernel {
-  FQ_KERNEL_AUTO = 0,       /* resident kernel when it applies, else streaming */
+  FQ_KERNEL_AUTO = 0,       /* resident kernel when it applies, else tiled, else streaming */
   FQ_KERNEL_STREAM = 1,     /* tridiagonal: one launch per Chebyshev term, states in HBM */
-  FQ_KERNEL_RESIDENT = 2    /* tridiagonal FP32: one CTA per state runs the whole chain on chip
+  FQ_KERNEL_RESIDENT = 2,   /* tridiagonal FP32: one CTA per state runs the whole chain on chip
                                (N <= 10240, L <= 128); FQ_EUNSUPPORTED otherwise */
+  FQ_KERNEL_TILED = 3       /* tridiagonal FP64 or FP32, any N, L <= 128: one launch per step, each
+                               CTA runs the step's L products on a segment of one state plus L
+                               halo rows a side; FQ_EUNSUPPORTED otherwise.  AUTO picks RESIDENT,
+                               then TILED, then STREAM. */
 } fq_kernel;
 
 /* Problem statement (Eq. 13, §3): everything floquet_plan_create needs. */

@@ -58,6 +58,8 @@ size_t layout(const fq_plan* p, int nc, int nsteps, void* ws, StateWs* out) {
       for (int q = 0; q < 2; ++q) w.buf[b][q] = c.take<char>((size_t)nc * ld * es);
   } else if (p->path == PATH_TRI_RESIDENT) {
     w.coeff = c.take<char>(fq_resident_coeff_bytes(n, nsteps));
+  } else if (p->path == PATH_TRI_TILE) {
+    w.coeff = c.take<char>(fq_tile_workspace(p, nc, nsteps));
   } else if (p->path == PATH_DENSE_SPLIT) {
     w.coeff = c.take<char>(fq_split_workspace(p, nc, nullptr, nullptr));
   }
@@ -169,6 +171,11 @@ fq_status propagate_impl(fq_plan* p, const double* x0, double* x, int nc, int m_
     if (st != FQ_OK) return st;
     return cuda_ok(cudaGetLastError(), "resident chain");
   }
+  if (p->path == PATH_TRI_TILE) {
+    st = fq_tile_propagate(p, x0, x, nc, m_begin, m_end, identity, transpose_out, w.coeff, s);
+    if (st != FQ_OK) return st;
+    return cuda_ok(cudaGetLastError(), "tiled tridiagonal chain");
+  }
   if (p->path == PATH_DENSE_SPLIT) {
     st = fq_split_propagate(p, x0, x, nc, m_begin, m_end, identity, transpose_out, w.coeff, s);
     if (st != FQ_OK) return st;
@@ -232,12 +239,23 @@ fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
   const int n = p->n, M = p->steps;
   if (p->format == FQ_TRIDIAG) {
     const bool res_ok = p->precision == FQ_FP32 && fq_resident_supported(n, p->L);
+    const bool tile_ok = fq_tile_supported(p->L) != 0;
     if (prob->kernel == FQ_KERNEL_RESIDENT && !res_ok) {
       fq_set_error("resident kernel needs FQ_FP32, N <= 10240 and L <= 128 (N = %d, L = %d)", n, p->L);
       delete p;
       return FQ_EUNSUPPORTED;
     }
-    p->path = (res_ok && prob->kernel != FQ_KERNEL_STREAM) ? PATH_TRI_RESIDENT : PATH_TRI_STREAM;
+    if (prob->kernel == FQ_KERNEL_TILED && !tile_ok) {
+      fq_set_error("tiled kernel needs L <= 128 (L = %d)", p->L);
+      delete p;
+      return FQ_EUNSUPPORTED;
+    }
+    switch (prob->kernel) {
+      case FQ_KERNEL_STREAM: p->path = PATH_TRI_STREAM; break;
+      case FQ_KERNEL_RESIDENT: p->path = PATH_TRI_RESIDENT; break;
+      case FQ_KERNEL_TILED: p->path = PATH_TRI_TILE; break;
+      default: p->path = res_ok ? PATH_TRI_RESIDENT : (tile_ok ? PATH_TRI_TILE : PATH_TRI_STREAM);
+    }
   } else {
     p->path = p->precision == FQ_FP64 ? PATH_DENSE_F64 : PATH_DENSE_SPLIT;
   }

@@ -21,6 +21,7 @@ enum fq_path : int {
   PATH_DENSE_SPLIT = 1,   // tcgen05 BF16 split GEMM per term
   PATH_TRI_STREAM = 2,    // streaming tridiagonal term kernel (FP32 or FP64)
   PATH_TRI_RESIDENT = 3,  // one CTA per state, whole chain on chip (FP32)
+  PATH_TRI_TILE = 5,      // one launch per step, each CTA runs a step's L products on a state segment
 };
 
 struct fq_plan {
@@ -118,6 +119,11 @@ void fq_launch_term_tri_f32(const float* d, const float* er, const float* ei, in
 
 // resident tridiagonal chain (tri_resident.cu)
 int fq_resident_supported(int n, int L);
+// Tiled tridiagonal chain (tri_tile.cu): FP64 or FP32, any n, L <= 128.
+int fq_tile_supported(int L);
+size_t fq_tile_workspace(const fq_plan* p, int nc, int nsteps);
+fq_status fq_tile_propagate(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
+                            int transpose_out, void* ws, cudaStream_t s);
 size_t fq_resident_coeff_bytes(int n, int steps);
 // per-step (2 d, 2 e') of the gauge-real operator and the frame rotations, into `coeff`
 void fq_launch_gauge_coeffs(const fq_plan* p, int m_begin, int nsteps, void* coeff, cudaStream_t s);

@@ -27,15 +27,13 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "gauge.cuh"
 #include "internal.h"
 
 namespace {
 
 constexpr int RES_MAXNW = 32;
 constexpr int RES_MAXL = 128;
-constexpr int GAUGE_NT = 1024;
-constexpr int GAUGE_MAXC = 10;  // ld <= 10240
-
 struct ResCoef {
   float cr[RES_MAXL + 1];  // c_k = (-i)^k a_k: real for even k, imaginary for odd k
   float ci[RES_MAXL + 1];
@@ -54,87 +52,6 @@ struct ResShared {
 __host__ __device__ __forceinline__ size_t res_index(int i, int nt, int ept) {
   const int t = i / ept, q = i - t * ept;
   return ((size_t)(q >> 1) * nt + t) * 2 + (q & 1);
-}
-
-// Operator data the gauge kernel reads (device pointers of the plan).
-struct GaugeArgs {
-  int n, M;
-  const double* h0d;
-  const double* h0o;
-  const double* h1d;
-  const double* ko;
-  const double* scal;  // sa | sb | sc, M each
-  double sbeta;
-};
-
-// ---------------------------------------------------------------------------- gauge
-// Omega~[k+1][k] = sa_m H0[k+1][k] + i sc_m [H0,H1][k+1][k]  (k < n-1, else 0)
-__device__ __forceinline__ void offdiag(const GaugeArgs& p, int m, int k, double& er, double& ei) {
-  if (k + 1 < p.n) {
-    er = p.scal[m] * p.h0o[k];
-    ei = p.scal[2 * p.M + m] * p.ko[k];
-  } else {
-    er = 0.0;
-    ei = 0.0;
-  }
-}
-
-// phi_k = arg(e_k) reduced to (-pi/2, pi/2], so that e_k e^{-i phi_k} is real (+-|e_k|).
-__device__ __forceinline__ double reduced_arg(double er, double ei) {
-  if (er == 0.0) return ei == 0.0 ? 0.0 : 0.5 * 3.14159265358979323846;
-  return atan(ei / er);
-}
-
-// Block-wide exclusive prefix of per-thread chunk sums (GAUGE_NT threads).
-__device__ double block_exclusive_scan(double x, double* sw) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double incl = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    double y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) sw[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    double w = lane < GAUGE_NT / 32 ? sw[lane] : 0.0;
-    double wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      double y = __shfl_up_sync(0xffffffffu, wi, o);
-      if (lane >= o) wi += y;
-    }
-    sw[32 + lane] = wi - w;  // exclusive warp offsets
-  }
-  __syncthreads();
-  const double r = sw[32 + warp] + incl - x;
-  __syncthreads();
-  return r;
-}
-
-// theta_k = sum_{j<k} phi_j for k in this thread's chunk [C t, C t + C) of step m (0 if m < 0).
-__device__ void phases(const GaugeArgs& p, int m, int ld, int C, double (&th)[GAUGE_MAXC], double* sw) {
-  const int k0 = threadIdx.x * C;
-  double ph[GAUGE_MAXC];
-  double local = 0.0;
-#pragma unroll
-  for (int q = 0; q < GAUGE_MAXC; ++q) {
-    double v = 0.0;
-    const int k = k0 + q;
-    if (m >= 0 && q < C && k < ld) {
-      double er, ei;
-      offdiag(p, m, k, er, ei);
-      v = reduced_arg(er, ei);
-    }
-    ph[q] = v;
-    local += v;
-  }
-  double run = block_exclusive_scan(local, sw);
-#pragma unroll
-  for (int q = 0; q < GAUGE_MAXC; ++q) {
-    th[q] = run;
-    run += ph[q];
-  }
 }
 
 // CTA s < nsteps (step m = m_begin + s): cf[s][k] = (2 d_k, 2 e'_k) and

@@ -99,9 +99,9 @@ def dimer_plan(fq, d, precision, kernel=0):
                            kernel=kernel)
 
 
-@pytest.mark.parametrize("precision,kernel", [(0, 1), (1, 1), (1, 2)])
+@pytest.mark.parametrize("precision,kernel", [(0, 1), (1, 1), (1, 2), (0, 3), (1, 3)])
 def test_dimer40_all_paths(fq, precision, kernel):
-    """Small dimer (dim 41, M = 100): FP64 streaming, FP32 streaming, FP32 resident."""
+    """Small dimer (dim 41, M = 100): FP64 / FP32 streaming, FP32 resident, FP64 / FP32 tiled."""
     d = fi.config_dimer(nb=40, steps=100)
     plan = dimer_plan(fq, d, precision, kernel)
     U = to_np(plan.build_UT())
@@ -266,3 +266,38 @@ def test_paper_dimer_parameters(fq, precision, kernel):
     ref = o.propagate_tridiag(d.h0_diag, d.h0_off, d.h1_diag, refp, x0.T, 3, 28).T
     tol = 1e-10 if precision == 0 else tol_f32(25, plan.info.L, plan.info.R)
     assert np.max(np.abs(X - ref)) <= tol
+
+
+@pytest.mark.parametrize("precision,nb,m_end", [(0, 3000, 6), (1, 3000, 6), (0, 10000, 3), (1, 12000, 3),
+                                                 (0, 2011, 4), (0, 2012, 4)])
+def test_dimer_tiled_kernel_segments(fq, precision, nb, m_end):
+    """Tiled chain (one launch per step, L halo rows a side): several segments with a ragged tail
+    (dim 3001, 10001), FP32 beyond the resident kernel's 10240 rows (dim 12001), and dims at one
+    segment and one past it (2012 and 2013 rows: 2048-row tiles at L = 18); first, middle and last basis
+    states and a random unit vector, steps 1..m_end-1 of the M = 2000 chain (phase offset drive)."""
+    d = fi.config_dimer(nb=nb, steps=2000)
+    d.drive = fi.Drive(0.2, 1.5, 3.0, 0.4)
+    plan = dimer_plan(fq, d, precision, 3)
+    n = d.n
+    x0 = np.zeros((4, n), complex)
+    x0[0, 0] = 1
+    x0[1, n // 2] = 1
+    x0[2, n - 1] = 1
+    x0[3] = np.exp(2j * np.pi * fi.uniform(2201, n))
+    x0[3] /= np.linalg.norm(x0[3])
+    X = to_np(plan.propagate(cuda_c128(x0), 1, m_end))
+    assert plan.check_status() == fq.FQ_OK
+    refp = o.plan_for_drive_tridiag(d.h0_diag, d.h0_off, d.h1_diag, d.drive, d.steps)
+    ref = o.propagate_tridiag(d.h0_diag, d.h0_off, d.h1_diag, refp, x0.T, 1, m_end).T
+    tol = 1e-10 if precision == 0 else tol_f32(m_end - 1, plan.info.L, plan.info.R)
+    assert np.max(np.abs(X - ref)) <= tol
+
+
+def test_tiled_kernel_rejects_long_series(fq):
+    """L above 128 (one step over a whole period of the dim-1001 dimer) is refused, not run."""
+    d = fi.config_dimer(nb=1000, steps=1)
+    prob, keep = fq.make_problem(d.n, fq.FQ_TRIDIAG, d.h0_diag, d.h1_diag, d.drive.period, d.steps, h0_off=d.h0_off,
+                                 f_ac=1.5, omega=3.0, precision=fq.FQ_FP64, kernel=fq.FQ_KERNEL_TILED)
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_plan_create(prob)
+    assert e.value.status == fq.FQ_EUNSUPPORTED
