@@ -6,8 +6,8 @@
 // Omega~_m = D_m Omega'_m D_m^+ where Omega'_m is REAL symmetric tridiagonal (off-diagonal
 // e'_k = +-|e_k|).  Hence exp(-i Omega_m) = e^{-i beta h} D_m P(Omega'_m) D_m^+ and the chain
 // runs in the frame of each step: v <- (D_m^+ D_{m-1}) v before step m, X = D_last v at the end.
-// A real operator acts on the (re, im) pair of every entry alike, so each product is three
-// packed FP32x2 FMAs per entry.
+// A real operator acts on the (re, im) pair of every entry alike, so each product is four
+// packed FP32x2 FMAs per entry (c v - b_{k+2}, then the three operator entries).
 //
 // Each step applies sum_{k=0}^{L} c_k T_k(Omega') v with c_k = (-i)^k a_k (Eqs. 10 and 12:
 // psi_k = (-i)^k T_k(Omega~) v) by Clenshaw's backward recurrence
@@ -16,13 +16,14 @@
 // which needs the same L products as the forward recurrence of Eq. 10 but only two live
 // vectors besides v.  Then X_m = e^{-i beta h} sum.
 //
-// Layout: NT threads (512, or 256 for N <= 1024); thread t owns rows i = t*EPT .. t*EPT+EPT-1
-// (EPT even).  b_{k+1}, b_{k+2} live in registers as (re, im) pairs; v and the step's (2 d, 2 e')
-// pairs live in shared memory as float4 holding rows (2p, 2p+1) of thread t at [p][t], so one
-// conflict-free 16-byte access serves two rows.  The per-step coefficient and rotation arrays
-// are written in global memory in exactly that order ("resident order"), so their loads are
-// coalesced.  The one-row halo of b_{k+1} crosses lanes by warp shuffles and warps through a
-// small double-buffered shared slot array (one __syncthreads per product).
+// Layout: NT threads (256 x 40 rows above 9216 rows, 512 x <= 18 below, 256 x 2 or 4 up to 1024);
+// thread t owns rows i = t*EPT .. t*EPT+EPT-1 (EPT even).  b_{k+1}, b_{k+2} live in registers as
+// (re, im) pairs; v and the step's (2 d, 2 e') pairs live in shared memory as float4 holding rows
+// (2p, 2p+1) of thread t at [p][t], so one conflict-free 16-byte access serves two rows.  The
+// per-step coefficient and rotation arrays are written in global memory in exactly that order
+// ("resident order"), so their loads are coalesced.  Each sweep over a thread's rows applies two
+// products (Chain::pass); the two-row halo of b_{k+1} crosses lanes by warp shuffles and warps
+// through small double-buffered shared arrays (one __syncthreads per two products).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -432,8 +433,8 @@ fq_status launch_cfg(const fq_plan* p, const float4* cf, const float4* rot, cons
 }
 
 // (threads, rows per thread) for dimension n; 0 threads if the resident kernel does not apply.
-// 512 x 20 keeps b_{k+1}, b_{k+2} of 20 rows in 124 registers without spills (1024 x 10 would
-// have to fit in 64 registers and spills).
+// Above 9216 rows, 256 x 40 (250 registers, no spills) beats 512 x 20, which has to fit in 128
+// registers and spills; 1024 x 10 would have to fit in 64.
 void res_config(int n, int* nt, int* ept) {
   *nt = 0;
   *ept = 0;
