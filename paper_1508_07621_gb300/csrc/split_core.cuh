@@ -1,23 +1,24 @@
 // Split-precision dense GEMM core on the 5th-generation tensor cores (tcgen05, sm_103a), shared by
-// the forward Chebyshev term (dense_split.cu) and the adjoint (adjoint_split.cu).
+// the forward Chebyshev chain (dense_split.cu) and the adjoint (adjoint_split.cu).
 //
-// One term of Eq. 10 on a block of nc state rows: Y^T = Psi^T Omega~^T with Omega~ = S + i A
-// (S real symmetric, A real antisymmetric), i.e. with X.B := sum_k X[j][k] B[i][k]
-//   Yr = Psi_r.S - Psi_i.A,   Yi = Psi_r.A + Psi_i.S.
-// Each K stage loads the Psi_r, Psi_i tiles and one S and one A tile, and four MMA streams
+// One product on a block of state rows: Y^T = Psi^T Omega~^T with Omega~ = S + i A (S real
+// symmetric, A real antisymmetric), i.e. with X.B := sum_k X[j][k] B[i][k]
+//   Yr = Psi_r.S - Psi_i.A,   Yi = Psi_r.A + Psi_i.S       (HAS_A; A = 0 drops two streams).
+// Each K stage loads the Psi_r, Psi_i tiles and one S (and one A) tile, and four MMA streams
 // (the minus sign through the instruction's negate-A bit) use every tile twice.  Every operand
-// is held as NS BF16 slices
-// (x = x_0 + x_1 + ..., x_s = bf16 of the remainder), and the products x_a y_b with a + b < NS
-// (3 for NS = 2, 6 for NS = 3) are summed in FP32 in tensor memory.  The epilogue applies the
-// recurrence psi_{l+1} = -2i Y + psi_{l-1}, the Bessel accumulation and the step phase on FP32
-// master copies (Eqs. 10, 12) and writes the next term's slices.
+// is held as NS BF16 slices (x = x_0 + x_1 + ..., x_s = bf16 of the remainder), and the products
+// x_a y_b with a + b < NS (3 for NS = 2, 6 for NS = 3) are summed in FP32 in tensor memory.
+// The epilogue (epi_chunk) is one of: the Chebyshev term (recurrence psi_{l+1} = -2i Y +
+// psi_{l-1}, Bessel accumulation and step phase on FP32 masters, Eqs. 10 and 12), the adjoint
+// term, or the gradient dot; the first two also write the next product's slices.
 //
-// CTA: 128 threads, tile 128 state rows x BN output columns, tiles rasterized in groups of 8 row
-// blocks so that co-running CTAs share operands in L2.  Thread 0 of warp 0 issues TMA loads
-// (K-major, 128- or 64-byte swizzle), thread 0 of warp 1 issues tcgen05.mma (A and B from shared memory,
-// D in tensor memory), stages handed over by mbarriers; all four warps read the accumulators
-// back with tcgen05.ld for the epilogue.  Every wait is bounded; a wait that gives up records
-// FQ_BIT_TIMEOUT, drains this CTA's own copies and MMAs, frees tensor memory and returns.
+// k_split_term: one 128-row x BN-column tile per CTA of 128 threads.  k_split_persist: one CTA
+// per SM walks its tiles with a dedicated TMA warp, MMA warp and four epilogue warps, and two
+// tensor-memory buffers so that a tile's epilogue overlaps the next tile's MMAs.  Tiles are
+// rasterized in groups of 8 row blocks so that co-running CTAs share operands in L2.  TMA loads
+// are K-major with 128- or 64-byte swizzle; stages and buffers are handed over by mbarriers.
+// Every wait is bounded; a wait that gives up records FQ_BIT_TIMEOUT, drains this CTA's own
+// copies and MMAs, frees tensor memory and returns.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
