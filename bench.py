@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--workload", choices=["dimer", "dimer-paper"], default="dimer",
                     help="dimer: nb = 10^4, J = 1, U nb = 2, f = 1.5 cos 3t, M = 2000 (default); "
                          "dimer-paper: the paper's parameters (U/2)(n1 - n2)^2, f = 2.7 + 2.5 cos 3t, M = 8000")
-    ap.add_argument("--ncu-case", choices=["resident", "stream", "split"], default=None,
+    ap.add_argument("--ncu-case", choices=["resident", "stream", "split", "tile", "adjoint"], default=None,
                     help="run one small capture case of a kernel twice and exit (for ncu --set full)")
     return ap.parse_args()
 
@@ -54,10 +54,25 @@ def run_ncu_case(case):
     """Small cases for detailed ncu captures (a few GB at most, inputs larger than L2):
     resident: 152 states (one wave on 152 SMs) over steps 0..19 of the benchmark chain;
     stream:   2048 states through step 0 (39 streaming FP32 term launches, 0.5 GB of states);
-    split:    dense GOE N = 4096 (seeds 3, 4), BF16X3 tensor-core terms of step 0 on the identity."""
+    split:    dense GOE N = 4096 (seeds 3, 4), BF16X3 tensor-core terms of step 0 on the identity;
+    tile:     2048 states through step 0 on the FP64 tiled kernel (0.65 GB of states);
+    adjoint:  the BF16X3 gradient at N = 1024 (seeds 6-9) over the first 16 of its 256 steps."""
+    import math
     import torch
     import floquet_inputs as fi
     import paper_1508_07621_gb300 as fq
+    if case == "adjoint":
+        n, M = 1024, 16
+        fm = 1.0 + 0.1 * fi.normal(9, 256)[:M]
+        plan = fq.Plan.piecewise(fi.goe(n, 6), fi.goe(n, 7), fm, period=2 * math.pi * M / 256,
+                                 checkpoint_stride=16, precision=fq.FQ_BF16X3, tile_n=64)
+        W = torch.tensor(fi.haar_unitary(n, 8), dtype=torch.complex128, device="cuda")
+        f = torch.tensor(fm, device="cuda")
+        for _ in range(2):
+            plan.grad(f, W)
+        torch.cuda.synchronize()
+        print(f"ncu case adjoint: status {plan.check_status()}")
+        return
     if case == "split":
         m = fi.config_goe4096()
         plan = fq.Plan.dense(m.h0, m.h1, omega=m.drive.omega, f_ac=m.drive.f_ac, steps=m.steps,
@@ -72,9 +87,9 @@ def run_ncu_case(case):
         return
     d = fi.config_dimer(nb=NB, steps=STEPS)
     n = d.n
-    kernel = fq.FQ_KERNEL_RESIDENT if case == "resident" else fq.FQ_KERNEL_STREAM
+    kernel = {"resident": fq.FQ_KERNEL_RESIDENT, "stream": fq.FQ_KERNEL_STREAM, "tile": fq.FQ_KERNEL_TILED}[case]
     plan = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=d.drive.f_ac,
-                           steps=d.steps, precision=fq.FQ_FP32, kernel=kernel)
+                           steps=d.steps, precision=fq.FQ_FP64 if case == "tile" else fq.FQ_FP32, kernel=kernel)
     nc, m_end = (152, 20) if case == "resident" else (2048, 1)
     x0 = torch.zeros((nc, n), dtype=torch.complex128, device="cuda")
     x0[torch.arange(nc), torch.arange(nc) * (n // nc)] = 1.0
