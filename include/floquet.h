@@ -68,7 +68,10 @@ typedef enum fq_precision {
   FQ_FP64 = 0,          /* every product and accumulation in FP64 (baseline path) */
   FQ_FP32 = 1,          /* FP32 storage and FP32 arithmetic (tridiagonal format) */
   FQ_BF16X3 = 2,        /* dense: 2-slice BF16 split, products hi*hi + hi*lo + lo*hi, FP32 accumulate */
-  FQ_BF16X6 = 3         /* dense: 3-slice BF16 split, 6 slice products, FP32 accumulate */
+  FQ_BF16X6 = 3,        /* dense: 3-slice BF16 split, 6 slice products, FP32 accumulate */
+  FQ_DF32 = 4           /* tridiagonal: double-float arithmetic (each value a pair of FP32 numbers,
+                           about 48 significant bits) on the FP32 pipes; FP64 states in HBM; tiled
+                           kernel (L <= 128); FP64-level results */
 } fq_precision;
 
 typedef enum fq_drive_kind {

@@ -245,8 +245,13 @@ fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
       delete p;
       return FQ_EUNSUPPORTED;
     }
-    if (prob->kernel == FQ_KERNEL_TILED && !tile_ok) {
+    if ((prob->kernel == FQ_KERNEL_TILED || p->precision == FQ_DF32) && !tile_ok) {
       fq_set_error("tiled kernel needs L <= 128 (L = %d)", p->L);
+      delete p;
+      return FQ_EUNSUPPORTED;
+    }
+    if (p->precision == FQ_DF32 && prob->kernel != FQ_KERNEL_AUTO && prob->kernel != FQ_KERNEL_TILED) {
+      fq_set_error("FQ_DF32 runs on the tiled kernel only");
       delete p;
       return FQ_EUNSUPPORTED;
     }

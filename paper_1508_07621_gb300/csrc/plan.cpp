@@ -362,12 +362,12 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan) {
     return FQ_EINVAL;
   }
   if (p->drive_kind == FQ_DRIVE_PIECEWISE && !p->f_steps) { fq_set_error("piecewise drive needs f_steps"); return FQ_EINVAL; }
-  if (p->precision < FQ_FP64 || p->precision > FQ_BF16X6) { fq_set_error("bad precision %d", p->precision); return FQ_EINVAL; }
-  if (p->format == FQ_TRIDIAG && p->precision > FQ_FP32) {
-    fq_set_error("tridiagonal format supports FQ_FP64 and FQ_FP32");
+  if (p->precision < FQ_FP64 || p->precision > FQ_DF32) { fq_set_error("bad precision %d", p->precision); return FQ_EINVAL; }
+  if (p->format == FQ_TRIDIAG && (p->precision == FQ_BF16X3 || p->precision == FQ_BF16X6)) {
+    fq_set_error("tridiagonal format supports FQ_FP64, FQ_FP32 and FQ_DF32");
     return FQ_EUNSUPPORTED;
   }
-  if (p->format == FQ_DENSE && p->precision == FQ_FP32) {
+  if (p->format == FQ_DENSE && (p->precision == FQ_FP32 || p->precision == FQ_DF32)) {
     fq_set_error("dense format supports FQ_FP64, FQ_BF16X3 and FQ_BF16X6");
     return FQ_EUNSUPPORTED;
   }

@@ -9,6 +9,11 @@
 // row further in from the tile's edge (the rows beyond it are taken as zero), so after the L
 // products of a step the segment's rows are exact; only those are written.
 //
+// FQ_DF32 runs the same step in double-float arithmetic: every value is an unevaluated sum
+// hi + lo of two FP32 numbers (Dekker's splitting, Knuth's two-sum, and two-product by FMA), so
+// the products keep about 48 significant bits on the FP32 pipes, which GB300 runs at many times
+// its FP64 rate.  States stay FP64 in HBM between steps.
+//
 // Layout: states as rows, planar re / im planes [nc][ld] (the streaming kernel's layout).
 // Per step and row: (2 d, 2 e') and (cos theta, sin theta) of D_m, in the kernel's precision,
 // computed once per call in FP64 by k_gauge_tile.
@@ -26,9 +31,44 @@ constexpr int TILE_EPT = 8;
 constexpr int TILE_ROWS = TILE_NT * TILE_EPT;
 constexpr int TILE_MAXL = 128;
 
+// double-float value hi + lo, |lo| <= ulp(hi) / 2
+struct dfl {
+  float h, l;
+};
+
+__device__ __forceinline__ dfl dfl_of(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double dfl_value(dfl a) { return (double)a.h + (double)a.l; }
+
+// a * b + c in double-float: exact two-product of the high parts (FMA), the cross terms, a
+// two-sum with c's high part, and a final fast renormalisation.  Every step uses an explicitly
+// rounded operation, so the compiler cannot contract or reorder it.
+__device__ __forceinline__ dfl dfl_fma(dfl a, dfl b, dfl c) {
+  const float p = __fmul_rn(a.h, b.h);
+  float pe = __fmaf_rn(a.h, b.h, -p);
+  pe = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, pe));
+  const float s = __fadd_rn(p, c.h);
+  const float bb = __fsub_rn(s, p);
+  float se = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(c.h, bb));
+  se = __fadd_rn(se, __fadd_rn(pe, c.l));
+  const float h = __fadd_rn(s, se);
+  return {h, __fsub_rn(se, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ dfl dfl_neg(dfl a) { return {-a.h, -a.l}; }
+
 template <typename T> struct V2;
 template <> struct V2<double> { using t = double2; };
 template <> struct V2<float> { using t = float2; };
+struct dfl2 {
+  dfl x, y;
+};
+template <> struct V2<dfl> { using t = dfl2; };
+
+// FP64 value into the kernel's coefficient type
+template <typename T> __device__ __forceinline__ T coeff_of(double x) { return (T)x; }
+template <> __device__ __forceinline__ dfl coeff_of<dfl>(double x) { return dfl_of(x); }
 
 // Block s, step m = m_begin + s: cf[s][k] = (2 d_k, 2 e'_k) and rot[s][k] = (cos, sin) theta_k,
 // theta_k = sum_{j<k} phi_j, for k < ld (rows >= n: zero operator).  The prefix sum runs over
@@ -55,8 +95,8 @@ __global__ void __launch_bounds__(GAUGE_NT) k_gauge_tile(GaugeArgs p, int ld, in
       double sp, cp, st, ct;
       sincos(ph, &sp, &cp);
       sincos(th, &st, &ct);
-      cfs[k] = {(T)(2.0 * d), (T)(2.0 * (er * cp + ei * sp))};
-      rts[k] = {(T)ct, (T)st};
+      cfs[k] = {coeff_of<T>(2.0 * d), coeff_of<T>(2.0 * (er * cp + ei * sp))};
+      rts[k] = {coeff_of<T>(ct), coeff_of<T>(st)};
     }
     if (threadIdx.x == GAUGE_NT - 1) chunk_total = th - carry + ph;
     __syncthreads();
@@ -213,6 +253,202 @@ k_tri_tile(const typename V2<T>::t* __restrict__ cf, const typename V2<T>::t* __
   if (bad) atomicOr(status, FQ_BIT_BOUND);
 }
 
+// ---------------------------------------------------------------------------- double-float
+struct DflTile {
+  static constexpr int NW = TILE_NT / 32;
+  dfl2* slot_last;   // [2][NW]
+  dfl2* slot_first;  // [2][NW]
+  int lane, warp;
+
+  __device__ __forceinline__ static dfl2 shfl(dfl2 a, int delta, bool up) {
+    dfl2 r;
+    if (up) {
+      r.x.h = __shfl_up_sync(0xffffffffu, a.x.h, delta);
+      r.x.l = __shfl_up_sync(0xffffffffu, a.x.l, delta);
+      r.y.h = __shfl_up_sync(0xffffffffu, a.y.h, delta);
+      r.y.l = __shfl_up_sync(0xffffffffu, a.y.l, delta);
+    } else {
+      r.x.h = __shfl_down_sync(0xffffffffu, a.x.h, delta);
+      r.x.l = __shfl_down_sync(0xffffffffu, a.x.l, delta);
+      r.y.h = __shfl_down_sync(0xffffffffu, a.y.h, delta);
+      r.y.l = __shfl_down_sync(0xffffffffu, a.y.l, delta);
+    }
+    return r;
+  }
+
+  __device__ __forceinline__ void halo(const dfl2 (&x)[TILE_EPT], int par, dfl2& left, dfl2& right) {
+    dfl2 l = shfl(x[TILE_EPT - 1], 1, true);
+    dfl2 r = shfl(x[0], 1, false);
+    if (lane == 31) slot_last[par * NW + warp] = x[TILE_EPT - 1];
+    if (lane == 0) slot_first[par * NW + warp] = x[0];
+    __syncthreads();
+    const dfl2 z = {{0.f, 0.f}, {0.f, 0.f}};
+    if (lane == 0) l = warp > 0 ? slot_last[par * NW + warp - 1] : z;
+    if (lane == 31) r = warp < NW - 1 ? slot_first[par * NW + warp + 1] : z;
+    left = l;
+    right = r;
+  }
+
+  // out = c v + (2 Omega' x) - out, or with Omega' x (HALF); c = cc or i cc (IM); all double-float
+  template <bool IM, bool HALF>
+  __device__ __forceinline__ void apply(const dfl2 (&x)[TILE_EPT], dfl2 (&out)[TILE_EPT], const dfl2 (&v)[TILE_EPT],
+                                        const dfl (&d)[TILE_EPT], const dfl (&e)[TILE_EPT], dfl el0, dfl cc, int par) {
+    dfl2 left, right;
+    halo(x, par, left, right);
+#pragma unroll
+    for (int q = 0; q < TILE_EPT; ++q) {
+      const dfl2 xm = q == 0 ? left : x[q - 1];
+      const dfl2 xp = q == TILE_EPT - 1 ? right : x[q + 1];
+      const dfl el = q == 0 ? el0 : e[q - 1];
+      dfl ar, ai;
+      if (HALF) {  // c v - out + (1/2)(2 Omega' x): the stored operator entries are halved exactly
+        const dfl hd = {0.5f * d[q].h, 0.5f * d[q].l}, hl = {0.5f * el.h, 0.5f * el.l};
+        const dfl he = {0.5f * e[q].h, 0.5f * e[q].l};
+        ar = dfl_fma(hd, x[q].x, dfl_fma(hl, xm.x, dfl_fma(he, xp.x, dfl_neg(out[q].x))));
+        ai = dfl_fma(hd, x[q].y, dfl_fma(hl, xm.y, dfl_fma(he, xp.y, dfl_neg(out[q].y))));
+      } else {
+        ar = dfl_fma(d[q], x[q].x, dfl_fma(el, xm.x, dfl_fma(e[q], xp.x, dfl_neg(out[q].x))));
+        ai = dfl_fma(d[q], x[q].y, dfl_fma(el, xm.y, dfl_fma(e[q], xp.y, dfl_neg(out[q].y))));
+      }
+      if (IM) {
+        out[q] = {dfl_fma(dfl_neg(cc), v[q].y, ar), dfl_fma(cc, v[q].x, ai)};
+      } else {
+        out[q] = {dfl_fma(cc, v[q].x, ar), dfl_fma(cc, v[q].y, ai)};
+      }
+    }
+  }
+};
+
+struct DflCoef {
+  dfl c[TILE_MAXL + 1];  // as TileCoef: c_k = c[k] (even k) or i c[k] (odd k)
+};
+
+// One step of the double-float tiled chain; states FP64 planar in HBM.
+__global__ void __launch_bounds__(TILE_NT)
+k_tri_tile_dfl(const dfl2* __restrict__ cf, const dfl2* __restrict__ rot, const double* __restrict__ xr,
+               const double* __restrict__ xi, double* __restrict__ yr, double* __restrict__ yi, int n, int ld, int L,
+               int seg, DflCoef coef, double ph_re, double ph_im, double bound2, unsigned int* status) {
+  __shared__ dfl2 slots[4 * DflTile::NW];
+  DflTile tl;
+  tl.slot_last = slots;
+  tl.slot_first = slots + 2 * DflTile::NW;
+  tl.lane = threadIdx.x & 31;
+  tl.warp = threadIdx.x >> 5;
+  const size_t j = blockIdx.y;
+  const int first = blockIdx.x * seg;
+  const int i0 = first - L + (int)threadIdx.x * TILE_EPT;
+  const dfl zero = {0.f, 0.f};
+  dfl2 v[TILE_EPT], A[TILE_EPT], B[TILE_EPT];
+  dfl d[TILE_EPT], e[TILE_EPT];
+#pragma unroll
+  for (int q = 0; q < TILE_EPT; ++q) {
+    const int i = i0 + q;
+    if (i >= 0 && i < n) {
+      const double x_r = xr[j * ld + i], x_i = xi[j * ld + i];
+      const dfl2 r = rot[i], c = cf[i];
+      const double rc = dfl_value(r.x), rs = dfl_value(r.y);
+      v[q] = {dfl_of(rc * x_r + rs * x_i), dfl_of(rc * x_i - rs * x_r)};  // D^+ x, formed in FP64
+      d[q] = c.x;
+      e[q] = c.y;
+    } else {
+      v[q] = {zero, zero};
+      d[q] = zero;
+      e[q] = zero;
+    }
+  }
+  dfl el0;
+  el0.h = __shfl_up_sync(0xffffffffu, e[TILE_EPT - 1].h, 1);
+  el0.l = __shfl_up_sync(0xffffffffu, e[TILE_EPT - 1].l, 1);
+  if (tl.lane == 0) {
+    el0 = zero;
+    if (i0 > 0 && i0 - 1 < n) el0 = cf[i0 - 1].y;
+  }
+  const dfl cL = coef.c[L];
+#pragma unroll
+  for (int q = 0; q < TILE_EPT; ++q) {
+    // c_L v as a double-float product (L odd: i cL v = (-cL v_im, cL v_re))
+    if (L & 1) A[q] = {dfl_fma(dfl_neg(cL), v[q].y, zero), dfl_fma(cL, v[q].x, zero)};
+    else A[q] = {dfl_fma(cL, v[q].x, zero), dfl_fma(cL, v[q].y, zero)};
+    B[q] = {zero, zero};
+  }
+  int k = L - 1, par = 0;
+  while (k >= 2) {
+    if (k & 1) tl.apply<true, false>(A, B, v, d, e, el0, coef.c[k], par);
+    else tl.apply<false, false>(A, B, v, d, e, el0, coef.c[k], par);
+    par ^= 1;
+    --k;
+    if (k & 1) tl.apply<true, false>(B, A, v, d, e, el0, coef.c[k], par);
+    else tl.apply<false, false>(B, A, v, d, e, el0, coef.c[k], par);
+    par ^= 1;
+    --k;
+  }
+  if (k == 1) {
+    tl.apply<true, false>(A, B, v, d, e, el0, coef.c[1], par);
+    par ^= 1;
+    tl.apply<false, true>(B, A, v, d, e, el0, coef.c[0], par);
+  } else {
+    tl.apply<false, true>(A, B, v, d, e, el0, coef.c[0], par);
+#pragma unroll
+    for (int q = 0; q < TILE_EPT; ++q) A[q] = B[q];
+  }
+  bool bad = false;
+#pragma unroll
+  for (int q = 0; q < TILE_EPT; ++q) {
+    const int i = i0 + q;
+    if (i >= first && i < first + seg && i < n) {
+      const double sr = dfl_value(A[q].x), si = dfl_value(A[q].y);
+      const double y_r = ph_re * sr - ph_im * si, y_i = ph_re * si + ph_im * sr;
+      const dfl2 r = rot[i];
+      const double rc = dfl_value(r.x), rs = dfl_value(r.y);
+      const double o_r = rc * y_r - rs * y_i, o_i = rc * y_i + rs * y_r;
+      bad |= !(o_r * o_r + o_i * o_i <= bound2);
+      yr[j * ld + i] = o_r;
+      yi[j * ld + i] = o_i;
+    }
+  }
+  if (bad) atomicOr(status, FQ_BIT_BOUND);
+}
+
+fq_status dfl_chain(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
+                    int transpose_out, void* ws, cudaStream_t s) {
+  const int n = p->n, ld = (n + 3) & ~3, nsteps = m_end - m_begin, L = p->L;
+  const int seg = TILE_ROWS - 2 * L;
+  dfl2* cf = (dfl2*)ws;
+  dfl2* rot = cf + (size_t)nsteps * ld;
+  double* bufs = (double*)(rot + (size_t)nsteps * ld);
+  const size_t plane = (size_t)nc * ld;
+  fq_blk<double> b[2] = {{bufs, bufs + plane}, {bufs + 2 * plane, bufs + 3 * plane}};
+  GaugeArgs ga{p->n, p->steps, p->d_h0, p->d_h0o, p->d_h1, p->d_k, p->d_scal, p->sbeta};
+  k_gauge_tile<dfl><<<nsteps, GAUGE_NT, 0, s>>>(ga, ld, m_begin, cf, rot);
+  if (identity) fq_launch_identity_f64(b[0], nc, n, ld, s);
+  else fq_launch_load_states(x0, b[0], nc, n, ld, s);
+  DflCoef coef{};
+  for (int k = 0; k <= L; ++k) {
+    const double a = p->cheb[k];
+    const double c = (k & 3) == 0 || (k & 3) == 3 ? a : -a;
+    const float h = (float)c;
+    coef.c[k] = {h, (float)(c - (double)h)};
+  }
+  const int segs = (n + seg - 1) / seg;
+  int cur = 0;
+  for (int m = 0; m < nsteps; ++m) {
+    for (int r0 = 0; r0 < nc; r0 += 65535) {
+      const int rows = nc - r0 < 65535 ? nc - r0 : 65535;
+      const size_t o = (size_t)r0 * ld;
+      k_tri_tile_dfl<<<dim3(segs, rows), TILE_NT, 0, s>>>(cf + (size_t)m * ld, rot + (size_t)m * ld, b[cur].re + o,
+                                                          b[cur].im + o, b[cur ^ 1].re + o, b[cur ^ 1].im + o, n, ld,
+                                                          L, seg, coef, p->phase_re, p->phase_im, 1.0 + 1e-9,
+                                                          p->d_status);
+    }
+    cur ^= 1;
+  }
+  if (transpose_out) fq_launch_store_transpose_f64(b[cur], x, n, ld, s);
+  else fq_launch_store_states_f64(b[cur], x, nc, n, ld, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fq_cuda_fail(e, "double-float tiled chain");
+  return FQ_OK;
+}
+
 // state load / store helpers of the streaming path, by precision
 void load_block(const double* x0, fq_blk<double> b, int nc, int n, int ld, cudaStream_t s) {
   fq_launch_load_states(x0, b, nc, n, ld, s);
@@ -283,8 +519,10 @@ fq_status tile_chain(fq_plan* p, const double* x0, double* x, int nc, int m_begi
 int fq_tile_supported(int L) { return L >= 1 && L <= TILE_MAXL && 2 * L < TILE_ROWS / 2; }
 
 size_t fq_tile_workspace(const fq_plan* p, int nc, int nsteps) {
-  const size_t es = p->precision == FQ_FP64 ? sizeof(double) : sizeof(float);
   const size_t ld = (p->n + 3) & ~3;
+  if (p->precision == FQ_DF32)  // double-float coefficients (16 B a pair), FP64 states
+    return 2 * (size_t)nsteps * ld * sizeof(dfl2) + 4 * (size_t)nc * ld * sizeof(double);
+  const size_t es = p->precision == FQ_FP64 ? sizeof(double) : sizeof(float);
   return 2 * (size_t)nsteps * ld * 2 * es + 4 * (size_t)nc * ld * es;
 }
 
@@ -292,5 +530,6 @@ fq_status fq_tile_propagate(fq_plan* p, const double* x0, double* x, int nc, int
                             int transpose_out, void* ws, cudaStream_t s) {
   if (p->precision == FQ_FP64)
     return tile_chain<double>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s);
+  if (p->precision == FQ_DF32) return dfl_chain(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s);
   return tile_chain<float>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s);
 }

@@ -99,16 +99,17 @@ def dimer_plan(fq, d, precision, kernel=0):
                            kernel=kernel)
 
 
-@pytest.mark.parametrize("precision,kernel", [(0, 1), (1, 1), (1, 2), (0, 3), (1, 3)])
+@pytest.mark.parametrize("precision,kernel", [(0, 1), (1, 1), (1, 2), (0, 3), (1, 3), (4, 3), (4, 0)])
 def test_dimer40_all_paths(fq, precision, kernel):
-    """Small dimer (dim 41, M = 100): FP64 / FP32 streaming, FP32 resident, FP64 / FP32 tiled."""
+    """Small dimer (dim 41, M = 100): FP64 / FP32 streaming, FP32 resident, FP64 / FP32 tiled,
+    double-float tiled (explicit and by AUTO)."""
     d = fi.config_dimer(nb=40, steps=100)
     plan = dimer_plan(fq, d, precision, kernel)
     U = to_np(plan.build_UT())
     assert plan.check_status() == fq.FQ_OK
     ref = o.build_ut_tridiag(d.h0_diag, d.h0_off, d.h1_diag,
                              o.plan_for_drive_tridiag(d.h0_diag, d.h0_off, d.h1_diag, d.drive, d.steps))
-    tol = 1e-10 if precision == 0 else tol_f32(d.steps, plan.info.L, plan.info.R)
+    tol = tol_f32(d.steps, plan.info.L, plan.info.R) if precision == 1 else 1e-10
     assert np.max(np.abs(U - ref)) <= tol
 
 
@@ -269,7 +270,7 @@ def test_paper_dimer_parameters(fq, precision, kernel):
 
 
 @pytest.mark.parametrize("precision,nb,m_end", [(0, 3000, 6), (1, 3000, 6), (0, 10000, 3), (1, 12000, 3),
-                                                 (0, 2011, 4), (0, 2012, 4)])
+                                                 (0, 2011, 4), (0, 2012, 4), (4, 3000, 6), (4, 10000, 3)])
 def test_dimer_tiled_kernel_segments(fq, precision, nb, m_end):
     """Tiled chain (one launch per step, L halo rows a side): several segments with a ragged tail
     (dim 3001, 10001), FP32 beyond the resident kernel's 10240 rows (dim 12001), and dims at one
@@ -289,7 +290,7 @@ def test_dimer_tiled_kernel_segments(fq, precision, nb, m_end):
     assert plan.check_status() == fq.FQ_OK
     refp = o.plan_for_drive_tridiag(d.h0_diag, d.h0_off, d.h1_diag, d.drive, d.steps)
     ref = o.propagate_tridiag(d.h0_diag, d.h0_off, d.h1_diag, refp, x0.T, 1, m_end).T
-    tol = 1e-10 if precision == 0 else tol_f32(m_end - 1, plan.info.L, plan.info.R)
+    tol = tol_f32(m_end - 1, plan.info.L, plan.info.R) if precision == 1 else 1e-10
     assert np.max(np.abs(X - ref)) <= tol
 
 
@@ -301,3 +302,21 @@ def test_tiled_kernel_rejects_long_series(fq):
     with pytest.raises(fq.FloquetError) as e:
         fq.floquet_plan_create(prob)
     assert e.value.status == fq.FQ_EUNSUPPORTED
+
+
+@pytest.mark.slow
+def test_dimer_full_size_double_float_sampled_columns(fq):
+    """The benchmark dimer (dim 10001, M = 2000, L = 39) built in double-float on the tiled kernel:
+    sampled columns against the FP64 oracle at the FP64 tolerance 1e-10."""
+    cols = [0, 5000, 10000]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(cols)) as pool:
+        pending = pool.map_async(_oracle_dimer_column, cols)
+        d = fi.config_dimer()
+        plan = dimer_plan(fq, d, fq.FQ_DF32, 0)
+        U = plan.build_UT()
+        assert plan.check_status() == fq.FQ_OK
+        ref = np.stack(pending.get(timeout=1800), axis=1)
+    err = np.max(np.abs(to_np(U[:, cols]) - ref))
+    print(f"dimer 10001 double-float tiled: max err {err:.3e}")
+    assert err <= 1e-10
