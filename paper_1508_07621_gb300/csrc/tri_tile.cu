@@ -254,35 +254,67 @@ k_tri_tile(const typename V2<T>::t* __restrict__ cf, const typename V2<T>::t* __
 }
 
 // ---------------------------------------------------------------------------- double-float
+// A complex double-float value packed for FP32x2 arithmetic: h = (re.hi, im.hi), l = (re.lo, im.lo).
+// A real operator entry acts on the real and imaginary parts alike, so every double-float FMA of
+// the step runs on both components at once with packed FFMA2 / FADD2 / FMUL2.
+struct dflc {
+  float2 h, l;
+};
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// a * x + c for a real double-float a and complex double-float x, c
+__device__ __forceinline__ dflc dflc_fma(dfl a, dflc x, dflc c) {
+  const float2 ah = make_float2(a.h, a.h), al = make_float2(a.l, a.l);
+  const float2 p = __fmul2_rn(ah, x.h);
+  float2 pe = __ffma2_rn(ah, x.h, neg2(p));
+  pe = __ffma2_rn(ah, x.l, __ffma2_rn(al, x.h, pe));
+  const float2 sm = __fadd2_rn(p, c.h);
+  const float2 bb = __fadd2_rn(sm, neg2(p));
+  float2 se = __fadd2_rn(__fadd2_rn(p, neg2(__fadd2_rn(sm, neg2(bb)))), __fadd2_rn(c.h, neg2(bb)));
+  se = __fadd2_rn(se, __fadd2_rn(pe, c.l));
+  const float2 h = __fadd2_rn(sm, se);
+  return {h, __fadd2_rn(se, neg2(__fadd2_rn(h, neg2(sm))))};
+}
+
+// i cc * v + c: (-cc v_im, cc v_re) + c, one component at a time
+__device__ __forceinline__ dflc dflc_ifma(dfl cc, dflc v, dflc c) {
+  const dfl r = dfl_fma(dfl_neg(cc), dfl{v.h.y, v.l.y}, dfl{c.h.x, c.l.x});
+  const dfl i = dfl_fma(cc, dfl{v.h.x, v.l.x}, dfl{c.h.y, c.l.y});
+  return {make_float2(r.h, i.h), make_float2(r.l, i.l)};
+}
+
+__device__ __forceinline__ dflc dflc_neg(dflc a) { return {neg2(a.h), neg2(a.l)}; }
+
 struct DflTile {
   static constexpr int NW = TILE_NT / 32;
-  dfl2* slot_last;   // [2][NW]
-  dfl2* slot_first;  // [2][NW]
+  dflc* slot_last;   // [2][NW]
+  dflc* slot_first;  // [2][NW]
   int lane, warp;
 
-  __device__ __forceinline__ static dfl2 shfl(dfl2 a, int delta, bool up) {
-    dfl2 r;
+  __device__ __forceinline__ static dflc shfl(dflc a, bool up) {
+    dflc r;
     if (up) {
-      r.x.h = __shfl_up_sync(0xffffffffu, a.x.h, delta);
-      r.x.l = __shfl_up_sync(0xffffffffu, a.x.l, delta);
-      r.y.h = __shfl_up_sync(0xffffffffu, a.y.h, delta);
-      r.y.l = __shfl_up_sync(0xffffffffu, a.y.l, delta);
+      r.h.x = __shfl_up_sync(0xffffffffu, a.h.x, 1);
+      r.h.y = __shfl_up_sync(0xffffffffu, a.h.y, 1);
+      r.l.x = __shfl_up_sync(0xffffffffu, a.l.x, 1);
+      r.l.y = __shfl_up_sync(0xffffffffu, a.l.y, 1);
     } else {
-      r.x.h = __shfl_down_sync(0xffffffffu, a.x.h, delta);
-      r.x.l = __shfl_down_sync(0xffffffffu, a.x.l, delta);
-      r.y.h = __shfl_down_sync(0xffffffffu, a.y.h, delta);
-      r.y.l = __shfl_down_sync(0xffffffffu, a.y.l, delta);
+      r.h.x = __shfl_down_sync(0xffffffffu, a.h.x, 1);
+      r.h.y = __shfl_down_sync(0xffffffffu, a.h.y, 1);
+      r.l.x = __shfl_down_sync(0xffffffffu, a.l.x, 1);
+      r.l.y = __shfl_down_sync(0xffffffffu, a.l.y, 1);
     }
     return r;
   }
 
-  __device__ __forceinline__ void halo(const dfl2 (&x)[TILE_EPT], int par, dfl2& left, dfl2& right) {
-    dfl2 l = shfl(x[TILE_EPT - 1], 1, true);
-    dfl2 r = shfl(x[0], 1, false);
+  __device__ __forceinline__ void halo(const dflc (&x)[TILE_EPT], int par, dflc& left, dflc& right) {
+    dflc l = shfl(x[TILE_EPT - 1], true);
+    dflc r = shfl(x[0], false);
     if (lane == 31) slot_last[par * NW + warp] = x[TILE_EPT - 1];
     if (lane == 0) slot_first[par * NW + warp] = x[0];
     __syncthreads();
-    const dfl2 z = {{0.f, 0.f}, {0.f, 0.f}};
+    const dflc z = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     if (lane == 0) l = warp > 0 ? slot_last[par * NW + warp - 1] : z;
     if (lane == 31) r = warp < NW - 1 ? slot_first[par * NW + warp + 1] : z;
     left = l;
@@ -291,30 +323,22 @@ struct DflTile {
 
   // out = c v + (2 Omega' x) - out, or with Omega' x (HALF); c = cc or i cc (IM); all double-float
   template <bool IM, bool HALF>
-  __device__ __forceinline__ void apply(const dfl2 (&x)[TILE_EPT], dfl2 (&out)[TILE_EPT], const dfl2 (&v)[TILE_EPT],
+  __device__ __forceinline__ void apply(const dflc (&x)[TILE_EPT], dflc (&out)[TILE_EPT], const dflc (&v)[TILE_EPT],
                                         const dfl (&d)[TILE_EPT], const dfl (&e)[TILE_EPT], dfl el0, dfl cc, int par) {
-    dfl2 left, right;
+    dflc left, right;
     halo(x, par, left, right);
 #pragma unroll
     for (int q = 0; q < TILE_EPT; ++q) {
-      const dfl2 xm = q == 0 ? left : x[q - 1];
-      const dfl2 xp = q == TILE_EPT - 1 ? right : x[q + 1];
-      const dfl el = q == 0 ? el0 : e[q - 1];
-      dfl ar, ai;
-      if (HALF) {  // c v - out + (1/2)(2 Omega' x): the stored operator entries are halved exactly
-        const dfl hd = {0.5f * d[q].h, 0.5f * d[q].l}, hl = {0.5f * el.h, 0.5f * el.l};
-        const dfl he = {0.5f * e[q].h, 0.5f * e[q].l};
-        ar = dfl_fma(hd, x[q].x, dfl_fma(hl, xm.x, dfl_fma(he, xp.x, dfl_neg(out[q].x))));
-        ai = dfl_fma(hd, x[q].y, dfl_fma(hl, xm.y, dfl_fma(he, xp.y, dfl_neg(out[q].y))));
-      } else {
-        ar = dfl_fma(d[q], x[q].x, dfl_fma(el, xm.x, dfl_fma(e[q], xp.x, dfl_neg(out[q].x))));
-        ai = dfl_fma(d[q], x[q].y, dfl_fma(el, xm.y, dfl_fma(e[q], xp.y, dfl_neg(out[q].y))));
+      const dflc xm = q == 0 ? left : x[q - 1];
+      const dflc xp = q == TILE_EPT - 1 ? right : x[q + 1];
+      dfl dq = d[q], el = q == 0 ? el0 : e[q - 1], eh = e[q];
+      if (HALF) {  // the closing sum uses Omega' = (stored operator) / 2, halved exactly
+        dq = {0.5f * dq.h, 0.5f * dq.l};
+        el = {0.5f * el.h, 0.5f * el.l};
+        eh = {0.5f * eh.h, 0.5f * eh.l};
       }
-      if (IM) {
-        out[q] = {dfl_fma(dfl_neg(cc), v[q].y, ar), dfl_fma(cc, v[q].x, ai)};
-      } else {
-        out[q] = {dfl_fma(cc, v[q].x, ar), dfl_fma(cc, v[q].y, ai)};
-      }
+      const dflc acc = dflc_fma(dq, x[q], dflc_fma(el, xm, dflc_fma(eh, xp, dflc_neg(out[q]))));
+      out[q] = IM ? dflc_ifma(cc, v[q], acc) : dflc_fma(cc, v[q], acc);
     }
   }
 };
@@ -328,7 +352,7 @@ __global__ void __launch_bounds__(TILE_NT)
 k_tri_tile_dfl(const dfl2* __restrict__ cf, const dfl2* __restrict__ rot, const double* __restrict__ xr,
                const double* __restrict__ xi, double* __restrict__ yr, double* __restrict__ yi, int n, int ld, int L,
                int seg, DflCoef coef, double ph_re, double ph_im, double bound2, unsigned int* status) {
-  __shared__ dfl2 slots[4 * DflTile::NW];
+  __shared__ dflc slots[4 * DflTile::NW];
   DflTile tl;
   tl.slot_last = slots;
   tl.slot_first = slots + 2 * DflTile::NW;
@@ -338,7 +362,8 @@ k_tri_tile_dfl(const dfl2* __restrict__ cf, const dfl2* __restrict__ rot, const 
   const int first = blockIdx.x * seg;
   const int i0 = first - L + (int)threadIdx.x * TILE_EPT;
   const dfl zero = {0.f, 0.f};
-  dfl2 v[TILE_EPT], A[TILE_EPT], B[TILE_EPT];
+  const dflc zc = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  dflc v[TILE_EPT], A[TILE_EPT], B[TILE_EPT];
   dfl d[TILE_EPT], e[TILE_EPT];
 #pragma unroll
   for (int q = 0; q < TILE_EPT; ++q) {
@@ -347,11 +372,12 @@ k_tri_tile_dfl(const dfl2* __restrict__ cf, const dfl2* __restrict__ rot, const 
       const double x_r = xr[j * ld + i], x_i = xi[j * ld + i];
       const dfl2 r = rot[i], c = cf[i];
       const double rc = dfl_value(r.x), rs = dfl_value(r.y);
-      v[q] = {dfl_of(rc * x_r + rs * x_i), dfl_of(rc * x_i - rs * x_r)};  // D^+ x, formed in FP64
+      const dfl vr = dfl_of(rc * x_r + rs * x_i), vi = dfl_of(rc * x_i - rs * x_r);  // D^+ x in FP64
+      v[q] = {make_float2(vr.h, vi.h), make_float2(vr.l, vi.l)};
       d[q] = c.x;
       e[q] = c.y;
     } else {
-      v[q] = {zero, zero};
+      v[q] = zc;
       d[q] = zero;
       e[q] = zero;
     }
@@ -363,13 +389,12 @@ k_tri_tile_dfl(const dfl2* __restrict__ cf, const dfl2* __restrict__ rot, const 
     el0 = zero;
     if (i0 > 0 && i0 - 1 < n) el0 = cf[i0 - 1].y;
   }
+  // b_L = c_L v (L odd: i cL v)
   const dfl cL = coef.c[L];
 #pragma unroll
   for (int q = 0; q < TILE_EPT; ++q) {
-    // c_L v as a double-float product (L odd: i cL v = (-cL v_im, cL v_re))
-    if (L & 1) A[q] = {dfl_fma(dfl_neg(cL), v[q].y, zero), dfl_fma(cL, v[q].x, zero)};
-    else A[q] = {dfl_fma(cL, v[q].x, zero), dfl_fma(cL, v[q].y, zero)};
-    B[q] = {zero, zero};
+    A[q] = (L & 1) ? dflc_ifma(cL, v[q], zc) : dflc_fma(cL, v[q], zc);
+    B[q] = zc;
   }
   int k = L - 1, par = 0;
   while (k >= 2) {
@@ -396,7 +421,7 @@ k_tri_tile_dfl(const dfl2* __restrict__ cf, const dfl2* __restrict__ rot, const 
   for (int q = 0; q < TILE_EPT; ++q) {
     const int i = i0 + q;
     if (i >= first && i < first + seg && i < n) {
-      const double sr = dfl_value(A[q].x), si = dfl_value(A[q].y);
+      const double sr = (double)A[q].h.x + (double)A[q].l.x, si = (double)A[q].h.y + (double)A[q].l.y;
       const double y_r = ph_re * sr - ph_im * si, y_i = ph_re * si + ph_im * sr;
       const dfl2 r = rot[i];
       const double rc = dfl_value(r.x), rs = dfl_value(r.y);
