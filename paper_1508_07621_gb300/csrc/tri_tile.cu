@@ -254,6 +254,11 @@ k_tri_tile(const typename V2<T>::t* __restrict__ cf, const typename V2<T>::t* __
 }
 
 // ---------------------------------------------------------------------------- double-float
+// 4 rows a thread keep the registers under 128, so two CTAs (16 warps) share an SM: the
+// double-float FMA chains are long, and latency, not the FP32 pipe, limits one CTA per SM.
+constexpr int DFL_NT = 256;
+constexpr int DFL_EPT = 4;
+constexpr int DFL_ROWS = DFL_NT * DFL_EPT;
 // A complex double-float value packed for FP32x2 arithmetic: h = (re.hi, im.hi), l = (re.lo, im.lo).
 // A real operator entry acts on the real and imaginary parts alike, so every double-float FMA of
 // the step runs on both components at once with packed FFMA2 / FADD2 / FMUL2.
@@ -287,7 +292,7 @@ __device__ __forceinline__ dflc dflc_ifma(dfl cc, dflc v, dflc c) {
 __device__ __forceinline__ dflc dflc_neg(dflc a) { return {neg2(a.h), neg2(a.l)}; }
 
 struct DflTile {
-  static constexpr int NW = TILE_NT / 32;
+  static constexpr int NW = DFL_NT / 32;
   dflc* slot_last;   // [2][NW]
   dflc* slot_first;  // [2][NW]
   int lane, warp;
@@ -308,10 +313,10 @@ struct DflTile {
     return r;
   }
 
-  __device__ __forceinline__ void halo(const dflc (&x)[TILE_EPT], int par, dflc& left, dflc& right) {
-    dflc l = shfl(x[TILE_EPT - 1], true);
+  __device__ __forceinline__ void halo(const dflc (&x)[DFL_EPT], int par, dflc& left, dflc& right) {
+    dflc l = shfl(x[DFL_EPT - 1], true);
     dflc r = shfl(x[0], false);
-    if (lane == 31) slot_last[par * NW + warp] = x[TILE_EPT - 1];
+    if (lane == 31) slot_last[par * NW + warp] = x[DFL_EPT - 1];
     if (lane == 0) slot_first[par * NW + warp] = x[0];
     __syncthreads();
     const dflc z = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
@@ -323,14 +328,14 @@ struct DflTile {
 
   // out = c v + (2 Omega' x) - out, or with Omega' x (HALF); c = cc or i cc (IM); all double-float
   template <bool IM, bool HALF>
-  __device__ __forceinline__ void apply(const dflc (&x)[TILE_EPT], dflc (&out)[TILE_EPT], const dflc (&v)[TILE_EPT],
-                                        const dfl (&d)[TILE_EPT], const dfl (&e)[TILE_EPT], dfl el0, dfl cc, int par) {
+  __device__ __forceinline__ void apply(const dflc (&x)[DFL_EPT], dflc (&out)[DFL_EPT], const dflc (&v)[DFL_EPT],
+                                        const dfl (&d)[DFL_EPT], const dfl (&e)[DFL_EPT], dfl el0, dfl cc, int par) {
     dflc left, right;
     halo(x, par, left, right);
 #pragma unroll
-    for (int q = 0; q < TILE_EPT; ++q) {
+    for (int q = 0; q < DFL_EPT; ++q) {
       const dflc xm = q == 0 ? left : x[q - 1];
-      const dflc xp = q == TILE_EPT - 1 ? right : x[q + 1];
+      const dflc xp = q == DFL_EPT - 1 ? right : x[q + 1];
       dfl dq = d[q], el = q == 0 ? el0 : e[q - 1], eh = e[q];
       if (HALF) {  // the closing sum uses Omega' = (stored operator) / 2, halved exactly
         dq = {0.5f * dq.h, 0.5f * dq.l};
@@ -348,7 +353,7 @@ struct DflCoef {
 };
 
 // One step of the double-float tiled chain; states FP64 planar in HBM.
-__global__ void __launch_bounds__(TILE_NT)
+__global__ void __launch_bounds__(DFL_NT, 2)
 k_tri_tile_dfl(const dfl2* __restrict__ cf, const dfl2* __restrict__ rot, const double* __restrict__ xr,
                const double* __restrict__ xi, double* __restrict__ yr, double* __restrict__ yi, int n, int ld, int L,
                int seg, DflCoef coef, double ph_re, double ph_im, double bound2, unsigned int* status) {
@@ -360,13 +365,13 @@ k_tri_tile_dfl(const dfl2* __restrict__ cf, const dfl2* __restrict__ rot, const 
   tl.warp = threadIdx.x >> 5;
   const size_t j = blockIdx.y;
   const int first = blockIdx.x * seg;
-  const int i0 = first - L + (int)threadIdx.x * TILE_EPT;
+  const int i0 = first - L + (int)threadIdx.x * DFL_EPT;
   const dfl zero = {0.f, 0.f};
   const dflc zc = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-  dflc v[TILE_EPT], A[TILE_EPT], B[TILE_EPT];
-  dfl d[TILE_EPT], e[TILE_EPT];
+  dflc v[DFL_EPT], A[DFL_EPT], B[DFL_EPT];
+  dfl d[DFL_EPT], e[DFL_EPT];
 #pragma unroll
-  for (int q = 0; q < TILE_EPT; ++q) {
+  for (int q = 0; q < DFL_EPT; ++q) {
     const int i = i0 + q;
     if (i >= 0 && i < n) {
       const double x_r = xr[j * ld + i], x_i = xi[j * ld + i];
@@ -383,8 +388,8 @@ k_tri_tile_dfl(const dfl2* __restrict__ cf, const dfl2* __restrict__ rot, const 
     }
   }
   dfl el0;
-  el0.h = __shfl_up_sync(0xffffffffu, e[TILE_EPT - 1].h, 1);
-  el0.l = __shfl_up_sync(0xffffffffu, e[TILE_EPT - 1].l, 1);
+  el0.h = __shfl_up_sync(0xffffffffu, e[DFL_EPT - 1].h, 1);
+  el0.l = __shfl_up_sync(0xffffffffu, e[DFL_EPT - 1].l, 1);
   if (tl.lane == 0) {
     el0 = zero;
     if (i0 > 0 && i0 - 1 < n) el0 = cf[i0 - 1].y;
@@ -392,7 +397,7 @@ k_tri_tile_dfl(const dfl2* __restrict__ cf, const dfl2* __restrict__ rot, const 
   // b_L = c_L v (L odd: i cL v)
   const dfl cL = coef.c[L];
 #pragma unroll
-  for (int q = 0; q < TILE_EPT; ++q) {
+  for (int q = 0; q < DFL_EPT; ++q) {
     A[q] = (L & 1) ? dflc_ifma(cL, v[q], zc) : dflc_fma(cL, v[q], zc);
     B[q] = zc;
   }
@@ -414,11 +419,11 @@ k_tri_tile_dfl(const dfl2* __restrict__ cf, const dfl2* __restrict__ rot, const 
   } else {
     tl.apply<false, true>(A, B, v, d, e, el0, coef.c[0], par);
 #pragma unroll
-    for (int q = 0; q < TILE_EPT; ++q) A[q] = B[q];
+    for (int q = 0; q < DFL_EPT; ++q) A[q] = B[q];
   }
   bool bad = false;
 #pragma unroll
-  for (int q = 0; q < TILE_EPT; ++q) {
+  for (int q = 0; q < DFL_EPT; ++q) {
     const int i = i0 + q;
     if (i >= first && i < first + seg && i < n) {
       const double sr = (double)A[q].h.x + (double)A[q].l.x, si = (double)A[q].h.y + (double)A[q].l.y;
@@ -437,7 +442,7 @@ k_tri_tile_dfl(const dfl2* __restrict__ cf, const dfl2* __restrict__ rot, const 
 fq_status dfl_chain(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
                     int transpose_out, void* ws, cudaStream_t s) {
   const int n = p->n, ld = (n + 3) & ~3, nsteps = m_end - m_begin, L = p->L;
-  const int seg = TILE_ROWS - 2 * L;
+  const int seg = DFL_ROWS - 2 * L;
   dfl2* cf = (dfl2*)ws;
   dfl2* rot = cf + (size_t)nsteps * ld;
   double* bufs = (double*)(rot + (size_t)nsteps * ld);
@@ -460,7 +465,7 @@ fq_status dfl_chain(fq_plan* p, const double* x0, double* x, int nc, int m_begin
     for (int r0 = 0; r0 < nc; r0 += 65535) {
       const int rows = nc - r0 < 65535 ? nc - r0 : 65535;
       const size_t o = (size_t)r0 * ld;
-      k_tri_tile_dfl<<<dim3(segs, rows), TILE_NT, 0, s>>>(cf + (size_t)m * ld, rot + (size_t)m * ld, b[cur].re + o,
+      k_tri_tile_dfl<<<dim3(segs, rows), DFL_NT, 0, s>>>(cf + (size_t)m * ld, rot + (size_t)m * ld, b[cur].re + o,
                                                           b[cur].im + o, b[cur ^ 1].re + o, b[cur ^ 1].im + o, n, ld,
                                                           L, seg, coef, p->phase_re, p->phase_im, 1.0 + 1e-9,
                                                           p->d_status);
