@@ -254,8 +254,8 @@ k_tri_tile(const typename V2<T>::t* __restrict__ cf, const typename V2<T>::t* __
 }
 
 // ---------------------------------------------------------------------------- double-float
-// 4 rows a thread keep the registers under 128, so two CTAs (16 warps) share an SM: the
-// double-float FMA chains are long, and latency, not the FP32 pipe, limits one CTA per SM.
+// 4 rows a thread and an 80-register cap (a few spills) let three CTAs (24 warps) share an SM:
+// the double-float FMA chains are long, and latency, not the FP32 pipe, limits fewer warps.
 constexpr int DFL_NT = 256;
 constexpr int DFL_EPT = 4;
 constexpr int DFL_ROWS = DFL_NT * DFL_EPT;
@@ -353,7 +353,7 @@ struct DflCoef {
 };
 
 // One step of the double-float tiled chain; states FP64 planar in HBM.
-__global__ void __launch_bounds__(DFL_NT, 2)
+__global__ void __launch_bounds__(DFL_NT, 3)
 k_tri_tile_dfl(const dfl2* __restrict__ cf, const dfl2* __restrict__ rot, const double* __restrict__ xr,
                const double* __restrict__ xi, double* __restrict__ yr, double* __restrict__ yi, int n, int ld, int L,
                int seg, DflCoef coef, double ph_re, double ph_im, double bound2, unsigned int* status) {
