@@ -158,6 +158,7 @@ def test_dimer_full_size_resident_sampled_columns(fq):
     err = np.max(np.abs(got - ref))
     print(f"dimer 10001 FP32 resident: max err {err:.3e} (tol {tol:.3e})")
     assert err <= tol
+    assert err <= 1e-5  # the accuracy target for FP32-level paths, tighter than the bound here
     sample = torch.arange(0, d.n, 157, dtype=torch.int32, device="cuda")
     mx, fro = fq.api.unitarity_defect(U, sample)
     assert mx <= 2 * tol
