@@ -234,7 +234,8 @@ fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
   *out = nullptr;
   fq_plan* p = new (std::nothrow) fq_plan();
   if (!p) { fq_set_error("host allocation failed"); return FQ_ENOMEM; }
-  fq_status st = fq_host_plan(prob, p);
+  // dense spectral bounds wait for H0, H1 on the device (their Lanczos products run there)
+  fq_status st = fq_host_plan(prob, p, prob && prob->format == FQ_DENSE);
   if (st != FQ_OK) { delete p; return st; }
   const int n = p->n, M = p->steps;
   if (p->format == FQ_TRIDIAG) {
@@ -281,6 +282,32 @@ fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
   if ((e = cudaMemset(p->d_status, 0, sizeof(unsigned int))) != cudaSuccess) return fail(e, "status clear");
   if ((e = cudaMemcpy(p->d_h0, prob->h0, opsz * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "upload H0");
   if ((e = cudaMemcpy(p->d_h1, prob->h1, opsz * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "upload H1");
+  if (p->dense_bounds_pending) {
+    // Lanczos on the device-resident H0, H1: each product reads the matrices at HBM rate, the
+    // n-vectors travel over the link (reading R4)
+    double *d_x = nullptr, *d_y = nullptr;
+    if ((e = cudaMalloc(&d_x, 2 * (size_t)n * sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc Lanczos");
+    d_y = d_x + n;
+    cudaError_t ae = cudaSuccess;
+    const fq_dense_apply apply = [&](int which, double g, const double* x, double* y) {
+      if (ae != cudaSuccess) {
+        std::fill(y, y + n, 0.0);
+        return;
+      }
+      ae = cudaMemcpy(d_x, x, (size_t)n * sizeof(double), cudaMemcpyHostToDevice);
+      if (ae == cudaSuccess) {
+        fq_launch_symv2(p->d_h0, p->d_h1, g, which, d_x, d_y, n, 0);
+        ae = cudaMemcpy(y, d_y, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost);
+      }
+      if (ae != cudaSuccess) std::fill(y, y + n, 0.0);
+    };
+    double emin, emax;
+    fq_dense_bounds(n, p->dense_glo, p->dense_ghi, p->dense_kmax, apply, &emin, &emax);
+    cudaFree(d_x);
+    if (ae != cudaSuccess) return fail(ae, "Lanczos products");
+    fq_finish_computed_bounds(p, emin, emax);
+    p->dense_bounds_pending = false;
+  }
   std::vector<double> scal(3 * (size_t)M);
   std::copy(p->sa.begin(), p->sa.end(), scal.begin());
   std::copy(p->sb.begin(), p->sb.end(), scal.begin() + M);

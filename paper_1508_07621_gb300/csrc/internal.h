@@ -9,6 +9,7 @@
 #include <vector>
 
 #include <atomic>
+#include <functional>
 
 #include "floquet.h"
 
@@ -53,6 +54,10 @@ struct fq_plan {
   double* d_k = nullptr;     // DENSE: [H0,H1] n*n   TRIDIAG: lower off-diagonal of [H0,H1], n-1
   double* d_h0o = nullptr;   // TRIDIAG: off-diagonal of H0, n-1
   double* d_scal = nullptr;  // 3*M: sa | sb | sc
+  // dense bounds left to the caller of fq_host_plan (plan creation runs them on the device):
+  // extremes of H0 + g H1 for g in [glo, ghi], widened by kmax ||[H0,H1]||_2
+  bool dense_bounds_pending = false;
+  double dense_glo = 0, dense_ghi = 0, dense_kmax = 0;
   unsigned int* d_status = nullptr;
   // dense split path: per-plan constants prepared once
   void* split = nullptr;
@@ -67,8 +72,22 @@ double fq_drive_f(int deriv, double f_dc, double f_ac, double omega, double phi0
 void fq_bessel_miller(double R, int L, double* out);    // J_0..J_L
 int fq_cheb_order(double R, double tol);
 void fq_tridiag_extremes(const double* diag, const double* off, int n, double* lo, double* hi);
-void fq_lanczos_extremes(const double* a, int n, int ksteps, uint64_t seed, double* lo, double* hi);
-fq_status fq_host_plan(const fq_problem* p, fq_plan* plan);   // everything but device work
+// y = A x for the operator whose extreme eigenvalues are wanted (host vectors of length n)
+using fq_matvec = std::function<void(const double* x, double* y)>;
+void fq_lanczos_extremes(const fq_matvec& mv, int n, int ksteps, uint64_t seed, double* lo, double* hi);
+// Extremes of H0 + g H1 over g in [glo, ghi], widened by kmax ||[H0,H1]||_2 (dense format):
+// apply(which, g, x, y) computes y = (H0 + g H1) x (which 0), H0 x (1) or H1 x (2).
+using fq_dense_apply = std::function<void(int which, double g, const double* x, double* y)>;
+void fq_dense_bounds(int n, double glo, double ghi, double kmax, const fq_dense_apply& apply, double* emin,
+                     double* emax);
+// everything but device work; with defer_dense_bounds the dense bounds (and what depends on
+// them) are left pending for the caller (see fq_plan::dense_bounds_pending)
+fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_bounds = false);
+// margins of computed bounds, then fq_finish_bounds
+void fq_finish_computed_bounds(fq_plan* plan, double emin, double emax);
+// y = (H0 + g H1) x (which 0), H0 x (1) or H1 x (2) for dense device H0, H1 (kernels.cu)
+void fq_launch_symv2(const double* h0, const double* h1, double g, int which, const double* x, double* y, int n,
+                     cudaStream_t s);
 // beta, Delta E, R, L, a_l, phase and the Omega~ scalars from bounds [emin, emax] of Omega/h
 void fq_finish_bounds(fq_plan* plan, double emin, double emax);
 constexpr int FQ_M6_TERMS = 11;

@@ -516,6 +516,34 @@ void fq_launch_term_tri_f32(const float* d, const float* er, const float* ei, in
   }
 }
 
+namespace {
+// y = (h0 + g h1) x (which 0), h0 x (1) or h1 x (2): dense row-major FP64, one warp per row
+// (the Lanczos matrix-vector products of the spectral bounds, stage a1)
+__global__ void k_symv2(const double* __restrict__ h0, const double* __restrict__ h1, double g, int which,
+                        const double* __restrict__ x, double* __restrict__ y, int n) {
+  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double* a = h0 + (size_t)row * n;
+  const double* b = h1 + (size_t)row * n;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) {
+    const double xv = x[j];
+    if (which == 0) s = fma(fma(g, b[j], a[j]), xv, s);
+    else if (which == 1) s = fma(a[j], xv, s);
+    else s = fma(b[j], xv, s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) y[row] = s;
+}
+
+}  // namespace
+
+void fq_launch_symv2(const double* h0, const double* h1, double g, int which, const double* x, double* y, int n,
+                     cudaStream_t s) {
+  k_symv2<<<(n + 7) / 8, 256, 0, s>>>(h0, h1, g, which, x, y, n);
+}
+
 void fq_launch_defect(const double* u, int n, const int32_t* cols, int k, double* partial, cudaStream_t s) {
   dim3 g((n + 255) / 256, (k + 15) / 16);
   k_defect<<<g, 256, 0, s>>>((const double2*)u, n, cols, k, partial);

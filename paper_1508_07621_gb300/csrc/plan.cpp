@@ -126,15 +126,24 @@ void fq_tridiag_extremes(const double* d, const double* e, int n, double* lo, do
   *hi = b;  // count(b) = n: every eigenvalue < b
 }
 
+// sum_i a[i] b[i] with four independent partial sums (the compiler may not reassociate one)
+static double dot4(const double* a, const double* b, int n) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int i = 0;
+  for (; i + 4 <= n; i += 4) {
+    s0 += a[i] * b[i];
+    s1 += a[i + 1] * b[i + 1];
+    s2 += a[i + 2] * b[i + 2];
+    s3 += a[i + 3] * b[i + 3];
+  }
+  for (; i < n; ++i) s0 += a[i] * b[i];
+  return (s0 + s1) + (s2 + s3);
+}
+
 // y = A x for a dense row-major symmetric A, rows split over host threads.
 static void matvec(const double* a, const double* x, double* y, int n, int nthreads) {
   auto work = [&](int r0, int r1) {
-    for (int i = r0; i < r1; ++i) {
-      const double* row = a + (size_t)i * n;
-      double s = 0.0;
-      for (int j = 0; j < n; ++j) s += row[j] * x[j];
-      y[i] = s;
-    }
+    for (int i = r0; i < r1; ++i) y[i] = dot4(a + (size_t)i * n, x, n);
   };
   if (nthreads <= 1 || n < 256) { work(0, n); return; }
   std::vector<std::thread> th;
@@ -146,62 +155,18 @@ static void matvec(const double* a, const double* x, double* y, int n, int nthre
   for (auto& t : th) t.join();
 }
 
-// Extreme eigenvalues of the dense symmetric A by the Lanczos method (Lanczos 1950) with
-// full reorthogonalisation.  Returned [lo, hi] is the Ritz interval widened by the residual
-// norms of the two extreme Ritz pairs (each such pair has an eigenvalue within its residual)
-// plus 1e-6 of the span; with k >= n it is exact up to rounding.
-void fq_lanczos_extremes(const double* a, int n, int ksteps, uint64_t seed, double* lo, double* hi) {
-  const int k = std::min(n, ksteps);
-  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  std::vector<double> V((size_t)(k + 1) * n), w(n), alpha(k), beta(k + 1, 0.0);
-  // start vector: splitmix64 uniforms in (-1, 1)
-  uint64_t s = seed;
-  double nrm = 0.0;
-  for (int i = 0; i < n; ++i) {
-    s += 0x9E3779B97F4A7C15ull;
-    uint64_t z = s;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    V[i] = ((double)(z >> 11) + 0.5) * (2.0 / 9007199254740992.0) - 1.0;
-    nrm += V[i] * V[i];
-  }
-  nrm = sqrt(nrm);
-  for (int i = 0; i < n; ++i) V[i] /= nrm;
-  int m = k;
-  for (int j = 0; j < k; ++j) {
-    double* vj = &V[(size_t)j * n];
-    matvec(a, vj, w.data(), n, (int)nt);
-    double al = 0.0;
-    for (int i = 0; i < n; ++i) al += w[i] * vj[i];
-    alpha[j] = al;
-    // full reorthogonalisation (twice is enough)
-    for (int pass = 0; pass < 2; ++pass)
-      for (int q = 0; q <= j; ++q) {
-        const double* vq = &V[(size_t)q * n];
-        double c = 0.0;
-        for (int i = 0; i < n; ++i) c += w[i] * vq[i];
-        for (int i = 0; i < n; ++i) w[i] -= c * vq[i];
-      }
-    double b = 0.0;
-    for (int i = 0; i < n; ++i) b += w[i] * w[i];
-    b = sqrt(b);
-    beta[j + 1] = b;
-    if (j + 1 == k) break;
-    if (b < 1e-13 * (fabs(al) + 1e-300)) { m = j + 1; break; }  // invariant subspace
-    double* vn = &V[(size_t)(j + 1) * n];
-    for (int i = 0; i < n; ++i) vn[i] = w[i] / b;
-  }
-  // Ritz values of T_m
+// Extreme Ritz values of the Lanczos tridiagonal T_m (alpha, beta[1..m-1]) and the residual
+// beta_m |s_{m-1}| of each extreme Ritz vector s (inverse iteration on T_m); a Ritz pair has an
+// eigenvalue of A within its residual.
+static void ritz_extremes(const std::vector<double>& alpha, const std::vector<double>& beta, int m, bool exact,
+                          double* tlo, double* thi, double* rlo, double* rhi) {
   std::vector<double> off(std::max(1, m - 1));
   for (int i = 0; i + 1 < m; ++i) off[i] = beta[i + 1];
-  double tlo, thi;
-  fq_tridiag_extremes(alpha.data(), off.data(), m, &tlo, &thi);
-  // residual beta_m |s_{m-1}| of each extreme Ritz vector s (inverse iteration on T_m)
-  auto resid = [&](double theta) {
-    if (m >= n) return 0.0;
+  fq_tridiag_extremes(alpha.data(), off.data(), m, tlo, thi);
+  auto resid = [&](double theta, bool top) {
+    if (exact) return 0.0;
     std::vector<double> x(m, 1.0), dd(m), cc(m), y(m);
-    const double shift = theta + 1e-10 * (fabs(theta) + 1.0) * (theta == thi ? 1 : -1);
+    const double shift = theta + 1e-10 * (fabs(theta) + 1.0) * (top ? 1 : -1);
     for (int it = 0; it < 4; ++it) {
       // solve (T - shift) y = x by the tridiagonal Thomas algorithm
       for (int i = 0; i < m; ++i) dd[i] = alpha[i] - shift;
@@ -222,9 +187,63 @@ void fq_lanczos_extremes(const double* a, int n, int ksteps, uint64_t seed, doub
     }
     return fabs(beta[m] * x[m - 1]);
   };
+  *rlo = resid(*tlo, false);
+  *rhi = resid(*thi, true);
+}
+
+// Extreme eigenvalues of the dense symmetric A by the Lanczos method (Lanczos 1950) with
+// full reorthogonalisation.  Returned [lo, hi] is the Ritz interval widened by the residual
+// norms of the two extreme Ritz pairs (each such pair has an eigenvalue within its residual)
+// plus 1e-6 of the span; with k >= n it is exact up to rounding.  The iteration stops early
+// once both residuals are below 1e-5 of the span (checked every 8 steps from step 24); the
+// returned interval is widened by them, so this only trades a slightly wider interval for time.
+void fq_lanczos_extremes(const fq_matvec& mv, int n, int ksteps, uint64_t seed, double* lo, double* hi) {
+  const int k = std::min(n, ksteps);
+  std::vector<double> V((size_t)(k + 1) * n), w(n), alpha(k), beta(k + 1, 0.0);
+  // start vector: splitmix64 uniforms in (-1, 1)
+  uint64_t s = seed;
+  double nrm = 0.0;
+  for (int i = 0; i < n; ++i) {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    V[i] = ((double)(z >> 11) + 0.5) * (2.0 / 9007199254740992.0) - 1.0;
+    nrm += V[i] * V[i];
+  }
+  nrm = sqrt(nrm);
+  for (int i = 0; i < n; ++i) V[i] /= nrm;
+  int m = k;
+  for (int j = 0; j < k; ++j) {
+    double* vj = &V[(size_t)j * n];
+    mv(vj, w.data());
+    const double al = dot4(w.data(), vj, n);
+    alpha[j] = al;
+    // full reorthogonalisation (twice is enough)
+    for (int pass = 0; pass < 2; ++pass)
+      for (int q = 0; q <= j; ++q) {
+        const double* vq = &V[(size_t)q * n];
+        const double c = dot4(w.data(), vq, n);
+        for (int i = 0; i < n; ++i) w[i] -= c * vq[i];
+      }
+    const double b = sqrt(dot4(w.data(), w.data(), n));
+    beta[j + 1] = b;
+    if (j + 1 == k) break;
+    if (b < 1e-13 * (fabs(al) + 1e-300)) { m = j + 1; break; }  // invariant subspace
+    if (j + 1 >= 24 && (j + 1) % 8 == 0) {
+      double tl, th, rl, rh;
+      ritz_extremes(alpha, beta, j + 1, false, &tl, &th, &rl, &rh);
+      if (std::max(rl, rh) < 1e-5 * (th - tl)) { m = j + 1; break; }
+    }
+    double* vn = &V[(size_t)(j + 1) * n];
+    for (int i = 0; i < n; ++i) vn[i] = w[i] / b;
+  }
+  double tlo, thi, rlo, rhi;
+  ritz_extremes(alpha, beta, m, m >= n, &tlo, &thi, &rlo, &rhi);
   const double span = thi - tlo;
-  *lo = tlo - resid(tlo) - 1e-6 * span;
-  *hi = thi + resid(thi) + 1e-6 * span;
+  *lo = tlo - rlo - 1e-6 * span;
+  *hi = thi + rhi + 1e-6 * span;
 }
 
 // ---------------------------------------------------------------- 6th-order Magnus (reading R12)
@@ -346,7 +365,38 @@ void fq_finish_bounds(fq_plan* plan, double emin, double emax) {
 
 // Host part of plan creation: validates the problem, forms the Magnus scalars (reading R1),
 // bounds (reading R4), R, L and a_l (Eq. 12, reading R5).  No device work.
-fq_status fq_host_plan(const fq_problem* p, fq_plan* plan) {
+void fq_dense_bounds(int n, double glo, double ghi, double kmax, const fq_dense_apply& apply, double* emin,
+                     double* emax) {
+  double l1, h1v, l2, h2v;
+  fq_lanczos_extremes([&](const double* x, double* y) { apply(0, glo, x, y); }, n, 320, 0x1234567ull, &l1, &h1v);
+  fq_lanczos_extremes([&](const double* x, double* y) { apply(0, ghi, x, y); }, n, 320, 0x7654321ull, &l2, &h2v);
+  double lo = std::min(l1, l2), hi = std::max(h1v, h2v);
+  if (kmax > 0) {  // ||[H0,H1]||_2 <= 2 ||H0||_2 ||H1||_2
+    double a0, b0, a1, b1;
+    fq_lanczos_extremes([&](const double* x, double* y) { apply(1, 0.0, x, y); }, n, 160, 0x51ull, &a0, &b0);
+    fq_lanczos_extremes([&](const double* x, double* y) { apply(2, 0.0, x, y); }, n, 160, 0x52ull, &a1, &b1);
+    const double w = kmax * 2.0 * std::max(fabs(a0), fabs(b0)) * std::max(fabs(a1), fabs(b1));
+    lo -= w;
+    hi += w;
+  }
+  *emin = lo;
+  *emax = hi;
+}
+
+// The margins fq_host_plan adds to computed bounds, then the Chebyshev data (fq_finish_bounds).
+void fq_finish_computed_bounds(fq_plan* plan, double emin, double emax) {
+  const double margin = 1e-12 * std::max(std::max(fabs(emin), fabs(emax)), 1.0);
+  emin -= margin;
+  emax += margin;
+  if (!(emax > emin)) {  // degenerate spectrum (N = 1, or H a multiple of 1)
+    const double w = 1e-12 * std::max(fabs(emin), 1.0);
+    emin -= w;
+    emax += w;
+  }
+  fq_finish_bounds(plan, emin, emax);
+}
+
+fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_bounds) {
   if (!p) { fq_set_error("problem is NULL"); return FQ_EINVAL; }
   if (p->n < 1 || p->steps < 1 || !(p->period > 0)) {
     fq_set_error("need n >= 1, steps >= 1, period > 0 (got %d, %d, %g)", p->n, p->steps, p->period);
@@ -459,34 +509,31 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan) {
       emin -= w;
       emax += w;
     }
+  } else if (defer_dense_bounds) {
+    plan->dense_bounds_pending = true;
+    plan->dense_glo = glo;
+    plan->dense_ghi = ghi;
+    plan->dense_kmax = kmax;
+    return FQ_OK;
   } else {
-    std::vector<double> a((size_t)n * n);
-    double l1, h1v, l2, h2v;
-    for (size_t i = 0; i < (size_t)n * n; ++i) a[i] = p->h0[i] + glo * p->h1[i];
-    fq_lanczos_extremes(a.data(), n, 320, 0x1234567ull, &l1, &h1v);
-    for (size_t i = 0; i < (size_t)n * n; ++i) a[i] = p->h0[i] + ghi * p->h1[i];
-    fq_lanczos_extremes(a.data(), n, 320, 0x7654321ull, &l2, &h2v);
-    emin = std::min(l1, l2);
-    emax = std::max(h1v, h2v);
-    if (kmax > 0) {  // ||[H0,H1]||_2 <= 2 ||H0||_2 ||H1||_2
-      double a0, b0, a1, b1;
-      fq_lanczos_extremes(p->h0, n, 160, 0x51ull, &a0, &b0);
-      fq_lanczos_extremes(p->h1, n, 160, 0x52ull, &a1, &b1);
-      const double w = kmax * 2.0 * std::max(fabs(a0), fabs(b0)) * std::max(fabs(a1), fabs(b1));
-      emin -= w;
-      emax += w;
-    }
+    // about 2^20 multiply-adds per thread at least: thread start-up costs more below that
+    const int nt = (int)std::max(1u, std::min<unsigned>(std::min(16u, std::thread::hardware_concurrency()),
+                                                         (unsigned)(((size_t)n * n) >> 20)));
+    std::vector<double> t(n);
+    const fq_dense_apply apply = [&](int which, double g, const double* x, double* y) {
+      if (which == 2) {
+        matvec(p->h1, x, y, n, nt);
+        return;
+      }
+      matvec(p->h0, x, y, n, nt);
+      if (which == 0 && g != 0.0) {
+        matvec(p->h1, x, t.data(), n, nt);
+        for (int i = 0; i < n; ++i) y[i] += g * t[i];
+      }
+    };
+    fq_dense_bounds(n, glo, ghi, kmax, apply, &emin, &emax);
   }
-  if (!(p->e_max > p->e_min)) {
-    const double margin = 1e-12 * std::max(std::max(fabs(emin), fabs(emax)), 1.0);
-    emin -= margin;
-    emax += margin;
-  }
-  if (!(emax > emin)) {  // degenerate spectrum (N = 1, or H a multiple of 1)
-    const double w = 1e-12 * std::max(fabs(emin), 1.0);
-    emin -= w;
-    emax += w;
-  }
-  fq_finish_bounds(plan, emin, emax);
+  if (p->e_max > p->e_min) fq_finish_bounds(plan, emin, emax);
+  else fq_finish_computed_bounds(plan, emin, emax);
   return FQ_OK;
 }

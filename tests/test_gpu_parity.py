@@ -321,3 +321,28 @@ def test_dimer_full_size_double_float_sampled_columns(fq):
     err = np.max(np.abs(to_np(U[:, cols]) - ref))
     print(f"dimer 10001 double-float tiled: max err {err:.3e}")
     assert err <= 1e-10
+
+
+@pytest.mark.parametrize("case", ["resident", "tiled64", "dense64", "split3"])
+def test_column_slices_bitwise_and_deterministic(fq, case):
+    """Columns of U_T are independent (one state per unit of work): U_T built in one call equals,
+    bit for bit, the propagation of the identity in three uneven slices of states, and a second
+    build equals the first bit for bit."""
+    import torch
+    if case in ("resident", "tiled64"):
+        d = fi.config_dimer(nb=700, steps=60)
+        plan = dimer_plan(fq, d, 1 if case == "resident" else 0, 2 if case == "resident" else 3)
+        n = d.n
+    else:
+        n = 200
+        h0, h1 = fi.goe(n, 2301), fi.goe(n, 2302)
+        plan = fq.Plan.dense(h0, h1, omega=1.3, f_ac=1.1, steps=12, precision=0 if case == "dense64" else fq.FQ_BF16X3)
+    U = plan.build_UT()
+    U2 = plan.build_UT()
+    assert plan.check_status() == fq.FQ_OK
+    assert torch.equal(U, U2)
+    eye = torch.eye(n, dtype=torch.complex128, device="cuda")
+    cuts = [0, 37, n // 2 + 5, n]
+    for a, b in zip(cuts, cuts[1:]):
+        X = plan.propagate(eye[a:b].contiguous())          # rows = states a..b-1
+        assert torch.equal(X.transpose(0, 1), U[:, a:b])
