@@ -81,9 +81,12 @@ typedef enum fq_drive_kind {
 
 typedef enum fq_kernel {
   FQ_KERNEL_AUTO = 0,       /* resident kernel when it applies, else tiled, else streaming */
-  FQ_KERNEL_STREAM = 1,     /* tridiagonal: one launch per Chebyshev term, states in HBM */
+  FQ_KERNEL_STREAM = 1,     /* tridiagonal: one launch per Chebyshev term, states in HBM;
+                               dense FP64: one tiled GEMM launch per term (also for TILED) */
   FQ_KERNEL_RESIDENT = 2,   /* tridiagonal FP32: one CTA per state runs the whole chain on chip
-                               (N <= 10240, L <= 128); FQ_EUNSUPPORTED otherwise */
+                               (N <= 10240, L <= 128); dense FP64: a cluster of ceil(N/32) CTAs
+                               per state runs 64 steps per launch on chip (N <= 128, L <= 128);
+                               FQ_EUNSUPPORTED otherwise */
   FQ_KERNEL_TILED = 3       /* tridiagonal FP64 or FP32, any N, L <= 128: one launch per step, each
                                CTA runs the step's L products on a segment of one state plus L
                                halo rows a side; FQ_EUNSUPPORTED otherwise.  AUTO picks RESIDENT,
@@ -107,7 +110,8 @@ typedef struct fq_problem {
   double e_min, e_max;      /* if e_max > e_min: caller's bounds of Omega/h, used as given */
   int32_t precision;        /* fq_precision */
   int32_t checkpoint_stride;/* floquet_grad: X_m stored every s steps; <= 0 selects 16 */
-  int32_t kernel;           /* fq_kernel: which tridiagonal kernel family runs the chain */
+  int32_t kernel;           /* fq_kernel: which kernel family runs the chain (tridiagonal, and
+                               dense FP64); ignored by the split precisions */
   int32_t tile_n;           /* split path: tensor-core output tile width 64 or 128; 0 = 128 until
                                floquet_autotune picks one */
   int32_t magnus_order;     /* 4 (default, also 0) or 6: Eq. 14 in full with its alphas taken as

@@ -45,7 +45,12 @@ size_t layout(const fq_plan* p, int nc, int nsteps, void* ws, StateWs* out) {
   Carver c(ws);
   StateWs w;
   const int n = p->n;
-  if (p->path == PATH_DENSE_F64) {
+  if (p->path == PATH_DENSE_F64 && p->dense_resident) {
+    // Omega~ of a chunk of steps, one state block updated in place
+    w.S = c.take<double>(fq_dense_resident_omega_count(n, nsteps));
+    w.A = c.take<double>(fq_dense_resident_omega_count(n, nsteps));
+    for (int q = 0; q < 2; ++q) w.buf[0][q] = c.take<double>((size_t)nc * n);
+  } else if (p->path == PATH_DENSE_F64) {
     w.S = c.take<double>((size_t)n * n);
     w.A = c.take<double>((size_t)n * n);
     for (int b = 0; b < 3; ++b)
@@ -197,7 +202,12 @@ fq_status propagate_impl(fq_plan* p, const double* x0, double* x, int nc, int m_
     fq_blk<double> b0 = blk<double>(w.buf[0]);
     if (identity) fq_launch_identity_f64(b0, nc, n, ld, s);
     else fq_launch_load_states(x0, b0, nc, n, ld, s);
-    xb = run_chain<double>(p, w, 0, nc, m_begin, m_end, s);
+    if (p->path == PATH_DENSE_F64 && p->dense_resident) {
+      st = fq_dense_resident_chain(p, b0.re, b0.im, nc, m_begin, m_end, w.S, w.A, s);
+      if (st != FQ_OK) return st;
+    } else {
+      xb = run_chain<double>(p, w, 0, nc, m_begin, m_end, s);
+    }
     fq_blk<double> bx = blk<double>(w.buf[xb]);
     if (transpose_out) fq_launch_store_transpose_f64(bx, x, n, ld, s);
     else fq_launch_store_states_f64(bx, x, nc, n, ld, s);
@@ -362,6 +372,16 @@ fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
       if ((e = cudaMemcpy(p->d_k, kl.data(), (n - 1) * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e, "upload K");
     }
+  }
+  if (p->path == PATH_DENSE_F64) {
+    // small dense problems: one resident launch per chunk of steps instead of one per term
+    const bool ok = fq_dense_resident_supported(n, p->L);
+    if (prob->kernel == FQ_KERNEL_RESIDENT && !ok) {
+      fq_set_error("dense resident kernel needs N <= 128 and L <= 128 (N = %d, L = %d)", n, p->L);
+      free_plan(p);
+      return FQ_EUNSUPPORTED;
+    }
+    p->dense_resident = ok && (prob->kernel == FQ_KERNEL_AUTO || prob->kernel == FQ_KERNEL_RESIDENT);
   }
   *out = p;
   return FQ_OK;

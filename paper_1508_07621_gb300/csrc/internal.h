@@ -39,6 +39,7 @@ struct fq_plan {
   std::vector<double> sa, sb, sc;      // Omega~_m = sa H0 + sb H1 + sc i[H0,H1] - sbeta 1
   double sbeta = 0;
   int path = PATH_DENSE_F64;
+  bool dense_resident = false;   // PATH_DENSE_F64: small-N resident chain (dense_resident.cu)
   // 6th-order scheme: per step 11 coefficients of Omega_m over {H0, H1, K, K0, K1, K00, K01, K10,
   // K11, KK0, KK1} (K = [H0,H1], K0 = [H0,K], K1 = [H1,K], K00 = [H0,K0], K01 = [H0,K1],
   // K10 = [H1,K0], K11 = [H1,K1], KK0 = [K,K0], KK1 = [K,K1]); real for the symmetric ones,
@@ -140,6 +141,13 @@ void fq_launch_term_tri_f32(const float* d, const float* er, const float* ei, in
 int fq_resident_supported(int n, int L);
 // Tiled tridiagonal chain (tri_tile.cu): FP64 or FP32, any n, L <= 128.
 int fq_tile_supported(int L);
+// ---------------------------------------------------------------- dense_resident.cu
+bool fq_dense_resident_supported(int n, int L);
+// doubles in each of the S and A regions the resident chain needs for nsteps steps
+size_t fq_dense_resident_omega_count(int n, int nsteps);
+// steps [m_begin, m_end) on planar FP64 states x (nc rows of n), in place
+fq_status fq_dense_resident_chain(const fq_plan* p, double* xr, double* xi, int nc, int m_begin, int m_end,
+                                  double* S, double* A, cudaStream_t s);
 size_t fq_tile_workspace(const fq_plan* p, int nc, int nsteps);
 fq_status fq_tile_propagate(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
                             int transpose_out, void* ws, cudaStream_t s);

@@ -228,9 +228,11 @@ def test_bound_violation_sets_status(fq):
     m = fi.config_goe64()
     pm = o.plan_for_drive_dense(m.h0, m.h1, m.drive, m.steps)
     c, w = 0.5 * (pm.e_min + pm.e_max), 0.2 * (pm.e_max - pm.e_min)
-    plan = fq.Plan.dense(m.h0, m.h1, omega=1.0, f_ac=1.0, steps=m.steps, e_min=c - w, e_max=c + w)
-    plan.build_UT()
-    assert plan.check_status() == fq.FQ_EBOUND
+    for kernel in (fq.FQ_KERNEL_RESIDENT, fq.FQ_KERNEL_TILED):
+        plan = fq.Plan.dense(m.h0, m.h1, omega=1.0, f_ac=1.0, steps=m.steps, e_min=c - w, e_max=c + w,
+                             kernel=kernel)
+        plan.build_UT()
+        assert plan.check_status() == fq.FQ_EBOUND, kernel
 
 
 def test_workspace_errors(fq):
@@ -346,3 +348,40 @@ def test_column_slices_bitwise_and_deterministic(fq, case):
     for a, b in zip(cuts, cuts[1:]):
         X = plan.propagate(eye[a:b].contiguous())          # rows = states a..b-1
         assert torch.equal(X.transpose(0, 1), U[:, a:b])
+
+
+# ------------------------------------------------------------------ dense FP64, resident kernel
+@pytest.mark.parametrize("n", [1, 5, 32, 33, 64, 65, 100, 128])
+def test_dense_fp64_resident_kernel(fq, n):
+    """The small-N resident chain (clusters of ceil(N/32) CTAs, 64 steps per launch) against the
+    oracle and against the per-term kernel: ragged row blocks (33, 65, 100), one to four CTAs per
+    state, M = 70 crossing a launch boundary, a non-even drive."""
+    M = 70
+    h0, h1 = fi.goe(n, 1101), fi.goe(n, 1102)
+    drv = fi.Drive(0.2, 1.3, 1.7, 0.4)
+    kw = dict(omega=drv.omega, f_ac=drv.f_ac, f_dc=drv.f_dc, phi0=drv.phi0, steps=M)
+    res = fq.Plan.dense(h0, h1, kernel=fq.FQ_KERNEL_RESIDENT, **kw)
+    til = fq.Plan.dense(h0, h1, kernel=fq.FQ_KERNEL_TILED, **kw)
+    U, V = res.build_UT(), til.build_UT()
+    assert res.check_status() == fq.FQ_OK and til.check_status() == fq.FQ_OK
+    ref = o.build_ut_dense(h0, h1, o.plan_for_drive_dense(h0, h1, drv, M))
+    assert np.max(np.abs(to_np(U) - ref)) <= 1e-10
+    assert np.max(np.abs(to_np(U) - to_np(V))) <= 1e-12
+
+
+def test_dense_fp64_resident_segments_and_limits(fq):
+    """Steps 50..139 of 150 (two launch boundaries inside the range) on 7 states, against the
+    oracle; N = 129 cannot take the resident kernel when it is asked for."""
+    n, M = 48, 150
+    h0, h1 = fi.goe(n, 1201), fi.goe(n, 1202)
+    drv = fi.Drive(0.0, 1.0, 1.0, 0.3)
+    x0 = fi.ginibre(n, 1203)[:7]
+    x0 /= np.linalg.norm(x0, axis=1, keepdims=True)
+    plan = fq.Plan.dense(h0, h1, omega=drv.omega, f_ac=drv.f_ac, phi0=drv.phi0, steps=M,
+                         kernel=fq.FQ_KERNEL_RESIDENT)
+    X = plan.propagate(cuda_c128(x0), 50, 140)
+    ref = o.propagate_dense(h0, h1, o.plan_for_drive_dense(h0, h1, drv, M), x0.T, 50, 140).T
+    assert np.max(np.abs(to_np(X) - ref)) <= 1e-10
+    with pytest.raises(fq.FloquetError) as e:
+        fq.Plan.dense(fi.goe(129, 1), fi.goe(129, 2), omega=1.0, f_ac=1.0, steps=4, kernel=fq.FQ_KERNEL_RESIDENT)
+    assert e.value.status == fq.FQ_EUNSUPPORTED
