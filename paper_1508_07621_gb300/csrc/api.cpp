@@ -67,6 +67,8 @@ size_t layout(const fq_plan* p, int nc, int nsteps, void* ws, StateWs* out) {
     w.coeff = c.take<char>(fq_tile_workspace(p, nc, nsteps));
   } else if (p->path == PATH_DENSE_SPLIT) {
     w.coeff = c.take<char>(fq_split_workspace(p, nc, nullptr, nullptr));
+  } else if (p->path == PATH_DENSE_OZAKI) {
+    w.coeff = c.take<char>(fq_ozaki_workspace(p, nc, nullptr, nullptr));
   }
   if (out) *out = w;
   return c.used;
@@ -186,6 +188,11 @@ fq_status propagate_impl(fq_plan* p, const double* x0, double* x, int nc, int m_
     if (st != FQ_OK) return st;
     return cuda_ok(cudaGetLastError(), "split-precision chain");
   }
+  if (p->path == PATH_DENSE_OZAKI) {
+    st = fq_ozaki_propagate(p, x0, x, nc, m_begin, m_end, identity, transpose_out, w.coeff, s);
+    if (st != FQ_OK) return st;
+    return cuda_ok(cudaGetLastError(), "FP64-emulation chain");
+  }
   const bool f64 = p->precision == FQ_FP64;
   const int ld = p->path == PATH_DENSE_F64 ? n : tri_ld(n);
   if (p->path == PATH_TRI_STREAM) {
@@ -273,7 +280,7 @@ fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
       default: p->path = res_ok ? PATH_TRI_RESIDENT : (tile_ok ? PATH_TRI_TILE : PATH_TRI_STREAM);
     }
   } else {
-    p->path = p->precision == FQ_FP64 ? PATH_DENSE_F64 : PATH_DENSE_SPLIT;
+    p->path = p->precision == FQ_FP64 ? PATH_DENSE_F64 : (p->precision == FQ_OZAKI ? PATH_DENSE_OZAKI : PATH_DENSE_SPLIT);
   }
   cudaGetDevice(&p->device);
   auto fail = [&](cudaError_t e, const char* what) {

@@ -23,6 +23,7 @@ enum fq_path : int {
   PATH_TRI_STREAM = 2,    // streaming tridiagonal term kernel (FP32 or FP64)
   PATH_TRI_RESIDENT = 3,  // one CTA per state, whole chain on chip (FP32)
   PATH_TRI_TILE = 5,      // one launch per step, each CTA runs a step's L products on a state segment
+  PATH_DENSE_OZAKI = 6,   // tcgen05 FP64 emulation (fixed-point BF16 slices, exact FP32 sums) per term
 };
 
 struct fq_plan {
@@ -157,6 +158,10 @@ void fq_launch_gauge_coeffs(const fq_plan* p, int m_begin, int nsteps, void* coe
 fq_status fq_launch_resident(const fq_plan* p, const void* coeff, const double* x0, double* x, int transpose_out,
                              int nc, int m_begin, int m_end, cudaStream_t s);
 
+// FP64 emulation on the tensor cores (ozaki.cu)
+size_t fq_ozaki_workspace(const fq_plan* p, int nc, void* base, void* out);
+fq_status fq_ozaki_propagate(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
+                             int transpose_out, void* ws, cudaStream_t s);
 // split-precision dense path (dense_split.cu)
 size_t fq_split_workspace(const fq_plan* p, int nc, void* base, void* out);
 // True the first time it is called on the current device for this flag word (one bit per

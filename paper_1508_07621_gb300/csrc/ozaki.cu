@@ -1,0 +1,580 @@
+// FP64 emulation of the dense Chebyshev product on the BF16 tensor cores (FQ_OZAKI): Ozaki's
+// error-free splitting (Ozaki, Ogita, Oishi, Rump 2012, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its applications") with
+// fixed-point BF16 slices and exact FP32 sums in tensor memory.
+//
+// Splitting.  Every row r of an operand (a state row of Psi, re and im together; a row of
+// Omega~_m, S and A together) gets one power-of-two scale 2^e_r >= its largest entry.  x / 2^e_r
+// is cut into OZ_S digits of OZ_BITS bits,
+//   x = 2^e_r * sum_q d_q 2^(-8 (q+1)) + (remainder below 2^-48 of the scale),
+// |d_0| <= 256, |d_q| <= 128 after, each slice d_q 2^(-8(q+1)) exact in BF16.  The slices of a
+// row share one binary grid, so a product of slice a of the left and slice b of the right
+// operand is an integer multiple of 2^(-8(a+b+2)) and sums of such products are exact in FP32
+// while they stay below 2^24 units.
+//
+// Product.  Y[j][i] = sum_k Psi[j][k] (S[i][k] + i A[i][k]) takes the 21 slice pairs (a, b) with
+// a + b <= 5 (terms beyond carry less than 2^-48 of the scales).  Pairs with a + b = 0, 1, 2 go
+// to three exact accumulators, the rest (a + b >= 3, at most 2^-24 of the leading term) to a
+// fourth one whose FP32 rounding stays near 2^-48 relative.  Per 64 values of k the four
+// accumulators are drained into double-float registers (an FP32 pair, about 48 bits) by the
+// epilogue warps: over 64 values of k the worst exact sum is 5 * 2^14 * 128 < 2^24 units.  The
+// complex product uses three right-operand blocks per row block, [-A; S; A]: Psi_r . [S; A]^T
+// and Psi_i . [-A; S]^T accumulate Yr and Yi side by side, two MMAs of N = 128 per pair.
+//
+// Chain (Eqs. 10-12).  States stay FP64 in HBM; the epilogue applies the recurrence, the Bessel
+// accumulation and the step phase in FP64, as the plain FP64 path does.  A separate pass slices
+// each new Psi_{l+1} (its row scales need the whole row).
+//
+// Kernel.  One 128-state x 64-column tile per CTA: warp 0 streams TMA stages (K = 16 per stage,
+// 32-byte rows with 32-byte swizzle), warp 1 issues the MMAs, warps 2-17 drain tensor memory
+// (four warps per lane quarter, 16 complex columns each).  The 512 tensor-memory columns hold
+// the four accumulators (128 columns each), so the MMAs wait for each drain.  Every wait is
+// bounded; a wait that gives up records FQ_BIT_TIMEOUT, drains this CTA's own copies and MMAs,
+// frees tensor memory and returns.
+#include "split_core.cuh"
+
+namespace {
+
+constexpr int OZ_S = 6;                     // slices per operand
+constexpr int OZ_PAIRS = OZ_S * (OZ_S + 1) / 2;
+constexpr int OZ_BN = 64;                   // complex output columns per tile
+constexpr int OZ_ROWB = 32;                 // bytes per K row of a stage (K = 16 BF16)
+constexpr int OZ_BKE = OZ_ROWB / 2;
+constexpr int OZ_KB_PER_DRAIN = 4;          // 64 values of k between drains
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_EPI_WARPS = 16;
+constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
+constexpr int OZ_A_BYTES = BM * OZ_ROWB;                   // one slice of Psi_r or Psi_i
+constexpr int OZ_R_BYTES = 3 * OZ_BN * OZ_ROWB;            // one slice of [-A; S; A]
+constexpr int OZ_STAGE_BYTES = 2 * OZ_S * OZ_A_BYTES + OZ_S * OZ_R_BYTES;
+constexpr size_t OZ_SMEM = (size_t)OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
+constexpr uint32_t OZ_TMEM_COLS = 512;      // 4 accumulators x (Yr | Yi) x 64 columns
+
+struct OzMaps {
+  CUtensorMap a[OZ_S];  // left slices [ncp][2 np]: Psi_r in columns [0, np), Psi_i in [np, 2 np)
+  CUtensorMap r[OZ_S];  // right slices [3 np][np]: per 64-row block of Omega~, rows -A, S, A
+};
+
+struct OzEpi {
+  int n, nc;
+  const double* cur_re;   // psi_l (first term: psi_0)
+  const double* cur_im;
+  const double* prev_re;  // psi_{l-1}
+  const double* prev_im;
+  double* acc_re;
+  double* acc_im;
+  double* out_re;         // psi_{l+1} (in place of psi_{l-1}) or X at the last term
+  double* out_im;
+  const int* es;          // row exponents of the left slices
+  const int* et;          // row exponents of the right slices
+  fq_term t;
+};
+
+// K-major 32-byte rows with 32-byte swizzle, 8-row atoms of 256 bytes
+__device__ __forceinline__ uint64_t oz_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)((8 * OZ_ROWB) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)6 << 61;
+  return d;
+}
+
+// pair p -> (a, b), ordered by a + b, then a
+__device__ __forceinline__ void oz_pair(int p, int& a, int& b) {
+  int d = 0, base = 0;
+  while (p >= base + d + 1) {
+    base += d + 1;
+    ++d;
+  }
+  a = p - base;
+  b = d - a;
+}
+
+// (h, l) += v in double-float: two-sum, then a fast renormalisation
+__device__ __forceinline__ void dd_add(float& h, float& l, float v) {
+  const float s = __fadd_rn(h, v);
+  const float bb = __fsub_rn(s, h);
+  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+  const float lo = __fadd_rn(l, e);
+  const float h2 = __fadd_rn(s, lo);
+  l = __fsub_rn(lo, __fsub_rn(h2, s));
+  h = h2;
+}
+
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// exponent e with |x| < 2^e for the row maximum m (0 for a zero row), kept in the normal range
+__device__ __forceinline__ int oz_exponent(double m) {
+  if (!(m > 0.0)) return 0;
+  int e;
+  frexp(m, &e);
+  return e < -960 ? -960 : e;
+}
+
+// The digits of r = x / 2^e (|r| < 1) as BF16 slices d_q 2^(-8(q+1))
+__device__ __forceinline__ void oz_digits(double r, __nv_bfloat16 (&s)[OZ_S]) {
+#pragma unroll
+  for (int q = 0; q < OZ_S; ++q) {
+    const double t = r * 256.0;
+    const double d = rint(t);
+    s[q] = __float2bfloat16_rn((float)(d * pow2(-8 * (q + 1))));
+    r = t - d;
+  }
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  double m = 0.0;
+  for (int q = 0; q < nw; ++q) m = fmax(m, red[q]);
+  __syncthreads();
+  return m;
+}
+
+// Left slices of the state rows: one CTA per row j of the padded block (rows >= nc are zero).
+__global__ void k_oz_slice_left(const double* __restrict__ re, const double* __restrict__ im, int n, int nc, int np,
+                                size_t astride, __nv_bfloat16* __restrict__ left, int* __restrict__ es) {
+  __shared__ double red[32];
+  const int j = blockIdx.x;
+  double m = 0.0;
+  if (j < nc)
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+      m = fmax(m, fmax(fabs(re[(size_t)j * n + k]), fabs(im[(size_t)j * n + k])));
+  const int e = oz_exponent(block_max(m, red));
+  const double inv = pow2(-e);
+  __nv_bfloat16* row = left + (size_t)j * 2 * np;
+  for (int k = threadIdx.x; k < np; k += blockDim.x) {
+    double xr = 0.0, xi = 0.0;
+    if (j < nc && k < n) {
+      xr = re[(size_t)j * n + k] * inv;
+      xi = im[(size_t)j * n + k] * inv;
+    }
+    __nv_bfloat16 sr[OZ_S], si[OZ_S];
+    oz_digits(xr, sr);
+    oz_digits(xi, si);
+#pragma unroll
+    for (int q = 0; q < OZ_S; ++q) {
+      row[q * astride + k] = sr[q];
+      row[q * astride + np + k] = si[q];
+    }
+  }
+  if (threadIdx.x == 0) es[j] = e;
+}
+
+// Omega~_m = sum_t c_t M_t - sbeta 1 split into S (symmetric terms) and A (antisymmetric ones).
+struct OzOmega {
+  const double* m[FQ_M6_TERMS];
+  double c[FQ_M6_TERMS];
+  int anti[FQ_M6_TERMS];
+  int terms;
+  double sbeta;
+};
+
+__device__ __forceinline__ void oz_omega_entry(const OzOmega& a, int n, int i, int k, double& S, double& A) {
+  S = i == k ? -a.sbeta : 0.0;
+  A = 0.0;
+  const size_t o = (size_t)i * n + k;
+  for (int t = 0; t < a.terms; ++t) {
+    if (a.anti[t]) A = fma(a.c[t], a.m[t][o], A);
+    else S = fma(a.c[t], a.m[t][o], S);
+  }
+}
+
+// Right slices of step m: one CTA per row i of the padded operator (rows >= n are zero).
+__global__ void k_oz_omega(const __grid_constant__ OzOmega a, int n, int np, size_t rstride,
+                           __nv_bfloat16* __restrict__ right, int* __restrict__ et) {
+  __shared__ double red[32];
+  const int i = blockIdx.x;
+  double m = 0.0;
+  if (i < n)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      double S, A;
+      oz_omega_entry(a, n, i, k, S, A);
+      m = fmax(m, fmax(fabs(S), fabs(A)));
+    }
+  const int e = oz_exponent(block_max(m, red));
+  const double inv = pow2(-e);
+  const size_t rb = (size_t)(3 * OZ_BN) * (i / OZ_BN) + (i % OZ_BN);  // row of -A; S and A follow
+  for (int k = threadIdx.x; k < np; k += blockDim.x) {
+    double S = 0.0, A = 0.0;
+    if (i < n && k < n) oz_omega_entry(a, n, i, k, S, A);
+    __nv_bfloat16 ss[OZ_S], sa[OZ_S];
+    oz_digits(S * inv, ss);
+    oz_digits(A * inv, sa);
+#pragma unroll
+    for (int q = 0; q < OZ_S; ++q) {
+      __nv_bfloat16* base = right + q * rstride + k;
+      base[rb * np] = __hneg(sa[q]);
+      base[(rb + OZ_BN) * np] = ss[q];
+      base[(rb + 2 * OZ_BN) * np] = sa[q];
+    }
+  }
+  if (threadIdx.x == 0) et[i] = e;
+}
+
+// One Chebyshev term on a 128-state x 64-column tile (see the file comment).
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_oz_term(const __grid_constant__ OzMaps maps, int nk, int tiles_j, int tiles_i, int np, OzEpi e) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + OZ_STAGES * OZ_STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 3);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + OZ_STAGES);
+  const uint32_t tfull = smem_u32(bars + 2 * OZ_STAGES), tempty = smem_u32(bars + 2 * OZ_STAGES + 1);
+  const uint32_t done = smem_u32(bars + 2 * OZ_STAGES + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunks = nk / OZ_KB_PER_DRAIN;
+
+  int tj, ti;
+  {
+    const int b = blockIdx.x, per = RASTER_GROUP * tiles_i, g = b / per;
+    const int gj = min(RASTER_GROUP, tiles_j - g * RASTER_GROUP), r = b - g * per;
+    tj = g * RASTER_GROUP + r % gj;
+    ti = r / gj;
+  }
+  const int j0 = tj * BM, i0 = ti * OZ_BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, OZ_EPI_WARPS);
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(OZ_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------- TMA producer
+      int issued = 0;
+      bool ok = true;
+      for (int kb = 0; kb < nk && ok; ++kb) {
+        const int s = kb % OZ_STAGES;
+        if (kb >= OZ_STAGES && !(ok = mbar_wait(empty0 + 8 * s, ((kb / OZ_STAGES) - 1) & 1))) break;
+        if (*(volatile int*)abort_flag) {
+          ok = false;
+          break;
+        }
+        const uint32_t st = base + s * OZ_STAGE_BYTES;
+        const uint32_t bar = full0 + 8 * s;
+        mbar_expect_tx(bar, OZ_STAGE_BYTES);
+        const int kx = kb * OZ_BKE;
+#pragma unroll
+        for (int q = 0; q < OZ_S; ++q) {
+          tma_load_2d(st + (2 * q) * OZ_A_BYTES, &maps.a[q], bar, kx, j0);           // Psi_r
+          tma_load_2d(st + (2 * q + 1) * OZ_A_BYTES, &maps.a[q], bar, np + kx, j0);  // Psi_i
+          tma_load_2d(st + 2 * OZ_S * OZ_A_BYTES + q * OZ_R_BYTES, &maps.r[q], bar, kx, 3 * i0);  // -A, S, A
+        }
+        issued = kb + 1;
+      }
+      if (!ok) {
+        atomicExch(abort_flag, 1);
+        atomicOr(e.t.status, FQ_BIT_TIMEOUT);
+      }
+      for (int kb = max(0, issued - OZ_STAGES); kb < issued; ++kb)
+        mbar_wait(full0 + 8 * (kb % OZ_STAGES), (kb / OZ_STAGES) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------- MMA issuer
+      constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * OZ_BN) >> 3) << 17) |
+                                 ((uint32_t)(BM >> 4) << 24);
+      bool ok = true;
+      int kb = 0;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        if (c > 0 && !(ok = mbar_wait(tempty, (c - 1) & 1))) break;
+        tc_fence_after();
+        for (int kq = 0; kq < OZ_KB_PER_DRAIN; ++kq, ++kb) {
+          const int s = kb % OZ_STAGES;
+          ok = mbar_wait(full0 + 8 * s, (kb / OZ_STAGES) & 1);
+          if (!ok || *(volatile int*)abort_flag) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = base + s * OZ_STAGE_BYTES;
+          // descriptors of the stage's tiles: the start-address field is the low 14 bits (16-byte
+          // units), so an offset inside shared memory adds to the descriptor without a carry
+          const uint64_t d0 = oz_desc(st);
+#pragma unroll 1
+          for (int p = 0; p < OZ_PAIRS; ++p) {
+            int a, b;
+            oz_pair(p, a, b);
+            const int g = a + b < 3 ? a + b : 3;
+            const bool lead = p == 0 || p == 1 || p == 3 || p == 6;  // first pair of each accumulator
+            const uint32_t acc = tmem + (uint32_t)g * (2 * OZ_BN);
+            const uint32_t rb = 2 * OZ_S * OZ_A_BYTES + b * OZ_R_BYTES;
+            mma_bf16(acc, d0 + (uint64_t)(((2 * a) * OZ_A_BYTES) >> 4), d0 + (uint64_t)((rb + OZ_BN * OZ_ROWB) >> 4),
+                     idesc, (kq == 0 && lead) ? 0u : 1u);  // Psi_r . [S; A]
+            mma_bf16(acc, d0 + (uint64_t)(((2 * a + 1) * OZ_A_BYTES) >> 4), d0 + (uint64_t)(rb >> 4), idesc,
+                     1u);                                   // Psi_i . [-A; S]
+          }
+          mma_commit(empty0 + 8 * s);
+        }
+        if (!ok) break;
+        mma_commit(tfull);
+      }
+      if (!ok) {
+        atomicExch(abort_flag, 1);
+        atomicOr(e.t.status, FQ_BIT_TIMEOUT);
+      }
+      mma_commit(done);
+      mbar_wait(done, 0);
+    }
+  } else {  // ---------------- drain warps 2-17
+    const int quarter = warp & 3, part = (warp - 2) >> 2;
+    const int j = j0 + quarter * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(part * 16);
+    float hr[16], lr[16], hi[16], li[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) hr[q] = lr[q] = hi[q] = li[q] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      bool go = mbar_wait(tfull, c & 1);
+      tc_fence_after();
+      go = __all_sync(0xffffffffu, go && !*(volatile int*)abort_flag);
+      if (!go) {
+        ok = false;
+        break;
+      }
+      // one 16-column load at a time keeps the double-float sums and one load in registers
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+#pragma unroll
+        for (int part_im = 0; part_im < 2; ++part_im) {
+          float v[16];
+          tmem_ld16(trow + g * (2 * OZ_BN) + part_im * OZ_BN, v);
+          tmem_wait_ld();
+          float* h = part_im ? hi : hr;
+          float* l = part_im ? li : lr;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            if (g < 3) dd_add(h[q], l[q], v[q]);
+            else l[q] = __fadd_rn(l[q], v[q]);  // below 2^-24 of the leading sum: the low word carries it
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty);
+    }
+    if (!ok) {
+      atomicExch(abort_flag, 1);
+      atomicOr(e.t.status, FQ_BIT_TIMEOUT);
+    } else if (j < e.nc) {
+      // ---------------- Chebyshev epilogue in FP64 (as in the plain FP64 path).  The stages are
+      // idle now (the last MMAs have completed): the sums wait there, one column per pass.
+      float* xs = reinterpret_cast<float*>(gbase) + (threadIdx.x - 64);
+      constexpr int XS = 32 * OZ_EPI_WARPS;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        xs[(4 * q) * XS] = hr[q];
+        xs[(4 * q + 1) * XS] = lr[q];
+        xs[(4 * q + 2) * XS] = hi[q];
+        xs[(4 * q + 3) * XS] = li[q];
+      }
+      const fq_term& t = e.t;
+      const int ej = e.es[j];
+      bool bad = false;
+#pragma unroll 1
+      for (int q = 0; q < 16; ++q) {
+        const int i = i0 + part * 16 + q;
+        if (i >= e.n) break;
+        const double sc = pow2(ej + e.et[i]);
+        const double yr = ((double)xs[(4 * q) * XS] + (double)xs[(4 * q + 1) * XS]) * sc;
+        const double yi = ((double)xs[(4 * q + 2) * XS] + (double)xs[(4 * q + 3) * XS]) * sc;
+        const size_t idx = (size_t)j * e.n + i;
+        double pr, pi;
+        if (t.first) {
+          pr = yi;
+          pi = -yr;
+        } else {
+          pr = fma(2.0, yi, e.prev_re[idx]);
+          pi = fma(-2.0, yr, e.prev_im[idx]);
+        }
+        bad |= !(pr * pr + pi * pi <= t.bound2);
+        double ar, ai;
+        if (t.first) {
+          ar = fma(t.coef, pr, t.coef0 * e.cur_re[idx]);
+          ai = fma(t.coef, pi, t.coef0 * e.cur_im[idx]);
+        } else {
+          ar = fma(t.coef, pr, e.acc_re[idx]);
+          ai = fma(t.coef, pi, e.acc_im[idx]);
+        }
+        if (t.last) {
+          e.out_re[idx] = t.ph_re * ar - t.ph_im * ai;
+          e.out_im[idx] = t.ph_re * ai + t.ph_im * ar;
+        } else {
+          e.out_re[idx] = pr;
+          e.out_im[idx] = pi;
+          e.acc_re[idx] = ar;
+          e.acc_im[idx] = ai;
+        }
+      }
+      if (bad) atomicOr(t.status, FQ_BIT_BOUND);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
+  }
+}
+
+struct OzWs {
+  __nv_bfloat16* left;   // OZ_S slices [ncp][2 np]
+  __nv_bfloat16* right;  // OZ_S slices [3 np][np]
+  int* es;               // [ncp]
+  int* et;               // [np]
+  double* m[3][2];       // FP64 state masters [nc][n], planar
+  int np, ncp;
+  size_t astride, rstride;
+};
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+OzOmega omega_args(const fq_plan* p, int m) {
+  OzOmega a{};
+  a.sbeta = p->sbeta;
+  if (p->order == 6) {
+    static const int anti[FQ_M6_TERMS] = {0, 0, 1, 0, 0, 1, 1, 1, 1, 0, 0};
+    const size_t nn = (size_t)p->n * p->n;
+    const double inv = 1.0 / (p->h * p->delta_e);
+    a.terms = FQ_M6_TERMS;
+    a.m[0] = p->d_h0;
+    a.m[1] = p->d_h1;
+    a.m[2] = p->d_k;
+    for (int q = 0; q < 8; ++q) a.m[3 + q] = p->d_cm + q * nn;
+    for (int q = 0; q < FQ_M6_TERMS; ++q) {
+      a.c[q] = p->coef6[(size_t)m * FQ_M6_TERMS + q] * inv;
+      a.anti[q] = anti[q];
+    }
+  } else {
+    a.terms = 3;
+    a.m[0] = p->d_h0;
+    a.m[1] = p->d_h1;
+    a.m[2] = p->d_k;
+    a.c[0] = p->sa[m];
+    a.c[1] = p->sb[m];
+    a.c[2] = p->sc[m];
+    a.anti[2] = 1;
+  }
+  return a;
+}
+
+}  // namespace
+
+size_t fq_ozaki_workspace(const fq_plan* p, int nc, void* base, void* out) {
+  OzWs w{};
+  w.np = (p->n + 127) & ~127;
+  w.ncp = (nc + BM - 1) / BM * BM;
+  w.astride = (size_t)w.ncp * 2 * w.np;
+  w.rstride = (size_t)3 * w.np * w.np;
+  char* b = (char*)base;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* q = b ? b + off : nullptr;
+    off += up256(bytes);
+    return q;
+  };
+  w.left = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.astride);
+  w.right = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.rstride);
+  w.es = (int*)take(sizeof(int) * w.ncp);
+  w.et = (int*)take(sizeof(int) * w.np);
+  for (int q = 0; q < 3; ++q)
+    for (int r = 0; r < 2; ++r) w.m[q][r] = (double*)take(sizeof(double) * (size_t)nc * p->n);
+  if (out) *(OzWs*)out = w;
+  return off;
+}
+
+fq_status fq_ozaki_propagate(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
+                             int transpose_out, void* ws, cudaStream_t s) {
+  fq_status st = encode_fn();
+  if (st != FQ_OK) return st;
+  OzWs w;
+  fq_ozaki_workspace(p, nc, ws, &w);
+  const int n = p->n, L = p->L;
+  OzMaps maps;
+  for (int q = 0; q < OZ_S; ++q) {
+    if ((st = make_map(&maps.a[q], w.left + q * w.astride, w.ncp, 2 * w.np, BM, OZ_BKE)) != FQ_OK) return st;
+    if ((st = make_map(&maps.r[q], w.right + q * w.rstride, 3 * w.np, w.np, 3 * OZ_BN, OZ_BKE)) != FQ_OK) return st;
+  }
+  static std::atomic<unsigned> attr_set{0};
+  if (fq_first_on_device(attr_set)) {
+    cudaError_t e = cudaFuncSetAttribute(k_oz_term, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+    if (e != cudaSuccess) return fq_cuda_fail(e, "Ozaki kernel shared-memory attribute");
+  }
+  fq_blk<double> b0{w.m[0][0], w.m[0][1]};
+  if (identity) fq_launch_identity_f64(b0, nc, n, n, s);
+  else fq_launch_load_states(x0, b0, nc, n, n, s);
+  int xb = 0;
+  if (m_end > m_begin)
+    k_oz_slice_left<<<w.ncp, 256, 0, s>>>(w.m[0][0], w.m[0][1], n, nc, w.np, w.astride, w.left, w.es);
+  const int tiles_i = w.np / OZ_BN, tiles_j = w.ncp / BM;
+  const int nk = w.np / OZ_BKE;
+  fq_term t{};
+  t.coef0 = p->cheb[0];
+  t.ph_re = p->phase_re;
+  t.ph_im = p->phase_im;
+  t.bound2 = 1.0 + 1e-9;
+  t.status = p->d_status;
+  for (int m = m_begin; m < m_end; ++m) {
+    k_oz_omega<<<w.np, 256, 0, s>>>(omega_args(p, m), n, w.np, w.rstride, w.right, w.et);
+    int cur = xb, nxt = (xb + 1) % 3, acc = (xb + 2) % 3, prv = -1;
+    for (int l = 0; l < L; ++l) {
+      t.first = l == 0;
+      t.last = l == L - 1;
+      t.coef = p->cheb[l + 1];
+      const int out = l == 0 ? nxt : prv;
+      OzEpi e{};
+      e.n = n;
+      e.nc = nc;
+      e.cur_re = w.m[cur][0];
+      e.cur_im = w.m[cur][1];
+      e.prev_re = prv >= 0 ? w.m[prv][0] : w.m[cur][0];
+      e.prev_im = prv >= 0 ? w.m[prv][1] : w.m[cur][1];
+      e.acc_re = w.m[acc][0];
+      e.acc_im = w.m[acc][1];
+      e.out_re = w.m[out][0];
+      e.out_im = w.m[out][1];
+      e.es = w.es;
+      e.et = w.et;
+      e.t = t;
+      k_oz_term<<<tiles_i * tiles_j, OZ_THREADS, OZ_SMEM, s>>>(maps, nk, tiles_j, tiles_i, w.np, e);
+      if (!(t.last && m == m_end - 1))
+        k_oz_slice_left<<<w.ncp, 256, 0, s>>>(w.m[out][0], w.m[out][1], n, nc, w.np, w.astride, w.left, w.es);
+      if (t.last) {
+        xb = out;
+      } else {
+        prv = cur;
+        cur = out;
+      }
+    }
+  }
+  fq_blk<double> bx{w.m[xb][0], w.m[xb][1]};
+  if (transpose_out) fq_launch_store_transpose_f64(bx, x, n, n, s);
+  else fq_launch_store_states_f64(bx, x, nc, n, n, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fq_cuda_fail(e, "Ozaki kernels");
+  return FQ_OK;
+}

@@ -412,13 +412,14 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_boun
     return FQ_EINVAL;
   }
   if (p->drive_kind == FQ_DRIVE_PIECEWISE && !p->f_steps) { fq_set_error("piecewise drive needs f_steps"); return FQ_EINVAL; }
-  if (p->precision < FQ_FP64 || p->precision > FQ_DF32) { fq_set_error("bad precision %d", p->precision); return FQ_EINVAL; }
-  if (p->format == FQ_TRIDIAG && (p->precision == FQ_BF16X3 || p->precision == FQ_BF16X6)) {
+  if (p->precision < FQ_FP64 || p->precision > FQ_OZAKI) { fq_set_error("bad precision %d", p->precision); return FQ_EINVAL; }
+  if (p->format == FQ_TRIDIAG &&
+      (p->precision == FQ_BF16X3 || p->precision == FQ_BF16X6 || p->precision == FQ_OZAKI)) {
     fq_set_error("tridiagonal format supports FQ_FP64, FQ_FP32 and FQ_DF32");
     return FQ_EUNSUPPORTED;
   }
   if (p->format == FQ_DENSE && (p->precision == FQ_FP32 || p->precision == FQ_DF32)) {
-    fq_set_error("dense format supports FQ_FP64, FQ_BF16X3 and FQ_BF16X6");
+    fq_set_error("dense format supports FQ_FP64, FQ_BF16X3, FQ_BF16X6 and FQ_OZAKI");
     return FQ_EUNSUPPORTED;
   }
   const int n = p->n, M = p->steps;

@@ -87,3 +87,16 @@ def test_argument_errors(fq):
     with pytest.raises(fq.FloquetError) as e:
         fq.floquet_plan_inspect(prob)
     assert e.value.status == fq.FQ_EUNSUPPORTED
+    for prec in (fq.FQ_BF16X6, fq.FQ_OZAKI):
+        prob, keep = fq.make_problem(4, fq.FQ_TRIDIAG, np.zeros(4), np.zeros(4), 1.0, 2, h0_off=np.zeros(3),
+                                     precision=prec)
+        with pytest.raises(fq.FloquetError) as e:
+            fq.floquet_plan_inspect(prob)
+        assert e.value.status == fq.FQ_EUNSUPPORTED
+    prob, keep = fq.make_problem(4, fq.FQ_DENSE, np.eye(4), np.eye(4), 1.0, 2, precision=fq.FQ_OZAKI + 1)
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_plan_inspect(prob)
+    assert e.value.status == fq.FQ_EINVAL
+    prob, keep = fq.make_problem(4, fq.FQ_DENSE, np.eye(4), np.eye(4), 1.0, 2, precision=fq.FQ_OZAKI)
+    info, _ = fq.floquet_plan_inspect(prob)
+    assert info.precision == fq.FQ_OZAKI
