@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--workload", choices=["dimer", "dimer-paper"], default="dimer",
                     help="dimer: nb = 10^4, J = 1, U nb = 2, f = 1.5 cos 3t, M = 2000 (default); "
                          "dimer-paper: the paper's parameters (U/2)(n1 - n2)^2, f = 2.7 + 2.5 cos 3t, M = 8000")
-    ap.add_argument("--ncu-case", choices=["resident", "stream", "split", "tile", "adjoint"], default=None,
+    ap.add_argument("--ncu-case", choices=["resident", "stream", "split", "tile", "adjoint", "ozaki", "dense-resident"],
+                    default=None,
                     help="run one small capture case of a kernel twice and exit (for ncu --set full)")
     return ap.parse_args()
 
@@ -56,7 +57,10 @@ def run_ncu_case(case):
     stream:   2048 states through step 0 (39 streaming FP32 term launches, 0.5 GB of states);
     split:    dense GOE N = 4096 (seeds 3, 4), BF16X3 tensor-core terms of step 0 on the identity;
     tile:     2048 states through step 0 on the FP64 tiled kernel (0.65 GB of states);
-    adjoint:  the BF16X3 gradient at N = 1024 (seeds 6-9) over the first 16 of its 256 steps."""
+    adjoint:  the BF16X3 gradient at N = 1024 (seeds 6-9) over the first 16 of its 256 steps;
+    ozaki:    dense GOE N = 2048 (seeds 3, 4; A = 2, omega = 2, M = 64), FQ_OZAKI terms of step 0 on
+              the identity (0.25 GB of slices, 0.2 GB of FP64 states);
+    dense-resident: GOE N = 64 (seeds 1, 2), M = 200, the FP64 resident chain (4 launches)."""
     import math
     import torch
     import floquet_inputs as fi
@@ -72,6 +76,19 @@ def run_ncu_case(case):
             plan.grad(f, W)
         torch.cuda.synchronize()
         print(f"ncu case adjoint: status {plan.check_status()}")
+        return
+    if case in ("ozaki", "dense-resident"):
+        m = fi.config_goe4096(2048, 64) if case == "ozaki" else fi.config_goe64()
+        prec = fq.FQ_OZAKI if case == "ozaki" else fq.FQ_FP64
+        plan = fq.Plan.dense(m.h0, m.h1, omega=m.drive.omega, f_ac=m.drive.f_ac, steps=m.steps, precision=prec)
+        n = m.n
+        x0 = torch.eye(n, dtype=torch.complex128, device="cuda")
+        x = torch.empty_like(x0)
+        ws = fq.workspace(plan.workspace_size(n))
+        for _ in range(2):
+            fq.floquet_propagate(plan.handle, x0, x, n, 0, 1 if case == "ozaki" else m.steps, ws)
+        torch.cuda.synchronize()
+        print(f"ncu case {case}: status {plan.check_status()}, L = {plan.info.L}")
         return
     if case == "split":
         m = fi.config_goe4096()

@@ -5,19 +5,21 @@
 //
 // Splitting.  Every row r of an operand (a state row of Psi, re and im together; a row of
 // Omega~_m, S and A together) gets one power-of-two scale 2^e_r >= its largest entry.  x / 2^e_r
-// is cut into OZ_S digits of OZ_BITS bits,
-//   x = 2^e_r * sum_q d_q 2^(-8 (q+1)) + (remainder below 2^-48 of the scale),
-// |d_0| <= 256, |d_q| <= 128 after, each slice d_q 2^(-8(q+1)) exact in BF16.  The slices of a
-// row share one binary grid, so a product of slice a of the left and slice b of the right
-// operand is an integer multiple of 2^(-8(a+b+2)) and sums of such products are exact in FP32
-// while they stay below 2^24 units.
+// (|x / 2^e_r| < 1/2) is rounded to 48 fractional bits as a 64-bit integer and cut into OZ_S
+// signed digits of 8 bits by rounding shifts,
+//   x = 2^e_r * sum_q d_q 2^(-8 (q+1)) + (remainder below 2^-49 of the scale),  |d_q| <= 128,
+// each slice d_q 2^(-8(q+1)) exact in BF16 (integer work only: GB300 runs FP64 far below its
+// integer and FP32 rates).  The slices of a row share one binary grid, so a product of slice a
+// of the left and slice b of the right operand is an integer multiple of 2^(-8(a+b+2)) and sums
+// of such products are exact in FP32 while they stay below 2^24 units.
 //
 // Product.  Y[j][i] = sum_k Psi[j][k] (S[i][k] + i A[i][k]) takes the 21 slice pairs (a, b) with
 // a + b <= 5 (terms beyond carry less than 2^-48 of the scales).  Pairs with a + b = 0, 1, 2 go
 // to three exact accumulators, the rest (a + b >= 3, at most 2^-24 of the leading term) to a
-// fourth one whose FP32 rounding stays near 2^-48 relative.  Per 64 values of k the four
+// fourth one whose FP32 rounding stays near 2^-48 relative.  Per 128 values of k the four
 // accumulators are drained into double-float registers (an FP32 pair, about 48 bits) by the
-// epilogue warps: over 64 values of k the worst exact sum is 5 * 2^14 * 128 < 2^24 units.  The
+// epilogue warps: over 128 values of k (256 products per pair) the worst exact sum is
+// 3 pairs * 2^14 * 256 < 2^24 units.  The
 // complex product uses three right-operand blocks per row block, [-A; S; A]: Psi_r . [S; A]^T
 // and Psi_i . [-A; S]^T accumulate Yr and Yi side by side, two MMAs of N = 128 per pair.
 //
@@ -40,7 +42,7 @@ constexpr int OZ_PAIRS = OZ_S * (OZ_S + 1) / 2;
 constexpr int OZ_BN = 64;                   // complex output columns per tile
 constexpr int OZ_ROWB = 32;                 // bytes per K row of a stage (K = 16 BF16)
 constexpr int OZ_BKE = OZ_ROWB / 2;
-constexpr int OZ_KB_PER_DRAIN = 4;          // 64 values of k between drains
+constexpr int OZ_KB_PER_DRAIN = 8;          // 128 values of k between drains
 constexpr int OZ_STAGES = 2;
 constexpr int OZ_EPI_WARPS = 16;
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
@@ -92,46 +94,65 @@ __device__ __forceinline__ void oz_pair(int p, int& a, int& b) {
   b = d - a;
 }
 
-// (h, l) += v in double-float: two-sum, then a fast renormalisation
-__device__ __forceinline__ void dd_add(float& h, float& l, float v) {
-  const float s = __fadd_rn(h, v);
-  const float bb = __fsub_rn(s, h);
-  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(v, bb));
-  const float lo = __fadd_rn(l, e);
-  const float h2 = __fadd_rn(s, lo);
-  l = __fsub_rn(lo, __fsub_rn(h2, s));
+__device__ __forceinline__ float2 neg2f(float2 a) { return make_float2(-a.x, -a.y); }
+
+// (h, l) += v in double-float for two values at once (packed FP32x2): Knuth's two-sum, then a
+// fast renormalisation; explicitly rounded operations only
+__device__ __forceinline__ void dd_add2(float2& h, float2& l, float2 v) {
+  const float2 s = __fadd2_rn(h, v);
+  const float2 bb = __fadd2_rn(s, neg2f(h));
+  const float2 e = __fadd2_rn(__fadd2_rn(h, neg2f(__fadd2_rn(s, neg2f(bb)))), __fadd2_rn(v, neg2f(bb)));
+  const float2 lo = __fadd2_rn(l, e);
+  const float2 h2 = __fadd2_rn(s, lo);
+  l = __fadd2_rn(lo, neg2f(__fadd2_rn(h2, neg2f(s))));
   h = h2;
 }
 
 __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 
-// exponent e with |x| < 2^e for the row maximum m (0 for a zero row), kept in the normal range
-__device__ __forceinline__ int oz_exponent(double m) {
-  if (!(m > 0.0)) return 0;
-  int e;
-  frexp(m, &e);
+// |x| as an ordered integer key (the bit pattern of a non-negative double orders like its value)
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// row exponent E with |x| < 2^(E-1) for the row maximum (key of |max|; 0 for a zero row):
+// E = (unbiased exponent of max) + 2, kept in the normal range
+__device__ __forceinline__ int oz_exponent(unsigned long long key) {
+  if (key == 0) return 0;
+  const int be = (int)(key >> 52);  // biased exponent (subnormals: 0)
+  const int e = be - 1023 + 2;
   return e < -960 ? -960 : e;
 }
 
-// The digits of r = x / 2^e (|r| < 1) as BF16 slices d_q 2^(-8(q+1))
-__device__ __forceinline__ void oz_digits(double r, __nv_bfloat16 (&s)[OZ_S]) {
+// The digits of r = x / 2^E (|r| < 1/2): R = rint(r 2^48), then d_q by rounding shifts of 8 bits;
+// slices d_q 2^(-8(q+1)) in BF16.  `scale` = 2^(48 - E).
+__device__ __forceinline__ void oz_digits(double x, double scale, __nv_bfloat16 (&s)[OZ_S]) {
+  long long R = __double2ll_rn(x * scale);
 #pragma unroll
   for (int q = 0; q < OZ_S; ++q) {
-    const double t = r * 256.0;
-    const double d = rint(t);
-    s[q] = __float2bfloat16_rn((float)(d * pow2(-8 * (q + 1))));
-    r = t - d;
+    const int sh = 40 - 8 * q;
+    long long d;
+    if (sh > 0) {
+      d = (R + (1ll << (sh - 1))) >> sh;
+      R -= d << sh;
+    } else {
+      d = R;
+    }
+    s[q] = __float2bfloat16_rn((float)(int)d * __int_as_float((127 - 8 * (q + 1)) << 23));
   }
 }
 
-__device__ __forceinline__ double block_max(double v, double* red) {
+__device__ __forceinline__ unsigned long long block_max_key(unsigned long long v, unsigned long long* red) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
   const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if ((threadIdx.x & 31) == 0) red[w] = v;
   __syncthreads();
-  double m = 0.0;
-  for (int q = 0; q < nw; ++q) m = fmax(m, red[q]);
+  unsigned long long m = 0;
+  for (int q = 0; q < nw; ++q) m = red[q] > m ? red[q] : m;
   __syncthreads();
   return m;
 }
@@ -139,24 +160,27 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 // Left slices of the state rows: one CTA per row j of the padded block (rows >= nc are zero).
 __global__ void k_oz_slice_left(const double* __restrict__ re, const double* __restrict__ im, int n, int nc, int np,
                                 size_t astride, __nv_bfloat16* __restrict__ left, int* __restrict__ es) {
-  __shared__ double red[32];
+  __shared__ unsigned long long red[32];
   const int j = blockIdx.x;
-  double m = 0.0;
+  unsigned long long m = 0;
   if (j < nc)
-    for (int k = threadIdx.x; k < n; k += blockDim.x)
-      m = fmax(m, fmax(fabs(re[(size_t)j * n + k]), fabs(im[(size_t)j * n + k])));
-  const int e = oz_exponent(block_max(m, red));
-  const double inv = pow2(-e);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const unsigned long long a = abs_key(re[(size_t)j * n + k]), b = abs_key(im[(size_t)j * n + k]);
+      m = a > m ? a : m;
+      m = b > m ? b : m;
+    }
+  const int e = oz_exponent(block_max_key(m, red));
+  const double scale = pow2(48 - e);
   __nv_bfloat16* row = left + (size_t)j * 2 * np;
   for (int k = threadIdx.x; k < np; k += blockDim.x) {
     double xr = 0.0, xi = 0.0;
     if (j < nc && k < n) {
-      xr = re[(size_t)j * n + k] * inv;
-      xi = im[(size_t)j * n + k] * inv;
+      xr = re[(size_t)j * n + k];
+      xi = im[(size_t)j * n + k];
     }
     __nv_bfloat16 sr[OZ_S], si[OZ_S];
-    oz_digits(xr, sr);
-    oz_digits(xi, si);
+    oz_digits(xr, scale, sr);
+    oz_digits(xi, scale, si);
 #pragma unroll
     for (int q = 0; q < OZ_S; ++q) {
       row[q * astride + k] = sr[q];
@@ -188,24 +212,26 @@ __device__ __forceinline__ void oz_omega_entry(const OzOmega& a, int n, int i, i
 // Right slices of step m: one CTA per row i of the padded operator (rows >= n are zero).
 __global__ void k_oz_omega(const __grid_constant__ OzOmega a, int n, int np, size_t rstride,
                            __nv_bfloat16* __restrict__ right, int* __restrict__ et) {
-  __shared__ double red[32];
+  __shared__ unsigned long long red[32];
   const int i = blockIdx.x;
-  double m = 0.0;
+  unsigned long long m = 0;
   if (i < n)
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       double S, A;
       oz_omega_entry(a, n, i, k, S, A);
-      m = fmax(m, fmax(fabs(S), fabs(A)));
+      const unsigned long long x = abs_key(S), y = abs_key(A);
+      m = x > m ? x : m;
+      m = y > m ? y : m;
     }
-  const int e = oz_exponent(block_max(m, red));
-  const double inv = pow2(-e);
+  const int e = oz_exponent(block_max_key(m, red));
+  const double scale = pow2(48 - e);
   const size_t rb = (size_t)(3 * OZ_BN) * (i / OZ_BN) + (i % OZ_BN);  // row of -A; S and A follow
   for (int k = threadIdx.x; k < np; k += blockDim.x) {
     double S = 0.0, A = 0.0;
     if (i < n && k < n) oz_omega_entry(a, n, i, k, S, A);
     __nv_bfloat16 ss[OZ_S], sa[OZ_S];
-    oz_digits(S * inv, ss);
-    oz_digits(A * inv, sa);
+    oz_digits(S, scale, ss);
+    oz_digits(A, scale, sa);
 #pragma unroll
     for (int q = 0; q < OZ_S; ++q) {
       __nv_bfloat16* base = right + q * rstride + k;
@@ -315,7 +341,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           // descriptors of the stage's tiles: the start-address field is the low 14 bits (16-byte
           // units), so an offset inside shared memory adds to the descriptor without a carry
           const uint64_t d0 = oz_desc(st);
-#pragma unroll 1
+#pragma unroll
           for (int p = 0; p < OZ_PAIRS; ++p) {
             int a, b;
             oz_pair(p, a, b);
@@ -344,9 +370,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int quarter = warp & 3, part = (warp - 2) >> 2;
     const int j = j0 + quarter * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(part * 16);
-    float hr[16], lr[16], hi[16], li[16];
+    float2 hr[8], lr[8], hi[8], li[8];  // double-float sums of columns (2p, 2p + 1)
 #pragma unroll
-    for (int q = 0; q < 16; ++q) hr[q] = lr[q] = hi[q] = li[q] = 0.f;
+    for (int q = 0; q < 8; ++q) hr[q] = lr[q] = hi[q] = li[q] = make_float2(0.f, 0.f);
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       bool go = mbar_wait(tfull, c & 1);
@@ -364,12 +390,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           float v[16];
           tmem_ld16(trow + g * (2 * OZ_BN) + part_im * OZ_BN, v);
           tmem_wait_ld();
-          float* h = part_im ? hi : hr;
-          float* l = part_im ? li : lr;
+          float2* h = part_im ? hi : hr;
+          float2* l = part_im ? li : lr;
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            if (g < 3) dd_add(h[q], l[q], v[q]);
-            else l[q] = __fadd_rn(l[q], v[q]);  // below 2^-24 of the leading sum: the low word carries it
+          for (int q = 0; q < 8; ++q) {
+            const float2 w = make_float2(v[2 * q], v[2 * q + 1]);
+            if (g < 3) dd_add2(h[q], l[q], w);
+            else l[q] = __fadd2_rn(l[q], w);  // below 2^-24 of the leading sum: the low word carries it
           }
         }
       }
@@ -386,11 +413,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       float* xs = reinterpret_cast<float*>(gbase) + (threadIdx.x - 64);
       constexpr int XS = 32 * OZ_EPI_WARPS;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        xs[(4 * q) * XS] = hr[q];
-        xs[(4 * q + 1) * XS] = lr[q];
-        xs[(4 * q + 2) * XS] = hi[q];
-        xs[(4 * q + 3) * XS] = li[q];
+      for (int q = 0; q < 8; ++q) {
+        xs[(8 * q) * XS] = hr[q].x;
+        xs[(8 * q + 1) * XS] = lr[q].x;
+        xs[(8 * q + 2) * XS] = hi[q].x;
+        xs[(8 * q + 3) * XS] = li[q].x;
+        xs[(8 * q + 4) * XS] = hr[q].y;
+        xs[(8 * q + 5) * XS] = lr[q].y;
+        xs[(8 * q + 6) * XS] = hi[q].y;
+        xs[(8 * q + 7) * XS] = li[q].y;
       }
       const fq_term& t = e.t;
       const int ej = e.es[j];
@@ -399,9 +430,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       for (int q = 0; q < 16; ++q) {
         const int i = i0 + part * 16 + q;
         if (i >= e.n) break;
-        const double sc = pow2(ej + e.et[i]);
-        const double yr = ((double)xs[(4 * q) * XS] + (double)xs[(4 * q + 1) * XS]) * sc;
-        const double yi = ((double)xs[(4 * q + 2) * XS] + (double)xs[(4 * q + 3) * XS]) * sc;
+        const int ex = ej + e.et[i];
+        const double sc = pow2(ex < -1022 ? -1022 : ex);  // below that the product is below 2^-1022
+        const int b = 8 * (q >> 1) + 4 * (q & 1);  // slots of column q: hr, lr, hi, li
+        const double yr = ((double)xs[b * XS] + (double)xs[(b + 1) * XS]) * sc;
+        const double yi = ((double)xs[(b + 2) * XS] + (double)xs[(b + 3) * XS]) * sc;
         const size_t idx = (size_t)j * e.n + i;
         double pr, pi;
         if (t.first) {

@@ -105,3 +105,25 @@ def test_ozaki_goe4096_sampled(fq):
     err = np.max(np.abs(X - ref))
     print(f"GOE4096 Ozaki 8 steps: max err {err:.3e}")
     assert err <= TOL
+
+
+@pytest.mark.slow
+def test_ozaki_goe4096_full_build_sampled_columns(fq):
+    """The dense benchmark workload end to end in FP64 emulation (GOE N = 4096, M = 512): the U_T
+    the library builds against the oracle's propagation of 4 sampled basis states through all
+    512 steps, and the unitarity defect over 64 columns."""
+    import torch
+    m = fi.config_goe4096()
+    plan = fq.Plan.dense(m.h0, m.h1, omega=m.drive.omega, f_ac=m.drive.f_ac, steps=m.steps, precision=fq.FQ_OZAKI)
+    U = plan.build_UT()
+    assert plan.check_status() == fq.FQ_OK
+    cols = [0, 1500, 2047, 4095]
+    x0 = np.zeros((4096, len(cols)), complex)
+    x0[cols, np.arange(len(cols))] = 1.0
+    ref = o.propagate_dense(m.h0, m.h1, o.plan_for_drive_dense(m.h0, m.h1, m.drive, m.steps), x0)
+    err = np.max(np.abs(U[:, cols].cpu().numpy() - ref))
+    sample = torch.arange(0, 4096, 64, dtype=torch.int32, device="cuda")
+    mx, fro = fq.api.unitarity_defect(U, sample)
+    print(f"GOE4096 Ozaki full build: max err {err:.3e}; defect max {mx:.2e} fro {fro:.2e}")
+    assert err <= TOL
+    assert mx <= 1e-11
