@@ -178,7 +178,8 @@ fq_status floquet_unitarity_defect(const void* d_U, int32_t n, const int32_t* d_
  * Magnus-Chebyshev chain (Clenshaw-form adjoint of Eqs. 10-12) with X_m kept every
  * checkpoint_stride steps and recomputed in between.  Precision FQ_FP64 (SIMT FP64) or
  * FQ_BF16X3 / FQ_BF16X6 (tensor-core products on BF16 slices, FP32 accumulation and FP32
- * state masters; the loss, tau and the gradient sums stay FP64).  FQ_EUNSUPPORTED otherwise.
+ * state masters; the loss, tau and the gradient sums stay FP64), or FQ_OZAKI (tensor-core FP64
+ * emulation, FP64 states and epilogues).  FQ_EUNSUPPORTED otherwise.
  * d_ws: floquet_grad_workspace_size (256-byte aligned), else FQ_EINVAL. */
 size_t floquet_grad_workspace_size(const fq_plan* plan);
 fq_status floquet_grad(fq_plan* plan, const double* d_f, const void* d_W, double* d_loss,

@@ -322,9 +322,19 @@ void fq_launch_grad_reduce(const double2* partial, int ncta, int L, double* grad
   k_grad_reduce<<<1, 256, 0, s>>>(partial, ncta, L, grad_m);
 }
 
+void fq_launch_trace_f64(const double* W, const double* xr, const double* xi, int n, double2* partial,
+                         cudaStream_t s) {
+  k_trace_partials<<<n, 256, 0, s>>>((const double2*)W, xr, xi, n, partial);
+}
+
+void fq_launch_seed_f64(const double* W, const double2* tau, int n, double* gr, double* gi, cudaStream_t s) {
+  k_seed<<<grid_n((size_t)n * n), 256, 0, s>>>((const double2*)W, tau, n, gr, gi);
+}
+
 extern "C" size_t floquet_grad_workspace_size(const fq_plan* p) {
   if (!p || p->format != FQ_DENSE || p->drive_kind != FQ_DRIVE_PIECEWISE) return 0;
   if (p->precision == FQ_BF16X3 || p->precision == FQ_BF16X6) return fq_grad_split_workspace(p);
+  if (p->precision == FQ_OZAKI) return fq_grad_ozaki_workspace(p);
   return grad_layout(p, nullptr, nullptr);
 }
 
@@ -338,8 +348,9 @@ extern "C" fq_status floquet_grad(fq_plan* p, const double* d_f, const void* d_W
     fq_set_error("floquet_grad needs a dense plan with FQ_DRIVE_PIECEWISE");
     return FQ_EINVAL;
   }
-  if (p->precision != FQ_FP64 && p->precision != FQ_BF16X3 && p->precision != FQ_BF16X6) {
-    fq_set_error("floquet_grad: FQ_FP64, FQ_BF16X3 and FQ_BF16X6 are built");
+  if (p->precision != FQ_FP64 && p->precision != FQ_BF16X3 && p->precision != FQ_BF16X6 &&
+      p->precision != FQ_OZAKI) {
+    fq_set_error("floquet_grad: FQ_FP64, FQ_BF16X3, FQ_BF16X6 and FQ_OZAKI are built");
     return FQ_EUNSUPPORTED;
   }
   const size_t need = floquet_grad_workspace_size(p);
@@ -348,6 +359,7 @@ extern "C" fq_status floquet_grad(fq_plan* p, const double* d_f, const void* d_W
     return FQ_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (p->precision == FQ_OZAKI) return fq_grad_ozaki(p, d_f, d_W, d_loss, d_grad, d_ws, s);
   if (p->precision != FQ_FP64) return fq_grad_split(p, d_f, d_W, d_loss, d_grad, d_ws, s);
   GradWs w;
   grad_layout(p, d_ws, &w);

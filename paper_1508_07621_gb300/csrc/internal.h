@@ -158,7 +158,15 @@ void fq_launch_gauge_coeffs(const fq_plan* p, int m_begin, int nsteps, void* coe
 fq_status fq_launch_resident(const fq_plan* p, const void* coeff, const double* x0, double* x, int transpose_out,
                              int nc, int m_begin, int m_end, cudaStream_t s);
 
-// FP64 emulation on the tensor cores (ozaki.cu)
+// FP64 emulation on the tensor cores (ozaki.cu, ozaki_grad.cu)
+size_t fq_grad_ozaki_workspace(const fq_plan* p);
+fq_status fq_grad_ozaki(fq_plan* p, const double* d_f, const void* d_W, double* d_loss, double* d_grad, void* d_ws,
+                        cudaStream_t s);
+// FP64 loss pieces of adjoint.cu: tau partials over the rows of X_M (FP64 planar, stride n) and
+// the seed G_M = -tau W / N^2 as rows
+void fq_launch_trace_f64(const double* W, const double* xr, const double* xi, int n, double2* partial,
+                         cudaStream_t s);
+void fq_launch_seed_f64(const double* W, const double2* tau, int n, double* gr, double* gi, cudaStream_t s);
 size_t fq_ozaki_workspace(const fq_plan* p, int nc, void* base, void* out);
 fq_status fq_ozaki_propagate(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
                              int transpose_out, void* ws, cudaStream_t s);

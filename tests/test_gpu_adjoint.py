@@ -177,3 +177,62 @@ def test_fidelity_loss_autograd(fq):
         lm = fq.fidelity_loss(plan, cuda(fm - d * v), W).item()
     gv = float(g.cpu().numpy() @ v)
     assert abs((lp - lm) / (2 * d) - gv) <= 1e-6 * abs(gv)
+
+
+# ------------------------------------------------------------------ FP64 emulation (FQ_OZAKI)
+@pytest.mark.parametrize("n,M,stride", [(12, 20, 6), (33, 7, 1), (200, 12, 5), (130, 9, 16)])
+def test_ozaki_grad_matches_oracle(fq, n, M, stride):
+    """Gradient with every product in FP64 emulation on the tensor cores against the FP64 oracle,
+    held to the FP64 criterion (1e-9 of max |g|, loss to 1e-11): ragged tiles, ragged checkpoint
+    segments, s = 1 and a single segment."""
+    h0, h1 = fi.goe(n, 1901), fi.goe(n, 1902)
+    w = fi.haar_unitary(n, 1903)
+    fm = 1.0 + 0.1 * fi.normal(1904, M)
+    T = 2 * math.pi
+    plan = fq.Plan.piecewise(h0, h1, fm, period=T, checkpoint_stride=stride, precision=fq.FQ_OZAKI)
+    loss, g = plan.grad(cuda(fm), cuda(w.astype(np.complex128)))
+    assert plan.check_status() == fq.FQ_OK
+    g = g.cpu().numpy()
+    ref_plan = o.plan_piecewise(h0, h1, T, fm)
+    ref_loss, ref_g = o.grad_piecewise(h0, h1, w, ref_plan, fm)
+    err = np.max(np.abs(g - ref_g))
+    print(f"Ozaki grad n={n}: max err {err:.2e} (max |g| {np.max(np.abs(ref_g)):.2e}), "
+          f"loss err {abs(float(loss.item()) - ref_loss):.1e}")
+    assert abs(float(loss.item()) - ref_loss) <= 1e-11
+    assert err <= 1e-9 * np.max(np.abs(ref_g))
+
+
+def test_ozaki_grad_matches_fp64_path(fq):
+    """N = 512, M = 32: the emulated gradient against the plain FP64 GPU gradient (1e-9 of max |g|)."""
+    n, M = 512, 32
+    h0, h1 = fi.goe(n, 2001), fi.goe(n, 2002)
+    w = cuda(fi.haar_unitary(n, 2003).astype(np.complex128))
+    fm = 1.0 + 0.1 * fi.normal(2004, M)
+    T = 2 * math.pi
+    p64 = fq.Plan.piecewise(h0, h1, fm, period=T, checkpoint_stride=16)
+    poz = fq.Plan.piecewise(h0, h1, fm, period=T, checkpoint_stride=16, precision=fq.FQ_OZAKI)
+    l64, g64 = p64.grad(cuda(fm), w)
+    loz, goz = poz.grad(cuda(fm), w)
+    g64, goz = g64.cpu().numpy(), goz.cpu().numpy()
+    print(f"Ozaki vs FP64 grad n=512: {np.max(np.abs(goz - g64)):.2e} (max |g| {np.max(np.abs(g64)):.2e})")
+    assert abs(l64.item() - loz.item()) <= 1e-11
+    assert np.max(np.abs(goz - g64)) <= 1e-9 * np.max(np.abs(g64))
+
+
+def test_ozaki_grad_directional_fd(fq):
+    """<grad, v> against a central difference of the emulated loss along v (<= 1e-6 relative), at
+    the size of the FP64 finite-difference test (the gradient shrinks like 1/N, and at N = 512 the
+    loss's own rounding divided by the step would already reach the criterion)."""
+    n, M = 64, 32
+    h0, h1 = fi.goe(n, 1201), fi.goe(n, 1202)
+    w = cuda(fi.haar_unitary(n, 1203).astype(np.complex128))
+    fm = 1.0 + 0.1 * fi.normal(1204, M)
+    v = fi.normal(1205, M)
+    plan = fq.Plan.piecewise(h0, h1, fm, period=2 * math.pi, checkpoint_stride=8, precision=fq.FQ_OZAKI)
+    _, g = plan.grad(cuda(fm), w)
+    d = 1e-5
+    lp, _ = plan.grad(cuda(fm + d * v), w)
+    lm, _ = plan.grad(cuda(fm - d * v), w)
+    fd = (lp.item() - lm.item()) / (2 * d)
+    gv = float(g.cpu().numpy() @ v)
+    assert abs(fd - gv) <= 1e-6 * abs(gv)
