@@ -42,10 +42,16 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["dimer", "dimer-paper"], default="dimer",
+    ap.add_argument("--workload", choices=["dimer", "dimer-paper", "goe4096", "adjoint"], default="dimer",
                     help="dimer: nb = 10^4, J = 1, U nb = 2, f = 1.5 cos 3t, M = 2000 (default); "
-                         "dimer-paper: the paper's parameters (U/2)(n1 - n2)^2, f = 2.7 + 2.5 cos 3t, M = 8000")
-    ap.add_argument("--ncu-case", choices=["resident", "stream", "split", "tile", "adjoint", "ozaki", "dense-resident"],
+                         "dimer-paper: the paper's parameters (U/2)(n1 - n2)^2, f = 2.7 + 2.5 cos 3t, M = 8000; "
+                         "goe4096: dense GOE N = 4096 (seeds 3, 4), A = 2, omega = 2, M = 512, U_T builds/s; "
+                         "adjoint: gate-fidelity gradient, GOE N = 1024 (seeds 6-9), M = 256, s = 16, grads/s")
+    ap.add_argument("--precision", choices=["x3", "x6", "ozaki", "fp64"], default=None,
+                    help="goe4096 / adjoint: BF16X3 (default), BF16X6, FQ_OZAKI (FP64 emulation) or FP64 "
+                         "(adjoint only)")
+    ap.add_argument("--ncu-case", choices=["resident", "stream", "split", "tile", "adjoint", "ozaki", "dense-resident",
+                             "ozaki-grad"],
                     default=None,
                     help="run one small capture case of a kernel twice and exit (for ncu --set full)")
     return ap.parse_args()
@@ -58,6 +64,7 @@ def run_ncu_case(case):
     split:    dense GOE N = 4096 (seeds 3, 4), BF16X3 tensor-core terms of step 0 on the identity;
     tile:     2048 states through step 0 on the FP64 tiled kernel (0.65 GB of states);
     adjoint:  the BF16X3 gradient at N = 1024 (seeds 6-9) over the first 16 of its 256 steps;
+    ozaki-grad: the same in FP64 emulation (FQ_OZAKI);
     ozaki:    dense GOE N = 2048 (seeds 3, 4; A = 2, omega = 2, M = 64), FQ_OZAKI terms of step 0 on
               the identity (0.25 GB of slices, 0.2 GB of FP64 states);
     dense-resident: GOE N = 64 (seeds 1, 2), M = 200, the FP64 resident chain (4 launches)."""
@@ -65,17 +72,18 @@ def run_ncu_case(case):
     import torch
     import floquet_inputs as fi
     import paper_1508_07621_gb300 as fq
-    if case == "adjoint":
+    if case in ("adjoint", "ozaki-grad"):
         n, M = 1024, 16
         fm = 1.0 + 0.1 * fi.normal(9, 256)[:M]
         plan = fq.Plan.piecewise(fi.goe(n, 6), fi.goe(n, 7), fm, period=2 * math.pi * M / 256,
-                                 checkpoint_stride=16, precision=fq.FQ_BF16X3, tile_n=64)
+                                 checkpoint_stride=16, tile_n=64,
+                                 precision=fq.FQ_BF16X3 if case == "adjoint" else fq.FQ_OZAKI)
         W = torch.tensor(fi.haar_unitary(n, 8), dtype=torch.complex128, device="cuda")
         f = torch.tensor(fm, device="cuda")
         for _ in range(2):
             plan.grad(f, W)
         torch.cuda.synchronize()
-        print(f"ncu case adjoint: status {plan.check_status()}")
+        print(f"ncu case {case}: status {plan.check_status()}")
         return
     if case in ("ozaki", "dense-resident"):
         m = fi.config_goe4096(2048, 64) if case == "ozaki" else fi.config_goe64()
@@ -116,6 +124,18 @@ def run_ncu_case(case):
         fq.floquet_propagate(plan.handle, x0, x, nc, 0, m_end, ws)
     torch.cuda.synchronize()
     print(f"ncu case {case}: {nc} states, steps 0..{m_end - 1}, status {plan.check_status()}")
+
+
+def measured_peaks():
+    """The driver-written measured peaks (HBM copy, cuBLAS bf16 burst and sustained), else the
+    earlier fallback measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            m = json.load(fh)
+        return {"hbm_gbs": m["hbm_gbs"], "bf16": m["bf16_tflops"], "bf16_sustained": m["bf16_tflops_sustained"],
+                "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
 
 
 def dist_env():
@@ -399,11 +419,330 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------- dense and gradient workloads
+PREC_NAMES = {"x3": "FQ_BF16X3", "x6": "FQ_BF16X6", "ozaki": "FQ_OZAKI", "fp64": "FQ_FP64"}
+SLICE_PRODUCTS = {"x3": 3, "x6": 6, "ozaki": 21, "fp64": 1}
+
+
+def timed_loop(fn, steps, stream, world, dist):
+    """CUDA-event timing of `steps` calls of fn on `stream`, barrier + synchronize on both sides;
+    returns (per-call seconds, total seconds, clock record)."""
+    import torch
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.5)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(steps):
+        fn()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    return [ev[k].elapsed_time(ev[k + 1]) / 1000.0 for k in range(steps)], ev[0].elapsed_time(ev[-1]) / 1000.0, clk
+
+
+def dense_oracle_sample(m, states=64, steps=4):
+    """FP64 oracle (numpy, BLAS on every host core) on `states` basis states over the first `steps`
+    steps of the dense workload; returns (U_T/s scaled to the full build, seconds, description,
+    (idx, x, steps))."""
+    import numpy as np
+    import oracle as o
+    plan = o.plan_for_drive_dense(m.h0, m.h1, m.drive, m.steps)
+    idx = np.linspace(0, m.n - 1, states).astype(int)
+    x0 = np.zeros((m.n, states), complex)
+    x0[idx, np.arange(states)] = 1.0
+    t0 = time.perf_counter()
+    x = o.propagate_dense(m.h0, m.h1, plan, x0, 0, steps)
+    dt = time.perf_counter() - t0
+    frac = (states / m.n) * (steps / m.steps)
+    desc = f"{states} of {m.n} basis states over {steps} of {m.steps} steps (FP64 numpy oracle, BLAS threads)"
+    return frac / dt, dt, desc, (idx, x, steps)
+
+
+def adjoint_oracle_sample(a, steps=2):
+    """FP64 oracle gradient of the sub-problem made of the first `steps` steps (same N, same step
+    length); returns (gradients/s scaled to M steps, seconds, description, (loss, g, f, T))."""
+    import oracle as o
+    M = len(a.f)
+    fm = a.f[:steps]
+    T = a.period * steps / M
+    plan = o.plan_piecewise(a.h0, a.h1, T, fm)
+    t0 = time.perf_counter()
+    loss, g = o.grad_piecewise(a.h0, a.h1, a.target, plan, fm)
+    dt = time.perf_counter() - t0
+    desc = (f"oracle gradient of the first {steps} of {M} steps at N = {a.h0.shape[0]} (FP64 numpy, BLAS "
+            f"threads), scaled by {M}/{steps}")
+    return (steps / M) / dt, dt, desc, (loss, g, fm, T)
+
+
+def run_dense(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import floquet_inputs as fi
+    import paper_1508_07621_gb300 as fq
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = args.precision or "x3"
+    if prec == "fp64":
+        raise SystemExit("goe4096 in plain FP64 takes about 20 minutes per U_T; use x3, x6 or ozaki")
+    m = fi.config_goe4096()
+    f_ac = rank_drive_amplitude(m.drive.f_ac, rank)
+    n = m.n
+    precision = getattr(fq, PREC_NAMES[prec])
+    stream = torch.cuda.current_stream()
+    plan = fq.Plan.dense(m.h0, m.h1, omega=m.drive.omega, f_ac=f_ac, steps=m.steps, precision=precision)
+    ws = fq.workspace(plan.workspace_size())
+    tile = plan.autotune(ws) if prec != "ozaki" else 0
+    L = plan.info.L
+    U = torch.empty((n, n), dtype=torch.complex128, device="cuda")
+    for _ in range(max(args.warmup, 0)):
+        fq.floquet_build_UT(plan.handle, U, ws, stream)
+    torch.cuda.synchronize()
+    if plan.check_status() != fq.FQ_OK:
+        raise RuntimeError("device check fired during warm-up")
+    per_step, total, clk = timed_loop(lambda: fq.floquet_build_UT(plan.handle, U, ws, stream), args.steps, stream,
+                                      world, dist)
+    value, total = job_throughput(total, args.steps, dist if world > 1 else None, "cuda")
+    status_ok = plan.check_status() == fq.FQ_OK
+    sample_cols = torch.arange(0, n, n // 64, dtype=torch.int32, device="cuda")[:64]
+    defect_max, defect_fro = fq.api.unitarity_defect(U, sample_cols)
+    # end to end: plan from host arrays (H0, H1 uploaded inside the call), build, U_T to pinned host
+    host_u = torch.empty((n, n), dtype=torch.complex128, pin_memory=True)
+    e2e_times = []
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p2 = fq.Plan.dense(m.h0, m.h1, omega=m.drive.omega, f_ac=f_ac, steps=m.steps, precision=precision,
+                           tile_n=tile)
+        fq.floquet_build_UT(p2.handle, U, ws, stream)
+        host_u.copy_(U, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        p2.close()
+    e2e_value = world / statistics.median(e2e_times)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    useful = 8.0 * n ** 3 * L * m.steps
+    issued = useful * SLICE_PRODUCTS[prec]
+    avg = statistics.mean(per_step)
+    achieved = issued / avg / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
+                "frac": achieved / peaks["bf16_sustained"], "traffic": None,
+                "kernel": "k_oz_term<false, OZ_FWD>" if prec == "ozaki" else "k_split_persist",
+                "useful_tflops": useful / avg / 1e12,
+                "note": (f"issued BF16 MMA flop = {SLICE_PRODUCTS[prec]} slice products x 8 N^3 per term x M L terms "
+                         "per build over the build's CUDA-event time (the operator and slicing kernels, a few "
+                         f"percent, included); peak: {peaks['source']} sustained cuBLAS bf16 (a build is seconds "
+                         "of back-to-back GEMMs)")}
+    accuracy = {"unitarity_defect_max": defect_max, "unitarity_defect_fro": defect_fro,
+                "defect_columns": int(sample_cols.numel())}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, dt, desc, (idx, xs, nst) = dense_oracle_sample(m)
+        cpu = {"value": v, "unit": "U_T/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+        rows = torch.zeros((len(idx), n), dtype=torch.complex128, device="cuda")
+        rows[torch.arange(len(idx)), torch.as_tensor(idx, device="cuda")] = 1.0
+        got = plan.propagate(rows, 0, nst).cpu().numpy().T
+        accuracy["sample_max_err_vs_oracle"] = float(np.max(np.abs(got - xs)))
+        accuracy["sample"] = desc
+    launches = 2 + m.steps * (1 + (2 * L if prec == "ozaki" else L))
+    line = {"metric": f"U_T builds/sec (dense GOE N={n}, M={m.steps})", "value": value, "unit": "U_T/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 slices, f64 states" if prec == "ozaki" else "bf16 slices, f32 accumulate",
+            "data": "synthetic",
+            "config": {"workload": f"dense GOE N={n} (seeds 3, 4), A=2, omega=2, M={m.steps}, L={L}, "
+                                   f"{PREC_NAMES[prec]}",
+                       "n": n, "steps_per_period": m.steps, "chebyshev_L": L, "R": plan.info.R, "tile_n": tile,
+                       "l2": "working set larger than L2 (operand slices and states, > 1 GB)",
+                       "parallelism": f"weak: {world} independent drive amplitudes"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "U_T/s", "h2d_bytes_per_step": 16 * n * n + 24 * m.steps,
+                    "d2h_bytes_per_step": 16 * n * n},
+            "gpu_launches": launches * args.steps, "clocks": clk, "device_status_ok": status_ok,
+            "accuracy": accuracy, "median_step_s": statistics.median(per_step), "per_step_s": per_step,
+            "host": host_info()}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_adjoint(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import floquet_inputs as fi
+    import paper_1508_07621_gb300 as fq
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = args.precision or "x3"
+    a = fi.config_adjoint()
+    n, M = a.h0.shape[0], len(a.f)
+    fm = a.f + 0.01 * rank  # rank r: its own initial amplitudes (an independent problem)
+    precision = getattr(fq, PREC_NAMES[prec])
+    stream = torch.cuda.current_stream()
+    tile = 64 if prec in ("x3", "x6") else 0
+    plan = fq.Plan.piecewise(a.h0, a.h1, fm, period=a.period, checkpoint_stride=16, precision=precision, tile_n=tile)
+    L = plan.info.L
+    f = torch.tensor(fm, device="cuda")
+    W = torch.tensor(a.target, dtype=torch.complex128, device="cuda")
+    ws = fq.workspace(fq.floquet_grad_workspace_size(plan.handle))
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty(M, dtype=torch.float64, device="cuda")
+
+    def step():
+        fq.floquet_grad(plan.handle, f, W, loss, g, ws, stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    if plan.check_status() != fq.FQ_OK:
+        raise RuntimeError("device check fired during warm-up")
+    per_step, total, clk = timed_loop(step, args.steps, stream, world, dist)
+    value, total = job_throughput(total, args.steps, dist if world > 1 else None, "cuda")
+    status_ok = plan.check_status() == fq.FQ_OK
+    loss_value = float(loss.item())
+    # end to end: plan from host arrays, f and W from pinned host memory, gradient and loss back
+    f_h = torch.tensor(fm).pin_memory()
+    w_h = torch.tensor(a.target, dtype=torch.complex128).pin_memory()
+    g_h = torch.empty(M, dtype=torch.float64).pin_memory()
+    l_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p2 = fq.Plan.piecewise(a.h0, a.h1, fm, period=a.period, checkpoint_stride=16, precision=precision,
+                               tile_n=tile)
+        f.copy_(f_h, non_blocking=True)
+        W.copy_(w_h, non_blocking=True)
+        fq.floquet_grad(p2.handle, f, W, loss, g, ws, stream)
+        g_h.copy_(g, non_blocking=True)
+        l_h.copy_(loss, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        p2.close()
+    e2e_value = world / statistics.median(e2e_times)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    # products per gradient: the forward, recompute and adjoint chains (M L each) and the L dots
+    # of every step; each is complex states x real operator, 4 N^3 useful flop
+    useful = 4.0 * M * L * 4.0 * n ** 3
+    issued = useful * SLICE_PRODUCTS[prec]
+    avg = statistics.mean(per_step)
+    achieved = issued / avg / 1e12
+    if prec == "fp64":
+        roofline = {"bound": "alu", "achieved": achieved, "peak": 1.19, "unit": "TFLOP/s", "frac": achieved / 1.19,
+                    "traffic": None, "kernel": "k_adj_term / k_dot / dense_tile_f64",
+                    "note": "FP64 SIMT; peak = the FP64 rate measured with the dense FP64 term kernel (1.19 TF)"}
+    else:
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
+                    "frac": achieved / peaks["bf16_sustained"], "traffic": None,
+                    "kernel": "k_oz_term<true, *>" if prec == "ozaki" else "k_split_persist / k_split_term",
+                    "useful_tflops": useful / avg / 1e12,
+                    "note": (f"issued BF16 MMA flop = {SLICE_PRODUCTS[prec]} slice products x 4 M L x 4 N^3 per "
+                             "gradient over the gradient's CUDA-event time (every other kernel included); peak: "
+                             f"{peaks['source']} sustained cuBLAS bf16")}
+    accuracy = {"loss": loss_value}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, dt, desc, (rl, rg, fs, Ts) = adjoint_oracle_sample(a)
+        cpu = {"value": v, "unit": "grads/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+        ps = fq.Plan.piecewise(a.h0, a.h1, fs, period=Ts, checkpoint_stride=16, precision=precision, tile_n=tile)
+        ls, gs = ps.grad(torch.tensor(fs, device="cuda"), W)
+        accuracy["sample_grad_max_err_vs_oracle"] = float(np.max(np.abs(gs.cpu().numpy() - rg)))
+        accuracy["sample_grad_max_abs"] = float(np.max(np.abs(rg)))
+        accuracy["sample_loss_err_vs_oracle"] = abs(float(ls.item()) - rl)
+        accuracy["sample"] = desc
+    line = {"metric": f"gradients/sec (gate fidelity, GOE N={n}, M={M} piecewise steps, checkpoints every 16)",
+            "value": value, "unit": "grads/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": {"x3": "bf16 slices, f32 accumulate", "x6": "bf16 slices, f32 accumulate",
+                      "ozaki": "bf16 slices, f64 states", "fp64": "f64"}[prec],
+            "data": "synthetic",
+            "config": {"workload": f"adjoint: GOE N={n} (seeds 6, 7), Haar W (seed 8), f ~ N(1, 0.1^2) (seed 9), "
+                                   f"M={M}, s=16, L={L}, {PREC_NAMES[prec]}",
+                       "n": n, "steps": M, "chebyshev_L": L,
+                       "l2": "working set larger than L2 (checkpoints and kept slices, > 1 GB)",
+                       "parallelism": f"weak: {world} independent amplitude vectors"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "grads/s", "h2d_bytes_per_step": 2 * 8 * n * n + 8 * M + 16 * n * n,
+                    "d2h_bytes_per_step": 8 * M + 8},
+            "clocks": clk, "device_status_ok": status_ok, "accuracy": accuracy,
+            "median_step_s": statistics.median(per_step), "per_step_s": per_step, "host": host_info()}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference_other(args):
+    """--impl reference for goe4096 / adjoint: the oracle on a bounded sample, same metric."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import floquet_inputs as fi
+    vals, desc = [], ""
+    if args.workload == "goe4096":
+        m = fi.config_goe4096()
+        for _ in range(args.warmup):
+            dense_oracle_sample(m, states=8, steps=1)
+        for _ in range(args.steps):
+            v, dt, desc, _ = dense_oracle_sample(m)
+            vals.append(v)
+        metric, unit = f"U_T builds/sec (dense GOE N={m.n}, M={m.steps})", "U_T/s"
+        cfg = f"dense GOE N={m.n} (seeds 3, 4), A=2, omega=2, M={m.steps}"
+    else:
+        a = fi.config_adjoint()
+        for _ in range(args.warmup):
+            adjoint_oracle_sample(a, steps=1)
+        for _ in range(args.steps):
+            v, dt, desc, _ = adjoint_oracle_sample(a)
+            vals.append(v)
+        metric = (f"gradients/sec (gate fidelity, GOE N={a.h0.shape[0]}, M={len(a.f)} piecewise steps, "
+                  "checkpoints every 16)")
+        unit = "grads/s"
+        cfg = f"adjoint: GOE N={a.h0.shape[0]}, M={len(a.f)}"
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": cfg},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": os.cpu_count(), "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.ncu_case:
         run_ncu_case(a.ncu_case)
     elif a.impl == "reference":
-        run_reference(a)
+        if a.workload in ("goe4096", "adjoint"):
+            run_reference_other(a)
+        else:
+            run_reference(a)
+    elif a.workload == "goe4096":
+        run_dense(a)
+    elif a.workload == "adjoint":
+        run_adjoint(a)
     else:
         run_ours(a)

@@ -194,6 +194,11 @@ __device__ __forceinline__ void oz_row_value(const double* re, const double* im,
   vi = cr * b + ci * a;
 }
 
+__device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c, __nv_bfloat16 d) {
+  return make_uint2((uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16),
+                    (uint32_t)__bfloat16_as_ushort(c) | ((uint32_t)__bfloat16_as_ushort(d) << 16));
+}
+
 __global__ void k_oz_slice_left(const double* __restrict__ re, const double* __restrict__ im, double cr, double ci,
                                 double* __restrict__ out_re, double* __restrict__ out_im, int n, int nc, int np,
                                 size_t astride, __nv_bfloat16* __restrict__ left, int* __restrict__ es) {
@@ -215,16 +220,21 @@ __global__ void k_oz_slice_left(const double* __restrict__ re, const double* __r
   const int e = oz_exponent(block_max_key(m, red));
   const double scale = pow2(48 - e);
   __nv_bfloat16* row = left + (size_t)j * 2 * np;
-  for (int k = threadIdx.x; k < np; k += blockDim.x) {
-    double xr = 0.0, xi = 0.0;
-    if (j < nc && k < n) oz_row_value(re, im, cr, ci, n, j, k, xr, xi);
-    __nv_bfloat16 sr[OZ_S], si[OZ_S];
-    oz_digits(xr, scale, sr);
-    oz_digits(xi, scale, si);
+  // four consecutive columns per thread: one 8-byte store per slice and part (np % 4 == 0, and
+  // every slice row starts on an 8-byte boundary)
+  for (int k0 = 4 * threadIdx.x; k0 < np; k0 += 4 * blockDim.x) {
+    __nv_bfloat16 sr[4][OZ_S], si[4][OZ_S];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      double xr = 0.0, xi = 0.0;
+      if (j < nc && k0 + u < n) oz_row_value(re, im, cr, ci, n, j, k0 + u, xr, xi);
+      oz_digits(xr, scale, sr[u]);
+      oz_digits(xi, scale, si[u]);
+    }
 #pragma unroll
     for (int q = 0; q < OZ_S; ++q) {
-      row[q * astride + k] = sr[q];
-      row[q * astride + np + k] = si[q];
+      *reinterpret_cast<uint2*>(row + q * astride + k0) = pack4(sr[0][q], sr[1][q], sr[2][q], sr[3][q]);
+      *reinterpret_cast<uint2*>(row + q * astride + np + k0) = pack4(si[0][q], si[1][q], si[2][q], si[3][q]);
     }
   }
   if (threadIdx.x == 0) es[j] = e;
@@ -306,12 +316,16 @@ __global__ void k_oz_real(const double* __restrict__ h0, const double* __restric
     }
   const int e = oz_exponent(block_max_key(mx, red));
   const double scale = pow2(48 - e);
-  for (int k = threadIdx.x; k < np; k += blockDim.x) {
-    const double v = (i < n && k < n) ? oz_real_entry(h0, h1, c1, inv, shift, n, i, k) : 0.0;
-    __nv_bfloat16 sl[OZ_S];
-    oz_digits(v, scale, sl);
+  for (int k0 = 4 * threadIdx.x; k0 < np; k0 += 4 * blockDim.x) {
+    __nv_bfloat16 sl[4][OZ_S];
 #pragma unroll
-    for (int q = 0; q < OZ_S; ++q) right[q * rstride + (size_t)i * np + k] = sl[q];
+    for (int u = 0; u < 4; ++u) {
+      const double v = (i < n && k0 + u < n) ? oz_real_entry(h0, h1, c1, inv, shift, n, i, k0 + u) : 0.0;
+      oz_digits(v, scale, sl[u]);
+    }
+#pragma unroll
+    for (int q = 0; q < OZ_S; ++q)
+      *reinterpret_cast<uint2*>(right + q * rstride + (size_t)i * np + k0) = pack4(sl[0][q], sl[1][q], sl[2][q], sl[3][q]);
   }
   if (threadIdx.x == 0) et[i] = e;
 }
