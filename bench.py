@@ -8,6 +8,10 @@ work per GPU is fixed and no collective touches the data path ("scaling": "weak"
 
 --impl reference times the FP64 CPU oracle on this host on a bounded sample of the same
 workload (a few states over a slice of the period) and reports the same metric.
+
+--workload goe4096 (dense GOE N = 4096, M = 512: U_T builds/s) and --workload adjoint (the
+gate-fidelity gradient at N = 1024, M = 256: gradients/s), with --precision x3 | x6 | ozaki
+(| fp64 for the gradient), print the same contract for the metric's other parts.
 """
 from __future__ import annotations
 
