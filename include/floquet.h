@@ -69,9 +69,10 @@ typedef enum fq_precision {
   FQ_FP32 = 1,          /* FP32 storage and FP32 arithmetic (tridiagonal format) */
   FQ_BF16X3 = 2,        /* dense: 2-slice BF16 split, products hi*hi + hi*lo + lo*hi, FP32 accumulate */
   FQ_BF16X6 = 3,        /* dense: 3-slice BF16 split, 6 slice products, FP32 accumulate */
-  FQ_DF32 = 4,          /* tridiagonal: double-float arithmetic (each value a pair of FP32 numbers,
-                           about 48 significant bits) on the FP32 pipes; FP64 states in HBM; tiled
-                           kernel (L <= 128); FP64-level results */
+  FQ_DF32 = 4,          /* double-float arithmetic (each value a pair of FP32 numbers, about 48
+                           significant bits) on the FP32 pipes; FP64 states in HBM; FP64-level
+                           results.  Tridiagonal: tiled kernel (L <= 128); dense: resident
+                           kernel (N <= 128, L <= 128); FQ_EUNSUPPORTED otherwise */
   FQ_OZAKI = 5          /* dense: FP64 emulation on the BF16 tensor cores (Ozaki-style splitting):
                            six 8-bit fixed-point slices per row, 21 slice products, exact FP32
                            partial sums combined in double-float; FP64 states; FP64-level results */

@@ -193,7 +193,7 @@ fq_status propagate_impl(fq_plan* p, const double* x0, double* x, int nc, int m_
     if (st != FQ_OK) return st;
     return cuda_ok(cudaGetLastError(), "FP64-emulation chain");
   }
-  const bool f64 = p->precision == FQ_FP64;
+  const bool f64 = p->precision == FQ_FP64 || p->path == PATH_DENSE_F64;  // dense FQ_DF32: FP64 states
   const int ld = p->path == PATH_DENSE_F64 ? n : tri_ld(n);
   if (p->path == PATH_TRI_STREAM) {
     if (f64) {
@@ -280,7 +280,9 @@ fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
       default: p->path = res_ok ? PATH_TRI_RESIDENT : (tile_ok ? PATH_TRI_TILE : PATH_TRI_STREAM);
     }
   } else {
-    p->path = p->precision == FQ_FP64 ? PATH_DENSE_F64 : (p->precision == FQ_OZAKI ? PATH_DENSE_OZAKI : PATH_DENSE_SPLIT);
+    p->path = (p->precision == FQ_FP64 || p->precision == FQ_DF32)
+                  ? PATH_DENSE_F64
+                  : (p->precision == FQ_OZAKI ? PATH_DENSE_OZAKI : PATH_DENSE_SPLIT);
   }
   cudaGetDevice(&p->device);
   auto fail = [&](cudaError_t e, const char* what) {
@@ -383,8 +385,14 @@ fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
   if (p->path == PATH_DENSE_F64) {
     // small dense problems: one resident launch per chunk of steps instead of one per term
     const bool ok = fq_dense_resident_supported(n, p->L);
-    if (prob->kernel == FQ_KERNEL_RESIDENT && !ok) {
-      fq_set_error("dense resident kernel needs N <= 128 and L <= 128 (N = %d, L = %d)", n, p->L);
+    const bool need = prob->kernel == FQ_KERNEL_RESIDENT || p->precision == FQ_DF32;
+    if (need && !ok) {
+      fq_set_error("dense resident kernel (and dense FQ_DF32) needs N <= 128 and L <= 128 (N = %d, L = %d)", n, p->L);
+      free_plan(p);
+      return FQ_EUNSUPPORTED;
+    }
+    if (p->precision == FQ_DF32 && prob->kernel != FQ_KERNEL_AUTO && prob->kernel != FQ_KERNEL_RESIDENT) {
+      fq_set_error("dense FQ_DF32 runs on the resident kernel only");
       free_plan(p);
       return FQ_EUNSUPPORTED;
     }

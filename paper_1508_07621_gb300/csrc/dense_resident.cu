@@ -19,12 +19,17 @@
 // Omega~_m for the chunk's steps is formed beforehand in HBM (it is L2-resident: 64 steps x
 // 2 x N^2 doubles = 4 MB at N = 64) by one batched launch (order 4) or one launch per step
 // (order 6).
+//
+// FQ_DF32 runs the same chain in double-float arithmetic (dfl.cuh) on the FP32 pipes, which
+// GB300 runs at many times its FP64 rate: Omega~ is converted once per step to FP32 pairs, the
+// state lives in shared memory as packed complex pairs, and the states in HBM stay FP64.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
 #include <algorithm>
 
+#include "dfl.cuh"
 #include "internal.h"
 
 namespace {
@@ -143,6 +148,117 @@ __global__ void __launch_bounds__(DR_ROWS* KG)
   if (C > 1) cluster_sync_all();  // no CTA leaves while a peer could still address its memory
 }
 
+__device__ __forceinline__ void st_cluster_f32x4(const void* local, unsigned rank, float4 v) {
+  const unsigned la = (unsigned)__cvta_generic_to_shared(local);
+  unsigned ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(rank));
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(ra), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
+__device__ __forceinline__ dflc dflc_shfl_xor(dflc a, int o) {
+  return {make_float2(__shfl_xor_sync(0xffffffffu, a.h.x, o), __shfl_xor_sync(0xffffffffu, a.h.y, o)),
+          make_float2(__shfl_xor_sync(0xffffffffu, a.l.x, o), __shfl_xor_sync(0xffffffffu, a.l.y, o))};
+}
+
+// The chain of k_dense_resident in double-float arithmetic: S, A as FP32 pairs [nsteps][n][n]
+// (float2 = (hi, lo)), the state as packed complex pairs in shared memory.
+template <int KG>
+__global__ void __launch_bounds__(DR_ROWS* KG)
+    k_dense_resident_dfl(const float2* __restrict__ S, const float2* __restrict__ A, int n, int nsteps, int L, int C,
+                         DrCoef cf, double ph_re, double ph_im, double bound2, double* xr, double* xi,
+                         unsigned* status) {
+  constexpr int NT = DR_ROWS * KG;
+  constexpr int NV = KG * DR_KPT;
+  __shared__ dflc phi[2][NV];
+  const int t = threadIdx.x, rl = t / KG, g = t % KG;
+  const unsigned rank = C > 1 ? cluster_rank() : 0u;
+  const int j = blockIdx.x / C;
+  const int i = (int)rank * DR_ROWS + rl;
+  const bool own = g == 0 && i < n;
+  const dflc zc = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  for (int q = t; q < 2 * NV; q += NT) {
+    const int b = q / NV, k = q % NV;
+    dflc v = zc;
+    if (b == 0 && k < n) {
+      const dfl r = dfl_of(xr[(size_t)j * n + k]), m = dfl_of(xi[(size_t)j * n + k]);
+      v = {make_float2(r.h, m.h), make_float2(r.l, m.l)};
+    }
+    phi[b][k] = v;
+  }
+  __syncthreads();
+  if (C > 1) cluster_sync_all();
+  const size_t nn = (size_t)n * n;
+  const dfl ph_c = dfl_of(ph_re), ph_s = dfl_of(ph_im);
+  int buf = 0;
+  bool bad = false;
+  for (int m = 0; m < nsteps; ++m) {
+    dfl s[DR_KPT], a[DR_KPT];
+#pragma unroll
+    for (int q = 0; q < DR_KPT; ++q) {
+      const int k = g + KG * q;
+      const bool ok = i < n && k < n;
+      const float2 sv = ok ? S[m * nn + (size_t)i * n + k] : make_float2(0.f, 0.f);
+      const float2 av = ok ? A[m * nn + (size_t)i * n + k] : make_float2(0.f, 0.f);
+      s[q] = dfl{sv.x, sv.y};
+      a[q] = dfl{av.x, av.y};
+    }
+    dflc acc = zc, pv = zc;
+    for (int l = 0; l < L; ++l) {
+      dflc ys = zc, ya = zc;  // S phi and i A phi, two independent chains
+#pragma unroll
+      for (int q = 0; q < DR_KPT; ++q) {
+        const dflc v = phi[buf][g + KG * q];
+        ys = dflc_fma(s[q], v, ys);
+        ya = dflc_ifma2(a[q], v, ya);
+      }
+      dflc y = dflc_add(ys, ya);
+#pragma unroll
+      for (int o = KG / 2; o > 0; o >>= 1) y = dflc_add(y, dflc_shfl_xor(y, o));
+      if (own) {
+        const dflc cur = phi[buf][i];
+        // -i y (first product) or -2i y + phi_{l-1}: (y_im, -y_re) scaled exactly
+        const float sc = l == 0 ? 1.f : 2.f;
+        const dflc my = {make_float2(sc * y.h.y, -sc * y.h.x), make_float2(sc * y.l.y, -sc * y.l.x)};
+        const dflc nx = l == 0 ? my : dflc_add(my, pv);
+        const dfl al = dfl_of(cf.a[l + 1]);
+        acc = l == 0 ? dflc_fma(al, nx, dflc_fma(dfl_of(cf.a[0]), cur, zc)) : dflc_fma(al, nx, acc);
+        pv = cur;
+        const double nr = (double)nx.h.x + (double)nx.l.x, ni = (double)nx.h.y + (double)nx.l.y;
+        bad |= !(nr * nr + ni * ni <= bound2);
+        dflc out = nx;
+        if (l == L - 1) out = dflc_ifma2(ph_s, acc, dflc_fma(ph_c, acc, zc));  // (ph_re + i ph_im) acc
+        const float4 w = make_float4(out.h.x, out.h.y, out.l.x, out.l.y);
+        if (C > 1) {
+          for (int c = 0; c < C; ++c) st_cluster_f32x4(&phi[buf ^ 1][i], (unsigned)c, w);
+        } else {
+          phi[buf ^ 1][i] = out;
+        }
+      }
+      if (C > 1) cluster_sync_all();
+      else __syncthreads();
+      buf ^= 1;
+    }
+  }
+  if (own) {
+    const dflc v = phi[buf][i];
+    xr[(size_t)j * n + i] = (double)v.h.x + (double)v.l.x;
+    xi[(size_t)j * n + i] = (double)v.h.y + (double)v.l.y;
+  }
+  if (bad) atomicOr(status, FQ_BIT_BOUND);
+  if (C > 1) cluster_sync_all();
+}
+
+// S, A of a chunk as FP32 pairs
+__global__ void k_to_dfl(const double* __restrict__ S, const double* __restrict__ A, size_t count, float2* Sd,
+                         float2* Ad) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < count; q += (size_t)gridDim.x * blockDim.x) {
+    const dfl s = dfl_of(S[q]), a = dfl_of(A[q]);
+    Sd[q] = make_float2(s.h, s.l);
+    Ad[q] = make_float2(a.h, a.l);
+  }
+}
+
 // Omega~ of steps m0 .. m0+nsteps-1 (order 4, Eq. 11 on Omega_m/h): S = sa H0 + sb H1 - sbeta 1,
 // A = sc [H0,H1], scalars from the plan's device copy (sa | sb | sc, M each).
 __global__ void k_omega_dense_steps(const double* __restrict__ h0, const double* __restrict__ h1,
@@ -160,8 +276,8 @@ __global__ void k_omega_dense_steps(const double* __restrict__ h0, const double*
 }
 
 template <int KG>
-cudaError_t launch_resident(const fq_plan* p, const double* S, const double* A, int nsteps, int C, double* xr,
-                            double* xi, int nc, cudaStream_t s) {
+cudaError_t launch_resident(const fq_plan* p, const double* S, const double* A, const float2* Sd, const float2* Ad,
+                            int nsteps, int C, double* xr, double* xi, int nc, cudaStream_t s) {
   DrCoef cf{};
   for (int l = 0; l <= p->L; ++l) cf.a[l] = p->cheb[l];
   const double bound2 = 1.0 + 1e-9;
@@ -178,6 +294,9 @@ cudaError_t launch_resident(const fq_plan* p, const double* S, const double* A, 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
   }
+  if (p->precision == FQ_DF32)
+    return cudaLaunchKernelEx(&cfg, k_dense_resident_dfl<KG>, (const float2*)Sd, (const float2*)Ad, p->n, nsteps,
+                              p->L, C, cf, p->phase_re, p->phase_im, bound2, xr, xi, p->d_status);
   return cudaLaunchKernelEx(&cfg, k_dense_resident<KG>, S, A, p->n, nsteps, p->L, C, cf, p->phase_re, p->phase_im,
                             bound2, xr, xi, p->d_status);
 }
@@ -187,7 +306,8 @@ cudaError_t launch_resident(const fq_plan* p, const double* S, const double* A, 
 bool fq_dense_resident_supported(int n, int L) { return n >= 1 && n <= DR_MAXN && L >= 1 && L <= DR_MAXL; }
 
 size_t fq_dense_resident_omega_count(int n, int nsteps) {
-  return (size_t)std::min(nsteps, DR_CHUNK) * n * n;
+  // FP64 S (or A) of a chunk, and room for its FP32-pair copy (FQ_DF32) after it
+  return 2 * (size_t)std::min(nsteps, DR_CHUNK) * n * n;
 }
 
 fq_status fq_dense_resident_chain(const fq_plan* p, double* xr, double* xi, int nc, int m_begin, int m_end,
@@ -210,8 +330,16 @@ fq_status fq_dense_resident_chain(const fq_plan* p, double* xr, double* xi, int 
       k_omega_dense_steps<<<grid, 256, 0, s>>>(p->d_h0, p->d_h1, p->d_k, n, p->d_scal, p->steps, m0, cnt, p->sbeta,
                                                S, A);
     }
-    cudaError_t e = n <= 64 ? launch_resident<8>(p, S, A, cnt, C, xr, xi, nc, s)
-                            : launch_resident<16>(p, S, A, cnt, C, xr, xi, nc, s);
+    // FQ_DF32: FP32-pair copies in the second half of each region
+    const size_t cap = (size_t)std::min(m_end - m_begin, DR_CHUNK);  // chunk size the regions were sized for
+    float2* Sd = reinterpret_cast<float2*>(S + cap * nn);
+    float2* Ad = reinterpret_cast<float2*>(A + cap * nn);
+    if (p->precision == FQ_DF32) {
+      const size_t total = nn * cnt;
+      k_to_dfl<<<(int)std::min<size_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(S, A, total, Sd, Ad);
+    }
+    cudaError_t e = n <= 64 ? launch_resident<8>(p, S, A, Sd, Ad, cnt, C, xr, xi, nc, s)
+                            : launch_resident<16>(p, S, A, Sd, Ad, cnt, C, xr, xi, nc, s);
     if (e != cudaSuccess) return fq_cuda_fail(e, "dense resident chain");
   }
   return FQ_OK;

@@ -418,8 +418,8 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_boun
     fq_set_error("tridiagonal format supports FQ_FP64, FQ_FP32 and FQ_DF32");
     return FQ_EUNSUPPORTED;
   }
-  if (p->format == FQ_DENSE && (p->precision == FQ_FP32 || p->precision == FQ_DF32)) {
-    fq_set_error("dense format supports FQ_FP64, FQ_BF16X3, FQ_BF16X6 and FQ_OZAKI");
+  if (p->format == FQ_DENSE && p->precision == FQ_FP32) {
+    fq_set_error("dense format supports FQ_FP64, FQ_DF32 (N <= 128), FQ_BF16X3, FQ_BF16X6 and FQ_OZAKI");
     return FQ_EUNSUPPORTED;
   }
   const int n = p->n, M = p->steps;

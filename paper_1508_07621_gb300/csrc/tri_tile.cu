@@ -21,6 +21,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "dfl.cuh"
 #include "gauge.cuh"
 #include "internal.h"
 
@@ -30,33 +31,6 @@ constexpr int TILE_NT = 256;
 constexpr int TILE_EPT = 8;
 constexpr int TILE_ROWS = TILE_NT * TILE_EPT;
 constexpr int TILE_MAXL = 128;
-
-// double-float value hi + lo, |lo| <= ulp(hi) / 2
-struct dfl {
-  float h, l;
-};
-
-__device__ __forceinline__ dfl dfl_of(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
-}
-__device__ __forceinline__ double dfl_value(dfl a) { return (double)a.h + (double)a.l; }
-
-// a * b + c in double-float: exact two-product of the high parts (FMA), the cross terms, a
-// two-sum with c's high part, and a final fast renormalisation.  Every step uses an explicitly
-// rounded operation, so the compiler cannot contract or reorder it.
-__device__ __forceinline__ dfl dfl_fma(dfl a, dfl b, dfl c) {
-  const float p = __fmul_rn(a.h, b.h);
-  float pe = __fmaf_rn(a.h, b.h, -p);
-  pe = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, pe));
-  const float s = __fadd_rn(p, c.h);
-  const float bb = __fsub_rn(s, p);
-  float se = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(c.h, bb));
-  se = __fadd_rn(se, __fadd_rn(pe, c.l));
-  const float h = __fadd_rn(s, se);
-  return {h, __fsub_rn(se, __fsub_rn(h, s))};
-}
-__device__ __forceinline__ dfl dfl_neg(dfl a) { return {-a.h, -a.l}; }
 
 template <typename T> struct V2;
 template <> struct V2<double> { using t = double2; };
@@ -259,38 +233,6 @@ k_tri_tile(const typename V2<T>::t* __restrict__ cf, const typename V2<T>::t* __
 constexpr int DFL_NT = 256;
 constexpr int DFL_EPT = 4;
 constexpr int DFL_ROWS = DFL_NT * DFL_EPT;
-// A complex double-float value packed for FP32x2 arithmetic: h = (re.hi, im.hi), l = (re.lo, im.lo).
-// A real operator entry acts on the real and imaginary parts alike, so every double-float FMA of
-// the step runs on both components at once with packed FFMA2 / FADD2 / FMUL2.
-struct dflc {
-  float2 h, l;
-};
-
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-
-// a * x + c for a real double-float a and complex double-float x, c
-__device__ __forceinline__ dflc dflc_fma(dfl a, dflc x, dflc c) {
-  const float2 ah = make_float2(a.h, a.h), al = make_float2(a.l, a.l);
-  const float2 p = __fmul2_rn(ah, x.h);
-  float2 pe = __ffma2_rn(ah, x.h, neg2(p));
-  pe = __ffma2_rn(ah, x.l, __ffma2_rn(al, x.h, pe));
-  const float2 sm = __fadd2_rn(p, c.h);
-  const float2 bb = __fadd2_rn(sm, neg2(p));
-  float2 se = __fadd2_rn(__fadd2_rn(p, neg2(__fadd2_rn(sm, neg2(bb)))), __fadd2_rn(c.h, neg2(bb)));
-  se = __fadd2_rn(se, __fadd2_rn(pe, c.l));
-  const float2 h = __fadd2_rn(sm, se);
-  return {h, __fadd2_rn(se, neg2(__fadd2_rn(h, neg2(sm))))};
-}
-
-// i cc * v + c: (-cc v_im, cc v_re) + c, one component at a time
-__device__ __forceinline__ dflc dflc_ifma(dfl cc, dflc v, dflc c) {
-  const dfl r = dfl_fma(dfl_neg(cc), dfl{v.h.y, v.l.y}, dfl{c.h.x, c.l.x});
-  const dfl i = dfl_fma(cc, dfl{v.h.x, v.l.x}, dfl{c.h.y, c.l.y});
-  return {make_float2(r.h, i.h), make_float2(r.l, i.l)};
-}
-
-__device__ __forceinline__ dflc dflc_neg(dflc a) { return {neg2(a.h), neg2(a.l)}; }
-
 struct DflTile {
   static constexpr int NW = DFL_NT / 32;
   dflc* slot_last;   // [2][NW]

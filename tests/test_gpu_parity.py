@@ -385,3 +385,38 @@ def test_dense_fp64_resident_segments_and_limits(fq):
     with pytest.raises(fq.FloquetError) as e:
         fq.Plan.dense(fi.goe(129, 1), fi.goe(129, 2), omega=1.0, f_ac=1.0, steps=4, kernel=fq.FQ_KERNEL_RESIDENT)
     assert e.value.status == fq.FQ_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("n", [1, 5, 33, 64, 100, 128])
+def test_dense_double_float_resident(fq, n):
+    """FQ_DF32 on the dense resident chain (double-float arithmetic on the FP32 pipes, FP64
+    states): against the oracle at the FP64 / emulated target, M = 70 across a launch boundary,
+    a non-even drive."""
+    M = 70
+    h0, h1 = fi.goe(n, 1101), fi.goe(n, 1102)
+    drv = fi.Drive(0.2, 1.3, 1.7, 0.4)
+    plan = fq.Plan.dense(h0, h1, omega=drv.omega, f_ac=drv.f_ac, f_dc=drv.f_dc, phi0=drv.phi0, steps=M,
+                         precision=fq.FQ_DF32)
+    U = plan.build_UT()
+    assert plan.check_status() == fq.FQ_OK
+    ref = o.build_ut_dense(h0, h1, o.plan_for_drive_dense(h0, h1, drv, M))
+    err = np.max(np.abs(to_np(U) - ref))
+    print(f"dense double-float resident N={n}: max err {err:.3e}")
+    assert err <= 1e-10
+
+
+def test_dense_double_float_limits_and_bounds(fq):
+    """Dense FQ_DF32 needs the resident kernel (N <= 128); caller bounds at 0.4 of the true span
+    raise FQ_EBOUND from its device check."""
+    for n, kernel in ((129, fq.FQ_KERNEL_AUTO), (64, fq.FQ_KERNEL_TILED)):
+        with pytest.raises(fq.FloquetError) as e:
+            fq.Plan.dense(fi.goe(n, 1), fi.goe(n, 2), omega=1.0, f_ac=1.0, steps=4, precision=fq.FQ_DF32,
+                          kernel=kernel)
+        assert e.value.status == fq.FQ_EUNSUPPORTED
+    m = fi.config_goe64()
+    pm = o.plan_for_drive_dense(m.h0, m.h1, m.drive, m.steps)
+    c, w = 0.5 * (pm.e_min + pm.e_max), 0.2 * (pm.e_max - pm.e_min)
+    plan = fq.Plan.dense(m.h0, m.h1, omega=1.0, f_ac=1.0, steps=m.steps, e_min=c - w, e_max=c + w,
+                         precision=fq.FQ_DF32)
+    plan.build_UT()
+    assert plan.check_status() == fq.FQ_EBOUND
