@@ -163,18 +163,18 @@ __device__ __forceinline__ dflc dflc_shfl_xor(dflc a, int o) {
 
 // The chain of k_dense_resident in double-float arithmetic: S, A as FP32 pairs [nsteps][n][n]
 // (float2 = (hi, lo)), the state as packed complex pairs in shared memory.
-template <int KG>
-__global__ void __launch_bounds__(DR_ROWS* KG)
+template <int ROWS, int KG>
+__global__ void __launch_bounds__(ROWS* KG)
     k_dense_resident_dfl(const float2* __restrict__ S, const float2* __restrict__ A, int n, int nsteps, int L, int C,
                          DrCoef cf, double ph_re, double ph_im, double bound2, double* xr, double* xi,
                          unsigned* status) {
-  constexpr int NT = DR_ROWS * KG;
+  constexpr int NT = ROWS * KG;
   constexpr int NV = KG * DR_KPT;
   __shared__ dflc phi[2][NV];
   const int t = threadIdx.x, rl = t / KG, g = t % KG;
   const unsigned rank = C > 1 ? cluster_rank() : 0u;
   const int j = blockIdx.x / C;
-  const int i = (int)rank * DR_ROWS + rl;
+  const int i = (int)rank * ROWS + rl;
   const bool own = g == 0 && i < n;
   const dflc zc = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   for (int q = t; q < 2 * NV; q += NT) {
@@ -275,15 +275,16 @@ __global__ void k_omega_dense_steps(const double* __restrict__ h0, const double*
   }
 }
 
-template <int KG>
+template <int ROWS, int KG>
 cudaError_t launch_resident(const fq_plan* p, const double* S, const double* A, const float2* Sd, const float2* Ad,
-                            int nsteps, int C, double* xr, double* xi, int nc, cudaStream_t s) {
+                            int nsteps, double* xr, double* xi, int nc, cudaStream_t s) {
+  const int C = (p->n + ROWS - 1) / ROWS;
   DrCoef cf{};
   for (int l = 0; l <= p->L; ++l) cf.a[l] = p->cheb[l];
   const double bound2 = 1.0 + 1e-9;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(nc * C));
-  cfg.blockDim = dim3(DR_ROWS * KG);
+  cfg.blockDim = dim3(ROWS * KG);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   if (C > 1) {
@@ -295,10 +296,14 @@ cudaError_t launch_resident(const fq_plan* p, const double* S, const double* A, 
     cfg.numAttrs = 1;
   }
   if (p->precision == FQ_DF32)
-    return cudaLaunchKernelEx(&cfg, k_dense_resident_dfl<KG>, (const float2*)Sd, (const float2*)Ad, p->n, nsteps,
+    return cudaLaunchKernelEx(&cfg, k_dense_resident_dfl<ROWS, KG>, (const float2*)Sd, (const float2*)Ad, p->n, nsteps,
                               p->L, C, cf, p->phase_re, p->phase_im, bound2, xr, xi, p->d_status);
-  return cudaLaunchKernelEx(&cfg, k_dense_resident<KG>, S, A, p->n, nsteps, p->L, C, cf, p->phase_re, p->phase_im,
-                            bound2, xr, xi, p->d_status);
+  if constexpr (ROWS != DR_ROWS) {
+    return cudaErrorInvalidValue;  // the FP64 chain has DR_ROWS rows per CTA
+  } else {
+    return cudaLaunchKernelEx(&cfg, k_dense_resident<KG>, S, A, p->n, nsteps, p->L, C, cf, p->phase_re,
+                              p->phase_im, bound2, xr, xi, p->d_status);
+  }
 }
 
 }  // namespace
@@ -313,7 +318,6 @@ size_t fq_dense_resident_omega_count(int n, int nsteps) {
 fq_status fq_dense_resident_chain(const fq_plan* p, double* xr, double* xi, int nc, int m_begin, int m_end,
                                   double* S, double* A, cudaStream_t s) {
   const int n = p->n;
-  const int C = (n + DR_ROWS - 1) / DR_ROWS;
   const size_t nn = (size_t)n * n;
   for (int m0 = m_begin; m0 < m_end; m0 += DR_CHUNK) {
     const int cnt = std::min(DR_CHUNK, m_end - m0);
@@ -338,8 +342,13 @@ fq_status fq_dense_resident_chain(const fq_plan* p, double* xr, double* xi, int 
       const size_t total = nn * cnt;
       k_to_dfl<<<(int)std::min<size_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(S, A, total, Sd, Ad);
     }
-    cudaError_t e = n <= 64 ? launch_resident<8>(p, S, A, Sd, Ad, cnt, C, xr, xi, nc, s)
-                            : launch_resident<16>(p, S, A, Sd, Ad, cnt, C, xr, xi, nc, s);
+    // double-float: CTAs of 16 rows, a cluster of up to eight per state (the products are cheap
+    // on the FP32 pipes; more SMs share each product)
+    cudaError_t e;
+    if (p->precision == FQ_DF32 && n <= 64) e = launch_resident<16, 8>(p, S, A, Sd, Ad, cnt, xr, xi, nc, s);
+    else if (p->precision == FQ_DF32) e = launch_resident<16, 16>(p, S, A, Sd, Ad, cnt, xr, xi, nc, s);
+    else if (n <= 64) e = launch_resident<DR_ROWS, 8>(p, S, A, Sd, Ad, cnt, xr, xi, nc, s);
+    else e = launch_resident<DR_ROWS, 16>(p, S, A, Sd, Ad, cnt, xr, xi, nc, s);
     if (e != cudaSuccess) return fq_cuda_fail(e, "dense resident chain");
   }
   return FQ_OK;
