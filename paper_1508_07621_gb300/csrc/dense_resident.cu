@@ -63,18 +63,18 @@ __device__ __forceinline__ void st_cluster_f64x2(const void* local, unsigned ran
 }
 
 // S, A: [nsteps][n][n] (Omega~ of the chunk's steps); x: planar states [nc][n], updated in place.
-template <int KG>
-__global__ void __launch_bounds__(DR_ROWS* KG)
+template <int ROWS, int KG>
+__global__ void __launch_bounds__(ROWS* KG)
     k_dense_resident(const double* __restrict__ S, const double* __restrict__ A, int n, int nsteps, int L, int C,
                      DrCoef cf, double ph_re, double ph_im, double bound2, double* xr, double* xi,
                      unsigned* status) {
-  constexpr int NT = DR_ROWS * KG;
+  constexpr int NT = ROWS * KG;
   constexpr int NV = KG * DR_KPT;  // vector length held per buffer (>= n)
   __shared__ double2 phi[2][NV];
   const int t = threadIdx.x, rl = t / KG, g = t % KG;
   const unsigned rank = C > 1 ? cluster_rank() : 0u;
   const int j = blockIdx.x / C;  // the state this cluster carries
-  const int i = (int)rank * DR_ROWS + rl;
+  const int i = (int)rank * ROWS + rl;
   const bool own = g == 0 && i < n;
   for (int q = t; q < 2 * NV; q += NT) {
     const int b = q / NV, k = q % NV;
@@ -298,12 +298,8 @@ cudaError_t launch_resident(const fq_plan* p, const double* S, const double* A, 
   if (p->precision == FQ_DF32)
     return cudaLaunchKernelEx(&cfg, k_dense_resident_dfl<ROWS, KG>, (const float2*)Sd, (const float2*)Ad, p->n, nsteps,
                               p->L, C, cf, p->phase_re, p->phase_im, bound2, xr, xi, p->d_status);
-  if constexpr (ROWS != DR_ROWS) {
-    return cudaErrorInvalidValue;  // the FP64 chain has DR_ROWS rows per CTA
-  } else {
-    return cudaLaunchKernelEx(&cfg, k_dense_resident<KG>, S, A, p->n, nsteps, p->L, C, cf, p->phase_re,
-                              p->phase_im, bound2, xr, xi, p->d_status);
-  }
+  return cudaLaunchKernelEx(&cfg, k_dense_resident<ROWS, KG>, S, A, p->n, nsteps, p->L, C, cf, p->phase_re,
+                            p->phase_im, bound2, xr, xi, p->d_status);
 }
 
 }  // namespace
