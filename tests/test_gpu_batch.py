@@ -19,7 +19,8 @@ def fq():
 
 
 def test_batch_matches_individual_builds(fq):
-    """Mixed scan (split X3 of several sizes, FP64 dense, FP32 resident tridiagonal) as one graph
+    """Mixed scan (split X3 of several sizes, FP64 dense, FP64 emulation, double-float dense, FP32
+    resident tridiagonal) as one graph
     on 3 lanes: every output equals the same plan's own floquet_build_UT bit for bit (the kernels
     are deterministic), and one instance equals the oracle within the split tolerance."""
     import torch
@@ -27,6 +28,11 @@ def test_batch_matches_individual_builds(fq):
     plans = [fq.Plan.dense(fi.goe(s.n, s.seed_h0), fi.goe(s.n, s.seed_h1), omega=s.omega, f_ac=s.amplitude,
                            steps=12, precision=fq.FQ_BF16X3) for s in insts]
     plans.append(fq.Plan.dense(fi.goe(48, 5001), fi.goe(48, 5002), omega=1.0, f_ac=1.0, steps=10))
+    # the emulated paths: tensor-core FP64 emulation and the double-float resident chain
+    plans.append(fq.Plan.dense(fi.goe(150, 5003), fi.goe(150, 5004), omega=1.0, f_ac=1.0, steps=6,
+                               precision=fq.FQ_OZAKI))
+    plans.append(fq.Plan.dense(fi.goe(70, 5005), fi.goe(70, 5006), omega=1.0, f_ac=1.0, steps=9,
+                               precision=fq.FQ_DF32))
     d = fi.config_dimer(nb=40, steps=20)
     plans.append(fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=3.0, f_ac=1.5, steps=20))
     outs = [torch.empty((p.n, p.n), dtype=torch.complex128, device="cuda") for p in plans]

@@ -21,11 +21,14 @@ def fq():
     return fq
 
 
-def test_dense_fp64_averages_match_oracle(fq):
+@pytest.mark.parametrize("precision", ["FQ_FP64", "FQ_DF32", "FQ_OZAKI"])
+def test_dense_fp64_averages_match_oracle(fq, precision):
+    """Period averages through the FP64 chain and the two emulated ones (same FP64 criterion)."""
     n, M = 40, 60
     h0, h1 = fi.goe(n, 1401), fi.goe(n, 1402)
     drv = fi.Drive(0.1, 1.1, 1.2, 0.3)
-    plan = fq.Plan.dense(h0, h1, omega=drv.omega, f_ac=drv.f_ac, f_dc=drv.f_dc, phi0=drv.phi0, steps=M)
+    plan = fq.Plan.dense(h0, h1, omega=drv.omega, f_ac=drv.f_ac, f_dc=drv.f_dc, phi0=drv.phi0, steps=M,
+                         precision=getattr(fq, precision))
     eps, states = fq.floquet_states(plan.build_UT(), drv.period)
     e_avg = plan.average_observable(states, 1.0, 0.0, 1.0).cpu().numpy()       # <H(t)>_T
     h1_avg = plan.average_observable(states, 0.0, 1.0, 0.0).cpu().numpy()      # <H1>_T
