@@ -46,11 +46,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["dimer", "dimer-paper", "goe4096", "adjoint"], default="dimer",
+    ap.add_argument("--workload", choices=["dimer", "dimer-paper", "goe4096", "adjoint", "paper-table1"],
+                    default="dimer",
                     help="dimer: nb = 10^4, J = 1, U nb = 2, f = 1.5 cos 3t, M = 2000 (default); "
                          "dimer-paper: the paper's parameters (U/2)(n1 - n2)^2, f = 2.7 + 2.5 cos 3t, M = 8000; "
                          "goe4096: dense GOE N = 4096 (seeds 3, 4), A = 2, omega = 2, M = 512, U_T builds/s; "
-                         "adjoint: gate-fidelity gradient, GOE N = 1024 (seeds 6-9), M = 256, s = 16, grads/s")
+                         "adjoint: gate-fidelity gradient, GOE N = 1024 (seeds 6-9), M = 256, s = 16, grads/s; "
+                         "paper-table1: the paper's timing run (GOE N = 4096 with unit-variance entries, "
+                         "f = cos(pi t), M = 100, L = 50, 6th order), compared with its Table 1 time")
     ap.add_argument("--precision", choices=["x3", "x6", "ozaki", "fp64"], default=None,
                     help="goe4096 / adjoint: BF16X3 (default), BF16X6, FQ_OZAKI (FP64 emulation) or FP64 "
                          "(adjoint only)")
@@ -426,6 +429,9 @@ def run_ours(args):
 # ---------------------------------------------------------------------- dense and gradient workloads
 PREC_NAMES = {"x3": "FQ_BF16X3", "x6": "FQ_BF16X6", "ozaki": "FQ_OZAKI", "fp64": "FQ_FP64"}
 SLICE_PRODUCTS = {"x3": 3, "x6": 6, "ozaki": 21, "fp64": 1}
+# The paper's Table 1, N = 4096, M = 100, L = 50, 6th order: 9730.5 s of Chebyshev iterations for
+# one U_T on one node (2 x 8-core Xeon E5-2660, FP64 MKL zgemm).
+PAPER_TABLE1_CHEB_S = 9730.5
 
 
 def timed_loop(fn, steps, stream, world, dist):
@@ -450,13 +456,16 @@ def timed_loop(fn, steps, stream, world, dist):
     return [ev[k].elapsed_time(ev[k + 1]) / 1000.0 for k in range(steps)], ev[0].elapsed_time(ev[-1]) / 1000.0, clk
 
 
-def dense_oracle_sample(m, states=64, steps=4):
+def dense_oracle_sample(m, states=64, steps=4, cheb_terms=0):
     """FP64 oracle (numpy, BLAS on every host core) on `states` basis states over the first `steps`
     steps of the dense workload; returns (U_T/s scaled to the full build, seconds, description,
-    (idx, x, steps))."""
+    (idx, x, steps)).  cheb_terms > 0 fixes L (its weights from the oracle's own Bessel routine)."""
+    import dataclasses
     import numpy as np
     import oracle as o
     plan = o.plan_for_drive_dense(m.h0, m.h1, m.drive, m.steps)
+    if cheb_terms:
+        plan = dataclasses.replace(plan, L=cheb_terms, coeffs=o.bessel_coefficients(plan.R, cheb_terms))
     idx = np.linspace(0, m.n - 1, states).astype(int)
     x0 = np.zeros((m.n, states), complex)
     x0[idx, np.arange(states)] = 1.0
@@ -465,6 +474,8 @@ def dense_oracle_sample(m, states=64, steps=4):
     dt = time.perf_counter() - t0
     frac = (states / m.n) * (steps / m.steps)
     desc = f"{states} of {m.n} basis states over {steps} of {m.steps} steps (FP64 numpy oracle, BLAS threads)"
+    if cheb_terms:
+        desc += f", L = {cheb_terms}, 4th-order operator (the L products per step dominate)"
     return frac / dt, dt, desc, (idx, x, steps)
 
 
@@ -496,15 +507,18 @@ def run_dense(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    prec = args.precision or "x3"
+    paper = args.workload == "paper-table1"
+    prec = args.precision or ("ozaki" if paper else "x3")
     if prec == "fp64":
-        raise SystemExit("goe4096 in plain FP64 takes about 20 minutes per U_T; use x3, x6 or ozaki")
-    m = fi.config_goe4096()
+        raise SystemExit("N = 4096 in plain FP64 takes many minutes per U_T; use x3, x6 or ozaki")
+    m = fi.config_goe_paper() if paper else fi.config_goe4096()
+    order, terms = (6, 50) if paper else (0, 0)
     f_ac = rank_drive_amplitude(m.drive.f_ac, rank)
     n = m.n
     precision = getattr(fq, PREC_NAMES[prec])
     stream = torch.cuda.current_stream()
-    plan = fq.Plan.dense(m.h0, m.h1, omega=m.drive.omega, f_ac=f_ac, steps=m.steps, precision=precision)
+    plan = fq.Plan.dense(m.h0, m.h1, omega=m.drive.omega, f_ac=f_ac, steps=m.steps, precision=precision,
+                         magnus_order=order, cheb_terms=terms)
     ws = fq.workspace(plan.workspace_size())
     tile = plan.autotune(ws) if prec != "ozaki" else 0
     L = plan.info.L
@@ -527,7 +541,7 @@ def run_dense(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         p2 = fq.Plan.dense(m.h0, m.h1, omega=m.drive.omega, f_ac=f_ac, steps=m.steps, precision=precision,
-                           tile_n=tile)
+                           tile_n=tile, magnus_order=order, cheb_terms=terms)
         fq.floquet_build_UT(p2.handle, U, ws, stream)
         host_u.copy_(U, non_blocking=True)
         torch.cuda.synchronize()
@@ -555,21 +569,30 @@ def run_dense(args):
                 "defect_columns": int(sample_cols.numel())}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, dt, desc, (idx, xs, nst) = dense_oracle_sample(m)
+        v, dt, desc, (idx, xs, nst) = dense_oracle_sample(m, steps=2 if paper else 4, cheb_terms=terms)
         cpu = {"value": v, "unit": "U_T/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
-        rows = torch.zeros((len(idx), n), dtype=torch.complex128, device="cuda")
-        rows[torch.arange(len(idx)), torch.as_tensor(idx, device="cuda")] = 1.0
-        got = plan.propagate(rows, 0, nst).cpu().numpy().T
-        accuracy["sample_max_err_vs_oracle"] = float(np.max(np.abs(got - xs)))
-        accuracy["sample"] = desc
+        if not paper:  # (the paper's run is 6th order; the oracle sample times the 4th-order chain)
+            rows = torch.zeros((len(idx), n), dtype=torch.complex128, device="cuda")
+            rows[torch.arange(len(idx)), torch.as_tensor(idx, device="cuda")] = 1.0
+            got = plan.propagate(rows, 0, nst).cpu().numpy().T
+            accuracy["sample_max_err_vs_oracle"] = float(np.max(np.abs(got - xs)))
+            accuracy["sample"] = desc
     launches = 2 + m.steps * (1 + (2 * L if prec == "ozaki" else L))
-    line = {"metric": f"U_T builds/sec (dense GOE N={n}, M={m.steps})", "value": value, "unit": "U_T/s",
+    if paper:
+        metric = (f"U_T builds/sec (the paper's Table 1 timing run: GOE N={n} with unit-variance entries, "
+                  f"f = cos(pi t), M={m.steps}, L={L}, 6th-order Magnus)")
+        vs = value * PAPER_TABLE1_CHEB_S
+        workload = (f"paper Table 1: GOE N={n} (seeds 3, 4, unit-variance entries), f=cos(pi t), T=2, M={m.steps}, "
+                    f"L={L} fixed, 6th-order Magnus, {PREC_NAMES[prec]}")
+    else:
+        metric, vs = f"U_T builds/sec (dense GOE N={n}, M={m.steps})", None
+        workload = f"dense GOE N={n} (seeds 3, 4), A=2, omega=2, M={m.steps}, L={L}, {PREC_NAMES[prec]}"
+    line = {"metric": metric, "value": value, "unit": "U_T/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": vs,
             "dtype": "bf16 slices, f64 states" if prec == "ozaki" else "bf16 slices, f32 accumulate",
             "data": "synthetic",
-            "config": {"workload": f"dense GOE N={n} (seeds 3, 4), A=2, omega=2, M={m.steps}, L={L}, "
-                                   f"{PREC_NAMES[prec]}",
+            "config": {"workload": workload,
                        "n": n, "steps_per_period": m.steps, "chebyshev_L": L, "R": plan.info.R, "tile_n": tile,
                        "l2": "working set larger than L2 (operand slices and states, > 1 GB)",
                        "parallelism": f"weak: {world} independent drive amplitudes"},
@@ -579,6 +602,10 @@ def run_dense(args):
             "gpu_launches": launches * args.steps, "clocks": clk, "device_status_ok": status_ok,
             "accuracy": accuracy, "median_step_s": statistics.median(per_step), "per_step_s": per_step,
             "host": host_info()}
+    if paper:
+        line["vs_baseline_note"] = (f"value x {PAPER_TABLE1_CHEB_S} s: the paper's Chebyshev-iteration time for one "
+                                    "U_T of this run on one 16-core Xeon node in FP64 (Table 1); context, not a "
+                                    "target (another machine)")
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -706,15 +733,23 @@ def run_reference_other(args):
         return
     import floquet_inputs as fi
     vals, desc = [], ""
-    if args.workload == "goe4096":
-        m = fi.config_goe4096()
+    if args.workload in ("goe4096", "paper-table1"):
+        paper = args.workload == "paper-table1"
+        m = fi.config_goe_paper() if paper else fi.config_goe4096()
+        terms = 50 if paper else 0
         for _ in range(args.warmup):
-            dense_oracle_sample(m, states=8, steps=1)
+            dense_oracle_sample(m, states=8, steps=1, cheb_terms=terms)
         for _ in range(args.steps):
-            v, dt, desc, _ = dense_oracle_sample(m)
+            v, dt, desc, _ = dense_oracle_sample(m, steps=2 if paper else 4, cheb_terms=terms)
             vals.append(v)
-        metric, unit = f"U_T builds/sec (dense GOE N={m.n}, M={m.steps})", "U_T/s"
-        cfg = f"dense GOE N={m.n} (seeds 3, 4), A=2, omega=2, M={m.steps}"
+        unit = "U_T/s"
+        if paper:
+            metric = (f"U_T builds/sec (the paper's Table 1 timing run: GOE N={m.n} with unit-variance entries, "
+                      f"f = cos(pi t), M={m.steps}, L=50, 6th-order Magnus)")
+            cfg = f"paper Table 1: GOE N={m.n}, f=cos(pi t), M={m.steps}, L=50"
+        else:
+            metric = f"U_T builds/sec (dense GOE N={m.n}, M={m.steps})"
+            cfg = f"dense GOE N={m.n} (seeds 3, 4), A=2, omega=2, M={m.steps}"
     else:
         a = fi.config_adjoint()
         for _ in range(args.warmup):
@@ -740,11 +775,11 @@ if __name__ == "__main__":
     if a.ncu_case:
         run_ncu_case(a.ncu_case)
     elif a.impl == "reference":
-        if a.workload in ("goe4096", "adjoint"):
+        if a.workload in ("goe4096", "adjoint", "paper-table1"):
             run_reference_other(a)
         else:
             run_reference(a)
-    elif a.workload == "goe4096":
+    elif a.workload in ("goe4096", "paper-table1"):
         run_dense(a)
     elif a.workload == "adjoint":
         run_adjoint(a)

@@ -183,6 +183,15 @@ def config_goe4096(n: int = 4096, steps: int = 512) -> DenseModel:
     return DenseModel(goe(n, 3), goe(n, 4), Drive(0.0, 2.0, 2.0), steps)
 
 
+def config_goe_paper(n: int = 4096, steps: int = 100) -> DenseModel:
+    """The paper's timing workload (§6, Table 1): GOE matrices with unit-variance entries
+    (G + G^T)/sqrt(2), G_ij ~ N(0, 1), seeds 3 (H0) and 4 (H1); f(t) = cos(pi t), T = 2; M = 100
+    steps per period (the runs also fix L = 50 Chebyshev products per step and use the 6th-order
+    scheme; those are plan options)."""
+    s = math.sqrt(n)  # goe() is normalised by sqrt(2 n); this undoes the sqrt(n) part
+    return DenseModel(goe(n, 3) * s, goe(n, 4) * s, Drive(0.0, 1.0, math.pi), steps)
+
+
 @dataclasses.dataclass(frozen=True)
 class ScanInstance:
     n: int

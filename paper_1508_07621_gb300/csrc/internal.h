@@ -30,6 +30,7 @@ struct fq_plan {
   // problem
   int n = 0, steps = 0, format = 0, precision = 0, drive_kind = 0, stride = 16, L = 0;
   double period = 0, h = 0, tol = 1e-14;
+  int cheb_terms = 0;                   // > 0: fixed L (Table 1's timing runs), else L from tol
   double f_dc = 0, f_ac = 0, omega = 0, phi0 = 0;   // cosine drive (observables)
   // bounds of Omega/h (Eq. 11) and Chebyshev data (Eq. 12)
   double e_min = 0, e_max = 0, beta = 0, delta_e = 0, R = 0;

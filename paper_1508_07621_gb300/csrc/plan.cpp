@@ -344,7 +344,7 @@ void fq_finish_bounds(fq_plan* plan, double emin, double emax) {
   plan->delta_e = 0.5 * (emax - emin);
   plan->beta = plan->delta_e + emin;
   plan->R = h * plan->delta_e;
-  plan->L = fq_cheb_order(plan->R, plan->tol);
+  plan->L = plan->cheb_terms > 0 ? std::max(plan->cheb_terms, fq_cheb_order(plan->R, 1.0)) : fq_cheb_order(plan->R, plan->tol);
   plan->cheb.assign(plan->L + 1, 0.0);
   fq_bessel_miller(plan->R, plan->L, plan->cheb.data());
   for (int l = 1; l <= plan->L; ++l) plan->cheb[l] *= 2.0;
@@ -444,6 +444,11 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_boun
   plan->tile_n = p->tile_n ? p->tile_n : 128;
   plan->period = p->period;
   plan->tol = p->cheb_tol > 0 ? p->cheb_tol : 1e-14;
+  if (p->cheb_terms < 0 || p->cheb_terms > 1024) {
+    fq_set_error("cheb_terms must be in [0, 1024] (got %d)", p->cheb_terms);
+    return FQ_EINVAL;
+  }
+  plan->cheb_terms = p->cheb_terms;
   plan->f_dc = p->f_dc;
   plan->f_ac = p->f_ac;
   plan->omega = p->omega;

@@ -2,6 +2,7 @@
 host planner (stage a1: Magnus scalars, bounds, R, L, Bessel weights) agrees with the oracle.
 No compute call needs a GPU here."""
 import ctypes
+import math
 import os
 import re
 
@@ -100,3 +101,27 @@ def test_argument_errors(fq):
     prob, keep = fq.make_problem(4, fq.FQ_DENSE, np.eye(4), np.eye(4), 1.0, 2, precision=fq.FQ_OZAKI)
     info, _ = fq.floquet_plan_inspect(prob)
     assert info.precision == fq.FQ_OZAKI
+
+
+def test_fixed_chebyshev_terms(fq):
+    """cheb_terms fixes L (the paper's timing runs use L = 50): the library's weights are then
+    a_0 = J_0(R), a_l = 2 J_l(R) for l = 1..50 (scipy's Bessel functions), a value below the
+    minimum L > R is raised to it, and out-of-range values are rejected."""
+    from scipy.special import jv
+    m = fi.config_goe_paper(64, 100)
+    prob, keep = fq.make_problem(64, fq.FQ_DENSE, m.h0, m.h1, m.drive.period, m.steps, f_ac=1.0,
+                                 omega=m.drive.omega, cheb_terms=50)
+    info, a = fq.floquet_plan_inspect(prob)
+    assert info.L == 50
+    ref = np.array([jv(0, info.R)] + [2 * jv(l, info.R) for l in range(1, 51)])
+    big = np.abs(ref) > 1e-290
+    assert np.max(np.abs(a[big] - ref[big]) / np.abs(ref[big])) <= 1e-12
+    prob, keep = fq.make_problem(64, fq.FQ_DENSE, m.h0, m.h1, m.drive.period, m.steps, f_ac=1.0,
+                                 omega=m.drive.omega, cheb_terms=1)
+    info, _ = fq.floquet_plan_inspect(prob)
+    assert info.L == int(math.floor(info.R)) + 1
+    for bad in (-1, 1025):
+        prob, keep = fq.make_problem(64, fq.FQ_DENSE, m.h0, m.h1, 2.0, 10, cheb_terms=bad)
+        with pytest.raises(fq.FloquetError) as e:
+            fq.floquet_plan_inspect(prob)
+        assert e.value.status == fq.FQ_EINVAL

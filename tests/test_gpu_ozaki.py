@@ -127,3 +127,22 @@ def test_ozaki_goe4096_full_build_sampled_columns(fq):
     print(f"GOE4096 Ozaki full build: max err {err:.3e}; defect max {mx:.2e} fro {fro:.2e}")
     assert err <= TOL
     assert mx <= 1e-11
+
+
+@pytest.mark.parametrize("precision", ["FQ_FP64", "FQ_OZAKI", "FQ_BF16X6"])
+def test_fixed_chebyshev_terms_match_converged_series(fq, precision):
+    """L fixed at 50 (the paper's timing runs) with the 6th-order scheme: past convergence the
+    extra terms carry Bessel weights below 1e-30, so U_T equals the oracle's tolerance-truncated
+    chain to each path's accuracy."""
+    n, M = 48, 16
+    h0, h1 = fi.goe(n, 2101), fi.goe(n, 2102)
+    drv = fi.Drive(0.2, 1.4, 1.1, 0.5)
+    plan = fq.Plan.dense(h0, h1, omega=drv.omega, f_ac=drv.f_ac, f_dc=drv.f_dc, phi0=drv.phi0, steps=M,
+                         magnus_order=6, cheb_terms=50, precision=getattr(fq, precision))
+    assert plan.info.L == 50
+    U = plan.build_UT().cpu().numpy()
+    assert plan.check_status() == fq.FQ_OK
+    rp, oms = o.plan_dense6(h0, h1, drv, M)
+    err = np.max(np.abs(U - o.build_ut_dense6(rp, oms)))
+    print(f"L = 50 {precision}: max err {err:.2e} (oracle L = {rp.L})")
+    assert err <= (1e-10 if precision != "FQ_BF16X6" else 1e-5)
