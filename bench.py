@@ -36,6 +36,10 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # steps 0..19, k_tri_resident<256, 40>): bytes read, of which the 152 initial states are a fixed
 # part; the rest is the per-step (2d, 2e') and rotation stream, which grows with waves x steps.
 RES_NCU = {"read": 28.519936e6, "x0": 152 * 10001 * 16, "states": 152, "steps": 20}
+# The paper's Table 1 (M = 100, L = 50, 6th order): seconds of Chebyshev iterations for one U_T
+# on one node (2 x 8-core Xeon E5-2660, FP64 MKL zgemm), by N.
+PAPER_TABLE1_CHEB_S = {256: 4.3, 512: 25.3, 1024: 177.3, 2048: 1296.6, 4096: 9730.5, 5120: 18667.2,
+                       10240: 181722.3}
 
 
 def parse():
@@ -54,6 +58,8 @@ def parse():
                          "adjoint: gate-fidelity gradient, GOE N = 1024 (seeds 6-9), M = 256, s = 16, grads/s; "
                          "paper-table1: the paper's timing run (GOE N = 4096 with unit-variance entries, "
                          "f = cos(pi t), M = 100, L = 50, 6th order), compared with its Table 1 time")
+    ap.add_argument("--n", type=int, default=4096, choices=sorted(PAPER_TABLE1_CHEB_S),
+                    help="paper-table1: the matrix size (the rows of the paper's Table 1)")
     ap.add_argument("--precision", choices=["x3", "x6", "ozaki", "fp64"], default=None,
                     help="goe4096 / adjoint: BF16X3 (default), BF16X6, FQ_OZAKI (FP64 emulation) or FP64 "
                          "(adjoint only)")
@@ -429,9 +435,6 @@ def run_ours(args):
 # ---------------------------------------------------------------------- dense and gradient workloads
 PREC_NAMES = {"x3": "FQ_BF16X3", "x6": "FQ_BF16X6", "ozaki": "FQ_OZAKI", "fp64": "FQ_FP64"}
 SLICE_PRODUCTS = {"x3": 3, "x6": 6, "ozaki": 21, "fp64": 1}
-# The paper's Table 1, N = 4096, M = 100, L = 50, 6th order: 9730.5 s of Chebyshev iterations for
-# one U_T on one node (2 x 8-core Xeon E5-2660, FP64 MKL zgemm).
-PAPER_TABLE1_CHEB_S = 9730.5
 
 
 def timed_loop(fn, steps, stream, world, dist):
@@ -511,7 +514,7 @@ def run_dense(args):
     prec = args.precision or ("ozaki" if paper else "x3")
     if prec == "fp64":
         raise SystemExit("N = 4096 in plain FP64 takes many minutes per U_T; use x3, x6 or ozaki")
-    m = fi.config_goe_paper() if paper else fi.config_goe4096()
+    m = fi.config_goe_paper(args.n) if paper else fi.config_goe4096()
     order, terms = (6, 50) if paper else (0, 0)
     f_ac = rank_drive_amplitude(m.drive.f_ac, rank)
     n = m.n
@@ -581,7 +584,7 @@ def run_dense(args):
     if paper:
         metric = (f"U_T builds/sec (the paper's Table 1 timing run: GOE N={n} with unit-variance entries, "
                   f"f = cos(pi t), M={m.steps}, L={L}, 6th-order Magnus)")
-        vs = value * PAPER_TABLE1_CHEB_S
+        vs = value * PAPER_TABLE1_CHEB_S[n]
         workload = (f"paper Table 1: GOE N={n} (seeds 3, 4, unit-variance entries), f=cos(pi t), T=2, M={m.steps}, "
                     f"L={L} fixed, 6th-order Magnus, {PREC_NAMES[prec]}")
     else:
@@ -603,7 +606,7 @@ def run_dense(args):
             "accuracy": accuracy, "median_step_s": statistics.median(per_step), "per_step_s": per_step,
             "host": host_info()}
     if paper:
-        line["vs_baseline_note"] = (f"value x {PAPER_TABLE1_CHEB_S} s: the paper's Chebyshev-iteration time for one "
+        line["vs_baseline_note"] = (f"value x {PAPER_TABLE1_CHEB_S[n]} s: the paper's Chebyshev-iteration time for one "
                                     "U_T of this run on one 16-core Xeon node in FP64 (Table 1); context, not a "
                                     "target (another machine)")
     print(json.dumps(line), flush=True)
@@ -735,7 +738,7 @@ def run_reference_other(args):
     vals, desc = [], ""
     if args.workload in ("goe4096", "paper-table1"):
         paper = args.workload == "paper-table1"
-        m = fi.config_goe_paper() if paper else fi.config_goe4096()
+        m = fi.config_goe_paper(args.n) if paper else fi.config_goe4096()
         terms = 50 if paper else 0
         for _ in range(args.warmup):
             dense_oracle_sample(m, states=8, steps=1, cheb_terms=terms)
