@@ -56,7 +56,7 @@ typedef enum fq_status {
   FQ_ECUDA = 3,         /* a CUDA runtime call failed; see floquet_last_error */
   FQ_EBOUND = 4,        /* device check: |entry| above the unitarity bound, or NaN */
   FQ_ETIMEOUT = 5,      /* a bounded device wait gave up */
-  FQ_EUNSUPPORTED = 6   /* valid request this build does not implement */
+  FQ_EUNSUPPORTED = 6   /* valid request the library does not implement */
 } fq_status;
 
 typedef enum fq_format {
