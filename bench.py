@@ -606,6 +606,12 @@ def run_dense(args):
             "gpu_launches": launches * args.steps, "clocks": clk, "device_status_ok": status_ok,
             "accuracy": accuracy, "median_step_s": statistics.median(per_step), "per_step_s": per_step,
             "host": host_info()}
+    # the quasienergies (Eq. 5) from the timed U_T by host FP64 LAPACK zgeev, outside the timed
+    # region (the paper's Table 1 lists it separately)
+    t0 = time.perf_counter()
+    eps, _ = fq.floquet_states(U, m.drive.period)
+    line["quasienergies"] = {"host_zgeev_s": time.perf_counter() - t0, "count": int(len(eps)),
+                             "cores": os.cpu_count()}
     if paper:
         line["vs_baseline_note"] = (f"value x {PAPER_TABLE1_CHEB_S[n]} s: the paper's Chebyshev-iteration time for one "
                                     "U_T of this run on one 16-core Xeon node in FP64 (Table 1); context, not a "
