@@ -79,12 +79,15 @@ def test_dense_fp64_ragged_propagate_range(fq):
     assert np.array_equal(to_np(Y), x0)
 
 
+@pytest.mark.parametrize("precision", ["FQ_FP64", "FQ_DF32", "FQ_OZAKI"])
 @pytest.mark.parametrize("n,scale", [(1, 1.0), (2, 1.0), (6, 1e-9)])
-def test_dense_fp64_degenerate(fq, n, scale):
-    """N = 1 (zero spectral width), N = 2, and a tiny operator with L = 1 (one-term steps)."""
+def test_dense_fp64_degenerate(fq, n, scale, precision):
+    """N = 1 (zero spectral width), N = 2, and a tiny operator with L = 1 (one-term steps), on the
+    FP64 path and the two emulated ones."""
     h0, h1 = scale * fi.goe(n, 901), scale * fi.goe(n, 902)
     drv = fi.Drive(0.1, 0.7, 1.0, 0.2)
-    plan = fq.Plan.dense(h0, h1, omega=1.0, f_ac=0.7, f_dc=0.1, phi0=0.2, steps=12)
+    plan = fq.Plan.dense(h0, h1, omega=1.0, f_ac=0.7, f_dc=0.1, phi0=0.2, steps=12,
+                         precision=getattr(fq, precision))
     if scale < 1e-6:
         assert plan.info.L == 1
     U = to_np(plan.build_UT())
