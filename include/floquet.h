@@ -240,9 +240,16 @@ void floquet_batch_destroy(fq_batch* batch);
  * other paths.  *tile_n receives the chosen width (NULL allowed). */
 fq_status floquet_autotune(fq_plan* plan, void* d_ws, size_t ws_bytes, void* stream, int32_t* tile_n);
 
-/* Synchronises `stream`; returns FQ_EBOUND (and clears the word) if a device check of this
- * plan fired since the last call, FQ_OK otherwise. */
+/* Synchronises `stream`; returns FQ_ETIMEOUT if a bounded device wait of this plan's kernels
+ * gave up, else FQ_EBOUND if a numerical device check fired, since the last call (and clears
+ * the word); FQ_OK otherwise. */
 fq_status floquet_check_status(fq_plan* plan, void* stream);
+
+/* Diagnostic of the timeout path: one thread waits, bounded by `cycles` SM clock cycles (at most
+ * 2^31), on a shared-memory mbarrier that nothing arrives on, exactly as the tensor-core
+ * kernels wait on their pipeline barriers, then records the timeout in the plan's status word
+ * and returns.  The next floquet_check_status reports FQ_ETIMEOUT; the context stays usable. */
+fq_status floquet_selftest_wait(fq_plan* plan, int64_t cycles, void* stream);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* floquet_last_error(void);

@@ -60,6 +60,7 @@ _SIGS = {
     "floquet_unitarity_defect": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _sz, _vp, _dp, _dp]),
     "floquet_grad_workspace_size": (_sz, [_vp]),
     "floquet_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "floquet_selftest_wait": (ctypes.c_int, [_vp, ctypes.c_int64, _vp]),
     "floquet_check_status": (ctypes.c_int, [_vp, _vp]),
     "floquet_build_UT_static": (ctypes.c_int, [ctypes.POINTER(fq_problem), _vp, _vp]),
     "floquet_batch_workspace_size": (_sz, [ctypes.POINTER(_vp), _i32]),
@@ -235,6 +236,10 @@ def floquet_average_observable(plan: int, X0, ncols: int, a0: float, a1: float, 
 
 def floquet_check_status(plan: int, stream=None) -> int:
     return int(lib.floquet_check_status(_vp(plan), _stream(stream)))
+
+
+def floquet_selftest_wait(plan: int, cycles: int, stream=None) -> None:
+    _check(lib.floquet_selftest_wait(_vp(plan), int(cycles), _stream(stream)), "floquet_selftest_wait")
 
 
 def floquet_last_error() -> str:

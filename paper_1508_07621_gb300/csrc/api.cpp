@@ -492,6 +492,15 @@ fq_status floquet_unitarity_defect(const void* d_U, int32_t n, const int32_t* d_
   return FQ_OK;
 }
 
+fq_status floquet_selftest_wait(fq_plan* p, int64_t cycles, void* stream) {
+  if (!p || cycles < 1 || cycles > (1ll << 31)) {
+    fq_set_error("floquet_selftest_wait: needs a plan and 1 <= cycles <= 2^31");
+    return FQ_EINVAL;
+  }
+  fq_launch_wait_probe(p->d_status, (long long)cycles, (cudaStream_t)stream);
+  return cuda_ok(cudaGetLastError(), "wait probe");
+}
+
 fq_status floquet_check_status(fq_plan* p, void* stream) {
   if (!p) { fq_set_error("NULL plan"); return FQ_EINVAL; }
   unsigned int v = 0;

@@ -143,6 +143,8 @@ void fq_launch_term_tri_f32(const float* d, const float* er, const float* ei, in
 int fq_resident_supported(int n, int L);
 // Tiled tridiagonal chain (tri_tile.cu): FP64 or FP32, any n, L <= 128.
 int fq_tile_supported(int L);
+// one bounded wait on an mbarrier nobody arrives on, then FQ_BIT_TIMEOUT (kernels.cu)
+void fq_launch_wait_probe(unsigned int* status, long long cycles, cudaStream_t s);
 // ---------------------------------------------------------------- dense_resident.cu
 bool fq_dense_resident_supported(int n, int L);
 // doubles in each of the S and A regions the resident chain needs for nsteps steps

@@ -544,6 +544,33 @@ void fq_launch_symv2(const double* h0, const double* h1, double g, int which, co
   k_symv2<<<(n + 7) / 8, 256, 0, s>>>(h0, h1, g, which, x, y, n);
 }
 
+namespace {
+// Bounded wait on an mbarrier nobody arrives on (the same try_wait loop as the pipelines'), then
+// the timeout bit: the diagnostic of floquet_selftest_wait.
+__global__ void k_wait_probe(unsigned int* status, long long cycles) {
+  __shared__ __align__(8) unsigned long long bar;
+  const unsigned addr = (unsigned)__cvta_generic_to_shared(&bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(1) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const long long t0 = clock64();
+  bool done = false;
+  while (!done && clock64() - t0 < cycles) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(addr), "r"(0)
+        : "memory");
+    done = ok != 0;
+  }
+  if (!done) atomicOr(status, FQ_BIT_TIMEOUT);
+}
+}  // namespace
+
+void fq_launch_wait_probe(unsigned int* status, long long cycles, cudaStream_t s) {
+  k_wait_probe<<<1, 1, 0, s>>>(status, cycles);
+}
+
 void fq_launch_defect(const double* u, int n, const int32_t* cols, int k, double* partial, cudaStream_t s) {
   dim3 g((n + 255) / 256, (k + 15) / 16);
   k_defect<<<g, 256, 0, s>>>((const double2*)u, n, cols, k, partial);

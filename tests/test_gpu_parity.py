@@ -423,3 +423,21 @@ def test_dense_double_float_limits_and_bounds(fq):
                          precision=fq.FQ_DF32)
     plan.build_UT()
     assert plan.check_status() == fq.FQ_EBOUND
+
+
+def test_bounded_wait_timeout_is_reported(fq):
+    """Failure detection without a fault: a wait on an mbarrier that nothing arrives on gives up
+    after its cycle limit and records the timeout; the host reads FQ_ETIMEOUT once, the word is
+    cleared, and the context and the plan keep working."""
+    m = fi.config_goe64()
+    plan = fq.Plan.dense(m.h0, m.h1, omega=1.0, f_ac=1.0, steps=4)
+    fq.floquet_selftest_wait(plan.handle, 2_000_000)
+    assert plan.check_status() == fq.FQ_ETIMEOUT
+    assert plan.check_status() == fq.FQ_OK
+    U = plan.build_UT()
+    assert plan.check_status() == fq.FQ_OK
+    mx, _ = fq.api.unitarity_defect(U)
+    assert mx <= 1e-12
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_selftest_wait(plan.handle, 0)
+    assert e.value.status == fq.FQ_EINVAL
