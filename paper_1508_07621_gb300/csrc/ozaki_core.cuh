@@ -145,10 +145,20 @@ __device__ __forceinline__ int oz_exponent(unsigned long long key) {
   return e < -960 ? -960 : e;
 }
 
-// The digits of r = x / 2^E (|r| < 1/2): R = rint(r 2^48), then d_q by rounding shifts of 8 bits;
-// slices d_q 2^(-8(q+1)) in BF16.  `scale` = 2^(48 - E).
-__device__ __forceinline__ void oz_digits(double x, double scale, __nv_bfloat16 (&s)[OZ_S]) {
-  long long R = __double2ll_rn(x * scale);
+// The digits of r = x / 2^E (|r| < 1/2): R = r 2^48 rounded to an integer, then d_q by rounding
+// shifts of 8 bits; slices d_q 2^(-8(q+1)) in BF16.  R comes straight from the bit pattern of x
+// (x = m 2^(b - 1075) with the 53-bit significand m and biased exponent b, so R = m shifted right
+// by 1027 + E - b >= 6 bits, rounded half away from zero): integer work only.
+__device__ __forceinline__ void oz_digits(double x, int E, __nv_bfloat16 (&s)[OZ_S]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int b = (int)((bits >> 52) & 0x7FF);
+  const int sh = 1027 + E - b;
+  long long R = 0;
+  if (b != 0 && sh < 64) {  // zero and subnormal entries (below 2^-1022) give zero digits
+    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    R = (long long)((m + (1ull << (sh - 1))) >> sh);
+    if (bits >> 63) R = -R;
+  }
 #pragma unroll
   for (int q = 0; q < OZ_S; ++q) {
     const int sh = 40 - 8 * q;
@@ -190,8 +200,13 @@ __device__ __forceinline__ void oz_row_value(const double* re, const double* im,
     a = j == k ? 1.0 : 0.0;
     b = 0.0;
   }
-  vr = cr * a - ci * b;
-  vi = cr * b + ci * a;
+  if (ci == 0.0 && cr == 1.0) {  // plain slicing: no FP64 arithmetic
+    vr = a;
+    vi = b;
+  } else {
+    vr = cr * a - ci * b;
+    vi = cr * b + ci * a;
+  }
 }
 
 __device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c, __nv_bfloat16 d) {
@@ -218,7 +233,6 @@ __global__ void k_oz_slice_left(const double* __restrict__ re, const double* __r
       m = b > m ? b : m;
     }
   const int e = oz_exponent(block_max_key(m, red));
-  const double scale = pow2(48 - e);
   __nv_bfloat16* row = left + (size_t)j * 2 * np;
   // four consecutive columns per thread: one 8-byte store per slice and part (np % 4 == 0, and
   // every slice row starts on an 8-byte boundary)
@@ -228,8 +242,8 @@ __global__ void k_oz_slice_left(const double* __restrict__ re, const double* __r
     for (int u = 0; u < 4; ++u) {
       double xr = 0.0, xi = 0.0;
       if (j < nc && k0 + u < n) oz_row_value(re, im, cr, ci, n, j, k0 + u, xr, xi);
-      oz_digits(xr, scale, sr[u]);
-      oz_digits(xi, scale, si[u]);
+      oz_digits(xr, e, sr[u]);
+      oz_digits(xi, e, si[u]);
     }
 #pragma unroll
     for (int q = 0; q < OZ_S; ++q) {
@@ -274,14 +288,13 @@ __global__ void k_oz_omega(const __grid_constant__ OzOmega a, int n, int np, siz
       m = y > m ? y : m;
     }
   const int e = oz_exponent(block_max_key(m, red));
-  const double scale = pow2(48 - e);
   const size_t rb = (size_t)(3 * OZ_BN) * (i / OZ_BN) + (i % OZ_BN);  // row of -A; S and A follow
   for (int k = threadIdx.x; k < np; k += blockDim.x) {
     double S = 0.0, A = 0.0;
     if (i < n && k < n) oz_omega_entry(a, n, i, k, S, A);
     __nv_bfloat16 ss[OZ_S], sa[OZ_S];
-    oz_digits(S, scale, ss);
-    oz_digits(A, scale, sa);
+    oz_digits(S, e, ss);
+    oz_digits(A, e, sa);
 #pragma unroll
     for (int q = 0; q < OZ_S; ++q) {
       __nv_bfloat16* base = right + q * rstride + k;
@@ -315,13 +328,12 @@ __global__ void k_oz_real(const double* __restrict__ h0, const double* __restric
       mx = a > mx ? a : mx;
     }
   const int e = oz_exponent(block_max_key(mx, red));
-  const double scale = pow2(48 - e);
   for (int k0 = 4 * threadIdx.x; k0 < np; k0 += 4 * blockDim.x) {
     __nv_bfloat16 sl[4][OZ_S];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const double v = (i < n && k0 + u < n) ? oz_real_entry(h0, h1, c1, inv, shift, n, i, k0 + u) : 0.0;
-      oz_digits(v, scale, sl[u]);
+      oz_digits(v, e, sl[u]);
     }
 #pragma unroll
     for (int q = 0; q < OZ_S; ++q)
