@@ -4,7 +4,8 @@
 // fixed-point slices of ozaki_core.cuh, FP64 states and FP64 epilogues.
 //
 // Piecewise-constant f makes Omega~_m = (H0 + f_m H1 - beta) / Delta E real symmetric, so every
-// product has a real right operand (k_oz_term<true, .>):
+// product has a real right operand (k_oz_real_term of ozaki_real.cuh: the real and imaginary rows
+// of 64 states stacked as one 128-row MMA operand, double-buffered drains):
 //   forward term   (OZ_FWD): psi_{l+1} = -2i Y + psi_{l-1}, acc += a_{l+1} psi_{l+1}, phase;
 //   adjoint term   (OZ_ADJ): bbar_l = conj(e^{-i beta h}) a_l G + i cw Omega~ bbar_{l+1} + bbar_{l+2}
 //                            (cw = 2, and 1 for l = 0);
@@ -17,7 +18,7 @@
 // rows against the stacked FP64 bbar_1 .. bbar_L.
 #include <vector>
 
-#include "ozaki_core.cuh"
+#include "ozaki_real.cuh"
 
 namespace {
 
@@ -68,7 +69,7 @@ size_t oz_grad_layout(const fq_plan* p, void* base, OzGradWs* out) {
   w.astride = (size_t)w.ncp * 2 * w.np;
   w.rstride = (size_t)w.np * w.np;
   w.plane = (size_t)n * n;
-  w.ncta = (w.ncp / BM) * (w.np / OZ_BN);
+  w.ncta = (w.ncp / OZR_BM) * (w.np / OZ_BN);
   char* b = (char*)base;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -109,18 +110,17 @@ fq_status oz_gemm(const OzGradWs& w, const __nv_bfloat16* left, size_t lstride, 
   OzMaps maps{};
   fq_status st;
   for (int q = 0; q < OZ_S; ++q) {
-    if ((st = make_map(&maps.a[q], left + q * lstride, rows, 2 * w.np, BM, OZ_BKE)) != FQ_OK) return st;
+    if ((st = make_map(&maps.a[q], left + q * lstride, rows, 2 * w.np, OZR_BM, OZ_BKE)) != FQ_OK) return st;
     if ((st = make_map(&maps.r[q], right + q * w.rstride, w.np, w.np, OZ_BN, OZ_BKE)) != FQ_OK) return st;
   }
   static std::atomic<unsigned> attr_set{0};
   if (fq_first_on_device(attr_set)) {
-    cudaError_t r = cudaFuncSetAttribute(k_oz_term<true, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)OzCfg<true>::SMEM);
+    cudaError_t r = cudaFuncSetAttribute(k_oz_real_term<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)OZR_SMEM);
     if (r != cudaSuccess) return fq_cuda_fail(r, "FP64-emulation gradient kernel shared-memory attribute");
   }
-  const int tiles_i = w.np / OZ_BN, tiles_j = rows / BM;
-  k_oz_term<true, EPI><<<tiles_i * tiles_j, OZ_THREADS, OzCfg<true>::SMEM, s>>>(maps, w.np / OZ_BKE, tiles_j, tiles_i,
-                                                                               w.np, e);
+  const int tiles_i = w.np / OZ_BN, tiles_j = rows / OZR_BM;
+  k_oz_real_term<EPI><<<tiles_i * tiles_j, OZ_THREADS, OZR_SMEM, s>>>(maps, w.np / OZ_BKE, tiles_j, tiles_i, w.np, e);
   return FQ_OK;
 }
 
