@@ -1,5 +1,5 @@
 // Forward chain of the FP64 emulation (FQ_OZAKI, kernels in ozaki_core.cuh): per step the
-// fixed-point slices of Omega~_m, then L terms of Eq. 10 through k_oz_term<false, OZ_FWD> whose
+// fixed-point slices of Omega~_m, then L terms of Eq. 10 through k_oz_term whose
 // FP64 epilogue applies the recurrence, the Bessel accumulation of Eq. 12 and the step phase;
 // each new state block is sliced again (its row scales need whole rows).
 #include "ozaki_core.cuh"
@@ -86,8 +86,8 @@ fq_status fq_ozaki_propagate(fq_plan* p, const double* x0, double* x, int nc, in
   }
   static std::atomic<unsigned> attr_set{0};
   if (fq_first_on_device(attr_set)) {
-    cudaError_t e = cudaFuncSetAttribute(k_oz_term<false, OZ_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)OzCfg<false>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_oz_term, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)OzCfg::SMEM);
     if (e != cudaSuccess) return fq_cuda_fail(e, "Ozaki kernel shared-memory attribute");
   }
   fq_blk<double> b0{w.m[0][0], w.m[0][1]};
@@ -127,7 +127,7 @@ fq_status fq_ozaki_propagate(fq_plan* p, const double* x0, double* x, int nc, in
       e.es = w.es;
       e.et = w.et;
       e.t = t;
-      k_oz_term<false, OZ_FWD><<<tiles_i * tiles_j, OZ_THREADS, OzCfg<false>::SMEM, s>>>(maps, nk, tiles_j, tiles_i,
+      k_oz_term<<<tiles_i * tiles_j, OZ_THREADS, OzCfg::SMEM, s>>>(maps, nk, tiles_j, tiles_i,
                                                                                         w.np, e);
       if (!(t.last && m == m_end - 1))
         k_oz_slice_left<<<w.ncp, 256, 0, s>>>(w.m[out][0], w.m[out][1], 1.0, 0.0, nullptr, nullptr, n, nc, w.np,

@@ -51,22 +51,21 @@ constexpr int OZ_A_BYTES = BM * OZ_ROWB;                   // one slice of Psi_r
 constexpr uint32_t OZ_TMEM_COLS = 512;      // 4 accumulators x (Yr | Yi) x 64 columns
 constexpr int OZ_XS_BYTES = 64 * 4 * 32 * OZ_EPI_WARPS;   // drained sums staged for the epilogue
 
-// Stage layout.  Complex right operand (Omega~ = S + i A): one slice is the [-A; S; A] rows of a
-// 64-row block.  Real right operand (the adjoint's real symmetric Omega~ and H1 / Delta E): one
-// slice is the 64 rows of S, two N = 64 MMAs per pair (Yr from Psi_r, Yi from Psi_i).
-template <bool REAL>
+// Stage layout of the complex product (Omega~ = S + i A): one right slice is the [-A; S; A] rows
+// of a 64-row block.  (Products with a real right operand use ozaki_real.cuh.)
 struct OzCfg {
-  static constexpr int R_ROWS = REAL ? OZ_BN : 3 * OZ_BN;
+  static constexpr int R_ROWS = 3 * OZ_BN;
   static constexpr int R_BYTES = R_ROWS * OZ_ROWB;
   static constexpr int STAGE_BYTES = 2 * OZ_S * OZ_A_BYTES + OZ_S * R_BYTES;
-  static constexpr int STAGES = REAL ? 3 : 2;
+  static constexpr int STAGES = 2;
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
   static_assert((size_t)STAGES * STAGE_BYTES >= OZ_XS_BYTES + 16 * sizeof(double2), "epilogue staging");
 };
 
 struct OzMaps {
   CUtensorMap a[OZ_S];  // left slices [rows][2 np]: Psi_r in columns [0, np), Psi_i in [np, 2 np)
-  CUtensorMap r[OZ_S];  // right slices: [3 np][np] (per 64-row block of Omega~, rows -A, S, A) or [np][np]
+  CUtensorMap r[OZ_S];  // right slices: [3 np][np] (per 64-row block of Omega~, rows -A, S, A), or
+                        // [np][np] for a real operator (ozaki_real.cuh)
 };
 
 // Epilogue of one product Y = Psi . Omega~^T (FP64 states, row stride n):
@@ -342,11 +341,10 @@ __global__ void k_oz_real(const double* __restrict__ h0, const double* __restric
   if (threadIdx.x == 0) et[i] = e;
 }
 
-// One product on a 128-state x 64-column tile (see the file comment).
-template <bool REAL, int EPI>
+// One Chebyshev term (OZ_FWD) on a 128-state x 64-column tile (see the file comment).
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_oz_term(const __grid_constant__ OzMaps maps, int nk, int tiles_j, int tiles_i, int np, OzEpi e) {
-  using Cfg = OzCfg<REAL>;
+  using Cfg = OzCfg;
   constexpr int OZ_STAGES = Cfg::STAGES;
   constexpr int OZ_STAGE_BYTES = Cfg::STAGE_BYTES;
   constexpr int OZ_R_BYTES = Cfg::R_BYTES;
@@ -413,8 +411,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         for (int q = 0; q < OZ_S; ++q) {
           tma_load_2d(st + (2 * q) * OZ_A_BYTES, &maps.a[q], bar, kx, j0);           // Psi_r
           tma_load_2d(st + (2 * q + 1) * OZ_A_BYTES, &maps.a[q], bar, np + kx, j0);  // Psi_i
-          tma_load_2d(st + 2 * OZ_S * OZ_A_BYTES + q * OZ_R_BYTES, &maps.r[q], bar, kx,
-                      REAL ? i0 : 3 * i0);  // S, or -A, S, A
+          tma_load_2d(st + 2 * OZ_S * OZ_A_BYTES + q * OZ_R_BYTES, &maps.r[q], bar, kx, 3 * i0);  // -A, S, A
         }
         issued = kb + 1;
       }
@@ -427,8 +424,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---------------- MMA issuer
-      constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                                 ((uint32_t)((REAL ? OZ_BN : 2 * OZ_BN) >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+      constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * OZ_BN) >> 3) << 17) |
+                                 ((uint32_t)(BM >> 4) << 24);
       bool ok = true;
       int kb = 0;
       for (int c = 0; c < nchunks && ok; ++c) {
@@ -455,16 +452,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const uint32_t acc = tmem + (uint32_t)g * (2 * OZ_BN);
             const uint32_t rb = 2 * OZ_S * OZ_A_BYTES + b * OZ_R_BYTES;
             const uint32_t first = (kq == 0 && lead) ? 0u : 1u;
-            if (REAL) {  // Yr = Psi_r . S, Yi = Psi_i . S
-              mma_bf16(acc, d0 + (uint64_t)(((2 * a) * OZ_A_BYTES) >> 4), d0 + (uint64_t)(rb >> 4), idesc, first);
-              mma_bf16(acc + OZ_BN, d0 + (uint64_t)(((2 * a + 1) * OZ_A_BYTES) >> 4), d0 + (uint64_t)(rb >> 4), idesc,
-                       first);
-            } else {
-              mma_bf16(acc, d0 + (uint64_t)(((2 * a) * OZ_A_BYTES) >> 4),
-                       d0 + (uint64_t)((rb + OZ_BN * OZ_ROWB) >> 4), idesc, first);  // Psi_r . [S; A]
-              mma_bf16(acc, d0 + (uint64_t)(((2 * a + 1) * OZ_A_BYTES) >> 4), d0 + (uint64_t)(rb >> 4), idesc,
-                       1u);                                                            // Psi_i . [-A; S]
-            }
+            mma_bf16(acc, d0 + (uint64_t)(((2 * a) * OZ_A_BYTES) >> 4), d0 + (uint64_t)((rb + OZ_BN * OZ_ROWB) >> 4),
+                     idesc, first);  // Psi_r . [S; A]
+            mma_bf16(acc, d0 + (uint64_t)(((2 * a + 1) * OZ_A_BYTES) >> 4), d0 + (uint64_t)(rb >> 4), idesc,
+                     1u);            // Psi_i . [-A; S]
           }
           mma_commit(empty0 + 8 * s);
         }
@@ -516,7 +507,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty);
     }
-    double dsr = 0.0, dsi = 0.0;  // DOT partial of this thread
     if (!ok) {
       atomicExch(abort_flag, 1);
       atomicOr(e.t.status, FQ_BIT_TIMEOUT);
@@ -549,25 +539,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const double yr = ((double)xs[b * XS] + (double)xs[(b + 1) * XS]) * sc;
         const double yi = ((double)xs[(b + 2) * XS] + (double)xs[(b + 3) * XS]) * sc;
         const size_t idx = (size_t)j * e.n + i;
-        if (EPI == OZ_DOT) {  // conj(b) Y
-          const double br = e.cur_re[idx], bi = e.cur_im[idx];
-          dsr = fma(br, yr, fma(bi, yi, dsr));
-          dsi = fma(br, yi, fma(-bi, yr, dsi));
-          continue;
-        }
-        if (EPI == OZ_ADJ) {  // out = cpa g + i cw Y + b2
-          const double gr = e.cur_re[idx], gi = e.cur_im[idx];
-          double orr = e.cpa_re * gr - e.cpa_im * gi - e.cw * yi;
-          double oi = e.cpa_re * gi + e.cpa_im * gr + e.cw * yr;
-          if (e.prev_re) {
-            orr += e.prev_re[idx];
-            oi += e.prev_im[idx];
-          }
-          bad |= !(orr * orr + oi * oi <= t.bound2);
-          e.out_re[idx] = orr;
-          e.out_im[idx] = oi;
-          continue;
-        }
         double pr, pi;
         if (t.first) {
           pr = yi;
@@ -596,24 +567,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         }
       }
       if (bad) atomicOr(t.status, FQ_BIT_BOUND);
-    }
-    if (EPI == OZ_DOT) {  // per-CTA partial, summed in a fixed order (bit-reproducible)
-      double2* red = reinterpret_cast<double2*>(gbase + OZ_XS_BYTES);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        dsr += __shfl_xor_sync(0xffffffffu, dsr, o);
-        dsi += __shfl_xor_sync(0xffffffffu, dsi, o);
-      }
-      if (lane == 0) red[warp - 2] = make_double2(dsr, dsi);
-      asm volatile("bar.sync 1, %0;" ::"n"(32 * OZ_EPI_WARPS) : "memory");  // the drain warps only
-      if (warp == 2 && lane == 0) {
-        double sr = 0.0, si = 0.0;
-        for (int q = 0; q < OZ_EPI_WARPS; ++q) {
-          sr += red[q].x;
-          si += red[q].y;
-        }
-        e.partial[tj * tiles_i + ti] = make_double2(sr, si);
-      }
     }
   }
   tc_fence_before();
