@@ -563,7 +563,7 @@ def run_dense(args):
     achieved = issued / avg / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
                 "frac": achieved / peaks["bf16_sustained"], "traffic": None,
-                "kernel": "k_oz_term<false, OZ_FWD>" if prec == "ozaki" else "k_split_persist",
+                "kernel": "k_oz_term" if prec == "ozaki" else "k_split_persist",
                 "useful_tflops": useful / avg / 1e12,
                 "note": (f"issued BF16 MMA flop = {SLICE_PRODUCTS[prec]} slice products x 8 N^3 per term x M L terms "
                          "per build over the build's CUDA-event time (the operator and slicing kernels, a few "
@@ -698,7 +698,7 @@ def run_adjoint(args):
     else:
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
                     "frac": achieved / peaks["bf16_sustained"], "traffic": None,
-                    "kernel": "k_oz_term<true, *>" if prec == "ozaki" else "k_split_persist / k_split_term",
+                    "kernel": "k_oz_real_term<*>" if prec == "ozaki" else "k_split_persist / k_split_term",
                     "useful_tflops": useful / avg / 1e12,
                     "note": (f"issued BF16 MMA flop = {SLICE_PRODUCTS[prec]} slice products x 4 M L x 4 N^3 per "
                              "gradient over the gradient's CUDA-event time (every other kernel included); peak: "
