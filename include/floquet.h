@@ -135,7 +135,7 @@ typedef struct fq_plan_info {
 } fq_plan_info;
 
 /* Host planning + upload (§3: Magnus scalars, [H0,H1] computed once, bounds, Bessel
- * coefficients; Algorithm 1 steps 1-4).  Uses the current CUDA device; allocates the plan's
+ * coefficients; the set-up part of Algorithm 1).  Uses the current CUDA device; allocates the plan's
  * device copies.  On failure *plan is NULL. */
 fq_status floquet_plan_create(fq_plan** plan, const fq_problem* problem);
 
@@ -152,7 +152,7 @@ fq_status floquet_plan_inspect(const fq_problem* problem, fq_plan_info* info, do
 /* Bytes of workspace floquet_propagate / floquet_build_UT need for ncols states. */
 size_t floquet_workspace_size(const fq_plan* plan, int32_t ncols);
 
-/* U_T (Algorithm 1 steps 5-11): propagates the N x N identity over all M steps and writes
+/* U_T (the propagation part of Algorithm 1): propagates the N x N identity over all M steps and writes
  * d_U = N x N complex128, U[i][j] = <i|U_T|j>.  d_ws: floquet_workspace_size(plan, N) bytes,
  * 256-byte aligned.  Asynchronous on `stream`. */
 fq_status floquet_build_UT(fq_plan* plan, void* d_U, void* d_ws, size_t ws_bytes, void* stream);

@@ -305,7 +305,7 @@ def chebyshev_step(apply, x, coeffs, phase):
 # ------------------------------------------------------------------------ propagation
 def propagate_dense(h0, h1, plan: Plan, x0, m_begin=0, m_end=None):
     """Chain of Eq. 9 from step m_begin to m_end (0-based, exclusive end) on the block x0
-    (n x c, one state per column); Algorithm 1, steps 6-10."""
+    (n x c, one state per column); the step loop of Algorithm 1."""
     m_end = plan.steps if m_end is None else m_end
     k = commutator_dense(h0, h1)
     x = np.array(x0, dtype=np.complex128)
@@ -363,7 +363,7 @@ def plan_for_drive_tridiag(h0_diag, h0_off, h1_diag, drive, steps, tol=1e-14):
 def quasienergies(u: np.ndarray, period: float) -> np.ndarray:
     """Eqs. 4-5 with reading R7: U_T phi = e^{-i theta} phi, eps = theta/T,
     theta = -arg(lambda) in [-pi, pi); returned sorted ascending.  Eigenvalues by
-    LAPACK zgeev (§5, Algorithm 1 step 12)."""
+    LAPACK zgeev (§5; the last part of Algorithm 1)."""
     lam = np.linalg.eigvals(u)
     theta = -np.angle(lam)
     theta = np.where(theta >= math.pi, theta - 2.0 * math.pi, theta)

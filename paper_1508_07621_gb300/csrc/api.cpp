@@ -1,5 +1,5 @@
 // C ABI: plan lifetime, workspace layout and the host loops that chain the kernels
-// (Algorithm 1 steps 5-11: M steps of L Chebyshev terms each, U_T written in place).
+// (the propagation part of Algorithm 1: M steps of L Chebyshev terms each, U_T written in place).
 #include <math.h>
 #include <string.h>
 

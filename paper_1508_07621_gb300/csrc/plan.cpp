@@ -1,7 +1,7 @@
 // Host planning (FP64): drive samples, Magnus-4 scalars, spectral bounds, Bessel weights.
 //
-// Everything here is computed once per plan, before any propagation (§3: the commutators
-// "have to be calculated only once"; Algorithm 1 steps 2-4).
+// Everything here is computed once per plan, before any propagation (§3: the commutators are
+// formed a single time for the whole chain; the set-up part of Algorithm 1).
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
