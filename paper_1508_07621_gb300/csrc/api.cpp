@@ -118,26 +118,21 @@ int run_chain(fq_plan* p, StateWs& w, int x, int nc, int m_begin, int m_end, cud
       t.coef = p->cheb[l + 1];
       // output: psi_{l+1} goes to a fresh buffer on the first term, in place of psi_{l-1}
       // afterwards; the step result of a one-term step goes to the free third buffer
-      int out;
-      if (l == 0) out = t.last ? nxt : nxt;
-      else out = prv;
-      fq_blk<T> bc = blk<T>(w.buf[cur]);
-      fq_blk<T> bp = prv >= 0 ? blk<T>(w.buf[prv]) : bc;
-      fq_blk<T> ba = blk<T>(w.buf[acc]);
-      fq_blk<T> bo = blk<T>(w.buf[out]);
+      const int out = l == 0 ? nxt : prv;
+      const int pq = prv >= 0 ? prv : cur;  // psi_{l-1} (unused on the first term)
       if (p->path == PATH_DENSE_F64) {
-        fq_launch_term_dense_f64(w.S, w.A, n, *(fq_blk<double>*)&bc, *(fq_blk<double>*)&bp, *(fq_blk<double>*)&ba,
-                                 *(fq_blk<double>*)&bo, nc, t, s);
+        fq_launch_term_dense_f64(w.S, w.A, n, blk<double>(w.buf[cur]), blk<double>(w.buf[pq]),
+                                 blk<double>(w.buf[acc]), blk<double>(w.buf[out]), nc, t, s);
       } else {
         const size_t off = (size_t)(m - m_begin) * ld;
         if (sizeof(T) == 8)
           fq_launch_term_tri_f64((const double*)cd + off, (const double*)cer + off, (const double*)cei + off, n,
-                                 *(fq_blk<double>*)&bc, *(fq_blk<double>*)&bp, *(fq_blk<double>*)&ba,
-                                 *(fq_blk<double>*)&bo, nc, ld, t, s);
+                                 blk<double>(w.buf[cur]), blk<double>(w.buf[pq]), blk<double>(w.buf[acc]),
+                                 blk<double>(w.buf[out]), nc, ld, t, s);
         else
           fq_launch_term_tri_f32((const float*)cd + off, (const float*)cer + off, (const float*)cei + off, n,
-                                 *(fq_blk<float>*)&bc, *(fq_blk<float>*)&bp, *(fq_blk<float>*)&ba,
-                                 *(fq_blk<float>*)&bo, nc, ld, t, s);
+                                 blk<float>(w.buf[cur]), blk<float>(w.buf[pq]), blk<float>(w.buf[acc]),
+                                 blk<float>(w.buf[out]), nc, ld, t, s);
       }
       if (t.last) {
         x = out;
