@@ -125,3 +125,45 @@ def test_fixed_chebyshev_terms(fq):
         with pytest.raises(fq.FloquetError) as e:
             fq.floquet_plan_inspect(prob)
         assert e.value.status == fq.FQ_EINVAL
+
+
+@pytest.mark.parametrize("case,status", [
+    ("steps0", "FQ_EINVAL"), ("period0", "FQ_EINVAL"), ("format9", "FQ_EINVAL"), ("drive9", "FQ_EINVAL"),
+    ("piecewise_without_f", "FQ_EINVAL"), ("order5", "FQ_EINVAL"), ("order6_tridiag", "FQ_EUNSUPPORTED"),
+    ("order6_piecewise", "FQ_EUNSUPPORTED"), ("tile96", "FQ_EINVAL"), ("dense_fp32", "FQ_EUNSUPPORTED"),
+    ("tridiag_ozaki", "FQ_EUNSUPPORTED")])
+def test_problem_validation(fq, case, status):
+    """Every rejected problem fails in host planning with its status and a message, before any
+    device work."""
+    n = 8
+    d = np.arange(n, dtype=float)
+    g = fi.goe(n, 5)
+    kw = dict(f_ac=1.0, omega=1.0)
+    if case == "steps0":
+        prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 0, **kw)
+    elif case == "period0":
+        prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 0.0, 4, **kw)
+    elif case == "format9":
+        prob, keep = fq.make_problem(n, 9, g, g, 1.0, 4, **kw)
+    elif case == "drive9":
+        prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, drive_kind=9, **kw)
+    elif case == "piecewise_without_f":
+        prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, drive_kind=fq.FQ_DRIVE_PIECEWISE, **kw)
+    elif case == "order5":
+        prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, magnus_order=5, **kw)
+    elif case == "order6_tridiag":
+        prob, keep = fq.make_problem(n, fq.FQ_TRIDIAG, d, d, 1.0, 4, h0_off=np.ones(n - 1), magnus_order=6, **kw)
+    elif case == "order6_piecewise":
+        prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, drive_kind=fq.FQ_DRIVE_PIECEWISE,
+                                     f_steps=np.ones(4), magnus_order=6)
+    elif case == "tile96":
+        prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, precision=fq.FQ_BF16X3, tile_n=96, **kw)
+    elif case == "dense_fp32":
+        prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, precision=fq.FQ_FP32, **kw)
+    else:
+        prob, keep = fq.make_problem(n, fq.FQ_TRIDIAG, d, d, 1.0, 4, h0_off=np.ones(n - 1),
+                                     precision=fq.FQ_OZAKI, **kw)
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_plan_inspect(prob)
+    assert e.value.status == getattr(fq, status)
+    assert fq.floquet_last_error()
