@@ -251,6 +251,16 @@ fq_status floquet_check_status(fq_plan* plan, void* stream);
  * and returns.  The next floquet_check_status reports FQ_ETIMEOUT; the context stays usable. */
 fq_status floquet_selftest_wait(fq_plan* plan, int64_t cycles, void* stream);
 
+/* Quasienergies (Eq. 5) and Floquet states of U_T on the host, outside the timed propagation:
+ * U = N x N complex128 host array, row-major, U[i][j] = <i|U_T|j> (as floquet_build_UT writes it).
+ * eps_out: N doubles, eps_mu = theta_mu / T with theta_mu = -arg(lambda_mu) folded into
+ * [-pi, pi), ascending.  states_out (NULL: not computed): N x N complex128, row mu = the unit
+ * Floquet state of eps_out[mu].  Complex Schur form by Householder reduction and shifted QR
+ * (no LAPACK linked; O(N^3) on one core: about 5 s at N = 1000 for eps alone, 15 s with the
+ * states); U_T is normal, so the Schur vectors are its eigenvectors.  FQ_EINVAL on bad
+ * arguments or if the iteration does not converge.  Needs no device. */
+fq_status floquet_quasienergies(const void* U, int32_t n, double period, double* eps_out, void* states_out);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* floquet_last_error(void);
 

@@ -61,6 +61,7 @@ _SIGS = {
     "floquet_grad_workspace_size": (_sz, [_vp]),
     "floquet_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "floquet_selftest_wait": (ctypes.c_int, [_vp, ctypes.c_int64, _vp]),
+    "floquet_quasienergies": (ctypes.c_int, [_vp, _i32, ctypes.c_double, _dp, _vp]),
     "floquet_check_status": (ctypes.c_int, [_vp, _vp]),
     "floquet_build_UT_static": (ctypes.c_int, [ctypes.POINTER(fq_problem), _vp, _vp]),
     "floquet_batch_workspace_size": (_sz, [ctypes.POINTER(_vp), _i32]),
@@ -236,6 +237,19 @@ def floquet_average_observable(plan: int, X0, ncols: int, a0: float, a1: float, 
 
 def floquet_check_status(plan: int, stream=None) -> int:
     return int(lib.floquet_check_status(_vp(plan), _stream(stream)))
+
+
+def floquet_quasienergies(u, period: float, states: bool = True):
+    """(eps ascending, Floquet states as rows or None) of the host complex128 N x N array u by
+    the library's host Schur solver."""
+    import numpy as np
+    u = np.ascontiguousarray(u, dtype=np.complex128)
+    n = u.shape[0]
+    eps = np.empty(n)
+    out = np.empty((n, n), dtype=np.complex128) if states else None
+    _check(lib.floquet_quasienergies(u.ctypes.data_as(_vp), n, float(period), eps.ctypes.data_as(_dp),
+                                     out.ctypes.data_as(_vp) if states else None), "floquet_quasienergies")
+    return eps, out
 
 
 def floquet_selftest_wait(plan: int, cycles: int, stream=None) -> None:

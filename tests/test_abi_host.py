@@ -167,3 +167,62 @@ def test_problem_validation(fq, case, status):
         fq.floquet_plan_inspect(prob)
     assert e.value.status == getattr(fq, status)
     assert fq.floquet_last_error()
+
+
+def _built_spectrum(n, seed, theta):
+    """U = V diag(e^{-i theta}) V^H with Haar V: quasienergies theta/T and states V known by
+    construction (Eq. 5)."""
+    v = fi.haar_unitary(n, seed)
+    return (v * np.exp(-1j * theta)[None, :]) @ v.conj().T, v
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 64, 200])
+def test_host_quasienergies_known_spectrum(fq, n):
+    """The library's host Schur solver recovers a spectrum fixed by construction (eps = theta/T,
+    ascending in [-pi/T, pi/T)), with orthonormal states that satisfy U phi = e^{-i eps T} phi
+    and match the constructed eigenvectors up to phase; eps alone gives the same values."""
+    T = 2.5
+    theta = np.sort(np.random.default_rng(n).uniform(-math.pi, math.pi, n))
+    u, v = _built_spectrum(n, 40 + n, theta)
+    eps, st = fq.floquet_quasienergies(u, T)
+    assert np.all(np.diff(eps) >= 0)
+    assert np.max(np.abs(eps - theta / T)) <= 1e-12
+    assert np.max(np.abs(u @ st.T - st.T * np.exp(-1j * eps * T)[None, :])) <= 1e-12
+    assert np.max(np.abs(st.conj() @ st.T - np.eye(n))) <= 1e-12
+    gap = np.min(np.diff(np.concatenate([theta, [theta[0] + 2 * math.pi]]))) if n > 1 else 1.0
+    if gap > 1e-6:  # well separated: each state is the constructed column up to a phase
+        assert np.max(np.abs(np.abs(np.sum(st.conj() * v.T, axis=1)) - 1)) <= 1e-12 / gap
+    eps2, none = fq.floquet_quasienergies(u, T, states=False)
+    assert none is None and np.max(np.abs(eps2 - eps)) <= 1e-12
+
+
+def test_host_quasienergies_special_cases(fq):
+    """Closed forms: the cyclic shift has the N-th roots of unity as eigenvalues; the identity
+    is fully degenerate (eps = 0, any orthonormal basis); a diagonal U is already in Schur form,
+    including the branch point theta = -pi (lambda = -1 maps to eps = -pi/T, not +pi/T)."""
+    n = 12
+    shift = np.roll(np.eye(n), 1, axis=0).astype(complex)
+    eps, st = fq.floquet_quasienergies(shift, 1.0)
+    ref = np.sort(np.array([-(2 * math.pi * k / n) for k in range(n)]))
+    ref = np.sort(np.where(ref < -math.pi, ref + 2 * math.pi, ref))
+    assert np.max(np.abs(eps - ref)) <= 1e-13
+    eps, st = fq.floquet_quasienergies(np.eye(5, dtype=complex), 3.0)
+    assert np.max(np.abs(eps)) == 0 and np.max(np.abs(st.conj() @ st.T - np.eye(5))) <= 1e-15
+    d = np.exp(-1j * np.array([0.5, -math.pi, 2.0]))
+    d[1] = -1.0
+    eps, st = fq.floquet_quasienergies(np.diag(d), 2.0)
+    assert np.allclose(eps, np.array([-math.pi, 0.5, 2.0]) / 2.0, atol=1e-15, rtol=0)
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_quasienergies(np.eye(3, dtype=complex), 0.0)
+    assert e.value.status == fq.FQ_EINVAL
+
+
+def test_host_quasienergies_of_oracle_UT(fq):
+    """On a propagated U_T (GOE64 drive, the oracle's FP64 chain), the library's quasienergies
+    equal the oracle's (LAPACK zgeev)."""
+    m = fi.config_goe64()
+    p = o.plan_for_drive_dense(m.h0, m.h1, m.drive, 40)
+    u = o.build_ut_dense(m.h0, m.h1, p)
+    T = m.drive.period
+    eps, _ = fq.floquet_quasienergies(u, T, states=False)
+    assert np.max(np.abs(eps - o.quasienergies(u, T))) <= 1e-12
