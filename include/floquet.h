@@ -10,6 +10,18 @@
  * recurrence (Eq. 10) with Bessel weights a_0 = J_0(R), a_l = 2 J_l(R), R = h Delta E (Eq. 12).
  * hbar = 1 throughout.
  *
+ * Stages of the path, as the sources label them
+ *  a1  host planning: Magnus scalars per step, spectral bounds, R, L, Bessel weights
+ *  a2  the rescaled step exponent Omega~_m (Eq. 11), formed in FP64 once per step
+ *  a3  one dense Chebyshev term (a complex N x N product, Eq. 10)
+ *  a4  one tridiagonal Chebyshev term
+ *  a5  the Bessel-weighted accumulation, fused into the term's epilogue
+ *  a6  the step close (phase e^{-i beta h}) and the chaining of the M steps
+ *  a7  the unitarity defect of U_T
+ *  a8  operand preparation for the tensor cores (BF16 or fixed-point slices)
+ *  a9  many plans' U_T builds in one CUDA graph
+ *  a10 the adjoint chain and the gradient of the gate-fidelity loss in the drive amplitudes
+ *
  * Conventions
  *  - Complex numbers at the boundary are interleaved (re, im) doubles, i.e. C99 double
  *    complex / torch.complex128.
