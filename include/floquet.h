@@ -49,6 +49,10 @@
  *    synchronises the stream, returns FQ_EBOUND if any bit was set, and clears it.  The
  *    library never traps or aborts.  floquet_last_error returns a message for the last
  *    failing call of the calling thread.
+ *  - Problems are checked in host planning: every operator entry, drive parameter, drive sample
+ *    and caller bound must be finite (else FQ_EINVAL), and R = h Delta E must be at most 16384
+ *    (about R + 300 Chebyshev products per step; beyond it FQ_EUNSUPPORTED: use more steps).
+ *  - No C++ exception leaves the library: a failed host allocation is FQ_ENOMEM.
  *  - Plans are not thread-safe: one plan must not be used by two concurrent calls.
  */
 #ifndef FLOQUET_H

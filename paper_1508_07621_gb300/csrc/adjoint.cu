@@ -338,8 +338,8 @@ extern "C" size_t floquet_grad_workspace_size(const fq_plan* p) {
   return grad_layout(p, nullptr, nullptr);
 }
 
-extern "C" fq_status floquet_grad(fq_plan* p, const double* d_f, const void* d_W, double* d_loss, double* d_grad,
-                                  void* d_ws, size_t ws_bytes, void* stream) {
+static fq_status floquet_grad_body(fq_plan* p, const double* d_f, const void* d_W, double* d_loss, double* d_grad,
+                                   void* d_ws, size_t ws_bytes, void* stream) {
   if (!p || !d_f || !d_W || !d_loss || !d_grad) {
     fq_set_error("floquet_grad: NULL argument");
     return FQ_EINVAL;
@@ -433,4 +433,11 @@ extern "C" fq_status floquet_grad(fq_plan* p, const double* d_f, const void* d_W
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fq_cuda_fail(e, "floquet_grad kernels");
   return FQ_OK;
+}
+
+extern "C" fq_status floquet_grad(fq_plan* p, const double* d_f, const void* d_W, double* d_loss, double* d_grad,
+                                  void* d_ws, size_t ws_bytes, void* stream) {
+  return fq_guard("floquet_grad", [&] {
+    return floquet_grad_body(p, d_f, d_W, d_loss, d_grad, d_ws, ws_bytes, stream);
+  });
 }

@@ -227,45 +227,43 @@ fq_status propagate_impl(fq_plan* p, const double* x0, double* x, int nc, int m_
 
 void free_plan(fq_plan* p) {
   if (!p) return;
-  cudaFree(p->d_h0);
-  cudaFree(p->d_h1);
-  cudaFree(p->d_k);
-  cudaFree(p->d_h0o);
-  cudaFree(p->d_scal);
-  cudaFree(p->d_status);
-  cudaFree(p->d_cm);
+  for (void* d : {(void*)p->d_h0, (void*)p->d_h1, (void*)p->d_k, (void*)p->d_h0o, (void*)p->d_scal,
+                  (void*)p->d_status, (void*)p->d_cm})
+    if (d) cudaFree(d);
   delete p;
 }
 
-}  // namespace
+// Owns a plan under construction until it is handed to the caller.
+struct PlanOwner {
+  fq_plan* p;
+  ~PlanOwner() { free_plan(p); }
+  fq_plan* release() {
+    fq_plan* q = p;
+    p = nullptr;
+    return q;
+  }
+};
 
-extern "C" {
-
-fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
-  if (!out) { fq_set_error("plan pointer is NULL"); return FQ_EINVAL; }
-  *out = nullptr;
-  fq_plan* p = new (std::nothrow) fq_plan();
-  if (!p) { fq_set_error("host allocation failed"); return FQ_ENOMEM; }
+fq_status plan_create(fq_plan** out, const fq_problem* prob) {
+  PlanOwner own{new fq_plan()};  // frees the plan on every early return and on an exception
+  fq_plan* p = own.p;
   // dense spectral bounds wait for H0, H1 on the device (their Lanczos products run there)
   fq_status st = fq_host_plan(prob, p, prob && prob->format == FQ_DENSE);
-  if (st != FQ_OK) { delete p; return st; }
+  if (st != FQ_OK) return st;
   const int n = p->n, M = p->steps;
   if (p->format == FQ_TRIDIAG) {
     const bool res_ok = p->precision == FQ_FP32 && fq_resident_supported(n, p->L);
     const bool tile_ok = fq_tile_supported(p->L) != 0;
     if (prob->kernel == FQ_KERNEL_RESIDENT && !res_ok) {
       fq_set_error("resident kernel needs FQ_FP32, N <= 10240 and L <= 128 (N = %d, L = %d)", n, p->L);
-      delete p;
       return FQ_EUNSUPPORTED;
     }
     if ((prob->kernel == FQ_KERNEL_TILED || p->precision == FQ_DF32) && !tile_ok) {
       fq_set_error("tiled kernel needs L <= 128 (L = %d)", p->L);
-      delete p;
       return FQ_EUNSUPPORTED;
     }
     if (p->precision == FQ_DF32 && prob->kernel != FQ_KERNEL_AUTO && prob->kernel != FQ_KERNEL_TILED) {
       fq_set_error("FQ_DF32 runs on the tiled kernel only");
-      delete p;
       return FQ_EUNSUPPORTED;
     }
     switch (prob->kernel) {
@@ -283,7 +281,6 @@ fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
   auto fail = [&](cudaError_t e, const char* what) {
     fq_status r = (e == cudaErrorMemoryAllocation) ? FQ_ENOMEM : FQ_ECUDA;
     fq_cuda_fail(e, what);
-    free_plan(p);
     return r;
   };
   cudaError_t e;
@@ -319,7 +316,7 @@ fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
     fq_dense_bounds(n, p->dense_glo, p->dense_ghi, p->dense_kmax, apply, &emin, &emax);
     cudaFree(d_x);
     if (ae != cudaSuccess) return fail(ae, "Lanczos products");
-    fq_finish_computed_bounds(p, emin, emax);
+    if ((st = fq_finish_computed_bounds(p, emin, emax)) != FQ_OK) return st;
     p->dense_bounds_pending = false;
   }
   std::vector<double> scal(3 * (size_t)M);
@@ -363,7 +360,7 @@ fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
           for (int m = 0; m < M; ++m) cmax = std::max(cmax, fabs(p->coef6[(size_t)m * FQ_M6_TERMS + q]));
           wsum += cmax / p->h * sqrt(nrm[q - 2]);
         }
-        fq_finish_bounds(p, p->e_min - wsum, p->e_max + wsum);
+        if ((st = fq_finish_bounds(p, p->e_min - wsum, p->e_max + wsum)) != FQ_OK) return st;
       }
     }
   } else {
@@ -383,18 +380,26 @@ fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
     const bool need = prob->kernel == FQ_KERNEL_RESIDENT || p->precision == FQ_DF32;
     if (need && !ok) {
       fq_set_error("dense resident kernel (and dense FQ_DF32) needs N <= 128 and L <= 128 (N = %d, L = %d)", n, p->L);
-      free_plan(p);
       return FQ_EUNSUPPORTED;
     }
     if (p->precision == FQ_DF32 && prob->kernel != FQ_KERNEL_AUTO && prob->kernel != FQ_KERNEL_RESIDENT) {
       fq_set_error("dense FQ_DF32 runs on the resident kernel only");
-      free_plan(p);
       return FQ_EUNSUPPORTED;
     }
     p->dense_resident = ok && (prob->kernel == FQ_KERNEL_AUTO || prob->kernel == FQ_KERNEL_RESIDENT);
   }
-  *out = p;
+  *out = own.release();
   return FQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
+  if (!out) { fq_set_error("plan pointer is NULL"); return FQ_EINVAL; }
+  *out = nullptr;
+  return fq_guard("floquet_plan_create", [&] { return plan_create(out, prob); });
 }
 
 void floquet_plan_destroy(fq_plan* p) {
@@ -421,13 +426,15 @@ fq_status floquet_plan_get_info(const fq_plan* p, fq_plan_info* info) {
 }
 
 fq_status floquet_plan_inspect(const fq_problem* prob, fq_plan_info* info, double* coeffs, int32_t cap) {
-  fq_plan p;
-  fq_status st = fq_host_plan(prob, &p);
-  if (st != FQ_OK) return st;
-  st = floquet_plan_get_info(&p, info);
-  if (coeffs)
-    for (int l = 0; l <= p.L && l < cap; ++l) coeffs[l] = p.cheb[l];
-  return st;
+  return fq_guard("floquet_plan_inspect", [&] {
+    fq_plan p;
+    fq_status st = fq_host_plan(prob, &p);
+    if (st != FQ_OK) return st;
+    st = floquet_plan_get_info(&p, info);
+    if (coeffs)
+      for (int l = 0; l <= p.L && l < cap; ++l) coeffs[l] = p.cheb[l];
+    return st;
+  });
 }
 
 size_t floquet_workspace_size(const fq_plan* p, int32_t ncols) {
@@ -473,7 +480,7 @@ fq_status floquet_unitarity_defect(const void* d_U, int32_t n, const int32_t* d_
   if (!d_ws || ws_bytes < need) { fq_set_error("defect workspace too small (%zu < %zu)", ws_bytes, need); return FQ_EINVAL; }
   cudaStream_t s = (cudaStream_t)stream;
   fq_launch_defect((const double*)d_U, n, d_cols, rows, (double*)d_ws, s);
-  std::vector<double> h(2 * (size_t)chunks * nb);
+  std::vector<double> h(2 * (size_t)chunks * nb, 0.0);  // at most 2 * 16 * N / 256 doubles: N ~ 10^4 is 2.5 KB
   cudaError_t e = cudaMemcpyAsync(h.data(), d_ws, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fq_cuda_fail(e, "defect");

@@ -26,8 +26,8 @@ extern "C" size_t floquet_batch_workspace_size(fq_plan* const* plans, int32_t co
   return tot;
 }
 
-extern "C" fq_status floquet_batch_create(fq_batch** out, fq_plan* const* plans, int32_t count, void* const* d_U,
-                                          void* d_ws, size_t ws_bytes, int32_t lanes) {
+static fq_status floquet_batch_create_body(fq_batch** out, fq_plan* const* plans, int32_t count, void* const* d_U,
+                                           void* d_ws, size_t ws_bytes, int32_t lanes) {
   if (!out || !plans || !d_U || count < 1 || lanes < 1 || lanes > 32) {
     fq_set_error("floquet_batch_create: bad arguments");
     return FQ_EINVAL;
@@ -104,6 +104,13 @@ extern "C" fq_status floquet_batch_create(fq_batch** out, fq_plan* const* plans,
   }
   *out = b;
   return FQ_OK;
+}
+
+extern "C" fq_status floquet_batch_create(fq_batch** out, fq_plan* const* plans, int32_t count, void* const* d_U,
+                                          void* d_ws, size_t ws_bytes, int32_t lanes) {
+  return fq_guard("floquet_batch_create", [&] {
+    return floquet_batch_create_body(out, plans, count, d_U, d_ws, ws_bytes, lanes);
+  });
 }
 
 extern "C" fq_status floquet_batch_launch(fq_batch* b, void* stream) {

@@ -247,7 +247,7 @@ fq_status fq_split_propagate(fq_plan* p, const double* x0, double* x, int nc, in
 }
 
 // Times each tile width on two steps of the identity block and keeps the fastest.
-extern "C" fq_status floquet_autotune(fq_plan* p, void* ws, size_t bytes, void* stream, int32_t* tile_n) {
+static fq_status floquet_autotune_body(fq_plan* p, void* ws, size_t bytes, void* stream, int32_t* tile_n) {
   if (!p) {
     fq_set_error("floquet_autotune: NULL plan");
     return FQ_EINVAL;
@@ -265,21 +265,23 @@ extern "C" fq_status floquet_autotune(fq_plan* p, void* ws, size_t bytes, void* 
   const int cand[2] = {64, 128};
   float best = 1e30f;
   int pick = 64;
-  cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
+  const int before = p->tile_n;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  fq_status st = e == cudaSuccess ? FQ_OK : fq_cuda_fail(e, "autotune events");
   for (int c : cand) {
+    if (st != FQ_OK) break;
     p->tile_n = c;
-    fq_status st = fq_split_propagate(p, nullptr, nullptr, p->n, 0, steps, 1, 0, ws, s);  // warm-up
+    st = fq_split_propagate(p, nullptr, nullptr, p->n, 0, steps, 1, 0, ws, s);  // warm-up
     if (st != FQ_OK) break;
     cudaEventRecord(a, s);
-    fq_split_propagate(p, nullptr, nullptr, p->n, 0, steps, 1, 0, ws, s);
+    st = fq_split_propagate(p, nullptr, nullptr, p->n, 0, steps, 1, 0, ws, s);
+    if (st != FQ_OK) break;
     cudaEventRecord(b, s);
-    cudaError_t e = cudaEventSynchronize(b);
-    if (e != cudaSuccess) {
-      cudaEventDestroy(a);
-      cudaEventDestroy(b);
-      return fq_cuda_fail(e, "autotune");
+    if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
+      st = fq_cuda_fail(e, "autotune");
+      break;
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, a, b);
@@ -288,9 +290,17 @@ extern "C" fq_status floquet_autotune(fq_plan* p, void* ws, size_t bytes, void* 
       pick = c;
     }
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (st != FQ_OK) {  // the plan keeps the width it had
+    p->tile_n = before;
+    return st;
+  }
   p->tile_n = pick;
   if (tile_n) *tile_n = pick;
   return FQ_OK;
+}
+
+extern "C" fq_status floquet_autotune(fq_plan* p, void* ws, size_t bytes, void* stream, int32_t* tile_n) {
+  return fq_guard("floquet_autotune", [&] { return floquet_autotune_body(p, ws, bytes, stream, tile_n); });
 }

@@ -9,7 +9,9 @@
 #include <vector>
 
 #include <atomic>
+#include <exception>
 #include <functional>
+#include <new>
 
 #include "floquet.h"
 
@@ -70,10 +72,31 @@ struct fq_plan {
 void fq_set_error(const char* fmt, ...);
 fq_status fq_cuda_fail(cudaError_t e, const char* what);
 
+// Runs an entry point's body so that no C++ exception unwinds through the C ABI: a failed host
+// allocation becomes FQ_ENOMEM, any other exception FQ_EINVAL, each with a message.
+template <class F>
+fq_status fq_guard(const char* where, F&& body) noexcept {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    fq_set_error("%s: host allocation failed", where);
+    return FQ_ENOMEM;
+  } catch (const std::exception& e) {
+    fq_set_error("%s: %s", where, e.what());
+    return FQ_EINVAL;
+  } catch (...) {
+    fq_set_error("%s: unexpected host exception", where);
+    return FQ_EINVAL;
+  }
+}
+
 // ---------------------------------------------------------------- host planning (plan.cpp)
 double fq_drive_f(int deriv, double f_dc, double f_ac, double omega, double phi0, double t);
 void fq_bessel_miller(double R, int L, double* out);    // J_0..J_L
-int fq_cheb_order(double R, double tol);
+int fq_cheb_order(double R, double tol);  // needs 0 <= R <= FQ_R_MAX
+// largest R = h Delta E a plan accepts: about R + 300 Chebyshev products per step; beyond it a
+// step is too long for its spectral width and more steps per period are the remedy
+constexpr double FQ_R_MAX = 16384.0;
 void fq_tridiag_extremes(const double* diag, const double* off, int n, double* lo, double* hi);
 // y = A x for the operator whose extreme eigenvalues are wanted (host vectors of length n)
 using fq_matvec = std::function<void(const double* x, double* y)>;
@@ -87,12 +110,13 @@ void fq_dense_bounds(int n, double glo, double ghi, double kmax, const fq_dense_
 // them) are left pending for the caller (see fq_plan::dense_bounds_pending)
 fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_bounds = false);
 // margins of computed bounds, then fq_finish_bounds
-void fq_finish_computed_bounds(fq_plan* plan, double emin, double emax);
+fq_status fq_finish_computed_bounds(fq_plan* plan, double emin, double emax);
 // y = (H0 + g H1) x (which 0), H0 x (1) or H1 x (2) for dense device H0, H1 (kernels.cu)
 void fq_launch_symv2(const double* h0, const double* h1, double g, int which, const double* x, double* y, int n,
                      cudaStream_t s);
-// beta, Delta E, R, L, a_l, phase and the Omega~ scalars from bounds [emin, emax] of Omega/h
-void fq_finish_bounds(fq_plan* plan, double emin, double emax);
+// beta, Delta E, R, L, a_l, phase and the Omega~ scalars from bounds [emin, emax] of Omega/h;
+// FQ_EINVAL unless emin < emax are finite, FQ_EUNSUPPORTED if R = h Delta E > FQ_R_MAX
+fq_status fq_finish_bounds(fq_plan* plan, double emin, double emax);
 constexpr int FQ_M6_TERMS = 11;
 
 // ---------------------------------------------------------------- kernels (kernels.cu)

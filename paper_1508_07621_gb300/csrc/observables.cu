@@ -89,9 +89,9 @@ extern "C" size_t floquet_observable_workspace_size(const fq_plan* p, int32_t nc
   return up256((size_t)ncols * p->n * 16) + up256((size_t)ncols * 8) + floquet_workspace_size(p, ncols);
 }
 
-extern "C" fq_status floquet_average_observable(fq_plan* p, const void* d_X0, int32_t ncols, double a0, double a1,
-                                                double s_drive, double* d_avg, void* d_ws, size_t ws_bytes,
-                                                void* stream) {
+static fq_status floquet_average_observable_body(fq_plan* p, const void* d_X0, int32_t ncols, double a0, double a1,
+                                                 double s_drive, double* d_avg, void* d_ws, size_t ws_bytes,
+                                                 void* stream) {
   if (!p || !d_X0 || !d_avg || ncols < 1) {
     fq_set_error("floquet_average_observable: bad arguments");
     return FQ_EINVAL;
@@ -150,4 +150,12 @@ extern "C" fq_status floquet_average_observable(fq_plan* p, const void* d_X0, in
   k_scale_out<<<(ncols + 255) / 256, 256, 0, s>>>(acc, ncols, 1.0 / p->period, d_avg);
   e = cudaGetLastError();
   return e == cudaSuccess ? FQ_OK : fq_cuda_fail(e, "observable kernels");
+}
+
+extern "C" fq_status floquet_average_observable(fq_plan* p, const void* d_X0, int32_t ncols, double a0, double a1,
+                                                double s_drive, double* d_avg, void* d_ws, size_t ws_bytes,
+                                                void* stream) {
+  return fq_guard("floquet_average_observable", [&] {
+    return floquet_average_observable_body(p, d_X0, ncols, a0, a1, s_drive, d_avg, d_ws, ws_bytes, stream);
+  });
 }

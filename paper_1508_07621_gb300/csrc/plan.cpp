@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <thread>
 #include <vector>
 
@@ -76,13 +77,14 @@ void fq_bessel_miller(double R, int L, double* out) {
 }
 
 // Truncation order (reading R5): smallest integer l > R, l >= 1, with |J_{l+1}(R)| < tol.
+// J_l(R) falls faster than geometrically once l - R exceeds a few R^{1/3}, so the search ends
+// within a few hundred indices of R (it stops at R + 4096 whatever tol is).
 int fq_cheb_order(double R, double tol) {
-  int l = std::max(1, (int)floor(R) + 1);
-  for (;;) {
+  const int l0 = std::max(1, (int)floor(R) + 1);
+  for (int l = l0;; ++l) {
     std::vector<double> j(l + 2);
     fq_bessel_miller(R, l + 1, j.data());
-    if (fabs(j[l + 1]) < tol || l > 100000) return l;
-    ++l;
+    if (fabs(j[l + 1]) < tol || l >= l0 + 4096) return l;
   }
 }
 
@@ -336,12 +338,23 @@ static void magnus6_coefficients(double h, double f1, double f2, double f3, doub
   }
 }
 
-void fq_finish_bounds(fq_plan* plan, double emin, double emax) {
+fq_status fq_finish_bounds(fq_plan* plan, double emin, double emax) {
   const double h = plan->h;
   const int M = plan->steps;
+  if (!(std::isfinite(emin) && std::isfinite(emax) && emin < emax)) {
+    fq_set_error("spectral bounds [%g, %g] of Omega/h are not a finite interval", emin, emax);
+    return FQ_EINVAL;
+  }
+  const double half = 0.5 * emax - 0.5 * emin;  // Delta E, without overflow for bounds near DBL_MAX
+  const double r = h * half;
+  if (!(r <= FQ_R_MAX)) {
+    fq_set_error("R = h Delta E = %g is above %g: the step is too long for the spectral width (use more steps)", r,
+                 FQ_R_MAX);
+    return FQ_EUNSUPPORTED;
+  }
   plan->e_min = emin;
   plan->e_max = emax;
-  plan->delta_e = 0.5 * (emax - emin);
+  plan->delta_e = half;
   plan->beta = plan->delta_e + emin;
   plan->R = h * plan->delta_e;
   plan->L = plan->cheb_terms > 0 ? std::max(plan->cheb_terms, fq_cheb_order(plan->R, 1.0)) : fq_cheb_order(plan->R, plan->tol);
@@ -361,6 +374,7 @@ void fq_finish_bounds(fq_plan* plan, double emin, double emax) {
     plan->sc[m] = plan->mc[m] * inv;
   }
   plan->sbeta = plan->beta / plan->delta_e;
+  return FQ_OK;
 }
 
 // Host part of plan creation: validates the problem, forms the Magnus scalars (reading R1),
@@ -384,7 +398,7 @@ void fq_dense_bounds(int n, double glo, double ghi, double kmax, const fq_dense_
 }
 
 // The margins fq_host_plan adds to computed bounds, then the Chebyshev data (fq_finish_bounds).
-void fq_finish_computed_bounds(fq_plan* plan, double emin, double emax) {
+fq_status fq_finish_computed_bounds(fq_plan* plan, double emin, double emax) {
   const double margin = 1e-12 * std::max(std::max(fabs(emin), fabs(emax)), 1.0);
   emin -= margin;
   emax += margin;
@@ -393,13 +407,13 @@ void fq_finish_computed_bounds(fq_plan* plan, double emin, double emax) {
     emin -= w;
     emax += w;
   }
-  fq_finish_bounds(plan, emin, emax);
+  return fq_finish_bounds(plan, emin, emax);
 }
 
 fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_bounds) {
   if (!p) { fq_set_error("problem is NULL"); return FQ_EINVAL; }
-  if (p->n < 1 || p->steps < 1 || !(p->period > 0)) {
-    fq_set_error("need n >= 1, steps >= 1, period > 0 (got %d, %d, %g)", p->n, p->steps, p->period);
+  if (p->n < 1 || p->steps < 1 || !(p->period > 0) || !std::isfinite(p->period)) {
+    fq_set_error("need n >= 1, steps >= 1, finite period > 0 (got %d, %d, %g)", p->n, p->steps, p->period);
     return FQ_EINVAL;
   }
   if (p->format != FQ_DENSE && p->format != FQ_TRIDIAG) { fq_set_error("bad format %d", p->format); return FQ_EINVAL; }
@@ -412,6 +426,30 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_boun
     return FQ_EINVAL;
   }
   if (p->drive_kind == FQ_DRIVE_PIECEWISE && !p->f_steps) { fq_set_error("piecewise drive needs f_steps"); return FQ_EINVAL; }
+  if (p->drive_kind == FQ_DRIVE_COS &&
+      !(std::isfinite(p->f_dc) && std::isfinite(p->f_ac) && std::isfinite(p->omega) && std::isfinite(p->phi0))) {
+    fq_set_error("drive parameters must be finite (f_dc %g, f_ac %g, omega %g, phi0 %g)", p->f_dc, p->f_ac, p->omega,
+                 p->phi0);
+    return FQ_EINVAL;
+  }
+  if (p->e_max > p->e_min && !(std::isfinite(p->e_min) && std::isfinite(p->e_max))) {
+    fq_set_error("caller's bounds [%g, %g] must be finite", p->e_min, p->e_max);
+    return FQ_EINVAL;
+  }
+  {  // every operator entry and drive sample finite: a NaN or Inf would reach the bounds and L
+    const size_t nop = p->format == FQ_DENSE ? (size_t)p->n * p->n : (size_t)p->n;
+    const struct { const double* a; size_t k; const char* what; } arrays[] = {
+        {p->h0, nop, "H0"},
+        {p->h1, nop, "H1"},
+        {p->format == FQ_TRIDIAG ? p->h0_off : nullptr, (size_t)p->n - 1, "the H0 off-diagonal"},
+        {p->drive_kind == FQ_DRIVE_PIECEWISE ? p->f_steps : nullptr, (size_t)p->steps, "f_steps"}};
+    for (const auto& x : arrays)
+      for (size_t i = 0; x.a && i < x.k; ++i)
+        if (!std::isfinite(x.a[i])) {
+          fq_set_error("%s has a non-finite entry at %zu", x.what, i);
+          return FQ_EINVAL;
+        }
+  }
   if (p->precision < FQ_FP64 || p->precision > FQ_OZAKI) { fq_set_error("bad precision %d", p->precision); return FQ_EINVAL; }
   if (p->format == FQ_TRIDIAG &&
       (p->precision == FQ_BF16X3 || p->precision == FQ_BF16X6 || p->precision == FQ_OZAKI)) {
@@ -442,6 +480,10 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_boun
     return FQ_EINVAL;
   }
   plan->tile_n = p->tile_n ? p->tile_n : 128;
+  if (p->kernel < FQ_KERNEL_AUTO || p->kernel > FQ_KERNEL_TILED) {
+    fq_set_error("kernel must be one of FQ_KERNEL_AUTO .. FQ_KERNEL_TILED (got %d)", p->kernel);
+    return FQ_EINVAL;
+  }
   plan->period = p->period;
   plan->tol = p->cheb_tol > 0 ? p->cheb_tol : 1e-14;
   if (p->cheb_terms < 0 || p->cheb_terms > 1024) {
@@ -539,7 +581,6 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_boun
     };
     fq_dense_bounds(n, glo, ghi, kmax, apply, &emin, &emax);
   }
-  if (p->e_max > p->e_min) fq_finish_bounds(plan, emin, emax);
-  else fq_finish_computed_bounds(plan, emin, emax);
-  return FQ_OK;
+  if (p->e_max > p->e_min) return fq_finish_bounds(plan, emin, emax);
+  return fq_finish_computed_bounds(plan, emin, emax);
 }

@@ -171,8 +171,8 @@ struct Schur {
 
 }  // namespace
 
-extern "C" fq_status floquet_quasienergies(const void* U, int32_t n, double period, double* eps_out,
-                                           void* states_out) {
+static fq_status floquet_quasienergies_body(const void* U, int32_t n, double period, double* eps_out,
+                                            void* states_out) {
   if (!U || !eps_out || n < 1 || !(period > 0)) {
     fq_set_error("floquet_quasienergies: needs U, eps_out, n >= 1 and period > 0");
     return FQ_EINVAL;
@@ -207,4 +207,11 @@ extern "C" fq_status floquet_quasienergies(const void* U, int32_t n, double peri
       for (int i = 0; i < n; ++i) out[(size_t)mu * n + i] = s.q(i, order[mu]);
   }
   return FQ_OK;
+}
+
+extern "C" fq_status floquet_quasienergies(const void* U, int32_t n, double period, double* eps_out,
+                                           void* states_out) {
+  return fq_guard("floquet_quasienergies", [&] {
+    return floquet_quasienergies_body(U, n, period, eps_out, states_out);
+  });
 }

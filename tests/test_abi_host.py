@@ -131,7 +131,7 @@ def test_fixed_chebyshev_terms(fq):
     ("steps0", "FQ_EINVAL"), ("period0", "FQ_EINVAL"), ("format9", "FQ_EINVAL"), ("drive9", "FQ_EINVAL"),
     ("piecewise_without_f", "FQ_EINVAL"), ("order5", "FQ_EINVAL"), ("order6_tridiag", "FQ_EUNSUPPORTED"),
     ("order6_piecewise", "FQ_EUNSUPPORTED"), ("tile96", "FQ_EINVAL"), ("dense_fp32", "FQ_EUNSUPPORTED"),
-    ("tridiag_ozaki", "FQ_EUNSUPPORTED")])
+    ("tridiag_ozaki", "FQ_EUNSUPPORTED"), ("kernel9", "FQ_EINVAL")])
 def test_problem_validation(fq, case, status):
     """Every rejected problem fails in host planning with its status and a message, before any
     device work."""
@@ -160,6 +160,8 @@ def test_problem_validation(fq, case, status):
         prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, precision=fq.FQ_BF16X3, tile_n=96, **kw)
     elif case == "dense_fp32":
         prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, precision=fq.FQ_FP32, **kw)
+    elif case == "kernel9":
+        prob, keep = fq.make_problem(n, fq.FQ_TRIDIAG, d, d, 1.0, 4, h0_off=np.ones(n - 1), kernel=9, **kw)
     else:
         prob, keep = fq.make_problem(n, fq.FQ_TRIDIAG, d, d, 1.0, 4, h0_off=np.ones(n - 1),
                                      precision=fq.FQ_OZAKI, **kw)
@@ -167,6 +169,68 @@ def test_problem_validation(fq, case, status):
         fq.floquet_plan_inspect(prob)
     assert e.value.status == getattr(fq, status)
     assert fq.floquet_last_error()
+
+
+NAN, INF = float("nan"), float("inf")
+
+
+@pytest.mark.parametrize("case,status", [
+    ("f_ac_nan", "FQ_EINVAL"), ("omega_inf", "FQ_EINVAL"), ("phi0_nan", "FQ_EINVAL"), ("period_inf", "FQ_EINVAL"),
+    ("h0_nan_dense", "FQ_EINVAL"), ("h1_inf_dense", "FQ_EINVAL"), ("h0_nan_tridiag", "FQ_EINVAL"),
+    ("h0_off_inf", "FQ_EINVAL"), ("f_steps_nan", "FQ_EINVAL"), ("user_bounds_inf", "FQ_EINVAL"),
+    ("overflowing_bounds", "FQ_EUNSUPPORTED"), ("R_above_cap", "FQ_EUNSUPPORTED")])
+def test_non_finite_and_oversized_problems(fq, case, status):
+    """A NaN or Inf anywhere in the problem, bounds that overflow, or an R = h Delta E beyond what
+    any step can hold (about R + 300 products) are rejected in host planning with a message;
+    none of them may hang the search for L or abort the process."""
+    n = 8
+    g = fi.goe(n, 5)
+    d = np.arange(n, dtype=float)
+    off = np.ones(n - 1)
+    kw = dict(f_ac=1.0, omega=1.0)
+    bad = lambda a, v: np.where(np.arange(a.size).reshape(a.shape) == a.size // 2, v, a)
+    make = {
+        "f_ac_nan": lambda: fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, f_ac=NAN, omega=1.0),
+        "omega_inf": lambda: fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, f_ac=1.0, omega=INF),
+        "phi0_nan": lambda: fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, phi0=NAN, **kw),
+        "period_inf": lambda: fq.make_problem(n, fq.FQ_DENSE, g, g, INF, 4, **kw),
+        "h0_nan_dense": lambda: fq.make_problem(n, fq.FQ_DENSE, bad(g, NAN), g, 1.0, 4, **kw),
+        "h1_inf_dense": lambda: fq.make_problem(n, fq.FQ_DENSE, g, bad(g, INF), 1.0, 4, **kw),
+        "h0_nan_tridiag": lambda: fq.make_problem(n, fq.FQ_TRIDIAG, bad(d, NAN), d, 1.0, 4, h0_off=off, **kw),
+        "h0_off_inf": lambda: fq.make_problem(n, fq.FQ_TRIDIAG, d, d, 1.0, 4, h0_off=bad(off, INF), **kw),
+        "f_steps_nan": lambda: fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, drive_kind=fq.FQ_DRIVE_PIECEWISE,
+                                               f_steps=np.array([1.0, NAN, 1.0, 1.0])),
+        "user_bounds_inf": lambda: fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, e_min=-1.0, e_max=INF, **kw),
+        "overflowing_bounds": lambda: fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, e_min=-1.7e308, e_max=1.7e308,
+                                                      **kw),
+        "R_above_cap": lambda: fq.make_problem(n, fq.FQ_DENSE, g * 1e6, g, 1.0, 1, **kw),
+    }
+    prob, keep = make[case]()
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_plan_inspect(prob)
+    assert e.value.status == getattr(fq, status)
+    assert fq.floquet_last_error()
+
+
+def test_largest_accepted_R(fq):
+    """Just below the cap the plan is accepted, with L = the smallest l > R whose next Bessel
+    weight is below the tolerance (scipy's J_l as the check)."""
+    from scipy.special import jv
+    prob, keep = fq.make_problem(2, fq.FQ_DENSE, np.eye(2), np.zeros((2, 2)), 1.0, 1, f_ac=1.0, omega=1.0,
+                                 e_min=-16000.0, e_max=16000.0)
+    info, a = fq.floquet_plan_inspect(prob, cap=20000)
+    assert info.R == pytest.approx(16000.0) and info.L > 16000
+    assert abs(jv(info.L + 1, info.R)) < 1e-14 and abs(jv(info.L, info.R)) >= 1e-14
+
+
+def test_plan_create_rejects_before_device_work(fq):
+    """An invalid problem fails in floquet_plan_create's host planning with the same status as in
+    floquet_plan_inspect, without needing a device, and leaves no plan behind."""
+    g = fi.goe(4, 5)
+    prob, keep = fq.make_problem(4, fq.FQ_DENSE, g, g, 1.0, 4, f_ac=NAN, omega=1.0)
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_plan_create(prob)
+    assert e.value.status == fq.FQ_EINVAL and "finite" in fq.floquet_last_error()
 
 
 def _built_spectrum(n, seed, theta):
