@@ -82,8 +82,9 @@ for _name, (_res, _args) in _SIGS.items():
 
 
 class FloquetError(RuntimeError):
-    def __init__(self, status: int, where: str):
-        msg = lib.floquet_last_error().decode(errors="replace")
+    def __init__(self, status: int, where: str, msg: str | None = None):
+        if msg is None:
+            msg = lib.floquet_last_error().decode(errors="replace")
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
         self.status = status
 
@@ -93,9 +94,41 @@ def _check(status: int, where: str):
         raise FloquetError(status, where)
 
 
-def _ptr(t):
-    """Device pointer of a tensor (None -> NULL)."""
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+def _dev(t, dtype, count: int, what: str, where: str):
+    """Device pointer of `t` once it is known to be a contiguous CUDA tensor on the current
+    device, of `dtype` (None: any) and with at least `count` elements; None -> NULL.  The library
+    takes raw device pointers on trust, so a host, strided, mistyped or short tensor is refused
+    here with FQ_EINVAL instead of reaching a kernel."""
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise FloquetError(FQ_EINVAL, where, f"{what} must be a CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise FloquetError(FQ_EINVAL, where, f"{what} is on {t.device}, the current device is "
+                           f"cuda:{torch.cuda.current_device()}")
+    if not t.is_contiguous():
+        raise FloquetError(FQ_EINVAL, where, f"{what} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise FloquetError(FQ_EINVAL, where, f"{what} must be {dtype} (got {t.dtype})")
+    if t.numel() < count:
+        raise FloquetError(FQ_EINVAL, where, f"{what} has {t.numel()} elements, the call needs {count}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _ws(ws, where: str):
+    """(pointer, bytes) of a workspace tensor (any dtype; its size is checked by the library)."""
+    return _dev(ws, None, 0, "workspace", where), (ws.numel() * ws.element_size() if ws is not None else 0)
+
+
+def _c128():
+    import torch
+    return torch.complex128
+
+
+def _f64():
+    import torch
+    return torch.float64
 
 
 def _stream(stream):
@@ -122,6 +155,12 @@ def make_problem(n, fmt, h0, h1, period, steps, h0_off=None, drive_kind=FQ_DRIVE
     a1, p1 = _darr(h1)
     ao, po = _darr(h0_off)
     af, pf = _darr(f_steps)
+    # the library reads these host arrays to the sizes the problem implies
+    nop = n * n if fmt == FQ_DENSE else n if fmt == FQ_TRIDIAG else 0
+    for arr, need, what in ((a0, nop, "h0"), (a1, nop, "h1"), (ao, n - 1 if fmt == FQ_TRIDIAG else 0, "h0_off"),
+                            (af, steps if drive_kind == FQ_DRIVE_PIECEWISE else 0, "f_steps")):
+        if arr is not None and arr.size < need:
+            raise ValueError(f"make_problem: {what} has {arr.size} values, the problem needs {need}")
     prob = fq_problem(n, fmt, p0, po, p1, period, steps, drive_kind, f_dc, f_ac, omega, phi0, pf, cheb_tol,
                       e_min, e_max, precision, checkpoint_stride, kernel, tile_n, magnus_order, cheb_terms)
     return prob, (a0, a1, ao, af)
@@ -157,14 +196,20 @@ def floquet_workspace_size(plan: int, ncols: int) -> int:
 
 
 def floquet_build_UT(plan: int, U, ws, stream=None) -> None:
-    _check(lib.floquet_build_UT(_vp(plan), _ptr(U), _ptr(ws), ws.numel() * ws.element_size() if ws is not None else 0,
-                                _stream(stream)), "floquet_build_UT")
+    w = "floquet_build_UT"
+    n = floquet_plan_get_info(plan).n
+    pu = _dev(U, _c128(), n * n, "U", w)
+    pw, nb = _ws(ws, w)
+    _check(lib.floquet_build_UT(_vp(plan), pu, pw, nb, _stream(stream)), w)
 
 
 def floquet_propagate(plan: int, X0, X, ncols: int, m_begin: int, m_end: int, ws, stream=None) -> None:
-    _check(lib.floquet_propagate(_vp(plan), _ptr(X0), _ptr(X), ncols, m_begin, m_end, _ptr(ws),
-                                 ws.numel() * ws.element_size() if ws is not None else 0, _stream(stream)),
-           "floquet_propagate")
+    w = "floquet_propagate"
+    n = floquet_plan_get_info(plan).n
+    need = max(int(ncols), 0) * n
+    px0, px = _dev(X0, _c128(), need, "X0", w), _dev(X, _c128(), need, "X", w)
+    pw, nb = _ws(ws, w)
+    _check(lib.floquet_propagate(_vp(plan), px0, px, ncols, m_begin, m_end, pw, nb, _stream(stream)), w)
 
 
 def floquet_defect_workspace_size(n: int) -> int:
@@ -172,10 +217,13 @@ def floquet_defect_workspace_size(n: int) -> int:
 
 
 def floquet_unitarity_defect(U, n: int, cols, k: int, ws, stream=None):
+    import torch
+    w = "floquet_unitarity_defect"
     mx, fro = ctypes.c_double(), ctypes.c_double()
-    _check(lib.floquet_unitarity_defect(_ptr(U), n, _ptr(cols), k, _ptr(ws), ws.numel() * ws.element_size(),
-                                        _stream(stream), ctypes.byref(mx), ctypes.byref(fro)),
-           "floquet_unitarity_defect")
+    pu = _dev(U, _c128(), max(int(n), 0) ** 2, "U", w)
+    pc = _dev(cols, torch.int32, max(int(k), 0), "cols", w)
+    pw, nb = _ws(ws, w)
+    _check(lib.floquet_unitarity_defect(pu, n, pc, k, pw, nb, _stream(stream), ctypes.byref(mx), ctypes.byref(fro)), w)
     return mx.value, fro.value
 
 
@@ -184,14 +232,19 @@ def floquet_grad_workspace_size(plan: int) -> int:
 
 
 def floquet_grad(plan: int, f, W, loss, grad, ws, stream=None) -> None:
-    _check(lib.floquet_grad(_vp(plan), _ptr(f), _ptr(W), _ptr(loss), _ptr(grad), _ptr(ws),
-                            ws.numel() * ws.element_size() if ws is not None else 0, _stream(stream)),
-           "floquet_grad")
+    w = "floquet_grad"
+    info = floquet_plan_get_info(plan)
+    pf, pW = _dev(f, _f64(), info.steps, "f", w), _dev(W, _c128(), info.n * info.n, "W", w)
+    pl, pg = _dev(loss, _f64(), 1, "loss", w), _dev(grad, _f64(), info.steps, "grad", w)
+    pw, nb = _ws(ws, w)
+    _check(lib.floquet_grad(_vp(plan), pf, pW, pl, pg, pw, nb, _stream(stream)), w)
 
 
 def floquet_build_UT_static(problem, U, stream=None) -> None:
     """No-allocation U_T (resident FP32 tridiagonal chain, static device scratch); see floquet.h."""
-    _check(lib.floquet_build_UT_static(ctypes.byref(problem), _ptr(U), _stream(stream)), "floquet_build_UT_static")
+    w = "floquet_build_UT_static"
+    _check(lib.floquet_build_UT_static(ctypes.byref(problem), _dev(U, _c128(), max(problem.n, 0) ** 2, "U", w),
+                                       _stream(stream)), w)
 
 
 def floquet_batch_workspace_size(plans) -> int:
@@ -201,11 +254,15 @@ def floquet_batch_workspace_size(plans) -> int:
 
 def floquet_batch_create(plans, outputs, ws, lanes: int = 8) -> int:
     """One CUDA graph for the U_T builds of all plans; outputs[i]: N_i x N_i complex128 tensors."""
+    w = "floquet_batch_create"
+    if len(outputs) != len(plans):
+        raise FloquetError(FQ_EINVAL, w, f"{len(plans)} plans but {len(outputs)} outputs")
     arr = (_vp * len(plans))(*plans)
-    outs = (_vp * len(outputs))(*[o.data_ptr() for o in outputs])
+    outs = (_vp * len(outputs))(*[_dev(o, _c128(), floquet_plan_get_info(p).n ** 2, f"outputs[{i}]", w)
+                                  for i, (p, o) in enumerate(zip(plans, outputs))])
     b = _vp()
-    _check(lib.floquet_batch_create(ctypes.byref(b), arr, len(plans), outs, _ptr(ws), ws.numel() * ws.element_size(),
-                                    lanes), "floquet_batch_create")
+    pw, nb = _ws(ws, w)
+    _check(lib.floquet_batch_create(ctypes.byref(b), arr, len(plans), outs, pw, nb, lanes), w)
     return b.value
 
 
@@ -219,8 +276,8 @@ def floquet_batch_destroy(batch: int) -> None:
 
 def floquet_autotune(plan: int, ws, stream=None) -> int:
     tile = _i32()
-    _check(lib.floquet_autotune(_vp(plan), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream),
-                                ctypes.byref(tile)), "floquet_autotune")
+    pw, nb = _ws(ws, "floquet_autotune")
+    _check(lib.floquet_autotune(_vp(plan), pw, nb, _stream(stream), ctypes.byref(tile)), "floquet_autotune")
     return tile.value
 
 
@@ -230,9 +287,12 @@ def floquet_observable_workspace_size(plan: int, ncols: int) -> int:
 
 def floquet_average_observable(plan: int, X0, ncols: int, a0: float, a1: float, s_drive: float, out, ws,
                                stream=None) -> None:
-    _check(lib.floquet_average_observable(_vp(plan), _ptr(X0), ncols, a0, a1, s_drive, _ptr(out), _ptr(ws),
-                                          ws.numel() * ws.element_size(), _stream(stream)),
-           "floquet_average_observable")
+    w = "floquet_average_observable"
+    n = floquet_plan_get_info(plan).n
+    px = _dev(X0, _c128(), max(int(ncols), 0) * n, "X0", w)
+    po = _dev(out, _f64(), max(int(ncols), 0), "out", w)
+    pw, nb = _ws(ws, w)
+    _check(lib.floquet_average_observable(_vp(plan), px, ncols, a0, a1, s_drive, po, pw, nb, _stream(stream)), w)
 
 
 def floquet_check_status(plan: int, stream=None) -> int:
@@ -244,6 +304,8 @@ def floquet_quasienergies(u, period: float, states: bool = True):
     the library's host Schur solver."""
     import numpy as np
     u = np.ascontiguousarray(u, dtype=np.complex128)
+    if u.ndim != 2 or u.shape[0] != u.shape[1]:
+        raise FloquetError(FQ_EINVAL, "floquet_quasienergies", f"U must be a square matrix (got shape {u.shape})")
     n = u.shape[0]
     eps = np.empty(n)
     out = np.empty((n, n), dtype=np.complex128) if states else None

@@ -49,7 +49,7 @@ fq_status scratch_address(void** out) {
 
 }  // namespace
 
-extern "C" fq_status floquet_build_UT_static(const fq_problem* prob, void* d_U, void* stream) {
+static fq_status build_static(const fq_problem* prob, void* d_U, void* stream) {
   if (!prob || !d_U) {
     fq_set_error("floquet_build_UT_static: NULL problem or output");
     return FQ_EINVAL;
@@ -126,4 +126,8 @@ extern "C" fq_status floquet_build_UT_static(const fq_problem* prob, void* d_U, 
     return FQ_EBOUND;
   }
   return FQ_OK;
+}
+
+extern "C" fq_status floquet_build_UT_static(const fq_problem* prob, void* d_U, void* stream) {
+  return fq_guard("floquet_build_UT_static", [&] { return build_static(prob, d_U, stream); });
 }

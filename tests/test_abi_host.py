@@ -290,3 +290,32 @@ def test_host_quasienergies_of_oracle_UT(fq):
     T = m.drive.period
     eps, _ = fq.floquet_quasienergies(u, T, states=False)
     assert np.max(np.abs(eps - o.quasienergies(u, T))) <= 1e-12
+
+
+def test_binding_refuses_bad_buffers(fq):
+    """The binding hands raw pointers to the library, so it refuses, with FQ_EINVAL and before any
+    call into it, a host tensor where device memory is expected, host arrays shorter than the
+    problem implies, and a non-square U_T for the host eigensolver."""
+    import torch
+    d = np.arange(6, dtype=float)
+    prob, keep = fq.make_problem(6, fq.FQ_TRIDIAG, d, d, 1.0, 4, h0_off=np.ones(5), f_ac=1.0, omega=1.0,
+                                 precision=fq.FQ_FP32)
+    host_u = torch.zeros((6, 6), dtype=torch.complex128)
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_build_UT_static(prob, host_u)
+    assert e.value.status == fq.FQ_EINVAL and "CUDA tensor" in str(e.value)
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_unitarity_defect(host_u, 6, None, 6, torch.zeros(256, dtype=torch.uint8))
+    assert e.value.status == fq.FQ_EINVAL and "CUDA tensor" in str(e.value)
+    g = fi.goe(8, 5)
+    for kw in (dict(h0=g[:7]), dict(h1=g.ravel()[:63]), dict(h0_off=np.ones(6), fmt=fq.FQ_TRIDIAG),
+               dict(f_steps=np.ones(3), drive_kind=fq.FQ_DRIVE_PIECEWISE)):
+        fmt = kw.pop("fmt", fq.FQ_DENSE)
+        args = dict(h0=np.diag(g) if fmt == fq.FQ_TRIDIAG else g, h1=np.diag(g) if fmt == fq.FQ_TRIDIAG else g)
+        args.update({k: v for k, v in kw.items() if k in ("h0", "h1")})
+        extra = {k: v for k, v in kw.items() if k not in ("h0", "h1")}
+        with pytest.raises(ValueError):
+            fq.make_problem(8, fmt, args["h0"], args["h1"], 1.0, 4, **extra)
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_quasienergies(np.eye(3, 4, dtype=complex), 1.0)
+    assert e.value.status == fq.FQ_EINVAL

@@ -50,7 +50,7 @@ def test_static_entry_rejects_oversize():
     import paper_1508_07621_gb300 as fq
     d = fi.config_dimer(nb=10000, steps=2000)     # 3 * 2000 * 10004 floats > 16 MiB
     prob, keep = _problem(fq, d)
-    U = torch.empty((1, 1), dtype=torch.complex128, device="cuda")
+    U = torch.empty((d.n, d.n), dtype=torch.complex128, device="cuda")
     with pytest.raises(fq.FloquetError) as e:
         fq.floquet_build_UT_static(prob, U)
-    assert e.value.status == fq.FQ_EINVAL
+    assert e.value.status == fq.FQ_EINVAL and "floquet_build_UT_static" in fq.floquet_last_error()
