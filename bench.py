@@ -395,10 +395,12 @@ def run_ours(args):
     achieved = flops / avg / 1e12
     peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     per_wave_step = (RES_NCU["read"] - RES_NCU["x0"]) / RES_NCU["steps"]
-    traffic = per_wave_step * (n / RES_NCU["states"]) * d.steps + 16.0 * n * n
+    traffic_before = per_wave_step * (n / RES_NCU["states"]) * d.steps + 16.0 * n * n
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_note": "bytes per launch, scaled from an ncu capture of 152 states "
-                "x 20 steps (per-step coefficient reads x waves x steps) plus the U_T write",
+                "traffic": None, "traffic_note": f"null: the kernel gained an L2 prefetch of the next step's "
+                f"coefficients after its last ncu capture; that capture (152 states x 20 steps) scales to "
+                f"{traffic_before:.3e} bytes per launch (per-step coefficient reads x waves x steps, plus the "
+                f"U_T write)",
                 "kernel": "k_tri_resident<256, 40>",
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)"}
     cpu = None
