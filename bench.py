@@ -51,18 +51,20 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["dimer", "dimer-paper", "goe4096", "adjoint", "paper-table1"],
+    ap.add_argument("--workload", choices=["dimer", "dimer-paper", "goe4096", "adjoint", "paper-table1", "batch"],
                     default="dimer",
                     help="dimer: nb = 10^4, J = 1, U nb = 2, f = 1.5 cos 3t, M = 2000 (default); "
                          "dimer-paper: the paper's parameters (U/2)(n1 - n2)^2, f = 2.7 + 2.5 cos 3t, M = 8000; "
                          "goe4096: dense GOE N = 4096 (seeds 3, 4), A = 2, omega = 2, M = 512, U_T builds/s; "
                          "adjoint: gate-fidelity gradient, GOE N = 1024 (seeds 6-9), M = 256, s = 16, grads/s; "
                          "paper-table1: the paper's timing run (GOE N = 4096 with unit-variance entries, "
-                         "f = cos(pi t), M = 100, L = 50, 6th order), compared with its Table 1 time")
+                         "f = cos(pi t), M = 100, L = 50, 6th order), compared with its Table 1 time; "
+                         "batch: a scan of 48 dense GOE instances (N ~ U{256..2048}, omega ~ U[0.5, 4], "
+                         "A ~ U[0.5, 3], M = 256) as one CUDA graph over 8 lanes, instances/s")
     ap.add_argument("--n", type=int, default=4096, choices=sorted(PAPER_TABLE1_CHEB_S),
                     help="paper-table1: the matrix size (the rows of the paper's Table 1)")
     ap.add_argument("--precision", choices=["x3", "x6", "ozaki", "fp64"], default=None,
-                    help="goe4096 / adjoint: BF16X3 (default), BF16X6, FQ_OZAKI (FP64 emulation) or FP64 "
+                    help="goe4096 / adjoint / batch: BF16X3 (default), BF16X6, FQ_OZAKI (FP64 emulation) or FP64 "
                          "(adjoint only)")
     ap.add_argument("--ncu-case", choices=["resident", "stream", "split", "tile", "adjoint", "ozaki", "dense-resident",
                              "ozaki-grad"],
@@ -623,6 +625,153 @@ def run_dense(args):
         dist.destroy_process_group()
 
 
+BATCH_STEPS, BATCH_LANES = 256, 8
+
+
+def batch_flops(insts, Ls):
+    """Useful flop of one scan: 8 N^3 per Chebyshev term (a complex N x N product as real
+    products), L terms per step, M steps per instance."""
+    return sum(8.0 * s.n ** 3 * L * BATCH_STEPS for s, L in zip(insts, Ls))
+
+
+def batch_oracle_sample(insts, states=None, steps=16):
+    """FP64 oracle on `states` basis states over `steps` steps of the scan's first instance,
+    scaled to the whole scan by each instance's share of N^3 L (the oracle's products are BLAS
+    GEMMs, so its time follows the flop count); returns (instances/s, seconds, description).
+    L_i for the scaling comes from the oracle's truncation rule at R_i = h_i (2 + 2 A_i): the
+    GOE matrices of the scan have spectral radius 2, so |H0 + f H1| <= 2 + 2 |A|."""
+    import math
+    import oracle as o
+    import floquet_inputs as fi
+    m0 = fi.scan_model(insts[0], BATCH_STEPS)
+    # the whole identity block of instance 0 by default: narrower blocks run the oracle's BLAS
+    # products below their speed and overstate its time
+    v0, dt, desc0, _ = dense_oracle_sample(m0, states=states or m0.n, steps=steps)
+    est = [o.chebyshev_order(2 * math.pi / s.omega / BATCH_STEPS * (2 + 2 * s.amplitude)) for s in insts]
+    scale = sum((s.n / m0.n) ** 3 * (est[i] / est[0]) for i, s in enumerate(insts))
+    t_scan = scale / v0  # seconds for the whole scan: v0 is instance 0's U_T/s
+    desc = (f"{desc0} of instance 0 (N = {m0.n}), scaled to the {len(insts)}-instance scan by sum (N_i / N_0)^3 "
+            f"(L_i / L_0) with L_i from R_i = h_i (2 + 2 A_i)")
+    return len(insts) / t_scan, dt, desc
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import floquet_inputs as fi
+    import paper_1508_07621_gb300 as fq
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = args.precision or "x3"
+    if prec == "fp64":
+        raise SystemExit("the scan's N = 2048 instances take minutes each in plain FP64; use x3, x6 or ozaki")
+    precision = getattr(fq, PREC_NAMES[prec])
+    insts = fi.batch_scan()
+    # weak scaling: rank r scans amplitudes shifted by 0.01 r (independent problems of the same cost)
+    models = [(fi.goe(s.n, s.seed_h0), fi.goe(s.n, s.seed_h1), s.omega, rank_drive_amplitude(s.amplitude, rank))
+              for s in insts]
+
+    def make_plans(tiles=None):
+        return [fq.Plan.dense(h0, h1, omega=om, f_ac=amp, steps=BATCH_STEPS, precision=precision,
+                              tile_n=tiles[i] if tiles else 0)
+                for i, (h0, h1, om, amp) in enumerate(models)]
+
+    stream = torch.cuda.current_stream()
+    plans = make_plans()
+    ws1 = fq.workspace(max(p.workspace_size() for p in plans))
+    tiles = [p.autotune(ws1) if prec != "ozaki" else 0 for p in plans]
+    del ws1
+    Ls = [p.info.L for p in plans]
+    outs = [torch.empty((p.n, p.n), dtype=torch.complex128, device="cuda") for p in plans]
+    handles = [p.handle for p in plans]
+    ws = fq.workspace(fq.floquet_batch_workspace_size(handles))
+    graph = fq.floquet_batch_create(handles, outs, ws, BATCH_LANES)
+    try:
+        for _ in range(max(args.warmup, 0)):
+            fq.floquet_batch_launch(graph, stream)
+        torch.cuda.synchronize()
+        if any(p.check_status() != fq.FQ_OK for p in plans):
+            raise RuntimeError("device check fired during warm-up")
+        per_step, total, clk = timed_loop(lambda: fq.floquet_batch_launch(graph, stream), args.steps, stream,
+                                          world, dist)
+    finally:
+        fq.floquet_batch_destroy(graph)
+    status_ok = all(p.check_status() == fq.FQ_OK for p in plans)
+    value, total = job_throughput(total, args.steps, dist if world > 1 else None, "cuda")
+    value *= len(plans)  # instances/s: each launch builds every instance's U_T
+    defect = max(fq.api.unitarity_defect(u, torch.arange(0, u.shape[0], max(1, u.shape[0] // 16),
+                                                         dtype=torch.int32, device="cuda")[:16])[0]
+                 for u in outs)
+    # end to end: every plan from host arrays, the graph, one launch, every U_T to pinned host
+    host = [torch.empty(tuple(u.shape), dtype=torch.complex128, pin_memory=True) for u in outs]
+    e2e_times = []
+    for _ in range(min(args.e2e_steps, 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p2 = make_plans(tiles)
+        g2 = fq.floquet_batch_create([p.handle for p in p2], outs, ws, BATCH_LANES)
+        fq.floquet_batch_launch(g2, stream)
+        for h, u in zip(host, outs):
+            h.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        fq.floquet_batch_destroy(g2)
+        for p in p2:
+            p.close()
+    e2e_value = world * len(plans) / statistics.median(e2e_times)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    useful = batch_flops(insts, Ls)
+    issued = useful * SLICE_PRODUCTS[prec]
+    avg = statistics.mean(per_step)
+    achieved = issued / avg / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
+                "frac": achieved / peaks["bf16_sustained"], "traffic": None,
+                "kernel": "k_oz_term" if prec == "ozaki" else "k_split_persist",
+                "useful_tflops": useful / avg / 1e12,
+                "note": (f"issued BF16 MMA flop = {SLICE_PRODUCTS[prec]} slice products x 8 N_i^3 L_i M summed over "
+                         f"the {len(plans)} instances, over one graph launch's CUDA-event time; peak: "
+                         f"{peaks['source']} sustained cuBLAS bf16")}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, dt, desc = batch_oracle_sample(insts)
+        cpu = {"value": v, "unit": "instances/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+    per_inst = [2 + BATCH_STEPS * (1 + (2 * L if prec == "ozaki" else L)) for L in Ls]
+    ns = [s.n for s in insts]
+    line = {"metric": f"instances/sec ({len(plans)}-instance dense GOE scan, N ~ U{{256..2048}}, M={BATCH_STEPS}, "
+                      "one CUDA graph)",
+            "value": value, "unit": "instances/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 slices, f64 states" if prec == "ozaki" else "bf16 slices, f32 accumulate",
+            "data": "synthetic",
+            "config": {"workload": (f"batched scan: {len(plans)} GOE instances (seeds 1000 + 2i, 1001 + 2i), "
+                                    f"N in [{min(ns)}, {max(ns)}], omega ~ U[0.5, 4], A ~ U[0.5, 3], M={BATCH_STEPS}, "
+                                    f"{PREC_NAMES[prec]}, {BATCH_LANES} graph lanes"),
+                       "instances": len(plans), "lanes": BATCH_LANES, "L_range": [min(Ls), max(Ls)],
+                       "tiles": tiles,
+                       "l2": "working set larger than L2 (operand slices and states of 48 instances, > 1 GB)",
+                       "parallelism": f"weak: {world} independent scans"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "instances/s",
+                    "h2d_bytes_per_step": sum(16 * n * n + 24 * BATCH_STEPS for n in ns),
+                    "d2h_bytes_per_step": sum(16 * n * n for n in ns)},
+            "gpu_launches": sum(per_inst) * args.steps, "clocks": clk, "device_status_ok": status_ok,
+            "accuracy": {"unitarity_defect_max": defect, "defect_columns_per_instance": 16},
+            "median_step_s": statistics.median(per_step), "per_step_s": per_step, "host": host_info()}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_adjoint(args):
     import numpy as np
     import torch
@@ -745,7 +894,18 @@ def run_reference_other(args):
         return
     import floquet_inputs as fi
     vals, desc = [], ""
-    if args.workload in ("goe4096", "paper-table1"):
+    if args.workload == "batch":
+        insts = fi.batch_scan()
+        for _ in range(args.warmup):
+            batch_oracle_sample(insts[:1], states=4, steps=1)
+        for _ in range(args.steps):
+            v, dt, desc = batch_oracle_sample(insts)
+            vals.append(v)
+        unit = "instances/s"
+        metric = (f"instances/sec ({len(insts)}-instance dense GOE scan, N ~ U{{256..2048}}, M={BATCH_STEPS}, "
+                  "one CUDA graph)")
+        cfg = f"batched scan: {len(insts)} GOE instances, M={BATCH_STEPS}"
+    elif args.workload in ("goe4096", "paper-table1"):
         paper = args.workload == "paper-table1"
         m = fi.config_goe_paper(args.n) if paper else fi.config_goe4096()
         terms = 50 if paper else 0
@@ -787,7 +947,7 @@ if __name__ == "__main__":
     if a.ncu_case:
         run_ncu_case(a.ncu_case)
     elif a.impl == "reference":
-        if a.workload in ("goe4096", "adjoint", "paper-table1"):
+        if a.workload in ("goe4096", "adjoint", "paper-table1", "batch"):
             run_reference_other(a)
         else:
             run_reference(a)
@@ -795,5 +955,7 @@ if __name__ == "__main__":
         run_dense(a)
     elif a.workload == "adjoint":
         run_adjoint(a)
+    elif a.workload == "batch":
+        run_batch(a)
     else:
         run_ours(a)
