@@ -152,10 +152,9 @@ def fidelity_loss(plan, f, W):
 
 def unitarity_defect(U, cols=None, stream=None):
     """(max |U^+U - 1|, Frobenius / sqrt(k)) over the listed columns (all if None)."""
-    import torch
     n = U.shape[0]
     k = n if cols is None else cols.numel()
-    ws = workspace(2 * 8 * ((k + 15) // 16) * ((n + 255) // 256) + 256)
+    ws = workspace(B.floquet_defect_workspace_size(n))  # sized for all n rows, so enough for any k <= n
     return B.floquet_unitarity_defect(U, n, cols, k, ws, stream)
 
 
