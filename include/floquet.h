@@ -152,12 +152,16 @@ typedef struct fq_plan_info {
 
 /* Host planning + upload (§3: Magnus scalars, [H0,H1] computed once, bounds, Bessel
  * coefficients; the set-up part of Algorithm 1).  Uses the current CUDA device; allocates the plan's
- * device copies.  On failure *plan is NULL. */
+ * device copies, which the plan owns until floquet_plan_destroy.  Synchronous.  On failure *plan is
+ * NULL and nothing stays allocated: FQ_EINVAL (invalid problem, see fq_problem), FQ_EUNSUPPORTED
+ * (a valid combination no kernel implements), FQ_ENOMEM (an allocation failed) or FQ_ECUDA. */
 fq_status floquet_plan_create(fq_plan** plan, const fq_problem* problem);
 
 /* Frees the plan and its device memory (synchronises the device first).  NULL is a no-op. */
 void floquet_plan_destroy(fq_plan* plan);
 
+/* Copies the plan's planning results (sizes, bounds, R, L) into the caller's *info.  Host only;
+ * FQ_EINVAL if either pointer is NULL. */
 fq_status floquet_plan_get_info(const fq_plan* plan, fq_plan_info* info);
 
 /* Host planning only (no device needed): fills *info as floquet_plan_create would and writes
@@ -165,18 +169,23 @@ fq_status floquet_plan_get_info(const fq_plan* plan, fq_plan_info* info);
 fq_status floquet_plan_inspect(const fq_problem* problem, fq_plan_info* info, double* coeffs,
                                int32_t cap);
 
-/* Bytes of workspace floquet_propagate / floquet_build_UT need for ncols states. */
+/* Bytes of workspace floquet_propagate / floquet_build_UT need for ncols states (0 for a NULL plan
+ * or ncols < 0).  Host only. */
 size_t floquet_workspace_size(const fq_plan* plan, int32_t ncols);
 
 /* U_T (the propagation part of Algorithm 1): propagates the N x N identity over all M steps and writes
- * d_U = N x N complex128, U[i][j] = <i|U_T|j>.  d_ws: floquet_workspace_size(plan, N) bytes,
- * 256-byte aligned.  Asynchronous on `stream`. */
+ * d_U = N x N complex128, U[i][j] = <i|U_T|j> (caller-owned device memory).  d_ws: caller-owned,
+ * floquet_workspace_size(plan, N) bytes, 256-byte aligned, else FQ_EINVAL before any work.
+ * Asynchronous on `stream`: FQ_ECUDA reports a failed launch; the numerical device checks are read
+ * by floquet_check_status. */
 fq_status floquet_build_UT(fq_plan* plan, void* d_U, void* d_ws, size_t ws_bytes, void* stream);
 
 /* Propagates a block of ncols states through steps m_begin .. m_end-1 (0-based), i.e.
  * X = U_{m_end} ... U_{m_begin+1} X0 (Eq. 9 restricted to those steps).  d_X0, d_X: ncols x N
- * complex128, row r = state r; d_X may equal d_X0.  Used for the second propagation round of
- * §3 (eigenvectors as initial states) and for resuming a chain. */
+ * complex128, row r = state r, caller-owned device memory; d_X may equal d_X0.  FQ_EINVAL for a
+ * NULL pointer, ncols < 0 or a range outside 0 <= m_begin <= m_end <= M; m_begin = m_end copies.
+ * d_ws as for floquet_build_UT with ncols states.  Asynchronous on `stream`.  Used for the second
+ * propagation round of §3 (eigenvectors as initial states) and for resuming a chain. */
 fq_status floquet_propagate(fq_plan* plan, const void* d_X0, void* d_X, int32_t ncols,
                             int32_t m_begin, int32_t m_end, void* d_ws, size_t ws_bytes,
                             void* stream);
@@ -210,7 +219,9 @@ fq_status floquet_grad(fq_plan* plan, const double* d_f, const void* d_W, double
  * and writes d_avg[r] = <A>_T = (1/T) int_0^T <psi_r(t)|A(t)|psi_r(t)> dt (Eq. 17) for
  * A(t) = a0 H0 + (a1 + s_drive f(t)) H1 (A = H(t): a0 = 1, a1 = 0, s_drive = 1), the integral by
  * composite Simpson over the step boundaries (trapezoid if M is odd).  Cosine-drive plans; dense
- * N <= 8192.  d_X0 is not modified.  d_ws: floquet_observable_workspace_size(plan, ncols). */
+ * N <= 8192 (else FQ_EUNSUPPORTED).  d_X0 is not modified; d_avg: ncols device doubles.  All
+ * buffers are caller-owned; d_ws: floquet_observable_workspace_size(plan, ncols) bytes, else
+ * FQ_EINVAL.  Asynchronous on `stream`. */
 size_t floquet_observable_workspace_size(const fq_plan* plan, int32_t ncols);
 fq_status floquet_average_observable(fq_plan* plan, const void* d_X0, int32_t ncols, double a0, double a1,
                                      double s_drive, double* d_avg, void* d_ws, size_t ws_bytes, void* stream);
@@ -274,7 +285,7 @@ fq_status floquet_selftest_wait(fq_plan* plan, int64_t cycles, void* stream);
  * Floquet state of eps_out[mu].  Complex Schur form by Householder reduction and shifted QR
  * (no LAPACK linked; O(N^3) on one core: about 5 s at N = 1000 for eps alone, 15 s with the
  * states); U_T is normal, so the Schur vectors are its eigenvectors.  FQ_EINVAL on bad
- * arguments or if the iteration does not converge.  Needs no device. */
+ * arguments or if the iteration does not converge.  Needs no device; every array is the caller's. */
 fq_status floquet_quasienergies(const void* U, int32_t n, double period, double* eps_out, void* states_out);
 
 /* Message of the last failing call on this thread ("" if none). */
