@@ -319,3 +319,15 @@ def test_binding_refuses_bad_buffers(fq):
     with pytest.raises(fq.FloquetError) as e:
         fq.floquet_quasienergies(np.eye(3, 4, dtype=complex), 1.0)
     assert e.value.status == fq.FQ_EINVAL
+
+
+def test_host_quasienergies_concurrent_calls(fq):
+    """Calls from several host threads at once (ctypes releases the GIL) each get their own
+    worker pool and return exactly what a lone call returns."""
+    import concurrent.futures as cf
+    us = [fi.haar_unitary(160, 900 + i) for i in range(4)]
+    alone = [fq.floquet_quasienergies(u, 1.0) for u in us]
+    with cf.ThreadPoolExecutor(4) as ex:
+        together = list(ex.map(lambda u: fq.floquet_quasienergies(u, 1.0), us))
+    for (e1, s1), (e2, s2) in zip(alone, together):
+        assert np.array_equal(e1, e2) and np.array_equal(s1, s2)
