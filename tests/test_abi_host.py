@@ -331,3 +331,22 @@ def test_host_quasienergies_concurrent_calls(fq):
         together = list(ex.map(lambda u: fq.floquet_quasienergies(u, 1.0), us))
     for (e1, s1), (e2, s2) in zip(alone, together):
         assert np.array_equal(e1, e2) and np.array_equal(s1, s2)
+
+
+def test_library_bessel_sweep_to_the_R_cap(fq):
+    """Across R = 1e-8 .. 16000 (up to the planning cap): the library's L equals the oracle's
+    truncation rule (smallest l > R with |J_{l+1}(R)| < 1e-14), and every weight a_l equals
+    scipy's (2 -) J_l(R) to 16 eps sqrt(L) absolute: Miller's recurrence is stable downward for
+    any R, and its rounding (like scipy's) accumulates as a random walk over the ~L steps (about
+    9 eps sqrt(L) seen at R = 16000)."""
+    from scipy.special import jv
+    n, h = 2, 1.0
+    for R in np.concatenate([np.logspace(-8, 4, 25), [12345.6, 16000.0]]):
+        prob, keep = fq.make_problem(n, fq.FQ_TRIDIAG, np.zeros(n), np.zeros(n), h, 1, h0_off=np.zeros(n - 1),
+                                     f_ac=0.0, omega=1.0, e_min=-R, e_max=R)
+        info, a = fq.floquet_plan_inspect(prob, cap=20000)
+        assert abs(info.R - R) <= 1e-15 * R
+        assert info.L == o.chebyshev_order(info.R), R
+        ref = jv(np.arange(info.L + 1), info.R)
+        ref[1:] *= 2
+        assert np.max(np.abs(a - ref)) <= 16 * 2.2e-16 * math.sqrt(info.L) + 1e-18, (R, np.max(np.abs(a - ref)))
