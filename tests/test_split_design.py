@@ -1,7 +1,8 @@
 """The arithmetic the split-precision paths (FQ_BF16X3, FQ_BF16X6; reading R10) rest on, checked
 on CPU: BF16 rounding to nearest even, the slice recurrence x_s = bf16(x - x_0 - ... - x_{s-1}),
 and the error of the sliced product with the pairs a + b < NS summed in FP32, against a bound
-derived from those two facts.  (The CUDA kernels are checked against the oracle by the GPU tests.)"""
+derived from those two facts; then the whole BF16X3 step chain on one instance of the batched
+scan.  (The CUDA kernels are checked against the oracle by the GPU tests.)"""
 import numpy as np
 import pytest
 
@@ -101,3 +102,63 @@ def test_sliced_product_error(ns, products):
         assert rel < 2.0 ** -18                 # FP32 level (k 2^-24 = 2^-16 is the worst case)
         three_only, _ = sliced_product(Om, X, 3, keep=[(0, 0), (0, 1), (1, 0)])
         assert np.max(np.abs(three_only - exact) / AB) > 8 * rel
+
+
+def _x3_real_product(P, X):
+    """P X for a real operator given as two BF16 slices (from FP64) and FP32 states X, sliced
+    in turn; the three pairs a + b < 2 summed in FP32."""
+    x0, x1 = slices(X, 2)
+    out = (P[1] @ x0).astype(np.float32)
+    out = (out + (P[0] @ x1).astype(np.float32)).astype(np.float32)
+    return (out + (P[0] @ x0).astype(np.float32)).astype(np.float32)
+
+
+def test_x3_chain_on_a_scan_instance():
+    """The whole BF16X3 step chain modelled on CPU for the batched scan's smallest instance
+    (N = 257, M = 256): operator slices from FP64, state slices from FP32 masters, the Chebyshev
+    recurrence, Bessel sum and phase in FP32 (Eqs. 10 and 12), against the FP64 oracle on three
+    basis states.  The model stays far inside the 1e-5 target of the split paths (7e-7 seen)."""
+    import floquet_inputs as fi
+    import oracle as o
+    insts = fi.batch_scan()
+    s = min(insts, key=lambda t: t.n)
+    h0, h1 = fi.goe(s.n, s.seed_h0), fi.goe(s.n, s.seed_h1)
+    drv = fi.Drive(0.0, s.amplitude, s.omega)
+    M = 256
+    plan = o.plan_for_drive_dense(h0, h1, drv, M)
+    k = o.commutator_dense(h0, h1)
+    cols = [0, s.n // 2, s.n - 1]
+    x0 = np.zeros((s.n, len(cols)), complex)
+    x0[cols, np.arange(len(cols))] = 1.0
+    ref = o.propagate_dense(h0, h1, plan, x0)
+
+    def op_slices(P):
+        hi = bf16_rne(P.astype(np.float32))
+        return hi, bf16_rne((P - hi.astype(np.float64)).astype(np.float32))
+
+    f32 = np.float32
+    xr, xi = x0.real.astype(f32), x0.imag.astype(f32)
+    a = plan.coeffs.astype(f32)
+    for m in range(M):
+        om = o.omega_tilde_dense(h0, h1, k, plan, m)
+        S, A = op_slices(om.real), op_slices(om.imag)
+
+        def apply(pr, pi):  # (S + i A)(pr + i pi)
+            return ((_x3_real_product(S, pr) - _x3_real_product(A, pi)).astype(f32),
+                    (_x3_real_product(S, pi) + _x3_real_product(A, pr)).astype(f32))
+
+        p0r, p0i = xr, xi
+        yr, yi = apply(p0r, p0i)
+        p1r, p1i = yi, (-yr).astype(f32)                  # psi_1 = -i Y
+        accr = (a[0] * p0r + a[1] * p1r).astype(f32)
+        acci = (a[0] * p0i + a[1] * p1i).astype(f32)
+        for l in range(1, plan.L):
+            yr, yi = apply(p1r, p1i)
+            nr, ni = (2 * yi + p0r).astype(f32), (-2 * yr + p0i).astype(f32)   # -2i Y + psi_{l-1}
+            accr, acci = (accr + a[l + 1] * nr).astype(f32), (acci + a[l + 1] * ni).astype(f32)
+            p0r, p0i, p1r, p1i = p1r, p1i, nr, ni
+        ph = plan.phase
+        xr = (ph.real * accr - ph.imag * acci).astype(f32)
+        xi = (ph.real * acci + ph.imag * accr).astype(f32)
+    err = np.max(np.abs(xr.astype(np.float64) + 1j * xi.astype(np.float64) - ref))
+    assert err <= 1e-5 / 4, err
