@@ -426,6 +426,8 @@ def expect_dense(h0, h1, a0, a1, s_drive, drive):
 
 
 def expect_tridiag(h0_diag, h0_off, h1_diag, a0, a1, s_drive, drive):
+    """expect_dense for tridiagonal H0 (diagonal, off-diagonal) and diagonal H1: <x|A(t)|x> per
+    column with A(t) = a0 H0 + (a1 + s_drive f(t)) H1, the integrand of Eq. 17 for the dimer."""
     def ev(t, x):
         f = float(cos_drive(drive.f_dc, drive.f_ac, drive.omega, drive.phi0, t)[0])
         d = a0 * h0_diag + (a1 + s_drive * f) * h1_diag

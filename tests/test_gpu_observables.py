@@ -66,7 +66,8 @@ def test_hellmann_feynman_on_gpu(fq):
 @pytest.mark.parametrize("precision,kernel", [(0, 1), (1, 2)])
 def test_dimer_average_energy(fq, precision, kernel):
     """Dimer (dim 41, M = 100): <H(t)>_T of its Floquet states (the paper's sorting key, §7), FP64
-    streaming and FP32 resident, against the oracle; FP32 tolerance 2 ||H|| tol_f32."""
+    streaming and FP32 resident, against the oracle.  A state error e moves <H> by at most
+    2 ||H|| e, so the FP32 tolerance is 2 ||H|| min(1e-5, the FP32 rounding bound of the states)."""
     d = fi.config_dimer(nb=40, steps=100)
     plan = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=3.0, f_ac=1.5, steps=d.steps,
                            precision=precision, kernel=kernel)
@@ -87,7 +88,7 @@ def test_dimer_average_energy(fq, precision, kernel):
         tol = 1e-9
     else:
         hn = max(abs(plan.info.e_min), abs(plan.info.e_max))
-        tol = 2 * hn * (2 * d.steps * plan.info.R * U32 + 4 * math.sqrt(d.steps) * plan.info.L * U32)
+        tol = 2 * hn * min(1e-5, 2 * d.steps * plan.info.R * U32 + 4 * math.sqrt(d.steps) * plan.info.L * U32)
     assert np.max(np.abs(avg - ref)) <= tol
     order = np.argsort(avg)      # the paper sorts Floquet states by mean energy
     assert len(set(order.tolist())) == d.n

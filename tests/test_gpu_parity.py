@@ -8,7 +8,8 @@ Tolerances (written here, derived in the design notes):
     systematic error adds up coherently over M steps.  Second term: the rounding of the L
     operator products of a step (about L u per step on a unit-norm state) adds up as a random
     walk over M unitary steps (factor 4 of headroom).  Both bound a column's 2-norm error and so
-    its largest entry error.
+    its largest entry error.  Every FP32 check is also held to the 1e-5 accuracy target of
+    FP32-level paths: the test tolerance is min(1e-5, that bound).
 """
 import math
 import multiprocessing as mp
@@ -25,7 +26,8 @@ U32 = 2.0 ** -24
 
 
 def tol_f32(M, L, R):
-    return 2.0 * M * R * U32 + 4.0 * math.sqrt(M) * L * U32
+    """min(1e-5, 2 M R u + 4 sqrt(M) L u): the FP32 rounding bound, capped at the FP32-level target."""
+    return min(1e-5, 2.0 * M * R * U32 + 4.0 * math.sqrt(M) * L * U32)
 
 
 @pytest.fixture(scope="module")
@@ -161,7 +163,6 @@ def test_dimer_full_size_resident_sampled_columns(fq):
     err = np.max(np.abs(got - ref))
     print(f"dimer 10001 FP32 resident: max err {err:.3e} (tol {tol:.3e})")
     assert err <= tol
-    assert err <= 1e-5  # the accuracy target for FP32-level paths, tighter than the bound here
     sample = torch.arange(0, d.n, 157, dtype=torch.int32, device="cuda")
     mx, fro = fq.api.unitarity_defect(U, sample)
     assert mx <= 2 * tol

@@ -437,3 +437,37 @@ def test_overlap_phase_error_decays_at_fourth_order():
     s = [np.max(o.overlap_phase_error(u[M], u[2 * M], drv.period)[1]) for M in (16, 32, 64)]
     for a, b in zip(s, s[1:]):
         assert 12.0 < a / b < 20.0, s
+
+
+def test_expect_tridiag_matches_dense_form():
+    """<x|A(t)|x> of the tridiagonal form (Eq. 17's integrand for the dimer) against the dense
+    form on the same dimer written as full matrices: driven, with a0, a1 and s all non-zero and
+    different and a phase offset, at several instants and on complex states.  A swapped a0 / a1,
+    a dropped off-diagonal or a wrong drive factor changes the result at O(1)."""
+    nb = 24
+    d, off, h1d = fi.dimer_matrices(nb, 1.0, U=0.11)
+    h0 = np.diag(d) + np.diag(off, -1) + np.diag(off, 1)
+    h1 = np.diag(h1d).astype(np.float64)
+    drv = fi.Drive(0.35, 1.4, 2.3, 0.6)
+    a0, a1, s = 0.7, -1.3, 2.1
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((nb + 1, 5)) + 1j * rng.standard_normal((nb + 1, 5))
+    et = o.expect_tridiag(d, off, h1d, a0, a1, s, drv)
+    ed = o.expect_dense(h0, h1, a0, a1, s, drv)
+    for t in (0.0, 0.37, 1.9, drv.period * 0.8):
+        got, ref = et(t, x), ed(t, x)
+        assert np.max(np.abs(got - ref)) < 1e-11 * np.max(np.abs(ref))
+    # the instant enters only through f(t): at t and t + T the values agree
+    assert np.max(np.abs(et(0.37, x) - et(0.37 + drv.period, x))) < 1e-9
+
+
+def test_expect_tridiag_stationary_states():
+    """Undriven (s = 0): the eigenvectors of the tridiagonal A = a0 H0 + a1 H1 (LAPACK's
+    tridiagonal solver) give <v|A|v> = their eigenvalues exactly, at any t."""
+    from scipy.linalg import eigh_tridiagonal
+    nb = 40
+    d, off, h1d = fi.dimer_matrices(nb, 1.0, U=0.05)
+    a0, a1 = 1.3, 0.45
+    lam, v = eigh_tridiagonal(a0 * d + a1 * h1d, a0 * off)
+    ev = o.expect_tridiag(d, off, h1d, a0, a1, 0.0, fi.Drive(0.2, 1.1, 3.0))
+    assert np.max(np.abs(ev(0.8, v.astype(np.complex128)) - lam)) < 1e-11 * np.max(np.abs(lam))
