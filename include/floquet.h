@@ -234,14 +234,22 @@ fq_status floquet_average_observable(fq_plan* plan, const void* d_X0, int32_t nc
  * memory, or that must not grow its device footprint after start-up).  It runs the same
  * resident FP32 tridiagonal chain as floquet_build_UT, but takes the problem directly (host
  * arrays, no plan) and keeps every intermediate - operators, per-step scalars, the per-step
- * operator coefficients and frame rotations ((2M + 1) * ceil4(N) float pairs) and the status
- * word - in one static __device__
- * array of FLOQUET_STATIC_SCRATCH_BYTES that each GPU loading the library holds until exit.
- *  - problem: FQ_TRIDIAG with FQ_FP32 only (N <= 10240, L <= 128); larger scratch needs are
- *    rejected with FQ_EINVAL before any work, as are other formats (FQ_EUNSUPPORTED).
+ * operator coefficients and frame rotations, and the status word - in one static __device__
+ * array of FLOQUET_STATIC_SCRATCH_BYTES that each GPU running it holds until exit.
+ *  - Limit: (2M + 1) * rows * 8 bytes plus about 3M * 8 + 4N * 8 bytes must fit in
+ *    FLOQUET_STATIC_SCRATCH_BYTES, where rows is the resident kernel's padded row count:
+ *    512 for N <= 512, 1024 for N <= 1024, 512 * (ceil(N / 512) rounded up to even) for
+ *    N <= 9216, 10240 above
+ *    (e.g. N = 701, M = 300 fits; N = 1100 needs 2048 rows, so M <= 511).  Larger needs are
+ *    rejected with FQ_EINVAL before any work.
+ *  - problem: FQ_TRIDIAG with FQ_FP32, kernel FQ_KERNEL_AUTO or FQ_KERNEL_RESIDENT only
+ *    (N <= 10240, L <= 128); anything else returns FQ_EUNSUPPORTED.
  *  - d_U: caller-owned N x N complex128 output, U[i][j] = <i|U_T|j>, as floquet_build_UT.
  *  - Calls no cudaMalloc/cudaFree.  The first call on a device looks up the array's device
- *    address with that device current (make it before any stream capture).
+ *    address with that device current (make it before any stream capture).  Under CUDA's lazy
+ *    module loading (the default) the array is committed on a device at that first call, not
+ *    when the library is opened: make the first call at start-up, or set
+ *    CUDA_MODULE_LOADING=EAGER, if device memory may run out later.
  *  - Synchronises `stream` and returns FQ_EBOUND if the device check fired.
  *  - Every call shares the array and overwrites what the previous call left there; calls
  *    that overlap on the GPU (other streams, other host threads) race and must not be made. */

@@ -14,7 +14,9 @@
 
 #include "internal.h"
 
-// 16 MiB, resident in every GPU that loads the library until the process exits.
+// 16 MiB on every GPU where the library's device code is loaded, held until the process exits.
+// With CUDA's lazy module loading (the default) that happens at the first call on a device, not
+// when the library is opened.
 static __device__ __align__(256) unsigned char g_fq_static_scratch[FLOQUET_STATIC_SCRATCH_BYTES];
 
 namespace {
@@ -58,6 +60,10 @@ static fq_status build_static(const fq_problem* prob, void* d_U, void* stream) {
     fq_set_error("floquet_build_UT_static: only FQ_TRIDIAG with FQ_FP32 (resident kernel)");
     return FQ_EUNSUPPORTED;
   }
+  if (prob->kernel != FQ_KERNEL_AUTO && prob->kernel != FQ_KERNEL_RESIDENT) {
+    fq_set_error("floquet_build_UT_static: runs the resident kernel only (kernel = %d requested)", (int)prob->kernel);
+    return FQ_EUNSUPPORTED;
+  }
   fq_plan p;
   fq_status st = fq_host_plan(prob, &p);
   if (st != FQ_OK) return st;
@@ -76,9 +82,9 @@ static fq_status build_static(const fq_problem* prob, void* d_U, void* stream) {
   const size_t off_coef = off_k + up256(nm1 * sizeof(double));
   const size_t need = off_coef + up256(fq_resident_coeff_bytes(n, M));
   if (need > (size_t)FLOQUET_STATIC_SCRATCH_BYTES) {
-    fq_set_error("floquet_build_UT_static: needs %zu bytes of scratch ((2M+1)*ceil4(N)*8 + small), limit %zu; "
-                 "use floquet_build_UT with a caller workspace",
-                 need, (size_t)FLOQUET_STATIC_SCRATCH_BYTES);
+    fq_set_error("floquet_build_UT_static: needs %zu bytes of scratch ((2M+1) * %zu padded rows * 8 B + small), "
+                 "limit %zu; use floquet_build_UT with a caller workspace",
+                 need, fq_resident_coeff_bytes(n, 0) / sizeof(float2), (size_t)FLOQUET_STATIC_SCRATCH_BYTES);
     return FQ_EINVAL;
   }
   void* base = nullptr;
