@@ -226,6 +226,19 @@ size_t floquet_observable_workspace_size(const fq_plan* plan, int32_t ncols);
 fq_status floquet_average_observable(fq_plan* plan, const void* d_X0, int32_t ncols, double a0, double a1,
                                      double s_drive, double* d_avg, void* d_ws, size_t ws_bytes, void* stream);
 
+/* Overlap phase error of Eq. 20 (§7) under the reading that fixes its phases: for the ncols
+ * Floquet states phi~_r (d_states, ncols x N complex128 rows, unit norm; e.g. those of the U_T of
+ * the same drive at step h/2) with quasienergies eps~_r (d_eps, ncols device doubles),
+ *   d_sigma[r] = |1 - e^{i eps~_r T} <phi~_r| U_T |phi~_r>|,
+ * where U_T phi~_r is the plan's whole chain (step h) applied to the state on the device and the
+ * overlap is reduced in FP64.  It is the one-period error of the plan's chain against the exact
+ * evolution e^{-i eps~ T} phi~ of the finer Floquet state.  d_states is not modified; every
+ * buffer is caller-owned; d_ws: floquet_overlap_workspace_size(plan, ncols) bytes, 256-byte
+ * aligned, else FQ_EINVAL.  Asynchronous on `stream`. */
+size_t floquet_overlap_workspace_size(const fq_plan* plan, int32_t ncols);
+fq_status floquet_overlap_phase_error(fq_plan* plan, const void* d_states, int32_t ncols, const double* d_eps,
+                                      double* d_sigma, void* d_ws, size_t ws_bytes, void* stream);
+
 /* Size of the library's static device scratch array used by floquet_build_UT_static. */
 #define FLOQUET_STATIC_SCRATCH_BYTES (16u << 20)
 

@@ -73,6 +73,8 @@ _SIGS = {
     "floquet_observable_workspace_size": (_sz, [_vp, _i32]),
     "floquet_average_observable": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_double, ctypes.c_double,
                                                   ctypes.c_double, _vp, _vp, _sz, _vp]),
+    "floquet_overlap_workspace_size": (_sz, [_vp, _i32]),
+    "floquet_overlap_phase_error": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
     "floquet_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -293,6 +295,20 @@ def floquet_average_observable(plan: int, X0, ncols: int, a0: float, a1: float, 
     po = _dev(out, _f64(), max(int(ncols), 0), "out", w)
     pw, nb = _ws(ws, w)
     _check(lib.floquet_average_observable(_vp(plan), px, ncols, a0, a1, s_drive, po, pw, nb, _stream(stream)), w)
+
+
+def floquet_overlap_workspace_size(plan: int, ncols: int) -> int:
+    return int(lib.floquet_overlap_workspace_size(_vp(plan), ncols))
+
+
+def floquet_overlap_phase_error(plan: int, states, ncols: int, eps, sigma, ws, stream=None) -> None:
+    w = "floquet_overlap_phase_error"
+    n = floquet_plan_get_info(plan).n
+    ps = _dev(states, _c128(), max(int(ncols), 0) * n, "states", w)
+    pe = _dev(eps, _f64(), max(int(ncols), 0), "eps", w)
+    po = _dev(sigma, _f64(), max(int(ncols), 0), "sigma", w)
+    pw, nb = _ws(ws, w)
+    _check(lib.floquet_overlap_phase_error(_vp(plan), ps, ncols, pe, po, pw, nb, _stream(stream)), w)
 
 
 def floquet_check_status(plan: int, stream=None) -> int:

@@ -159,23 +159,18 @@ def unitarity_defect(U, cols=None, stream=None):
 
 
 def floquet_states(U, period):
-    """Quasienergies eps (Eq. 5, eps = theta/T, theta = -arg(lambda) in [-pi, pi)) and Floquet
-    states (rows, unit norm) from U_T, by host FP64 LAPACK (zgeev) - outside the timed path."""
-    import numpy as np
+    """Quasienergies eps (Eq. 5, eps = theta/T, theta = -arg(lambda) in [-pi, pi), ascending) and
+    Floquet states (rows, unit norm, on U's device) of U_T by the library's host solver
+    (floquet_quasienergies) - outside the timed path.  Returns (eps as a numpy array, states)."""
     import torch
-    u = U.detach().cpu().numpy()
-    lam, v = np.linalg.eig(u)
-    theta = -np.angle(lam)
-    theta = np.where(theta >= math.pi, theta - 2.0 * math.pi, theta)
-    order = np.argsort(theta)
-    v = v[:, order] / np.linalg.norm(v[:, order], axis=0, keepdims=True)
-    return theta[order] / period, torch.from_numpy(np.ascontiguousarray(v.T)).to(U.device)
+    eps, v = B.floquet_quasienergies(U.detach().cpu().numpy(), period, states=True)
+    return eps, torch.from_numpy(v).to(U.device)
 
 
 def floquet_analysis(plan, U=None):
-    """The paper's post-processing (§3 last paragraph, §7): Floquet states of U_T (host zgeev),
-    their period-averaged energies <H(t)>_T from a second propagation round (Eq. 17, on the
-    library), and the states sorted by that energy.  Returns (avg_energy, eps, states), sorted
+    """The paper's post-processing (§3 last paragraph, §7): Floquet states of U_T (library host
+    solver), their period-averaged energies <H(t)>_T from a second propagation round (Eq. 17, on
+    the library), and the states sorted by that energy.  Returns (avg_energy, eps, states), sorted
     ascending in avg_energy; states are rows (complex128, device)."""
     import numpy as np
     import torch
@@ -188,16 +183,17 @@ def floquet_analysis(plan, U=None):
     return avg[order], eps[order], states.index_select(0, idx)
 
 
-def overlap_phase_error(plan, U_fine):
+def overlap_phase_error(plan, U_fine, stream=None):
     """Overlap phase error of Eq. 20 for the chain of `plan` (step h): with (phi~, eps~) the
     Floquet states of U_fine, the U_T of the same drive at step h/2, Sigma_mu =
-    |1 - e^{i eps~_mu T} <phi~_mu| U_T |phi~_mu>|.  U_T phi~ comes from propagating the states
-    through the plan's chain on the library; the eigenvectors and the M overlaps are host FP64.
-    Returns (eps~ ascending, Sigma in that order)."""
-    import numpy as np
+    |1 - e^{i eps~_mu T} <phi~_mu| U_T |phi~_mu>| (floquet_overlap_phase_error: the chain and the
+    overlaps on the device).  Returns (eps~ ascending, Sigma in that order) as numpy arrays."""
+    import torch
     T = plan.info.steps * plan.info.h
     eps, states = floquet_states(U_fine, T)
-    moved = plan.propagate(states).cpu().numpy()
-    phi = states.cpu().numpy()
-    overlap = np.einsum("mi,mi->m", phi.conj(), moved)
-    return eps, np.abs(1.0 - np.exp(1j * eps * T) * overlap)
+    n = states.shape[0]
+    d_eps = torch.from_numpy(eps).to(states.device)
+    sigma = torch.empty(n, dtype=torch.float64, device=states.device)
+    ws = workspace(B.floquet_overlap_workspace_size(plan.handle, n))
+    B.floquet_overlap_phase_error(plan.handle, states, n, d_eps, sigma, ws, stream)
+    return eps, sigma.cpu().numpy()

@@ -1,5 +1,5 @@
 // Second propagation round (§3, last paragraph; §7): period averages of an observable along the
-// chain,  <A>_T = (1/T) int_0^T <psi(t)|A(t)|psi(t)> dt  (Eq. 17),
+// chain (and, below, the overlap phase error of Eq. 20),  <A>_T = (1/T) int_0^T <psi(t)|A(t)|psi(t)> dt  (Eq. 17),
 // for A(t) = a0 H0 + (a1 + s f(t)) H1 (A = H(t) for a0 = 1, a1 = 0, s = 1), evaluated at the
 // step boundaries t_m = m h with composite Simpson weights (trapezoid for odd M).
 #include <cuda_runtime.h>
@@ -74,6 +74,29 @@ __global__ void k_expect_dense(const double2* __restrict__ x, int n, const doubl
   }
   s = block_sum(s, red);
   if (threadIdx.x == 0) acc[blockIdx.x] += w * s;
+}
+
+// sigma[r] = |1 - e^{i eps_r T} <phi_r|moved_r>| (Eq. 20, reading R14), one CTA per state row.
+__global__ void k_overlap_sigma(const double2* __restrict__ phi, const double2* __restrict__ moved, int n,
+                                const double* __restrict__ eps, double period, double* __restrict__ sigma) {
+  __shared__ double red[32];
+  const double2* a = phi + (size_t)blockIdx.x * n;
+  const double2* b = moved + (size_t)blockIdx.x * n;
+  double sr = 0.0, si = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double2 x = a[k], y = b[k];
+    sr = fma(x.x, y.x, fma(x.y, y.y, sr));   // Re(conj(x) y)
+    si = fma(x.x, y.y, fma(-x.y, y.x, si));  // Im(conj(x) y)
+  }
+  sr = block_sum(sr, red);
+  __syncthreads();
+  si = block_sum(si, red);
+  if (threadIdx.x == 0) {
+    double sn, cs;
+    sincos(eps[blockIdx.x] * period, &sn, &cs);
+    const double zr = 1.0 - (cs * sr - sn * si), zi = -(cs * si + sn * sr);
+    sigma[blockIdx.x] = hypot(zr, zi);
+  }
 }
 
 __global__ void k_scale_out(const double* acc, int nc, double s, double* out) {
@@ -157,5 +180,43 @@ extern "C" fq_status floquet_average_observable(fq_plan* p, const void* d_X0, in
                                                 void* stream) {
   return fq_guard("floquet_average_observable", [&] {
     return floquet_average_observable_body(p, d_X0, ncols, a0, a1, s_drive, d_avg, d_ws, ws_bytes, stream);
+  });
+}
+
+extern "C" size_t floquet_overlap_workspace_size(const fq_plan* p, int32_t ncols) {
+  if (!p || ncols < 1) return 0;
+  return up256((size_t)ncols * p->n * 16) + floquet_workspace_size(p, ncols);
+}
+
+static fq_status floquet_overlap_phase_error_body(fq_plan* p, const void* d_states, int32_t ncols,
+                                                  const double* d_eps, double* d_sigma, void* d_ws, size_t ws_bytes,
+                                                  void* stream) {
+  if (!p || !d_states || !d_eps || !d_sigma || ncols < 1) {
+    fq_set_error("floquet_overlap_phase_error: bad arguments");
+    return FQ_EINVAL;
+  }
+  const size_t need = floquet_overlap_workspace_size(p, ncols);
+  if (!d_ws || ws_bytes < need || ((uintptr_t)d_ws & 255)) {
+    fq_set_error("floquet_overlap_phase_error: workspace must be >= %zu bytes, 256-byte aligned", need);
+    return FQ_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = p->n;
+  char* b = (char*)d_ws;
+  double* moved = (double*)b;
+  const size_t head = up256((size_t)ncols * n * 16);
+  // U_T phi~ for every state: the plan's whole chain (step h) on the given rows
+  fq_status st = floquet_propagate(p, d_states, moved, ncols, 0, p->steps, b + head, ws_bytes - head, stream);
+  if (st != FQ_OK) return st;
+  k_overlap_sigma<<<ncols, 256, 0, s>>>((const double2*)d_states, (const double2*)moved, n, d_eps, p->period,
+                                        d_sigma);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? FQ_OK : fq_cuda_fail(e, "overlap kernel");
+}
+
+extern "C" fq_status floquet_overlap_phase_error(fq_plan* p, const void* d_states, int32_t ncols, const double* d_eps,
+                                                 double* d_sigma, void* d_ws, size_t ws_bytes, void* stream) {
+  return fq_guard("floquet_overlap_phase_error", [&] {
+    return floquet_overlap_phase_error_body(p, d_states, ncols, d_eps, d_sigma, d_ws, ws_bytes, stream);
   });
 }
