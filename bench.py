@@ -1,10 +1,13 @@
 """Benchmark: U_T builds per second on the Bose-Hubbard dimer with nb = 10^4 bosons
 (dim 10001, tridiagonal Fock basis), M = 2000 Magnus-4 steps per period, Chebyshev truncated at
-|J_{L+1}(R)| < 1e-14 (L = 39), FP32 resident tridiagonal kernel.
+|J_{L+1}(R)| < 1e-14 (L = 39), in FP64-level arithmetic by default (--precision df32: the
+double-float tiled chain), with the FP32 resident kernel timed beside it (the line's "fp32" key;
+--precision fp32 makes it the headline).
 
-One step = one floquet_build_UT call (the full 10001 x 10001 identity propagated over the period).
-N > 1 (torchrun): every rank builds the U_T of its own drive amplitude (a parameter scan), so
-work per GPU is fixed and no collective touches the data path ("scaling": "weak").
+One step = one U_T build (the full 10001 x 10001 identity propagated over the period).
+N > 1 (torchrun): by default the ranks split each U_T's columns (§5: column blocks propagate
+independently, one all-gather assembles U_T; "scaling": "strong"); --shard replicas instead gives
+every rank its own drive amplitude (independent problems, "scaling": "weak").
 
 --impl reference times the FP64 CPU oracle on this host on a bounded sample of the same
 workload (a few states over a slice of the period) and reports the same metric.
@@ -37,6 +40,10 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # steps 0..19, k_tri_resident<256, 40>): bytes read, of which the 152 initial states are a fixed
 # part; the rest is the per-step (2d, 2e') and rotation stream, which grows with waves x steps.
 RES_NCU = {"read": 28.519936e6, "x0": 152 * 10001 * 16, "states": 152, "steps": 20}
+RES_TRAFFIC_NOTE = "see profiles/k_tri_resident_dimer10001.md for the DRAM bytes of the resident kernel"
+# double-float tiled chain: FP32 lane operations per element-term (4 complex double-float FMAs of
+# 15 packed FP32x2 operations each)
+DFL_LANE_OPS_PER_ELEMENT_TERM = 120
 # The paper's Table 1 (M = 100, L = 50, 6th order): seconds of Chebyshev iterations for one U_T
 # on one node (2 x 8-core Xeon E5-2660, FP64 MKL zgemm), by N.
 PAPER_TABLE1_CHEB_S = {256: 4.3, 512: 25.3, 1024: 177.3, 2048: 1296.6, 4096: 9730.5, 5120: 18667.2,
@@ -46,11 +53,17 @@ PAPER_TABLE1_CHEB_S = {256: 4.3, 512: 25.3, 1024: 177.3, 2048: 1296.6, 4096: 973
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-extra", action="store_true",
+                    help="dimer: skip the FP32 resident timing reported beside an FP64-level headline")
+    ap.add_argument("--fp32-steps", type=int, default=3, help="dimer: timed FP32 resident builds beside the headline")
+    ap.add_argument("--shard", choices=["columns", "replicas"], default="columns",
+                    help="dimer under torchrun: split each U_T's columns over the ranks with one all-gather "
+                         "(default), or give every rank its own drive amplitude")
     ap.add_argument("--workload", choices=["dimer", "dimer-paper", "goe4096", "adjoint", "paper-table1", "batch"],
                     default="dimer",
                     help="dimer: nb = 10^4, J = 1, U nb = 2, f = 1.5 cos 3t, M = 2000 (default); "
@@ -63,11 +76,11 @@ def parse():
                          "A ~ U[0.5, 3], M = 256) as one CUDA graph over 8 lanes, instances/s")
     ap.add_argument("--n", type=int, default=4096, choices=sorted(PAPER_TABLE1_CHEB_S),
                     help="paper-table1: the matrix size (the rows of the paper's Table 1)")
-    ap.add_argument("--precision", choices=["x3", "x6", "ozaki", "fp64"], default=None,
+    ap.add_argument("--precision", choices=["x3", "x6", "ozaki", "fp64", "fp32", "df32"], default=None,
                     help="goe4096 / adjoint / batch: BF16X3 (default), BF16X6, FQ_OZAKI (FP64 emulation) or FP64 "
-                         "(adjoint only)")
-    ap.add_argument("--ncu-case", choices=["resident", "stream", "split", "tile", "adjoint", "ozaki", "dense-resident",
-                             "ozaki-grad"],
+                         "(adjoint only); dimer: df32 (double-float, FP64-level; default) or fp32 (resident)")
+    ap.add_argument("--ncu-case", choices=["resident", "stream", "split", "tile", "dfl", "adjoint", "ozaki",
+                                           "dense-resident", "ozaki-grad"],
                     default=None,
                     help="run one small capture case of a kernel twice and exit (for ncu --set full)")
     return ap.parse_args()
@@ -79,6 +92,7 @@ def run_ncu_case(case):
     stream:   2048 states through step 0 (39 streaming FP32 term launches, 0.5 GB of states);
     split:    dense GOE N = 4096 (seeds 3, 4), BF16X3 tensor-core terms of step 0 on the identity;
     tile:     2048 states through step 0 on the FP64 tiled kernel (0.65 GB of states);
+    dfl:      2048 states through step 0 on the double-float tiled kernel (FQ_DF32, 0.65 GB);
     adjoint:  the BF16X3 gradient at N = 1024 (seeds 6-9) over the first 16 of its 256 steps;
     ozaki-grad: the same in FP64 emulation (FQ_OZAKI);
     ozaki:    dense GOE N = 2048 (seeds 3, 4; A = 2, omega = 2, M = 64), FQ_OZAKI terms of step 0 on
@@ -128,9 +142,11 @@ def run_ncu_case(case):
         return
     d = fi.config_dimer(nb=NB, steps=STEPS)
     n = d.n
-    kernel = {"resident": fq.FQ_KERNEL_RESIDENT, "stream": fq.FQ_KERNEL_STREAM, "tile": fq.FQ_KERNEL_TILED}[case]
+    kernel = {"resident": fq.FQ_KERNEL_RESIDENT, "stream": fq.FQ_KERNEL_STREAM, "tile": fq.FQ_KERNEL_TILED,
+              "dfl": fq.FQ_KERNEL_TILED}[case]
+    precision = {"tile": fq.FQ_FP64, "dfl": fq.FQ_DF32}.get(case, fq.FQ_FP32)
     plan = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=d.drive.f_ac,
-                           steps=d.steps, precision=fq.FQ_FP64 if case == "tile" else fq.FQ_FP32, kernel=kernel)
+                           steps=d.steps, precision=precision, kernel=kernel)
     nc, m_end = (152, 20) if case == "resident" else (2048, 1)
     x0 = torch.zeros((nc, n), dtype=torch.complex128, device="cuda")
     x0[torch.arange(nc), torch.arange(nc) * (n // nc)] = 1.0
@@ -305,17 +321,49 @@ def run_reference(args):
         vals.append(v)
         secs += dt
     value = statistics.median(vals)
-    line = {"impl": "reference", "metric": "U_T builds/sec (dim 10001 Bose-Hubbard dimer, M=2000)",
+    line = {"impl": "reference", "metric": "U_T builds/sec (dim 10001 Bose-Hubbard dimer, M=2000, FP64-level)",
             "value": value, "unit": "U_T/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "bose-hubbard dimer nb=10000 (dim 10001), M=2000, L=39"},
+            "config": {"workload": "bose-hubbard dimer nb=10000 (dim 10001), M=2000, L=39",
+                       "kernel": "FP64 numpy oracle (host cores)"},
             "cpu_baseline": {"value": value, "unit": "U_T/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "U_T/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------------- our arm
+# The dimer kernels the bench times, with how one launch's work is counted for the roofline; the
+# unit is the element-term (one entry of one state through one Chebyshev product).
+DIMER_PATHS = {
+    # FP32 resident chain (one launch per U_T): 26 flop per element-term against the FP32 FMA peak
+    "fp32": {"precision": "FQ_FP32", "kernel": "FQ_KERNEL_RESIDENT", "dtype": "f32", "level": "FP32",
+             "kernel_name": "k_tri_resident<256, 40>", "unit": "TFLOP/s", "per_unit": FLOPS_PER_ELEMENT_TERM,
+             "launches_per_step": 2,
+             "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived from unit counts and clocks)"},
+    # double-float tiled chain (FP64-level, one launch per step): 4 double-float complex FMAs per
+    # element-term, each 15 packed FP32x2 operations (30 FP32 lane operations), against the FP32
+    # lane-operation peak
+    "df32": {"precision": "FQ_DF32", "kernel": "FQ_KERNEL_TILED", "dtype": "df32 (FP32 pairs, FP64 states)",
+             "level": "FP64", "kernel_name": "k_tri_tile_dfl", "unit": "Tops/s",
+             "per_unit": DFL_LANE_OPS_PER_ELEMENT_TERM, "launches_per_step": STEPS + 3,
+             "peak_note": "FP32 lane operations: 152 SMs x 128 lanes x 2070 MHz (derived from unit counts and clocks)"},
+}
+
+
+def dimer_roofline(path, n, steps, L, seconds_per_launch, per_launch_units):
+    """Roofline of the dominant dimer kernel: algorithmic work of one launch / its CUDA-event time."""
+    work = path["per_unit"] * per_launch_units
+    achieved = work / seconds_per_launch / 1e12
+    if path["unit"] == "TFLOP/s":
+        peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    else:
+        peak = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": path["unit"], "frac": achieved / peak,
+            "kernel": path["kernel_name"], "work_per_unit": path["per_unit"], "units_per_launch": per_launch_units,
+            "peak_note": path["peak_note"]}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -323,51 +371,67 @@ def run_ours(args):
 
     import floquet_inputs as fi
     import paper_1508_07621_gb300 as fq
+    from paper_1508_07621_gb300 import shard
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    # rank r scans its own drive amplitude; rank 0 runs exactly the workload's amplitude
     paper = args.workload == "dimer-paper"
+    prec = args.precision or "df32"
+    if prec not in DIMER_PATHS:
+        raise SystemExit(f"--precision for the dimer: one of {sorted(DIMER_PATHS)}")
+    path = DIMER_PATHS[prec]
     d = fi.config_dimer_paper(nb=NB, steps=8000) if paper else fi.config_dimer(nb=NB, steps=STEPS)
-    f_ac = rank_drive_amplitude(d.drive.f_ac, rank)
+    sharded = world > 1 and args.shard == "columns"
+    # replicas: rank r builds the U_T of its own drive amplitude; columns: all ranks share one U_T
+    f_ac = d.drive.f_ac if sharded else rank_drive_amplitude(d.drive.f_ac, rank)
     f_dc = d.drive.f_dc
     n = d.n
     stream = torch.cuda.current_stream()
-    plan = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=f_ac, f_dc=f_dc,
-                           steps=d.steps, precision=fq.FQ_FP32, kernel=fq.FQ_KERNEL_RESIDENT)
-    L = plan.info.L
-    ws = fq.workspace(plan.workspace_size())
-    U = torch.empty((n, n), dtype=torch.complex128, device="cuda")
-    for _ in range(max(args.warmup, 0)):
-        fq.floquet_build_UT(plan.handle, U, ws, stream)
-    torch.cuda.synchronize()
-    if plan.check_status() != fq.FQ_OK:
-        raise RuntimeError("device bound check fired during warm-up")
 
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.5)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev[0].record(stream)
-    for k in range(args.steps):
-        fq.floquet_build_UT(plan.handle, U, ws, stream)
-        ev[k + 1].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    per_step = [ev[k].elapsed_time(ev[k + 1]) / 1000.0 for k in range(args.steps)]
-    value, total = job_throughput(ev[0].elapsed_time(ev[-1]) / 1000.0, args.steps, dist if world > 1 else None,
-                                  "cuda")
+    def make_plan(p):
+        return fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=f_ac, f_dc=f_dc,
+                               steps=d.steps, precision=getattr(fq, p["precision"]), kernel=getattr(fq, p["kernel"]))
+
+    def timed_build(p, warmup, steps):
+        """Warm-up, then `steps` CUDA-event-timed U_T builds of path p; returns the plan, the last
+        U_T (row-major, or column-major when sharded), per-step seconds, total seconds, clocks."""
+        plan = make_plan(p)
+        if sharded:
+            buf = shard.gather_buffer(n, world)
+            ws = shard.columns_workspace(plan, world)
+            out = {}
+
+            def step():
+                out["U"] = shard.build_ut_sharded(plan, dist, buf, ws, stream)
+        else:
+            ws = fq.workspace(plan.workspace_size())
+            U = torch.empty((n, n), dtype=torch.complex128, device="cuda")
+            out = {"U": U}
+
+            def step():
+                fq.floquet_build_UT(plan.handle, U, ws, stream)
+        for _ in range(max(warmup, 0)):
+            step()
+        torch.cuda.synchronize()
+        if plan.check_status() != fq.FQ_OK:
+            raise RuntimeError("device bound check fired during warm-up")
+        per_step, total, clk = timed_loop(step, steps, stream, world, dist)
+        return plan, out["U"], per_step, total, clk
+
+    plan, U, per_step, total, clk = timed_build(path, args.warmup, args.steps)
+    value, total = job_throughput(total, args.steps, dist if world > 1 else None, "cuda")
+    if sharded:
+        value /= world  # every rank took part in the same U_T builds
+    L = plan.info.L
     status_ok = plan.check_status() == fq.FQ_OK
-    # accuracy of the timed result: unitarity defect of U_T over 64 sampled columns (FP64, on the GPU)
+    # accuracy of the timed result: unitarity defect over 64 sampled columns (FP64, on the GPU);
+    # the sharded result is column-major, whose row defect is that of U_T's columns
     sample_cols = torch.arange(0, n, n // 64, dtype=torch.int32, device="cuda")[:64]
-    defect_max, defect_fro = fq.api.unitarity_defect(U, sample_cols)
+    Urm = U.mT.contiguous() if sharded else U
+    defect_max, defect_fro = fq.api.unitarity_defect(Urm, sample_cols)
+    del Urm
 
     # end to end through the C ABI with host buffers: plan from host arrays (H2D inside the
     # call), build, and the D2H copy of U_T into pinned host memory, every step
@@ -376,35 +440,54 @@ def run_ours(args):
     h2d = 8 * (n + n + (n - 1)) + 8 * (n - 1) + 3 * 8 * d.steps
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
-        p2 = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=f_ac, f_dc=f_dc,
-                             steps=d.steps, precision=fq.FQ_FP32, kernel=fq.FQ_KERNEL_RESIDENT)
-        fq.floquet_build_UT(p2.handle, U, ws, stream)
-        host_u.copy_(U, non_blocking=True)
+        p2 = make_plan(path)
+        if sharded:
+            Ue = shard.build_ut_sharded(p2, dist, stream=stream)
+        else:
+            Ue = U
+            fq.floquet_build_UT(p2.handle, Ue, fq.workspace(p2.workspace_size()), stream)
+        host_u.copy_(Ue, non_blocking=True)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
         p2.close()
-    e2e_value = world / statistics.median(e2e_times)
+        del Ue
+    e2e_local = statistics.median(e2e_times) if e2e_times else float("nan")
+    e2e_value, _ = job_throughput(e2e_local, 1, dist if world > 1 else None, "cuda")
+    if sharded:
+        e2e_value /= world
+
+    # the FP32 resident kernel alongside an FP64-level headline (same workload, its own timing)
+    fp32 = None
+    if prec != "fp32" and not args.no_fp32_extra:
+        p32, _, ps32, tot32, clk32 = timed_build(DIMER_PATHS["fp32"], min(args.warmup, 3), args.fp32_steps)
+        v32, tot32 = job_throughput(tot32, args.fp32_steps, dist if world > 1 else None, "cuda")
+        if sharded:
+            v32 /= world
+        avg32 = statistics.mean(ps32)
+        fp32 = {"value": v32, "unit": "U_T/s", "ms_per_step": 1000.0 * tot32 / args.fp32_steps,
+                "steps": args.fp32_steps, "dtype": "f32", "per_step_s": ps32, "clocks": clk32,
+                "roofline": dimer_roofline(DIMER_PATHS["fp32"], n, d.steps, L, avg32,
+                                           float(n) * n * d.steps * L / (world if sharded else 1))}
+        p32.close()
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
-    # roofline of the dominant kernel (the resident chain; the per-step coefficient kernel is
-    # <0.1% of a step per the committed launch list)
-    flops = FLOPS_PER_ELEMENT_TERM * float(n) * n * d.steps * L
     avg = statistics.mean(per_step)
-    achieved = flops / avg / 1e12
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    per_wave_step = (RES_NCU["read"] - RES_NCU["x0"]) / RES_NCU["steps"]
-    traffic_before = per_wave_step * (n / RES_NCU["states"]) * d.steps + 16.0 * n * n
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "traffic_note": f"null: the kernel gained an L2 prefetch of the next step's "
-                f"coefficients after its last ncu capture; that capture (152 states x 20 steps) scales to "
-                f"{traffic_before:.3e} bytes per launch (per-step coefficient reads x waves x steps, plus the "
-                f"U_T write)",
-                "kernel": "k_tri_resident<256, 40>",
-                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)"}
+    if prec == "fp32":  # one launch per U_T: the whole chain
+        roofline = dimer_roofline(path, n, d.steps, L, avg, float(n) * n * d.steps * L / (world if sharded else 1))
+        roofline["traffic"] = None
+        roofline["traffic_note"] = RES_TRAFFIC_NOTE
+    else:  # one launch per step: units of one launch over the launch's mean duration
+        per_launch = float(n) * n * L / (world if sharded else 1)
+        roofline = dimer_roofline(path, n, d.steps, L, avg / d.steps, per_launch)
+        roofline["traffic"] = None
+        roofline["traffic_note"] = "see profiles/ for the kernel's DRAM bytes per launch"
+        roofline["launch_seconds_note"] = "mean step time / M: the tiled kernel is >99% of a step"
     cpu = None
     accuracy = {"unitarity_defect_max": defect_max, "unitarity_defect_fro": defect_fro,
                 "defect_columns": int(sample_cols.numel())}
@@ -417,21 +500,26 @@ def run_ours(args):
         accuracy["sample_max_err_vs_oracle"] = float(np.max(np.abs(got - xs)))
         accuracy["sample"] = desc
     tag = ", paper parameters" if paper else ""
-    line = {"metric": f"U_T builds/sec (dim {n} Bose-Hubbard dimer{tag}, M={d.steps})", "value": value,
-            "unit": "U_T/s",
+    parallelism = (f"columns: {world} ranks share each U_T (column blocks + one all-gather)" if sharded
+                   else f"replicas: {world} independent drive amplitudes" if world > 1 else "1 GPU")
+    line = {"metric": f"U_T builds/sec (dim {n} Bose-Hubbard dimer{tag}, M={d.steps}, {path['level']}-level)",
+            "value": value, "unit": "U_T/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"bose-hubbard dimer{tag} nb={n - 1} (dim {n}), M={d.steps}, L={L}, "
-                                   "FP32 resident kernel",
+            "higher_is_better": True, "scaling": "strong" if sharded else "weak", "vs_baseline": None,
+            "dtype": path["dtype"], "data": "synthetic",
+            "config": {"workload": f"bose-hubbard dimer{tag} nb={n - 1} (dim {n}), M={d.steps}, L={L}",
+                       "kernel": f"{path['level']}-level arithmetic on {path['kernel_name']}",
                        "dim": n, "steps_per_period": d.steps, "chebyshev_L": L, "R": plan.info.R,
                        "delta_e": plan.info.delta_e,
-                       "l2": "working set larger than L2 (2*Omega~ coefficients 240 MB, U_T 1.6 GB per step)",
-                       "parallelism": f"weak: {world} independent drive amplitudes"},
+                       "l2": "working set larger than L2 (U_T 1.6 GB; per-step operator coefficients)",
+                       "parallelism": parallelism},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "U_T/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * n * n},
-            "gpu_launches": 2 * args.steps, "clocks": clk, "device_status_ok": status_ok,
+            "gpu_launches": path["launches_per_step"] * args.steps, "clocks": clk, "device_status_ok": status_ok,
             "accuracy": accuracy, "median_step_s": statistics.median(per_step), "per_step_s": per_step,
             "host": host_info()}
+    if fp32 is not None:
+        line["fp32"] = fp32
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -190,6 +190,18 @@ fq_status floquet_propagate(fq_plan* plan, const void* d_X0, void* d_X, int32_t 
                             int32_t m_begin, int32_t m_end, void* d_ws, size_t ws_bytes,
                             void* stream);
 
+/* Columns j0 .. j0+ncols-1 of U_T: the basis states e_j of those columns of the identity
+ * propagated over all M steps, which is one node's share in the column split of §5 (Fig. 2, the
+ * distribute part of Algorithm 1; the columns are independent, so no exchange happens while
+ * they propagate).  d_X: ncols x N complex128, caller-owned device memory, row r = column
+ * j0 + r of U_T (X[r][i] = <i|U_T|j0+r>), so the blocks of consecutive column ranges concatenate
+ * into U_T in column-major order.  d_ws: floquet_columns_workspace_size(plan, ncols) bytes,
+ * 256-byte aligned.  FQ_EINVAL for a NULL pointer, ncols < 1 or columns outside [0, N), or a short
+ * or misaligned workspace, before any work.  Asynchronous on `stream`. */
+size_t floquet_columns_workspace_size(const fq_plan* plan, int32_t ncols);
+fq_status floquet_build_UT_columns(fq_plan* plan, int32_t j0, int32_t ncols, void* d_X, void* d_ws,
+                                   size_t ws_bytes, void* stream);
+
 /* Unitarity defect (§2: truncated Omega is Hermitian, so every step is unitary):
  * over the k columns listed in d_cols (int32, device; NULL = all N columns, k ignored) of the
  * N x N complex128 d_U, computes max_{c in cols, j} |(U^+ U - 1)[c][j]| and the Frobenius

@@ -56,6 +56,8 @@ _SIGS = {
     "floquet_workspace_size": (_sz, [_vp, _i32]),
     "floquet_build_UT": (ctypes.c_int, [_vp, _vp, _vp, _sz, _vp]),
     "floquet_propagate": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _sz, _vp]),
+    "floquet_columns_workspace_size": (_sz, [_vp, _i32]),
+    "floquet_build_UT_columns": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _sz, _vp]),
     "floquet_defect_workspace_size": (_sz, [_i32]),
     "floquet_unitarity_defect": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _sz, _vp, _dp, _dp]),
     "floquet_grad_workspace_size": (_sz, [_vp]),
@@ -295,6 +297,18 @@ def floquet_average_observable(plan: int, X0, ncols: int, a0: float, a1: float, 
     po = _dev(out, _f64(), max(int(ncols), 0), "out", w)
     pw, nb = _ws(ws, w)
     _check(lib.floquet_average_observable(_vp(plan), px, ncols, a0, a1, s_drive, po, pw, nb, _stream(stream)), w)
+
+
+def floquet_columns_workspace_size(plan: int, ncols: int) -> int:
+    return int(lib.floquet_columns_workspace_size(_vp(plan), ncols))
+
+
+def floquet_build_UT_columns(plan: int, j0: int, ncols: int, out, ws, stream=None) -> None:
+    w = "floquet_build_UT_columns"
+    n = floquet_plan_get_info(plan).n
+    po = _dev(out, _c128(), max(int(ncols), 0) * n, "out", w)
+    pw, nb = _ws(ws, w)
+    _check(lib.floquet_build_UT_columns(_vp(plan), j0, ncols, po, pw, nb, _stream(stream)), w)
 
 
 def floquet_overlap_workspace_size(plan: int, ncols: int) -> int:

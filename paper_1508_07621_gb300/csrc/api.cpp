@@ -464,6 +464,30 @@ fq_status floquet_propagate(fq_plan* p, const void* d_X0, void* d_X, int32_t nco
                         (cudaStream_t)stream);
 }
 
+size_t floquet_columns_workspace_size(const fq_plan* p, int32_t ncols) {
+  if (!p || ncols < 1) return 0;
+  return align_up((size_t)ncols * p->n * 16) + layout(p, ncols, p->steps, nullptr, nullptr);
+}
+
+fq_status floquet_build_UT_columns(fq_plan* p, int32_t j0, int32_t ncols, void* d_X, void* d_ws, size_t ws_bytes,
+                                   void* stream) {
+  if (!p || !d_X) { fq_set_error("NULL plan or output"); return FQ_EINVAL; }
+  if (ncols < 1 || j0 < 0 || (int64_t)j0 + ncols > p->n) {
+    fq_set_error("floquet_build_UT_columns: columns [%d, %lld) outside [0, %d)", j0, (long long)j0 + ncols, p->n);
+    return FQ_EINVAL;
+  }
+  const size_t head = align_up((size_t)ncols * p->n * 16);
+  if (!d_ws || ws_bytes < head || ((uintptr_t)d_ws & (kAlign - 1))) {
+    fq_set_error("floquet_build_UT_columns: workspace must be >= %zu bytes, 256-byte aligned",
+                 floquet_columns_workspace_size(p, ncols));
+    return FQ_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double* x0 = (double*)d_ws;
+  fq_launch_basis_rows(x0, ncols, p->n, j0, s);
+  return propagate_impl(p, x0, (double*)d_X, ncols, 0, p->steps, 0, 0, (char*)d_ws + head, ws_bytes - head, s);
+}
+
 size_t floquet_defect_workspace_size(int32_t n) {
   if (n < 1) return 0;
   return align_up(2 * sizeof(double) * (size_t)((n + 15) / 16) * ((n + 255) / 256));

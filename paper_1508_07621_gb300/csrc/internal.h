@@ -134,6 +134,7 @@ template <typename T> struct fq_blk { T* re; T* im; };
 void fq_launch_load_states(const double* x_interleaved, fq_blk<double> out, int nc, int n, int ld, cudaStream_t s);
 void fq_launch_load_states_f32(const double* x_interleaved, fq_blk<float> out, int nc, int n, int ld, cudaStream_t s);
 void fq_launch_identity_f64(fq_blk<double> out, int nc, int n, int ld, cudaStream_t s);
+void fq_launch_basis_rows(double* x_interleaved, int nc, int n, int j0, cudaStream_t s);
 void fq_launch_identity_f32(fq_blk<float> out, int nc, int n, int ld, cudaStream_t s);
 void fq_launch_store_states_f64(fq_blk<double> in, double* x, int nc, int n, int ld, cudaStream_t s);
 void fq_launch_store_states_f32(fq_blk<float> in, double* x, int nc, int n, int ld, cudaStream_t s);

@@ -80,6 +80,16 @@ __global__ void k_identity(T* re, T* im, int nc, int n, int ld) {
   }
 }
 
+// Rows r = 0 .. nc-1 of an interleaved complex128 block are the basis states e_{j0 + r} (the
+// columns j0 .. j0+nc-1 of the identity that one rank propagates, §5).
+__global__ void k_basis_rows(double2* x, int nc, int n, int j0) {
+  const size_t total = (size_t)nc * n;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(q / n), i = (int)(q % n);
+    x[q] = make_double2(i == j0 + r ? 1.0 : 0.0, 0.0);
+  }
+}
+
 template <typename T>
 __global__ void k_store_states(const T* __restrict__ re, const T* __restrict__ im, double2* x, int nc, int n, int ld) {
   size_t total = (size_t)nc * n;
@@ -402,6 +412,9 @@ void fq_launch_load_states(const double* x, fq_blk<double> out, int nc, int n, i
 }
 void fq_launch_load_states_f32(const double* x, fq_blk<float> out, int nc, int n, int ld, cudaStream_t s) {
   k_load_states<float><<<grid_for((size_t)nc * ld, 256), 256, 0, s>>>((const double2*)x, out.re, out.im, nc, n, ld);
+}
+void fq_launch_basis_rows(double* x, int nc, int n, int j0, cudaStream_t s) {
+  k_basis_rows<<<grid_for((size_t)nc * n, 256), 256, 0, s>>>((double2*)x, nc, n, j0);
 }
 void fq_launch_identity_f64(fq_blk<double> out, int nc, int n, int ld, cudaStream_t s) {
   k_identity<double><<<grid_for((size_t)nc * ld, 256), 256, 0, s>>>(out.re, out.im, nc, n, ld);

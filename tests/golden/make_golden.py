@@ -4,6 +4,12 @@ The paper prints no worked example (its Tables 1-3 are timings and its figures c
 values), so these fixtures are regression anchors of the oracle on the small random-matrix
 workload (GOE N=64, seeds 1/2, f = cos t, T = 2 pi, M = 200) and on a small dimer
 (nb = 40, U nb/J = 2, eps1 = 1.5, omega = 3, M = 100).  Run:  python tests/golden/make_golden.py
+
+`python tests/golden/make_golden.py adjoint1024` writes adjoint1024.txt: the oracle's loss and
+gradient for the gate-fidelity workload at its own size (GOE N = 1024, seeds 6 and 7 for H0 and
+H1, Haar target seed 8, f_m ~ N(1, 0.1^2) seed 9, M = 256 piecewise-constant steps, T = 2 pi,
+bounds frozen from f as in reading R11).  It takes several minutes and about 5 GB of memory (the
+oracle keeps every X_m), so it is a separate target.
 """
 import os
 import sys
@@ -61,7 +67,45 @@ def read(name):
     return out
 
 
+def adjoint1024():
+    import math
+    n, steps = 1024, 256
+    h0, h1 = fi.goe(n, 6), fi.goe(n, 7)
+    w = fi.haar_unitary(n, 8)
+    fm = 1.0 + 0.1 * fi.normal(9, steps)
+    plan = o.plan_piecewise(h0, h1, 2 * math.pi, fm)
+    loss, grad = o.grad_piecewise(h0, h1, w, plan, fm)
+    return plan, loss, grad
+
+
+def write_adjoint(name, plan, loss, grad):
+    with open(os.path.join(HERE, name), "w") as fh:
+        fh.write("# written by tests/golden/make_golden.py adjoint1024 from oracle/ only\n")
+        fh.write(f"R {float(plan.R)!r}\nL {plan.L}\n")
+        fh.write(f"beta {float(plan.beta)!r}\ndelta_e {float(plan.delta_e)!r}\n")
+        fh.write(f"loss {float(loss)!r}\n")
+        for m, g in enumerate(grad):
+            fh.write(f"g {m} {float(g)!r}\n")
+
+
+def read_adjoint(name):
+    out = {"g": []}
+    with open(os.path.join(HERE, name)) as fh:
+        for line in fh:
+            if line.startswith("#"):
+                continue
+            k, *v = line.split()
+            if k == "g":
+                out["g"].append(float(v[1]))
+            else:
+                out[k] = float(v[0])
+    return out
+
+
 if __name__ == "__main__":
-    write("goe64.txt", *goe64())
-    write("dimer40.txt", *dimer40())
+    if sys.argv[1:] == ["adjoint1024"]:
+        write_adjoint("adjoint1024.txt", *adjoint1024())
+    else:
+        write("goe64.txt", *goe64())
+        write("dimer40.txt", *dimer40())
     print("written")

@@ -236,3 +236,40 @@ def test_ozaki_grad_directional_fd(fq):
     fd = (lp.item() - lm.item()) / (2 * d)
     gv = float(g.cpu().numpy() @ v)
     assert abs(fd - gv) <= 1e-6 * abs(gv)
+
+
+# ------------------------------------------------------------------ the gradient workload at its size
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["FQ_FP64", "FQ_OZAKI", "FQ_BF16X3", "FQ_BF16X6"])
+def test_grad_config5_full_size_vs_stored_oracle(fq, prec):
+    """The gate-fidelity workload at its own size (GOE N = 1024, seeds 6-9, M = 256 piecewise
+    steps, T = 2 pi, checkpoints every 16) against the oracle's loss and gradient, computed once
+    by tests/golden/make_golden.py adjoint1024 (oracle only).  FP64 and the FP64 emulation are
+    held to 1e-9 of max |g| and the loss to 1e-11; the split precisions to their arithmetic bound
+    (split_grad_tol) with the loss to the forward split bound."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "make_golden", os.path.join(os.path.dirname(__file__), "golden", "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    ref = mg.read_adjoint("adjoint1024.txt")
+    ref_g = np.array(ref["g"])
+    a = fi.config_adjoint()
+    assert a.h0.shape[0] == 1024 and len(a.f) == 256 == len(ref_g)
+    plan = fq.Plan.piecewise(a.h0, a.h1, a.f, period=a.period, checkpoint_stride=16, precision=getattr(fq, prec))
+    assert plan.info.L == int(ref["L"])
+    loss, g = plan.grad(cuda(a.f), cuda(a.target.astype(np.complex128)))
+    assert plan.check_status() == fq.FQ_OK
+    g = g.cpu().numpy()
+    err = np.max(np.abs(g - ref_g))
+    lerr = abs(float(loss.item()) - ref["loss"])
+    print(f"config-5 gradient {prec}: max err {err:.2e} (max |g| {np.max(np.abs(ref_g)):.2e}), loss err {lerr:.1e}")
+    if prec in ("FQ_FP64", "FQ_OZAKI"):
+        assert lerr <= 1e-11
+        assert err <= 1e-9 * np.max(np.abs(ref_g))
+    else:
+        eps = 2.0 ** -17 if prec == "FQ_BF16X3" else 2.0 ** -23
+        assert err <= split_grad_tol(plan, a.h1, eps, ref["loss"])
+        M, R, L = plan.info.steps, plan.info.R, plan.info.L
+        assert lerr <= 4 * (2 * M * R * eps + 4 * math.sqrt(M * L) * eps)

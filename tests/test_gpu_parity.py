@@ -354,6 +354,36 @@ def test_column_slices_bitwise_and_deterministic(fq, case):
         assert torch.equal(X.transpose(0, 1), U[:, a:b])
 
 
+@pytest.mark.parametrize("case", ["resident", "dfl", "dense64", "split"])
+def test_column_blocks_assemble_build_UT(fq, case):
+    """floquet_build_UT_columns (one rank's share of the column split, §5): the uneven blocks a
+    2- or 3-rank split gives, written into their slots of one gather buffer, are U_T in
+    column-major order, bit for bit the single-call build; out-of-range blocks are refused."""
+    import torch
+    from paper_1508_07621_gb300 import shard
+    if case in ("resident", "dfl"):
+        d = fi.config_dimer(nb=700, steps=40)
+        plan = dimer_plan(fq, d, 1 if case == "resident" else 4, 2 if case == "resident" else 3)
+        n = d.n
+    else:
+        n = 130
+        h0, h1 = fi.goe(n, 2401), fi.goe(n, 2402)
+        plan = fq.Plan.dense(h0, h1, omega=1.3, f_ac=1.1, steps=10, precision=0 if case == "dense64" else fq.FQ_BF16X3)
+    U = plan.build_UT()
+    for world in (2, 3):
+        buf = torch.full((world * -(-n // world), n), float("nan"), dtype=torch.complex128, device="cuda")
+        ws = fq.workspace(fq.floquet_columns_workspace_size(plan.handle, -(-n // world)))
+        for r in range(world):
+            j0, j1, _ = shard.column_block(n, r, world)
+            if j1 > j0:
+                fq.floquet_build_UT_columns(plan.handle, j0, j1 - j0, shard.slot(buf, r, world), ws)
+        assert plan.check_status() == fq.FQ_OK
+        assert torch.equal(buf[:n].transpose(0, 1), U)
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_build_UT_columns(plan.handle, n - 2, 3, buf, ws)
+    assert e.value.status == fq.FQ_EINVAL
+
+
 # ------------------------------------------------------------------ dense FP64, resident kernel
 @pytest.mark.parametrize("n", [1, 5, 32, 33, 64, 65, 100, 128])
 def test_dense_fp64_resident_kernel(fq, n):

@@ -471,3 +471,23 @@ def test_expect_tridiag_stationary_states():
     lam, v = eigh_tridiagonal(a0 * d + a1 * h1d, a0 * off)
     ev = o.expect_tridiag(d, off, h1d, a0, a1, 0.0, fi.Drive(0.2, 1.1, 3.0))
     assert np.max(np.abs(ev(0.8, v.astype(np.complex128)) - lam)) < 1e-11 * np.max(np.abs(lam))
+
+
+def test_adjoint1024_golden_plan_and_format():
+    """The stored oracle gradient of the N = 1024 gate-fidelity workload (written once by
+    tests/golden/make_golden.py adjoint1024, several CPU minutes) belongs to that workload's
+    frozen plan: L, R, beta and Delta E recomputed here (cheap) match the file, and it holds a
+    finite loss in [0, 1] and 256 finite gradient entries."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "make_golden", os.path.join(os.path.dirname(__file__), "golden", "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    g = mg.read_adjoint("adjoint1024.txt")
+    a = fi.config_adjoint()
+    plan = o.plan_piecewise(a.h0, a.h1, a.period, a.f)
+    assert plan.L == int(g["L"])
+    for k in ("R", "beta", "delta_e"):
+        assert abs(getattr(plan, k) - g[k]) <= 1e-12 * abs(g[k])
+    assert 0.0 <= g["loss"] <= 1.0 and len(g["g"]) == 256 and np.all(np.isfinite(g["g"]))
