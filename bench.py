@@ -78,8 +78,9 @@ def parse():
                     help="paper-table1: the matrix size (the rows of the paper's Table 1)")
     ap.add_argument("--precision", choices=["x3", "x6", "ozaki", "fp64", "fp32", "df32"], default=None,
                     help="goe4096 / adjoint / batch: BF16X3 (default), BF16X6, FQ_OZAKI (FP64 emulation) or FP64 "
-                         "(adjoint only); dimer: df32 (double-float, FP64-level; default) or fp32 (resident)")
-    ap.add_argument("--ncu-case", choices=["resident", "stream", "split", "tile", "dfl", "adjoint", "ozaki",
+                         "(adjoint only); dimer: df32 (double-float tiled, FP64-level; default), ozaki (band "
+                         "kernel on the tensor cores, FP64-level) or fp32 (resident)")
+    ap.add_argument("--ncu-case", choices=["resident", "stream", "split", "tile", "dfl", "band", "adjoint", "ozaki",
                                            "dense-resident", "ozaki-grad"],
                     default=None,
                     help="run one small capture case of a kernel twice and exit (for ncu --set full)")
@@ -93,6 +94,8 @@ def run_ncu_case(case):
     split:    dense GOE N = 4096 (seeds 3, 4), BF16X3 tensor-core terms of step 0 on the identity;
     tile:     2048 states through step 0 on the FP64 tiled kernel (0.65 GB of states);
     dfl:      2048 states through step 0 on the double-float tiled kernel (FQ_DF32, 0.65 GB);
+    band:     2048 states through steps 0..1 on the band kernel (FQ_OZAKI: 0.66 GB of double-float
+              states, 0.5 GB of slices);
     adjoint:  the BF16X3 gradient at N = 1024 (seeds 6-9) over the first 16 of its 256 steps;
     ozaki-grad: the same in FP64 emulation (FQ_OZAKI);
     ozaki:    dense GOE N = 2048 (seeds 3, 4; A = 2, omega = 2, M = 64), FQ_OZAKI terms of step 0 on
@@ -143,11 +146,11 @@ def run_ncu_case(case):
     d = fi.config_dimer(nb=NB, steps=STEPS)
     n = d.n
     kernel = {"resident": fq.FQ_KERNEL_RESIDENT, "stream": fq.FQ_KERNEL_STREAM, "tile": fq.FQ_KERNEL_TILED,
-              "dfl": fq.FQ_KERNEL_TILED}[case]
-    precision = {"tile": fq.FQ_FP64, "dfl": fq.FQ_DF32}.get(case, fq.FQ_FP32)
+              "dfl": fq.FQ_KERNEL_TILED, "band": fq.FQ_KERNEL_BAND}[case]
+    precision = {"tile": fq.FQ_FP64, "dfl": fq.FQ_DF32, "band": fq.FQ_OZAKI}.get(case, fq.FQ_FP32)
     plan = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=d.drive.f_ac,
                            steps=d.steps, precision=precision, kernel=kernel)
-    nc, m_end = (152, 20) if case == "resident" else (2048, 1)
+    nc, m_end = {"resident": (152, 20), "band": (2048, 2)}.get(case, (2048, 1))
     x0 = torch.zeros((nc, n), dtype=torch.complex128, device="cuda")
     x0[torch.arange(nc), torch.arange(nc) * (n // nc)] = 1.0
     ws = fq.workspace(plan.workspace_size(nc))
@@ -344,6 +347,14 @@ DIMER_PATHS = {
     # double-float tiled chain (FP64-level, one launch per step): 4 double-float complex FMAs per
     # element-term, each 15 packed FP32x2 operations (30 FP32 lane operations), against the FP32
     # lane-operation peak
+    # band kernel (FP64-level, FQ_OZAKI): per step the band matrix of the step's polynomial times
+    # every state on the tensor cores in FP64 emulation; 26 flop per element-term of the method
+    # (as the FP32 line counts it) against the measured sustained bf16 peak, with the issued
+    # slice-product rate beside it
+    "ozaki": {"precision": "FQ_OZAKI", "kernel": "FQ_KERNEL_BAND", "dtype": "ozaki (bf16 slices, fp32 sums)",
+              "level": "FP64", "kernel_name": "k_oz_band", "unit": "TFLOP/s", "per_unit": FLOPS_PER_ELEMENT_TERM,
+              "launches_per_step": 3 * STEPS + 3, "tensor": True,
+              "peak_note": "measured sustained cuBLAS bf16 (MEASURED_PEAKS.json)"},
     "df32": {"precision": "FQ_DF32", "kernel": "FQ_KERNEL_TILED", "dtype": "df32 (FP32 pairs, FP64 states)",
              "level": "FP64", "kernel_name": "k_tri_tile_dfl", "unit": "Tops/s",
              "per_unit": DFL_LANE_OPS_PER_ELEMENT_TERM, "launches_per_step": STEPS + 3,
@@ -351,10 +362,26 @@ DIMER_PATHS = {
 }
 
 
+def band_issued_flops(n, nc):
+    """BF16 MMA flops the band kernel issues per step: tiles of 128 states x 64 operator rows, a
+    160-column K window, 21 slice pairs of two N = 128 MMAs."""
+    tiles = -(-nc // 128) * -(-n // 64)
+    return tiles * 21 * 2 * 2.0 * 128 * 128 * 160
+
+
 def dimer_roofline(path, n, steps, L, seconds_per_launch, per_launch_units):
     """Roofline of the dominant dimer kernel: algorithmic work of one launch / its CUDA-event time."""
     work = path["per_unit"] * per_launch_units
     achieved = work / seconds_per_launch / 1e12
+    if path.get("tensor"):
+        peak = measured_peaks()["bf16_sustained"]
+        issued = band_issued_flops(n, n) * per_launch_units / (float(n) * n * L) / seconds_per_launch / 1e12
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "kernel": path["kernel_name"], "work_per_unit": path["per_unit"],
+                "units_per_launch": per_launch_units, "issued_tflops": issued, "issued_frac": issued / peak,
+                "peak_note": path["peak_note"] + " (" + measured_peaks()["source"] + ")",
+                "work_note": "achieved counts the method's 26 flop per element-term (useful work, as the FP32 "
+                             "line); issued counts the BF16 slice products the emulation runs"}
     if path["unit"] == "TFLOP/s":
         peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     else:
@@ -487,7 +514,8 @@ def run_ours(args):
         roofline = dimer_roofline(path, n, d.steps, L, avg / d.steps, per_launch)
         roofline["traffic"] = None
         roofline["traffic_note"] = "see profiles/ for the kernel's DRAM bytes per launch"
-        roofline["launch_seconds_note"] = "mean step time / M: the tiled kernel is >99% of a step"
+        roofline["launch_seconds_note"] = ("mean U_T time / M, which also holds the step's other launches "
+                                           "(their share is in the profiles' launch list)")
     cpu = None
     accuracy = {"unitarity_defect_max": defect_max, "unitarity_defect_fro": defect_fro,
                 "defect_columns": int(sample_cols.numel())}

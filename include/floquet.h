@@ -89,9 +89,11 @@ typedef enum fq_precision {
                            significant bits) on the FP32 pipes; FP64 states in HBM; FP64-level
                            results.  Tridiagonal: tiled kernel (L <= 128); dense: resident
                            kernel (N <= 128, L <= 128); FQ_EUNSUPPORTED otherwise */
-  FQ_OZAKI = 5          /* dense: FP64 emulation on the BF16 tensor cores (Ozaki-style splitting):
-                           six 8-bit fixed-point slices per row, 21 slice products, exact FP32
-                           partial sums combined in double-float; FP64 states; FP64-level results */
+  FQ_OZAKI = 5          /* FP64 emulation on the BF16 tensor cores (Ozaki-style splitting): six
+                           8-bit fixed-point slices per row, 21 slice products, exact FP32 partial
+                           sums combined in double-float; FP64-level results.  Dense: per
+                           Chebyshev term, FP64 states.  Tridiagonal: the band kernel
+                           (FQ_KERNEL_BAND, L <= 47), double-float states */
 } fq_precision;
 
 typedef enum fq_drive_kind {
@@ -107,10 +109,16 @@ typedef enum fq_kernel {
                                (N <= 10240, L <= 128); dense FP64: a cluster of ceil(N/32) CTAs
                                per state runs 64 steps per launch on chip (N <= 128, L <= 128);
                                FQ_EUNSUPPORTED otherwise */
-  FQ_KERNEL_TILED = 3       /* tridiagonal FP64 or FP32, any N, L <= 128: one launch per step, each
+  FQ_KERNEL_TILED = 3,      /* tridiagonal FP64 or FP32, any N, L <= 128: one launch per step, each
                                CTA runs the step's L products on a segment of one state plus L
                                halo rows a side; FQ_EUNSUPPORTED otherwise.  AUTO picks RESIDENT,
                                then TILED, then STREAM. */
+  FQ_KERNEL_BAND = 4        /* tridiagonal FQ_OZAKI (the only kernel for it; AUTO selects it),
+                               L <= 47: per step the band matrix P_m = e^{-i beta h} sum_k c_k
+                               T_k(Omega~_m) of Eqs. 10-12 (2L+1 diagonals) is formed once, and every
+                               state is multiplied by it on the tensor cores in FP64 emulation
+                               (fixed-point BF16 slices, exact FP32 sums), one windowed product per
+                               step; states are double-float pairs between steps */
 } fq_kernel;
 
 /* Problem statement (Eq. 13, §3): everything floquet_plan_create needs. */

@@ -17,7 +17,7 @@ FQ_OK, FQ_EINVAL, FQ_ENOMEM, FQ_ECUDA, FQ_EBOUND, FQ_ETIMEOUT, FQ_EUNSUPPORTED =
 FQ_DENSE, FQ_TRIDIAG = 0, 1
 FQ_FP64, FQ_FP32, FQ_BF16X3, FQ_BF16X6, FQ_DF32, FQ_OZAKI = 0, 1, 2, 3, 4, 5
 FQ_DRIVE_COS, FQ_DRIVE_PIECEWISE = 0, 1
-FQ_KERNEL_AUTO, FQ_KERNEL_STREAM, FQ_KERNEL_RESIDENT, FQ_KERNEL_TILED = 0, 1, 2, 3
+FQ_KERNEL_AUTO, FQ_KERNEL_STREAM, FQ_KERNEL_RESIDENT, FQ_KERNEL_TILED, FQ_KERNEL_BAND = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "FQ_OK", 1: "FQ_EINVAL", 2: "FQ_ENOMEM", 3: "FQ_ECUDA", 4: "FQ_EBOUND",
                 5: "FQ_ETIMEOUT", 6: "FQ_EUNSUPPORTED"}
 

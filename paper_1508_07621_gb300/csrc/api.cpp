@@ -65,6 +65,8 @@ size_t layout(const fq_plan* p, int nc, int nsteps, void* ws, StateWs* out) {
     w.coeff = c.take<char>(fq_resident_coeff_bytes(n, nsteps));
   } else if (p->path == PATH_TRI_TILE) {
     w.coeff = c.take<char>(fq_tile_workspace(p, nc, nsteps));
+  } else if (p->path == PATH_TRI_BAND) {
+    w.coeff = c.take<char>(fq_band_workspace(p, nc, nsteps));
   } else if (p->path == PATH_DENSE_SPLIT) {
     w.coeff = c.take<char>(fq_split_workspace(p, nc, nullptr, nullptr));
   } else if (p->path == PATH_DENSE_OZAKI) {
@@ -178,6 +180,11 @@ fq_status propagate_impl(fq_plan* p, const double* x0, double* x, int nc, int m_
     if (st != FQ_OK) return st;
     return cuda_ok(cudaGetLastError(), "tiled tridiagonal chain");
   }
+  if (p->path == PATH_TRI_BAND) {
+    st = fq_band_propagate(p, x0, x, nc, m_begin, m_end, identity, transpose_out, w.coeff, s);
+    if (st != FQ_OK) return st;
+    return cuda_ok(cudaGetLastError(), "band chain");
+  }
   if (p->path == PATH_DENSE_SPLIT) {
     st = fq_split_propagate(p, x0, x, nc, m_begin, m_end, identity, transpose_out, w.coeff, s);
     if (st != FQ_OK) return st;
@@ -266,11 +273,24 @@ fq_status plan_create(fq_plan** out, const fq_problem* prob) {
       fq_set_error("FQ_DF32 runs on the tiled kernel only");
       return FQ_EUNSUPPORTED;
     }
+    if (p->precision == FQ_OZAKI || prob->kernel == FQ_KERNEL_BAND) {
+      if (p->precision != FQ_OZAKI || (prob->kernel != FQ_KERNEL_AUTO && prob->kernel != FQ_KERNEL_BAND)) {
+        fq_set_error("the band kernel runs FQ_OZAKI tridiagonal plans, and they run on it only");
+        return FQ_EUNSUPPORTED;
+      }
+      if (!fq_band_supported(p->L)) {
+        fq_set_error("band kernel needs L <= 47 (L = %d): more steps per period lower L", p->L);
+        return FQ_EUNSUPPORTED;
+      }
+    }
     switch (prob->kernel) {
       case FQ_KERNEL_STREAM: p->path = PATH_TRI_STREAM; break;
       case FQ_KERNEL_RESIDENT: p->path = PATH_TRI_RESIDENT; break;
       case FQ_KERNEL_TILED: p->path = PATH_TRI_TILE; break;
-      default: p->path = res_ok ? PATH_TRI_RESIDENT : (tile_ok ? PATH_TRI_TILE : PATH_TRI_STREAM);
+      case FQ_KERNEL_BAND: p->path = PATH_TRI_BAND; break;
+      default:
+        p->path = p->precision == FQ_OZAKI ? PATH_TRI_BAND
+                                           : (res_ok ? PATH_TRI_RESIDENT : (tile_ok ? PATH_TRI_TILE : PATH_TRI_STREAM));
     }
   } else {
     p->path = (p->precision == FQ_FP64 || p->precision == FQ_DF32)

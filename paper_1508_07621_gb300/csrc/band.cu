@@ -1,0 +1,633 @@
+// The tridiagonal chain as one banded product per step on the tensor cores, in FP64 emulation
+// (FQ_OZAKI with a tridiagonal plan).
+//
+// Step m applies X_m = P_m X_{m-1} with P_m = e^{-i beta h} sum_k c_k T_k(Omega~_m), c_k =
+// (-i)^k a_k (Eqs. 10 and 12).  Omega~_m is tridiagonal, so T_k(Omega~_m) has bandwidth k and the
+// step's whole polynomial is a band matrix with 2L + 1 diagonals.  Instead of L sparse products on
+// every state, each step
+//   1. forms the rows of P_m once (k_band_rows): in the real gauge frame Omega~ = D Omega' D^+
+//      (gauge.cuh), row i of P(Omega') is P(Omega') e_i (P(Omega') is complex symmetric), computed
+//      by Clenshaw's recurrence in double-float arithmetic on a 96-row window around i, which holds
+//      its support i +- L; then P_m[i][k] = e^{-i beta h} e^{i theta_i} v_k e^{-i theta_k} in FP64;
+//   2. cuts the state rows into fixed-point BF16 slices (k_band_slice, as FQ_OZAKI does for dense
+//      operators, ozaki_core.cuh);
+//   3. multiplies every state by the band on the tensor cores (k_oz_band): a tile of 64 operator
+//      rows [i0, i0 + 64) needs only the state columns [i0 - 48, i0 + 112), so its K loop is that
+//      160-wide window instead of all N columns.  The 21 slice pairs sum exactly in FP32 tensor
+//      memory over the whole window (3 pairs x 2^14 x 320 products < 2^24 units), so one drain
+//      per tile suffices, and the epilogue writes the new state as double-float pairs with FP32
+//      instructions only (GB300's FP64 rate is far below its FP32 and tensor rates).
+// The product is the same polynomial the Chebyshev recurrence applies, so the result agrees with
+// the plain chain to the emulation's rounding (48 bits per slice product).  Needs L <= 47.
+//
+// Layouts (all in the caller's workspace):
+//   states     double-float [nc][npl] float4 (re_hi, re_lo, im_hi, im_lo), npl = N rounded to 128
+//   left       OZ_S slices [ncp][2 npl] BF16: re in columns [0, npl), im in [npl, 2 npl)
+//   right      OZ_S slices [3 nrows][160] BF16: per 64-row block b the rows -Im, Re, Im of P_m,
+//              column c = k - (64 b - 48)
+//   cf, rot    per step (2 d, 2 e') and (cos, sin) theta of the gauge frame, FP64, [nsteps][nrows]
+#include <atomic>
+
+#include "gauge.cuh"
+#include "ozaki_core.cuh"
+
+namespace {
+
+constexpr int BAND_LANE_ROWS = 3;                       // window rows per lane
+constexpr int BAND_WIN = 32 * BAND_LANE_ROWS;           // 96-row window, centre at position 48
+constexpr int BAND_MAXL = BAND_WIN / 2 - 1;             // support i +- L inside the window
+constexpr int BAND_KH = 48;                             // K half-width of a 64-row block's window
+constexpr int BAND_KW = OZ_BN + 2 * BAND_KH;            // 160 columns of K per tile
+constexpr int BAND_NK = BAND_KW / OZ_BKE;               // 10 K stages per tile
+constexpr int BAND_ROWS_PER_CTA = 8;                    // one warp per operator row
+static_assert(BAND_KH >= BAND_MAXL, "the K window covers every row's band");
+static_assert(3LL * (1 << 14) * (2 * BAND_KW) < (1LL << 24), "one drain per tile keeps the exact sums exact");
+
+struct BandCoef {
+  dfl c[BAND_MAXL + 1];  // c_k = c[k] for even k, i c[k] for odd k
+};
+
+__device__ __forceinline__ dflc shfl_dflc(dflc a, int delta, bool up) {
+  dflc r;
+  if (up) {
+    r.h.x = __shfl_up_sync(0xffffffffu, a.h.x, delta);
+    r.h.y = __shfl_up_sync(0xffffffffu, a.h.y, delta);
+    r.l.x = __shfl_up_sync(0xffffffffu, a.l.x, delta);
+    r.l.y = __shfl_up_sync(0xffffffffu, a.l.y, delta);
+  } else {
+    r.h.x = __shfl_down_sync(0xffffffffu, a.h.x, delta);
+    r.h.y = __shfl_down_sync(0xffffffffu, a.h.y, delta);
+    r.l.x = __shfl_down_sync(0xffffffffu, a.l.x, delta);
+    r.l.y = __shfl_down_sync(0xffffffffu, a.l.y, delta);
+  }
+  return r;
+}
+
+// One Clenshaw update on the lane's three window rows: out = (2 Omega' x) - out (HALF: the
+// closing Omega' x - out), plus c_k at the centre row (c = cc or i cc for IM), double-float.
+template <bool IM, bool HALF>
+__device__ __forceinline__ void band_apply(const dflc (&x)[BAND_LANE_ROWS], dflc (&out)[BAND_LANE_ROWS],
+                                           const dfl (&d)[BAND_LANE_ROWS], const dfl (&e)[BAND_LANE_ROWS], dfl el0,
+                                           dfl cc, int lane) {
+  const dflc z = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  dflc left = shfl_dflc(x[BAND_LANE_ROWS - 1], 1, true);
+  dflc right = shfl_dflc(x[0], 1, false);
+  if (lane == 0) left = z;    // beyond the window: never reached by the support (L <= 47)
+  if (lane == 31) right = z;
+#pragma unroll
+  for (int q = 0; q < BAND_LANE_ROWS; ++q) {
+    const dflc xm = q == 0 ? left : x[q - 1];
+    const dflc xp = q == BAND_LANE_ROWS - 1 ? right : x[q + 1];
+    dfl dq = d[q], el = q == 0 ? el0 : e[q - 1], eh = e[q];
+    if (HALF) {  // the stored operator is 2 Omega'; halving is exact
+      dq = {0.5f * dq.h, 0.5f * dq.l};
+      el = {0.5f * el.h, 0.5f * el.l};
+      eh = {0.5f * eh.h, 0.5f * eh.l};
+    }
+    dflc acc = dflc_fma(dq, x[q], dflc_fma(el, xm, dflc_fma(eh, xp, dflc_neg(out[q]))));
+    if (q == 0 && lane == BAND_WIN / 2 / BAND_LANE_ROWS) {  // centre row: + c_k e_i
+      const dflc c = IM ? dflc{make_float2(0.f, cc.h), make_float2(0.f, cc.l)}
+                        : dflc{make_float2(cc.h, 0.f), make_float2(cc.l, 0.f)};
+      acc = dflc_add(acc, c);
+    }
+    out[q] = acc;
+  }
+}
+
+// Rows i < nrows of P_m into the right operand slices and their exponents et[i] (rows >= n are
+// zero); one warp per row.  cf, rot: the step's gauge tables (row stride irrelevant: row k).
+__global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
+    k_band_rows(const double2* __restrict__ cf, const double2* __restrict__ rot, int n, int nrows, int L,
+                BandCoef coef, double ph_re, double ph_im, size_t rstride, __nv_bfloat16* __restrict__ right,
+                int* __restrict__ et) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * BAND_ROWS_PER_CTA + (threadIdx.x >> 5);
+  if (i >= nrows) return;  // whole warp
+  const bool live = i < n;
+  const int w0 = i - BAND_WIN / 2;  // row of window position 0
+  const dfl zd = {0.f, 0.f};
+  const dflc zc = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  dfl d[BAND_LANE_ROWS], e[BAND_LANE_ROWS];
+  dflc A[BAND_LANE_ROWS], B[BAND_LANE_ROWS];
+#pragma unroll
+  for (int q = 0; q < BAND_LANE_ROWS; ++q) {
+    const int k = w0 + BAND_LANE_ROWS * lane + q;
+    if (live && k >= 0 && k < n) {
+      const double2 c = cf[k];
+      d[q] = dfl_of(c.x);
+      e[q] = dfl_of(c.y);  // 2 Omega'[k+1][k] (0 for the last row)
+    } else {
+      d[q] = zd;
+      e[q] = zd;
+    }
+    A[q] = zc;
+    B[q] = zc;
+  }
+  dfl el0;
+  el0.h = __shfl_up_sync(0xffffffffu, e[BAND_LANE_ROWS - 1].h, 1);
+  el0.l = __shfl_up_sync(0xffffffffu, e[BAND_LANE_ROWS - 1].l, 1);
+  if (lane == 0) el0 = (live && w0 >= 1 && w0 - 1 < n) ? dfl_of(cf[w0 - 1].y) : zd;
+
+  if (live) {
+    // b_L = c_L e_i, b_{L+1} = 0; then b_k = c_k e_i + 2 Omega' b_{k+1} - b_{k+2}
+    if (lane == BAND_WIN / 2 / BAND_LANE_ROWS) {
+      const dfl cL = coef.c[L];
+      A[0] = (L & 1) ? dflc{make_float2(0.f, cL.h), make_float2(0.f, cL.l)}
+                     : dflc{make_float2(cL.h, 0.f), make_float2(cL.l, 0.f)};
+    }
+    int k = L - 1;
+    while (k >= 2) {
+      if (k & 1) band_apply<true, false>(A, B, d, e, el0, coef.c[k], lane);
+      else band_apply<false, false>(A, B, d, e, el0, coef.c[k], lane);
+      --k;
+      if (k & 1) band_apply<true, false>(B, A, d, e, el0, coef.c[k], lane);
+      else band_apply<false, false>(B, A, d, e, el0, coef.c[k], lane);
+      --k;
+    }
+    if (k == 1) {  // b_1 into B, then the sum c_0 e_i + Omega' b_1 - b_2 into A
+      band_apply<true, false>(A, B, d, e, el0, coef.c[1], lane);
+      band_apply<false, true>(B, A, d, e, el0, coef.c[0], lane);
+    } else {  // b_1 in A, b_2 in B: the sum into B, then moved to A
+      band_apply<false, true>(A, B, d, e, el0, coef.c[0], lane);
+#pragma unroll
+      for (int q = 0; q < BAND_LANE_ROWS; ++q) A[q] = B[q];
+    }
+  }
+  // P_m[i][k] = e^{-i beta h} e^{i theta_i} v_k e^{-i theta_k} in FP64, and the row's scale
+  double vr[BAND_LANE_ROWS], vi[BAND_LANE_ROWS];
+  unsigned long long key = 0;
+  const double2 ri = live ? rot[i] : make_double2(1.0, 0.0);
+  const double wr = ph_re * ri.x - ph_im * ri.y, wi = ph_re * ri.y + ph_im * ri.x;  // e^{-i beta h} e^{i theta_i}
+#pragma unroll
+  for (int q = 0; q < BAND_LANE_ROWS; ++q) {
+    const int k = w0 + BAND_LANE_ROWS * lane + q;
+    vr[q] = vi[q] = 0.0;
+    if (live && k >= 0 && k < n) {
+      const double2 rk = rot[k];
+      const double ur = wr * rk.x + wi * rk.y, ui = wi * rk.x - wr * rk.y;  // times e^{-i theta_k}
+      const double sr = (double)A[q].h.x + (double)A[q].l.x, si = (double)A[q].h.y + (double)A[q].l.y;
+      vr[q] = ur * sr - ui * si;
+      vi[q] = ur * si + ui * sr;
+    }
+    const unsigned long long a = abs_key(vr[q]), b = abs_key(vi[q]);
+    key = a > key ? a : key;
+    key = b > key ? b : key;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, key, o);
+    key = w > key ? w : key;
+  }
+  const int E = oz_exponent(key);
+  const int r = i % OZ_BN;
+  const size_t rb = (size_t)(3 * OZ_BN) * (i / OZ_BN) + r;  // row of -Im; Re and Im follow
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+#pragma unroll
+  for (int q = 0; q < BAND_LANE_ROWS; ++q) {
+    __nv_bfloat16 sr[OZ_S], si[OZ_S];
+    oz_digits(vr[q], E, sr);
+    oz_digits(vi[q], E, si);
+    const size_t c = (size_t)(BAND_LANE_ROWS * lane + q + r);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+      __nv_bfloat16* base = right + s * rstride + c;
+      base[rb * BAND_KW] = __hneg(si[s]);
+      base[(rb + OZ_BN) * BAND_KW] = sr[s];
+      base[(rb + 2 * OZ_BN) * BAND_KW] = si[s];
+    }
+  }
+  // the row's other columns of the tile window: [0, r) and [r + 96, 160)
+#pragma unroll
+  for (int zz = 0; zz < 2; ++zz) {
+    const int z = lane + 32 * zz;
+    const size_t c = (size_t)(z < r ? z : z + BAND_WIN);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+      __nv_bfloat16* base = right + s * rstride + c;
+      base[rb * BAND_KW] = zero;
+      base[(rb + OZ_BN) * BAND_KW] = zero;
+      base[(rb + 2 * OZ_BN) * BAND_KW] = zero;
+    }
+  }
+  if (lane == 0) et[i] = E;
+}
+
+// 48-bit fixed-point value of an FP32 number relative to the scale 2^E: round(x 2^(48 - E)) from
+// the bit pattern (x = m 2^(b - 150), so the shift is 102 + E - b), integer work only.  Needs
+// |x| < 2^(E - 1), so a left shift is at most 23 bits; zero and subnormal inputs give 0.
+__device__ __forceinline__ long long fixed48_f32(float x, int E) {
+  const unsigned int bits = __float_as_uint(x);
+  const int b = (int)((bits >> 23) & 0xFF);
+  if (b == 0) return 0;
+  const long long m = (long long)((bits & 0x7FFFFFu) | 0x800000u);
+  const int sh = 102 + E - b;
+  long long R;
+  if (sh <= 0) R = m << (-sh);
+  else if (sh >= 64) R = 0;
+  else R = (m + (1ll << (sh - 1))) >> sh;
+  return (bits >> 31) ? -R : R;
+}
+
+// Left slices of double-float state rows: one CTA per row j of the padded block (rows >= nc and
+// columns >= n are zero).  R = fixed(hi) + fixed(lo) is within one unit of the pair's value.
+__global__ void k_band_slice(const float4* __restrict__ x, int n, int ld, int nc, int npl, size_t astride,
+                             __nv_bfloat16* __restrict__ left, int* __restrict__ es) {
+  __shared__ unsigned long long red[32];
+  const int j = blockIdx.x;
+  unsigned long long m = 0;
+  if (j < nc)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const float4 v = x[(size_t)j * ld + k];
+      // |hi| as an ordered key (FP32 bit pattern; no FP64 conversion): the row maximum of |hi|
+      // bounds |hi + lo| below 2^(E-1) as well (the exponent has a factor 2 to spare)
+      const unsigned long long a = __float_as_uint(v.x) & 0x7FFFFFFFu, b = __float_as_uint(v.z) & 0x7FFFFFFFu;
+      m = a > m ? a : m;
+      m = b > m ? b : m;
+    }
+  const unsigned long long mk = block_max_key(m, red);
+  // E = (unbiased exponent of the maximum) + 2, as oz_exponent for FP64 keys
+  const int E = mk == 0 ? 0 : (int)(mk >> 23) - 127 + 2;
+  __nv_bfloat16* row = left + (size_t)j * 2 * npl;
+  for (int k0 = 4 * threadIdx.x; k0 < npl; k0 += 4 * blockDim.x) {
+    __nv_bfloat16 sr[4][OZ_S], si[4][OZ_S];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j < nc && k0 + u < n) v = x[(size_t)j * ld + k0 + u];
+      oz_digits_fixed(fixed48_f32(v.x, E) + fixed48_f32(v.y, E), sr[u]);
+      oz_digits_fixed(fixed48_f32(v.z, E) + fixed48_f32(v.w, E), si[u]);
+    }
+#pragma unroll
+    for (int q = 0; q < OZ_S; ++q) {
+      *reinterpret_cast<uint2*>(row + q * astride + k0) = pack4(sr[0][q], sr[1][q], sr[2][q], sr[3][q]);
+      *reinterpret_cast<uint2*>(row + q * astride + npl + k0) = pack4(si[0][q], si[1][q], si[2][q], si[3][q]);
+    }
+  }
+  if (threadIdx.x == 0) es[j] = E;
+}
+
+struct BandEpi {
+  float4* out;     // X_m, double-float [nc][ld]
+  const int* es;   // row exponents of the left slices
+  const int* et;   // row exponents of the right slices
+  int n, nc, ld;
+  float bound2;
+  unsigned int* status;
+};
+
+// The banded product X_m[j][i] = sum_{k in window(i)} X_{m-1}[j][k] P_m[i][k] on 128-state x
+// 64-row tiles, persistent: one CTA per SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// in state-block-major order (co-running CTAs share a state block's slices in L2).  Warp 0 streams
+// TMA stages (K = 16 each, 32-byte swizzle), warp 1 issues the MMAs of the 21 slice pairs into the
+// four accumulators (512 tensor-memory columns), warps 2-17 drain them once per tile into
+// double-float registers, release the tensor memory and write the tile while the next tile's MMAs
+// run.  Every wait is bounded; a wait that gives up records FQ_BIT_TIMEOUT, drains this CTA's own
+// copies and MMAs, frees tensor memory and returns.
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_oz_band(const __grid_constant__ OzMaps maps, int tiles_j, int tiles_i, int npl, BandEpi e) {
+  using Cfg = OzCfg;
+  constexpr int STAGES = Cfg::STAGES;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * Cfg::STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 3);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t tfull = smem_u32(bars + 2 * STAGES), tempty = smem_u32(bars + 2 * STAGES + 1);
+  const uint32_t done = smem_u32(bars + 2 * STAGES + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = tiles_i * tiles_j;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, OZ_EPI_WARPS);
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(OZ_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------- TMA producer
+      int g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int j0 = (t / tiles_i) * BM, i0 = (t % tiles_i) * OZ_BN;
+        for (int kb = 0; kb < BAND_NK; ++kb, ++g) {
+          const int s = g % STAGES;
+          if (g >= STAGES && !(ok = mbar_wait(empty0 + 8 * s, ((g / STAGES) - 1) & 1))) break;
+          if (*(volatile int*)abort_flag) {
+            ok = false;
+            break;
+          }
+          const uint32_t st = base + s * Cfg::STAGE_BYTES;
+          const uint32_t bar = full0 + 8 * s;
+          mbar_expect_tx(bar, Cfg::STAGE_BYTES);
+          const int kx = i0 - BAND_KH + kb * OZ_BKE;  // multiple of 16 columns; negative at the first block
+#pragma unroll
+          for (int q = 0; q < OZ_S; ++q) {
+            tma_load_2d(st + (2 * q) * OZ_A_BYTES, &maps.a[q], bar, kx, j0);             // re
+            tma_load_2d(st + (2 * q + 1) * OZ_A_BYTES, &maps.a[q], bar, npl + kx, j0);   // im
+            tma_load_2d(st + 2 * OZ_S * OZ_A_BYTES + q * Cfg::R_BYTES, &maps.r[q], bar, kb * OZ_BKE, 3 * i0);
+          }
+        }
+      }
+      if (!ok) {
+        atomicExch(abort_flag, 1);
+        atomicOr(e.status, FQ_BIT_TIMEOUT);
+      }
+      for (int q = max(0, g - STAGES); q < g; ++q) mbar_wait(full0 + 8 * (q % STAGES), (q / STAGES) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------- MMA issuer
+      constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * OZ_BN) >> 3) << 17) |
+                                 ((uint32_t)(BM >> 4) << 24);
+      int g = 0, it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+        if (it > 0 && !(ok = mbar_wait(tempty, (it - 1) & 1))) break;  // the previous tile is drained
+        tc_fence_after();
+        for (int kb = 0; kb < BAND_NK; ++kb, ++g) {
+          const int s = g % STAGES;
+          ok = mbar_wait(full0 + 8 * s, (g / STAGES) & 1);
+          if (!ok || *(volatile int*)abort_flag) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = base + s * Cfg::STAGE_BYTES;
+          const uint64_t d0 = oz_desc(st);
+#pragma unroll
+          for (int p = 0; p < OZ_PAIRS; ++p) {
+            int a, b;
+            oz_pair(p, a, b);
+            const int grp = a + b < 3 ? a + b : 3;
+            const bool lead = p == 0 || p == 1 || p == 3 || p == 6;  // first pair of each accumulator
+            const uint32_t acc = tmem + (uint32_t)grp * (2 * OZ_BN);
+            const uint32_t rb = 2 * OZ_S * OZ_A_BYTES + b * Cfg::R_BYTES;
+            const uint32_t first = (kb == 0 && lead) ? 0u : 1u;
+            mma_bf16(acc, d0 + (uint64_t)(((2 * a) * OZ_A_BYTES) >> 4), d0 + (uint64_t)((rb + OZ_BN * OZ_ROWB) >> 4),
+                     idesc, first);  // re . [Re; Im]
+            mma_bf16(acc, d0 + (uint64_t)(((2 * a + 1) * OZ_A_BYTES) >> 4), d0 + (uint64_t)(rb >> 4), idesc,
+                     1u);            // im . [-Im; Re]
+          }
+          mma_commit(empty0 + 8 * s);
+        }
+        if (!ok) break;
+        mma_commit(tfull);
+      }
+      if (!ok) {
+        atomicExch(abort_flag, 1);
+        atomicOr(e.status, FQ_BIT_TIMEOUT);
+      }
+      mma_commit(done);
+      mbar_wait(done, 0);
+    }
+  } else {  // ---------------- drain and epilogue warps 2-17
+    const int quarter = warp & 3, part = (warp - 2) >> 2;
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(part * 16);
+    bool bad = false, ok = true;
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int j0 = (t / tiles_i) * BM, i0 = (t % tiles_i) * OZ_BN;
+      bool go = mbar_wait(tfull, it & 1);
+      tc_fence_after();
+      go = __all_sync(0xffffffffu, go && !*(volatile int*)abort_flag);
+      if (!go) {
+        ok = false;
+        break;
+      }
+      float2 hr[8], lr[8], hi[8], li[8];  // double-float sums of columns (2p, 2p + 1)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) hr[q] = lr[q] = hi[q] = li[q] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int grp = 0; grp < 4; ++grp) {
+#pragma unroll
+        for (int part_im = 0; part_im < 2; ++part_im) {
+          float v[16];
+          tmem_ld16(trow + grp * (2 * OZ_BN) + part_im * OZ_BN, v);
+          tmem_wait_ld();
+          float2* h = part_im ? hi : hr;
+          float2* l = part_im ? li : lr;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float2 w = make_float2(v[2 * q], v[2 * q + 1]);
+            if (grp < 3) dd_add2(h[q], l[q], w);
+            else l[q] = __fadd2_rn(l[q], w);  // below 2^-24 of the leading sum: the low word carries it
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty);  // the next tile's MMAs may start
+      const int j = j0 + quarter * 32 + lane;
+      if (j < e.nc) {
+        const int ej = e.es[j];
+        float4* orow = e.out + (size_t)j * e.ld;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int i = i0 + part * 16 + c;
+          if (i < e.n) {
+            int ex = ej + e.et[i];
+            ex = ex < -126 ? -126 : (ex > 127 ? 127 : ex);
+            const float sc = __int_as_float((127 + ex) << 23);
+            const float2 H = hr[c >> 1], Lr = lr[c >> 1], Hi = hi[c >> 1], Li = li[c >> 1];
+            const float rh0 = ((c & 1) ? H.y : H.x) * sc, rl0 = ((c & 1) ? Lr.y : Lr.x) * sc;
+            const float ih0 = ((c & 1) ? Hi.y : Hi.x) * sc, il0 = ((c & 1) ? Li.y : Li.x) * sc;
+            const float rh = __fadd_rn(rh0, rl0), ih = __fadd_rn(ih0, il0);  // renormalise the pairs
+            const float rl = __fsub_rn(rl0, __fsub_rn(rh, rh0)), il = __fsub_rn(il0, __fsub_rn(ih, ih0));
+            bad |= !(rh * rh + ih * ih <= e.bound2);
+            orow[i] = make_float4(rh, rl, ih, il);
+          }
+        }
+      }
+    }
+    if (!ok) {
+      atomicExch(abort_flag, 1);
+      atomicOr(e.status, FQ_BIT_TIMEOUT);
+    }
+    if (bad) atomicOr(e.status, FQ_BIT_BOUND);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
+  }
+}
+
+// complex128 rows (or the identity when x0 is NULL) into double-float rows [nc][ld], zero beyond n
+__global__ void k_band_load(const double2* __restrict__ x0, float4* __restrict__ x, int nc, int n, int ld) {
+  const size_t total = (size_t)nc * ld;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(q / ld), k = (int)(q % ld);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < n) {
+      if (x0) {
+        const double2 a = x0[(size_t)r * n + k];
+        const dfl re = dfl_of(a.x), im = dfl_of(a.y);
+        v = make_float4(re.h, re.l, im.h, im.l);
+      } else if (k == r) {
+        v.x = 1.f;
+      }
+    }
+    x[q] = v;
+  }
+}
+
+// double-float rows into complex128 rows [nc][n]
+__global__ void k_band_store(const float4* __restrict__ x, double2* __restrict__ out, int nc, int n, int ld) {
+  const size_t total = (size_t)nc * n;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(q / n), k = (int)(q % n);
+    const float4 v = x[(size_t)r * ld + k];
+    out[q] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+  }
+}
+
+// U[i][j] = X_j[i] (the n x n block of states as rows -> U_T), 32 x 32 tiles through shared memory
+__global__ void k_band_store_t(const float4* __restrict__ x, double2* __restrict__ u, int n, int ld) {
+  __shared__ double2 tile[32][33];
+  const int j0 = blockIdx.y * 32, i0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + r, i = i0 + threadIdx.x;
+    if (j < n && i < n) {
+      const float4 v = x[(size_t)j * ld + i];
+      tile[r][threadIdx.x] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, j = j0 + threadIdx.x;
+    if (i < n && j < n) u[(size_t)i * n + j] = tile[threadIdx.x][r];
+  }
+}
+
+struct BandWs {
+  double2* cf;
+  double2* rot;
+  __nv_bfloat16* right;
+  int* et;
+  __nv_bfloat16* left;
+  int* es;
+  float4* x[2];
+  int nrows, npl, ncp;
+  size_t rstride, astride;
+};
+
+size_t up256b(size_t v) { return (v + 255) & ~(size_t)255; }
+
+size_t band_layout(const fq_plan* p, int nc, int nsteps, void* base, BandWs* out) {
+  BandWs w{};
+  w.nrows = (p->n + OZ_BN - 1) / OZ_BN * OZ_BN;
+  w.npl = (p->n + 127) & ~127;
+  w.ncp = (nc + BM - 1) / BM * BM;
+  w.rstride = (size_t)3 * w.nrows * BAND_KW;
+  w.astride = (size_t)w.ncp * 2 * w.npl;
+  char* b = (char*)base;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* q = b ? b + off : nullptr;
+    off += up256b(bytes);
+    return q;
+  };
+  w.cf = (double2*)take(sizeof(double2) * (size_t)nsteps * w.nrows);
+  w.rot = (double2*)take(sizeof(double2) * (size_t)nsteps * w.nrows);
+  w.right = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.rstride);
+  w.et = (int*)take(sizeof(int) * w.nrows);
+  w.left = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.astride);
+  w.es = (int*)take(sizeof(int) * w.ncp);
+  for (int q = 0; q < 2; ++q) w.x[q] = (float4*)take(sizeof(float4) * (size_t)nc * w.npl);
+  if (out) *out = w;
+  return off;
+}
+
+int band_grid(size_t total) { return (int)std::min<size_t>(std::max<size_t>((total + 255) / 256, 1), 152 * 32); }
+
+}  // namespace
+
+int fq_band_supported(int L) { return L >= 1 && L <= BAND_MAXL; }
+
+size_t fq_band_workspace(const fq_plan* p, int nc, int nsteps) { return band_layout(p, nc, nsteps, nullptr, nullptr); }
+
+fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
+                            int transpose_out, void* ws, cudaStream_t s) {
+  fq_status st = encode_fn();
+  if (st != FQ_OK) return st;
+  const int n = p->n, L = p->L, nsteps = m_end - m_begin;
+  if (!fq_band_supported(L)) {
+    fq_set_error("band kernel needs L <= %d (L = %d)", BAND_MAXL, L);
+    return FQ_EUNSUPPORTED;
+  }
+  BandWs w;
+  band_layout(p, nc, nsteps, ws, &w);
+  OzMaps maps;
+  for (int q = 0; q < OZ_S; ++q) {
+    if ((st = make_map(&maps.a[q], w.left + q * w.astride, w.ncp, 2 * w.npl, BM, OZ_BKE)) != FQ_OK) return st;
+    if ((st = make_map(&maps.r[q], w.right + q * w.rstride, 3 * w.nrows, BAND_KW, 3 * OZ_BN, OZ_BKE)) != FQ_OK)
+      return st;
+  }
+  static std::atomic<unsigned> attr_set{0};
+  if (fq_first_on_device(attr_set)) {
+    cudaError_t e = cudaFuncSetAttribute(k_oz_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OzCfg::SMEM);
+    if (e != cudaSuccess) return fq_cuda_fail(e, "band kernel shared-memory attribute");
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (sms < 1) sms = 152;
+  GaugeArgs ga{p->n, p->steps, p->d_h0, p->d_h0o, p->d_h1, p->d_k, p->d_scal, p->sbeta};
+  k_gauge_tile<double><<<nsteps, GAUGE_NT, 0, s>>>(ga, w.nrows, m_begin, w.cf, w.rot);
+  k_band_load<<<band_grid((size_t)nc * w.npl), 256, 0, s>>>(identity ? nullptr : (const double2*)x0, w.x[0], nc, n,
+                                                            w.npl);
+  BandCoef coef{};
+  for (int k = 0; k <= L; ++k) {
+    const double a = p->cheb[k];
+    const double c = (k & 3) == 0 || (k & 3) == 3 ? a : -a;  // c_k = (-i)^k a_k: c or i c
+    const float h = (float)c;
+    coef.c[k] = {h, (float)(c - (double)h)};
+  }
+  const int tiles_i = (n + OZ_BN - 1) / OZ_BN, tiles_j = w.ncp / BM;
+  const int ntiles = tiles_i * tiles_j;
+  BandEpi e{};
+  e.es = w.es;
+  e.et = w.et;
+  e.n = n;
+  e.nc = nc;
+  e.ld = w.npl;
+  e.bound2 = (float)(1.0 + 1e-6);
+  e.status = p->d_status;
+  int cur = 0;
+  for (int m = 0; m < nsteps; ++m) {
+    k_band_rows<<<(w.nrows + BAND_ROWS_PER_CTA - 1) / BAND_ROWS_PER_CTA, 32 * BAND_ROWS_PER_CTA, 0, s>>>(
+        w.cf + (size_t)m * w.nrows, w.rot + (size_t)m * w.nrows, n, w.nrows, L, coef, p->phase_re, p->phase_im,
+        w.rstride, w.right, w.et);
+    k_band_slice<<<w.ncp, 256, 0, s>>>(w.x[cur], n, w.npl, nc, w.npl, w.astride, w.left, w.es);
+    e.out = w.x[cur ^ 1];
+    k_oz_band<<<std::min(ntiles, sms), OZ_THREADS, OzCfg::SMEM, s>>>(maps, tiles_j, tiles_i, w.npl, e);
+    cur ^= 1;
+  }
+  if (transpose_out) {
+    dim3 g((n + 31) / 32, (n + 31) / 32), b(32, 8);
+    k_band_store_t<<<g, b, 0, s>>>(w.x[cur], (double2*)x, n, w.npl);
+  } else {
+    k_band_store<<<band_grid((size_t)nc * n), 256, 0, s>>>(w.x[cur], (double2*)x, nc, n, w.npl);
+  }
+  cudaError_t e2 = cudaGetLastError();
+  if (e2 != cudaSuccess) return fq_cuda_fail(e2, "band chain");
+  return FQ_OK;
+}

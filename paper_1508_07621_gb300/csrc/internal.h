@@ -25,6 +25,7 @@ enum fq_path : int {
   PATH_TRI_STREAM = 2,    // streaming tridiagonal term kernel (FP32 or FP64)
   PATH_TRI_RESIDENT = 3,  // one CTA per state, whole chain on chip (FP32)
   PATH_TRI_TILE = 5,      // one launch per step, each CTA runs a step's L products on a state segment
+  PATH_TRI_BAND = 7,      // FQ_OZAKI tridiagonal: the step's band polynomial on tcgen05 in FP64 emulation
   PATH_DENSE_OZAKI = 6,   // tcgen05 FP64 emulation (fixed-point BF16 slices, exact FP32 sums) per term
 };
 
@@ -178,6 +179,11 @@ size_t fq_dense_resident_omega_count(int n, int nsteps);
 fq_status fq_dense_resident_chain(const fq_plan* p, double* xr, double* xi, int nc, int m_begin, int m_end,
                                   double* S, double* A, cudaStream_t s);
 size_t fq_tile_workspace(const fq_plan* p, int nc, int nsteps);
+// band.cu: FQ_OZAKI tridiagonal chain (one banded tensor-core product per step)
+int fq_band_supported(int L);
+size_t fq_band_workspace(const fq_plan* p, int nc, int nsteps);
+fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
+                            int transpose_out, void* ws, cudaStream_t s);
 fq_status fq_tile_propagate(fq_plan* p, const double* x0, double* x, int nc, int m_begin, int m_end, int identity,
                             int transpose_out, void* ws, cudaStream_t s);
 size_t fq_resident_coeff_bytes(int n, int steps);

@@ -144,6 +144,23 @@ __device__ __forceinline__ int oz_exponent(unsigned long long key) {
   return e < -960 ? -960 : e;
 }
 
+// Slices of a 48-bit fixed-point value R = r 2^48 (|r| < 1/2): signed 8-bit digits d_q by
+// rounding shifts, slice q = d_q 2^(-8(q+1)) in BF16 (exact: |d_q| <= 128).
+__device__ __forceinline__ void oz_digits_fixed(long long R, __nv_bfloat16 (&s)[OZ_S]) {
+#pragma unroll
+  for (int q = 0; q < OZ_S; ++q) {
+    const int sh = 40 - 8 * q;
+    long long d;
+    if (sh > 0) {
+      d = (R + (1ll << (sh - 1))) >> sh;
+      R -= d << sh;
+    } else {
+      d = R;
+    }
+    s[q] = __float2bfloat16_rn((float)(int)d * __int_as_float((127 - 8 * (q + 1)) << 23));
+  }
+}
+
 // The digits of r = x / 2^E (|r| < 1/2): R = r 2^48 rounded to an integer, then d_q by rounding
 // shifts of 8 bits; slices d_q 2^(-8(q+1)) in BF16.  R comes straight from the bit pattern of x
 // (x = m 2^(b - 1075) with the 53-bit significand m and biased exponent b, so R = m shifted right
@@ -158,18 +175,7 @@ __device__ __forceinline__ void oz_digits(double x, int E, __nv_bfloat16 (&s)[OZ
     R = (long long)((m + (1ull << (sh - 1))) >> sh);
     if (bits >> 63) R = -R;
   }
-#pragma unroll
-  for (int q = 0; q < OZ_S; ++q) {
-    const int sh = 40 - 8 * q;
-    long long d;
-    if (sh > 0) {
-      d = (R + (1ll << (sh - 1))) >> sh;
-      R -= d << sh;
-    } else {
-      d = R;
-    }
-    s[q] = __float2bfloat16_rn((float)(int)d * __int_as_float((127 - 8 * (q + 1)) << 23));
-  }
+  oz_digits_fixed(R, s);
 }
 
 __device__ __forceinline__ unsigned long long block_max_key(unsigned long long v, unsigned long long* red) {

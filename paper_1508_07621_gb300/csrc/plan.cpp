@@ -451,9 +451,8 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_boun
         }
   }
   if (p->precision < FQ_FP64 || p->precision > FQ_OZAKI) { fq_set_error("bad precision %d", p->precision); return FQ_EINVAL; }
-  if (p->format == FQ_TRIDIAG &&
-      (p->precision == FQ_BF16X3 || p->precision == FQ_BF16X6 || p->precision == FQ_OZAKI)) {
-    fq_set_error("tridiagonal format supports FQ_FP64, FQ_FP32 and FQ_DF32");
+  if (p->format == FQ_TRIDIAG && (p->precision == FQ_BF16X3 || p->precision == FQ_BF16X6)) {
+    fq_set_error("tridiagonal format supports FQ_FP64, FQ_FP32, FQ_DF32 and FQ_OZAKI");
     return FQ_EUNSUPPORTED;
   }
   if (p->format == FQ_DENSE && p->precision == FQ_FP32) {
@@ -480,8 +479,8 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_boun
     return FQ_EINVAL;
   }
   plan->tile_n = p->tile_n ? p->tile_n : 128;
-  if (p->kernel < FQ_KERNEL_AUTO || p->kernel > FQ_KERNEL_TILED) {
-    fq_set_error("kernel must be one of FQ_KERNEL_AUTO .. FQ_KERNEL_TILED (got %d)", p->kernel);
+  if (p->kernel < FQ_KERNEL_AUTO || p->kernel > FQ_KERNEL_BAND) {
+    fq_set_error("kernel must be one of FQ_KERNEL_AUTO .. FQ_KERNEL_BAND (got %d)", p->kernel);
     return FQ_EINVAL;
   }
   plan->period = p->period;

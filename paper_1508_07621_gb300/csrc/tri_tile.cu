@@ -32,53 +32,6 @@ constexpr int TILE_EPT = 8;
 constexpr int TILE_ROWS = TILE_NT * TILE_EPT;
 constexpr int TILE_MAXL = 128;
 
-template <typename T> struct V2;
-template <> struct V2<double> { using t = double2; };
-template <> struct V2<float> { using t = float2; };
-struct dfl2 {
-  dfl x, y;
-};
-template <> struct V2<dfl> { using t = dfl2; };
-
-// FP64 value into the kernel's coefficient type
-template <typename T> __device__ __forceinline__ T coeff_of(double x) { return (T)x; }
-template <> __device__ __forceinline__ dfl coeff_of<dfl>(double x) { return dfl_of(x); }
-
-// Block s, step m = m_begin + s: cf[s][k] = (2 d_k, 2 e'_k) and rot[s][k] = (cos, sin) theta_k,
-// theta_k = sum_{j<k} phi_j, for k < ld (rows >= n: zero operator).  The prefix sum runs over
-// chunks of GAUGE_NT rows with a carried offset, so any ld works.
-template <typename T>
-__global__ void __launch_bounds__(GAUGE_NT) k_gauge_tile(GaugeArgs p, int ld, int m_begin, typename V2<T>::t* cf,
-                                                         typename V2<T>::t* rot) {
-  __shared__ double sw[64];
-  __shared__ double chunk_total;
-  const int s = blockIdx.x, m = m_begin + s;
-  typename V2<T>::t* cfs = cf + (size_t)s * ld;
-  typename V2<T>::t* rts = rot + (size_t)s * ld;
-  double carry = 0.0;
-  for (int base = 0; base < ld; base += GAUGE_NT) {
-    const int k = base + threadIdx.x;
-    double er = 0.0, ei = 0.0, ph = 0.0;
-    if (k < ld) {
-      offdiag(p, m, k, er, ei);
-      ph = reduced_arg(er, ei);
-    }
-    const double th = carry + block_exclusive_scan(ph, sw);
-    if (k < ld) {
-      const double d = k < p.n ? p.scal[m] * p.h0d[k] + p.scal[p.M + m] * p.h1d[k] - p.sbeta : 0.0;
-      double sp, cp, st, ct;
-      sincos(ph, &sp, &cp);
-      sincos(th, &st, &ct);
-      cfs[k] = {coeff_of<T>(2.0 * d), coeff_of<T>(2.0 * (er * cp + ei * sp))};
-      rts[k] = {coeff_of<T>(ct), coeff_of<T>(st)};
-    }
-    if (threadIdx.x == GAUGE_NT - 1) chunk_total = th - carry + ph;
-    __syncthreads();
-    carry += chunk_total;
-    __syncthreads();
-  }
-}
-
 template <typename T>
 struct TileCoef {
   T c[TILE_MAXL + 1];  // |c_k|: c_k = c[k] for even k (real, sign included), i c[k] for odd k

@@ -88,7 +88,7 @@ def test_argument_errors(fq):
     with pytest.raises(fq.FloquetError) as e:
         fq.floquet_plan_inspect(prob)
     assert e.value.status == fq.FQ_EUNSUPPORTED
-    for prec in (fq.FQ_BF16X6, fq.FQ_OZAKI):
+    for prec in (fq.FQ_BF16X6,):
         prob, keep = fq.make_problem(4, fq.FQ_TRIDIAG, np.zeros(4), np.zeros(4), 1.0, 2, h0_off=np.zeros(3),
                                      precision=prec)
         with pytest.raises(fq.FloquetError) as e:
@@ -131,7 +131,7 @@ def test_fixed_chebyshev_terms(fq):
     ("steps0", "FQ_EINVAL"), ("period0", "FQ_EINVAL"), ("format9", "FQ_EINVAL"), ("drive9", "FQ_EINVAL"),
     ("piecewise_without_f", "FQ_EINVAL"), ("order5", "FQ_EINVAL"), ("order6_tridiag", "FQ_EUNSUPPORTED"),
     ("order6_piecewise", "FQ_EUNSUPPORTED"), ("tile96", "FQ_EINVAL"), ("dense_fp32", "FQ_EUNSUPPORTED"),
-    ("tridiag_ozaki", "FQ_EUNSUPPORTED"), ("kernel9", "FQ_EINVAL")])
+    ("tridiag_x6", "FQ_EUNSUPPORTED"), ("kernel9", "FQ_EINVAL")])
 def test_problem_validation(fq, case, status):
     """Every rejected problem fails in host planning with its status and a message, before any
     device work."""
@@ -164,7 +164,7 @@ def test_problem_validation(fq, case, status):
         prob, keep = fq.make_problem(n, fq.FQ_TRIDIAG, d, d, 1.0, 4, h0_off=np.ones(n - 1), kernel=9, **kw)
     else:
         prob, keep = fq.make_problem(n, fq.FQ_TRIDIAG, d, d, 1.0, 4, h0_off=np.ones(n - 1),
-                                     precision=fq.FQ_OZAKI, **kw)
+                                     precision=fq.FQ_BF16X6, **kw)
     with pytest.raises(fq.FloquetError) as e:
         fq.floquet_plan_inspect(prob)
     assert e.value.status == getattr(fq, status)

@@ -1,0 +1,150 @@
+"""The band form of the tridiagonal step (FQ_OZAKI on a tridiagonal plan, csrc/band.cu), checked in
+FP64 on CPU against the oracle, free of the emulation's rounding:
+
+  * P_m = e^{-i beta h} sum_k c_k T_k(Omega~_m) (Eqs. 10 and 12) is a band matrix with 2L + 1
+    diagonals, and row i of it is what the kernel forms: Clenshaw's recurrence on the basis vector
+    e_i in the real gauge frame, on a 96-row window centred on i (zero beyond it), rotated back by
+    e^{i theta_i} ... e^{-i theta_k};
+  * chaining X_m = P_m X_{m-1} reproduces the oracle's step-by-step recurrence;
+  * the tile window of 64 operator rows [i0, i0 + 64), state columns [i0 - 48, i0 + 112), holds
+    every row's band, and each row's window positions land inside the 160 columns of its tile;
+  * one drain per tile keeps the three exact FP32 sums exact (3 pairs x 2^14 x 320 < 2^24);
+  * the 48-bit fixed-point value of a double-float pair, taken from the FP32 bit patterns,
+    is within one unit of the exact value."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import floquet_inputs as fi
+import oracle as o
+from test_gauge_design import clenshaw, gauge
+
+WIN, CENTRE, KH, BN, KW = 96, 48, 48, 64, 160
+
+
+def band_rows(d, e_real, theta, coeffs, phase, n):
+    """The kernel's formation of P_m, row by row: v = P(Omega') e_i on the window [i - 48, i + 48)
+    (operator zero outside [0, n) and outside the window), then P[i][k] = phase e^{i theta_i} v_k
+    e^{-i theta_k}."""
+    P = np.zeros((n, n), complex)
+    for i in range(n):
+        w0 = i - CENTRE
+        ks = np.arange(w0, w0 + WIN)
+        inside = (ks >= 0) & (ks < n)
+        dw = np.where(inside, d[np.clip(ks, 0, n - 1)], 0.0)
+        ew = np.zeros(WIN)               # 2 Omega'[k+1][k] -> coupling of positions p and p + 1
+        ok = inside[:-1] & inside[1:]
+        ew[:-1][ok] = e_real[np.clip(ks[:-1], 0, n - 2)][ok]
+        v = np.zeros((WIN, 1), complex)
+        v[CENTRE] = 1.0
+        s = clenshaw(dw, ew[:-1], v, coeffs)[:, 0]
+        k = ks[inside]
+        P[i, k] = phase * np.exp(1j * theta[i]) * s[inside] * np.exp(-1j * theta[k])
+    return P
+
+
+def dimer_step(nb=150, M=40, m=7, drv=None):
+    h0d, h0o, h1d = fi.dimer_matrices(nb, 1.0, U=2.0 / nb)
+    drv = drv or fi.Drive(0.2, 1.5, 3.0, 0.4)
+    plan = o.plan_for_drive_tridiag(h0d, h0o, h1d, drv, M)
+    k_low = o.commutator_tridiag(h0o, h1d)
+    return h0d, h0o, h1d, plan, k_low, drv
+
+
+def test_band_rows_are_the_step_polynomial():
+    """The windowed Clenshaw rows equal the oracle's step applied to the identity, and the
+    oracle's step has exactly 2L + 1 non-zero diagonals (T_k of a tridiagonal matrix)."""
+    h0d, h0o, h1d, plan, k_low, _ = dimer_step()
+    n = h0d.shape[0]
+    m = 7
+    d, lower = o.omega_tilde_tridiag(h0d, h0o, h1d, k_low, plan, m)
+    assert np.max(np.abs(lower.imag)) > 0 and plan.L <= 47
+    ref = o.chebyshev_step(lambda v: o.apply_tridiag(d, lower, v), np.eye(n, dtype=complex), plan.coeffs,
+                           plan.phase)
+    i, k = np.indices((n, n))
+    assert np.all(ref[np.abs(i - k) > plan.L] == 0)
+    assert np.min(np.abs(ref[np.abs(i - k) == plan.L])) > 0
+    theta, e_real = gauge(lower)
+    P = band_rows(d, e_real.real, theta, plan.coeffs, plan.phase, n)
+    assert np.max(np.abs(P - ref)) <= 1e-14
+
+
+def test_band_chain_matches_oracle():
+    """X_m = P_m X_{m-1} over several steps (non-even drive) against the oracle's recurrence."""
+    nb, M = 60, 16
+    h0d, h0o, h1d, plan, k_low, drv = dimer_step(nb=nb, M=M)
+    n = nb + 1
+    x0 = fi.ginibre(n, 31)[:, :4]
+    x0 /= np.linalg.norm(x0, axis=0)
+    ref = o.propagate_tridiag(h0d, h0o, h1d, plan, x0, 0, 6)
+    x = np.array(x0)
+    for m in range(6):
+        d, lower = o.omega_tilde_tridiag(h0d, h0o, h1d, k_low, plan, m)
+        theta, e_real = gauge(lower)
+        x = band_rows(d, e_real.real, theta, plan.coeffs, plan.phase, n) @ x
+    assert np.max(np.abs(x - ref)) <= 1e-13
+
+
+@pytest.mark.parametrize("n,L", [(1, 1), (41, 20), (64, 47), (700, 39), (10001, 39), (10001, 47)])
+def test_tile_windows_hold_every_band(n, L):
+    """Rows [i0, i0 + 64) of a tile read state columns [i0 - 48, i0 + 112); every non-zero P[i][k]
+    (|i - k| <= L, both in [0, n)) sits in that window and in the row's 96-row formation window,
+    at tile column c = k - (i0 - 48) in [0, 160); the window start is a multiple of 16 columns
+    (the TMA alignment rule for BF16), and the row's zero columns [0, r) and [r + 96, 160) are
+    disjoint from its band columns [r, r + 96)."""
+    tiles = -(-n // BN)
+    for b in range(tiles):
+        i0 = BN * b
+        assert (i0 - KH) % 16 == 0
+        for i in range(i0, min(i0 + BN, n)):
+            r = i - i0
+            ks = np.arange(max(0, i - L), min(n, i + L + 1))
+            c = ks - (i0 - KH)
+            assert np.all((c >= 0) & (c < KW))
+            p = ks - (i - CENTRE)
+            assert np.all((p >= 0) & (p < WIN)) and np.array_equal(c, p + r)
+            zeros = [z if z < r else z + WIN for z in range(64)]
+            assert sorted(zeros + list(range(r, r + WIN))) == list(range(KW))
+
+
+def test_one_drain_per_tile_is_exact():
+    """Digits |d| <= 2^7, so a slice product is at most 2^14 units of its grid; the exact
+    accumulators take at most 3 pairs, and a 160-column window gives 2 x 160 products per entry
+    (real and imaginary parts of the state), so their sums stay below 2^24 units and FP32
+    represents every partial sum exactly."""
+    assert 3 * 2 ** 14 * (2 * KW) < 2 ** 24
+    assert 3 * 2 ** 14 * (2 * (KW + 32)) > 2 ** 24   # two more K stages would need a second drain
+
+
+def _fixed48_f32(x: np.float32, E: int) -> int:
+    """The kernel's fixed48_f32: round(x 2^(48 - E)) from the FP32 bit pattern, by shifts."""
+    bits = int(np.array(x, dtype=np.float32).view(np.uint32))
+    b = (bits >> 23) & 0xFF
+    if b == 0:
+        return 0
+    m = (bits & 0x7FFFFF) | 0x800000
+    sh = 102 + E - b
+    if sh <= 0:
+        R = m << (-sh)
+    elif sh >= 64:
+        R = 0
+    else:
+        R = (m + (1 << (sh - 1))) >> sh
+    return -R if bits >> 31 else R
+
+
+def test_double_float_fixed_point_within_one_unit():
+    """fixed(hi) + fixed(lo) against the exact round((hi + lo) 2^(48 - E)) for double-float pairs
+    of random magnitudes below 2^(E - 1), E from the row maximum as in k_band_slice."""
+    rng = np.random.default_rng(3)
+    for _ in range(2000):
+        x = float(rng.uniform(-1, 1) * 2.0 ** rng.integers(-30, 1))
+        h = np.float32(x)
+        lo = np.float32(x - float(h))
+        E = int(np.frexp(abs(float(h)) if h != 0 else 1.0)[1]) + 1   # |h| < 2^(E - 1)
+        exact = Fraction(float(h)) + Fraction(float(lo))
+        R = _fixed48_f32(h, E) + _fixed48_f32(lo, E)
+        target = exact * Fraction(2) ** (48 - E)
+        assert abs(Fraction(R) - target) <= 1
