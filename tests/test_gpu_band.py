@@ -55,11 +55,11 @@ def test_band_dimer40_whole_UT(fq, kernel):
 
 
 @pytest.mark.parametrize("nb,steps,m_end", [(4, 2000, 4), (63, 2000, 4), (64, 2000, 4), (700, 2000, 6),
-                                            (2047, 2000, 5), (10000, 2000, 3), (10000, 1330, 3)])
+                                            (2047, 2000, 5), (10000, 2000, 3), (10000, 1480, 3)])
 def test_band_ragged_sizes(fq, nb, steps, m_end):
     """First, middle and last basis states and two random unit vectors (5 states in one ragged
     128-state tile) through steps 1 .. m_end-1 of the chain with a phase-offset drive: 5 to 10001
-    rows (one to 157 operator blocks), L from 4 to 47 (M = 1330 at dim 10001)."""
+    rows (one to 157 operator blocks), L from 4 to 47 (M = 1480 at dim 10001)."""
     d = fi.config_dimer(nb=nb, steps=steps)
     d.drive = fi.Drive(0.2, 1.5, 3.0, 0.4)
     plan = band_plan(fq, d)
