@@ -87,7 +87,7 @@ def test_band_many_state_tiles_and_column_split(fq):
     blocks of a 3-rank split bit for bit, and matches the oracle."""
     import torch
     from paper_1508_07621_gb300 import shard
-    d = fi.config_dimer(nb=700, steps=60)
+    d = fi.config_dimer(nb=700, steps=200)    # L = 32
     plan = band_plan(fq, d)
     n = d.n
     U = plan.build_UT()
