@@ -51,7 +51,7 @@ def test_band_dimer40_whole_UT(fq, kernel):
     err = np.max(np.abs(U - ref))
     print(f"band dimer40: max err {err:.2e}")
     assert err <= 1e-10
-    assert np.max(np.abs(U.conj().T @ U - np.eye(d.n))) <= 1e-11
+    assert np.max(np.abs(U.conj().T @ U - np.eye(d.n))) <= 1e-10   # the FP64 criterion, on U^+ U - 1
 
 
 @pytest.mark.parametrize("nb,steps,m_end", [(4, 2000, 4), (63, 2000, 4), (64, 2000, 4), (700, 2000, 6),
