@@ -243,6 +243,35 @@ __device__ __forceinline__ float pow2f(int e) {
   return __int_as_float((127 + e) << 23);
 }
 
+__device__ __forceinline__ void two_sum2(float2& a, float2& b) {  // (a, b) <- (fl(a + b), its error), exact
+  const float2 s = __fadd2_rn(a, b);
+  const float2 bb = __fadd2_rn(s, neg2f(a));
+  b = __fadd2_rn(__fadd2_rn(a, neg2f(__fadd2_rn(s, neg2f(bb)))), __fadd2_rn(b, neg2f(bb)));
+  a = s;
+}
+
+// The OZ_S slices of v = a + b (a double-float pair, packed as (re, im), |v| < 1/2 in units of
+// the row scale), with FP32 instructions only: t_q = v rounded to a multiple of 2^(-8(q+1)) by
+// adding and subtracting 1.5 2^(15 - 8q) (exact for |v| < 2^(14 - 8q)), then v -= t_q (exact) and a
+// two-sum keeps the remainder as a normalised pair.  t_q = d_q 2^(-8(q+1)) with |d_q| <= 128 (a
+// remainder is at most half a grid step), exact in BF16; the part below 2^-49 is dropped.
+// Returns |t_0| <= 1/2 for both parts (false: the value broke the scale bound).
+__device__ __forceinline__ bool df_digits2(float2 a, float2 b, __nv_bfloat16 (&dr)[OZ_S], __nv_bfloat16 (&di)[OZ_S]) {
+  two_sum2(a, b);
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < OZ_S; ++q) {
+    const float c = __int_as_float((127 + 15 - 8 * q) << 23) * 1.5f;
+    const float2 t = __fadd2_rn(__fadd2_rn(a, make_float2(c, c)), make_float2(-c, -c));
+    if (q == 0) ok = fabsf(t.x) <= 0.5f && fabsf(t.y) <= 0.5f;
+    dr[q] = __float2bfloat16_rn(t.x);
+    di[q] = __float2bfloat16_rn(t.y);
+    a = __fadd2_rn(a, neg2f(t));
+    two_sum2(a, b);
+  }
+  return ok;
+}
+
 // Slices of the initial states (complex128 rows x0 [nc][n], or the identity rows when x0 is NULL)
 // with their exact row scales: one CTA per row j of the padded block (rows >= nc stay zero).
 // kmax[j]: the row's largest |re| or |im| as an FP32 key rounded up.
@@ -539,12 +568,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const unsigned int kr = __float_as_uint(ar), ki = __float_as_uint(ai);
           kmx = kr > kmx ? kr : kmx;
           kmx = ki > kmx ? ki : kmx;
-          const long long Rr = fixed48_f32(rh, Eout - ex) + fixed48_f32(rl, Eout - ex);
-          const long long Ri = fixed48_f32(ih, Eout - ex) + fixed48_f32(il, Eout - ex);
-          bad |= Rr > (1ll << 47) || Rr < -(1ll << 47) || Ri > (1ll << 47) || Ri < -(1ll << 47);
+          const float so = pow2f(ex - Eout);  // into units of the output row scale (exact)
           __nv_bfloat16 dr[OZ_S], di[OZ_S];
-          oz_digits_fixed(Rr, dr);
-          oz_digits_fixed(Ri, di);
+          bad |= !df_digits2(make_float2(rh * so, ih * so), make_float2(rl * so, il * so), dr, di);
 #pragma unroll
           for (int q = 0; q < OZ_S; ++q) {
             const uint32_t br = (uint32_t)__bfloat16_as_ushort(dr[q]), bi = (uint32_t)__bfloat16_as_ushort(di[q]);

@@ -177,3 +177,46 @@ def test_output_scale_bound_holds():
             y = P @ x
             E = u + 2 + G
             assert np.max(np.abs(np.concatenate([y.real, y.imag]))) < 2.0 ** (E - 1)
+
+
+def _f(x):
+    return np.float32(x)
+
+
+def _two_sum(a, b):
+    s = _f(a + b)
+    bb = _f(s - a)
+    return s, _f(_f(a - _f(s - bb)) + _f(b - bb))
+
+
+def _df_digits(a, b):
+    """The band kernel's FP32 digit cut of a double-float value a + b (|a + b| < 1/2 in units of
+    the row scale), one FP32 rounding per operation: t_q = a rounded to 2^(-8(q+1)) by adding
+    and subtracting 1.5 2^(15 - 8q), a -= t_q, then a two-sum."""
+    a, b = _two_sum(_f(a), _f(b))
+    ts = []
+    for q in range(6):
+        c = _f(1.5 * 2.0 ** (15 - 8 * q))
+        t = _f(_f(a + c) - c)
+        ts.append(t)
+        a = _f(a - t)
+        a, b = _two_sum(a, b)
+    return ts
+
+
+def test_fp32_digit_cut_reconstructs_the_pair():
+    """Each t_q is an integer of at most 128 in magnitude times 2^(-8(q+1)) (exact in BF16, and
+    small enough for the exact FP32 sums), and sum t_q equals the pair's exact value to within
+    2^-49, for pairs of every magnitude below 1/2."""
+    rng = np.random.default_rng(17)
+    for _ in range(3000):
+        x = float(rng.uniform(-0.5, 0.5) * 2.0 ** -rng.integers(0, 40))
+        a = np.float32(x)
+        b = np.float32(x - float(a))
+        ts = _df_digits(a, b)
+        exact = Fraction(float(a)) + Fraction(float(b))
+        for q, t in enumerate(ts):
+            d = Fraction(float(t)) * Fraction(2) ** (8 * (q + 1))
+            assert d.denominator == 1 and abs(d) <= 128
+            assert float(np.float32(t)) == float(t)
+        assert abs(sum(Fraction(float(t)) for t in ts) - exact) <= Fraction(1, 2 ** 49)
