@@ -8,21 +8,21 @@
 //   1. forms the rows of P_m once (k_band_rows): in the real gauge frame Omega~ = D Omega' D^+
 //      (gauge.cuh), row i of P(Omega') is P(Omega') e_i (P(Omega') is complex symmetric), computed
 //      by Clenshaw's recurrence in double-float arithmetic on a 96-row window around i, which holds
-//      its support i +- L; then P_m[i][k] = e^{-i beta h} e^{i theta_i} v_k e^{-i theta_k} in FP64,
-//      cut into the fixed-point BF16 slices of the FP64 emulation (ozaki_core.cuh);
-//   2. multiplies every state by the band on the tensor cores (k_oz_band): a tile of 64 operator
+//      its support i +- L; then P_m[i][k] = e^{-i beta h} e^{i theta_i} v_k e^{-i theta_k} in FP64;
+//   2. cuts the state rows into fixed-point BF16 slices (k_band_slice, as FQ_OZAKI does for dense
+//      operators, ozaki_core.cuh);
+//   3. multiplies every state by the band on the tensor cores (k_oz_band): a tile of 64 operator
 //      rows [i0, i0 + 64) needs only the state columns [i0 - 48, i0 + 112), so its K loop is that
 //      160-wide window instead of all N columns.  The 21 slice pairs sum exactly in FP32 tensor
 //      memory over the whole window (3 pairs x 2^14 x 320 products < 2^24 units), so one drain
-//      per tile suffices.  The epilogue cuts the new states straight into the next product's
-//      slices, with FP32 and integer instructions only (GB300's FP64 rate is far below its FP32
-//      and tensor rates): the states exist between steps only as their slices.
+//      per tile suffices, and the epilogue writes the new state as double-float pairs with FP32
+//      instructions only (GB300's FP64 rate is far below its FP32 and tensor rates).
 // The product is the same polynomial the Chebyshev recurrence applies, so the result agrees with
-// the plain chain to the emulation's rounding (48 bits of each row's scale).  Needs L <= 47.
+// the plain chain to the emulation's rounding (48 bits per slice product).  Needs L <= 47.
 //
 // Layouts (all in the caller's workspace):
-//   left       two buffers of OZ_S slices [ncp][2 npl] BF16 (the states of the current and the
-//              next step): re in columns [0, npl), im in [npl, 2 npl), npl = N rounded to 128
+//   states     double-float [nc][npl] float4 (re_hi, re_lo, im_hi, im_lo), npl = N rounded to 128
+//   left       OZ_S slices [ncp][2 npl] BF16: re in columns [0, npl), im in [npl, 2 npl)
 //   right      OZ_S slices [3 nrows][160] BF16: per 64-row block b the rows -Im, Re, Im of P_m,
 //              column c = k - (64 b - 48)
 //   cf, rot    per step (2 d, 2 e') and (cos, sin) theta of the gauge frame, FP64, [nsteps][nrows]
@@ -95,14 +95,11 @@ __device__ __forceinline__ void band_apply(const dflc (&x)[BAND_LANE_ROWS], dflc
 }
 
 // Rows i < nrows of P_m into the right operand slices and their exponents et[i] (rows >= n are
-// zero); one warp per row.  cf, rot: the step's gauge tables.  Also the step's bound for the
-// state scales: atomicMax into *rho of the largest row sum of |Re P[i][k]| + |Im P[i][k]| (as an
-// FP32 key rounded up), and the zeroing of the row-maximum keys the step's product will fill.
+// zero); one warp per row.  cf, rot: the step's gauge tables (row stride irrelevant: row k).
 __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
     k_band_rows(const double2* __restrict__ cf, const double2* __restrict__ rot, int n, int nrows, int L,
                 BandCoef coef, double ph_re, double ph_im, size_t rstride, __nv_bfloat16* __restrict__ right,
-                int* __restrict__ et, unsigned int* __restrict__ rho, unsigned int* __restrict__ kzero, int nzero) {
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nzero; q += gridDim.x * blockDim.x) kzero[q] = 0u;
+                int* __restrict__ et) {
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * BAND_ROWS_PER_CTA + (threadIdx.x >> 5);
   if (i >= nrows) return;  // whole warp
@@ -156,10 +153,9 @@ __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
       for (int q = 0; q < BAND_LANE_ROWS; ++q) A[q] = B[q];
     }
   }
-  // P_m[i][k] = e^{-i beta h} e^{i theta_i} v_k e^{-i theta_k} in FP64, the row's scale and sum
+  // P_m[i][k] = e^{-i beta h} e^{i theta_i} v_k e^{-i theta_k} in FP64, and the row's scale
   double vr[BAND_LANE_ROWS], vi[BAND_LANE_ROWS];
   unsigned long long key = 0;
-  double rowsum = 0.0;
   const double2 ri = live ? rot[i] : make_double2(1.0, 0.0);
   const double wr = ph_re * ri.x - ph_im * ri.y, wi = ph_re * ri.y + ph_im * ri.x;  // e^{-i beta h} e^{i theta_i}
 #pragma unroll
@@ -173,7 +169,6 @@ __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
       vr[q] = ur * sr - ui * si;
       vi[q] = ur * si + ui * sr;
     }
-    rowsum += fabs(vr[q]) + fabs(vi[q]);
     const unsigned long long a = abs_key(vr[q]), b = abs_key(vi[q]);
     key = a > key ? a : key;
     key = b > key ? b : key;
@@ -182,9 +177,7 @@ __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long w = __shfl_xor_sync(0xffffffffu, key, o);
     key = w > key ? w : key;
-    rowsum += __shfl_xor_sync(0xffffffffu, rowsum, o);
   }
-  if (lane == 0 && live) atomicMax(rho, __float_as_uint(__double2float_ru(rowsum)));
   const int E = oz_exponent(key);
   const int r = i % OZ_BN;
   const size_t rb = (size_t)(3 * OZ_BN) * (i / OZ_BN) + r;  // row of -Im; Re and Im follow
@@ -217,24 +210,6 @@ __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
     }
   }
   if (lane == 0) et[i] = E;
-}
-
-// 48-bit fixed-point value of an FP32 number relative to the scale 2^E: round(x 2^(48 - E)) from
-// the bit pattern (x = m 2^(b - 150), so the shift is 102 + E - b), integer work only.  For
-// |x| < 2^(E - 1) a left shift is at most 23 bits and |R| < 2^47; a larger x saturates at 2^62 so
-// that the caller's range check catches it.  Zero and subnormal inputs give 0.
-__device__ __forceinline__ long long fixed48_f32(float x, int E) {
-  const unsigned int bits = __float_as_uint(x);
-  const int b = (int)((bits >> 23) & 0xFF);
-  if (b == 0) return 0;
-  const long long m = (long long)((bits & 0x7FFFFFu) | 0x800000u);
-  const int sh = 102 + E - b;
-  long long R;
-  if (sh < -38) R = 1ll << 62;
-  else if (sh <= 0) R = m << (-sh);
-  else if (sh >= 64) R = 0;
-  else R = (m + (1ll << (sh - 1))) >> sh;
-  return (bits >> 31) ? -R : R;
 }
 
 // float 2^e for |e| <= 126 (clamped)
@@ -272,37 +247,36 @@ __device__ __forceinline__ bool df_digits2(float2 a, float2 b, __nv_bfloat16 (&d
   return ok;
 }
 
-// Slices of the initial states (complex128 rows x0 [nc][n], or the identity rows when x0 is NULL)
-// with their exact row scales: one CTA per row j of the padded block (rows >= nc stay zero).
-// kmax[j]: the row's largest |re| or |im| as an FP32 key rounded up.
-__global__ void k_band_init(const double2* __restrict__ x0, int n, int nc, int npl, size_t astride,
-                            __nv_bfloat16* __restrict__ left, int* __restrict__ es, unsigned int* __restrict__ kmax) {
+// Left slices of double-float state rows: one CTA per row j of the padded block (rows >= nc and
+// columns >= n are zero), the scale 2^E from the row's largest |hi| part, the digits by the FP32
+// cut of df_digits2 (re and im packed).
+__global__ void k_band_slice(const float4* __restrict__ x, int n, int ld, int nc, int npl, size_t astride,
+                             __nv_bfloat16* __restrict__ left, int* __restrict__ es) {
   __shared__ unsigned long long red[32];
   const int j = blockIdx.x;
   unsigned long long m = 0;
-  if (j < nc) {
-    if (x0) {
-      for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const double2 v = x0[(size_t)j * n + k];
-        const unsigned long long a = abs_key(v.x), b = abs_key(v.y);
-        m = a > m ? a : m;
-        m = b > m ? b : m;
-      }
-    } else if (j < n && threadIdx.x == 0) {
-      m = abs_key(1.0);
+  if (j < nc)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const float4 v = x[(size_t)j * ld + k];
+      // |hi| as an ordered key (FP32 bit pattern; no FP64 conversion): the row maximum of |hi|
+      // bounds |hi + lo| below 2^(E-1) as well (the exponent has a factor 2 to spare)
+      const unsigned long long a = __float_as_uint(v.x) & 0x7FFFFFFFu, b = __float_as_uint(v.z) & 0x7FFFFFFFu;
+      m = a > m ? a : m;
+      m = b > m ? b : m;
     }
-  }
   const unsigned long long mk = block_max_key(m, red);
-  const int E = oz_exponent(mk);
+  // E = (unbiased exponent of the maximum) + 2, as oz_exponent for FP64 keys
+  const int E = mk == 0 ? 0 : (int)(mk >> 23) - 127 + 2;
+  const float so = pow2f(-E);  // into units of the row scale (exact)
   __nv_bfloat16* row = left + (size_t)j * 2 * npl;
+  bool bad = false;
   for (int k0 = 4 * threadIdx.x; k0 < npl; k0 += 4 * blockDim.x) {
     __nv_bfloat16 sr[4][OZ_S], si[4][OZ_S];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      double2 v = make_double2(0.0, 0.0);
-      if (j < nc && k0 + u < n) v = x0 ? x0[(size_t)j * n + k0 + u] : make_double2(k0 + u == j ? 1.0 : 0.0, 0.0);
-      oz_digits(v.x, E, sr[u]);
-      oz_digits(v.y, E, si[u]);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j < nc && k0 + u < n) v = x[(size_t)j * ld + k0 + u];
+      bad |= !df_digits2(make_float2(v.x * so, v.z * so), make_float2(v.y * so, v.w * so), sr[u], si[u]);
     }
 #pragma unroll
     for (int q = 0; q < OZ_S; ++q) {
@@ -310,47 +284,30 @@ __global__ void k_band_init(const double2* __restrict__ x0, int n, int nc, int n
       *reinterpret_cast<uint2*>(row + q * astride + npl + k0) = pack4(si[0][q], si[1][q], si[2][q], si[3][q]);
     }
   }
-  if (threadIdx.x == 0) {
-    es[j] = E;
-    kmax[j] = mk ? __float_as_uint(__double2float_ru(__longlong_as_double((long long)mk))) : 0u;
-  }
+  if (threadIdx.x == 0) es[j] = E;
+  (void)bad;  // the scale comes from the row's own maximum: the cut cannot break it
 }
 
+constexpr int BAND_RG = 16;  // state blocks per raster group
+
 struct BandEpi {
-  __nv_bfloat16* slices;     // output slices (the next product's left operand), OZ_S of [ncp][2 npl]
-  size_t astride;
-  int npl;
-  int* es_out;               // scale exponents of the output rows
-  const int* es;             // scale exponents of the input rows
-  const int* et;             // row exponents of the operator slices
-  const unsigned int* kprev; // largest |re| or |im| of each input row (FP32 key)
-  unsigned int* kcur;        // the same for the output rows (atomicMax)
-  const unsigned int* rho;   // the step's largest operator row sum of |Re| + |Im| (FP32 key)
-  double2* out;              // last step: complex128 output instead of slices (NULL otherwise)
-  int transpose;             // last step: U[i][j] = X_j[i] (N x N) instead of rows X[j][i]
-  int n, nc;
+  float4* out;     // X_m, double-float [nc][ld]
+  const int* es;   // row exponents of the left slices
+  const int* et;   // row exponents of the right slices
+  int n, nc, ld;
   float bound2;
   unsigned int* status;
 };
 
-constexpr int BAND_RG = 16;  // state blocks per raster group
-
 // The banded product X_m[j][i] = sum_{k in window(i)} X_{m-1}[j][k] P_m[i][k] on 128-state x
 // 64-row tiles, persistent: one CTA per SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-// rasterized in groups of 16 state blocks that sweep the operator blocks together (co-running
-// CTAs share each operator block and the sliding state windows in L2).  Warp 0 streams TMA stages
-// (K = 16 each, 32-byte swizzle), warp 1 issues the MMAs of the 21 slice pairs into the four
-// accumulators (512 tensor-memory columns), warps 2-17 drain them once per tile into double-float
-// registers, release the tensor memory and, while the next tile's MMAs run, write the tile.
-//
-// The output is written straight as the next product's fixed-point slices: row j's scale 2^E must
-// exceed twice its largest entry before the row is complete, and
-//   |Re X_m[j][i]|, |Im X_m[j][i]| <= (max_i sum_k |Re P_m[i][k]| + |Im P_m[i][k]|) * max(|Re|, |Im| of X_{m-1}[j])
-// bounds it by the input row's maximum (known from the previous product) and the step's operator
-// row sums (from k_band_rows): E = exponent(that maximum) + 2 + ceil(log2 rho).  The rows' true
-// maxima are collected for the next step.  The last step writes complex128 states instead.
-// Every wait is bounded; a wait that gives up records FQ_BIT_TIMEOUT, drains this CTA's own copies
-// and MMAs, frees tensor memory and returns.
+// rasterized in groups of 16 state blocks that sweep the operator blocks together (co-running CTAs
+// share each operator block and the sliding state windows in L2).  Warp 0 streams
+// TMA stages (K = 16 each, 32-byte swizzle), warp 1 issues the MMAs of the 21 slice pairs into the
+// four accumulators (512 tensor-memory columns), warps 2-17 drain them once per tile into
+// double-float registers, release the tensor memory and write the tile while the next tile's MMAs
+// run.  Every wait is bounded; a wait that gives up records FQ_BIT_TIMEOUT, drains this CTA's own
+// copies and MMAs, frees tensor memory and returns.
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_oz_band(const __grid_constant__ OzMaps maps, int tiles_j, int tiles_i, int npl, BandEpi e) {
   using Cfg = OzCfg;
@@ -367,6 +324,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const uint32_t done = smem_u32(bars + 2 * STAGES + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = tiles_i * tiles_j;
+  auto coords = [&](int t, int& j0, int& i0) {
+    const int per = BAND_RG * tiles_i, g = t / per;
+    const int gj = min(BAND_RG, tiles_j - g * BAND_RG), r = t - g * per;
+    j0 = (g * BAND_RG + r % gj) * BM;
+    i0 = (r / gj) * OZ_BN;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -389,13 +352,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-
-  auto coords = [&](int t, int& j0, int& i0) {
-    const int per = BAND_RG * tiles_i, g = t / per;
-    const int gj = min(BAND_RG, tiles_j - g * BAND_RG), r = t - g * per;
-    j0 = (g * BAND_RG + r % gj) * BM;
-    i0 = (r / gj) * OZ_BN;
-  };
 
   if (warp == 0) {
     if (lane == 0) {  // ---------------- TMA producer
@@ -478,18 +434,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int quarter = warp & 3, part = (warp - 2) >> 2;
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(part * 16);
     bool bad = false, ok = true;
-    // the scale bound of this step's output rows: 2^G >= rho (with margin for the FP32 keys)
-    int G = 0;
-    if (!e.out) {
-      const float rf = __uint_as_float(*e.rho) * 1.0000005f;
-      const unsigned int rb_ = __float_as_uint(rf);
-      G = (int)(rb_ >> 23) - 127 + ((rb_ & 0x7FFFFFu) ? 1 : 0);
-      G = G < 0 ? 0 : G;
-    }
     int it = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
       int j0, i0;
-      coords(t, j0, i0);
+        coords(t, j0, i0);
       bool go = mbar_wait(tfull, it & 1);
       tc_fence_after();
       go = __all_sync(0xffffffffu, go && !*(volatile int*)abort_flag);
@@ -521,76 +469,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty);  // the next tile's MMAs may start
       const int j = j0 + quarter * 32 + lane;
-      if (j >= e.nc) continue;
-      const int ej = e.es[j];
-      const int ib = i0 + part * 16;
-      if (e.out) {  // ---- last step: complex128 states
+      if (j < e.nc) {
+        const int ej = e.es[j];
+        float4* orow = e.out + (size_t)j * e.ld;
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          const int i = ib + c;
-          if (i >= e.n) break;
-          const int ex = ej + e.et[i];
-          const float2 H = hr[c >> 1], Lr = lr[c >> 1], Hi = hi[c >> 1], Li = li[c >> 1];
-          const float rh = (c & 1) ? H.y : H.x, rl = (c & 1) ? Lr.y : Lr.x;
-          const float ih = (c & 1) ? Hi.y : Hi.x, il = (c & 1) ? Li.y : Li.x;
-          const double sc = pow2(ex < -1022 ? -1022 : ex);
-          const double yr = ((double)rh + (double)rl) * sc, yi = ((double)ih + (double)il) * sc;
-          bad |= !(yr * yr + yi * yi <= (double)e.bound2);
-          if (e.transpose) e.out[(size_t)i * e.n + j] = make_double2(yr, yi);
-          else e.out[(size_t)j * e.n + i] = make_double2(yr, yi);
-        }
-        continue;
-      }
-      // ---- the next product's slices, scale 2^Eout from the bound above
-      const unsigned int kp = e.kprev[j];
-      const int Eout = kp ? (int)(kp >> 23) - 127 + 2 + G : 0;
-      unsigned int kmx = 0u;
-      __nv_bfloat16* srow = e.slices + (size_t)j * 2 * e.npl + ib;
-#pragma unroll
-      for (int c4 = 0; c4 < 4; ++c4) {
-        uint32_t wr[OZ_S][2], wi[OZ_S][2];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int c = 4 * c4 + u;
-          const int i = ib + c;
-          const float2 H = hr[c >> 1], Lr = lr[c >> 1], Hi = hi[c >> 1], Li = li[c >> 1];
-          float rh = (c & 1) ? H.y : H.x, rl = (c & 1) ? Lr.y : Lr.x;
-          float ih = (c & 1) ? Hi.y : Hi.x, il = (c & 1) ? Li.y : Li.x;
-          int ex = 0;
+          const int i = i0 + part * 16 + c;
           if (i < e.n) {
-            ex = ej + e.et[i];
-          } else {  // operator rows beyond n: zero slices
-            rh = rl = ih = il = 0.f;
+            int ex = ej + e.et[i];
+            ex = ex < -126 ? -126 : (ex > 127 ? 127 : ex);
+            const float sc = __int_as_float((127 + ex) << 23);
+            const float2 H = hr[c >> 1], Lr = lr[c >> 1], Hi = hi[c >> 1], Li = li[c >> 1];
+            const float rh0 = ((c & 1) ? H.y : H.x) * sc, rl0 = ((c & 1) ? Lr.y : Lr.x) * sc;
+            const float ih0 = ((c & 1) ? Hi.y : Hi.x) * sc, il0 = ((c & 1) ? Li.y : Li.x) * sc;
+            const float rh = __fadd_rn(rh0, rl0), ih = __fadd_rn(ih0, il0);  // renormalise the pairs
+            const float rl = __fsub_rn(rl0, __fsub_rn(rh, rh0)), il = __fsub_rn(il0, __fsub_rn(ih, ih0));
+            bad |= !(rh * rh + ih * ih <= e.bound2);
+            orow[i] = make_float4(rh, rl, ih, il);
           }
-          const float sc = pow2f(ex);
-          const float ar = fabsf(rh * sc), ai = fabsf(ih * sc);
-          bad |= !(ar * ar + ai * ai <= e.bound2);
-          const unsigned int kr = __float_as_uint(ar), ki = __float_as_uint(ai);
-          kmx = kr > kmx ? kr : kmx;
-          kmx = ki > kmx ? ki : kmx;
-          const float so = pow2f(ex - Eout);  // into units of the output row scale (exact)
-          __nv_bfloat16 dr[OZ_S], di[OZ_S];
-          bad |= !df_digits2(make_float2(rh * so, ih * so), make_float2(rl * so, il * so), dr, di);
-#pragma unroll
-          for (int q = 0; q < OZ_S; ++q) {
-            const uint32_t br = (uint32_t)__bfloat16_as_ushort(dr[q]), bi = (uint32_t)__bfloat16_as_ushort(di[q]);
-            if (u & 1) {
-              wr[q][u >> 1] |= br << 16;
-              wi[q][u >> 1] |= bi << 16;
-            } else {
-              wr[q][u >> 1] = br;
-              wi[q][u >> 1] = bi;
-            }
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < OZ_S; ++q) {
-          *reinterpret_cast<uint2*>(srow + q * e.astride + 4 * c4) = make_uint2(wr[q][0], wr[q][1]);
-          *reinterpret_cast<uint2*>(srow + q * e.astride + e.npl + 4 * c4) = make_uint2(wi[q][0], wi[q][1]);
         }
       }
-      atomicMax(e.kcur + j, kmx);
-      if (i0 == 0 && part == 0) e.es_out[j] = Eout;
     }
     if (!ok) {
       atomicExch(abort_flag, 1);
@@ -606,15 +504,61 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   }
 }
 
+// complex128 rows (or the identity when x0 is NULL) into double-float rows [nc][ld], zero beyond n
+__global__ void k_band_load(const double2* __restrict__ x0, float4* __restrict__ x, int nc, int n, int ld) {
+  const size_t total = (size_t)nc * ld;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(q / ld), k = (int)(q % ld);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < n) {
+      if (x0) {
+        const double2 a = x0[(size_t)r * n + k];
+        const dfl re = dfl_of(a.x), im = dfl_of(a.y);
+        v = make_float4(re.h, re.l, im.h, im.l);
+      } else if (k == r) {
+        v.x = 1.f;
+      }
+    }
+    x[q] = v;
+  }
+}
+
+// double-float rows into complex128 rows [nc][n]
+__global__ void k_band_store(const float4* __restrict__ x, double2* __restrict__ out, int nc, int n, int ld) {
+  const size_t total = (size_t)nc * n;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(q / n), k = (int)(q % n);
+    const float4 v = x[(size_t)r * ld + k];
+    out[q] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+  }
+}
+
+// U[i][j] = X_j[i] (the n x n block of states as rows -> U_T), 32 x 32 tiles through shared memory
+__global__ void k_band_store_t(const float4* __restrict__ x, double2* __restrict__ u, int n, int ld) {
+  __shared__ double2 tile[32][33];
+  const int j0 = blockIdx.y * 32, i0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + r, i = i0 + threadIdx.x;
+    if (j < n && i < n) {
+      const float4 v = x[(size_t)j * ld + i];
+      tile[r][threadIdx.x] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, j = j0 + threadIdx.x;
+    if (i < n && j < n) u[(size_t)i * n + j] = tile[threadIdx.x][r];
+  }
+}
+
 struct BandWs {
   double2* cf;
   double2* rot;
   __nv_bfloat16* right;
   int* et;
-  __nv_bfloat16* left[2];
-  int* es[2];
-  unsigned int* kmax[2];
-  unsigned int* rho;
+  __nv_bfloat16* left;
+  int* es;
+  float4* x[2];
   int nrows, npl, ncp;
   size_t rstride, astride;
 };
@@ -639,15 +583,14 @@ size_t band_layout(const fq_plan* p, int nc, int nsteps, void* base, BandWs* out
   w.rot = (double2*)take(sizeof(double2) * (size_t)nsteps * w.nrows);
   w.right = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.rstride);
   w.et = (int*)take(sizeof(int) * w.nrows);
-  for (int q = 0; q < 2; ++q) {
-    w.left[q] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.astride);
-    w.es[q] = (int*)take(sizeof(int) * w.ncp);
-    w.kmax[q] = (unsigned int*)take(sizeof(unsigned int) * w.ncp);
-  }
-  w.rho = (unsigned int*)take(sizeof(unsigned int) * (size_t)(nsteps > 0 ? nsteps : 1));
+  w.left = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.astride);
+  w.es = (int*)take(sizeof(int) * w.ncp);
+  for (int q = 0; q < 2; ++q) w.x[q] = (float4*)take(sizeof(float4) * (size_t)nc * w.npl);
   if (out) *out = w;
   return off;
 }
+
+int band_grid(size_t total) { return (int)std::min<size_t>(std::max<size_t>((total + 255) / 256, 1), 152 * 32); }
 
 }  // namespace
 
@@ -664,23 +607,14 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
     fq_set_error("band kernel needs L <= %d (L = %d)", BAND_MAXL, L);
     return FQ_EUNSUPPORTED;
   }
-  if (transpose_out && nc != n) {
-    fq_set_error("band kernel: a transposed output needs N states (got %d of %d)", nc, n);
-    return FQ_EINVAL;
-  }
-  if (nsteps < 1) {
-    fq_set_error("band kernel: empty step range");
-    return FQ_EINVAL;
-  }
   BandWs w;
   band_layout(p, nc, nsteps, ws, &w);
-  OzMaps maps[2];
-  for (int b = 0; b < 2; ++b)
-    for (int q = 0; q < OZ_S; ++q) {
-      if ((st = make_map(&maps[b].a[q], w.left[b] + q * w.astride, w.ncp, 2 * w.npl, BM, OZ_BKE)) != FQ_OK) return st;
-      if ((st = make_map(&maps[b].r[q], w.right + q * w.rstride, 3 * w.nrows, BAND_KW, 3 * OZ_BN, OZ_BKE)) != FQ_OK)
-        return st;
-    }
+  OzMaps maps;
+  for (int q = 0; q < OZ_S; ++q) {
+    if ((st = make_map(&maps.a[q], w.left + q * w.astride, w.ncp, 2 * w.npl, BM, OZ_BKE)) != FQ_OK) return st;
+    if ((st = make_map(&maps.r[q], w.right + q * w.rstride, 3 * w.nrows, BAND_KW, 3 * OZ_BN, OZ_BKE)) != FQ_OK)
+      return st;
+  }
   static std::atomic<unsigned> attr_set{0};
   if (fq_first_on_device(attr_set)) {
     cudaError_t e = cudaFuncSetAttribute(k_oz_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OzCfg::SMEM);
@@ -689,16 +623,10 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
   if (sms < 1) sms = 152;
-  // padding rows and columns of both slice buffers stay zero; the bound slots start at zero
-  cudaError_t ce = cudaSuccess;
-  for (int b = 0; b < 2 && ce == cudaSuccess; ++b)
-    ce = cudaMemsetAsync(w.left[b], 0, sizeof(__nv_bfloat16) * OZ_S * w.astride, s);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(w.rho, 0, sizeof(unsigned int) * nsteps, s);
-  if (ce != cudaSuccess) return fq_cuda_fail(ce, "band workspace clear");
   GaugeArgs ga{p->n, p->steps, p->d_h0, p->d_h0o, p->d_h1, p->d_k, p->d_scal, p->sbeta};
   k_gauge_tile<double><<<nsteps, GAUGE_NT, 0, s>>>(ga, w.nrows, m_begin, w.cf, w.rot);
-  k_band_init<<<w.ncp, 256, 0, s>>>(identity ? nullptr : (const double2*)x0, n, nc, w.npl, w.astride, w.left[0],
-                                    w.es[0], w.kmax[0]);
+  k_band_load<<<band_grid((size_t)nc * w.npl), 256, 0, s>>>(identity ? nullptr : (const double2*)x0, w.x[0], nc, n,
+                                                            w.npl);
   BandCoef coef{};
   for (int k = 0; k <= L; ++k) {
     const double a = p->cheb[k];
@@ -708,29 +636,29 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
   }
   const int tiles_i = (n + OZ_BN - 1) / OZ_BN, tiles_j = w.ncp / BM;
   const int ntiles = tiles_i * tiles_j;
+  BandEpi e{};
+  e.es = w.es;
+  e.et = w.et;
+  e.n = n;
+  e.nc = nc;
+  e.ld = w.npl;
+  e.bound2 = (float)(1.0 + 1e-6);
+  e.status = p->d_status;
+  int cur = 0;
   for (int m = 0; m < nsteps; ++m) {
-    const int in = m & 1, out = in ^ 1;
-    const bool last = m == nsteps - 1;
     k_band_rows<<<(w.nrows + BAND_ROWS_PER_CTA - 1) / BAND_ROWS_PER_CTA, 32 * BAND_ROWS_PER_CTA, 0, s>>>(
         w.cf + (size_t)m * w.nrows, w.rot + (size_t)m * w.nrows, n, w.nrows, L, coef, p->phase_re, p->phase_im,
-        w.rstride, w.right, w.et, w.rho + m, w.kmax[out], w.ncp);
-    BandEpi e{};
-    e.slices = w.left[out];
-    e.astride = w.astride;
-    e.npl = w.npl;
-    e.es_out = w.es[out];
-    e.es = w.es[in];
-    e.et = w.et;
-    e.kprev = w.kmax[in];
-    e.kcur = w.kmax[out];
-    e.rho = w.rho + m;
-    e.out = last ? (double2*)x : nullptr;
-    e.transpose = transpose_out;
-    e.n = n;
-    e.nc = nc;
-    e.bound2 = (float)(1.0 + 1e-6);
-    e.status = p->d_status;
-    k_oz_band<<<std::min(ntiles, sms), OZ_THREADS, OzCfg::SMEM, s>>>(maps[in], tiles_j, tiles_i, w.npl, e);
+        w.rstride, w.right, w.et);
+    k_band_slice<<<w.ncp, 256, 0, s>>>(w.x[cur], n, w.npl, nc, w.npl, w.astride, w.left, w.es);
+    e.out = w.x[cur ^ 1];
+    k_oz_band<<<std::min(ntiles, sms), OZ_THREADS, OzCfg::SMEM, s>>>(maps, tiles_j, tiles_i, w.npl, e);
+    cur ^= 1;
+  }
+  if (transpose_out) {
+    dim3 g((n + 31) / 32, (n + 31) / 32), b(32, 8);
+    k_band_store_t<<<g, b, 0, s>>>(w.x[cur], (double2*)x, n, w.npl);
+  } else {
+    k_band_store<<<band_grid((size_t)nc * n), 256, 0, s>>>(w.x[cur], (double2*)x, nc, n, w.npl);
   }
   cudaError_t e2 = cudaGetLastError();
   if (e2 != cudaSuccess) return fq_cuda_fail(e2, "band chain");

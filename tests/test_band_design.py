@@ -9,9 +9,8 @@ FP64 on CPU against the oracle, free of the emulation's rounding:
   * the tile window of 64 operator rows [i0, i0 + 64), state columns [i0 - 48, i0 + 112), holds
     every row's band, and each row's window positions land inside the 160 columns of its tile;
   * one drain per tile keeps the three exact FP32 sums exact (3 pairs x 2^14 x 320 < 2^24);
-  * the scale of each output row, fixed before the row is complete, bounds its entries;
-  * the 48-bit fixed-point value of a double-float pair, taken from the FP32 bit patterns,
-    is within one unit of the exact value."""
+  * the FP32 cut of a double-float state entry into its 8-bit digits (k_band_slice) is exact to
+    2^-49 of the row scale, with digits that keep the tensor-core sums exact."""
 import math
 from fractions import Fraction
 
@@ -117,66 +116,6 @@ def test_one_drain_per_tile_is_exact():
     represents every partial sum exactly."""
     assert 3 * 2 ** 14 * (2 * KW) < 2 ** 24
     assert 3 * 2 ** 14 * (2 * (KW + 32)) > 2 ** 24   # two more K stages would need a second drain
-
-
-def _fixed48_f32(x: np.float32, E: int) -> int:
-    """The kernel's fixed48_f32: round(x 2^(48 - E)) from the FP32 bit pattern, by shifts."""
-    bits = int(np.array(x, dtype=np.float32).view(np.uint32))
-    b = (bits >> 23) & 0xFF
-    if b == 0:
-        return 0
-    m = (bits & 0x7FFFFF) | 0x800000
-    sh = 102 + E - b
-    if sh <= 0:
-        R = m << (-sh)
-    elif sh >= 64:
-        R = 0
-    else:
-        R = (m + (1 << (sh - 1))) >> sh
-    return -R if bits >> 31 else R
-
-
-def test_double_float_fixed_point_within_one_unit():
-    """fixed(hi) + fixed(lo) against the exact round((hi + lo) 2^(48 - E)) for double-float pairs
-    of random magnitudes below 2^(E - 1) (the band kernel's epilogue cuts its double-float sums
-    into the next product's digits this way)."""
-    rng = np.random.default_rng(3)
-    for _ in range(2000):
-        x = float(rng.uniform(-1, 1) * 2.0 ** rng.integers(-30, 1))
-        h = np.float32(x)
-        lo = np.float32(x - float(h))
-        E = int(np.frexp(abs(float(h)) if h != 0 else 1.0)[1]) + 1   # |h| < 2^(E - 1)
-        exact = Fraction(float(h)) + Fraction(float(lo))
-        R = _fixed48_f32(h, E) + _fixed48_f32(lo, E)
-        target = exact * Fraction(2) ** (48 - E)
-        assert abs(Fraction(R) - target) <= 1
-
-
-def test_output_scale_bound_holds():
-    """The epilogue scales row j of X_m by 2^E, E = u + 2 + G, before the row is complete: u is the
-    exponent of the input row's largest |Re| or |Im| (so that maximum is below 2^(u+1)) and 2^G >=
-    rho, the largest row sum of |Re P| + |Im P|.  Since |Re y_i|, |Im y_i| <= sum_k (|Re P_ik| +
-    |Im P_ik|) max(|Re x|, |Im x|), every output entry stays below 2^(E-1), as the digits need.
-    Checked on the real step operators of a driven dimer and on states of every spread, against
-    the computed products."""
-    h0d, h0o, h1d, plan, k_low, _ = dimer_step(nb=120, M=30)
-    n = h0d.shape[0]
-    rng = np.random.default_rng(11)
-    for m in (0, 9, 29):
-        d, lower = o.omega_tilde_tridiag(h0d, h0o, h1d, k_low, plan, m)
-        P = o.chebyshev_step(lambda v: o.apply_tridiag(d, lower, v), np.eye(n, dtype=complex), plan.coeffs,
-                             plan.phase)
-        rho = np.max(np.sum(np.abs(P.real) + np.abs(P.imag), axis=1))
-        G = max(0, math.ceil(math.log2(rho)))
-        for spread in (1, 5, n):
-            x = np.zeros(n, complex)
-            idx = rng.choice(n, spread, replace=False)
-            x[idx] = rng.normal(size=spread) + 1j * rng.normal(size=spread)
-            x /= np.linalg.norm(x)
-            u = math.frexp(np.max(np.abs(np.concatenate([x.real, x.imag]))))[1] - 1
-            y = P @ x
-            E = u + 2 + G
-            assert np.max(np.abs(np.concatenate([y.real, y.imag]))) < 2.0 ** (E - 1)
 
 
 def _f(x):
