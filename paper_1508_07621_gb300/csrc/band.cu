@@ -95,11 +95,13 @@ __device__ __forceinline__ void band_apply(const dflc (&x)[BAND_LANE_ROWS], dflc
 }
 
 // Rows i < nrows of P_m into the right operand slices and their exponents et[i] (rows >= n are
-// zero); one warp per row.  cf, rot: the step's gauge tables (row stride irrelevant: row k).
+// zero); one warp per row.  cf, rot: the step's gauge tables (row stride irrelevant: row k).  Also
+// clears the row-maximum keys kzero[0 .. nzero) that the step's product fills.
 __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
     k_band_rows(const double2* __restrict__ cf, const double2* __restrict__ rot, int n, int nrows, int L,
                 BandCoef coef, double ph_re, double ph_im, size_t rstride, __nv_bfloat16* __restrict__ right,
-                int* __restrict__ et) {
+                int* __restrict__ et, unsigned int* __restrict__ kzero, int nzero) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nzero; q += gridDim.x * blockDim.x) kzero[q] = 0u;
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * BAND_ROWS_PER_CTA + (threadIdx.x >> 5);
   if (i >= nrows) return;  // whole warp
@@ -249,13 +251,17 @@ __device__ __forceinline__ bool df_digits2(float2 a, float2 b, __nv_bfloat16 (&d
 
 // Left slices of double-float state rows: one CTA per row j of the padded block (rows >= nc and
 // columns >= n are zero), the scale 2^E from the row's largest |hi| part, the digits by the FP32
-// cut of df_digits2 (re and im packed).
+// cut of df_digits2 (re and im packed).  kmax (if not NULL) holds each row's largest |hi| as an
+// FP32 key, collected by the product that wrote the states; otherwise a first pass finds it.
 __global__ void k_band_slice(const float4* __restrict__ x, int n, int ld, int nc, int npl, size_t astride,
-                             __nv_bfloat16* __restrict__ left, int* __restrict__ es) {
+                             __nv_bfloat16* __restrict__ left, int* __restrict__ es,
+                             const unsigned int* __restrict__ kmax) {
   __shared__ unsigned long long red[32];
   const int j = blockIdx.x;
   unsigned long long m = 0;
-  if (j < nc)
+  if (kmax) {
+    if (j < nc && threadIdx.x == 0) m = kmax[j];
+  } else if (j < nc)
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       const float4 v = x[(size_t)j * ld + k];
       // |hi| as an ordered key (FP32 bit pattern; no FP64 conversion): the row maximum of |hi|
@@ -292,6 +298,7 @@ constexpr int BAND_RG = 16;  // state blocks per raster group
 
 struct BandEpi {
   float4* out;     // X_m, double-float [nc][ld]
+  unsigned int* kmax;  // per row of X_m: largest |hi| of re or im as an FP32 key (atomicMax)
   const int* es;   // row exponents of the left slices
   const int* et;   // row exponents of the right slices
   int n, nc, ld;
@@ -472,6 +479,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       if (j < e.nc) {
         const int ej = e.es[j];
         float4* orow = e.out + (size_t)j * e.ld;
+        unsigned int kmx = 0u;
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int i = i0 + part * 16 + c;
@@ -486,8 +494,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const float rl = __fsub_rn(rl0, __fsub_rn(rh, rh0)), il = __fsub_rn(il0, __fsub_rn(ih, ih0));
             bad |= !(rh * rh + ih * ih <= e.bound2);
             orow[i] = make_float4(rh, rl, ih, il);
+            const unsigned int kr = __float_as_uint(rh) & 0x7FFFFFFFu, ki = __float_as_uint(ih) & 0x7FFFFFFFu;
+            kmx = kr > kmx ? kr : kmx;
+            kmx = ki > kmx ? ki : kmx;
           }
         }
+        atomicMax(e.kmax + j, kmx);
       }
     }
     if (!ok) {
@@ -558,6 +570,7 @@ struct BandWs {
   int* et;
   __nv_bfloat16* left;
   int* es;
+  unsigned int* kmax;
   float4* x[2];
   int nrows, npl, ncp;
   size_t rstride, astride;
@@ -585,6 +598,7 @@ size_t band_layout(const fq_plan* p, int nc, int nsteps, void* base, BandWs* out
   w.et = (int*)take(sizeof(int) * w.nrows);
   w.left = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.astride);
   w.es = (int*)take(sizeof(int) * w.ncp);
+  w.kmax = (unsigned int*)take(sizeof(unsigned int) * w.ncp);
   for (int q = 0; q < 2; ++q) w.x[q] = (float4*)take(sizeof(float4) * (size_t)nc * w.npl);
   if (out) *out = w;
   return off;
@@ -646,11 +660,15 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
   e.status = p->d_status;
   int cur = 0;
   for (int m = 0; m < nsteps; ++m) {
+    // the states' slices (their row maxima from the previous product; the first step finds them),
+    // then P_m (clearing the maxima for this product), then the product
+    k_band_slice<<<w.ncp, 256, 0, s>>>(w.x[cur], n, w.npl, nc, w.npl, w.astride, w.left, w.es,
+                                       m == 0 ? nullptr : w.kmax);
     k_band_rows<<<(w.nrows + BAND_ROWS_PER_CTA - 1) / BAND_ROWS_PER_CTA, 32 * BAND_ROWS_PER_CTA, 0, s>>>(
         w.cf + (size_t)m * w.nrows, w.rot + (size_t)m * w.nrows, n, w.nrows, L, coef, p->phase_re, p->phase_im,
-        w.rstride, w.right, w.et);
-    k_band_slice<<<w.ncp, 256, 0, s>>>(w.x[cur], n, w.npl, nc, w.npl, w.astride, w.left, w.es);
+        w.rstride, w.right, w.et, w.kmax, w.ncp);
     e.out = w.x[cur ^ 1];
+    e.kmax = w.kmax;
     k_oz_band<<<std::min(ntiles, sms), OZ_THREADS, OzCfg::SMEM, s>>>(maps, tiles_j, tiles_i, w.npl, e);
     cur ^= 1;
   }
