@@ -37,10 +37,18 @@ STEPS = 2000
 FLOPS_PER_ELEMENT_TERM = 26   # complex tridiagonal apply 18 + recurrence 4 + Bessel accumulation 4
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM traffic of the resident kernel from one ncu capture of `--ncu-case resident` (152 states,
-# steps 0..19, k_tri_resident<256, 40>): bytes read, of which the 152 initial states are a fixed
-# part; the rest is the per-step (2d, 2e') and rotation stream, which grows with waves x steps.
-RES_NCU = {"read": 28.519936e6, "x0": 152 * 10001 * 16, "states": 152, "steps": 20}
-RES_TRAFFIC_NOTE = "see profiles/k_tri_resident_dimer10001.md for the DRAM bytes of the resident kernel"
+# steps 0..19, k_tri_resident<256, 40>, the current kernel with its L2 prefetch): bytes read, of
+# which the 152 initial states are a fixed part; the rest is the per-step (2d, 2e') and rotation
+# stream, which grows with waves x steps.  A build also writes U_T once.
+RES_NCU = {"read": 28515072.0, "x0": 152 * 10001 * 16, "states": 152, "steps": 20}
+RES_TRAFFIC_NOTE = ("per-wave-step coefficient reads of one ncu capture (profiles/k_tri_resident_dimer10001.md) "
+                    "x waves x steps, plus the 16 N^2 bytes of U_T")
+
+
+def resident_traffic(n, steps, states):
+    """DRAM bytes of one resident launch over `states` states, scaled from the capture."""
+    per_wave_step = (RES_NCU["read"] - RES_NCU["x0"]) / RES_NCU["steps"]
+    return per_wave_step * (states / RES_NCU["states"]) * steps + 16.0 * n * states
 # double-float tiled chain: FP32 lane operations per element-term (4 complex double-float FMAs of
 # 15 packed FP32x2 operations each)
 DFL_LANE_OPS_PER_ELEMENT_TERM = 120
@@ -78,8 +86,8 @@ def parse():
                     help="paper-table1: the matrix size (the rows of the paper's Table 1)")
     ap.add_argument("--precision", choices=["x3", "x6", "ozaki", "fp64", "fp32", "df32"], default=None,
                     help="goe4096 / adjoint / batch: BF16X3 (default), BF16X6, FQ_OZAKI (FP64 emulation) or FP64 "
-                         "(adjoint only); dimer: df32 (double-float tiled, FP64-level; default), ozaki (band "
-                         "kernel on the tensor cores, FP64-level) or fp32 (resident)")
+                         "(adjoint only); dimer: ozaki (band kernel on the tensor cores, FP64-level; default), "
+                         "df32 (double-float tiled, FP64-level) or fp32 (resident)")
     ap.add_argument("--ncu-case", choices=["resident", "stream", "split", "tile", "dfl", "band", "adjoint", "ozaki",
                                            "dense-resident", "ozaki-grad"],
                     default=None,
@@ -362,6 +370,12 @@ DIMER_PATHS = {
 }
 
 
+# DRAM bytes of one k_oz_band launch (one step's banded product) from the ncu capture of
+# `python bench.py --ncu-case band` (2048 states; profiles/k_oz_band_dimer10001.md), scaled to a
+# launch by states: the state slices read and the new states written grow with the states.
+BAND_NCU = {"read": None, "write": None, "states": 2048}
+
+
 def band_issued_flops(n, nc):
     """BF16 MMA flops the band kernel issues per step: tiles of 128 states x 64 operator rows, a
     160-column K window, 21 slice pairs of two N = 128 MMAs."""
@@ -405,7 +419,7 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     paper = args.workload == "dimer-paper"
-    prec = args.precision or "df32"
+    prec = args.precision or "ozaki"
     if prec not in DIMER_PATHS:
         raise SystemExit(f"--precision for the dimer: one of {sorted(DIMER_PATHS)}")
     path = DIMER_PATHS[prec]
@@ -496,8 +510,10 @@ def run_ours(args):
         avg32 = statistics.mean(ps32)
         fp32 = {"value": v32, "unit": "U_T/s", "ms_per_step": 1000.0 * tot32 / args.fp32_steps,
                 "steps": args.fp32_steps, "dtype": "f32", "per_step_s": ps32, "clocks": clk32,
-                "roofline": dimer_roofline(DIMER_PATHS["fp32"], n, d.steps, L, avg32,
-                                           float(n) * n * d.steps * L / (world if sharded else 1))}
+                "roofline": dict(dimer_roofline(DIMER_PATHS["fp32"], n, d.steps, L, avg32,
+                                                float(n) * n * d.steps * L / (world if sharded else 1)),
+                                 traffic=resident_traffic(n, d.steps, n / (world if sharded else 1)),
+                                 traffic_note=RES_TRAFFIC_NOTE)}
         p32.close()
 
     if rank != 0:
@@ -507,13 +523,18 @@ def run_ours(args):
     avg = statistics.mean(per_step)
     if prec == "fp32":  # one launch per U_T: the whole chain
         roofline = dimer_roofline(path, n, d.steps, L, avg, float(n) * n * d.steps * L / (world if sharded else 1))
-        roofline["traffic"] = None
+        roofline["traffic"] = resident_traffic(n, d.steps, n / (world if sharded else 1))
         roofline["traffic_note"] = RES_TRAFFIC_NOTE
     else:  # one launch per step: units of one launch over the launch's mean duration
         per_launch = float(n) * n * L / (world if sharded else 1)
         roofline = dimer_roofline(path, n, d.steps, L, avg / d.steps, per_launch)
         roofline["traffic"] = None
         roofline["traffic_note"] = "see profiles/ for the kernel's DRAM bytes per launch"
+        if prec == "ozaki" and BAND_NCU["read"] is not None:
+            roofline["traffic"] = (BAND_NCU["read"] + BAND_NCU["write"]) * (n / (world if sharded else 1)) / \
+                BAND_NCU["states"]
+            roofline["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of k_oz_band from one ncu capture "
+                                        "of --ncu-case band (2048 states), scaled to a launch by states")
         roofline["launch_seconds_note"] = ("mean U_T time / M, which also holds the step's other launches "
                                            "(their share is in the profiles' launch list)")
     cpu = None
@@ -680,15 +701,15 @@ def run_dense(args):
     useful = 8.0 * n ** 3 * L * m.steps
     issued = useful * SLICE_PRODUCTS[prec]
     avg = statistics.mean(per_step)
-    achieved = issued / avg / 1e12
+    achieved = useful / avg / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
                 "frac": achieved / peaks["bf16_sustained"], "traffic": None,
                 "kernel": "k_oz_term" if prec == "ozaki" else "k_split_persist",
-                "useful_tflops": useful / avg / 1e12,
-                "note": (f"issued BF16 MMA flop = {SLICE_PRODUCTS[prec]} slice products x 8 N^3 per term x M L terms "
-                         "per build over the build's CUDA-event time (the operator and slicing kernels, a few "
-                         f"percent, included); peak: {peaks['source']} sustained cuBLAS bf16 (a build is seconds "
-                         "of back-to-back GEMMs)")}
+                "issued_tflops": issued / avg / 1e12, "issued_frac": issued / avg / 1e12 / peaks["bf16_sustained"],
+                "note": (f"achieved: useful 8 N^3 flop per term x M L terms per build; issued: the "
+                         f"{SLICE_PRODUCTS[prec]} BF16 slice products each term runs; both over the build's "
+                         "CUDA-event time (the operator and slicing kernels, a few percent, included); peak: "
+                         f"{peaks['source']} sustained cuBLAS bf16 (a build is seconds of back-to-back GEMMs)")}
     accuracy = {"unitarity_defect_max": defect_max, "unitarity_defect_fro": defect_fro,
                 "defect_columns": int(sample_cols.numel())}
     cpu = None
@@ -848,14 +869,14 @@ def run_batch(args):
     useful = batch_flops(insts, Ls)
     issued = useful * SLICE_PRODUCTS[prec]
     avg = statistics.mean(per_step)
-    achieved = issued / avg / 1e12
+    achieved = useful / avg / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
                 "frac": achieved / peaks["bf16_sustained"], "traffic": None,
                 "kernel": "k_oz_term" if prec == "ozaki" else "k_split_persist",
-                "useful_tflops": useful / avg / 1e12,
-                "note": (f"issued BF16 MMA flop = {SLICE_PRODUCTS[prec]} slice products x 8 N_i^3 L_i M summed over "
-                         f"the {len(plans)} instances, over one graph launch's CUDA-event time; peak: "
-                         f"{peaks['source']} sustained cuBLAS bf16")}
+                "issued_tflops": issued / avg / 1e12, "issued_frac": issued / avg / 1e12 / peaks["bf16_sustained"],
+                "note": (f"achieved: useful 8 N_i^3 L_i M flop summed over the {len(plans)} instances; issued: "
+                         f"x {SLICE_PRODUCTS[prec]} BF16 slice products; both over one graph launch's CUDA-event "
+                         f"time; peak: {peaks['source']} sustained cuBLAS bf16")}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         v, dt, desc = batch_oracle_sample(insts)
@@ -957,7 +978,7 @@ def run_adjoint(args):
     useful = 4.0 * M * L * 4.0 * n ** 3
     issued = useful * SLICE_PRODUCTS[prec]
     avg = statistics.mean(per_step)
-    achieved = issued / avg / 1e12
+    achieved = useful / avg / 1e12
     if prec == "fp64":
         roofline = {"bound": "alu", "achieved": achieved, "peak": 1.19, "unit": "TFLOP/s", "frac": achieved / 1.19,
                     "traffic": None, "kernel": "k_adj_term / k_dot / dense_tile_f64",
@@ -966,10 +987,11 @@ def run_adjoint(args):
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
                     "frac": achieved / peaks["bf16_sustained"], "traffic": None,
                     "kernel": "k_oz_real_term<*>" if prec == "ozaki" else "k_split_persist / k_split_term",
-                    "useful_tflops": useful / avg / 1e12,
-                    "note": (f"issued BF16 MMA flop = {SLICE_PRODUCTS[prec]} slice products x 4 M L x 4 N^3 per "
-                             "gradient over the gradient's CUDA-event time (every other kernel included); peak: "
-                             f"{peaks['source']} sustained cuBLAS bf16")}
+                    "issued_tflops": issued / avg / 1e12,
+                    "issued_frac": issued / avg / 1e12 / peaks["bf16_sustained"],
+                    "note": (f"achieved: useful 4 M L x 4 N^3 flop per gradient; issued: x {SLICE_PRODUCTS[prec]} "
+                             "BF16 slice products; both over the gradient's CUDA-event time (every other kernel "
+                             f"included); peak: {peaks['source']} sustained cuBLAS bf16")}
     accuracy = {"loss": loss_value}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
