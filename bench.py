@@ -373,7 +373,7 @@ DIMER_PATHS = {
 # DRAM bytes of one k_oz_band launch (one step's banded product) from the ncu capture of
 # `python bench.py --ncu-case band` (2048 states; profiles/k_oz_band_dimer10001.md), scaled to a
 # launch by states: the state slices read and the new states written grow with the states.
-BAND_NCU = {"read": None, "write": None, "states": 2048}
+BAND_NCU = {"read": 586.6e6, "write": 297.3e6, "states": 2048}
 
 
 def band_issued_flops(n, nc):
