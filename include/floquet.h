@@ -188,6 +188,26 @@ size_t floquet_workspace_size(const fq_plan* plan, int32_t ncols);
  * by floquet_check_status. */
 fq_status floquet_build_UT(fq_plan* plan, void* d_U, void* d_ws, size_t ws_bytes, void* stream);
 
+/* What a build reports (§8(b)): the planning results it ran with (L, R, the bounds of Eq. 11),
+ * the unitarity defect of the U_T it wrote (max |U^+U - 1| entry and Frobenius / sqrt(k) over k
+ * evenly spaced columns, FP64 on the device, as floquet_unitarity_defect) and the device time of
+ * the build measured by CUDA events on the stream. */
+typedef struct fq_report {
+  int32_t L, defect_columns;
+  double R, e_min, e_max, beta, delta_e;
+  double defect_max, defect_fro;
+  double build_ms;
+} fq_report;
+
+/* floquet_build_UT followed by its report: the same build (same kernels, same result), then the
+ * defect over defect_columns evenly spaced columns (1 <= defect_columns <= N; the workspace,
+ * free after the build, holds the defect's scratch) and the timing.  Synchronises `stream`.
+ * d_ws: floquet_workspace_size(plan, N) bytes, and at least floquet_defect_workspace_size(N) +
+ * 4 defect_columns + 256 bytes.  FQ_EINVAL for a NULL report or a bad column count, otherwise as
+ * floquet_build_UT; FQ_EBOUND if the build's device checks fired (the report is still filled). */
+fq_status floquet_build_UT_report(fq_plan* plan, void* d_U, void* d_ws, size_t ws_bytes, void* stream,
+                                  int32_t defect_columns, fq_report* report);
+
 /* Propagates a block of ncols states through steps m_begin .. m_end-1 (0-based), i.e.
  * X = U_{m_end} ... U_{m_begin+1} X0 (Eq. 9 restricted to those steps).  d_X0, d_X: ncols x N
  * complex128, row r = state r, caller-owned device memory; d_X may equal d_X0.  FQ_EINVAL for a

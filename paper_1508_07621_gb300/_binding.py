@@ -42,6 +42,13 @@ class fq_plan_info(ctypes.Structure):
                 ("beta", ctypes.c_double), ("delta_e", ctypes.c_double), ("R", ctypes.c_double)]
 
 
+class fq_report(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("defect_columns", ctypes.c_int32), ("R", ctypes.c_double),
+                ("e_min", ctypes.c_double), ("e_max", ctypes.c_double), ("beta", ctypes.c_double),
+                ("delta_e", ctypes.c_double), ("defect_max", ctypes.c_double), ("defect_fro", ctypes.c_double),
+                ("build_ms", ctypes.c_double)]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is not built; run paper_1508_07621_gb300.build.build() "
                       "(nvcc for sm_103a) first - there is no CPU fallback")
@@ -56,6 +63,7 @@ _SIGS = {
     "floquet_workspace_size": (_sz, [_vp, _i32]),
     "floquet_build_UT": (ctypes.c_int, [_vp, _vp, _vp, _sz, _vp]),
     "floquet_propagate": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _sz, _vp]),
+    "floquet_build_UT_report": (ctypes.c_int, [_vp, _vp, _vp, _sz, _vp, _i32, ctypes.POINTER(fq_report)]),
     "floquet_columns_workspace_size": (_sz, [_vp, _i32]),
     "floquet_build_UT_columns": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _sz, _vp]),
     "floquet_defect_workspace_size": (_sz, [_i32]),
@@ -205,6 +213,18 @@ def floquet_build_UT(plan: int, U, ws, stream=None) -> None:
     pu = _dev(U, _c128(), n * n, "U", w)
     pw, nb = _ws(ws, w)
     _check(lib.floquet_build_UT(_vp(plan), pu, pw, nb, _stream(stream)), w)
+
+
+def floquet_build_UT_report(plan: int, U, ws, defect_columns: int = 64, stream=None) -> fq_report:
+    """floquet_build_UT plus its report (planning results, sampled unitarity defect, device time)."""
+    w = "floquet_build_UT_report"
+    n = floquet_plan_get_info(plan).n
+    pu = _dev(U, _c128(), n * n, "U", w)
+    pw, nb = _ws(ws, w)
+    rep = fq_report()
+    _check(lib.floquet_build_UT_report(_vp(plan), pu, pw, nb, _stream(stream), int(defect_columns),
+                                       ctypes.byref(rep)), w)
+    return rep
 
 
 def floquet_propagate(plan: int, X0, X, ncols: int, m_begin: int, m_end: int, ws, stream=None) -> None:

@@ -467,6 +467,55 @@ fq_status floquet_build_UT(fq_plan* p, void* d_U, void* d_ws, size_t ws_bytes, v
   return propagate_impl(p, nullptr, (double*)d_U, p->n, 0, p->steps, 1, 1, d_ws, ws_bytes, (cudaStream_t)stream);
 }
 
+fq_status floquet_build_UT_report(fq_plan* p, void* d_U, void* d_ws, size_t ws_bytes, void* stream,
+                                  int32_t defect_columns, fq_report* rep) {
+  if (!p || !d_U || !rep) { fq_set_error("NULL plan, output or report"); return FQ_EINVAL; }
+  const int n = p->n;
+  if (defect_columns < 1 || defect_columns > n) {
+    fq_set_error("floquet_build_UT_report: defect_columns must be in [1, %d] (got %d)", n, defect_columns);
+    return FQ_EINVAL;
+  }
+  const size_t dws = floquet_defect_workspace_size(n), need = dws + align_up(4 * (size_t)defect_columns);
+  if (!d_ws || ws_bytes < need) {
+    fq_set_error("floquet_build_UT_report: workspace must hold %zu bytes for the defect", need);
+    return FQ_EINVAL;
+  }
+  return fq_guard("floquet_build_UT_report", [&]() -> fq_status {
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+    fq_status st = ce == cudaSuccess ? floquet_build_UT(p, d_U, d_ws, ws_bytes, stream) : fq_cuda_fail(ce, "events");
+    if (st == FQ_OK && (ce = cudaEventRecord(e1, s)) != cudaSuccess) st = fq_cuda_fail(ce, "event record");
+    // the workspace is free again: the defect's partial sums, then the column list
+    std::vector<int32_t> cols(defect_columns);
+    for (int q = 0; q < defect_columns; ++q) cols[q] = (int32_t)(((int64_t)q * n) / defect_columns);
+    int32_t* d_cols = (int32_t*)((char*)d_ws + dws);
+    if (st == FQ_OK && (ce = cudaMemcpyAsync(d_cols, cols.data(), 4 * cols.size(), cudaMemcpyHostToDevice, s)) !=
+                           cudaSuccess)
+      st = fq_cuda_fail(ce, "defect columns");
+    double mx = 0.0, fro = 0.0;
+    if (st == FQ_OK) st = floquet_unitarity_defect(d_U, n, d_cols, defect_columns, d_ws, dws, stream, &mx, &fro);
+    float ms = 0.f;
+    if (st == FQ_OK && (ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) st = fq_cuda_fail(ce, "event time");
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != FQ_OK) return st;
+    rep->L = p->L;
+    rep->defect_columns = defect_columns;
+    rep->R = p->R;
+    rep->e_min = p->e_min;
+    rep->e_max = p->e_max;
+    rep->beta = p->beta;
+    rep->delta_e = p->delta_e;
+    rep->defect_max = mx;
+    rep->defect_fro = fro;
+    rep->build_ms = ms;
+    return floquet_check_status(p, stream);
+  });
+}
+
 fq_status floquet_propagate(fq_plan* p, const void* d_X0, void* d_X, int32_t ncols, int32_t m_begin, int32_t m_end,
                             void* d_ws, size_t ws_bytes, void* stream) {
   if (!p || !d_X0 || !d_X) { fq_set_error("NULL plan or state pointer"); return FQ_EINVAL; }

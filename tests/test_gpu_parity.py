@@ -360,6 +360,29 @@ def test_column_slices_bitwise_and_deterministic(fq, case):
         assert torch.equal(X.transpose(0, 1), U[:, a:b])
 
 
+@pytest.mark.parametrize("precision,kernel", [(1, 2), (5, 4), (0, 1)])
+def test_build_report(fq, precision, kernel):
+    """floquet_build_UT_report: the same U_T as floquet_build_UT bit for bit, the plan's L, R and
+    bounds, a unitarity defect at the path's level over sampled columns and a positive device time;
+    a bad column count is refused."""
+    import torch
+    d = fi.config_dimer(nb=300, steps=200)
+    plan = dimer_plan(fq, d, precision, kernel)
+    ref = plan.build_UT()
+    U = torch.empty_like(ref)
+    ws = fq.workspace(plan.workspace_size())
+    rep = fq.floquet_build_UT_report(plan.handle, U, ws, 32)
+    assert torch.equal(U, ref)
+    info = plan.info
+    assert rep.L == info.L and rep.R == info.R and rep.e_min == info.e_min and rep.e_max == info.e_max
+    assert rep.beta == info.beta and rep.delta_e == info.delta_e and rep.defect_columns == 32
+    assert rep.defect_max <= (2 * f32_bound(d.steps, info.L, info.R) if precision == 1 else 1e-10)
+    assert 0 < rep.defect_fro <= rep.defect_max * math.sqrt(d.n) and rep.build_ms > 0
+    with pytest.raises(fq.FloquetError) as e:
+        fq.floquet_build_UT_report(plan.handle, U, ws, d.n + 1)
+    assert e.value.status == fq.FQ_EINVAL
+
+
 @pytest.mark.parametrize("case", ["resident", "dfl", "dense64", "split"])
 def test_column_blocks_assemble_build_UT(fq, case):
     """floquet_build_UT_columns (one rank's share of the column split, §5): the uneven blocks a
