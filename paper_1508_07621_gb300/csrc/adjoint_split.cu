@@ -136,6 +136,7 @@ struct SplitGradWs {
   Master bbar;            // bbar_1 .. bbar_L of one step: L blocks of ncp rows (padding rows zero)
   float* ck_base;         // nseg checkpoints of X, each 2 planes [n][ldm]
   double2* partial;       // (L + 1) x ncta
+  unsigned int* flags;    // chain counters [CHAIN_MAXP][row blocks]
   double2* tau_partial;   // n
   double2* tau;
   size_t slot_slice() const { return (size_t)nslots * astride; }  // elements between slot slices
@@ -188,6 +189,7 @@ size_t split_grad_layout(const fq_plan* p, void* base, SplitGradWs* out) {
   w.bbar = Master{bb, bb ? bb + stacked : nullptr};
   w.ck_base = (float*)take(sizeof(float) * 2 * plane * (size_t)w.nseg);
   w.partial = (double2*)take(sizeof(double2) * (size_t)(L + 1) * w.ncta);
+  w.flags = (unsigned int*)take(sizeof(unsigned int) * CHAIN_MAXP * (size_t)(w.ncp / BM));
   w.tau_partial = (double2*)take(sizeof(double2) * n);
   w.tau = (double2*)take(sizeof(double2));
   if (out) *out = w;
@@ -249,6 +251,55 @@ fq_status gemm(const GemmCtx& c, Left left, const __nv_bfloat16* right, const Sp
   return c.bn == 128 ? gemm_cfg<2, 128, 32, EPI>(c, left, right, e, s) : gemm_cfg<2, 64, 64, EPI>(c, left, right, e, s);
 }
 
+// A chain of products with one right operand (the step's Omega~_m) as one cooperative launch
+// (split_core.cuh); FQ_EUNSUPPORTED where a chain cannot run (the caller launches each product).
+template <int NS, int BN, int BKE, int EPI>
+fq_status chain_cfg(const GemmCtx& c, const Left* lefts, const SplitEpi* eps, int nprod, const __nv_bfloat16* right,
+                    unsigned int* flags, cudaStream_t s) {
+  if (nprod > CHAIN_MAXP) return FQ_EUNSUPPORTED;
+  ChainArgs ch{};
+  fq_status st;
+  for (int q = 0; q < NS; ++q)
+    if ((st = make_map(&ch.rmaps.os[q], right + q * c.bstride, c.np, c.np, BN, BKE)) != FQ_OK) return st;
+  for (int pp = 0; pp < nprod; ++pp) {
+    for (int q = 0; q < NS; ++q)
+      if ((st = make_map(&ch.left[pp][q], lefts[pp].base + q * lefts[pp].lstride, lefts[pp].rows, c.kp, BM, BKE)) !=
+          FQ_OK)
+        return st;
+    ch.epi[pp] = eps[pp];
+  }
+  ch.nprod = nprod;
+  ch.nk = c.np / BKE;
+  ch.tiles_i = c.np / BN;
+  ch.tiles_j = lefts[0].rows / BM;
+  ch.flags = flags;
+  cudaError_t ce = cudaMemsetAsync(flags, 0, sizeof(unsigned int) * (size_t)nprod * ch.tiles_j, s);
+  if (ce != cudaSuccess) return fq_cuda_fail(ce, "chain counters");
+  return launch_chain<NS, BN, BKE, EPI, false>(ch, s);
+}
+
+template <int EPI>
+fq_status chain(const GemmCtx& c, const Left* lefts, const SplitEpi* eps, int nprod, const __nv_bfloat16* right,
+                unsigned int* flags, cudaStream_t s) {
+  if (c.ns == 3)
+    return c.bn == 128 ? chain_cfg<3, 128, 32, EPI>(c, lefts, eps, nprod, right, flags, s)
+                       : chain_cfg<3, 64, 32, EPI>(c, lefts, eps, nprod, right, flags, s);
+  return c.bn == 128 ? chain_cfg<2, 128, 32, EPI>(c, lefts, eps, nprod, right, flags, s)
+                     : chain_cfg<2, 64, 64, EPI>(c, lefts, eps, nprod, right, flags, s);
+}
+
+// The products of a chain: one cooperative launch, else one launch each.
+template <int EPI>
+fq_status run_products(const GemmCtx& c, const std::vector<Left>& lefts, const std::vector<SplitEpi>& eps,
+                       const __nv_bfloat16* right, unsigned int* flags, cudaStream_t s) {
+  const int nprod = (int)eps.size();
+  fq_status st = chain<EPI>(c, lefts.data(), eps.data(), nprod, right, flags, s);
+  if (st != FQ_EUNSUPPORTED) return st;
+  for (int pp = 0; pp < nprod; ++pp)
+    if ((st = gemm<EPI>(c, lefts[pp], right, eps[pp], s)) != FQ_OK) return st;
+  return FQ_OK;
+}
+
 template <int NS>
 void launch_real_slices(const fq_plan* p, const double* f, int m, bool omega, const SplitGradWs& w, cudaStream_t s) {
   if (omega)
@@ -306,6 +357,8 @@ struct Runner {
     t.bound2 = 1.0 + 2e-3;
     t.status = p->d_status;
     int cur = *xb, nxt = (*xb + 1) % 3, acc = (*xb + 2) % 3, prv = -1;
+    std::vector<SplitEpi> eps(L);
+    std::vector<Left> lefts(L);
     for (int l = 0; l < L; ++l) {
       t.first = l == 0;
       t.last = l == L - 1;
@@ -323,8 +376,8 @@ struct Runner {
       e.slice_out = left[l + 1];
       e.slice_stride = stride;
       e.t = t;
-      fq_status st = gemm<EPI_FWD>(c, Left{left[l], stride, w.ncp}, w.S, e, s);
-      if (st != FQ_OK) return st;
+      eps[l] = e;
+      lefts[l] = Left{left[l], stride, w.ncp};
       if (t.last) {
         *xb = out;
       } else {
@@ -332,7 +385,7 @@ struct Runner {
         cur = out;
       }
     }
-    return FQ_OK;
+    return run_products<EPI_FWD>(c, lefts, eps, w.S, w.flags, s);
   }
 };
 
@@ -401,6 +454,8 @@ fq_status fq_grad_split(fq_plan* p, const double* d_f, const void* d_W, double* 
       const double aL = p->cheb[L];
       r.scale_slices(w.f[gi], (float)(cph_r * aL), (float)(cph_i * aL), w.bbar_block(L), w.lsl[0], w.astride);
       int sl = 0;
+      std::vector<SplitEpi> aeps;
+      std::vector<Left> alefts;
       for (int l = L - 1; l >= 0; --l) {
         const double a = p->cheb[l];
         const Master out = l >= 1 ? w.bbar_block(l) : w.f[gn];
@@ -416,9 +471,11 @@ fq_status fq_grad_split(fq_plan* p, const double* d_f, const void* d_W, double* 
         e.cpa_im = (float)(cph_i * a);
         e.cw = l == 0 ? 1.f : 2.f;
         e.t.bound2 = 1e30;  // NaN / overflow check only
-        if ((st = gemm<EPI_ADJ>(r.c, Left{w.lsl[sl], w.astride, w.ncp}, w.S, e, s)) != FQ_OK) return st;
+        aeps.push_back(e);
+        alefts.push_back(Left{w.lsl[sl], w.astride, w.ncp});
         sl ^= 1;
       }
+      if ((st = run_products<EPI_ADJ>(r.c, alefts, aeps, w.S, w.flags, s)) != FQ_OK) return st;
       // D_l = <bbar_l, E psi_{l-1}>, l = 1..L, as one GEMM over the L stacked blocks: psi_0..psi_{L-1}
       // are the consecutive slots st*L .. st*L+L-1, bbar_1..bbar_L the stacked FP32 blocks
       SplitEpi d = r.epi();

@@ -2,6 +2,8 @@
 // the S and A slices of Omega~_m (FP64 arithmetic, Eqs. 11 and 14), then L terms of Eq. 10 through
 // k_split_term (split_core.cuh) whose epilogue applies the recurrence, the Bessel accumulation
 // of Eq. 12 and the step phase, and writes the next term's BF16 slices.
+#include <vector>
+
 #include "split_core.cuh"
 
 namespace {
@@ -100,6 +102,7 @@ struct SplitWs {
   __nv_bfloat16* oa;  // A slices
   __nv_bfloat16* a[2];
   float* m[3][2];
+  unsigned int* flags;  // chain counters: [CHAIN_MAXP][row blocks]
   int np, kp, ldm, ncp;
   size_t bstride, astride;
 };
@@ -128,6 +131,7 @@ size_t fq_split_workspace(const fq_plan* p, int nc, void* base, void* out) {
   w.a[1] = (__nv_bfloat16*)take(2 * NS * w.astride);
   for (int q = 0; q < 3; ++q)
     for (int r = 0; r < 2; ++r) w.m[q][r] = (float*)take(sizeof(float) * (size_t)nc * w.ldm);
+  w.flags = (unsigned int*)take(sizeof(unsigned int) * CHAIN_MAXP * (size_t)(w.ncp / BM));
   if (out) *(SplitWs*)out = w;
   return off;
 }
@@ -188,13 +192,19 @@ static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int 
       k_split_omega<NS><<<grid_1d(w.bstride), 256, 0, s>>>(p->d_h0, p->d_h1, p->d_k, n, w.np, p->sa[m], p->sb[m],
                                                            p->sc[m], p->sbeta, w.os, w.oa, w.bstride);
     }
+    // the step's L terms: their epilogues and left-operand buffers, then one cooperative chain
+    // launch (a term's tiles start as soon as the previous term has finished their row block), or
+    // one persistent launch per term where a chain cannot run (a capturing stream, L > CHAIN_MAXP)
+    std::vector<SplitEpi> eps(L);
+    std::vector<int> left_of(L);
     int cur = xb, nxt = (xb + 1) % 3, acc = (xb + 2) % 3, prv = -1;
     for (int l = 0; l < L; ++l) {
       t.first = l == 0;
       t.last = l == L - 1;
       t.coef = p->cheb[l + 1];
       const int out = l == 0 ? nxt : prv;
-      SplitEpi e{};
+      SplitEpi& e = eps[l];
+      e = SplitEpi{};
       e.n = n;
       e.nc = nc;
       e.ldm = w.ldm;
@@ -211,7 +221,7 @@ static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int 
       e.slice_out = w.a[av ^ 1];
       e.slice_stride = w.astride;
       e.t = t;
-      k_split_persist<NS, BN, BKE, EPI_FWD, true><<<grid, PTHREADS, Cfg::SMEM, s>>>(maps[av], nk, tiles_j, tiles_i, e);
+      left_of[l] = av;
       av ^= 1;
       if (t.last) {
         xb = out;
@@ -220,6 +230,28 @@ static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int 
         cur = out;
       }
     }
+    st = FQ_EUNSUPPORTED;
+    if (L <= CHAIN_MAXP) {
+      ChainArgs ch{};
+      ch.rmaps = maps[0];
+      ch.nprod = L;
+      ch.nk = nk;
+      ch.tiles_j = tiles_j;
+      ch.tiles_i = tiles_i;
+      ch.flags = w.flags;
+      for (int l = 0; l < L; ++l) {
+        ch.epi[l] = eps[l];
+        for (int q = 0; q < NS; ++q) ch.left[l][q] = maps[left_of[l]].a[q];
+      }
+      cudaError_t ce = cudaMemsetAsync(w.flags, 0, sizeof(unsigned int) * (size_t)L * tiles_j, s);
+      if (ce != cudaSuccess) return fq_cuda_fail(ce, "chain counters");
+      st = launch_chain<NS, BN, BKE, EPI_FWD, true>(ch, s);
+      if (st != FQ_OK && st != FQ_EUNSUPPORTED) return st;
+    }
+    if (st == FQ_EUNSUPPORTED)
+      for (int l = 0; l < L; ++l)
+        k_split_persist<NS, BN, BKE, EPI_FWD, true><<<grid, PTHREADS, Cfg::SMEM, s>>>(maps[left_of[l]], nk, tiles_j,
+                                                                                     tiles_i, eps[l]);
   }
   fq_blk<float> bx{w.m[xb][0], w.m[xb][1]};
   if (x == nullptr) {

@@ -721,6 +721,278 @@ k_split_persist(const __grid_constant__ SplitMaps maps, int nk, int tiles_j, int
   }
 }
 
+// ------------------------------------------------------------------------- chained products
+// A chain of dependent products Y_p = left_p . right^T, p = 0 .. nprod-1, with one right operand
+// (a step's Omega~_m) and product p's left operand written by product p-1's epilogue: the L
+// Chebyshev terms of a step (forward or adjoint).  One cooperative launch runs the whole chain:
+// work unit u = p * tiles + t (tiles in row-block-major order), CTA c takes the units c, c + G, ...
+// in increasing order.  Product p's tiles of state-row block tj need exactly the rows tj of its left
+// operand, i.e. the epilogues of product p-1's tiles (tj, *): a counter per (p - 1, tj) counts their
+// epilogue warps, and the TMA producer waits for it (bounded) before loading.  A unit waits only on units with a
+// smaller index, and all CTAs are resident (cooperative launch), so the chain always advances; the
+// epilogue of one unit overlaps the MMAs of the next as in k_split_persist.
+constexpr int CHAIN_MAXP = 12;
+
+struct ChainArgs {
+  SplitMaps rmaps;                 // right operand (os, oa); its a[] is unused
+  CUtensorMap left[CHAIN_MAXP][3]; // left operand slices of product p
+  SplitEpi epi[CHAIN_MAXP];        // epilogue of product p (slice_out = product p+1's left operand)
+  int nprod, nk, tiles_j, tiles_i;
+  unsigned int* flags;             // [nprod][tiles_j]: finished epilogue warps (4 a tile) of product p in
+                                   // row block tj (zeroed before the launch)
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// bounded wait until *p >= target (acquire); false if it gave up
+__device__ __forceinline__ bool wait_count(const unsigned int* p, unsigned int target) {
+  const long long t0 = clock64();
+  while (ld_acquire_u32(p) < target) {
+    if (clock64() - t0 > kWaitCycles) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+
+template <int NS, int BN, int BKE, int EPI, bool HAS_A>
+__global__ void __launch_bounds__(PTHREADS, 1) k_split_chain(const __grid_constant__ ChainArgs args) {
+  static_assert(EPI != EPI_DOT, "chains of forward or adjoint terms only");
+  using Cfg = SplitCfg<NS, BN, BKE, HAS_A>;
+  constexpr int STAGES = Cfg::STAGES;
+  constexpr uint32_t BUF_COLS = 2 * BN;
+  constexpr uint32_t TMEM_COLS = 2 * BUF_COLS;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * Cfg::STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t tfull0 = smem_u32(bars + 2 * STAGES), tempty0 = smem_u32(bars + 2 * STAGES + 2);
+  const uint32_t done = smem_u32(bars + 2 * STAGES + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles = args.tiles_i * args.tiles_j;
+  const int nunits = args.nprod * tiles;
+  unsigned int* status = args.epi[0].t.status;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, 4);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto unit = [&](int u, int& p, int& tj, int& j0, int& i0) {
+    p = u / tiles;
+    const int t = u - p * tiles;
+    tj = t / args.tiles_i;
+    j0 = tj * BM;
+    i0 = (t - tj * args.tiles_i) * BN;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------- TMA producer: waits for each unit's left operand
+      int g = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        int p, tj, j0, i0;
+        unit(u, p, tj, j0, i0);
+        if (p > 0) {
+          if (!(ok = wait_count(args.flags + (size_t)(p - 1) * args.tiles_j + tj, 4u * args.tiles_i))) break;
+          fence_proxy_async_global();  // the epilogues' generic stores, before this thread's TMA reads
+        }
+        const int np_ = args.epi[p].np;
+        for (int kb = 0; kb < args.nk; ++kb) {
+          const int s = g % STAGES;
+          if (g >= STAGES && !(ok = mbar_wait(empty0 + 8 * s, ((g / STAGES) - 1) & 1))) break;
+          if (*(volatile int*)abort_flag) {
+            ok = false;
+            break;
+          }
+          const uint32_t st = base + s * Cfg::STAGE_BYTES;
+          const uint32_t bar = full0 + 8 * s;
+          mbar_expect_tx(bar, Cfg::STAGE_BYTES);
+          const int kx = kb * BKE;
+#pragma unroll
+          for (int q = 0; q < NS; ++q) {
+            tma_load_2d(st + q * Cfg::A_BYTES, &args.left[p][q], bar, kx, j0);
+            tma_load_2d(st + (NS + q) * Cfg::A_BYTES, &args.left[p][q], bar, np_ + kx, j0);
+            tma_load_2d(st + 2 * NS * Cfg::A_BYTES + q * Cfg::B_BYTES, &args.rmaps.os[q], bar, kx, i0);
+            if (HAS_A)
+              tma_load_2d(st + 2 * NS * Cfg::A_BYTES + (NS + q) * Cfg::B_BYTES, &args.rmaps.oa[q], bar, kx, i0);
+          }
+          ++g;
+        }
+      }
+      if (!ok) {
+        atomicExch(abort_flag, 1);
+        atomicOr(status, FQ_BIT_TIMEOUT);
+      }
+      for (int q = max(0, g - STAGES); q < g; ++q) mbar_wait(full0 + 8 * (q % STAGES), (q / STAGES) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------- MMA issuer (as k_split_persist)
+      constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                 ((uint32_t)(BM >> 4) << 24);
+      constexpr uint32_t idesc_neg = idesc | (1u << 13);
+      int g = 0, i = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++i) {
+        const int b = i & 1;
+        if (i >= 2 && !(ok = mbar_wait(tempty0 + 8 * b, ((i >> 1) - 1) & 1))) break;
+        const uint32_t acc = tmem + (uint32_t)b * BUF_COLS;
+        for (int kb = 0; kb < args.nk; ++kb, ++g) {
+          const int s = g % STAGES;
+          ok = mbar_wait(full0 + 8 * s, (g / STAGES) & 1);
+          if (!ok || *(volatile int*)abort_flag) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = base + s * Cfg::STAGE_BYTES;
+#pragma unroll
+          for (int pp = 0; pp < Pairs<NS>::N; ++pp) {
+            const uint32_t pr = st + Pairs<NS>::a(pp) * Cfg::A_BYTES;
+            const uint32_t pi = st + (NS + Pairs<NS>::a(pp)) * Cfg::A_BYTES;
+            const uint32_t os = st + 2 * NS * Cfg::A_BYTES + Pairs<NS>::b(pp) * Cfg::B_BYTES;
+            const uint32_t oa = st + 2 * NS * Cfg::A_BYTES + (NS + Pairs<NS>::b(pp)) * Cfg::B_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BKE / 16; ++kk) {
+              const uint32_t first = (kb == 0 && pp == 0 && kk == 0) ? 0u : 1u;
+              const uint64_t dpr = smem_desc<Cfg::ROWB>(pr + 32 * kk), dpi = smem_desc<Cfg::ROWB>(pi + 32 * kk);
+              const uint64_t dos = smem_desc<Cfg::ROWB>(os + 32 * kk);
+              if (HAS_A) {
+                const uint64_t doa = smem_desc<Cfg::ROWB>(oa + 32 * kk);
+                mma_bf16(acc, dpr, dos, idesc, first);
+                mma_bf16(acc, dpi, doa, idesc_neg, 1u);
+                mma_bf16(acc + BN, dpr, doa, idesc, first);
+                mma_bf16(acc + BN, dpi, dos, idesc, 1u);
+              } else {
+                mma_bf16(acc, dpr, dos, idesc, first);
+                mma_bf16(acc + BN, dpi, dos, idesc, first);
+              }
+            }
+          }
+          mma_commit(empty0 + 8 * s);
+        }
+        if (!ok) break;
+        mma_commit(tfull0 + 8 * b);
+      }
+      if (!ok) {
+        atomicExch(abort_flag, 1);
+        atomicOr(status, FQ_BIT_TIMEOUT);
+      }
+      mma_commit(done);
+      mbar_wait(done, 0);
+    }
+  } else {  // ---------------- epilogue warps 2-5; then the unit's completion for its row block
+    const int quarter = warp & 3;
+    bool bad = false, ok = true;
+    double dsr = 0.0, dsi = 0.0;
+    int i = 0;
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++i) {
+      int p, tj, j0, i0;
+      unit(u, p, tj, j0, i0);
+      const int b = i & 1;
+      bool go = mbar_wait(tfull0 + 8 * b, (i >> 1) & 1);
+      tc_fence_after();
+      go = __all_sync(0xffffffffu, go && !*(volatile int*)abort_flag);
+      if (!go) {
+        ok = false;
+        break;
+      }
+      // the previous product's outputs this epilogue reads (prev, acc) were released with its counter
+      if (p > 0) ld_acquire_u32(args.flags + (size_t)(p - 1) * args.tiles_j + tj);
+      const SplitEpi& e = args.epi[p];
+      const int j = j0 + quarter * 32 + lane;
+      const uint32_t trow = tmem + (uint32_t)b * BUF_COLS + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float yr[16], yi[16];
+        tmem_ld16(trow + c0, yr);
+        tmem_ld16(trow + BN + c0, yi);
+        tmem_wait_ld();
+        const int ib = i0 + c0;
+        if (j >= e.nc || ib >= e.n) continue;
+        epi_chunk<NS, EPI>(e, yr, yi, j, ib, bad, dsr, dsi);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+      // this warp's stores of the unit made visible (to the async proxy too), then one release per
+      // warp: a tile is done when its four epilogue warps have counted
+      fence_proxy_async_global();
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) red_release_add(args.flags + (size_t)p * args.tiles_j + tj, 1u);
+    }
+    if (!ok) {
+      atomicExch(abort_flag, 1);
+      atomicOr(status, FQ_BIT_TIMEOUT);
+    }
+    if (bad) atomicOr(status, FQ_BIT_BOUND);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// Launches a chain cooperatively (all CTAs resident).  FQ_EUNSUPPORTED when that cannot be done
+// (a capturing stream, or the device refuses the cooperative launch): the caller then runs the
+// products one launch each.
+template <int NS, int BN, int BKE, int EPI, bool HAS_A>
+fq_status launch_chain(const ChainArgs& args, cudaStream_t s) {
+  using Cfg = SplitCfg<NS, BN, BKE, HAS_A>;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return FQ_EUNSUPPORTED;
+  static std::atomic<unsigned> attr_set{0};
+  if (fq_first_on_device(attr_set)) {
+    cudaError_t e = cudaFuncSetAttribute(k_split_chain<NS, BN, BKE, EPI, HAS_A>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    if (e != cudaSuccess) return fq_cuda_fail(e, "chain kernel shared-memory attribute");
+  }
+  const int tiles = args.tiles_i * args.tiles_j;
+  const int grid = std::min(tiles, fq_sm_count());
+  void* kargs[] = {(void*)&args};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_split_chain<NS, BN, BKE, EPI, HAS_A>, dim3(grid),
+                                              dim3(PTHREADS), kargs, Cfg::SMEM, s);
+  if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+    cudaGetLastError();
+    return FQ_EUNSUPPORTED;
+  }
+  return e == cudaSuccess ? FQ_OK : fq_cuda_fail(e, "chain kernel launch");
+}
+
 // ------------------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
