@@ -36,9 +36,8 @@ namespace {
 constexpr int BAND_LANE_ROWS = 3;                       // window rows per lane
 constexpr int BAND_WIN = 32 * BAND_LANE_ROWS;           // 96-row window, centre at position 48
 constexpr int BAND_MAXL = BAND_WIN / 2 - 1;             // support i +- L inside the window
-constexpr int BAND_KH = 48;                             // K half-width of a 64-row block's window
-constexpr int BAND_KW = OZ_BN + 2 * BAND_KH;            // 160 columns of K per tile
-constexpr int BAND_NK = BAND_KW / OZ_BKE;               // 10 K stages per tile
+constexpr int BAND_KH = 48;                             // widest K half-width of a 64-row block's window
+constexpr int BAND_KW = OZ_BN + 2 * BAND_KH;            // at most 160 columns of K per tile (10 stages)
 constexpr int BAND_ROWS_PER_CTA = 8;                    // one warp per operator row
 static_assert(BAND_KH >= BAND_MAXL, "the K window covers every row's band");
 static_assert(3LL * (1 << 14) * (2 * BAND_KW) < (1LL << 24), "one drain per tile keeps the exact sums exact");
@@ -95,12 +94,13 @@ __device__ __forceinline__ void band_apply(const dflc (&x)[BAND_LANE_ROWS], dflc
 }
 
 // Rows i < nrows of P_m into the right operand slices and their exponents et[i] (rows >= n are
-// zero); one warp per row.  cf, rot: the step's gauge tables (row stride irrelevant: row k).  Also
+// zero); one warp per row.  kh (32 or 48, >= L) is the K half-width of the product's tile windows:
+// a tile row holds 64 + 2 kh columns.  cf, rot: the step's gauge tables (row stride irrelevant: row k).  Also
 // clears the row-maximum keys kzero[0 .. nzero) that the step's product fills.
 __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
     k_band_rows(const double2* __restrict__ cf, const double2* __restrict__ rot, int n, int nrows, int L,
                 BandCoef coef, double ph_re, double ph_im, size_t rstride, __nv_bfloat16* __restrict__ right,
-                int* __restrict__ et, unsigned int* __restrict__ kzero, int nzero) {
+                int* __restrict__ et, unsigned int* __restrict__ kzero, int nzero, int kh) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nzero; q += gridDim.x * blockDim.x) kzero[q] = 0u;
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * BAND_ROWS_PER_CTA + (threadIdx.x >> 5);
@@ -184,31 +184,39 @@ __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
   const int r = i % OZ_BN;
   const size_t rb = (size_t)(3 * OZ_BN) * (i / OZ_BN) + r;  // row of -Im; Re and Im follow
   const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  // window positions [p0, p1) (the row's band; L <= kh) go to tile columns c = r + p - 48 + kh
+  const int kw = OZ_BN + 2 * kh;
+  const int p0 = BAND_WIN / 2 - kh > 0 ? BAND_WIN / 2 - kh : 0;
+  const int p1 = BAND_WIN / 2 + kh + 1 < BAND_WIN ? BAND_WIN / 2 + kh + 1 : BAND_WIN;
 #pragma unroll
   for (int q = 0; q < BAND_LANE_ROWS; ++q) {
+    const int pos = BAND_LANE_ROWS * lane + q;
+    if (pos < p0 || pos >= p1) continue;
     __nv_bfloat16 sr[OZ_S], si[OZ_S];
     oz_digits(vr[q], E, sr);
     oz_digits(vi[q], E, si);
-    const size_t c = (size_t)(BAND_LANE_ROWS * lane + q + r);
+    const size_t c = (size_t)(r + pos - BAND_WIN / 2 + kh);
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) {
       __nv_bfloat16* base = right + s * rstride + c;
-      base[rb * BAND_KW] = __hneg(si[s]);
-      base[(rb + OZ_BN) * BAND_KW] = sr[s];
-      base[(rb + 2 * OZ_BN) * BAND_KW] = si[s];
+      base[rb * kw] = __hneg(si[s]);
+      base[(rb + OZ_BN) * kw] = sr[s];
+      base[(rb + 2 * OZ_BN) * kw] = si[s];
     }
   }
-  // the row's other columns of the tile window: [0, r) and [r + 96, 160)
+  // the row's other columns of the tile window: [0, r) and [r + p1 - p0, kw)
+  const int bw = p1 - p0, nz = kw - bw;
 #pragma unroll
   for (int zz = 0; zz < 2; ++zz) {
     const int z = lane + 32 * zz;
-    const size_t c = (size_t)(z < r ? z : z + BAND_WIN);
+    if (z >= nz) continue;
+    const size_t c = (size_t)(z < r ? z : z + bw);
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) {
       __nv_bfloat16* base = right + s * rstride + c;
-      base[rb * BAND_KW] = zero;
-      base[(rb + OZ_BN) * BAND_KW] = zero;
-      base[(rb + 2 * OZ_BN) * BAND_KW] = zero;
+      base[rb * kw] = zero;
+      base[(rb + OZ_BN) * kw] = zero;
+      base[(rb + 2 * OZ_BN) * kw] = zero;
     }
   }
   if (lane == 0) et[i] = E;
@@ -316,7 +324,7 @@ struct BandEpi {
 // run.  Every wait is bounded; a wait that gives up records FQ_BIT_TIMEOUT, drains this CTA's own
 // copies and MMAs, frees tensor memory and returns.
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    k_oz_band(const __grid_constant__ OzMaps maps, int tiles_j, int tiles_i, int npl, BandEpi e) {
+    k_oz_band(const __grid_constant__ OzMaps maps, int tiles_j, int tiles_i, int npl, int kh, BandEpi e) {
   using Cfg = OzCfg;
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -331,6 +339,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const uint32_t done = smem_u32(bars + 2 * STAGES + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = tiles_i * tiles_j;
+  const int nk = (OZ_BN + 2 * kh) / OZ_BKE;  // K stages of the tile window
   auto coords = [&](int t, int& j0, int& i0) {
     const int per = BAND_RG * tiles_i, g = t / per;
     const int gj = min(BAND_RG, tiles_j - g * BAND_RG), r = t - g * per;
@@ -367,7 +376,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         int j0, i0;
         coords(t, j0, i0);
-        for (int kb = 0; kb < BAND_NK; ++kb, ++g) {
+        for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = g % STAGES;
           if (g >= STAGES && !(ok = mbar_wait(empty0 + 8 * s, ((g / STAGES) - 1) & 1))) break;
           if (*(volatile int*)abort_flag) {
@@ -377,7 +386,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const uint32_t st = base + s * Cfg::STAGE_BYTES;
           const uint32_t bar = full0 + 8 * s;
           mbar_expect_tx(bar, Cfg::STAGE_BYTES);
-          const int kx = i0 - BAND_KH + kb * OZ_BKE;  // multiple of 16 columns; negative at the first block
+          const int kx = i0 - kh + kb * OZ_BKE;  // a multiple of 16 columns; negative at the first block
 #pragma unroll
           for (int q = 0; q < OZ_S; ++q) {
             tma_load_2d(st + (2 * q) * OZ_A_BYTES, &maps.a[q], bar, kx, j0);             // re
@@ -401,7 +410,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
         if (it > 0 && !(ok = mbar_wait(tempty, (it - 1) & 1))) break;  // the previous tile is drained
         tc_fence_after();
-        for (int kb = 0; kb < BAND_NK; ++kb, ++g) {
+        for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = g % STAGES;
           ok = mbar_wait(full0 + 8 * s, (g / STAGES) & 1);
           if (!ok || *(volatile int*)abort_flag) {
@@ -570,9 +579,9 @@ struct BandWs {
   int* et;
   __nv_bfloat16* left;
   int* es;
-  unsigned int* kmax;
+  unsigned int* kmax[2];  // row maxima of the states a product writes (alternating per step)
   float4* x[2];
-  int nrows, npl, ncp;
+  int nrows, npl, ncp, kh, kw;
   size_t rstride, astride;
 };
 
@@ -583,7 +592,11 @@ size_t band_layout(const fq_plan* p, int nc, int nsteps, void* base, BandWs* out
   w.nrows = (p->n + OZ_BN - 1) / OZ_BN * OZ_BN;
   w.npl = (p->n + 127) & ~127;
   w.ncp = (nc + BM - 1) / BM * BM;
-  w.rstride = (size_t)3 * w.nrows * BAND_KW;
+  // the narrowest window that holds the band and starts on a 32-byte sector (16 columns): each
+  // 32-byte TMA box row of the state slices then reads one sector, not two
+  w.kh = p->L <= 32 ? 32 : BAND_KH;
+  w.kw = OZ_BN + 2 * w.kh;
+  w.rstride = (size_t)3 * w.nrows * w.kw;
   w.astride = (size_t)w.ncp * 2 * w.npl;
   char* b = (char*)base;
   size_t off = 0;
@@ -598,7 +611,7 @@ size_t band_layout(const fq_plan* p, int nc, int nsteps, void* base, BandWs* out
   w.et = (int*)take(sizeof(int) * w.nrows);
   w.left = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.astride);
   w.es = (int*)take(sizeof(int) * w.ncp);
-  w.kmax = (unsigned int*)take(sizeof(unsigned int) * w.ncp);
+  for (int q = 0; q < 2; ++q) w.kmax[q] = (unsigned int*)take(sizeof(unsigned int) * w.ncp);
   for (int q = 0; q < 2; ++q) w.x[q] = (float4*)take(sizeof(float4) * (size_t)nc * w.npl);
   if (out) *out = w;
   return off;
@@ -626,7 +639,7 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
   OzMaps maps;
   for (int q = 0; q < OZ_S; ++q) {
     if ((st = make_map(&maps.a[q], w.left + q * w.astride, w.ncp, 2 * w.npl, BM, OZ_BKE)) != FQ_OK) return st;
-    if ((st = make_map(&maps.r[q], w.right + q * w.rstride, 3 * w.nrows, BAND_KW, 3 * OZ_BN, OZ_BKE)) != FQ_OK)
+    if ((st = make_map(&maps.r[q], w.right + q * w.rstride, 3 * w.nrows, w.kw, 3 * OZ_BN, OZ_BKE)) != FQ_OK)
       return st;
   }
   static std::atomic<unsigned> attr_set{0};
@@ -658,20 +671,50 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
   e.ld = w.npl;
   e.bound2 = (float)(1.0 + 1e-6);
   e.status = p->d_status;
+  // P_{m} is formed on a second stream while the states of step m are sliced (ALU against HBM
+  // work); the product waits for both.  P_m may overwrite the band only once product m-1 is done.
+  // (A capturing stream keeps everything on itself: no stream of this call's own joins a capture.)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_prod = nullptr, ev_rows = nullptr;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+  const bool overlap = ce == cudaSuccess && cap == cudaStreamCaptureStatusNone;
+  if (overlap && ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+  if (overlap && ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ev_prod, cudaEventDisableTiming);
+  if (overlap && ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ev_rows, cudaEventDisableTiming);
+  const cudaStream_t rs = overlap ? side : s;
+  auto release = [&] {
+    if (ev_prod) cudaEventDestroy(ev_prod);
+    if (ev_rows) cudaEventDestroy(ev_rows);
+    if (side) cudaStreamDestroy(side);
+  };
+  if (ce != cudaSuccess) {
+    release();
+    return fq_cuda_fail(ce, "band chain streams");
+  }
   int cur = 0;
-  for (int m = 0; m < nsteps; ++m) {
-    // the states' slices (their row maxima from the previous product; the first step finds them),
-    // then P_m (clearing the maxima for this product), then the product
-    k_band_slice<<<w.ncp, 256, 0, s>>>(w.x[cur], n, w.npl, nc, w.npl, w.astride, w.left, w.es,
-                                       m == 0 ? nullptr : w.kmax);
-    k_band_rows<<<(w.nrows + BAND_ROWS_PER_CTA - 1) / BAND_ROWS_PER_CTA, 32 * BAND_ROWS_PER_CTA, 0, s>>>(
+  for (int m = 0; m < nsteps && ce == cudaSuccess; ++m) {
+    if (overlap) {
+      ce = cudaEventRecord(ev_prod, s);  // product m-1 (or the set-up) done
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(side, ev_prod, 0);
+      if (ce != cudaSuccess) break;
+    }
+    // P_m, clearing the row maxima product m will collect
+    k_band_rows<<<(w.nrows + BAND_ROWS_PER_CTA - 1) / BAND_ROWS_PER_CTA, 32 * BAND_ROWS_PER_CTA, 0, rs>>>(
         w.cf + (size_t)m * w.nrows, w.rot + (size_t)m * w.nrows, n, w.nrows, L, coef, p->phase_re, p->phase_im,
-        w.rstride, w.right, w.et, w.kmax, w.ncp);
+        w.rstride, w.right, w.et, w.kmax[m & 1], w.ncp, w.kh);
+    if (overlap) ce = cudaEventRecord(ev_rows, side);
+    // the states' slices, with the row maxima product m-1 collected (the first step finds them)
+    k_band_slice<<<w.ncp, 256, 0, s>>>(w.x[cur], n, w.npl, nc, w.npl, w.astride, w.left, w.es,
+                                       m == 0 ? nullptr : w.kmax[(m - 1) & 1]);
+    if (overlap && ce == cudaSuccess) ce = cudaStreamWaitEvent(s, ev_rows, 0);
     e.out = w.x[cur ^ 1];
-    e.kmax = w.kmax;
-    k_oz_band<<<std::min(ntiles, sms), OZ_THREADS, OzCfg::SMEM, s>>>(maps, tiles_j, tiles_i, w.npl, e);
+    e.kmax = w.kmax[m & 1];
+    k_oz_band<<<std::min(ntiles, sms), OZ_THREADS, OzCfg::SMEM, s>>>(maps, tiles_j, tiles_i, w.npl, w.kh, e);
     cur ^= 1;
   }
+  release();
+  if (ce != cudaSuccess) return fq_cuda_fail(ce, "band chain streams");
   if (transpose_out) {
     dim3 g((n + 31) / 32, (n + 31) / 32), b(32, 8);
     k_band_store_t<<<g, b, 0, s>>>(w.x[cur], (double2*)x, n, w.npl);

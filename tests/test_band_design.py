@@ -6,8 +6,8 @@ FP64 on CPU against the oracle, free of the emulation's rounding:
     e_i in the real gauge frame, on a 96-row window centred on i (zero beyond it), rotated back by
     e^{i theta_i} ... e^{-i theta_k};
   * chaining X_m = P_m X_{m-1} reproduces the oracle's step-by-step recurrence;
-  * the tile window of 64 operator rows [i0, i0 + 64), state columns [i0 - 48, i0 + 112), holds
-    every row's band, and each row's window positions land inside the 160 columns of its tile;
+  * the tile window of 64 operator rows [i0, i0 + 64), state columns [i0 - kh, i0 + 64 + kh)
+    (kh = 32 or 48), holds every row's band, and each row's window positions land inside it;
   * one drain per tile keeps the three exact FP32 sums exact (3 pairs x 2^14 x 320 < 2^24);
   * the FP32 cut of a double-float state entry into its 8-bit digits (k_band_slice) is exact to
     2^-49 of the row scale, with digits that keep the tensor-core sums exact."""
@@ -21,7 +21,14 @@ import floquet_inputs as fi
 import oracle as o
 from test_gauge_design import clenshaw, gauge
 
-WIN, CENTRE, KH, BN, KW = 96, 48, 48, 64, 160
+WIN, CENTRE, BN = 96, 48, 64
+
+
+def window(L):
+    """The product's K half-width and tile width for a series of L products: 32 and 128 columns
+    up to L = 32, else 48 and 160 (the window starts on a 16-column boundary)."""
+    kh = 32 if L <= 32 else 48
+    return kh, BN + 2 * kh
 
 
 def band_rows(d, e_real, theta, coeffs, phase, n):
@@ -87,26 +94,32 @@ def test_band_chain_matches_oracle():
     assert np.max(np.abs(x - ref)) <= 1e-13
 
 
-@pytest.mark.parametrize("n,L", [(1, 1), (41, 20), (64, 47), (700, 39), (10001, 39), (10001, 47)])
+@pytest.mark.parametrize("n,L", [(1, 1), (41, 20), (64, 47), (700, 32), (700, 33), (10001, 39), (10001, 47)])
 def test_tile_windows_hold_every_band(n, L):
-    """Rows [i0, i0 + 64) of a tile read state columns [i0 - 48, i0 + 112); every non-zero P[i][k]
-    (|i - k| <= L, both in [0, n)) sits in that window and in the row's 96-row formation window,
-    at tile column c = k - (i0 - 48) in [0, 160); the window start is a multiple of 16 columns
-    (the TMA alignment rule for BF16), and the row's zero columns [0, r) and [r + 96, 160) are
-    disjoint from its band columns [r, r + 96)."""
+    """Rows [i0, i0 + 64) of a tile read state columns [i0 - kh, i0 + 64 + kh) (kh = 32 up to
+    L = 32, else 48); every non-zero P[i][k] (|i - k| <= L, both in [0, n)) sits in that window and
+    in the row's 96-row formation window, at tile column c = k - (i0 - kh); the window start is a
+    multiple of 16 columns (32 bytes: one sector per TMA box row; the TMA rule needs 16 bytes) and
+    its width a multiple of the 16-column K stage; the row's band columns (window positions
+    [48 - kh, 48 + kh]) and its zero columns cover the tile row exactly once."""
+    kh, kw = window(L)
+    assert kw % 16 == 0 and L <= kh
+    p0, p1 = max(0, CENTRE - kh), min(WIN, CENTRE + kh + 1)
     tiles = -(-n // BN)
     for b in range(tiles):
         i0 = BN * b
-        assert (i0 - KH) % 16 == 0
+        assert (i0 - kh) % 16 == 0
         for i in range(i0, min(i0 + BN, n)):
             r = i - i0
             ks = np.arange(max(0, i - L), min(n, i + L + 1))
-            c = ks - (i0 - KH)
-            assert np.all((c >= 0) & (c < KW))
+            c = ks - (i0 - kh)
+            assert np.all((c >= 0) & (c < kw))
             p = ks - (i - CENTRE)
-            assert np.all((p >= 0) & (p < WIN)) and np.array_equal(c, p + r)
-            zeros = [z if z < r else z + WIN for z in range(64)]
-            assert sorted(zeros + list(range(r, r + WIN))) == list(range(KW))
+            assert np.all((p >= p0) & (p < p1)) and np.array_equal(c, r + p - CENTRE + kh)
+            bw = p1 - p0
+            zeros = [z if z < r else z + bw for z in range(kw - bw)]
+            band = list(range(r + p0 - CENTRE + kh, r + p1 - CENTRE + kh))
+            assert band[0] == r and sorted(zeros + band) == list(range(kw))
 
 
 def test_one_drain_per_tile_is_exact():
@@ -114,8 +127,8 @@ def test_one_drain_per_tile_is_exact():
     accumulators take at most 3 pairs, and a 160-column window gives 2 x 160 products per entry
     (real and imaginary parts of the state), so their sums stay below 2^24 units and FP32
     represents every partial sum exactly."""
-    assert 3 * 2 ** 14 * (2 * KW) < 2 ** 24
-    assert 3 * 2 ** 14 * (2 * (KW + 32)) > 2 ** 24   # two more K stages would need a second drain
+    assert 3 * 2 ** 14 * (2 * window(47)[1]) < 2 ** 24
+    assert 3 * 2 ** 14 * (2 * (window(47)[1] + 32)) > 2 ** 24   # two more K stages would need a second drain
 
 
 def _f(x):
