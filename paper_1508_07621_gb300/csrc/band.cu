@@ -20,11 +20,15 @@
 // The product is the same polynomial the Chebyshev recurrence applies, so the result agrees with
 // the plain chain to the emulation's rounding (48 bits per slice product).  Needs L <= 47.
 //
-// Layouts (all in the caller's workspace):
+// Layouts (all in the caller's workspace).  Both operands of the product are stored MN-major (the
+// states, or the operator rows, contiguous; K the outer index), so that every row of a TMA box is
+// 64 BF16 = 128 bytes (128-byte swizzle) although a K stage is only 16 deep: the K-major form
+// (16 BF16 = 32-byte box rows) fed the tensor cores at about two thirds of the rate.
 //   states     double-float [nc][npl] float4 (re_hi, re_lo, im_hi, im_lo), npl = N rounded to 128
-//   left       OZ_S slices [ncp][2 npl] BF16: re in columns [0, npl), im in [npl, 2 npl)
-//   right      OZ_S slices [3 nrows][160] BF16: per 64-row block b the rows -Im, Re, Im of P_m,
-//              column c = k - (64 b - 48)
+//   left       OZ_S slices [2 npl][ncp] BF16: row k the real parts of component k of every
+//              state, row npl + k the imaginary parts
+//   right      OZ_S slices [nrows / 64][kw][192] BF16: per 64-row block b and window column
+//              c = k - (64 b - kh) the columns -Im, Re, Im of rows 64 b .. 64 b + 63 of P_m
 //   cf, rot    per step (2 d, 2 e') and (cos, sin) theta of the gauge frame, FP64, [nsteps][nrows]
 #include <atomic>
 
@@ -94,17 +98,20 @@ __device__ __forceinline__ void band_apply(const dflc (&x)[BAND_LANE_ROWS], dflc
 }
 
 // Rows i < nrows of P_m into the right operand slices and their exponents et[i] (rows >= n are
-// zero); one warp per row.  kh (32 or 48, >= L) is the K half-width of the product's tile windows:
-// a tile row holds 64 + 2 kh columns.  cf, rot: the step's gauge tables (row stride irrelevant: row k).  Also
-// clears the row-maximum keys kzero[0 .. nzero) that the step's product fills.
+// zero); one warp per row, 8 rows per CTA (nrows is a multiple of 64, so the grid holds no partial
+// CTA and a CTA's rows share one 64-row block).  kh (a multiple of 8 in [L, 48]) is the K half-width
+// of the product's tile windows: a tile row holds 64 + 2 kh columns.  The CTA's rows are staged in shared
+// memory and leave as 16-byte pieces of the MN-major band (8 consecutive operator rows of one
+// window column).  cf, rot: the step's gauge tables (row stride irrelevant: row k).  Also clears
+// the row-maximum keys kzero[0 .. nzero) that the step's product fills.
 __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
     k_band_rows(const double2* __restrict__ cf, const double2* __restrict__ rot, int n, int nrows, int L,
                 BandCoef coef, double ph_re, double ph_im, size_t rstride, __nv_bfloat16* __restrict__ right,
                 int* __restrict__ et, unsigned int* __restrict__ kzero, int nzero, int kh) {
+  __shared__ __align__(16) __nv_bfloat16 stage[OZ_S][3][BAND_KW][BAND_ROWS_PER_CTA];
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nzero; q += gridDim.x * blockDim.x) kzero[q] = 0u;
-  const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * BAND_ROWS_PER_CTA + (threadIdx.x >> 5);
-  if (i >= nrows) return;  // whole warp
+  const int lane = threadIdx.x & 31, wr8 = threadIdx.x >> 5;
+  const int i = blockIdx.x * BAND_ROWS_PER_CTA + wr8;
   const bool live = i < n;
   const int w0 = i - BAND_WIN / 2;  // row of window position 0
   const dfl zd = {0.f, 0.f};
@@ -182,7 +189,6 @@ __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
   }
   const int E = oz_exponent(key);
   const int r = i % OZ_BN;
-  const size_t rb = (size_t)(3 * OZ_BN) * (i / OZ_BN) + r;  // row of -Im; Re and Im follow
   const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
   // window positions [p0, p1) (the row's band; L <= kh) go to tile columns c = r + p - 48 + kh
   const int kw = OZ_BN + 2 * kh;
@@ -195,13 +201,12 @@ __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
     __nv_bfloat16 sr[OZ_S], si[OZ_S];
     oz_digits(vr[q], E, sr);
     oz_digits(vi[q], E, si);
-    const size_t c = (size_t)(r + pos - BAND_WIN / 2 + kh);
+    const int c = r + pos - BAND_WIN / 2 + kh;
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) {
-      __nv_bfloat16* base = right + s * rstride + c;
-      base[rb * kw] = __hneg(si[s]);
-      base[(rb + OZ_BN) * kw] = sr[s];
-      base[(rb + 2 * OZ_BN) * kw] = si[s];
+      stage[s][0][c][wr8] = __hneg(si[s]);
+      stage[s][1][c][wr8] = sr[s];
+      stage[s][2][c][wr8] = si[s];
     }
   }
   // the row's other columns of the tile window: [0, r) and [r + p1 - p0, kw)
@@ -210,16 +215,23 @@ __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
   for (int zz = 0; zz < 2; ++zz) {
     const int z = lane + 32 * zz;
     if (z >= nz) continue;
-    const size_t c = (size_t)(z < r ? z : z + bw);
+    const int c = z < r ? z : z + bw;
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) {
-      __nv_bfloat16* base = right + s * rstride + c;
-      base[rb * kw] = zero;
-      base[(rb + OZ_BN) * kw] = zero;
-      base[(rb + 2 * OZ_BN) * kw] = zero;
+      stage[s][0][c][wr8] = zero;
+      stage[s][1][c][wr8] = zero;
+      stage[s][2][c][wr8] = zero;
     }
   }
   if (lane == 0) et[i] = E;
+  __syncthreads();
+  // column c of part (-Im, Re, Im) of block b: rows r0 .. r0 + 7 at [(b kw + c) 192 + 64 part + r0]
+  const int i0 = blockIdx.x * BAND_ROWS_PER_CTA, b = i0 / OZ_BN, r0 = i0 % OZ_BN;
+  for (int t = threadIdx.x; t < OZ_S * 3 * kw; t += blockDim.x) {
+    const int c = t % kw, sp = t / kw, part = sp % 3, s = sp / 3;
+    *reinterpret_cast<uint4*>(right + s * rstride + ((size_t)b * kw + c) * (3 * OZ_BN) + part * OZ_BN + r0) =
+        *reinterpret_cast<const uint4*>(&stage[s][part][c][0]);
+  }
 }
 
 // float 2^e for |e| <= 126 (clamped)
@@ -257,52 +269,79 @@ __device__ __forceinline__ bool df_digits2(float2 a, float2 b, __nv_bfloat16 (&d
   return ok;
 }
 
-// Left slices of double-float state rows: one CTA per row j of the padded block (rows >= nc and
-// columns >= n are zero), the scale 2^E from the row's largest |hi| part, the digits by the FP32
-// cut of df_digits2 (re and im packed).  kmax (if not NULL) holds each row's largest |hi| as an
-// FP32 key, collected by the product that wrote the states; otherwise a first pass finds it.
-__global__ void k_band_slice(const float4* __restrict__ x, int n, int ld, int nc, int npl, size_t astride,
-                             __nv_bfloat16* __restrict__ left, int* __restrict__ es,
-                             const unsigned int* __restrict__ kmax) {
+// Each state's largest |hi| part (re or im) as an FP32 key, for the slicing of states that no
+// product has written yet (the first step of a call); one CTA per state j < nc.
+__global__ void k_band_rowmax(const float4* __restrict__ x, int n, int ld, unsigned int* __restrict__ kmax) {
   __shared__ unsigned long long red[32];
   const int j = blockIdx.x;
   unsigned long long m = 0;
-  if (kmax) {
-    if (j < nc && threadIdx.x == 0) m = kmax[j];
-  } else if (j < nc)
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      const float4 v = x[(size_t)j * ld + k];
-      // |hi| as an ordered key (FP32 bit pattern; no FP64 conversion): the row maximum of |hi|
-      // bounds |hi + lo| below 2^(E-1) as well (the exponent has a factor 2 to spare)
-      const unsigned long long a = __float_as_uint(v.x) & 0x7FFFFFFFu, b = __float_as_uint(v.z) & 0x7FFFFFFFu;
-      m = a > m ? a : m;
-      m = b > m ? b : m;
-    }
-  const unsigned long long mk = block_max_key(m, red);
-  // E = (unbiased exponent of the maximum) + 2, as oz_exponent for FP64 keys
-  const int E = mk == 0 ? 0 : (int)(mk >> 23) - 127 + 2;
-  const float so = pow2f(-E);  // into units of the row scale (exact)
-  __nv_bfloat16* row = left + (size_t)j * 2 * npl;
-  bool bad = false;
-  for (int k0 = 4 * threadIdx.x; k0 < npl; k0 += 4 * blockDim.x) {
-    __nv_bfloat16 sr[4][OZ_S], si[4][OZ_S];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (j < nc && k0 + u < n) v = x[(size_t)j * ld + k0 + u];
-      bad |= !df_digits2(make_float2(v.x * so, v.z * so), make_float2(v.y * so, v.w * so), sr[u], si[u]);
-    }
-#pragma unroll
-    for (int q = 0; q < OZ_S; ++q) {
-      *reinterpret_cast<uint2*>(row + q * astride + k0) = pack4(sr[0][q], sr[1][q], sr[2][q], sr[3][q]);
-      *reinterpret_cast<uint2*>(row + q * astride + npl + k0) = pack4(si[0][q], si[1][q], si[2][q], si[3][q]);
-    }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const float4 v = x[(size_t)j * ld + k];
+    const unsigned long long a = __float_as_uint(v.x) & 0x7FFFFFFFu, b = __float_as_uint(v.z) & 0x7FFFFFFFu;
+    m = a > m ? a : m;
+    m = b > m ? b : m;
   }
-  if (threadIdx.x == 0) es[j] = E;
-  (void)bad;  // the scale comes from the row's own maximum: the cut cannot break it
+  m = block_max_key(m, red);
+  if (threadIdx.x == 0) kmax[j] = (unsigned int)m;
+}
+
+// Left slices of the double-float states, MN-major: slice q row k holds digit q of Re X[j][k] for
+// every state j (row npl + k: Im), each state at the scale 2^E_j from its largest |hi| part (the
+// key kmax[j]; E = its exponent + 2, so |X[j][k]| < 2^(E-1) with a factor 2 to spare); digits by
+// the FP32 cut of df_digits2.  Each thread cuts a 2 x 2 block (states j, j + 1; components k,
+// k + 1), so that a warp writes 128 contiguous bytes (64 states) of each slice row; states >= nc
+// and components >= n are zero.  Grid (ncp / 64, npl / 16), 256 threads.
+__global__ void __launch_bounds__(256)
+    k_band_slice(const float4* __restrict__ x, int n, int ld, int nc, int npl, int ncp, size_t astride,
+                 __nv_bfloat16* __restrict__ left, int* __restrict__ es, const unsigned int* __restrict__ kmax) {
+  const int j = 2 * (blockIdx.x * 32 + (threadIdx.x & 31));
+  const int k = 2 * (blockIdx.y * 8 + (threadIdx.x >> 5));
+  int E[2];
+  float so[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const unsigned int key = j + u < nc ? kmax[j + u] : 0u;
+    E[u] = key == 0u ? 0 : (int)(key >> 23) - 127 + 2;
+    so[u] = pow2f(-E[u]);  // into units of the state's scale (exact)
+  }
+  if (blockIdx.y == 0 && threadIdx.x < 32) {
+    es[j] = E[0];
+    es[j + 1] = E[1];
+  }
+  __nv_bfloat16 dr[2][2][OZ_S], di[2][2][OZ_S];  // [state][component][slice]
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j + u < nc && k + v < n) a = x[(size_t)(j + u) * ld + k + v];
+      df_digits2(make_float2(a.x * so[u], a.z * so[u]), make_float2(a.y * so[u], a.w * so[u]), dr[u][v], di[u][v]);
+    }
+#pragma unroll
+  for (int q = 0; q < OZ_S; ++q)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      __nv_bfloat16* col = left + q * astride + j;
+      *reinterpret_cast<__nv_bfloat162*>(col + (size_t)(k + v) * ncp) = __halves2bfloat162(dr[0][v][q], dr[1][v][q]);
+      *reinterpret_cast<__nv_bfloat162*>(col + (size_t)(npl + k + v) * ncp) =
+          __halves2bfloat162(di[0][v][q], di[1][v][q]);
+    }
 }
 
 constexpr int BAND_RG = 16;  // state blocks per raster group
+
+// Shared-memory descriptor of an MN-major operand with 128-byte swizzle, as the TMA boxes of
+// k_oz_band lay it out: 64-element atoms (128-byte rows, 8 K rows = 1 KB) at 2 KB steps along M or
+// N (one 16-row box each), the two 8-row K groups of a stage 1 KB apart.
+__device__ __forceinline__ uint64_t band_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(2048 >> 4) << 16;  // leading offset: next 64-element atom along M or N
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride offset: next 8 rows along K
+  d |= (uint64_t)1 << 46;            // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
 
 struct BandEpi {
   float4* out;     // X_m, double-float [nc][ld]
@@ -386,12 +425,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const uint32_t st = base + s * Cfg::STAGE_BYTES;
           const uint32_t bar = full0 + 8 * s;
           mbar_expect_tx(bar, Cfg::STAGE_BYTES);
-          const int kx = i0 - kh + kb * OZ_BKE;  // a multiple of 16 columns; negative at the first block
+          const int kx = i0 - kh + kb * OZ_BKE;  // K row of the states (any row); negative at the first block
+          const int kr = (i0 / OZ_BN) * (OZ_BN + 2 * kh) + kb * OZ_BKE;  // K row of the band block
 #pragma unroll
           for (int q = 0; q < OZ_S; ++q) {
-            tma_load_2d(st + (2 * q) * OZ_A_BYTES, &maps.a[q], bar, kx, j0);             // re
-            tma_load_2d(st + (2 * q + 1) * OZ_A_BYTES, &maps.a[q], bar, npl + kx, j0);   // im
-            tma_load_2d(st + 2 * OZ_S * OZ_A_BYTES + q * Cfg::R_BYTES, &maps.r[q], bar, kb * OZ_BKE, 3 * i0);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {  // states j0 + 64 h .. + 63: 2 KB boxes of 16 K rows
+              tma_load_2d(st + (2 * q) * OZ_A_BYTES + 2048 * h, &maps.a[q], bar, j0 + 64 * h, kx);        // re
+              tma_load_2d(st + (2 * q + 1) * OZ_A_BYTES + 2048 * h, &maps.a[q], bar, j0 + 64 * h, npl + kx);  // im
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c)  // band columns -Im, Re, Im
+              tma_load_2d(st + 2 * OZ_S * OZ_A_BYTES + q * Cfg::R_BYTES + 2048 * c, &maps.r[q], bar, 64 * c, kr);
           }
         }
       }
@@ -403,8 +448,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---------------- MMA issuer
-      constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * OZ_BN) >> 3) << 17) |
-                                 ((uint32_t)(BM >> 4) << 24);
+      // FP32 accumulate, BF16 A and B, both MN-major (bits 15 and 16), N = 128, M = 128
+      constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                                 ((uint32_t)((2 * OZ_BN) >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
       int g = 0, it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
@@ -419,7 +465,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           }
           tc_fence_after();
           const uint32_t st = base + s * Cfg::STAGE_BYTES;
-          const uint64_t d0 = oz_desc(st);
+          const uint64_t d0 = band_desc(st);
 #pragma unroll
           for (int p = 0; p < OZ_PAIRS; ++p) {
             int a, b;
@@ -429,10 +475,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const uint32_t acc = tmem + (uint32_t)grp * (2 * OZ_BN);
             const uint32_t rb = 2 * OZ_S * OZ_A_BYTES + b * Cfg::R_BYTES;
             const uint32_t first = (kb == 0 && lead) ? 0u : 1u;
-            mma_bf16(acc, d0 + (uint64_t)(((2 * a) * OZ_A_BYTES) >> 4), d0 + (uint64_t)((rb + OZ_BN * OZ_ROWB) >> 4),
-                     idesc, first);  // re . [Re; Im]
+            mma_bf16(acc, d0 + (uint64_t)(((2 * a) * OZ_A_BYTES) >> 4), d0 + (uint64_t)((rb + 2048) >> 4), idesc,
+                     first);  // re . [Re, Im] (band boxes 1, 2)
             mma_bf16(acc, d0 + (uint64_t)(((2 * a + 1) * OZ_A_BYTES) >> 4), d0 + (uint64_t)(rb >> 4), idesc,
-                     1u);            // im . [-Im; Re]
+                     1u);     // im . [-Im, Re] (band boxes 0, 1)
           }
           mma_commit(empty0 + 8 * s);
         }
@@ -592,9 +638,9 @@ size_t band_layout(const fq_plan* p, int nc, int nsteps, void* base, BandWs* out
   w.nrows = (p->n + OZ_BN - 1) / OZ_BN * OZ_BN;
   w.npl = (p->n + 127) & ~127;
   w.ncp = (nc + BM - 1) / BM * BM;
-  // the narrowest window that holds the band and starts on a 32-byte sector (16 columns): each
-  // 32-byte TMA box row of the state slices then reads one sector, not two
-  w.kh = p->L <= 32 ? 32 : BAND_KH;
+  // the narrowest window that holds the band with a width of whole 16-row K stages (K is the outer
+  // coordinate of the MN-major boxes, so the window may start on any row)
+  w.kh = std::min(BAND_KH, (p->L + 7) / 8 * 8);
   w.kw = OZ_BN + 2 * w.kh;
   w.rstride = (size_t)3 * w.nrows * w.kw;
   w.astride = (size_t)w.ncp * 2 * w.npl;
@@ -638,8 +684,10 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
   band_layout(p, nc, nsteps, ws, &w);
   OzMaps maps;
   for (int q = 0; q < OZ_S; ++q) {
-    if ((st = make_map(&maps.a[q], w.left + q * w.astride, w.ncp, 2 * w.npl, BM, OZ_BKE)) != FQ_OK) return st;
-    if ((st = make_map(&maps.r[q], w.right + q * w.rstride, 3 * w.nrows, w.kw, 3 * OZ_BN, OZ_BKE)) != FQ_OK)
+    // MN-major: 64-element (128-byte) box rows, 16 K rows per box
+    if ((st = make_map(&maps.a[q], w.left + q * w.astride, 2 * w.npl, w.ncp, OZ_BKE, 64)) != FQ_OK) return st;
+    if ((st = make_map(&maps.r[q], w.right + q * w.rstride, (w.nrows / OZ_BN) * w.kw, 3 * OZ_BN, OZ_BKE, 64)) !=
+        FQ_OK)
       return st;
   }
   static std::atomic<unsigned> attr_set{0};
@@ -704,9 +752,11 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
         w.cf + (size_t)m * w.nrows, w.rot + (size_t)m * w.nrows, n, w.nrows, L, coef, p->phase_re, p->phase_im,
         w.rstride, w.right, w.et, w.kmax[m & 1], w.ncp, w.kh);
     if (overlap) ce = cudaEventRecord(ev_rows, side);
-    // the states' slices, with the row maxima product m-1 collected (the first step finds them)
-    k_band_slice<<<w.ncp, 256, 0, s>>>(w.x[cur], n, w.npl, nc, w.npl, w.astride, w.left, w.es,
-                                       m == 0 ? nullptr : w.kmax[(m - 1) & 1]);
+    // the states' slices, with the row maxima product m-1 collected; the first step finds them
+    // (into the buffer k_band_rows of step 0 leaves alone)
+    if (m == 0) k_band_rowmax<<<nc, 256, 0, s>>>(w.x[cur], n, w.npl, w.kmax[1]);
+    k_band_slice<<<dim3(w.ncp / 64, w.npl / 16), 256, 0, s>>>(w.x[cur], n, w.npl, nc, w.npl, w.ncp, w.astride,
+                                                              w.left, w.es, w.kmax[(m + 1) & 1]);
     if (overlap && ce == cudaSuccess) ce = cudaStreamWaitEvent(s, ev_rows, 0);
     e.out = w.x[cur ^ 1];
     e.kmax = w.kmax[m & 1];

@@ -7,7 +7,8 @@ FP64 on CPU against the oracle, free of the emulation's rounding:
     e^{i theta_i} ... e^{-i theta_k};
   * chaining X_m = P_m X_{m-1} reproduces the oracle's step-by-step recurrence;
   * the tile window of 64 operator rows [i0, i0 + 64), state columns [i0 - kh, i0 + 64 + kh)
-    (kh = 32 or 48), holds every row's band, and each row's window positions land inside it;
+    (kh = L rounded up to a multiple of 8), holds every row's band, and each row's window
+    positions land inside it;
   * one drain per tile keeps the three exact FP32 sums exact (3 pairs x 2^14 x 320 < 2^24);
   * the FP32 cut of a double-float state entry into its 8-bit digits (k_band_slice) is exact to
     2^-49 of the row scale, with digits that keep the tensor-core sums exact."""
@@ -25,9 +26,9 @@ WIN, CENTRE, BN = 96, 48, 64
 
 
 def window(L):
-    """The product's K half-width and tile width for a series of L products: 32 and 128 columns
-    up to L = 32, else 48 and 160 (the window starts on a 16-column boundary)."""
-    kh = 32 if L <= 32 else 48
+    """The product's K half-width and tile width for a series of L products: kh = L rounded up
+    to a multiple of 8 (at most 48), so the window is a whole number of 16-row K stages."""
+    kh = min(48, -(-L // 8) * 8)
     return kh, BN + 2 * kh
 
 
@@ -94,21 +95,22 @@ def test_band_chain_matches_oracle():
     assert np.max(np.abs(x - ref)) <= 1e-13
 
 
-@pytest.mark.parametrize("n,L", [(1, 1), (41, 20), (64, 47), (700, 32), (700, 33), (10001, 39), (10001, 47)])
+@pytest.mark.parametrize("n,L", [(1, 1), (41, 20), (64, 47), (700, 8), (700, 9), (700, 32), (700, 33),
+                                 (10001, 39), (10001, 40), (10001, 41), (10001, 47)])
 def test_tile_windows_hold_every_band(n, L):
-    """Rows [i0, i0 + 64) of a tile read state columns [i0 - kh, i0 + 64 + kh) (kh = 32 up to
-    L = 32, else 48); every non-zero P[i][k] (|i - k| <= L, both in [0, n)) sits in that window and
-    in the row's 96-row formation window, at tile column c = k - (i0 - kh); the window start is a
-    multiple of 16 columns (32 bytes: one sector per TMA box row; the TMA rule needs 16 bytes) and
-    its width a multiple of the 16-column K stage; the row's band columns (window positions
-    [48 - kh, 48 + kh]) and its zero columns cover the tile row exactly once."""
+    """Rows [i0, i0 + 64) of a tile read state columns [i0 - kh, i0 + 64 + kh) (kh = L rounded up
+    to a multiple of 8); every non-zero P[i][k] (|i - k| <= L, both in [0, n)) sits in that window
+    and in the row's 96-row formation window, at tile column c = k - (i0 - kh); the window's width
+    is a multiple of the 16-row K stage (its start is the outer coordinate of the MN-major TMA
+    boxes, free of alignment rules); the row's band columns (window positions [48 - kh, 48 + kh])
+    and its zero columns (at most 64: two per lane) cover the tile row exactly once."""
     kh, kw = window(L)
     assert kw % 16 == 0 and L <= kh
     p0, p1 = max(0, CENTRE - kh), min(WIN, CENTRE + kh + 1)
+    assert kw - (p1 - p0) <= 64
     tiles = -(-n // BN)
     for b in range(tiles):
         i0 = BN * b
-        assert (i0 - kh) % 16 == 0
         for i in range(i0, min(i0 + BN, n)):
             r = i - i0
             ks = np.arange(max(0, i - L), min(n, i + L + 1))
