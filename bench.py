@@ -376,11 +376,17 @@ DIMER_PATHS = {
 BAND_NCU = {"read": 586.6e6, "write": 297.3e6, "states": 2048}
 
 
-def band_issued_flops(n, nc):
+def band_window(L):
+    """K width of the band kernel's tiles: 64 operator rows plus L rounded up to a multiple of 8
+    (at most 48) on each side."""
+    return 64 + 2 * min(48, -(-L // 8) * 8)
+
+
+def band_issued_flops(n, nc, L):
     """BF16 MMA flops the band kernel issues per step: tiles of 128 states x 64 operator rows, a
-    160-column K window, 21 slice pairs of two N = 128 MMAs."""
+    K window of band_window(L) columns, 21 slice pairs of two N = 128 MMAs."""
     tiles = -(-nc // 128) * -(-n // 64)
-    return tiles * 21 * 2 * 2.0 * 128 * 128 * 160
+    return tiles * 21 * 2 * 2.0 * 128 * 128 * band_window(L)
 
 
 def dimer_roofline(path, n, steps, L, seconds_per_launch, per_launch_units):
@@ -389,7 +395,7 @@ def dimer_roofline(path, n, steps, L, seconds_per_launch, per_launch_units):
     achieved = work / seconds_per_launch / 1e12
     if path.get("tensor"):
         peak = measured_peaks()["bf16_sustained"]
-        issued = band_issued_flops(n, n) * per_launch_units / (float(n) * n * L) / seconds_per_launch / 1e12
+        issued = band_issued_flops(n, n, L) * per_launch_units / (float(n) * n * L) / seconds_per_launch / 1e12
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "kernel": path["kernel_name"], "work_per_unit": path["per_unit"],
                 "units_per_launch": per_launch_units, "issued_tflops": issued, "issued_frac": issued / peak,

@@ -269,6 +269,18 @@ __device__ __forceinline__ bool df_digits2(float2 a, float2 b, __nv_bfloat16 (&d
   return ok;
 }
 
+// A state's slice exponent from its largest |hi| part (an FP32 bit pattern, 0 for a zero state):
+// E = exponent + 2, so every |X[j][k]| < 2^(E-1) with a factor 2 to spare, below 1/2 in units of
+// the scale 2^E.
+__device__ __forceinline__ int band_key_exp(unsigned int key) { return key == 0u ? 0 : (int)(key >> 23) - 127 + 2; }
+
+// The product's epilogue cuts X_m into the next step's slices before X_m's maxima are known, at
+// the exponent of X_{m-1}'s maximum plus this margin: a state then fits unless its maximum grows
+// by more than 2^BAND_MARGIN (between 2 and 4 times) in one step.  A margin of 0 flagged so many
+// states (any growth across a power of 2) that cutting them again cost more than the slicing
+// pass it replaces; 1 costs one bit of the 48 on the states' scale.
+constexpr int BAND_MARGIN = 1;
+
 // Each state's largest |hi| part (re or im) as an FP32 key, for the slicing of states that no
 // product has written yet (the first step of a call); one CTA per state j < nc.
 __global__ void k_band_rowmax(const float4* __restrict__ x, int n, int ld, unsigned int* __restrict__ kmax) {
@@ -285,10 +297,10 @@ __global__ void k_band_rowmax(const float4* __restrict__ x, int n, int ld, unsig
   if (threadIdx.x == 0) kmax[j] = (unsigned int)m;
 }
 
-// Left slices of the double-float states, MN-major: slice q row k holds digit q of Re X[j][k] for
-// every state j (row npl + k: Im), each state at the scale 2^E_j from its largest |hi| part (the
-// key kmax[j]; E = its exponent + 2, so |X[j][k]| < 2^(E-1) with a factor 2 to spare); digits by
-// the FP32 cut of df_digits2.  Each thread cuts a 2 x 2 block (states j, j + 1; components k,
+// Left slices of the double-float states (the first step of a call; later steps' slices come from
+// the product's epilogue), MN-major: slice q row k holds digit q of Re X[j][k] for every state j
+// (row npl + k: Im), each state at the scale 2^E_j of band_key_exp(kmax[j]); digits by the FP32
+// cut of df_digits2.  Each thread cuts a 2 x 2 block (states j, j + 1; components k,
 // k + 1), so that a warp writes 128 contiguous bytes (64 states) of each slice row; states >= nc
 // and components >= n are zero.  Grid (ncp / 64, npl / 16), 256 threads.
 __global__ void __launch_bounds__(256)
@@ -300,8 +312,7 @@ __global__ void __launch_bounds__(256)
   float so[2];
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
-    const unsigned int key = j + u < nc ? kmax[j + u] : 0u;
-    E[u] = key == 0u ? 0 : (int)(key >> 23) - 127 + 2;
+    E[u] = band_key_exp(j + u < nc ? kmax[j + u] : 0u);
     so[u] = pow2f(-E[u]);  // into units of the state's scale (exact)
   }
   if (blockIdx.y == 0 && threadIdx.x < 32) {
@@ -328,6 +339,37 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// After the product of a step: the scales of its slices of X_m (es_next: the predicted one of
+// each state, or, for a state the product flagged because an element outgrew that scale, the exact
+// one of the row maximum the product collected, knew) and the flagged states' slices cut again at
+// that scale from the double-float states; clears the flags.  One warp per state of the padded
+// block (256 threads, ncp / 8 CTAs).
+__global__ void __launch_bounds__(256)
+    k_band_fixup(const float4* __restrict__ x, int n, int ld, int nc, int npl, int ncp, size_t astride,
+                 __nv_bfloat16* __restrict__ lnext, int* __restrict__ es_next, const unsigned int* __restrict__ kprev,
+                 const unsigned int* __restrict__ knew, int* __restrict__ ovf) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (j >= ncp) return;  // whole warp (no barrier below)
+  const bool redo = j < nc && ovf[j] != 0;
+  const int E = redo ? band_key_exp(knew[j]) : (j < nc ? band_key_exp(kprev[j]) + BAND_MARGIN : 0);
+  if (lane == 0) es_next[j] = E;
+  if (!redo) return;
+  const float so = pow2f(-E);
+  for (int k = lane; k < n; k += 32) {
+    const float4 v = x[(size_t)j * ld + k];
+    __nv_bfloat16 dr[OZ_S], di[OZ_S];
+    df_digits2(make_float2(v.x * so, v.z * so), make_float2(v.y * so, v.w * so), dr, di);
+#pragma unroll
+    for (int q = 0; q < OZ_S; ++q) {
+      lnext[q * astride + (size_t)k * ncp + j] = dr[q];
+      lnext[q * astride + (size_t)(npl + k) * ncp + j] = di[q];
+    }
+  }
+  __syncwarp();
+  if (lane == 0) ovf[j] = 0;
+}
+
 constexpr int BAND_RG = 16;  // state blocks per raster group
 
 // Shared-memory descriptor of an MN-major operand with 128-byte swizzle, as the TMA boxes of
@@ -348,7 +390,11 @@ struct BandEpi {
   unsigned int* kmax;  // per row of X_m: largest |hi| of re or im as an FP32 key (atomicMax)
   const int* es;   // row exponents of the left slices
   const int* et;   // row exponents of the right slices
-  int n, nc, ld;
+  __nv_bfloat16* lnext;       // the left slices of X_m for the next step (MN-major, as k_band_slice)
+  const unsigned int* kprev;  // row maxima of X_{m-1}: the predicted scales of X_m's slices
+  int* ovf;                   // per state: an element outgrew the predicted scale (set to 1)
+  size_t astride;
+  int n, nc, ld, npl, ncp;
   float bound2;
   unsigned int* status;
 };
@@ -535,6 +581,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int ej = e.es[j];
         float4* orow = e.out + (size_t)j * e.ld;
         unsigned int kmx = 0u;
+        // the next step's slices of X_m at the scale X_{m-1}'s maximum predicts (the fixup pass
+        // cuts a state again if an element does not fit); a warp's lanes write 32 consecutive states
+        const float so = pow2f(-band_key_exp(e.kprev[j]) - BAND_MARGIN);
+        __nv_bfloat16* lcol = e.lnext + j;
+        bool fit = true;
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int i = i0 + part * 16 + c;
@@ -552,9 +603,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const unsigned int kr = __float_as_uint(rh) & 0x7FFFFFFFu, ki = __float_as_uint(ih) & 0x7FFFFFFFu;
             kmx = kr > kmx ? kr : kmx;
             kmx = ki > kmx ? ki : kmx;
+            __nv_bfloat16 dr[OZ_S], di[OZ_S];
+            fit &= df_digits2(make_float2(rh * so, ih * so), make_float2(rl * so, il * so), dr, di);
+#pragma unroll
+            for (int q = 0; q < OZ_S; ++q) {
+              lcol[q * e.astride + (size_t)i * e.ncp] = dr[q];
+              lcol[q * e.astride + (size_t)(e.npl + i) * e.ncp] = di[q];
+            }
           }
         }
         atomicMax(e.kmax + j, kmx);
+        if (!fit) e.ovf[j] = 1;
       }
     }
     if (!ok) {
@@ -623,8 +682,9 @@ struct BandWs {
   double2* rot;
   __nv_bfloat16* right;
   int* et;
-  __nv_bfloat16* left;
-  int* es;
+  __nv_bfloat16* left[2];  // slices of the states a product reads (alternating per step)
+  int* es[2];
+  int* ovf;
   unsigned int* kmax[2];  // row maxima of the states a product writes (alternating per step)
   float4* x[2];
   int nrows, npl, ncp, kh, kw;
@@ -655,8 +715,9 @@ size_t band_layout(const fq_plan* p, int nc, int nsteps, void* base, BandWs* out
   w.rot = (double2*)take(sizeof(double2) * (size_t)nsteps * w.nrows);
   w.right = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.rstride);
   w.et = (int*)take(sizeof(int) * w.nrows);
-  w.left = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.astride);
-  w.es = (int*)take(sizeof(int) * w.ncp);
+  for (int q = 0; q < 2; ++q) w.left[q] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.astride);
+  for (int q = 0; q < 2; ++q) w.es[q] = (int*)take(sizeof(int) * w.ncp);
+  w.ovf = (int*)take(sizeof(int) * w.ncp);
   for (int q = 0; q < 2; ++q) w.kmax[q] = (unsigned int*)take(sizeof(unsigned int) * w.ncp);
   for (int q = 0; q < 2; ++q) w.x[q] = (float4*)take(sizeof(float4) * (size_t)nc * w.npl);
   if (out) *out = w;
@@ -682,14 +743,15 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
   }
   BandWs w;
   band_layout(p, nc, nsteps, ws, &w);
-  OzMaps maps;
-  for (int q = 0; q < OZ_S; ++q) {
-    // MN-major: 64-element (128-byte) box rows, 16 K rows per box
-    if ((st = make_map(&maps.a[q], w.left + q * w.astride, 2 * w.npl, w.ncp, OZ_BKE, 64)) != FQ_OK) return st;
-    if ((st = make_map(&maps.r[q], w.right + q * w.rstride, (w.nrows / OZ_BN) * w.kw, 3 * OZ_BN, OZ_BKE, 64)) !=
-        FQ_OK)
-      return st;
-  }
+  OzMaps maps[2];  // per left slice buffer
+  for (int b = 0; b < 2; ++b)
+    for (int q = 0; q < OZ_S; ++q) {
+      // MN-major: 64-element (128-byte) box rows, 16 K rows per box
+      if ((st = make_map(&maps[b].a[q], w.left[b] + q * w.astride, 2 * w.npl, w.ncp, OZ_BKE, 64)) != FQ_OK) return st;
+      if ((st = make_map(&maps[b].r[q], w.right + q * w.rstride, (w.nrows / OZ_BN) * w.kw, 3 * OZ_BN, OZ_BKE, 64)) !=
+          FQ_OK)
+        return st;
+    }
   static std::atomic<unsigned> attr_set{0};
   if (fq_first_on_device(attr_set)) {
     cudaError_t e = cudaFuncSetAttribute(k_oz_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OzCfg::SMEM);
@@ -698,6 +760,15 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
   if (sms < 1) sms = 152;
+  // component rows >= n of the second slice buffer stay zero (the epilogue writes rows < n only;
+  // the first step's slicing pass fills the first buffer whole); no state is flagged yet
+  cudaError_t ce = cudaMemsetAsync(w.ovf, 0, sizeof(int) * w.ncp, s);
+  if (nsteps > 1 && w.npl > n)
+    for (int q = 0; q < OZ_S && ce == cudaSuccess; ++q)
+      for (int part = 0; part < 2 && ce == cudaSuccess; ++part)
+        ce = cudaMemsetAsync(w.left[1] + q * w.astride + (size_t)(part * w.npl + n) * w.ncp, 0,
+                             sizeof(__nv_bfloat16) * (size_t)(w.npl - n) * w.ncp, s);
+  if (ce != cudaSuccess) return fq_cuda_fail(ce, "band workspace clear");
   GaugeArgs ga{p->n, p->steps, p->d_h0, p->d_h0o, p->d_h1, p->d_k, p->d_scal, p->sbeta};
   k_gauge_tile<double><<<nsteps, GAUGE_NT, 0, s>>>(ga, w.nrows, m_begin, w.cf, w.rot);
   k_band_load<<<band_grid((size_t)nc * w.npl), 256, 0, s>>>(identity ? nullptr : (const double2*)x0, w.x[0], nc, n,
@@ -712,59 +783,41 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
   const int tiles_i = (n + OZ_BN - 1) / OZ_BN, tiles_j = w.ncp / BM;
   const int ntiles = tiles_i * tiles_j;
   BandEpi e{};
-  e.es = w.es;
   e.et = w.et;
+  e.ovf = w.ovf;
+  e.astride = w.astride;
   e.n = n;
   e.nc = nc;
   e.ld = w.npl;
+  e.npl = w.npl;
+  e.ncp = w.ncp;
   e.bound2 = (float)(1.0 + 1e-6);
   e.status = p->d_status;
-  // P_{m} is formed on a second stream while the states of step m are sliced (ALU against HBM
-  // work); the product waits for both.  P_m may overwrite the band only once product m-1 is done.
-  // (A capturing stream keeps everything on itself: no stream of this call's own joins a capture.)
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_prod = nullptr, ev_rows = nullptr;
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  cudaError_t ce = cudaStreamIsCapturing(s, &cap);
-  const bool overlap = ce == cudaSuccess && cap == cudaStreamCaptureStatusNone;
-  if (overlap && ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
-  if (overlap && ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ev_prod, cudaEventDisableTiming);
-  if (overlap && ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ev_rows, cudaEventDisableTiming);
-  const cudaStream_t rs = overlap ? side : s;
-  auto release = [&] {
-    if (ev_prod) cudaEventDestroy(ev_prod);
-    if (ev_rows) cudaEventDestroy(ev_rows);
-    if (side) cudaStreamDestroy(side);
-  };
-  if (ce != cudaSuccess) {
-    release();
-    return fq_cuda_fail(ce, "band chain streams");
+  // the first step's slices, at the scales of the states' own maxima
+  if (nsteps > 0) {
+    k_band_rowmax<<<nc, 256, 0, s>>>(w.x[0], n, w.npl, w.kmax[1]);
+    k_band_slice<<<dim3(w.ncp / 64, w.npl / 16), 256, 0, s>>>(w.x[0], n, w.npl, nc, w.npl, w.ncp, w.astride,
+                                                              w.left[0], w.es[0], w.kmax[1]);
   }
   int cur = 0;
-  for (int m = 0; m < nsteps && ce == cudaSuccess; ++m) {
-    if (overlap) {
-      ce = cudaEventRecord(ev_prod, s);  // product m-1 (or the set-up) done
-      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(side, ev_prod, 0);
-      if (ce != cudaSuccess) break;
-    }
-    // P_m, clearing the row maxima product m will collect
-    k_band_rows<<<(w.nrows + BAND_ROWS_PER_CTA - 1) / BAND_ROWS_PER_CTA, 32 * BAND_ROWS_PER_CTA, 0, rs>>>(
+  for (int m = 0; m < nsteps; ++m) {
+    const int b = m & 1, nb = b ^ 1;
+    // P_m, clearing the row maxima product m will collect (product m-1's stay for the prediction)
+    k_band_rows<<<w.nrows / BAND_ROWS_PER_CTA, 32 * BAND_ROWS_PER_CTA, 0, s>>>(
         w.cf + (size_t)m * w.nrows, w.rot + (size_t)m * w.nrows, n, w.nrows, L, coef, p->phase_re, p->phase_im,
-        w.rstride, w.right, w.et, w.kmax[m & 1], w.ncp, w.kh);
-    if (overlap) ce = cudaEventRecord(ev_rows, side);
-    // the states' slices, with the row maxima product m-1 collected; the first step finds them
-    // (into the buffer k_band_rows of step 0 leaves alone)
-    if (m == 0) k_band_rowmax<<<nc, 256, 0, s>>>(w.x[cur], n, w.npl, w.kmax[1]);
-    k_band_slice<<<dim3(w.ncp / 64, w.npl / 16), 256, 0, s>>>(w.x[cur], n, w.npl, nc, w.npl, w.ncp, w.astride,
-                                                              w.left, w.es, w.kmax[(m + 1) & 1]);
-    if (overlap && ce == cudaSuccess) ce = cudaStreamWaitEvent(s, ev_rows, 0);
+        w.rstride, w.right, w.et, w.kmax[b], w.ncp, w.kh);
+    // X_m = P_m X_{m-1}, and X_m's slices for the next step at the scales X_{m-1}'s maxima predict
     e.out = w.x[cur ^ 1];
-    e.kmax = w.kmax[m & 1];
-    k_oz_band<<<std::min(ntiles, sms), OZ_THREADS, OzCfg::SMEM, s>>>(maps, tiles_j, tiles_i, w.npl, w.kh, e);
+    e.kmax = w.kmax[b];
+    e.es = w.es[b];
+    e.lnext = w.left[nb];
+    e.kprev = w.kmax[nb];
+    k_oz_band<<<std::min(ntiles, sms), OZ_THREADS, OzCfg::SMEM, s>>>(maps[b], tiles_j, tiles_i, w.npl, w.kh, e);
+    // the slice scales of X_m, and the states that outgrew their predicted scale cut again
+    k_band_fixup<<<w.ncp / 8, 256, 0, s>>>(w.x[cur ^ 1], n, w.npl, nc, w.npl, w.ncp, w.astride, w.left[nb],
+                                           w.es[nb], w.kmax[nb], w.kmax[b], w.ovf);
     cur ^= 1;
   }
-  release();
-  if (ce != cudaSuccess) return fq_cuda_fail(ce, "band chain streams");
   if (transpose_out) {
     dim3 g((n + 31) / 32, (n + 31) / 32), b(32, 8);
     k_band_store_t<<<g, b, 0, s>>>(w.x[cur], (double2*)x, n, w.npl);

@@ -82,6 +82,42 @@ def test_band_ragged_sizes(fq, nb, steps, m_end):
     assert err <= 1e-10
 
 
+def test_band_refocusing_states_take_the_rescaling_path(fq):
+    """States that refocus: x0 = P_0^+ P_1^+ y with y = (e_a + e_b + e_c) / sqrt(3) (three basis
+    vectors far apart), so X_0 = P_1^+ y spreads over three bands of about 2L + 1 components and
+    X_1 = y.  The product cuts X_1 into the next step's slices at the scale X_0's largest |Re| or
+    |Im| predicts, one bit up: 2^(floor(log2 a) + 3) for a maximum a, which holds values up to
+    2^(floor(log2 a) + 2).  With a < 1/4 (checked on the oracle's X_0) that is at most 1/2, below
+    y's 1/sqrt(3), so those states are flagged and cut again from the double-float states at their
+    exact scale.  Three refocusing states and two plain ones (dim 701, 6 steps) against the oracle
+    at the FP64 criterion, and X_1 against y."""
+    d = fi.config_dimer(nb=700, steps=200)
+    d.drive = fi.Drive(0.2, 1.5, 3.0, 0.4)
+    plan = band_plan(fq, d)
+    n = d.n
+    refp = o.plan_for_drive_tridiag(d.h0_diag, d.h0_off, d.h1_diag, d.drive, d.steps)
+    prop = lambda x, m0, m1: o.propagate_tridiag(d.h0_diag, d.h0_off, d.h1_diag, refp, x, m0, m1)
+    eye = np.eye(n, dtype=complex)
+    p0, p1 = prop(eye, 0, 1), prop(eye, 1, 2)
+    y = np.zeros((n, 3), complex)
+    for c, ks in enumerate(((50, 300, 550), (100, 350, 600), (150, 400, 650))):
+        y[list(ks), c] = 1.0 / np.sqrt(3.0)
+    x_0 = p1.conj().T @ y                           # X_0 of the refocusing states
+    part_max = lambda v: np.max(np.maximum(np.abs(v.real), np.abs(v.imag)), axis=0)
+    assert np.all(part_max(x_0) < 0.25) and np.all(part_max(y) > 0.5)
+    x0 = np.concatenate([p0.conj().T @ x_0, np.zeros((n, 2), complex)], axis=1)
+    x0[0, 3] = 1.0
+    x0[:, 4] = np.exp(2j * np.pi * fi.uniform(2601, n)) / np.sqrt(n)
+    X1 = to_np(plan.propagate(cuda_c128(x0.T), 0, 2))
+    assert plan.check_status() == fq.FQ_OK
+    assert np.max(np.abs(X1[:3] - y.T)) <= 1e-10
+    X = to_np(plan.propagate(cuda_c128(x0.T), 0, 6))
+    ref = prop(x0, 0, 6).T
+    err = np.max(np.abs(X - ref))
+    print(f"band refocusing states: max err {err:.2e}")
+    assert err <= 1e-10
+
+
 def test_band_many_state_tiles_and_column_split(fq):
     """dim 701 (11 operator blocks), all 701 states (6 state tiles, ragged): U_T equals the column
     blocks of a 3-rank split bit for bit, and matches the oracle."""
