@@ -372,8 +372,9 @@ DIMER_PATHS = {
 
 # DRAM bytes of one k_oz_band launch (one step's banded product) from the ncu capture of
 # `python bench.py --ncu-case band` (2048 states; profiles/k_oz_band_dimer10001.md), scaled to a
-# launch by states: the state slices read and the new states written grow with the states.
-BAND_NCU = {"read": 586.6e6, "write": 297.3e6, "states": 2048}
+# launch by states: the state slices read, the new states and their slices written grow with the
+# states.
+BAND_NCU = {"read": 621.7e6, "write": 792.0e6, "states": 2048}
 
 
 def band_window(L):
@@ -464,10 +465,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         if plan.check_status() != fq.FQ_OK:
             raise RuntimeError("device bound check fired during warm-up")
+        # CUDA events around every launch of the step kernel, on its stream, over the timed region
+        fq.floquet_kernel_timing(plan.handle, True)
         per_step, total, clk = timed_loop(step, steps, stream, world, dist)
-        return plan, out["U"], per_step, total, clk
+        ktime = fq.floquet_kernel_time(plan.handle)
+        fq.floquet_kernel_timing(plan.handle, False)
+        return plan, out["U"], per_step, total, clk, ktime
 
-    plan, U, per_step, total, clk = timed_build(path, args.warmup, args.steps)
+    plan, U, per_step, total, clk, ktime = timed_build(path, args.warmup, args.steps)
     value, total = job_throughput(total, args.steps, dist if world > 1 else None, "cuda")
     if sharded:
         value /= world  # every rank took part in the same U_T builds
@@ -509,11 +514,11 @@ def run_ours(args):
     # the FP32 resident kernel alongside an FP64-level headline (same workload, its own timing)
     fp32 = None
     if prec != "fp32" and not args.no_fp32_extra:
-        p32, _, ps32, tot32, clk32 = timed_build(DIMER_PATHS["fp32"], min(args.warmup, 3), args.fp32_steps)
+        p32, _, ps32, tot32, clk32, kt32 = timed_build(DIMER_PATHS["fp32"], min(args.warmup, 3), args.fp32_steps)
         v32, tot32 = job_throughput(tot32, args.fp32_steps, dist if world > 1 else None, "cuda")
         if sharded:
             v32 /= world
-        avg32 = statistics.mean(ps32)
+        avg32 = kt32[1] / 1000.0 / kt32[0] if kt32[0] else statistics.mean(ps32)
         fp32 = {"value": v32, "unit": "U_T/s", "ms_per_step": 1000.0 * tot32 / args.fp32_steps,
                 "steps": args.fp32_steps, "dtype": "f32", "per_step_s": ps32, "clocks": clk32,
                 "roofline": dict(dimer_roofline(DIMER_PATHS["fp32"], n, d.steps, L, avg32,
@@ -527,13 +532,17 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     avg = statistics.mean(per_step)
+    # the step kernel's mean launch duration from its own events (else the build time per launch)
+    klaunches, kms, kname = ktime
     if prec == "fp32":  # one launch per U_T: the whole chain
-        roofline = dimer_roofline(path, n, d.steps, L, avg, float(n) * n * d.steps * L / (world if sharded else 1))
+        kavg = kms / 1000.0 / klaunches if klaunches else avg
+        roofline = dimer_roofline(path, n, d.steps, L, kavg, float(n) * n * d.steps * L / (world if sharded else 1))
         roofline["traffic"] = resident_traffic(n, d.steps, n / (world if sharded else 1))
         roofline["traffic_note"] = RES_TRAFFIC_NOTE
     else:  # one launch per step: units of one launch over the launch's mean duration
         per_launch = float(n) * n * L / (world if sharded else 1)
-        roofline = dimer_roofline(path, n, d.steps, L, avg / d.steps, per_launch)
+        kavg = kms / 1000.0 / klaunches if klaunches else avg / d.steps
+        roofline = dimer_roofline(path, n, d.steps, L, kavg, per_launch)
         roofline["traffic"] = None
         roofline["traffic_note"] = "see profiles/ for the kernel's DRAM bytes per launch"
         if prec == "ozaki" and BAND_NCU["read"] is not None:
@@ -541,8 +550,11 @@ def run_ours(args):
                 BAND_NCU["states"]
             roofline["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of k_oz_band from one ncu capture "
                                         "of --ncu-case band (2048 states), scaled to a launch by states")
-        roofline["launch_seconds_note"] = ("mean U_T time / M, which also holds the step's other launches "
-                                           "(their share is in the profiles' launch list)")
+    roofline["launch_seconds"] = kavg
+    roofline["launch_seconds_note"] = (
+        f"mean of {klaunches} CUDA-event-timed launches of {kname} on its stream over the timed region "
+        "(floquet_kernel_timing); the U_T time also holds the step's other launches (profiles' launch list)"
+        if klaunches else "mean U_T time / launches per U_T (no kernel events recorded)")
     cpu = None
     accuracy = {"unitarity_defect_max": defect_max, "unitarity_defect_fro": defect_fro,
                 "defect_columns": int(sample_cols.numel())}

@@ -208,6 +208,20 @@ typedef struct fq_report {
 fq_status floquet_build_UT_report(fq_plan* plan, void* d_U, void* d_ws, size_t ws_bytes, void* stream,
                                   int32_t defect_columns, fq_report* report);
 
+/* Kernel timing, a measurement aid (the paper has no counterpart).  While enabled, the calls that
+ * run the tridiagonal chain's step kernel with this plan record a pair of CUDA events on the
+ * caller's stream around each launch of that kernel: the band product k_oz_band (FQ_OZAKI), the
+ * resident chain k_tri_resident (FQ_FP32, one launch per call) or the double-float step
+ * k_tri_tile_dfl (FQ_DF32); other paths record nothing, and nothing is recorded on a stream that
+ * is capturing a graph.  floquet_kernel_timing switches this on (enable != 0) or off and clears the
+ * record.  floquet_kernel_time waits for the last recorded event and returns the launches recorded
+ * since the last read, the sum of their durations in milliseconds and the kernel's name
+ * (NUL-terminated, at most name_len - 1 characters; name may be NULL), then clears the record.
+ * FQ_EINVAL for a NULL plan or output; FQ_ECUDA if an event could not be created or recorded (the
+ * record is cleared).  Calls on one plan must not overlap in time. */
+fq_status floquet_kernel_timing(fq_plan* plan, int32_t enable);
+fq_status floquet_kernel_time(fq_plan* plan, int32_t* launches, double* total_ms, char* name, int32_t name_len);
+
 /* Propagates a block of ncols states through steps m_begin .. m_end-1 (0-based), i.e.
  * X = U_{m_end} ... U_{m_begin+1} X0 (Eq. 9 restricted to those steps).  d_X0, d_X: ncols x N
  * complex128, row r = state r, caller-owned device memory; d_X may equal d_X0.  FQ_EINVAL for a

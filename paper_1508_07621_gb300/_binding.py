@@ -85,6 +85,8 @@ _SIGS = {
                                                   ctypes.c_double, _vp, _vp, _sz, _vp]),
     "floquet_overlap_workspace_size": (_sz, [_vp, _i32]),
     "floquet_overlap_phase_error": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
+    "floquet_kernel_timing": (ctypes.c_int, [_vp, _i32]),
+    "floquet_kernel_time": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), _dp, ctypes.c_char_p, _i32]),
     "floquet_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -225,6 +227,20 @@ def floquet_build_UT_report(plan: int, U, ws, defect_columns: int = 64, stream=N
     _check(lib.floquet_build_UT_report(_vp(plan), pu, pw, nb, _stream(stream), int(defect_columns),
                                        ctypes.byref(rep)), w)
     return rep
+
+
+def floquet_kernel_timing(plan: int, enable: bool) -> None:
+    """Switches the event timing of the chain's step kernel on or off (and clears its record)."""
+    _check(lib.floquet_kernel_timing(_vp(plan), 1 if enable else 0), "floquet_kernel_timing")
+
+
+def floquet_kernel_time(plan: int) -> tuple[int, float, str]:
+    """(launches, total milliseconds, kernel name) recorded since the last read."""
+    n = _i32(0)
+    ms = ctypes.c_double(0.0)
+    buf = ctypes.create_string_buffer(64)
+    _check(lib.floquet_kernel_time(_vp(plan), ctypes.byref(n), ctypes.byref(ms), buf, 64), "floquet_kernel_time")
+    return int(n.value), float(ms.value), buf.value.decode()
 
 
 def floquet_propagate(plan: int, X0, X, ncols: int, m_begin: int, m_end: int, ws, stream=None) -> None:

@@ -1,6 +1,7 @@
 // C ABI: plan lifetime, workspace layout and the host loops that chain the kernels
 // (the propagation part of Algorithm 1: M steps of L Chebyshev terms each, U_T written in place).
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -237,6 +238,10 @@ void free_plan(fq_plan* p) {
   for (void* d : {(void*)p->d_h0, (void*)p->d_h1, (void*)p->d_k, (void*)p->d_h0o, (void*)p->d_scal,
                   (void*)p->d_status, (void*)p->d_cm})
     if (d) cudaFree(d);
+  if (p->ktimer) {
+    for (cudaEvent_t e : p->ktimer->ev) cudaEventDestroy(e);
+    delete p->ktimer;
+  }
   delete p;
 }
 
@@ -414,6 +419,33 @@ fq_status plan_create(fq_plan** out, const fq_problem* prob) {
 
 }  // namespace
 
+void fq_ktimer_start(const fq_plan* p, cudaStream_t s, const char* name) {
+  fq_ktimer* t = p->ktimer;
+  if (!t || !t->on || t->err != cudaSuccess) return;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
+  try {
+    while (t->ev.size() < t->used + 2) {
+      cudaEvent_t e = nullptr;
+      if ((t->err = cudaEventCreate(&e)) != cudaSuccess) return;
+      t->ev.push_back(e);
+    }
+  } catch (...) {
+    t->err = cudaErrorMemoryAllocation;
+    return;
+  }
+  if ((t->err = cudaEventRecord(t->ev[t->used], s)) != cudaSuccess) return;
+  t->name = name;
+  t->open = true;
+}
+
+void fq_ktimer_stop(const fq_plan* p, cudaStream_t s) {
+  fq_ktimer* t = p->ktimer;
+  if (!t || !t->open) return;
+  t->open = false;
+  if ((t->err = cudaEventRecord(t->ev[t->used + 1], s)) == cudaSuccess) t->used += 2;
+}
+
 extern "C" {
 
 fq_status floquet_plan_create(fq_plan** out, const fq_problem* prob) {
@@ -514,6 +546,48 @@ fq_status floquet_build_UT_report(fq_plan* p, void* d_U, void* d_ws, size_t ws_b
     rep->build_ms = ms;
     return floquet_check_status(p, stream);
   });
+}
+
+fq_status floquet_kernel_timing(fq_plan* p, int32_t enable) {
+  if (!p) { fq_set_error("NULL plan"); return FQ_EINVAL; }
+  return fq_guard("floquet_kernel_timing", [&]() -> fq_status {
+    if (!p->ktimer) p->ktimer = new fq_ktimer();
+    fq_ktimer* t = p->ktimer;
+    t->on = enable != 0;
+    t->open = false;
+    t->used = 0;
+    t->err = cudaSuccess;
+    t->name = "";
+    return FQ_OK;
+  });
+}
+
+fq_status floquet_kernel_time(fq_plan* p, int32_t* launches, double* total_ms, char* name, int32_t name_len) {
+  if (!p || !launches || !total_ms) { fq_set_error("NULL plan or output"); return FQ_EINVAL; }
+  *launches = 0;
+  *total_ms = 0.0;
+  if (name && name_len > 0) name[0] = '\0';
+  fq_ktimer* t = p->ktimer;
+  if (!t) return FQ_OK;
+  const size_t used = t->used;
+  const cudaError_t failed = t->err;
+  t->used = 0;
+  t->err = cudaSuccess;
+  if (failed != cudaSuccess) return fq_cuda_fail(failed, "kernel timing events");
+  double sum = 0.0;
+  if (used > 0) {
+    cudaError_t e = cudaEventSynchronize(t->ev[used - 1]);
+    for (size_t k = 0; k < used && e == cudaSuccess; k += 2) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, t->ev[k], t->ev[k + 1]);
+      sum += ms;
+    }
+    if (e != cudaSuccess) return fq_cuda_fail(e, "kernel timing");
+  }
+  *launches = (int32_t)(used / 2);
+  *total_ms = sum;
+  if (name && name_len > 0) snprintf(name, (size_t)name_len, "%s", used ? t->name : "");
+  return FQ_OK;
 }
 
 fq_status floquet_propagate(fq_plan* p, const void* d_X0, void* d_X, int32_t ncols, int32_t m_begin, int32_t m_end,

@@ -812,7 +812,9 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
     e.es = w.es[b];
     e.lnext = w.left[nb];
     e.kprev = w.kmax[nb];
+    fq_ktimer_start(p, s, "k_oz_band");
     k_oz_band<<<std::min(ntiles, sms), OZ_THREADS, OzCfg::SMEM, s>>>(maps[b], tiles_j, tiles_i, w.npl, w.kh, e);
+    fq_ktimer_stop(p, s);
     // the slice scales of X_m, and the states that outgrew their predicted scale cut again
     k_band_fixup<<<w.ncp / 8, 256, 0, s>>>(w.x[cur ^ 1], n, w.npl, nc, w.npl, w.ncp, w.astride, w.left[nb],
                                            w.es[nb], w.kmax[nb], w.kmax[b], w.ovf);

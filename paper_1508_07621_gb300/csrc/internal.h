@@ -29,6 +29,16 @@ enum fq_path : int {
   PATH_DENSE_OZAKI = 6,   // tcgen05 FP64 emulation (fixed-point BF16 slices, exact FP32 sums) per term
 };
 
+// Measurement aid (floquet_kernel_timing): CUDA event pairs recorded on the caller's stream around
+// each launch of a path's dominant kernel while enabled; the pool of events is reused.
+struct fq_ktimer {
+  bool on = false, open = false;  // open: a start event is recorded, its stop not yet
+  const char* name = "";
+  std::vector<cudaEvent_t> ev;    // (start, stop) pairs
+  size_t used = 0;                // events recorded since the last read
+  cudaError_t err = cudaSuccess;  // first failure since the last read
+};
+
 struct fq_plan {
   // problem
   int n = 0, steps = 0, format = 0, precision = 0, drive_kind = 0, stride = 16, L = 0;
@@ -67,7 +77,13 @@ struct fq_plan {
   unsigned int* d_status = nullptr;
   // dense split path: per-plan constants prepared once
   void* split = nullptr;
+  fq_ktimer* ktimer = nullptr;  // owned; NULL until floquet_kernel_timing
 };
+
+// Brackets one launch of a path's dominant kernel with the plan's timing events (no-ops unless
+// floquet_kernel_timing enabled them, and on a stream that is capturing a graph).
+void fq_ktimer_start(const fq_plan* p, cudaStream_t s, const char* name);
+void fq_ktimer_stop(const fq_plan* p, cudaStream_t s);
 
 // thread-local error message
 void fq_set_error(const char* fmt, ...);

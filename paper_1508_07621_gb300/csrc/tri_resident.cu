@@ -424,9 +424,11 @@ fq_status launch_cfg(const fq_plan* p, const float4* cf, const float4* rot, cons
         cudaFuncSetAttribute(k_tri_resident<NT, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fq_cuda_fail(e, "resident kernel smem attribute");
   }
+  fq_ktimer_start(p, s, "k_tri_resident");
   k_tri_resident<NT, EPT><<<nc, NT, smem, s>>>(cf, rot, p->n, p->L, nsteps, (const double2*)x0, (double2*)x,
                                                 transpose_out, coef, (float)p->phase_re, (float)p->phase_im, bcl,
                                                 p->d_status);
+  fq_ktimer_stop(p, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fq_cuda_fail(e, "resident kernel launch");
   return FQ_OK;

@@ -360,10 +360,12 @@ fq_status dfl_chain(fq_plan* p, const double* x0, double* x, int nc, int m_begin
     for (int r0 = 0; r0 < nc; r0 += 65535) {
       const int rows = nc - r0 < 65535 ? nc - r0 : 65535;
       const size_t o = (size_t)r0 * ld;
+      fq_ktimer_start(p, s, "k_tri_tile_dfl");
       k_tri_tile_dfl<<<dim3(segs, rows), DFL_NT, 0, s>>>(cf + (size_t)m * ld, rot + (size_t)m * ld, b[cur].re + o,
                                                           b[cur].im + o, b[cur ^ 1].re + o, b[cur ^ 1].im + o, n, ld,
                                                           L, seg, coef, p->phase_re, p->phase_im, 1.0 + 1e-9,
                                                           p->d_status);
+      fq_ktimer_stop(p, s);
     }
     cur ^= 1;
   }

@@ -156,6 +156,37 @@ def test_band_kernel_selection(fq):
     assert e.value.status == fq.FQ_EUNSUPPORTED
 
 
+def test_kernel_timing_records_the_step_kernel(fq):
+    """floquet_kernel_timing: a band build of M = 100 steps records 100 launches of k_oz_band whose
+    summed event time lies inside the build's own; reading clears the record; switched off,
+    nothing is recorded; an FP32 build records its one resident launch."""
+    import torch
+    d = fi.config_dimer(nb=40, steps=100)
+    stream = torch.cuda.current_stream()
+    U = torch.empty((d.n, d.n), dtype=torch.complex128, device="cuda")
+    plan = band_plan(fq, d)
+    ws = fq.workspace(plan.workspace_size())
+    fq.floquet_kernel_timing(plan.handle, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fq.floquet_build_UT(plan.handle, U, ws, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches, ms, name = fq.floquet_kernel_time(plan.handle)
+    assert (launches, name) == (100, "k_oz_band")
+    assert 0.0 < ms <= e0.elapsed_time(e1)
+    assert fq.floquet_kernel_time(plan.handle) == (0, 0.0, "")
+    fq.floquet_kernel_timing(plan.handle, False)
+    fq.floquet_build_UT(plan.handle, U, ws, stream)
+    assert fq.floquet_kernel_time(plan.handle)[0] == 0
+    p32 = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=d.drive.f_ac,
+                          steps=d.steps, precision=fq.FQ_FP32)
+    fq.floquet_kernel_timing(p32.handle, True)
+    fq.floquet_build_UT(p32.handle, U, fq.workspace(p32.workspace_size()), stream)
+    launches, ms, name = fq.floquet_kernel_time(p32.handle)
+    assert (launches, name) == (1, "k_tri_resident") and ms > 0.0
+
+
 def _oracle_dimer_column(j):
     d = fi.config_dimer()
     p = o.plan_for_drive_tridiag(d.h0_diag, d.h0_off, d.h1_diag, d.drive, d.steps)
