@@ -9,14 +9,18 @@
 //      (gauge.cuh), row i of P(Omega') is P(Omega') e_i (P(Omega') is complex symmetric), computed
 //      by Clenshaw's recurrence in double-float arithmetic on a 96-row window around i, which holds
 //      its support i +- L; then P_m[i][k] = e^{-i beta h} e^{i theta_i} v_k e^{-i theta_k} in FP64;
-//   2. cuts the state rows into fixed-point BF16 slices (k_band_slice, as FQ_OZAKI does for dense
-//      operators, ozaki_core.cuh);
-//   3. multiplies every state by the band on the tensor cores (k_oz_band): a tile of 64 operator
-//      rows [i0, i0 + 64) needs only the state columns [i0 - 48, i0 + 112), so its K loop is that
-//      160-wide window instead of all N columns.  The 21 slice pairs sum exactly in FP32 tensor
-//      memory over the whole window (3 pairs x 2^14 x 320 products < 2^24 units), so one drain
-//      per tile suffices, and the epilogue writes the new state as double-float pairs with FP32
-//      instructions only (GB300's FP64 rate is far below its FP32 and tensor rates).
+//   2. multiplies every state, held as fixed-point BF16 slices (as FQ_OZAKI does for dense
+//      operators, ozaki_core.cuh), by the band on the tensor cores (k_oz_band): a tile of 64
+//      operator rows [i0, i0 + 64) needs only the state columns [i0 - kh, i0 + 64 + kh) (kh = L
+//      rounded up to 8), so its K loop is that window instead of all N columns.  The 21 slice
+//      pairs sum exactly in FP32 tensor memory over the whole window (3 pairs x 2^14 x 320
+//      products < 2^24 units), so one drain per tile suffices; the epilogue forms the new states
+//      as double-float pairs with FP32 instructions only (GB300's FP64 rate is far below its FP32
+//      and tensor rates) and cuts them into the next step's slices at a predicted scale;
+//   3. fixes the scales and cuts again any state that outgrew its prediction (k_band_fixup).
+// Between steps the slices are the states; the double-float states are written at the last step
+// (and for single entries the slices cannot hold).  A call's input states are sliced once
+// (k_band_rowmax, k_band_slice).
 // The product is the same polynomial the Chebyshev recurrence applies, so the result agrees with
 // the plain chain to the emulation's rounding (48 bits per slice product).  Needs L <= 47.
 //
@@ -25,6 +29,7 @@
 // 64 BF16 = 128 bytes (128-byte swizzle) although a K stage is only 16 deep: the K-major form
 // (16 BF16 = 32-byte box rows) fed the tensor cores at about two thirds of the rate.
 //   states     double-float [nc][npl] float4 (re_hi, re_lo, im_hi, im_lo), npl = N rounded to 128
+//              (the input, the output, and entries the slices cannot hold)
 //   left       OZ_S slices [2 npl][ncp] BF16: row k the real parts of component k of every
 //              state, row npl + k the imaginary parts
 //   right      OZ_S slices [nrows / 64][kw][192] BF16: per 64-row block b and window column
@@ -342,7 +347,9 @@ __global__ void __launch_bounds__(256)
 // After the product of a step: the scales of its slices of X_m (es_next: the predicted one of
 // each state, or, for a state the product flagged because an element outgrew that scale, the exact
 // one of the row maximum the product collected, knew) and the flagged states' slices cut again at
-// that scale from the double-float states; clears the flags.  One warp per state of the padded
+// that scale; clears the flags.  A flagged state's entries come back from its slices at the
+// predicted scale (the six digits' sum is exact in FP64), or, for an entry marked by a NaN leading
+// digit, from the double-float value the product stored for it.  One warp per state of the padded
 // block (256 threads, ncp / 8 CTAs).
 __global__ void __launch_bounds__(256)
     k_band_fixup(const float4* __restrict__ x, int n, int ld, int nc, int npl, int ncp, size_t astride,
@@ -356,9 +363,29 @@ __global__ void __launch_bounds__(256)
   if (lane == 0) es_next[j] = E;
   if (!redo) return;
   const float so = pow2f(-E);
+  const double sp = ldexp(1.0, band_key_exp(kprev[j]) + BAND_MARGIN);  // the scale the product cut at
   for (int k = lane; k < n; k += 32) {
-    const float4 v = x[(size_t)j * ld + k];
+    float4 v;
     __nv_bfloat16 dr[OZ_S], di[OZ_S];
+#pragma unroll
+    for (int q = 0; q < OZ_S; ++q) {
+      dr[q] = lnext[q * astride + (size_t)k * ncp + j];
+      di[q] = lnext[q * astride + (size_t)(npl + k) * ncp + j];
+    }
+    if (__hisnan(dr[0]) || __hisnan(di[0])) {
+      v = x[(size_t)j * ld + k];
+    } else {
+      double re = 0.0, im = 0.0;
+#pragma unroll
+      for (int q = 0; q < OZ_S; ++q) {
+        re += (double)__bfloat162float(dr[q]);
+        im += (double)__bfloat162float(di[q]);
+      }
+      re *= sp;
+      im *= sp;
+      const float rh = (float)re, ih = (float)im;
+      v = make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
+    }
     df_digits2(make_float2(v.x * so, v.z * so), make_float2(v.y * so, v.w * so), dr, di);
 #pragma unroll
     for (int q = 0; q < OZ_S; ++q) {
@@ -394,6 +421,7 @@ struct BandEpi {
   const unsigned int* kprev;  // row maxima of X_{m-1}: the predicted scales of X_m's slices
   int* ovf;                   // per state: an element outgrew the predicted scale (set to 1)
   size_t astride;
+  int write_states;           // 1: write every entry of X_m (the last step); else only entries the slices cannot hold
   int n, nc, ld, npl, ncp;
   float bound2;
   unsigned int* status;
@@ -403,10 +431,10 @@ struct BandEpi {
 // 64-row tiles, persistent: one CTA per SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // rasterized in groups of 16 state blocks that sweep the operator blocks together (co-running CTAs
 // share each operator block and the sliding state windows in L2).  Warp 0 streams
-// TMA stages (K = 16 each, 32-byte swizzle), warp 1 issues the MMAs of the 21 slice pairs into the
-// four accumulators (512 tensor-memory columns), warps 2-17 drain them once per tile into
-// double-float registers, release the tensor memory and write the tile while the next tile's MMAs
-// run.  Every wait is bounded; a wait that gives up records FQ_BIT_TIMEOUT, drains this CTA's own
+// TMA stages (K = 16 each, 128-byte MN-major box rows), warp 1 issues the MMAs of the 21 slice
+// pairs into the four accumulators (512 tensor-memory columns), warps 2-17 drain them once per
+// tile into double-float registers, release the tensor memory and write the tile's slices for the
+// next step (and, at the last step, its double-float states) while the next tile's MMAs run.  Every wait is bounded; a wait that gives up records FQ_BIT_TIMEOUT, drains this CTA's own
 // copies and MMAs, frees tensor memory and returns.
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_oz_band(const __grid_constant__ OzMaps maps, int tiles_j, int tiles_i, int npl, int kh, BandEpi e) {
@@ -599,12 +627,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const float rh = __fadd_rn(rh0, rl0), ih = __fadd_rn(ih0, il0);  // renormalise the pairs
             const float rl = __fsub_rn(rl0, __fsub_rn(rh, rh0)), il = __fsub_rn(il0, __fsub_rn(ih, ih0));
             bad |= !(rh * rh + ih * ih <= e.bound2);
-            orow[i] = make_float4(rh, rl, ih, il);
             const unsigned int kr = __float_as_uint(rh) & 0x7FFFFFFFu, ki = __float_as_uint(ih) & 0x7FFFFFFFu;
             kmx = kr > kmx ? kr : kmx;
             kmx = ki > kmx ? ki : kmx;
             __nv_bfloat16 dr[OZ_S], di[OZ_S];
-            fit &= df_digits2(make_float2(rh * so, ih * so), make_float2(rl * so, il * so), dr, di);
+            const bool f = df_digits2(make_float2(rh * so, ih * so), make_float2(rl * so, il * so), dr, di);
+            // between steps the slices carry the state; an entry they cannot hold is kept whole,
+            // and its NaN leading digits send the fixup pass to it
+            if (e.write_states || !f) orow[i] = make_float4(rh, rl, ih, il);
+            if (!f) dr[0] = di[0] = __ushort_as_bfloat16((unsigned short)0x7FC0);
+            fit &= f;
 #pragma unroll
             for (int q = 0; q < OZ_S; ++q) {
               lcol[q * e.astride + (size_t)i * e.ncp] = dr[q];
@@ -812,6 +844,7 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
     e.es = w.es[b];
     e.lnext = w.left[nb];
     e.kprev = w.kmax[nb];
+    e.write_states = m == nsteps - 1;
     fq_ktimer_start(p, s, "k_oz_band");
     k_oz_band<<<std::min(ntiles, sms), OZ_THREADS, OzCfg::SMEM, s>>>(maps[b], tiles_j, tiles_i, w.npl, w.kh, e);
     fq_ktimer_stop(p, s);
