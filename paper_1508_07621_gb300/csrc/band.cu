@@ -102,21 +102,28 @@ __device__ __forceinline__ void band_apply(const dflc (&x)[BAND_LANE_ROWS], dflc
   }
 }
 
-// Rows i < nrows of P_m into the right operand slices and their exponents et[i] (rows >= n are
-// zero); one warp per row, 8 rows per CTA (nrows is a multiple of 64, so the grid holds no partial
-// CTA and a CTA's rows share one 64-row block).  kh (a multiple of 8 in [L, 48]) is the K half-width
-// of the product's tile windows: a tile row holds 64 + 2 kh columns.  The CTA's rows are staged in shared
-// memory and leave as 16-byte pieces of the MN-major band (8 consecutive operator rows of one
-// window column).  cf, rot: the step's gauge tables (row stride irrelevant: row k).  Also clears
-// the row-maximum keys kzero[0 .. nzero) that the step's product fills.
-__global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
-    k_band_rows(const double2* __restrict__ cf, const double2* __restrict__ rot, int n, int nrows, int L,
-                BandCoef coef, double ph_re, double ph_im, size_t rstride, __nv_bfloat16* __restrict__ right,
-                int* __restrict__ et, unsigned int* __restrict__ kzero, int nzero, int kh) {
-  __shared__ __align__(16) __nv_bfloat16 stage[OZ_S][3][BAND_KW][BAND_ROWS_PER_CTA];
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nzero; q += gridDim.x * blockDim.x) kzero[q] = 0u;
-  const int lane = threadIdx.x & 31, wr8 = threadIdx.x >> 5;
-  const int i = blockIdx.x * BAND_ROWS_PER_CTA + wr8;
+// What one step's band formation needs: the step's gauge tables (row k of cf, rot), the band
+// slices and row exponents it writes, and the tile geometry (kh, a multiple of 8 in [L, 48], is
+// the K half-width of the product's tile windows: a tile row holds 64 + 2 kh columns).
+struct BandRows {
+  const double2* cf;
+  const double2* rot;
+  __nv_bfloat16* right;
+  int* et;
+  size_t rstride;
+  double ph_re, ph_im;
+  int n, nrows, L, kh;
+};
+
+typedef __nv_bfloat16 BandStage[3][BAND_KW][BAND_ROWS_PER_CTA];  // one slice's staged 8-row block
+
+// One warp forms row i < nrows of P_m (zero for i >= n) into column r8 of the staged 8-row block
+// of the right operand slices, and its exponent et[i].
+__device__ __forceinline__ void band_form_row(const BandRows& a, const BandCoef& coef, int i, int r8,
+                                              BandStage* stage, int lane) {
+  const int n = a.n, L = a.L, kh = a.kh;
+  const double2* __restrict__ cf = a.cf;
+  const double2* __restrict__ rot = a.rot;
   const bool live = i < n;
   const int w0 = i - BAND_WIN / 2;  // row of window position 0
   const dfl zd = {0.f, 0.f};
@@ -171,7 +178,7 @@ __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
   double vr[BAND_LANE_ROWS], vi[BAND_LANE_ROWS];
   unsigned long long key = 0;
   const double2 ri = live ? rot[i] : make_double2(1.0, 0.0);
-  const double wr = ph_re * ri.x - ph_im * ri.y, wi = ph_re * ri.y + ph_im * ri.x;  // e^{-i beta h} e^{i theta_i}
+  const double wr = a.ph_re * ri.x - a.ph_im * ri.y, wi = a.ph_re * ri.y + a.ph_im * ri.x;  // e^{-i beta h} e^{i theta_i}
 #pragma unroll
   for (int q = 0; q < BAND_LANE_ROWS; ++q) {
     const int k = w0 + BAND_LANE_ROWS * lane + q;
@@ -209,9 +216,9 @@ __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
     const int c = r + pos - BAND_WIN / 2 + kh;
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) {
-      stage[s][0][c][wr8] = __hneg(si[s]);
-      stage[s][1][c][wr8] = sr[s];
-      stage[s][2][c][wr8] = si[s];
+      stage[s][0][c][r8] = __hneg(si[s]);
+      stage[s][1][c][r8] = sr[s];
+      stage[s][2][c][r8] = si[s];
     }
   }
   // the row's other columns of the tile window: [0, r) and [r + p1 - p0, kw)
@@ -223,20 +230,37 @@ __global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA)
     const int c = z < r ? z : z + bw;
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) {
-      stage[s][0][c][wr8] = zero;
-      stage[s][1][c][wr8] = zero;
-      stage[s][2][c][wr8] = zero;
+      stage[s][0][c][r8] = zero;
+      stage[s][1][c][r8] = zero;
+      stage[s][2][c][r8] = zero;
     }
   }
-  if (lane == 0) et[i] = E;
-  __syncthreads();
-  // column c of part (-Im, Re, Im) of block b: rows r0 .. r0 + 7 at [(b kw + c) 192 + 64 part + r0]
-  const int i0 = blockIdx.x * BAND_ROWS_PER_CTA, b = i0 / OZ_BN, r0 = i0 % OZ_BN;
-  for (int t = threadIdx.x; t < OZ_S * 3 * kw; t += blockDim.x) {
-    const int c = t % kw, sp = t / kw, part = sp % 3, s = sp / 3;
-    *reinterpret_cast<uint4*>(right + s * rstride + ((size_t)b * kw + c) * (3 * OZ_BN) + part * OZ_BN + r0) =
+  if (lane == 0) a.et[i] = E;
+}
+
+// The staged block of rows 8 b8 .. 8 b8 + 7 to the MN-major band: column c of part (-Im, Re, Im)
+// of 64-row block b, rows r0 .. r0 + 7, at [(b kw + c) 192 + 64 part + r0] as one 16-byte piece;
+// thread t of nt.
+__device__ __forceinline__ void band_store_block(const BandRows& a, int b8, const BandStage* stage, int t, int nt) {
+  const int kw = OZ_BN + 2 * a.kh;
+  const int i0 = b8 * BAND_ROWS_PER_CTA, b = i0 / OZ_BN, r0 = i0 % OZ_BN;
+  for (int x = t; x < OZ_S * 3 * kw; x += nt) {
+    const int c = x % kw, sp = x / kw, part = sp % 3, s = sp / 3;
+    *reinterpret_cast<uint4*>(a.right + s * a.rstride + ((size_t)b * kw + c) * (3 * OZ_BN) + part * OZ_BN + r0) =
         *reinterpret_cast<const uint4*>(&stage[s][part][c][0]);
   }
+}
+
+// Rows i < nrows of P_m (the first step of a call; later steps' bands are formed inside the
+// previous step's product, k_oz_band): one warp per row, 8 rows per CTA (nrows is a multiple of
+// 64, so the grid holds no partial CTA and a CTA's rows share one 64-row block), staged in shared
+// memory and written as 16-byte pieces of the MN-major band.
+__global__ void __launch_bounds__(32 * BAND_ROWS_PER_CTA) k_band_rows(const BandRows a, const BandCoef coef) {
+  __shared__ __align__(16) BandStage stage[OZ_S];
+  const int lane = threadIdx.x & 31, r8 = threadIdx.x >> 5;
+  band_form_row(a, coef, blockIdx.x * BAND_ROWS_PER_CTA + r8, r8, stage, lane);
+  __syncthreads();
+  band_store_block(a, blockIdx.x, stage, threadIdx.x, blockDim.x);
 }
 
 // float 2^e for |e| <= 126 (clamped)
@@ -347,23 +371,27 @@ __global__ void __launch_bounds__(256)
 // After the product of a step: the scales of its slices of X_m (es_next: the predicted one of
 // each state, or, for a state the product flagged because an element outgrew that scale, the exact
 // one of the row maximum the product collected, knew) and the flagged states' slices cut again at
-// that scale; clears the flags.  A flagged state's entries come back from its slices at the
+// that scale; clears the flags, and X_{m-1}'s row maxima (kprev) for the next product to fill.  A flagged state's entries come back from its slices at the
 // predicted scale (the six digits' sum is exact in FP64), or, for an entry marked by a NaN leading
 // digit, from the double-float value the product stored for it.  One warp per state of the padded
 // block (256 threads, ncp / 8 CTAs).
 __global__ void __launch_bounds__(256)
     k_band_fixup(const float4* __restrict__ x, int n, int ld, int nc, int npl, int ncp, size_t astride,
-                 __nv_bfloat16* __restrict__ lnext, int* __restrict__ es_next, const unsigned int* __restrict__ kprev,
+                 __nv_bfloat16* __restrict__ lnext, int* __restrict__ es_next, unsigned int* __restrict__ kprev,
                  const unsigned int* __restrict__ knew, int* __restrict__ ovf) {
   const int lane = threadIdx.x & 31;
   const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (j >= ncp) return;  // whole warp (no barrier below)
   const bool redo = j < nc && ovf[j] != 0;
   const int E = redo ? band_key_exp(knew[j]) : (j < nc ? band_key_exp(kprev[j]) + BAND_MARGIN : 0);
-  if (lane == 0) es_next[j] = E;
+  const double sp = ldexp(1.0, j < nc ? band_key_exp(kprev[j]) + BAND_MARGIN : 0);  // the scale the product cut at
+  __syncwarp();
+  if (lane == 0) {
+    es_next[j] = E;
+    kprev[j] = 0u;
+  }
   if (!redo) return;
   const float so = pow2f(-E);
-  const double sp = ldexp(1.0, band_key_exp(kprev[j]) + BAND_MARGIN);  // the scale the product cut at
   for (int k = lane; k < n; k += 32) {
     float4 v;
     __nv_bfloat16 dr[OZ_S], di[OZ_S];
@@ -436,8 +464,18 @@ struct BandEpi {
 // tile into double-float registers, release the tensor memory and write the tile's slices for the
 // next step (and, at the last step, its double-float states) while the next tile's MMAs run.  Every wait is bounded; a wait that gives up records FQ_BIT_TIMEOUT, drains this CTA's own
 // copies and MMAs, frees tensor memory and returns.
-__global__ void __launch_bounds__(OZ_THREADS, 1)
-    k_oz_band(const __grid_constant__ OzMaps maps, int tiles_j, int tiles_i, int npl, int kh, BandEpi e) {
+constexpr int BAND_FORM_WARPS = 2;                             // warps 18, 19 form the next step's band
+constexpr int BAND_THREADS = OZ_THREADS + 32 * BAND_FORM_WARPS;  // 20 warps x 96 registers: 5 per SM sub-partition
+// Forming the next band inside the product pays once the product outlasts it: with two warps per
+// SM the formation takes about a third of a 10001-state product at dim 10001, and both scale with
+// the band's rows, so the rule is a number of states.
+constexpr int BAND_FORM_MIN_STATES = 4096;
+constexpr size_t BAND_SMEM = OzCfg::SMEM + OZ_S * sizeof(BandStage);
+static_assert(BAND_SMEM <= 232448, "stages and the band staging fit the 227 KB of shared memory a CTA may use");
+
+__global__ void __launch_bounds__(BAND_THREADS, 1)
+    k_oz_band(const __grid_constant__ OzMaps maps, int tiles_j, int tiles_i, int npl, int kh, BandEpi e,
+              const __grid_constant__ BandRows next, const __grid_constant__ BandCoef coef, int form_next) {
   using Cfg = OzCfg;
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -447,6 +485,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * Cfg::STAGE_BYTES);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 3);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  BandStage* rstage = reinterpret_cast<BandStage*>(gbase + STAGES * Cfg::STAGE_BYTES + 256);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
   const uint32_t tfull = smem_u32(bars + 2 * STAGES), tempty = smem_u32(bars + 2 * STAGES + 1);
   const uint32_t done = smem_u32(bars + 2 * STAGES + 2);
@@ -566,6 +605,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mma_commit(done);
       mbar_wait(done, 0);
     }
+  } else if (warp >= OZ_THREADS / 32) {  // ---------------- the next step's band, in 8-row blocks
+    const int fw = warp - OZ_THREADS / 32, ft = threadIdx.x - OZ_THREADS;
+    if (form_next)
+      for (int b8 = blockIdx.x; b8 < next.nrows / BAND_ROWS_PER_CTA; b8 += gridDim.x) {
+        for (int r8 = fw; r8 < BAND_ROWS_PER_CTA; r8 += BAND_FORM_WARPS)
+          band_form_row(next, coef, b8 * BAND_ROWS_PER_CTA + r8, r8, rstage, lane);
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * BAND_FORM_WARPS) : "memory");  // the block is staged
+        band_store_block(next, b8, rstage, ft, 32 * BAND_FORM_WARPS);
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * BAND_FORM_WARPS) : "memory");  // and written: reuse it
+      }
   } else {  // ---------------- drain and epilogue warps 2-17
     const int quarter = warp & 3, part = (warp - 2) >> 2;
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(part * 16);
@@ -712,8 +761,8 @@ __global__ void k_band_store_t(const float4* __restrict__ x, double2* __restrict
 struct BandWs {
   double2* cf;
   double2* rot;
-  __nv_bfloat16* right;
-  int* et;
+  __nv_bfloat16* right[2];  // the band a product reads and the one it forms for the next step
+  int* et[2];
   __nv_bfloat16* left[2];  // slices of the states a product reads (alternating per step)
   int* es[2];
   int* ovf;
@@ -745,8 +794,8 @@ size_t band_layout(const fq_plan* p, int nc, int nsteps, void* base, BandWs* out
   };
   w.cf = (double2*)take(sizeof(double2) * (size_t)nsteps * w.nrows);
   w.rot = (double2*)take(sizeof(double2) * (size_t)nsteps * w.nrows);
-  w.right = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.rstride);
-  w.et = (int*)take(sizeof(int) * w.nrows);
+  for (int q = 0; q < 2; ++q) w.right[q] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.rstride);
+  for (int q = 0; q < 2; ++q) w.et[q] = (int*)take(sizeof(int) * w.nrows);
   for (int q = 0; q < 2; ++q) w.left[q] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * OZ_S * w.astride);
   for (int q = 0; q < 2; ++q) w.es[q] = (int*)take(sizeof(int) * w.ncp);
   w.ovf = (int*)take(sizeof(int) * w.ncp);
@@ -775,26 +824,28 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
   }
   BandWs w;
   band_layout(p, nc, nsteps, ws, &w);
-  OzMaps maps[2];  // per left slice buffer
+  OzMaps maps[2];  // per step parity: the state slices and the band a product reads
   for (int b = 0; b < 2; ++b)
     for (int q = 0; q < OZ_S; ++q) {
       // MN-major: 64-element (128-byte) box rows, 16 K rows per box
       if ((st = make_map(&maps[b].a[q], w.left[b] + q * w.astride, 2 * w.npl, w.ncp, OZ_BKE, 64)) != FQ_OK) return st;
-      if ((st = make_map(&maps[b].r[q], w.right + q * w.rstride, (w.nrows / OZ_BN) * w.kw, 3 * OZ_BN, OZ_BKE, 64)) !=
+      if ((st = make_map(&maps[b].r[q], w.right[b] + q * w.rstride, (w.nrows / OZ_BN) * w.kw, 3 * OZ_BN, OZ_BKE, 64)) !=
           FQ_OK)
         return st;
     }
   static std::atomic<unsigned> attr_set{0};
   if (fq_first_on_device(attr_set)) {
-    cudaError_t e = cudaFuncSetAttribute(k_oz_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OzCfg::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_oz_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BAND_SMEM);
     if (e != cudaSuccess) return fq_cuda_fail(e, "band kernel shared-memory attribute");
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
   if (sms < 1) sms = 152;
   // component rows >= n of the second slice buffer stay zero (the epilogue writes rows < n only;
-  // the first step's slicing pass fills the first buffer whole); no state is flagged yet
+  // the first step's slicing pass fills the first buffer whole); no state is flagged yet, and the
+  // row maxima the first product collects start at zero (the fixup pass clears them after that)
   cudaError_t ce = cudaMemsetAsync(w.ovf, 0, sizeof(int) * w.ncp, s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(w.kmax[0], 0, sizeof(unsigned int) * w.ncp, s);
   if (nsteps > 1 && w.npl > n)
     for (int q = 0; q < OZ_S && ce == cudaSuccess; ++q)
       for (int part = 0; part < 2 && ce == cudaSuccess; ++part)
@@ -815,7 +866,6 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
   const int tiles_i = (n + OZ_BN - 1) / OZ_BN, tiles_j = w.ncp / BM;
   const int ntiles = tiles_i * tiles_j;
   BandEpi e{};
-  e.et = w.et;
   e.ovf = w.ovf;
   e.astride = w.astride;
   e.n = n;
@@ -831,14 +881,30 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
     k_band_slice<<<dim3(w.ncp / 64, w.npl / 16), 256, 0, s>>>(w.x[0], n, w.npl, nc, w.npl, w.ncp, w.astride,
                                                               w.left[0], w.es[0], w.kmax[1]);
   }
+  // step m's band (its gauge tables, its buffer of the pair)
+  auto rows_of = [&](int m) {
+    BandRows r{};
+    r.cf = w.cf + (size_t)m * w.nrows;
+    r.rot = w.rot + (size_t)m * w.nrows;
+    r.right = w.right[m & 1];
+    r.et = w.et[m & 1];
+    r.rstride = w.rstride;
+    r.ph_re = p->phase_re;
+    r.ph_im = p->phase_im;
+    r.n = n;
+    r.nrows = w.nrows;
+    r.L = L;
+    r.kh = w.kh;
+    return r;
+  };
+  const bool fold = w.ncp >= BAND_FORM_MIN_STATES;  // the next band formed inside each product
   int cur = 0;
   for (int m = 0; m < nsteps; ++m) {
     const int b = m & 1, nb = b ^ 1;
-    // P_m, clearing the row maxima product m will collect (product m-1's stay for the prediction)
-    k_band_rows<<<w.nrows / BAND_ROWS_PER_CTA, 32 * BAND_ROWS_PER_CTA, 0, s>>>(
-        w.cf + (size_t)m * w.nrows, w.rot + (size_t)m * w.nrows, n, w.nrows, L, coef, p->phase_re, p->phase_im,
-        w.rstride, w.right, w.et, w.kmax[b], w.ncp, w.kh);
-    // X_m = P_m X_{m-1}, and X_m's slices for the next step at the scales X_{m-1}'s maxima predict
+    if (m == 0 || !fold) k_band_rows<<<w.nrows / BAND_ROWS_PER_CTA, 32 * BAND_ROWS_PER_CTA, 0, s>>>(rows_of(m), coef);
+    // X_m = P_m X_{m-1}, X_m's slices for the next step at the scales X_{m-1}'s maxima predict,
+    // and P_{m+1} formed alongside when folded (into the other band buffer, which product m-1 read)
+    e.et = w.et[b];
     e.out = w.x[cur ^ 1];
     e.kmax = w.kmax[b];
     e.es = w.es[b];
@@ -846,7 +912,9 @@ fq_status fq_band_propagate(fq_plan* p, const double* x0, double* x, int nc, int
     e.kprev = w.kmax[nb];
     e.write_states = m == nsteps - 1;
     fq_ktimer_start(p, s, "k_oz_band");
-    k_oz_band<<<std::min(ntiles, sms), OZ_THREADS, OzCfg::SMEM, s>>>(maps[b], tiles_j, tiles_i, w.npl, w.kh, e);
+    const int form = fold && m + 1 < nsteps;
+    k_oz_band<<<std::min(ntiles, sms), BAND_THREADS, BAND_SMEM, s>>>(maps[b], tiles_j, tiles_i, w.npl, w.kh, e,
+                                                                     rows_of(form ? m + 1 : m), coef, form);
     fq_ktimer_stop(p, s);
     // the slice scales of X_m, and the states that outgrew their predicted scale cut again
     k_band_fixup<<<w.ncp / 8, 256, 0, s>>>(w.x[cur ^ 1], n, w.npl, nc, w.npl, w.ncp, w.astride, w.left[nb],

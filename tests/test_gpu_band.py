@@ -118,6 +118,25 @@ def test_band_refocusing_states_take_the_rescaling_path(fq):
     assert err <= 1e-10
 
 
+def test_band_next_band_formed_inside_the_product(fq):
+    """4096 states (the product then forms the next step's band in its own warps): the dim-701
+    dimer (L = 32, 11 operator blocks, 88 blocks of 8 band rows spread over the persistent CTAs),
+    random unit states through 3 steps, every state against the oracle."""
+    d = fi.config_dimer(nb=700, steps=200)
+    d.drive = fi.Drive(0.2, 1.5, 3.0, 0.4)
+    plan = band_plan(fq, d)
+    n, nc = d.n, 4096
+    x0 = np.exp(2j * np.pi * fi.uniform(2701, n * nc)).reshape(n, nc) * (1.0 + fi.uniform(2702, n * nc).reshape(n, nc))
+    x0 /= np.linalg.norm(x0, axis=0)
+    X = to_np(plan.propagate(cuda_c128(x0.T), 1, 4))
+    assert plan.check_status() == fq.FQ_OK
+    refp = o.plan_for_drive_tridiag(d.h0_diag, d.h0_off, d.h1_diag, d.drive, d.steps)
+    ref = o.propagate_tridiag(d.h0_diag, d.h0_off, d.h1_diag, refp, x0, 1, 4).T
+    err = np.max(np.abs(X - ref))
+    print(f"band 4096 states, next band in the product: max err {err:.2e}")
+    assert err <= 1e-10
+
+
 def test_band_many_state_tiles_and_column_split(fq):
     """dim 701 (11 operator blocks), all 701 states (6 state tiles, ragged): U_T equals the column
     blocks of a 3-rank split bit for bit, and matches the oracle."""
