@@ -102,8 +102,9 @@ def run_ncu_case(case):
     split:    dense GOE N = 4096 (seeds 3, 4), BF16X3 tensor-core terms of step 0 on the identity;
     tile:     2048 states through step 0 on the FP64 tiled kernel (0.65 GB of states);
     dfl:      2048 states through step 0 on the double-float tiled kernel (FQ_DF32, 0.65 GB);
-    band:     2048 states through steps 0..1 on the band kernel (FQ_OZAKI: 0.66 GB of double-float
-              states, 0.5 GB of slices);
+    band:     4096 states through steps 0..2 on the band kernel (FQ_OZAKI, in place: 0.66 GB of
+              states, 1.3 GB of double-float states and 2 GB of slices in the workspace; at 4096
+              states each product also forms the next step's band, as at the full 10001)
     adjoint:  the BF16X3 gradient at N = 1024 (seeds 6-9) over the first 16 of its 256 steps;
     ozaki-grad: the same in FP64 emulation (FQ_OZAKI);
     ozaki:    dense GOE N = 2048 (seeds 3, 4; A = 2, omega = 2, M = 64), FQ_OZAKI terms of step 0 on
@@ -158,11 +159,11 @@ def run_ncu_case(case):
     precision = {"tile": fq.FQ_FP64, "dfl": fq.FQ_DF32, "band": fq.FQ_OZAKI}.get(case, fq.FQ_FP32)
     plan = fq.Plan.tridiag(d.h0_diag, d.h0_off, d.h1_diag, omega=d.drive.omega, f_ac=d.drive.f_ac,
                            steps=d.steps, precision=precision, kernel=kernel)
-    nc, m_end = {"resident": (152, 20), "band": (2048, 2)}.get(case, (2048, 1))
+    nc, m_end = {"resident": (152, 20), "band": (4096, 3)}.get(case, (2048, 1))
     x0 = torch.zeros((nc, n), dtype=torch.complex128, device="cuda")
     x0[torch.arange(nc), torch.arange(nc) * (n // nc)] = 1.0
     ws = fq.workspace(plan.workspace_size(nc))
-    x = torch.empty_like(x0)
+    x = x0 if case == "band" else torch.empty_like(x0)  # (in place: the band case's states are larger)
     for _ in range(2):
         fq.floquet_propagate(plan.handle, x0, x, nc, 0, m_end, ws)
     torch.cuda.synchronize()
@@ -371,10 +372,10 @@ DIMER_PATHS = {
 
 
 # DRAM bytes of one k_oz_band launch (one step's banded product) from the ncu capture of
-# `python bench.py --ncu-case band` (2048 states; profiles/k_oz_band_dimer10001.md), scaled to a
-# launch by states: the state slices read, the new states and their slices written grow with the
-# states.
-BAND_NCU = {"read": 621.7e6, "write": 792.0e6, "states": 2048}
+# `python bench.py --ncu-case band` (4096 states; profiles/k_oz_band_dimer10001.md), scaled to a
+# launch by states: the state slices read and the next step's slices written grow with the states
+# (a step that is not the last: no double-float states written).
+BAND_NCU = {"read": 1131.5e6, "write": 1007.0e6, "states": 4096}
 
 
 def band_window(L):
@@ -549,7 +550,7 @@ def run_ours(args):
             roofline["traffic"] = (BAND_NCU["read"] + BAND_NCU["write"]) * (n / (world if sharded else 1)) / \
                 BAND_NCU["states"]
             roofline["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of k_oz_band from one ncu capture "
-                                        "of --ncu-case band (2048 states), scaled to a launch by states")
+                                        "of --ncu-case band (4096 states), scaled to a launch by states")
     roofline["launch_seconds"] = kavg
     roofline["launch_seconds_note"] = (
         f"mean of {klaunches} CUDA-event-timed launches of {kname} on its stream over the timed region "
