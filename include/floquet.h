@@ -144,7 +144,9 @@ typedef struct fq_problem {
                                floquet_autotune picks one */
   int32_t magnus_order;     /* 4 (default, also 0) or 6: Eq. 14 in full with its alphas taken as
                                3-point Gauss-Legendre moments (nine commutators of H0, H1 computed
-                               once on the device); 6 needs FQ_DENSE and FQ_DRIVE_COS */
+                               once: on the device for FQ_DENSE, on the host as bands for
+                               FQ_TRIDIAG); 6 needs FQ_DRIVE_COS, and a tridiagonal plan FQ_FP64
+                               (its Omega~ is heptadiagonal: a streaming FP64 kernel applies it) */
   int32_t cheb_terms;       /* > 0: a fixed number L of Chebyshev products per step (the paper's
                                timing runs use L = 50, Table 1), overriding cheb_tol; at most
                                1024 and at least the R-dependent minimum (L > R); 0: from cheb_tol */

@@ -36,12 +36,15 @@ class Plan:
 
     @classmethod
     def tridiag(cls, h0_diag, h0_off, h1_diag, *, omega, f_ac, steps, f_dc=0.0, phi0=0.0, period=None,
-                precision=B.FQ_FP32, kernel=B.FQ_KERNEL_AUTO, cheb_tol=0.0, e_min=0.0, e_max=0.0):
+                precision=None, kernel=B.FQ_KERNEL_AUTO, cheb_tol=0.0, e_min=0.0, e_max=0.0, magnus_order=0):
+        """precision defaults to FQ_FP32 (FQ_FP64 for magnus_order 6, the only one it runs in)."""
         n = h0_diag.shape[0]
         T = period if period is not None else 2.0 * math.pi / omega
+        if precision is None:
+            precision = B.FQ_FP64 if magnus_order == 6 else B.FQ_FP32
         prob, keep = B.make_problem(n, B.FQ_TRIDIAG, h0_diag, h1_diag, T, steps, h0_off=h0_off, f_dc=f_dc,
                                     f_ac=f_ac, omega=omega, phi0=phi0, precision=precision, kernel=kernel,
-                                    cheb_tol=cheb_tol, e_min=e_min, e_max=e_max)
+                                    cheb_tol=cheb_tol, e_min=e_min, e_max=e_max, magnus_order=magnus_order)
         return cls(prob, keep)
 
     @classmethod

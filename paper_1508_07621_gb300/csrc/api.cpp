@@ -62,6 +62,12 @@ size_t layout(const fq_plan* p, int nc, int nsteps, void* ws, StateWs* out) {
     w.coeff = c.take<char>(3 * ld * (size_t)nsteps * es);
     for (int b = 0; b < 3; ++b)
       for (int q = 0; q < 2; ++q) w.buf[b][q] = c.take<char>((size_t)nc * ld * es);
+  } else if (p->path == PATH_TRI6) {
+    const size_t ld = tri_ld(n);
+    w.S = c.take<double>(7 * ld);  // Omega~_m's diagonals, re
+    w.A = c.take<double>(7 * ld);  // and im
+    for (int b = 0; b < 3; ++b)
+      for (int q = 0; q < 2; ++q) w.buf[b][q] = c.take<double>((size_t)nc * ld);
   } else if (p->path == PATH_TRI_RESIDENT) {
     w.coeff = c.take<char>(fq_resident_coeff_bytes(n, nsteps));
   } else if (p->path == PATH_TRI_TILE) {
@@ -111,6 +117,11 @@ int run_chain(fq_plan* p, StateWs& w, int x, int nc, int m_begin, int m_end, cud
       fq_launch_omega6_f64(p, c, w.S, w.A, s);
     } else if (p->path == PATH_DENSE_F64) {
       fq_launch_omega_dense_f64(p->d_h0, p->d_h1, p->d_k, n, p->sa[m], p->sb[m], p->sc[m], p->sbeta, w.S, w.A, s);
+    } else if (p->path == PATH_TRI6) {
+      double c[FQ_M6_TERMS];
+      const double inv = 1.0 / (p->h * p->delta_e);
+      for (int q = 0; q < FQ_M6_TERMS; ++q) c[q] = p->coef6[(size_t)m * FQ_M6_TERMS + q] * inv;
+      fq_launch_omega_band6(p, c, w.S, w.A, ld, s);
     }
     // buffers: cur = psi_l, prv = psi_{l-1}, acc; x holds psi_0
     int cur = x, nxt = (x + 1) % 3, acc = (x + 2) % 3;
@@ -126,6 +137,9 @@ int run_chain(fq_plan* p, StateWs& w, int x, int nc, int m_begin, int m_end, cud
       if (p->path == PATH_DENSE_F64) {
         fq_launch_term_dense_f64(w.S, w.A, n, blk<double>(w.buf[cur]), blk<double>(w.buf[pq]),
                                  blk<double>(w.buf[acc]), blk<double>(w.buf[out]), nc, t, s);
+      } else if (p->path == PATH_TRI6) {
+        fq_launch_term_band6_f64(w.S, w.A, n, blk<double>(w.buf[cur]), blk<double>(w.buf[pq]),
+                                 blk<double>(w.buf[acc]), blk<double>(w.buf[out]), nc, ld, t, s);
       } else {
         const size_t off = (size_t)(m - m_begin) * ld;
         if (sizeof(T) == 8)
@@ -263,7 +277,13 @@ fq_status plan_create(fq_plan** out, const fq_problem* prob) {
   fq_status st = fq_host_plan(prob, p, prob && prob->format == FQ_DENSE);
   if (st != FQ_OK) return st;
   const int n = p->n, M = p->steps;
-  if (p->format == FQ_TRIDIAG) {
+  if (p->format == FQ_TRIDIAG && p->order == 6) {
+    if (prob->kernel != FQ_KERNEL_AUTO && prob->kernel != FQ_KERNEL_STREAM) {
+      fq_set_error("6th-order tridiagonal plans run on the streaming FP64 kernel");
+      return FQ_EUNSUPPORTED;
+    }
+    p->path = PATH_TRI6;
+  } else if (p->format == FQ_TRIDIAG) {
     const bool res_ok = p->precision == FQ_FP32 && fq_resident_supported(n, p->L);
     const bool tile_ok = fq_tile_supported(p->L) != 0;
     if (prob->kernel == FQ_KERNEL_RESIDENT && !res_ok) {
@@ -389,6 +409,13 @@ fq_status plan_create(fq_plan** out, const fq_problem* prob) {
       }
     }
   } else {
+    if (p->order == 6) {  // the 6th-order basis as bands, computed on the host with the bounds
+      if ((e = cudaMalloc(&p->d_cm, p->band6.size() * sizeof(double))) != cudaSuccess)
+        return fail(e, "cudaMalloc basis bands");
+      if ((e = cudaMemcpy(p->d_cm, p->band6.data(), p->band6.size() * sizeof(double), cudaMemcpyHostToDevice)) !=
+          cudaSuccess)
+        return fail(e, "upload basis bands");
+    }
     std::vector<double> kl(std::max(1, n - 1), 0.0);
     for (int i = 0; i + 1 < n; ++i) kl[i] = prob->h0_off[i] * (prob->h1[i] - prob->h1[i + 1]);
     if ((e = cudaMalloc(&p->d_h0o, std::max(1, n - 1) * sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc H0 off");

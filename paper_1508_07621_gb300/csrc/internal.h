@@ -27,6 +27,7 @@ enum fq_path : int {
   PATH_TRI_TILE = 5,      // one launch per step, each CTA runs a step's L products on a state segment
   PATH_TRI_BAND = 7,      // FQ_OZAKI tridiagonal: the step's band polynomial on tcgen05 in FP64 emulation
   PATH_DENSE_OZAKI = 6,   // tcgen05 FP64 emulation (fixed-point BF16 slices, exact FP32 sums) per term
+  PATH_TRI6 = 8,          // 6th-order tridiagonal: heptadiagonal Omega~ per step, streaming FP64 term kernel
 };
 
 // Measurement aid (floquet_kernel_timing): CUDA event pairs recorded on the caller's stream around
@@ -61,6 +62,9 @@ struct fq_plan {
   // the imaginary factor of the antisymmetric ones
   int order = 4;
   std::vector<double> coef6;   // [M][11]
+  // tridiagonal plans of order 6: the 11 basis elements as bands of half-width 3, [11][7][n] with
+  // element (i, i + d) at [q][d + 3][i] (zero outside the matrix); on the device in d_cm
+  std::vector<double> band6;
   double* d_cm = nullptr;      // K0 .. KK1: 8 matrices n*n after d_k (= K)
   int tile_n = 128;          // split path: output tile width of the tensor-core kernel (autotuned)
   int device = 0;
@@ -115,6 +119,8 @@ int fq_cheb_order(double R, double tol);  // needs 0 <= R <= FQ_R_MAX
 // step is too long for its spectral width and more steps per period are the remedy
 constexpr double FQ_R_MAX = 16384.0;
 void fq_tridiag_extremes(const double* diag, const double* off, int n, double* lo, double* hi);
+// the 6th-order basis of a tridiagonal H0 (diag d0, off-diagonal e0) and diagonal H1 (d1) as bands
+void fq_tridiag_band6(const double* d0, const double* e0, const double* d1, int n, std::vector<double>& out);
 // y = A x for the operator whose extreme eigenvalues are wanted (host vectors of length n)
 using fq_matvec = std::function<void(const double* x, double* y)>;
 void fq_lanczos_extremes(const fq_matvec& mv, int n, int ksteps, uint64_t seed, double* lo, double* hi);
@@ -174,6 +180,13 @@ void fq_launch_tri_coeffs_f64(const fq_plan* p, int m_begin, int nsteps, double 
                               double* ei, cudaStream_t s);
 void fq_launch_tri_coeffs_f32(const fq_plan* p, int m_begin, int nsteps, double scale, float* d, float* er,
                               float* ei, cudaStream_t s);
+// 6th-order tridiagonal plans: Omega~_m's 7 diagonals (re then im, [7][ld] each, element (i, i + d)
+// at [d + 3][i]) from the plan's bands and the step's scaled coefficients c (with -sbeta on the
+// diagonal), and one streaming FP64 Chebyshev term with them
+void fq_launch_omega_band6(const fq_plan* p, const double* c, double* ore, double* oim, int ld, cudaStream_t s);
+void fq_launch_term_band6_f64(const double* ore, const double* oim, int n, fq_blk<double> cur, fq_blk<double> prev,
+                              fq_blk<double> acc, fq_blk<double> out, int nc, int ld, const fq_term& t,
+                              cudaStream_t s);
 void fq_launch_term_tri_f64(const double* d, const double* er, const double* ei, int n, fq_blk<double> cur,
                             fq_blk<double> prev, fq_blk<double> acc, fq_blk<double> out, int nc, int ld,
                             const fq_term& t, cudaStream_t s);

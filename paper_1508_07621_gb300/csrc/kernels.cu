@@ -332,6 +332,112 @@ k_term_tri(const T* __restrict__ d, const T* __restrict__ er, const T* __restric
   }
 }
 
+// ------------------------------------------------------------------ 6th-order tridiagonal plans
+// Omega~_m = sum_q c_q B_q - sbeta 1 over the 11 basis bands (Eq. 14 in full, reading R12): the
+// symmetric elements give the real part S, the antisymmetric ones (whose coefficient is the
+// imaginary factor) the imaginary part A, so Omega~ = S + i A is Hermitian.  Diagonal d + 3 of
+// the output holds (i, i + d); rows i >= n are zero.
+struct Band6Args {
+  const double* band;  // [11][7][n]
+  double c[FQ_M6_TERMS];
+  double sbeta;
+  int n, ld;
+};
+
+__global__ void k_omega_band6(Band6Args a, double* __restrict__ ore, double* __restrict__ oim) {
+  const int total = 7 * a.ld;
+  const size_t el = (size_t)7 * a.n;  // stride between basis elements
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const int d = q / a.ld, i = q % a.ld;
+    double sr = 0.0, si = 0.0;
+    if (i < a.n) {
+      const double* b = a.band + (size_t)d * a.n + i;
+      sr = a.c[0] * b[0];
+      sr = fma(a.c[1], b[el], sr);
+      sr = fma(a.c[3], b[3 * el], sr);
+      sr = fma(a.c[4], b[4 * el], sr);
+      sr = fma(a.c[9], b[9 * el], sr);
+      sr = fma(a.c[10], b[10 * el], sr);
+      si = a.c[2] * b[2 * el];
+      si = fma(a.c[5], b[5 * el], si);
+      si = fma(a.c[6], b[6 * el], si);
+      si = fma(a.c[7], b[7 * el], si);
+      si = fma(a.c[8], b[8 * el], si);
+      if (d == 3) sr -= a.sbeta;
+    }
+    ore[q] = sr;
+    oim[q] = si;
+  }
+}
+
+// One Chebyshev term with a heptadiagonal Omega~ (Eq. 10), FP64, streaming as k_term_tri: four
+// entries of one state per thread, y_i = sum_{d = -3..3} Omega~[i][i + d] x_{i + d}.
+__global__ void __launch_bounds__(256)
+k_term_band6(const double* __restrict__ ore, const double* __restrict__ oim, int ld, const double* __restrict__ cur_re,
+             const double* __restrict__ cur_im, const double* prev_re, const double* prev_im, double* acc_re,
+             double* acc_im, double* out_re, double* out_im, fq_term t) {
+  const int j = blockIdx.y;
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (i0 >= ld) return;
+  const size_t row = (size_t)j * ld;
+  double xr[10], xi[10];  // x_{i0 - 3} .. x_{i0 + 6}
+#pragma unroll
+  for (int u = 0; u < 10; ++u) {
+    const int k = i0 - 3 + u;
+    const bool in = k >= 0 && k < ld;
+    xr[u] = in ? cur_re[row + k] : 0.0;
+    xi[u] = in ? cur_im[row + k] : 0.0;
+  }
+  double pr[4], pi[4], ar[4], ai[4];
+  if (!t.first) {
+    Quad<double>::load(prev_re + row + i0, pr);
+    Quad<double>::load(prev_im + row + i0, pi);
+    Quad<double>::load(acc_re + row + i0, ar);
+    Quad<double>::load(acc_im + row + i0, ai);
+  }
+  double o_r[4], o_i[4], a_r[4], a_i[4];
+  bool bad = false;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double yr = 0.0, yi = 0.0;
+#pragma unroll
+    for (int d = 0; d < 7; ++d) {
+      const double wr = ore[(size_t)d * ld + i0 + q], wi = oim[(size_t)d * ld + i0 + q];
+      yr = fma(wr, xr[q + d], fma(-wi, xi[q + d], yr));
+      yi = fma(wr, xi[q + d], fma(wi, xr[q + d], yi));
+    }
+    double nr, ni, sr, si;
+    if (t.first) {
+      nr = yi;
+      ni = -yr;
+      sr = t.coef0 * xr[q + 3] + t.coef * nr;
+      si = t.coef0 * xi[q + 3] + t.coef * ni;
+    } else {
+      nr = 2.0 * yi + pr[q];
+      ni = -2.0 * yr + pi[q];
+      sr = ar[q] + t.coef * nr;
+      si = ai[q] + t.coef * ni;
+    }
+    bad |= !(nr * nr + ni * ni <= t.bound2);
+    if (t.last) {
+      o_r[q] = t.ph_re * sr - t.ph_im * si;
+      o_i[q] = t.ph_re * si + t.ph_im * sr;
+    } else {
+      o_r[q] = nr;
+      o_i[q] = ni;
+      a_r[q] = sr;
+      a_i[q] = si;
+    }
+  }
+  if (bad) atomicOr(t.status, FQ_BIT_BOUND);
+  Quad<double>::store(out_re + row + i0, o_r);
+  Quad<double>::store(out_im + row + i0, o_i);
+  if (!t.last) {
+    Quad<double>::store(acc_re + row + i0, a_r);
+    Quad<double>::store(acc_im + row + i0, a_i);
+  }
+}
+
 // ------------------------------------------------------------------ unitarity defect
 // D[c][j] = sum_i conj(U[i][c]) U[i][j] - delta_cj for up to 16 listed columns c (chunk
 // blockIdx.y) and the 256 columns j of this block: U is streamed once per chunk, row by row,
@@ -502,6 +608,29 @@ void fq_launch_tri_coeffs_f32(const fq_plan* p, int m_begin, int nsteps, double 
   const int ld = (p->n + 3) & ~3;
   k_tri_coeffs<float><<<grid_for((size_t)nsteps * ld, 256), 256, 0, s>>>(
       p->d_h0, p->d_h0o, p->d_h1, p->d_k, p->d_scal, p->n, ld, p->steps, m_begin, nsteps, p->sbeta, scale, d, er, ei);
+}
+
+void fq_launch_omega_band6(const fq_plan* p, const double* c, double* ore, double* oim, int ld, cudaStream_t s) {
+  Band6Args a;
+  a.band = p->d_cm;
+  for (int q = 0; q < FQ_M6_TERMS; ++q) a.c[q] = c[q];
+  a.sbeta = p->sbeta;
+  a.n = p->n;
+  a.ld = ld;
+  k_omega_band6<<<grid_for((size_t)7 * ld, 256), 256, 0, s>>>(a, ore, oim);
+}
+
+void fq_launch_term_band6_f64(const double* ore, const double* oim, int n, fq_blk<double> cur, fq_blk<double> prev,
+                              fq_blk<double> acc, fq_blk<double> out, int nc, int ld, const fq_term& t,
+                              cudaStream_t s) {
+  (void)n;
+  for (int r0 = 0; r0 < nc; r0 += 65535) {  // gridDim.y limit
+    const int rows = nc - r0 < 65535 ? nc - r0 : 65535;
+    const size_t o = (size_t)r0 * ld;
+    dim3 g((ld / 4 + 255) / 256, rows);
+    k_term_band6<<<g, 256, 0, s>>>(ore, oim, ld, cur.re + o, cur.im + o, prev.re + o, prev.im + o, acc.re + o,
+                                   acc.im + o, out.re + o, out.im + o, t);
+  }
 }
 
 void fq_launch_term_tri_f64(const double* d, const double* er, const double* ei, int n, fq_blk<double> cur,

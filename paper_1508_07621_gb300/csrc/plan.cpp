@@ -338,6 +338,54 @@ static void magnus6_coefficients(double h, double f1, double f2, double f3, doub
   }
 }
 
+// The 11 basis elements of the 6th-order scheme for a tridiagonal H0 (diagonal d0, off-diagonal
+// e0) and a diagonal H1 (d1), as bands of half-width 3: H0 and K = [H0,H1] have half-width 1, each
+// commutator with H0 or K widens it by one and one with H1 keeps it, so the deepest (K00 =
+// [H0,K0], KK0 = [K,K0]) reach 3.  Entry (i, i + d) of element q at band[(q * 7 + d + 3) * n + i].
+namespace {
+struct Band7 {
+  int n;
+  std::vector<double> a;  // [7][n]
+  explicit Band7(int n_) : n(n_), a((size_t)7 * n_, 0.0) {}
+  double get(int i, int j) const { return (j - i >= -3 && j - i <= 3 && i >= 0 && i < n && j >= 0 && j < n) ? a[(size_t)(j - i + 3) * n + i] : 0.0; }
+  void set(int i, int j, double v) { a[(size_t)(j - i + 3) * n + i] = v; }
+};
+// [X, Y] = XY - YX, entries beyond half-width 3 dropped (none arise in the 6th-order basis)
+Band7 band_comm(const Band7& x, const Band7& y) {
+  const int n = x.n;
+  Band7 c(n);
+  for (int i = 0; i < n; ++i)
+    for (int j = std::max(0, i - 3); j <= std::min(n - 1, i + 3); ++j) {
+      double v = 0.0;
+      for (int k = std::max(0, i - 3); k <= std::min(n - 1, i + 3); ++k)
+        v += x.get(i, k) * y.get(k, j) - y.get(i, k) * x.get(k, j);
+      c.set(i, j, v);
+    }
+  return c;
+}
+}  // namespace
+
+void fq_tridiag_band6(const double* d0, const double* e0, const double* d1, int n, std::vector<double>& out) {
+  Band7 h0(n), h1(n);
+  for (int i = 0; i < n; ++i) {
+    h0.set(i, i, d0[i]);
+    h1.set(i, i, d1[i]);
+    if (i + 1 < n) {
+      h0.set(i + 1, i, e0[i]);
+      h0.set(i, i + 1, e0[i]);
+    }
+  }
+  const Band7 k = band_comm(h0, h1);
+  const Band7 k0 = band_comm(h0, k), k1 = band_comm(h1, k);
+  const Band7* el[FQ_M6_TERMS];
+  const Band7 k00 = band_comm(h0, k0), k01 = band_comm(h0, k1), k10 = band_comm(h1, k0), k11 = band_comm(h1, k1);
+  const Band7 kk0 = band_comm(k, k0), kk1 = band_comm(k, k1);
+  el[0] = &h0; el[1] = &h1; el[2] = &k; el[3] = &k0; el[4] = &k1; el[5] = &k00;
+  el[6] = &k01; el[7] = &k10; el[8] = &k11; el[9] = &kk0; el[10] = &kk1;
+  out.assign((size_t)FQ_M6_TERMS * 7 * n, 0.0);
+  for (int q = 0; q < FQ_M6_TERMS; ++q) std::copy(el[q]->a.begin(), el[q]->a.end(), out.begin() + (size_t)q * 7 * n);
+}
+
 fq_status fq_finish_bounds(fq_plan* plan, double emin, double emax) {
   const double h = plan->h;
   const int M = plan->steps;
@@ -462,9 +510,13 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_boun
   const int n = p->n, M = p->steps;
   const int order = p->magnus_order == 0 ? 4 : p->magnus_order;
   if (order != 4 && order != 6) { fq_set_error("magnus_order must be 4 or 6 (got %d)", p->magnus_order); return FQ_EINVAL; }
-  if (order == 6 && (p->format != FQ_DENSE || p->drive_kind != FQ_DRIVE_COS)) {
-    fq_set_error("6th-order Magnus needs FQ_DENSE and FQ_DRIVE_COS (its nested commutators of a tridiagonal H0 are "
-                 "heptadiagonal)");
+  if (order == 6 && p->drive_kind != FQ_DRIVE_COS) {
+    fq_set_error("6th-order Magnus needs FQ_DRIVE_COS");
+    return FQ_EUNSUPPORTED;
+  }
+  if (order == 6 && p->format == FQ_TRIDIAG && p->precision != FQ_FP64) {
+    fq_set_error("6th-order Magnus on a tridiagonal plan runs in FQ_FP64 (its nested commutators make Omega~ "
+                 "heptadiagonal, which the streaming FP64 kernel applies)");
     return FQ_EUNSUPPORTED;
   }
   plan->order = order;
@@ -547,6 +599,23 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_boun
     fq_tridiag_extremes(d.data(), p->h0_off, n, &l2, &h2v);
     emin = std::min(l1, l2);
     emax = std::max(h1v, h2v);
+    if (order == 6) {  // Weyl widening by every commutator term, ||B_q||_2 <= its largest row sum
+      fq_tridiag_band6(p->h0, p->h0_off, p->h1, n, plan->band6);
+      double wsum = 0.0;
+      for (int q = 2; q < FQ_M6_TERMS; ++q) {
+        double cmax = 0.0;
+        for (int m = 0; m < M; ++m) cmax = std::max(cmax, fabs(plan->coef6[(size_t)m * FQ_M6_TERMS + q]));
+        double rmax = 0.0;
+        for (int i = 0; i < n; ++i) {
+          double r = 0.0;
+          for (int d = 0; d < 7; ++d) r += fabs(plan->band6[((size_t)q * 7 + d) * n + i]);
+          rmax = std::max(rmax, r);
+        }
+        wsum += cmax / h * rmax;
+      }
+      emin -= wsum;
+      emax += wsum;
+    }
     if (kmax > 0 && n > 1) {  // ||[H0,H1]||_2 from the tridiagonal with |K_{i+1,i}|
       std::vector<double> z(n, 0.0);
       for (int i = 0; i + 1 < n; ++i) k[i] = fabs(p->h0_off[i] * (p->h1[i] - p->h1[i + 1]));

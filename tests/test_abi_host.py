@@ -129,7 +129,7 @@ def test_fixed_chebyshev_terms(fq):
 
 @pytest.mark.parametrize("case,status", [
     ("steps0", "FQ_EINVAL"), ("period0", "FQ_EINVAL"), ("format9", "FQ_EINVAL"), ("drive9", "FQ_EINVAL"),
-    ("piecewise_without_f", "FQ_EINVAL"), ("order5", "FQ_EINVAL"), ("order6_tridiag", "FQ_EUNSUPPORTED"),
+    ("piecewise_without_f", "FQ_EINVAL"), ("order5", "FQ_EINVAL"), ("order6_tridiag_fp32", "FQ_EUNSUPPORTED"),
     ("order6_piecewise", "FQ_EUNSUPPORTED"), ("tile96", "FQ_EINVAL"), ("dense_fp32", "FQ_EUNSUPPORTED"),
     ("tridiag_x6", "FQ_EUNSUPPORTED"), ("kernel9", "FQ_EINVAL")])
 def test_problem_validation(fq, case, status):
@@ -151,8 +151,9 @@ def test_problem_validation(fq, case, status):
         prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, drive_kind=fq.FQ_DRIVE_PIECEWISE, **kw)
     elif case == "order5":
         prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, magnus_order=5, **kw)
-    elif case == "order6_tridiag":
-        prob, keep = fq.make_problem(n, fq.FQ_TRIDIAG, d, d, 1.0, 4, h0_off=np.ones(n - 1), magnus_order=6, **kw)
+    elif case == "order6_tridiag_fp32":
+        prob, keep = fq.make_problem(n, fq.FQ_TRIDIAG, d, d, 1.0, 4, h0_off=np.ones(n - 1), magnus_order=6,
+                                     precision=fq.FQ_FP32, **kw)
     elif case == "order6_piecewise":
         prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, drive_kind=fq.FQ_DRIVE_PIECEWISE,
                                      f_steps=np.ones(4), magnus_order=6)
@@ -350,3 +351,20 @@ def test_library_bessel_sweep_to_the_R_cap(fq):
         ref = jv(np.arange(info.L + 1), info.R)
         ref[1:] *= 2
         assert np.max(np.abs(a - ref)) <= 16 * 2.2e-16 * math.sqrt(info.L) + 1e-18, (R, np.max(np.abs(a - ref)))
+
+
+def test_tridiag_order6_bounds_contain_the_exact_ones(fq):
+    """A tridiagonal plan of the 6th-order scheme: the host's bounds of Omega_m / h (Sturm bounds
+    of H0 + g H1 widened by every commutator band's largest row sum) contain the exact extreme
+    eigenvalues over all steps (the oracle's dense Omega_m through LAPACK), and L is at least the
+    oracle's."""
+    d = fi.config_dimer(nb=30, steps=40)
+    drv = fi.Drive(0.2, 1.5, 3.0, 0.4)
+    prob, keep = fq.make_problem(d.n, fq.FQ_TRIDIAG, d.h0_diag, d.h1_diag, drv.period, d.steps, h0_off=d.h0_off,
+                                 f_dc=drv.f_dc, f_ac=drv.f_ac, omega=drv.omega, phi0=drv.phi0, magnus_order=6)
+    info, _ = fq.floquet_plan_inspect(prob)
+    h0 = np.diag(d.h0_diag) + np.diag(d.h0_off, 1) + np.diag(d.h0_off, -1)
+    rp, _ = o.plan_dense6(h0, np.diag(d.h1_diag), drv, d.steps)
+    lo, hi = rp.beta - rp.delta_e, rp.beta + rp.delta_e
+    assert info.e_min <= lo and info.e_max >= hi
+    assert info.L >= rp.L
