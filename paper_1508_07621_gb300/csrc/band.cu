@@ -483,12 +483,13 @@ __global__ void __launch_bounds__(BAND_THREADS, 1)
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* gbase = smem_raw + (base - raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * Cfg::STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 3);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   BandStage* rstage = reinterpret_cast<BandStage*>(gbase + STAGES * Cfg::STAGE_BYTES + 256);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
-  const uint32_t tfull = smem_u32(bars + 2 * STAGES), tempty = smem_u32(bars + 2 * STAGES + 1);
-  const uint32_t done = smem_u32(bars + 2 * STAGES + 2);
+  // tempty0 + 8 g: accumulator g of the last tile is drained (the epilogue releases them one by one)
+  const uint32_t tfull = smem_u32(bars + 2 * STAGES), tempty0 = smem_u32(bars + 2 * STAGES + 1);
+  const uint32_t done = smem_u32(bars + 2 * STAGES + 5);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = tiles_i * tiles_j;
   const int nk = (OZ_BN + 2 * kh) / OZ_BKE;  // K stages of the tile window
@@ -505,7 +506,7 @@ __global__ void __launch_bounds__(BAND_THREADS, 1)
       mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(tfull, 1);
-    mbar_init(tempty, OZ_EPI_WARPS);
+    for (int g = 0; g < 4; ++g) mbar_init(tempty0 + 8 * g, OZ_EPI_WARPS);
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -567,9 +568,7 @@ __global__ void __launch_bounds__(BAND_THREADS, 1)
       int g = 0, it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
-        if (it > 0 && !(ok = mbar_wait(tempty, (it - 1) & 1))) break;  // the previous tile is drained
-        tc_fence_after();
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        for (int kb = 0; kb < nk && ok; ++kb, ++g) {
           const int s = g % STAGES;
           ok = mbar_wait(full0 + 8 * s, (g / STAGES) & 1);
           if (!ok || *(volatile int*)abort_flag) {
@@ -579,12 +578,19 @@ __global__ void __launch_bounds__(BAND_THREADS, 1)
           tc_fence_after();
           const uint32_t st = base + s * Cfg::STAGE_BYTES;
           const uint64_t d0 = band_desc(st);
+          // the pairs in descending order, accumulator 3 (15 pairs) first: at a tile's first stage
+          // each accumulator's MMAs wait only for that accumulator's drain, so the later ones drain
+          // while accumulator 3's MMAs run
 #pragma unroll
-          for (int p = 0; p < OZ_PAIRS; ++p) {
+          for (int p = OZ_PAIRS - 1; p >= 0; --p) {
             int a, b;
             oz_pair(p, a, b);
             const int grp = a + b < 3 ? a + b : 3;
-            const bool lead = p == 0 || p == 1 || p == 3 || p == 6;  // first pair of each accumulator
+            const bool lead = p == 20 || p == 5 || p == 2 || p == 0;  // first pair of each accumulator
+            if (kb == 0 && lead && it > 0) {
+              if (!(ok = mbar_wait(tempty0 + 8 * grp, (it - 1) & 1))) break;
+              tc_fence_after();
+            }
             const uint32_t acc = tmem + (uint32_t)grp * (2 * OZ_BN);
             const uint32_t rb = 2 * OZ_S * OZ_A_BYTES + b * Cfg::R_BYTES;
             const uint32_t first = (kb == 0 && lead) ? 0u : 1u;
@@ -633,8 +639,9 @@ __global__ void __launch_bounds__(BAND_THREADS, 1)
       float2 hr[8], lr[8], hi[8], li[8];  // double-float sums of columns (2p, 2p + 1)
 #pragma unroll
       for (int q = 0; q < 8; ++q) hr[q] = lr[q] = hi[q] = li[q] = make_float2(0.f, 0.f);
+      // accumulator 3 first (the MMAs of the next tile start with it), each released once read
 #pragma unroll
-      for (int grp = 0; grp < 4; ++grp) {
+      for (int grp = 3; grp >= 0; --grp) {
 #pragma unroll
         for (int part_im = 0; part_im < 2; ++part_im) {
           float v[16];
@@ -646,13 +653,13 @@ __global__ void __launch_bounds__(BAND_THREADS, 1)
           for (int q = 0; q < 8; ++q) {
             const float2 w = make_float2(v[2 * q], v[2 * q + 1]);
             if (grp < 3) dd_add2(h[q], l[q], w);
-            else l[q] = __fadd2_rn(l[q], w);  // below 2^-24 of the leading sum: the low word carries it
+            else l[q] = w;  // below 2^-24 of the leading sum: the low word carries it
           }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * grp);  // the next tile's MMAs into it may start
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty);  // the next tile's MMAs may start
       const int j = j0 + quarter * 32 + lane;
       if (j < e.nc) {
         const int ej = e.es[j];
