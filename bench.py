@@ -711,7 +711,7 @@ def run_dense(args):
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
         p2.close()
-    e2e_value = world / statistics.median(e2e_times)
+    e2e_value = world / statistics.median(e2e_times) if e2e_times else None
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -879,7 +879,7 @@ def run_batch(args):
         fq.floquet_batch_destroy(g2)
         for p in p2:
             p.close()
-    e2e_value = world * len(plans) / statistics.median(e2e_times)
+    e2e_value = world * len(plans) / statistics.median(e2e_times) if e2e_times else None
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -986,7 +986,7 @@ def run_adjoint(args):
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
         p2.close()
-    e2e_value = world / statistics.median(e2e_times)
+    e2e_value = world / statistics.median(e2e_times) if e2e_times else None
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()

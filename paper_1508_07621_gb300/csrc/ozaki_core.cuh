@@ -359,11 +359,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* gbase = smem_raw + (base - raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + OZ_STAGES * OZ_STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 3);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 6);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + OZ_STAGES);
-  const uint32_t tfull = smem_u32(bars + 2 * OZ_STAGES), tempty = smem_u32(bars + 2 * OZ_STAGES + 1);
-  const uint32_t done = smem_u32(bars + 2 * OZ_STAGES + 2);
+  // tempty0 + 8 g: accumulator g of the last chunk is drained (the drain warps release them one by one)
+  const uint32_t tfull = smem_u32(bars + 2 * OZ_STAGES), tempty0 = smem_u32(bars + 2 * OZ_STAGES + 1);
+  const uint32_t done = smem_u32(bars + 2 * OZ_STAGES + 5);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = nk / OZ_KB_PER_DRAIN;
 
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(tfull, 1);
-    mbar_init(tempty, OZ_EPI_WARPS);
+    for (int g = 0; g < 4; ++g) mbar_init(tempty0 + 8 * g, OZ_EPI_WARPS);
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -435,9 +436,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       bool ok = true;
       int kb = 0;
       for (int c = 0; c < nchunks && ok; ++c) {
-        if (c > 0 && !(ok = mbar_wait(tempty, (c - 1) & 1))) break;
-        tc_fence_after();
-        for (int kq = 0; kq < OZ_KB_PER_DRAIN; ++kq, ++kb) {
+        for (int kq = 0; kq < OZ_KB_PER_DRAIN && ok; ++kq, ++kb) {
           const int s = kb % OZ_STAGES;
           ok = mbar_wait(full0 + 8 * s, (kb / OZ_STAGES) & 1);
           if (!ok || *(volatile int*)abort_flag) {
@@ -449,12 +448,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           // descriptors of the stage's tiles: the start-address field is the low 14 bits (16-byte
           // units), so an offset inside shared memory adds to the descriptor without a carry
           const uint64_t d0 = oz_desc(st);
+          // the pairs in descending order, accumulator 3 (15 pairs) first: at a chunk's first stage
+          // each accumulator's MMAs wait only for that accumulator's drain, so the later ones drain
+          // while accumulator 3's MMAs run
 #pragma unroll
-          for (int p = 0; p < OZ_PAIRS; ++p) {
+          for (int p = OZ_PAIRS - 1; p >= 0; --p) {
             int a, b;
             oz_pair(p, a, b);
             const int g = a + b < 3 ? a + b : 3;
-            const bool lead = p == 0 || p == 1 || p == 3 || p == 6;  // first pair of each accumulator
+            const bool lead = p == 20 || p == 5 || p == 2 || p == 0;  // first pair of each accumulator
+            if (kq == 0 && lead && c > 0) {
+              if (!(ok = mbar_wait(tempty0 + 8 * g, (c - 1) & 1))) break;
+              tc_fence_after();
+            }
             const uint32_t acc = tmem + (uint32_t)g * (2 * OZ_BN);
             const uint32_t rb = 2 * OZ_S * OZ_A_BYTES + b * OZ_R_BYTES;
             const uint32_t first = (kq == 0 && lead) ? 0u : 1u;
@@ -491,9 +497,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         ok = false;
         break;
       }
-      // one 16-column load at a time keeps the double-float sums and one load in registers
+      // one 16-column load at a time keeps the double-float sums and one load in registers;
+      // accumulator 3 first (the next chunk's MMAs start with it), each released once read
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
+      for (int g = 3; g >= 0; --g) {
 #pragma unroll
         for (int part_im = 0; part_im < 2; ++part_im) {
           float v[16];
@@ -508,10 +515,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             else l[q] = __fadd2_rn(l[q], w);  // below 2^-24 of the leading sum: the low word carries it
           }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * g);  // the next chunk's MMAs into it may start
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty);
     }
     if (!ok) {
       atomicExch(abort_flag, 1);
