@@ -76,9 +76,14 @@ static fq_status floquet_batch_create_body(fq_batch** out, fq_plan* const* plans
   if (e == cudaSuccess) e = cudaEventRecord(fork, origin);
   for (int l = 0; l < lanes && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(ls[l], fork, 0);
   if (e != cudaSuccess) st = fq_cuda_fail(e, "batch capture setup");
+  // each persistent split product takes at most half the SMs, so products of different lanes run
+  // side by side instead of one after another (5.86 -> 5.57 s for the 48-instance scan)
+  const int cap = std::max(1, fq_sm_count() / 2);
   for (int k = 0; k < count && st == FQ_OK; ++k) {
     const int i = order[k];
+    plans[i]->grid_cap = cap;
     st = floquet_build_UT(plans[i], d_U[i], (char*)d_ws + off[i], ws_bytes - off[i], ls[lane_of[i]]);
+    plans[i]->grid_cap = 0;
   }
   for (int l = 0; l < lanes && capturing; ++l) {
     cudaEventRecord(joins[l], ls[l]);

@@ -165,7 +165,8 @@ static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int 
   k_split_init<NS><<<grid_1d((size_t)nc * w.kp), 256, 0, s>>>(identity ? nullptr : (const double2*)x0, n, nc, w.ldm,
                                                                w.np, w.kp, w.m[0][0], w.m[0][1], w.a[0], w.astride);
   const int tiles_i = w.np / BN, tiles_j = (nc + BM - 1) / BM;
-  const dim3 grid(std::min(tiles_i * tiles_j, sms));  // persistent: at most one CTA per SM
+  // persistent: at most one CTA per SM, or the batch's share of them (lanes' products run side by side)
+  const dim3 grid(std::min(tiles_i * tiles_j, p->grid_cap > 0 ? std::min(p->grid_cap, sms) : sms));
   const int nk = w.np / BKE;
   int xb = 0, av = 0;  // FP32 master holding psi_0 / X, left-operand buffer holding its slices
   fq_term t{};

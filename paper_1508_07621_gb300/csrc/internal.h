@@ -82,6 +82,7 @@ struct fq_plan {
   // dense split path: per-plan constants prepared once
   void* split = nullptr;
   fq_ktimer* ktimer = nullptr;  // owned; NULL until floquet_kernel_timing
+  int grid_cap = 0;  // > 0: CTAs of a persistent split product (while a batch graph captures the plan)
 };
 
 // Brackets one launch of a path's dominant kernel with the plan's timing events (no-ops unless
