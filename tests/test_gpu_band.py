@@ -137,6 +137,33 @@ def test_band_next_band_formed_inside_the_product(fq):
     assert err <= 1e-10
 
 
+def test_band_propagation_captured_in_a_cuda_graph(fq):
+    """The band path on a capturing stream: floquet_propagate of 4096 states (so the product also
+    forms the next band) through 3 steps, captured in a CUDA graph and replayed twice, equals the
+    direct call bit for bit."""
+    import torch
+    d = fi.config_dimer(nb=700, steps=200)
+    d.drive = fi.Drive(0.2, 1.5, 3.0, 0.4)
+    plan = band_plan(fq, d)
+    n, nc = d.n, 4096
+    x0 = np.exp(2j * np.pi * fi.uniform(2801, n * nc)).reshape(nc, n) / np.sqrt(n)
+    X0 = cuda_c128(x0)
+    ws = fq.workspace(plan.workspace_size(nc))
+    ref = torch.empty_like(X0)
+    fq.floquet_propagate(plan.handle, X0, ref, nc, 1, 4, ws)
+    torch.cuda.synchronize()
+    out = torch.empty_like(X0)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fq.floquet_propagate(plan.handle, X0, out, nc, 1, 4, ws)
+    for _ in range(2):
+        out.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    assert plan.check_status() == fq.FQ_OK
+
+
 def test_band_many_state_tiles_and_column_split(fq):
     """dim 701 (11 operator blocks), all 701 states (6 state tiles, ragged): U_T equals the column
     blocks of a 3-rank split bit for bit, and matches the oracle."""
