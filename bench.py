@@ -375,7 +375,7 @@ DIMER_PATHS = {
 # `python bench.py --ncu-case band` (4096 states; profiles/k_oz_band_dimer10001.md), scaled to a
 # launch by states: the state slices read and the next step's slices written grow with the states
 # (a step that is not the last: no double-float states written).
-BAND_NCU = {"read": 1131.5e6, "write": 1007.0e6, "states": 4096}
+BAND_NCU = {"read": 1140.6e6, "write": 989.4e6, "states": 4096}
 
 
 def band_window(L):
