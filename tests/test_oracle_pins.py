@@ -491,3 +491,17 @@ def test_adjoint1024_golden_plan_and_format():
     for k in ("R", "beta", "delta_e"):
         assert abs(getattr(plan, k) - g[k]) <= 1e-12 * abs(g[k])
     assert 0.0 <= g["loss"] <= 1.0 and len(g["g"]) == 256 and np.all(np.isfinite(g["g"]))
+
+
+@pytest.mark.parametrize("steps", [2, 7, 40])
+def test_single_level_is_the_phase_of_the_period_average(steps):
+    """A single level (N = 1): every H(t) commutes, so U_T = exp(-i (h0 + h1 f_dc) T) (the
+    cosine part of the drive integrates to zero over a period).  The 4th-order scheme gets it
+    exactly, not just to O(h^4): the step midpoints of a cosine over a whole period sum to zero,
+    and so do the f'' corrections.  A dropped phase or a wrong sign of beta fails it."""
+    drv = fi.Drive(0.3, 1.5, 3.0, 0.4)
+    a, b = np.array([0.7]), np.array([-1.3])
+    p = o.plan_for_drive_tridiag(a, np.zeros(0), b, drv, steps)
+    U = o.build_ut_tridiag(a, np.zeros(0), b, p)
+    exact = np.exp(-1j * (a[0] + b[0] * drv.f_dc) * (2 * math.pi / drv.omega))
+    assert abs(U[0, 0] - exact) <= 1e-14
