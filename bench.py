@@ -362,7 +362,10 @@ DIMER_PATHS = {
     # slice-product rate beside it
     "ozaki": {"precision": "FQ_OZAKI", "kernel": "FQ_KERNEL_BAND", "dtype": "ozaki (bf16 slices, fp32 sums)",
               "level": "FP64", "kernel_name": "k_oz_band", "unit": "TFLOP/s", "per_unit": FLOPS_PER_ELEMENT_TERM,
-              "launches_per_step": 3 * STEPS + 3, "tensor": True,
+              # per U_T build: the product and the fixup pass of every step, plus the gauge tables, the
+              # load, the first step's row maxima, slices and band, and the store (10001 states: the
+              # product forms the next band itself)
+              "launches_per_step": 2 * STEPS + 6, "tensor": True,
               "peak_note": "measured sustained cuBLAS bf16 (MEASURED_PEAKS.json)"},
     "df32": {"precision": "FQ_DF32", "kernel": "FQ_KERNEL_TILED", "dtype": "df32 (FP32 pairs, FP64 states)",
              "level": "FP64", "kernel_name": "k_tri_tile_dfl", "unit": "Tops/s",
