@@ -84,6 +84,9 @@ def parse():
                          "A ~ U[0.5, 3], M = 256) as one CUDA graph over 8 lanes, instances/s")
     ap.add_argument("--n", type=int, default=4096, choices=sorted(PAPER_TABLE1_CHEB_S),
                     help="paper-table1: the matrix size (the rows of the paper's Table 1)")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="batch: 0 = one persistent launch over work units (split precisions), 1-32 = a graph of "
+                         "per-instance builds on that many branches")
     ap.add_argument("--precision", choices=["x3", "x6", "ozaki", "fp64", "fp32", "df32"], default=None,
                     help="goe4096 / adjoint / batch: BF16X3 (default), BF16X6, FQ_OZAKI (FP64 emulation) or FP64 "
                          "(adjoint only); dimer: ozaki (band kernel on the tensor cores, FP64-level; default), "
@@ -790,7 +793,28 @@ def run_dense(args):
         dist.destroy_process_group()
 
 
-BATCH_STEPS, BATCH_LANES = 256, 8
+BATCH_STEPS = 256
+
+
+def batch_mma_flops(insts, Ls, tiles, prec, scan):
+    """Tensor-core work the scan issues, padding included: per term, 128-row state blocks x the
+    output rows of whole tiles x K rounded up to the stage depth, times the slice products.  The
+    persistent scan runs one tile width for every instance (the one the plans' widths favour,
+    weighted by N^3 L); the lane graph runs each plan's own."""
+    def ceil(x, b):
+        return -(-x // b) * b
+    if prec not in ("x3", "x6"):
+        return None
+    if scan:
+        w = {64: 0.0, 128: 0.0}
+        for s, L, t in zip(insts, Ls, tiles):
+            w[128 if t == 128 else 64] += float(s.n) ** 3 * L
+        tiles = [128 if w[128] >= w[64] else 64] * len(insts)
+    tot = 0.0
+    for s, L, t in zip(insts, Ls, tiles):
+        bke = 32 if (prec == "x6" or t == 128) else 64
+        tot += 8.0 * ceil(s.n, 128) * ceil(s.n, 128) * ceil(s.n, bke) * L * BATCH_STEPS
+    return tot * SLICE_PRODUCTS[prec]
 
 
 def batch_flops(insts, Ls):
@@ -855,7 +879,10 @@ def run_batch(args):
     outs = [torch.empty((p.n, p.n), dtype=torch.complex128, device="cuda") for p in plans]
     handles = [p.handle for p in plans]
     ws = fq.workspace(fq.floquet_batch_workspace_size(handles))
-    graph = fq.floquet_batch_create(handles, outs, ws, BATCH_LANES)
+    # the persistent scan takes split-precision plans with L <= 32; anything else runs on 8 lanes
+    scan = args.lanes == 0 and prec in ("x3", "x6") and max(Ls) <= 32
+    lanes = 0 if scan else (args.lanes or 8)
+    graph = fq.floquet_batch_create(handles, outs, ws, lanes)
     try:
         for _ in range(max(args.warmup, 0)):
             fq.floquet_batch_launch(graph, stream)
@@ -879,7 +906,7 @@ def run_batch(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         p2 = make_plans(tiles)
-        g2 = fq.floquet_batch_create([p.handle for p in p2], outs, ws, BATCH_LANES)
+        g2 = fq.floquet_batch_create([p.handle for p in p2], outs, ws, lanes)
         fq.floquet_batch_launch(g2, stream)
         for h, u in zip(host, outs):
             h.copy_(u, non_blocking=True)
@@ -896,20 +923,25 @@ def run_batch(args):
     peaks = measured_peaks()
     useful = batch_flops(insts, Ls)
     issued = useful * SLICE_PRODUCTS[prec]
+    padded = batch_mma_flops(insts, Ls, tiles, prec, scan)
     avg = statistics.mean(per_step)
     achieved = useful / avg / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
                 "frac": achieved / peaks["bf16_sustained"], "traffic": None,
-                "kernel": "k_oz_term" if prec == "ozaki" else "k_split_persist",
+                "kernel": "k_split_scan" if scan else ("k_oz_term" if prec == "ozaki" else "k_split_persist"),
                 "issued_tflops": issued / avg / 1e12, "issued_frac": issued / avg / 1e12 / peaks["bf16_sustained"],
+                "issued_with_padding_frac": (padded / avg / 1e12 / peaks["bf16_sustained"]) if padded else None,
                 "note": (f"achieved: useful 8 N_i^3 L_i M flop summed over the {len(plans)} instances; issued: "
-                         f"x {SLICE_PRODUCTS[prec]} BF16 slice products; both over one graph launch's CUDA-event "
-                         f"time; peak: {peaks['source']} sustained cuBLAS bf16")}
+                         f"x {SLICE_PRODUCTS[prec]} BF16 slice products; issued_with_padding: the MMAs as run, "
+                         f"on whole 128-state blocks, whole output tiles and K rounded up to the stage depth; all "
+                         f"over one graph launch's CUDA-event time; peak: {peaks['source']} sustained cuBLAS bf16")}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         v, dt, desc = batch_oracle_sample(insts)
         cpu = {"value": v, "unit": "instances/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
-    per_inst = [2 + BATCH_STEPS * (1 + (2 * L if prec == "ozaki" else L)) for L in Ls]
+    # kernels per graph launch: the one persistent kernel, or per instance its init, store and per
+    # step the Omega~ slices and L terms (2 L with the FP64 emulation's fix-ups)
+    launches = 1 if scan else sum(2 + BATCH_STEPS * (1 + (2 * L if prec == "ozaki" else L)) for L in Ls)
     ns = [s.n for s in insts]
     line = {"metric": f"instances/sec ({len(plans)}-instance dense GOE scan, N ~ U{{256..2048}}, M={BATCH_STEPS}, "
                       "one CUDA graph)",
@@ -920,8 +952,9 @@ def run_batch(args):
             "data": "synthetic",
             "config": {"workload": (f"batched scan: {len(plans)} GOE instances (seeds 1000 + 2i, 1001 + 2i), "
                                     f"N in [{min(ns)}, {max(ns)}], omega ~ U[0.5, 4], A ~ U[0.5, 3], M={BATCH_STEPS}, "
-                                    f"{PREC_NAMES[prec]}, {BATCH_LANES} graph lanes"),
-                       "instances": len(plans), "lanes": BATCH_LANES, "L_range": [min(Ls), max(Ls)],
+                                    f"{PREC_NAMES[prec]}, "
+                                    + ("one persistent launch over work units" if scan else f"{lanes} graph lanes")),
+                       "instances": len(plans), "lanes": lanes, "L_range": [min(Ls), max(Ls)],
                        "tiles": tiles,
                        "l2": "working set larger than L2 (operand slices and states of 48 instances, > 1 GB)",
                        "parallelism": f"weak: {world} independent scans"},
@@ -929,7 +962,7 @@ def run_batch(args):
             "e2e": {"value": e2e_value, "unit": "instances/s",
                     "h2d_bytes_per_step": sum(16 * n * n + 24 * BATCH_STEPS for n in ns),
                     "d2h_bytes_per_step": sum(16 * n * n for n in ns)},
-            "gpu_launches": sum(per_inst) * args.steps, "clocks": clk, "device_status_ok": status_ok,
+            "gpu_launches": launches * args.steps, "clocks": clk, "device_status_ok": status_ok,
             "accuracy": {"unitarity_defect_max": defect, "defect_columns_per_instance": 16},
             "median_step_s": statistics.median(per_step), "per_step_s": per_step, "host": host_info()}
     print(json.dumps(line), flush=True)

@@ -324,13 +324,28 @@ fq_status floquet_overlap_phase_error(fq_plan* plan, const void* d_states, int32
  *    that overlap on the GPU (other streams, other host threads) race and must not be made. */
 fq_status floquet_build_UT_static(const fq_problem* problem, void* d_U, void* stream);
 
-/* Batched scan (many independent problems, one launch).  Captures floquet_build_UT of every
- * plan into one CUDA graph: plan i writes d_U[i] (its N_i x N_i complex128 output) using its
- * slice of d_ws, and the instances run concurrently on `lanes` (1..32) graph branches, assigned
- * longest-first by their cost N^3 M L.  floquet_batch_launch then replays the whole scan as a
- * single graph launch on `stream`.  The plans, outputs and workspace must outlive the batch;
- * the graph is bound to those pointers.  Capture enqueues nothing.
- * d_ws: floquet_batch_workspace_size(plans, count) bytes, 256-byte aligned. */
+/* Batched scan (many independent problems, one launch; the paper's method applied to a scan of
+ * drive parameters).  Plan i writes d_U[i] (its N_i x N_i complex128 U_T, as floquet_build_UT)
+ * and floquet_batch_launch replays the whole scan as one graph launch on `stream`.
+ *  - lanes = 0: when every plan is a split-precision dense plan (FQ_BF16X3 or FQ_BF16X6, Magnus
+ *    order 4, L <= 32) of one precision and one step count M, the graph holds ONE persistent
+ *    tensor-core kernel (one CTA per SM) whose CTAs take work units from a device counter: per
+ *    instance the blocks of Omega~_m's slices (Eqs. 11 and 14), and per step, term and output
+ *    tile the Chebyshev term of Eq. 10 (state blocks of 128 columns advance independently, each
+ *    unit waiting, with a bounded spin, only for the units it reads).  The tile width is the one
+ *    the plans' own widths favour (tile_n or floquet_autotune), weighted by N^3 M L; each U_T then
+ *    equals the plan's own floquet_build_UT bit for bit when the widths agree.  Other plans fall
+ *    back to 8 lanes.
+ *  - lanes = 1..32: floquet_build_UT of every plan captured on `lanes` concurrent graph
+ *    branches, assigned longest-first by their cost N^3 M L.
+ *  - A wait that gives up marks every plan's status word FQ_BIT_TIMEOUT (floquet_check_status
+ *    reports FQ_ETIMEOUT); the device check marks the plan it fired for.
+ * The plans, outputs and workspace must outlive the batch; the graph is bound to those pointers,
+ * and the batch's launches must not overlap one another on the GPU (they share the workspace).
+ * Creating the batch enqueues nothing (lanes = 0 writes its unit tables into d_ws with a
+ * synchronous copy).
+ * d_ws: floquet_batch_workspace_size(plans, count) bytes, 256-byte aligned (it includes the
+ * persistent scan's tables, counters and second Omega~ buffers when the plans qualify). */
 typedef struct fq_batch fq_batch;
 size_t floquet_batch_workspace_size(fq_plan* const* plans, int32_t count);
 fq_status floquet_batch_create(fq_batch** batch, fq_plan* const* plans, int32_t count, void* const* d_U,

@@ -292,8 +292,9 @@ def floquet_batch_workspace_size(plans) -> int:
     return int(lib.floquet_batch_workspace_size(arr, len(plans)))
 
 
-def floquet_batch_create(plans, outputs, ws, lanes: int = 8) -> int:
-    """One CUDA graph for the U_T builds of all plans; outputs[i]: N_i x N_i complex128 tensors."""
+def floquet_batch_create(plans, outputs, ws, lanes: int = 0) -> int:
+    """One CUDA graph for the U_T builds of all plans; outputs[i]: N_i x N_i complex128 tensors.
+    lanes = 0: one persistent launch over work units where the plans allow it (else 8 lanes)."""
     w = "floquet_batch_create"
     if len(outputs) != len(plans):
         raise FloquetError(FQ_EINVAL, w, f"{len(plans)} plans but {len(outputs)} outputs")

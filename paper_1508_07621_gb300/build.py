@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libfloquet.so")
-SOURCES = ["plan.cpp", "api.cpp", "kernels.cu", "tri_resident.cu", "tri_tile.cu", "dense_resident.cu", "noalloc.cu", "adjoint.cu", "dense_split.cu", "ozaki.cu", "ozaki_grad.cu", "adjoint_split.cu", "batch.cpp", "quasi.cpp", "observables.cu", "band.cu"]
+SOURCES = ["plan.cpp", "api.cpp", "kernels.cu", "tri_resident.cu", "tri_tile.cu", "dense_resident.cu", "noalloc.cu", "adjoint.cu", "dense_split.cu", "ozaki.cu", "ozaki_grad.cu", "adjoint_split.cu", "batch.cpp", "quasi.cpp", "observables.cu", "band.cu", "scan.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host complex arithmetic on unitary input: no product comes near overflow, so the NaN/Inf
 # recovery of C99 complex multiplication is not needed

@@ -1,4 +1,7 @@
 // Batched scan: many independent U_T builds captured into one CUDA graph (one launch per scan).
+// lanes = 0: split-precision dense plans of one precision and step count run as one persistent
+// launch over (instance, step, term, tile) work units (scan.cu); otherwise, or with lanes >= 1, the
+// graph holds every plan's own build on `lanes` concurrent branches.
 #include <algorithm>
 #include <new>
 #include <numeric>
@@ -16,19 +19,23 @@ size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 double cost(const fq_plan* p) { return (double)p->n * p->n * p->n * p->steps * p->L; }
 }  // namespace
 
+// the plans' own workspaces, back to back
+static size_t plans_bytes(fq_plan* const* plans, int count) {
+  size_t tot = 0;
+  for (int i = 0; i < count; ++i) tot += up256(floquet_workspace_size(plans[i], plans[i]->n));
+  return tot;
+}
+
 extern "C" size_t floquet_batch_workspace_size(fq_plan* const* plans, int32_t count) {
   if (!plans || count < 1) return 0;
-  size_t tot = 0;
-  for (int i = 0; i < count; ++i) {
+  for (int i = 0; i < count; ++i)
     if (!plans[i]) return 0;
-    tot += up256(floquet_workspace_size(plans[i], plans[i]->n));
-  }
-  return tot;
+  return plans_bytes(plans, count) + fq_scan_extra_bytes(plans, count);
 }
 
 static fq_status floquet_batch_create_body(fq_batch** out, fq_plan* const* plans, int32_t count, void* const* d_U,
                                            void* d_ws, size_t ws_bytes, int32_t lanes) {
-  if (!out || !plans || !d_U || count < 1 || lanes < 1 || lanes > 32) {
+  if (!out || !plans || !d_U || count < 1 || lanes < 0 || lanes > 32) {
     fq_set_error("floquet_batch_create: bad arguments");
     return FQ_EINVAL;
   }
@@ -43,6 +50,28 @@ static fq_status floquet_batch_create_body(fq_batch** out, fq_plan* const* plans
     fq_set_error("floquet_batch_create: workspace must be >= %zu bytes, 256-byte aligned", need);
     return FQ_EINVAL;
   }
+  std::vector<size_t> off(count);
+  size_t o = 0;
+  for (int i = 0; i < count; ++i) {
+    off[i] = o;
+    o += up256(floquet_workspace_size(plans[i], plans[i]->n));
+  }
+  fq_batch* b = new (std::nothrow) fq_batch();
+  if (!b) { fq_set_error("host allocation failed"); return FQ_ENOMEM; }
+  if (lanes == 0 && fq_scan_eligible(plans, count)) {  // one persistent launch over work units
+    fq_status st = fq_scan_graph(plans, count, d_U, d_ws, off.data(), plans_bytes(plans, count), &b->graph);
+    if (st == FQ_OK) {
+      cudaError_t e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+      if (e != cudaSuccess) st = fq_cuda_fail(e, "batch graph instantiate");
+    }
+    if (st != FQ_OK) {
+      floquet_batch_destroy(b);
+      return st;
+    }
+    *out = b;
+    return FQ_OK;
+  }
+  if (lanes == 0) lanes = 8;  // plans the persistent scan does not take: the lane graph
   // longest-processing-time assignment of instances to lanes
   std::vector<int> order(count);
   std::iota(order.begin(), order.end(), 0);
@@ -54,14 +83,6 @@ static fq_status floquet_batch_create_body(fq_batch** out, fq_plan* const* plans
     lane_of[i] = l;
     load[l] += cost(plans[i]);
   }
-  std::vector<size_t> off(count);
-  size_t o = 0;
-  for (int i = 0; i < count; ++i) {
-    off[i] = o;
-    o += up256(floquet_workspace_size(plans[i], plans[i]->n));
-  }
-  fq_batch* b = new (std::nothrow) fq_batch();
-  if (!b) { fq_set_error("host allocation failed"); return FQ_ENOMEM; }
   cudaStream_t origin = nullptr;
   std::vector<cudaStream_t> ls(lanes, nullptr);
   std::vector<cudaEvent_t> joins(lanes, nullptr);

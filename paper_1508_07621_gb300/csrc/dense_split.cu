@@ -8,24 +8,24 @@
 
 namespace {
 
-// Right operands of step m: S and A of Omega~_m = S + i A as NS BF16 slices [Np][Np] each, computed
-// in FP64 (stage a2): S = sa H0 + sb H1 - sbeta 1, A = sc [H0,H1]; zero outside N x N.
+// Right operands of step m: S and A of Omega~_m = S + i A as NS BF16 slices [Np][Np] each (stage
+// a2): S = sa H0 + sb H1 - sbeta 1, A = sc [H0,H1], formed in FP32 (omega_entry); zero outside
+// N x N.
 template <int NS>
 __global__ void k_split_omega(const double* __restrict__ h0, const double* __restrict__ h1,
-                              const double* __restrict__ k, int n, int np, double sa, double sb, double sc,
-                              double sbeta, __nv_bfloat16* os, __nv_bfloat16* oa, size_t slice_stride) {
+                              const double* __restrict__ k, int n, int np, float sa, float sb, float sc,
+                              float sbeta, __nv_bfloat16* os, __nv_bfloat16* oa, size_t slice_stride) {
   const size_t total = (size_t)np * np;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(q / np), c = (int)(q % np);
-    double S = 0.0, A = 0.0;
+    float S = 0.f, A = 0.f;
     if (i < n && c < n) {
       const size_t o = (size_t)i * n + c;
-      S = sa * h0[o] + sb * h1[o] - (i == c ? sbeta : 0.0);
-      A = sc * k[o];
+      omega_entry(h0[o], h1[o], k[o], i == c, sa, sb, sc, sbeta, S, A);
     }
     __nv_bfloat16 s1[NS], s2[NS];
-    split_f64<NS>(S, s1);
-    split_f64<NS>(A, s2);
+    split_f32<NS>(S, s1);
+    split_f32<NS>(A, s2);
 #pragma unroll
     for (int t = 0; t < NS; ++t) {
       os[t * slice_stride + q] = s1[t];
@@ -68,45 +68,10 @@ __global__ void k_split_omega6(Omega6Split a, __nv_bfloat16* os, __nv_bfloat16* 
   }
 }
 
-// Left operand and FP32 masters of the initial block: identity rows (build_UT) or given states.
-template <int NS>
-__global__ void k_split_init(const double2* __restrict__ x0, int n, int nc, int ldm, int np, int kp, float* mre,
-                             float* mim, __nv_bfloat16* sl, size_t slice_stride) {
-  const size_t total = (size_t)nc * kp;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(q / kp), c = (int)(q % kp);
-    const bool im_half = c >= np;
-    const int i = im_half ? c - np : c;
-    float v = 0.f;
-    if (i < n) {
-      double2 z = x0 ? x0[(size_t)j * n + i] : make_double2(i == j ? 1.0 : 0.0, 0.0);
-      v = (float)(im_half ? z.y : z.x);
-      if (im_half) mim[(size_t)j * ldm + i] = v;
-      else mre[(size_t)j * ldm + i] = v;
-    }
-    __nv_bfloat16 s[NS];
-    split_f32<NS>(v, s);
-#pragma unroll
-    for (int t = 0; t < NS; ++t) sl[t * slice_stride + q] = s[t];
-  }
-}
-
 
 }  // namespace
 
 // ------------------------------------------------------------------------- orchestration
-// Workspace: B slices (Br, Bi), two left-operand slice buffers (ping-pong across terms), three
-// FP32 master state buffers (planar) for psi_l / psi_{l-1} / acc.
-struct SplitWs {
-  __nv_bfloat16* os;  // S slices
-  __nv_bfloat16* oa;  // A slices
-  __nv_bfloat16* a[2];
-  float* m[3][2];
-  unsigned int* flags;  // chain counters: [CHAIN_MAXP][row blocks]
-  int np, kp, ldm, ncp;
-  size_t bstride, astride;
-};
-
 static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t fq_split_workspace(const fq_plan* p, int nc, void* base, void* out) {
@@ -167,7 +132,8 @@ static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int 
   const int tiles_i = w.np / BN, tiles_j = (nc + BM - 1) / BM;
   // persistent: at most one CTA per SM, or the batch's share of them (lanes' products run side by side)
   const dim3 grid(std::min(tiles_i * tiles_j, p->grid_cap > 0 ? std::min(p->grid_cap, sms) : sms));
-  const int nk = w.np / BKE;
+  // K runs to N rounded up to the stage depth: the operands' columns beyond N are zero
+  const int nk = (n + BKE - 1) / BKE;
   int xb = 0, av = 0;  // FP32 master holding psi_0 / X, left-operand buffer holding its slices
   fq_term t{};
   t.coef0 = p->cheb[0];
@@ -190,8 +156,9 @@ static fq_status run_split(fq_plan* p, const double* x0, double* x, int nc, int 
       a.np = w.np;
       k_split_omega6<NS><<<grid_1d(w.bstride), 256, 0, s>>>(a, w.os, w.oa, w.bstride);
     } else {
-      k_split_omega<NS><<<grid_1d(w.bstride), 256, 0, s>>>(p->d_h0, p->d_h1, p->d_k, n, w.np, p->sa[m], p->sb[m],
-                                                           p->sc[m], p->sbeta, w.os, w.oa, w.bstride);
+      k_split_omega<NS><<<grid_1d(w.bstride), 256, 0, s>>>(p->d_h0, p->d_h1, p->d_k, n, w.np, (float)p->sa[m],
+                                                           (float)p->sb[m], (float)p->sc[m], (float)p->sbeta,
+                                                           w.os, w.oa, w.bstride);
     }
     // the step's L terms: their epilogues and left-operand buffers, then one cooperative chain
     // launch (a term's tiles start as soon as the previous term has finished their row block), or

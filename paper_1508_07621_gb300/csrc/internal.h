@@ -236,6 +236,13 @@ fq_status fq_ozaki_propagate(fq_plan* p, const double* x0, double* x, int nc, in
                              int transpose_out, void* ws, cudaStream_t s);
 // split-precision dense path (dense_split.cu)
 size_t fq_split_workspace(const fq_plan* p, int nc, void* base, void* out);
+// batched scan as one persistent launch (scan.cu): whether the plans qualify, the bytes it needs
+// beyond the plans' own workspaces, and the graph (counter reset + the launch) writing d_U[i];
+// plan i's workspace at ws + off[i], the scan's region at ws + extra_off
+int fq_scan_eligible(fq_plan* const* plans, int count);
+size_t fq_scan_extra_bytes(fq_plan* const* plans, int count);
+fq_status fq_scan_graph(fq_plan* const* plans, int count, void* const* d_U, void* ws, const size_t* off,
+                        size_t extra_off, cudaGraph_t* graph);
 // True the first time it is called on the current device for this flag word (one bit per
 // device, devices 0..31): per-device one-time set-up such as kernel attributes, which the
 // runtime keeps per device.

@@ -144,6 +144,39 @@ __device__ __forceinline__ void split_f64(double x, __nv_bfloat16 (&s)[NS]) {
   }
 }
 
+// Entry (i, c) of Omega~_m = S + i A with S = sa H0 + sb H1 - sbeta 1 and A = sc [H0, H1]
+// (Eqs. 11 and 14), formed in FP32 from the FP64 operators: the split paths keep at most 24 bits
+// of an entry (three BF16 slices), and FP64 arithmetic runs at a small fraction of the FP32 rate
+// on this GPU.  The multiply-adds are spelt out so that every kernel forming it rounds alike.
+__device__ __forceinline__ void omega_entry(double h0, double h1, double k, bool diag, float sa, float sb,
+                                            float sc, float sbeta, float& S, float& A) {
+  S = fmaf(sa, (float)h0, fmaf(sb, (float)h1, diag ? -sbeta : 0.f));
+  A = sc * (float)k;
+}
+
+// Left operand and FP32 masters of the initial block: identity rows (build_UT) or given states.
+template <int NS>
+__global__ void k_split_init(const double2* __restrict__ x0, int n, int nc, int ldm, int np, int kp, float* mre,
+                             float* mim, __nv_bfloat16* sl, size_t slice_stride) {
+  const size_t total = (size_t)nc * kp;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(q / kp), c = (int)(q % kp);
+    const bool im_half = c >= np;
+    const int i = im_half ? c - np : c;
+    float v = 0.f;
+    if (i < n) {
+      double2 z = x0 ? x0[(size_t)j * n + i] : make_double2(i == j ? 1.0 : 0.0, 0.0);
+      v = (float)(im_half ? z.y : z.x);
+      if (im_half) mim[(size_t)j * ldm + i] = v;
+      else mre[(size_t)j * ldm + i] = v;
+    }
+    __nv_bfloat16 s[NS];
+    split_f32<NS>(v, s);
+#pragma unroll
+    for (int t = 0; t < NS; ++t) sl[t * slice_stride + q] = s[t];
+  }
+}
+
 // Products kept for NS slices: (a, b) with a + b < NS, ordered smallest first.
 template <int NS> struct Pairs;
 template <> struct Pairs<2> {
@@ -155,6 +188,19 @@ template <> struct Pairs<3> {
   static constexpr int N = 6;
   static __device__ __forceinline__ int a(int p) { const int t[6] = {1, 0, 2, 1, 0, 0}; return t[p]; }
   static __device__ __forceinline__ int b(int p) { const int t[6] = {1, 2, 0, 0, 1, 0}; return t[p]; }
+};
+
+// Workspace of the split chain (dense_split.cu's fq_split_workspace): the right operand's slices
+// (S, A), two left-operand slice buffers (ping-pong across terms), three FP32 master state buffers
+// (planar) for psi_l / psi_{l-1} / acc, and the chain counters.
+struct SplitWs {
+  __nv_bfloat16* os;  // S slices
+  __nv_bfloat16* oa;  // A slices
+  __nv_bfloat16* a[2];
+  float* m[3][2];
+  unsigned int* flags;  // chain counters: [CHAIN_MAXP][row blocks]
+  int np, kp, ldm, ncp;
+  size_t bstride, astride;
 };
 
 struct SplitMaps {

@@ -25,7 +25,8 @@ def fq():
 @pytest.mark.slow
 def test_full_scan_sampled_against_oracle(fq):
     """48 GOE instances (N ~ U{256..2048}, omega ~ U[0.5, 4], A ~ U[0.5, 3], M = 256), BF16X3
-    with autotuned tiles, built by one CUDA graph over 8 lanes: the smallest, the median and the
+    with autotuned tiles, built by one persistent launch over (instance, step, term, tile) work
+    units (lanes = 0, as bench.py times it): the smallest, the median and the
     largest instance each against the oracle's propagation of 3 basis states (first, middle and
     last) through all 256 steps, to the split target; every instance's unitarity defect over 16
     columns within what that target implies (|(U^+U - 1)_cj| <= 2 sqrt(N) e + N e^2)."""
@@ -41,7 +42,7 @@ def test_full_scan_sampled_against_oracle(fq):
     outs = [torch.empty((p.n, p.n), dtype=torch.complex128, device="cuda") for p in plans]
     handles = [p.handle for p in plans]
     ws = fq.workspace(fq.floquet_batch_workspace_size(handles))
-    b = fq.floquet_batch_create(handles, outs, ws, 8)
+    b = fq.floquet_batch_create(handles, outs, ws, 0)
     try:
         fq.floquet_batch_launch(b)
         torch.cuda.synchronize()

@@ -115,7 +115,7 @@ def _x3_real_product(P, X):
 
 def test_x3_chain_on_a_scan_instance():
     """The whole BF16X3 step chain modelled on CPU for the batched scan's smallest instance
-    (N = 257, M = 256): operator slices from FP64, state slices from FP32 masters, the Chebyshev
+    (N = 257, M = 256): operator entries in FP32 cut into slices, state slices from FP32 masters, the Chebyshev
     recurrence, Bessel sum and phase in FP32 (Eqs. 10 and 12), against the FP64 oracle on three
     basis states.  The model stays far inside the 1e-5 target of the split paths (7e-7 seen)."""
     import floquet_inputs as fi
@@ -132,9 +132,10 @@ def test_x3_chain_on_a_scan_instance():
     x0[cols, np.arange(len(cols))] = 1.0
     ref = o.propagate_dense(h0, h1, plan, x0)
 
-    def op_slices(P):
-        hi = bf16_rne(P.astype(np.float32))
-        return hi, bf16_rne((P - hi.astype(np.float64)).astype(np.float32))
+    def op_slices(P):  # entries formed in FP32, then cut into two BF16 slices in FP32
+        p32 = P.astype(np.float32)
+        hi = bf16_rne(p32)
+        return hi, bf16_rne((p32 - hi.astype(np.float32)).astype(np.float32))
 
     f32 = np.float32
     xr, xi = x0.real.astype(f32), x0.imag.astype(f32)
