@@ -6,9 +6,8 @@
 //   prologue  B(i, 0, b)     instance i, block b of 16 rows: the identity's left-operand slices and
 //                            FP32 masters, and the S and A slices of Omega~_0 (Eqs. 11 and 14);
 //   step m    T(i, m, p, t)  term p of step m of instance i (Eq. 10) on output tile t (128 states x
-//                            BN rows of Omega~); the instances in groups sized to L2 and to two
-//                            waves of tiles, level p of a group before its level p + 1;
-//             B(i, m + 1, b) the slices of Omega~_{m+1}, in shares after the instance's levels
+//                            BN rows of Omega~), term p of every instance before term p + 1;
+//             B(i, m + 1, b) the slices of Omega~_{m+1}, in shares after the instance's terms
 //                            1 .. L - 1;
 //   end       W(i, b)        16 states of U_T: FP32 masters to complex128, transposed.
 // CTAs take units from a device counter, so cheap and costly instances balance.  Units are taken in
@@ -40,7 +39,6 @@ constexpr int SCAN_RING = 8;     // units handed from the producer to the MMA th
 constexpr int SCAN_THREADS = 320;  // producer, MMA, four epilogue warps, four builder warps
 constexpr int BLOCK_ROWS = 16;   // rows of a B or W unit
 constexpr int SCAN_TAIL = 512;   // barriers, tensor-memory slot, abort flag and ring after the stages
-constexpr bool SCAN_GROUPS = false;  // run a step's instances in L2-sized groups (else all in lockstep)
 
 enum ScanUnitType { SU_TERM = 0, SU_OMEGA = 1, SU_STORE = 2, SU_END = 3 };
 
@@ -583,81 +581,66 @@ struct ScanLayout {
   int npro = 0, nstep = 0, nend = 0, upro = 0, ustep = 0, uend = 0;
 };
 
-int tiles_j_of(const fq_plan* p) { return (p->n + BM - 1) / BM; }
-int np_of(const fq_plan* p) { return (p->n + 127) & ~127; }
+// What the unit table needs of an instance: N, the series length L and the slices per operand.
+struct ScanShape {
+  int n, L, ns;
+};
 
-// false when the unit count would not fit the 32-bit counter
-bool scan_layout(fq_plan* const* plans, int count, int bn, ScanLayout& L) {
-  const int M = plans[0]->steps;
-  // costliest instances first
+int np_of(int n) { return (n + 127) & ~127; }
+int tiles_j_of(int n) { return (n + BM - 1) / BM; }
+
+std::vector<ScanShape> shapes_of(fq_plan* const* plans, int count) {
+  std::vector<ScanShape> sh(count);
+  for (int i = 0; i < count; ++i) sh[i] = ScanShape{plans[i]->n, plans[i]->L, scan_ns(plans[i])};
+  return sh;
+}
+
+// The unit table and the scan's region; false when the unit count would not fit the 32-bit counter.
+// Step order: term p of every instance (costliest first, state-block-major inside a term) before
+// term p + 1 of any, each instance's Omega~ blocks of the next step in L - 1 shares after its terms
+// 1 .. L - 1 (after term 0 when L = 1), so the builder warps' work spreads over the step.
+bool scan_layout(const std::vector<ScanShape>& sh, int steps, int bn, ScanLayout& L) {
+  const int count = (int)sh.size();
   std::vector<int> order(count);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    const fq_plan *a = plans[x], *b = plans[y];
-    return (double)a->n * a->n * a->n * a->L > (double)b->n * b->n * b->n * b->L;
+    return (double)sh[x].n * sh[x].n * sh[x].n * sh[x].L > (double)sh[y].n * sh[y].n * sh[y].n * sh[y].L;
   });
   long long u = 0;
   L.segs.clear();
   for (int i : order) {  // prologue: B(i, 0, *)
     L.segs.push_back(ScanSeg{(int)u, SU_OMEGA, i, 0});
-    u += np_of(plans[i]) / BLOCK_ROWS;
+    u += np_of(sh[i].n) / BLOCK_ROWS;
   }
   L.npro = (int)L.segs.size();
   L.upro = (int)u;
-  // A step runs the instances in groups, each group's levels in lockstep.  A group gathers
-  // instances until its tiles per level fill two waves of the SMs, or until its operands (left and
-  // right slices, 8 NS np^2 bytes an instance) would pass 3/4 of L2: an instance's L terms then
-  // follow one another while its operands are still in L2, and each level has enough tiles to keep
-  // the SMs busy while the previous level's last state blocks finish.
-  int dev = 0, l2 = 0;
-  cudaGetDevice(&dev);
-  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 <= 0) l2 = 64 << 20;
-  const double budget = 0.75 * l2;
-  const long long wave2 = 2LL * fq_sm_count();
   u = 0;
-  for (size_t g0 = 0; g0 < order.size();) {
-    size_t g1 = g0;
-    double bytes = 0;
-    long long tiles = 0;
-    while (g1 < order.size()) {
-      const fq_plan* q = plans[order[g1]];
-      const double b = 8.0 * scan_ns(q) * np_of(q) * np_of(q);
-      if (SCAN_GROUPS && g1 > g0 && (tiles >= wave2 || bytes + b > budget)) break;
-      bytes += b;
-      tiles += (long long)(np_of(q) / bn) * tiles_j_of(q);
-      ++g1;
-    }
-    int lmax = 0;
-    for (size_t k = g0; k < g1; ++k) lmax = std::max(lmax, plans[order[k]]->L);
-    for (int p = 0; p < lmax; ++p)
-      for (size_t k = g0; k < g1; ++k) {
-        const int i = order[k];
-        const fq_plan* q = plans[i];
-        if (p >= q->L) continue;
-        L.segs.push_back(ScanSeg{(int)u, SU_TERM, i, p});
-        u += (long long)(np_of(q) / bn) * tiles_j_of(q);
-        // Omega~_{m+1}'s blocks in L - 1 shares after the levels 1 .. L - 1 (after level 0 when
-        // L = 1): the epilogue warps' extra work spreads over the step instead of piling up
-        const int shares = std::max(1, q->L - 1), c = std::max(0, p - 1), nb = np_of(q) / BLOCK_ROWS;
-        if (p >= std::min(1, q->L - 1)) {
-          const int b0 = (int)((long long)c * nb / shares), b1 = (int)((long long)(c + 1) * nb / shares);
-          if (b1 > b0) L.segs.push_back(ScanSeg{(int)u, SU_OMEGA, i, b0});
-          u += b1 - b0;
-        }
-        if (u > INT_MAX / 4) return false;
+  int lmax = 0;
+  for (const ScanShape& q : sh) lmax = std::max(lmax, q.L);
+  for (int p = 0; p < lmax; ++p)
+    for (int i : order) {
+      const ScanShape& q = sh[i];
+      if (p >= q.L) continue;
+      L.segs.push_back(ScanSeg{(int)u, SU_TERM, i, p});
+      u += (long long)(np_of(q.n) / bn) * tiles_j_of(q.n);
+      const int shares = std::max(1, q.L - 1), c = std::max(0, p - 1), nb = np_of(q.n) / BLOCK_ROWS;
+      if (p >= std::min(1, q.L - 1)) {
+        const int b0 = (int)((long long)c * nb / shares), b1 = (int)((long long)(c + 1) * nb / shares);
+        if (b1 > b0) L.segs.push_back(ScanSeg{(int)u, SU_OMEGA, i, b0});
+        u += b1 - b0;
       }
-    g0 = g1;
-  }
+      if (u > INT_MAX / 4) return false;
+    }
   L.nstep = (int)L.segs.size() - L.npro;
   L.ustep = (int)u;
   u = 0;
   for (int i : order) {
     L.segs.push_back(ScanSeg{(int)u, SU_STORE, i, 0});
-    u += (plans[i]->n + BLOCK_ROWS - 1) / BLOCK_ROWS;
+    u += (sh[i].n + BLOCK_ROWS - 1) / BLOCK_ROWS;
   }
   L.nend = (int)L.segs.size() - L.npro - L.nstep;
   L.uend = (int)u;
-  if ((long long)L.upro + (long long)M * L.ustep + L.uend > INT_MAX - 4096) return false;
+  if ((long long)L.upro + (long long)steps * L.ustep + L.uend > INT_MAX - 4096) return false;
   size_t off = 0;
   L.inst = off;
   off += up256(sizeof(ScanInst) * count);
@@ -667,14 +650,14 @@ bool scan_layout(fq_plan* const* plans, int count, int bn, ScanLayout& L) {
   size_t words = 2;  // next, abort
   for (int i = 0; i < count; ++i) {
     L.termcnt[i] = words;
-    words += (size_t)plans[i]->L * tiles_j_of(plans[i]) + 2;
+    words += (size_t)sh[i].L * tiles_j_of(sh[i].n) + 2;
   }
   L.cnt = off;
   L.cnt_words = words;
   off += up256(sizeof(unsigned int) * words);
   L.omega2.resize(count);
   for (int i = 0; i < count; ++i) {
-    const size_t slices = (size_t)scan_ns(plans[i]) * np_of(plans[i]) * np_of(plans[i]);
+    const size_t slices = (size_t)sh[i].ns * np_of(sh[i].n) * np_of(sh[i].n);
     L.omega2[i] = off;
     off += 2 * up256(sizeof(__nv_bfloat16) * slices);
   }
@@ -701,7 +684,7 @@ fq_status scan_capture(fq_plan* const* plans, int count, void* const* d_U, char*
     I.L = p->L;
     I.steps = p->steps;
     I.tiles_i = w.np / BN;
-    I.tiles_j = tiles_j_of(p);
+    I.tiles_j = tiles_j_of(p->n);
     I.nk = (p->n + BKE - 1) / BKE;  // the operands' columns beyond N are zero
     I.nblk = w.np / BLOCK_ROWS;
     I.bstride = w.bstride;
@@ -785,13 +768,13 @@ int fq_scan_eligible(fq_plan* const* plans, int count) {
       return 0;
   }
   ScanLayout lay;
-  return scan_layout(plans, count, scan_bn(plans, count), lay) ? 1 : 0;
+  return scan_layout(shapes_of(plans, count), plans[0]->steps, scan_bn(plans, count), lay) ? 1 : 0;
 }
 
 size_t fq_scan_extra_bytes(fq_plan* const* plans, int count) {
   if (!fq_scan_eligible(plans, count)) return 0;
   ScanLayout lay;
-  scan_layout(plans, count, scan_bn(plans, count), lay);
+  scan_layout(shapes_of(plans, count), plans[0]->steps, scan_bn(plans, count), lay);
   return lay.total;
 }
 
@@ -805,7 +788,7 @@ fq_status fq_scan_graph(fq_plan* const* plans, int count, void* const* d_U, void
   }
   const int bn = scan_bn(plans, count);
   ScanLayout lay;
-  scan_layout(plans, count, bn, lay);
+  scan_layout(shapes_of(plans, count), plans[0]->steps, bn, lay);
   char* base = (char*)ws;
   char* extra = base + extra_off;
   const bool x6 = plans[0]->precision == FQ_BF16X6;
@@ -814,4 +797,30 @@ fq_status fq_scan_graph(fq_plan* const* plans, int count, void* const* d_U, void
                      : scan_capture<3, 64, 32>(plans, count, d_U, base, off, extra, lay, graph);
   return bn == 128 ? scan_capture<2, 128, 32>(plans, count, d_U, base, off, extra, lay, graph)
                    : scan_capture<2, 64, 64>(plans, count, d_U, base, off, extra, lay, graph);
+}
+
+// Test hook, outside the public header: the unit table of a scan of `count` instances (sizes n[i],
+// series lengths L[i]) over `steps` steps with tiles of bn rows of Omega~, as (begin, type, instance,
+// p) quadruples in seg (capacity cap quadruples): prologue, one step, end; counts receives the
+// segments and units of each part [npro, nstep, nend, upro, ustep, uend].  Returns the number of
+// segments, or -1 (arguments, capacity, or a unit count past the 32-bit counter).  Host only.
+extern "C" int fq_scan_table(int count, const int* n, const int* L, int steps, int bn, int* seg, int cap,
+                             int* counts) {
+  if (count < 1 || !n || !L || !seg || !counts || steps < 1 || (bn != 64 && bn != 128)) return -1;
+  std::vector<ScanShape> sh(count);
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 1 || L[i] < 1 || L[i] > SCAN_MAXL) return -1;
+    sh[i] = ScanShape{n[i], L[i], 2};
+  }
+  ScanLayout lay;
+  if (!scan_layout(sh, steps, bn, lay) || (int)lay.segs.size() > cap) return -1;
+  for (size_t k = 0; k < lay.segs.size(); ++k) {
+    seg[4 * k] = lay.segs[k].begin;
+    seg[4 * k + 1] = lay.segs[k].type;
+    seg[4 * k + 2] = lay.segs[k].inst;
+    seg[4 * k + 3] = lay.segs[k].p;
+  }
+  const int c[6] = {lay.npro, lay.nstep, lay.nend, lay.upro, lay.ustep, lay.uend};
+  for (int k = 0; k < 6; ++k) counts[k] = c[k];
+  return (int)lay.segs.size();
 }
