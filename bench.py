@@ -92,7 +92,7 @@ def parse():
                          "(adjoint only); dimer: ozaki (band kernel on the tensor cores, FP64-level; default), "
                          "df32 (double-float tiled, FP64-level) or fp32 (resident)")
     ap.add_argument("--ncu-case", choices=["resident", "stream", "split", "tile", "dfl", "band", "adjoint", "ozaki",
-                                           "dense-resident", "ozaki-grad"],
+                                           "dense-resident", "ozaki-grad", "scan"],
                     default=None,
                     help="run one small capture case of a kernel twice and exit (for ncu --set full)")
     return ap.parse_args()
@@ -112,7 +112,9 @@ def run_ncu_case(case):
     ozaki-grad: the same in FP64 emulation (FQ_OZAKI);
     ozaki:    dense GOE N = 2048 (seeds 3, 4; A = 2, omega = 2, M = 64), FQ_OZAKI terms of step 0 on
               the identity (0.25 GB of slices, 0.2 GB of FP64 states);
-    dense-resident: GOE N = 64 (seeds 1, 2), M = 200, the FP64 resident chain (4 launches)."""
+    dense-resident: GOE N = 64 (seeds 1, 2), M = 200, the FP64 resident chain (4 launches);
+    scan:     the batched scan's recipe at 6 instances of N in [256, 1024] (seed 5), M = 8, BF16X3
+              with 128-row tiles, as one persistent launch (about 0.4 GB of workspace)."""
     import math
     import torch
     import floquet_inputs as fi
@@ -142,6 +144,23 @@ def run_ncu_case(case):
             fq.floquet_propagate(plan.handle, x0, x, n, 0, 1 if case == "ozaki" else m.steps, ws)
         torch.cuda.synchronize()
         print(f"ncu case {case}: status {plan.check_status()}, L = {plan.info.L}")
+        return
+    if case == "scan":
+        insts = fi.batch_scan(count=6, seed=5, n_lo=256, n_hi=1024)
+        plans = [fq.Plan.dense(fi.goe(s.n, s.seed_h0), fi.goe(s.n, s.seed_h1), omega=s.omega, f_ac=s.amplitude,
+                               steps=8, precision=fq.FQ_BF16X3, tile_n=128) for s in insts]
+        outs = [torch.empty((p.n, p.n), dtype=torch.complex128, device="cuda") for p in plans]
+        handles = [p.handle for p in plans]
+        ws = fq.workspace(fq.floquet_batch_workspace_size(handles))
+        b = fq.floquet_batch_create(handles, outs, ws, 0)
+        try:
+            for _ in range(2):
+                fq.floquet_batch_launch(b)
+            torch.cuda.synchronize()
+        finally:
+            fq.floquet_batch_destroy(b)
+        print(f"ncu case scan: N = {[p.n for p in plans]}, L = {[p.info.L for p in plans]}, "
+              f"status {[p.check_status() for p in plans]}")
         return
     if case == "split":
         m = fi.config_goe4096()
