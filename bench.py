@@ -438,6 +438,35 @@ def dimer_roofline(path, n, steps, L, seconds_per_launch, per_launch_units):
             "peak_note": path["peak_note"]}
 
 
+def measured_fp32_rate(fq, torch, stream):
+    """The GPU's FP32 multiply-add rate, measured live by the library's probe (4 CTAs of 256 threads
+    per SM, independent chains): CUDA events around 5 launches after 3 warm-ups, packed (FFMA2) and
+    scalar (FFMA), in TFLOP/s."""
+    out = torch.empty(4 * SM_COUNT * 256, dtype=torch.float32, device="cuda")
+    rates = {}
+    for packed, key in ((True, "ffma2"), (False, "ffma")):
+        for _ in range(3):
+            fq.floquet_probe_fp32(packed, 16384, out, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = sum(fq.floquet_probe_fp32(packed, 16384, out, stream) for _ in range(5))
+        e1.record(stream)
+        e1.synchronize()
+        rates[key] = flops / (e0.elapsed_time(e1) / 1e3) / 1e12
+    return rates
+
+
+def with_measured_fp32(roof, rates):
+    """The FP32 roofline entry with the live-measured FP32 rate beside the derived peak."""
+    roof = dict(roof)
+    roof["peak_measured"] = rates["ffma2"]
+    roof["peak_measured_scalar"] = rates["ffma"]
+    roof["frac_of_measured"] = roof["achieved"] / rates["ffma2"]
+    roof["peak_measured_note"] = ("FP32 multiply-add rate of floquet_probe_fp32 (packed FFMA2; scalar FFMA "
+                                  "beside it), CUDA events over 5 launches in this run")
+    return roof
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -553,10 +582,11 @@ def run_ours(args):
         avg32 = kt32[1] / 1000.0 / kt32[0] if kt32[0] else statistics.mean(ps32)
         fp32 = {"value": v32, "unit": "U_T/s", "ms_per_step": 1000.0 * tot32 / args.fp32_steps,
                 "steps": args.fp32_steps, "dtype": "f32", "per_step_s": ps32, "clocks": clk32,
-                "roofline": dict(dimer_roofline(DIMER_PATHS["fp32"], n, d.steps, L, avg32,
-                                                float(n) * n * d.steps * L / (world if sharded else 1)),
-                                 traffic=resident_traffic(n, d.steps, n / (world if sharded else 1)),
-                                 traffic_note=RES_TRAFFIC_NOTE)}
+                "roofline": with_measured_fp32(
+                    dict(dimer_roofline(DIMER_PATHS["fp32"], n, d.steps, L, avg32,
+                                        float(n) * n * d.steps * L / (world if sharded else 1)),
+                         traffic=resident_traffic(n, d.steps, n / (world if sharded else 1)),
+                         traffic_note=RES_TRAFFIC_NOTE), measured_fp32_rate(fq, torch, stream))}
         p32.close()
 
     if rank != 0:
@@ -571,6 +601,7 @@ def run_ours(args):
         roofline = dimer_roofline(path, n, d.steps, L, kavg, float(n) * n * d.steps * L / (world if sharded else 1))
         roofline["traffic"] = resident_traffic(n, d.steps, n / (world if sharded else 1))
         roofline["traffic_note"] = RES_TRAFFIC_NOTE
+        roofline = with_measured_fp32(roofline, measured_fp32_rate(fq, torch, stream))
     else:  # one launch per step: units of one launch over the launch's mean duration
         per_launch = float(n) * n * L / (world if sharded else 1)
         kavg = kms / 1000.0 / klaunches if klaunches else avg / d.steps

@@ -370,6 +370,16 @@ fq_status floquet_check_status(fq_plan* plan, void* stream);
  * and returns.  The next floquet_check_status reports FQ_ETIMEOUT; the context stays usable. */
 fq_status floquet_selftest_wait(fq_plan* plan, int64_t cycles, void* stream);
 
+/* FP32 rate probe, a measurement aid (the paper has no counterpart): one launch of min(4 x SMs,
+ * out_len / 256) CTAs of 256 threads, each thread running independent chains of `iters` fused
+ * multiply-adds, packed over lane pairs (FFMA2, packed != 0) or scalar, enqueued on `stream`.
+ * d_out: caller-owned device buffer of out_len floats (one sum per thread is written).  *flops
+ * receives the launch's flop count (2 per multiply-add), so a caller timing the launch with CUDA
+ * events gets the GPU's sustained FP32 rate.  FQ_EINVAL for iters < 1, NULL pointers or
+ * out_len < 256. */
+fq_status floquet_probe_fp32(int32_t packed, int32_t iters, float* d_out, int64_t out_len, void* stream,
+                             double* flops);
+
 /* Quasienergies (Eq. 5) and Floquet states of U_T on the host, outside the timed propagation:
  * U = N x N complex128 host array, row-major, U[i][j] = <i|U_T|j> (as floquet_build_UT writes it).
  * eps_out: N doubles, eps_mu = theta_mu / T with theta_mu = -arg(lambda_mu) folded into

@@ -71,6 +71,7 @@ _SIGS = {
     "floquet_grad_workspace_size": (_sz, [_vp]),
     "floquet_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "floquet_selftest_wait": (ctypes.c_int, [_vp, ctypes.c_int64, _vp]),
+    "floquet_probe_fp32": (ctypes.c_int, [_i32, _i32, _vp, ctypes.c_int64, _vp, _dp]),
     "floquet_quasienergies": (ctypes.c_int, [_vp, _i32, ctypes.c_double, _dp, _vp]),
     "floquet_check_status": (ctypes.c_int, [_vp, _vp]),
     "floquet_build_UT_static": (ctypes.c_int, [ctypes.POINTER(fq_problem), _vp, _vp]),
@@ -383,6 +384,17 @@ def floquet_quasienergies(u, period: float, states: bool = True):
 
 def floquet_selftest_wait(plan: int, cycles: int, stream=None) -> None:
     _check(lib.floquet_selftest_wait(_vp(plan), int(cycles), _stream(stream)), "floquet_selftest_wait")
+
+
+def floquet_probe_fp32(packed: bool, iters: int, out, stream=None) -> float:
+    """Enqueues the FP32 rate probe on `stream` (out: float32 CUDA tensor of >= 256 elements);
+    returns the launch's flop count."""
+    w = "floquet_probe_fp32"
+    import torch
+    fl = ctypes.c_double()
+    _check(lib.floquet_probe_fp32(1 if packed else 0, int(iters), _dev(out, torch.float32, 256, "out", w),
+                                  out.numel(), _stream(stream), ctypes.byref(fl)), w)
+    return fl.value
 
 
 def floquet_last_error() -> str:

@@ -697,6 +697,17 @@ fq_status floquet_selftest_wait(fq_plan* p, int64_t cycles, void* stream) {
   return cuda_ok(cudaGetLastError(), "wait probe");
 }
 
+fq_status floquet_probe_fp32(int32_t packed, int32_t iters, float* d_out, int64_t out_len, void* stream,
+                             double* flops) {
+  const int64_t blocks = std::min<int64_t>(4LL * fq_sm_count(), out_len / 256);
+  if (!d_out || !flops || iters < 1 || blocks < 1) {
+    fq_set_error("floquet_probe_fp32: needs iters >= 1, flops and a device buffer of >= 256 floats");
+    return FQ_EINVAL;
+  }
+  *flops = fq_launch_fp32_probe(packed != 0, iters, d_out, (int)blocks, (cudaStream_t)stream);
+  return cuda_ok(cudaGetLastError(), "FP32 probe");
+}
+
 fq_status floquet_check_status(fq_plan* p, void* stream) {
   if (!p) { fq_set_error("NULL plan"); return FQ_EINVAL; }
   unsigned int v = 0;

@@ -239,6 +239,8 @@ size_t fq_split_workspace(const fq_plan* p, int nc, void* base, void* out);
 // batched scan as one persistent launch (scan.cu): whether the plans qualify, the bytes it needs
 // beyond the plans' own workspaces, and the graph (counter reset + the launch) writing d_U[i];
 // plan i's workspace at ws + off[i], the scan's region at ws + extra_off
+// FP32 rate probe (kernels.cu): one launch of `blocks` CTAs of 256 threads; returns its flop count
+double fq_launch_fp32_probe(int packed, int iters, float* out, int blocks, cudaStream_t s);
 int fq_scan_eligible(fq_plan* const* plans, int count);
 size_t fq_scan_extra_bytes(fq_plan* const* plans, int count);
 fq_status fq_scan_graph(fq_plan* const* plans, int count, void* const* d_U, void* ws, const size_t* off,

@@ -713,6 +713,45 @@ void fq_launch_wait_probe(unsigned int* status, long long cycles, cudaStream_t s
   k_wait_probe<<<1, 1, 0, s>>>(status, cycles);
 }
 
+namespace {
+// FP32 rate probe: each thread runs independent chains of `iters` fused multiply-adds, 8 chains
+// packed over lane pairs (FFMA2) or 16 scalar chains, and writes their sum so no work is dropped.
+template <bool PACKED>
+__global__ void __launch_bounds__(256) k_fp32_probe(float* out, int iters, float a, float b) {
+  const float s0 = 1e-3f * (float)(threadIdx.x & 31);
+  float t = 0.f;
+  if (PACKED) {
+    float2 acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = make_float2(s0 + k, s0 - k);
+    const float2 A = make_float2(a, a), B = make_float2(b, b);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] = __ffma2_rn(acc[k], A, B);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += acc[k].x + acc[k].y;
+  } else {
+    float acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = s0 + k;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc[k] = fmaf(acc[k], a, b);
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) t += acc[k];
+  }
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+}  // namespace
+
+double fq_launch_fp32_probe(int packed, int iters, float* out, int blocks, cudaStream_t s) {
+  if (packed) k_fp32_probe<true><<<blocks, 256, 0, s>>>(out, iters, 0.999f, 1e-3f);
+  else k_fp32_probe<false><<<blocks, 256, 0, s>>>(out, iters, 0.999f, 1e-3f);
+  return (double)blocks * 256 * iters * 16 * 2;  // 16 multiply-adds of 2 flop per thread and iteration
+}
+
 void fq_launch_defect(const double* u, int n, const int32_t* cols, int k, double* partial, cudaStream_t s) {
   dim3 g((n + 255) / 256, (k + 15) / 16);
   k_defect<<<g, 256, 0, s>>>((const double2*)u, n, cols, k, partial);
