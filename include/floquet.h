@@ -150,6 +150,9 @@ typedef struct fq_problem {
   int32_t cheb_terms;       /* > 0: a fixed number L of Chebyshev products per step (the paper's
                                timing runs use L = 50, Table 1), overriding cheb_tol; at most
                                1024 and at least the R-dependent minimum (L > R); 0: from cheb_tol */
+  int32_t tile_k;           /* split path, FQ_BF16X3 with 64-wide tiles: K elements a pipeline
+                               stage loads, 32 (four stages) or 64 (two); 0 = 64 until
+                               floquet_autotune picks one; other tiles take 32 */
 } fq_problem;
 
 typedef struct fq_plan fq_plan;
@@ -333,9 +336,9 @@ fq_status floquet_build_UT_static(const fq_problem* problem, void* d_U, void* st
  *    instance the blocks of Omega~_m's slices (Eqs. 11 and 14), and per step, term and output
  *    tile the Chebyshev term of Eq. 10 (state blocks of 128 columns advance independently, each
  *    unit waiting, with a bounded spin, only for the units it reads).  The tile width is the one
- *    the plans' own widths favour (tile_n or floquet_autotune), weighted by N^3 M L; each U_T then
- *    equals the plan's own floquet_build_UT bit for bit when the widths agree.  Other plans fall
- *    back to 8 lanes.
+ *    the plans' own widths favour (tile_n or floquet_autotune), weighted by N^3 M L, with the
+ *    width's default K stage; each U_T then equals the plan's own floquet_build_UT bit for bit
+ *    when the tile shapes agree.  Other plans fall back to 8 lanes.
  *  - lanes = 1..32: floquet_build_UT of every plan captured on `lanes` concurrent graph
  *    branches, assigned longest-first by their cost N^3 M L.
  *  - A wait that gives up marks every plan's status word FQ_BIT_TIMEOUT (floquet_check_status
@@ -353,10 +356,13 @@ fq_status floquet_batch_create(fq_batch** batch, fq_plan* const* plans, int32_t 
 fq_status floquet_batch_launch(fq_batch* batch, void* stream);
 void floquet_batch_destroy(fq_batch* batch);
 
-/* Autotuner for the split-precision dense path: times each tile width of the tensor-core term
+/* Autotuner for the split-precision dense path: times each tile shape of the tensor-core term
  * kernel on two steps of this plan (states: the identity block) and keeps the fastest for the
- * plan's later calls.  d_ws as for floquet_build_UT.  Synchronises `stream`; no-op (FQ_OK) for
- * other paths.  *tile_n receives the chosen width (NULL allowed). */
+ * plan's later calls.  Shapes: output widths 64 and 128 (K stages of 32 elements, 64 for 64-wide
+ * BF16X3 tiles), and for BF16X3 also 64-wide tiles with 32-element K stages; each runs as many
+ * stages as fit in shared memory.  d_ws as for floquet_build_UT.  Synchronises `stream`; no-op
+ * (FQ_OK) for other paths.  *tile_n receives the chosen width (NULL allowed); on an error the plan
+ * keeps the shape it had. */
 fq_status floquet_autotune(fq_plan* plan, void* d_ws, size_t ws_bytes, void* stream, int32_t* tile_n);
 
 /* Synchronises `stream`; returns FQ_ETIMEOUT if a bounded device wait of this plan's kernels

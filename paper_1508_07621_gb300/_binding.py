@@ -32,7 +32,7 @@ class fq_problem(ctypes.Structure):
                 ("phi0", ctypes.c_double), ("f_steps", _dp), ("cheb_tol", ctypes.c_double),
                 ("e_min", ctypes.c_double), ("e_max", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("checkpoint_stride", ctypes.c_int32), ("kernel", ctypes.c_int32), ("tile_n", ctypes.c_int32),
-                ("magnus_order", ctypes.c_int32), ("cheb_terms", ctypes.c_int32)]
+                ("magnus_order", ctypes.c_int32), ("cheb_terms", ctypes.c_int32), ("tile_k", ctypes.c_int32)]
 
 
 class fq_plan_info(ctypes.Structure):
@@ -164,7 +164,7 @@ def _darr(a):
 def make_problem(n, fmt, h0, h1, period, steps, h0_off=None, drive_kind=FQ_DRIVE_COS, f_dc=0.0, f_ac=0.0,
                  omega=1.0, phi0=0.0, f_steps=None, cheb_tol=0.0, e_min=0.0, e_max=0.0,
                  precision=FQ_FP64, checkpoint_stride=0, kernel=FQ_KERNEL_AUTO, tile_n=0, magnus_order=0,
-                 cheb_terms=0):
+                 cheb_terms=0, tile_k=0):
     """Builds an fq_problem; returns (struct, keepalive) - the host arrays must outlive the call."""
     a0, p0 = _darr(h0)
     a1, p1 = _darr(h1)
@@ -177,7 +177,7 @@ def make_problem(n, fmt, h0, h1, period, steps, h0_off=None, drive_kind=FQ_DRIVE
         if arr is not None and arr.size < need:
             raise ValueError(f"make_problem: {what} has {arr.size} values, the problem needs {need}")
     prob = fq_problem(n, fmt, p0, po, p1, period, steps, drive_kind, f_dc, f_ac, omega, phi0, pf, cheb_tol,
-                      e_min, e_max, precision, checkpoint_stride, kernel, tile_n, magnus_order, cheb_terms)
+                      e_min, e_max, precision, checkpoint_stride, kernel, tile_n, magnus_order, cheb_terms, tile_k)
     return prob, (a0, a1, ao, af)
 
 

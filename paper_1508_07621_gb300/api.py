@@ -26,12 +26,13 @@ class Plan:
     @classmethod
     def dense(cls, h0, h1, *, omega, f_ac, steps, f_dc=0.0, phi0=0.0, period=None, precision=B.FQ_FP64,
               cheb_tol=0.0, e_min=0.0, e_max=0.0, tile_n=0, magnus_order=0, kernel=B.FQ_KERNEL_AUTO,
-              cheb_terms=0):
+              cheb_terms=0, tile_k=0):
         n = h0.shape[0]
         T = period if period is not None else 2.0 * math.pi / omega
         prob, keep = B.make_problem(n, B.FQ_DENSE, h0, h1, T, steps, f_dc=f_dc, f_ac=f_ac, omega=omega,
                                     phi0=phi0, precision=precision, cheb_tol=cheb_tol, e_min=e_min, e_max=e_max,
-                                    tile_n=tile_n, magnus_order=magnus_order, kernel=kernel, cheb_terms=cheb_terms)
+                                    tile_n=tile_n, magnus_order=magnus_order, kernel=kernel, cheb_terms=cheb_terms,
+                                    tile_k=tile_k)
         return cls(prob, keep)
 
     @classmethod

@@ -242,11 +242,14 @@ fq_status fq_split_propagate(fq_plan* p, const double* x0, double* x, int nc, in
   if (p->precision == FQ_BF16X6)
     return wide ? run_split<3, 128, 32>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s)
                 : run_split<3, 64, 32>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s);
-  return wide ? run_split<2, 128, 32>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s)
-              : run_split<2, 64, 64>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s);
+  if (wide) return run_split<2, 128, 32>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s);
+  return p->tile_k == 32 ? run_split<2, 64, 32>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s)
+                         : run_split<2, 64, 64>(p, x0, x, nc, m_begin, m_end, identity, transpose_out, ws, s);
 }
 
-// Times each tile width on two steps of the identity block and keeps the fastest.
+// Times each tile shape on two steps of the identity block and keeps the fastest: output widths
+// 64 and 128, and for 64-wide BF16X3 tiles K stages of 64 or 32 elements (two stages of 96 KB or
+// four of 48 KB); each shape runs as many stages as fit in shared memory.
 static fq_status floquet_autotune_body(fq_plan* p, void* ws, size_t bytes, void* stream, int32_t* tile_n) {
   if (!p) {
     fq_set_error("floquet_autotune: NULL plan");
@@ -262,17 +265,22 @@ static fq_status floquet_autotune_body(fq_plan* p, void* ws, size_t bytes, void*
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int steps = p->steps < 2 ? p->steps : 2;
-  const int cand[2] = {64, 128};
+  struct Shape {
+    int n, k;
+  };
+  std::vector<Shape> cand = {{64, 0}, {128, 0}};
+  if (p->precision != FQ_BF16X6) cand.push_back({64, 32});
   float best = 1e30f;
-  int pick = 64;
-  const int before = p->tile_n;
+  Shape pick = cand[0];
+  const Shape before{p->tile_n, p->tile_k};
   cudaEvent_t a = nullptr, b = nullptr;
   cudaError_t e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
   fq_status st = e == cudaSuccess ? FQ_OK : fq_cuda_fail(e, "autotune events");
-  for (int c : cand) {
+  for (const Shape& c : cand) {
     if (st != FQ_OK) break;
-    p->tile_n = c;
+    p->tile_n = c.n;
+    p->tile_k = c.k;
     st = fq_split_propagate(p, nullptr, nullptr, p->n, 0, steps, 1, 0, ws, s);  // warm-up
     if (st != FQ_OK) break;
     cudaEventRecord(a, s);
@@ -292,13 +300,10 @@ static fq_status floquet_autotune_body(fq_plan* p, void* ws, size_t bytes, void*
   }
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
-  if (st != FQ_OK) {  // the plan keeps the width it had
-    p->tile_n = before;
-    return st;
-  }
-  p->tile_n = pick;
-  if (tile_n) *tile_n = pick;
-  return FQ_OK;
+  p->tile_n = st == FQ_OK ? pick.n : before.n;  // on failure the plan keeps the shape it had
+  p->tile_k = st == FQ_OK ? pick.k : before.k;
+  if (st == FQ_OK && tile_n) *tile_n = pick.n;
+  return st;
 }
 
 extern "C" fq_status floquet_autotune(fq_plan* p, void* ws, size_t bytes, void* stream, int32_t* tile_n) {

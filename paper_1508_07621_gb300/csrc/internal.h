@@ -67,6 +67,7 @@ struct fq_plan {
   std::vector<double> band6;
   double* d_cm = nullptr;      // K0 .. KK1: 8 matrices n*n after d_k (= K)
   int tile_n = 128;          // split path: output tile width of the tensor-core kernel (autotuned)
+  int tile_k = 0;            // split path, 64-wide BF16X3 tiles: K elements a stage (32 or 64; 0 = 64)
   int device = 0;
   // device copies (owned by the plan)
   double* d_h0 = nullptr;    // DENSE: n*n      TRIDIAG: diag n

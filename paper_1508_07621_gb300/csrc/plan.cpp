@@ -531,6 +531,11 @@ fq_status fq_host_plan(const fq_problem* p, fq_plan* plan, bool defer_dense_boun
     return FQ_EINVAL;
   }
   plan->tile_n = p->tile_n ? p->tile_n : 128;
+  if (p->tile_k != 0 && p->tile_k != 32 && p->tile_k != 64) {
+    fq_set_error("tile_k must be 0, 32 or 64 (got %d)", p->tile_k);
+    return FQ_EINVAL;
+  }
+  plan->tile_k = p->tile_k == 64 ? 0 : p->tile_k;
   if (p->kernel < FQ_KERNEL_AUTO || p->kernel > FQ_KERNEL_BAND) {
     fq_set_error("kernel must be one of FQ_KERNEL_AUTO .. FQ_KERNEL_BAND (got %d)", p->kernel);
     return FQ_EINVAL;

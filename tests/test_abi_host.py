@@ -130,7 +130,8 @@ def test_fixed_chebyshev_terms(fq):
 @pytest.mark.parametrize("case,status", [
     ("steps0", "FQ_EINVAL"), ("period0", "FQ_EINVAL"), ("format9", "FQ_EINVAL"), ("drive9", "FQ_EINVAL"),
     ("piecewise_without_f", "FQ_EINVAL"), ("order5", "FQ_EINVAL"), ("order6_tridiag_fp32", "FQ_EUNSUPPORTED"),
-    ("order6_piecewise", "FQ_EUNSUPPORTED"), ("tile96", "FQ_EINVAL"), ("dense_fp32", "FQ_EUNSUPPORTED"),
+    ("order6_piecewise", "FQ_EUNSUPPORTED"), ("tile96", "FQ_EINVAL"), ("tilek48", "FQ_EINVAL"),
+    ("dense_fp32", "FQ_EUNSUPPORTED"),
     ("tridiag_x6", "FQ_EUNSUPPORTED"), ("kernel9", "FQ_EINVAL")])
 def test_problem_validation(fq, case, status):
     """Every rejected problem fails in host planning with its status and a message, before any
@@ -159,6 +160,8 @@ def test_problem_validation(fq, case, status):
                                      f_steps=np.ones(4), magnus_order=6)
     elif case == "tile96":
         prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, precision=fq.FQ_BF16X3, tile_n=96, **kw)
+    elif case == "tilek48":
+        prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, precision=fq.FQ_BF16X3, tile_k=48, **kw)
     elif case == "dense_fp32":
         prob, keep = fq.make_problem(n, fq.FQ_DENSE, g, g, 1.0, 4, precision=fq.FQ_FP32, **kw)
     elif case == "kernel9":

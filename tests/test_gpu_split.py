@@ -43,11 +43,14 @@ def cuda_c128(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).cuda()
 
 
-@pytest.mark.parametrize("prec,ns,tile", [(2, 2, 64), (3, 3, 64), (2, 2, 128), (3, 3, 128)])
-def test_split_goe64_build(fq, prec, ns, tile):
+SHAPES = [(2, 2, 64, 0), (2, 2, 64, 32), (3, 3, 64, 0), (2, 2, 128, 0), (3, 3, 128, 0)]  # (prec, NS, width, K stage)
+
+
+@pytest.mark.parametrize("prec,ns,tile,tk", SHAPES)
+def test_split_goe64_build(fq, prec, ns, tile, tk):
     m = fi.config_goe64()
     plan = fq.Plan.dense(m.h0, m.h1, omega=m.drive.omega, f_ac=m.drive.f_ac, steps=m.steps, precision=prec,
-                         tile_n=tile)
+                         tile_n=tile, tile_k=tk)
     U = plan.build_UT().cpu().numpy()
     assert plan.check_status() == fq.FQ_OK
     ref = o.build_ut_dense(m.h0, m.h1, o.plan_for_drive_dense(m.h0, m.h1, m.drive, m.steps))
@@ -57,8 +60,8 @@ def test_split_goe64_build(fq, prec, ns, tile):
     assert err <= tol
 
 
-@pytest.mark.parametrize("prec,ns,tile", [(2, 2, 64), (3, 3, 64), (2, 2, 128), (3, 3, 128)])
-def test_split_ragged_propagate(fq, prec, ns, tile):
+@pytest.mark.parametrize("prec,ns,tile,tk", SHAPES)
+def test_split_ragged_propagate(fq, prec, ns, tile, tk):
     """N = 200 (K' padded to 512, output tiles ragged), 37 states (one partial 128-row tile),
     steps 2..9 of 24, non-even drive."""
     n, M = 200, 24
@@ -67,7 +70,7 @@ def test_split_ragged_propagate(fq, prec, ns, tile):
     x0 = fi.ginibre(n, 1303)[:37]
     x0 /= np.linalg.norm(x0, axis=1, keepdims=True)
     plan = fq.Plan.dense(h0, h1, omega=drv.omega, f_ac=drv.f_ac, f_dc=drv.f_dc, phi0=drv.phi0, steps=M,
-                         precision=prec, tile_n=tile)
+                         precision=prec, tile_n=tile, tile_k=tk)
     X = plan.propagate(cuda_c128(x0), 2, 10).cpu().numpy()
     ref = o.propagate_dense(h0, h1, o.plan_for_drive_dense(h0, h1, drv, M), x0.T, 2, 10).T
     err = np.max(np.abs(X - ref))
