@@ -201,3 +201,8 @@ def test_table_rejects_what_the_kernel_cannot_run(lib):
     assert lib.fq_scan_table(1, one(100), one(33), 4, 128, segs, 16, counts) == -1   # L > 32
     assert lib.fq_scan_table(1, one(100), one(4), 4, 96, segs, 16, counts) == -1     # tile width
     assert lib.fq_scan_table(1, one(100), one(4), 4, 128, segs, 1, counts) == -1     # capacity
+    # 8320 units a step (16 x 16 tiles x 32 terms + 128 Omega~ blocks) over 10^6 steps: past the
+    # kernel's 32-bit unit counter
+    big = (ctypes.c_int * 1024)()
+    assert lib.fq_scan_table(1, one(2048), one(32), 10 ** 6, 128, big, 256, counts) == -1
+    assert lib.fq_scan_table(1, one(2048), one(32), 10 ** 5, 128, big, 256, counts) == 65
